@@ -1,0 +1,390 @@
+"""FP64 reference operations of the tokenizer hot path.
+
+TEST INFRASTRUCTURE ONLY: the oracle. Only ``tests/``, the smoke check and the
+benchmark's CPU-baseline leg may import this package; the product path never
+does, and this package imports nothing from the product.
+
+Every function is written from the definition it follows, cited beside it,
+in float64, without blocking or fusion. Where the paper is silent the reading
+used is stated in the docstring.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+def _conv_lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        lib = ctypes.CDLL(path)
+        dp = ctypes.POINTER(ctypes.c_double)
+        i = ctypes.c_int
+        lib.oracle_conv3d_fwd.argtypes = [dp, i, i, i, i, i, dp, dp, i, i, i, i, i, i, i, i, dp, i, i, i]
+        lib.oracle_conv3d_dgrad.argtypes = [dp, i, i, i, i, i, dp, i, i, i, i, i, i, i, dp, i, i, i, i]
+        lib.oracle_conv3d_wgrad.argtypes = [dp, i, i, i, i, i, dp, i, i, i, i, i, i, i, i, i, i, i, dp, dp]
+        lib.oracle_num_threads.restype = i
+        _lib = lib
+    return _lib
+
+
+def num_threads() -> int:
+    """Number of OpenMP threads the oracle's convolution runs on."""
+    return int(_conv_lib().oracle_num_threads())
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+PAD_REPLICATE = 0
+PAD_ZERO = 1
+
+
+def conv_out_shape(T, H, W, k, s):
+    """Output extent of the causal conv: T_out = floor((T-1)/st) + 1 (causal
+    left pad kt-1), H_out = floor((H + 2*((kh-1)//2) - kh)/sh) + 1."""
+    kt, kh, kw = k
+    st, sh, sw = s
+    To = (T - 1) // st + 1
+    Ho = (H + 2 * ((kh - 1) // 2) - kh) // sh + 1
+    Wo = (W + 2 * ((kw - 1) // 2) - kw) // sw + 1
+    return To, Ho, Wo
+
+
+def conv3d(x, w, b, stride=(1, 1, 1), pad_mode=PAD_REPLICATE):
+    """Causal 3D convolution (direct loops in C, FP64).
+
+    x (N,T,H,W,Cin), w (Cout,kt,kh,kw,Cin), b (Cout,) or None.
+    Follows the causal residual-block convolution of the tokenizer the paper
+    builds on (Sec. 1, C2; encoder f_phi / decoder g_theta of Sec. 2.4):
+    frames are padded only on the past side, so output frame t never reads a
+    frame later than t*st.
+    """
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    N, T, H, W, Cin = x.shape
+    Cout, kt, kh, kw, Cin2 = w.shape
+    assert Cin == Cin2, (x.shape, w.shape)
+    st, sh, sw = stride
+    To, Ho, Wo = conv_out_shape(T, H, W, (kt, kh, kw), stride)
+    y = np.empty((N, To, Ho, Wo, Cout), dtype=np.float64)
+    bb = None if b is None else np.ascontiguousarray(b, dtype=np.float64)
+    _conv_lib().oracle_conv3d_fwd(_p(x), N, T, H, W, Cin, _p(w), _p(bb) if bb is not None else None,
+                                  Cout, kt, kh, kw, st, sh, sw, int(pad_mode), _p(y), To, Ho, Wo)
+    return y
+
+
+def conv3d_dgrad(dy, w, x_shape, stride=(1, 1, 1), pad_mode=PAD_REPLICATE):
+    """Adjoint of :func:`conv3d` with respect to its input."""
+    dy = np.ascontiguousarray(dy, dtype=np.float64)
+    w = np.ascontiguousarray(w, dtype=np.float64)
+    N, To, Ho, Wo, Cout = dy.shape
+    _, kt, kh, kw, Cin = w.shape
+    _, T, H, W, _ = x_shape
+    dx = np.empty((N, T, H, W, Cin), dtype=np.float64)
+    st, sh, sw = stride
+    _conv_lib().oracle_conv3d_dgrad(_p(dy), N, To, Ho, Wo, Cout, _p(w), kt, kh, kw, st, sh, sw,
+                                    int(pad_mode), _p(dx), T, H, W, Cin)
+    return dx
+
+
+def conv3d_wgrad(dy, x, k, stride=(1, 1, 1), pad_mode=PAD_REPLICATE):
+    """Gradient of :func:`conv3d` with respect to its weights and bias."""
+    dy = np.ascontiguousarray(dy, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    N, To, Ho, Wo, Cout = dy.shape
+    _, T, H, W, Cin = x.shape
+    kt, kh, kw = k
+    dw = np.empty((Cout, kt, kh, kw, Cin), dtype=np.float64)
+    db = np.empty((Cout,), dtype=np.float64)
+    st, sh, sw = stride
+    _conv_lib().oracle_conv3d_wgrad(_p(dy), N, To, Ho, Wo, Cout, _p(x), T, H, W, Cin,
+                                    kt, kh, kw, st, sh, sw, int(pad_mode), _p(dw), _p(db))
+    return dw, db
+
+
+# --------------------------------------------------------------------------
+# GroupNorm + SiLU
+# --------------------------------------------------------------------------
+
+def gn_groups(C: int, groups: int = 32) -> int:
+    """Number of GroupNorm groups used for C channels: min(groups, C // 2).
+
+    Reading: the architecture asks for GroupNorm(32); for narrow layers
+    (C < 64) that would leave fewer than 2 channels per group, so the group
+    count is capped at C/2."""
+    return max(1, min(groups, C // 2))
+
+
+def group_norm_frames(x, groups, eps=1e-6, gamma=None, beta=None):
+    """GroupNorm with statistics per (sample, group, frame).
+
+    Reading: the tokenizer is causal (Sec. 1, C2; streaming per GoP, Sec. 4.2),
+    so a normalisation may not mix frames; statistics are taken over the
+    group's channels and the frame's H x W positions only. Two-pass:
+    mean, then the mean of squared deviations (biased variance).
+    """
+    x = np.asarray(x, dtype=np.float64)
+    N, T, H, W, C = x.shape
+    cg = C // groups
+    xg = x.reshape(N, T, H * W, groups, cg)
+    mean = xg.mean(axis=(2, 4), keepdims=True)
+    var = ((xg - mean) ** 2).mean(axis=(2, 4), keepdims=True)
+    y = ((xg - mean) / np.sqrt(var + eps)).reshape(N, T, H, W, C)
+    if gamma is not None:
+        y = y * np.asarray(gamma, dtype=np.float64)
+    if beta is not None:
+        y = y + np.asarray(beta, dtype=np.float64)
+    return y
+
+
+def silu(x):
+    """SiLU(x) = x * sigmoid(x) = x / (1 + exp(-x))."""
+    x = np.asarray(x, dtype=np.float64)
+    return x / (1.0 + np.exp(-x))
+
+
+# --------------------------------------------------------------------------
+# Finite scalar quantisation (FSQ)
+# --------------------------------------------------------------------------
+
+FSQ_EPS = 1e-3
+
+
+def fsq_constants(levels):
+    """Per-channel FSQ constants, from the FSQ method (Mentzer et al., 2023):
+    half-range h = (L-1)(1-eps)/2, offset o = 0.5 for even L else 0,
+    shift s = atanh(o/h) (so that z = 0 maps to the code 0),
+    half-width floor(L/2), and the mixed-radix basis B_i = prod_{j<i} L_j
+    (channel 0 least significant)."""
+    L = np.asarray(levels, dtype=np.float64)
+    h = (L - 1.0) * (1.0 - FSQ_EPS) / 2.0
+    o = np.where(np.asarray(levels) % 2 == 0, 0.5, 0.0)
+    s = np.arctanh(o / h)
+    hw = np.asarray(levels, dtype=np.int64) // 2
+    basis = np.concatenate([[1], np.cumprod(np.asarray(levels, dtype=np.int64))[:-1]])
+    return h, o, s, hw, basis
+
+
+def fsq_bound(z, levels):
+    """b_i = tanh(z_i + s_i) * h_i - o_i (FP64)."""
+    h, o, s, _, _ = fsq_constants(levels)
+    z = np.asarray(z, dtype=np.float64)
+    return np.tanh(z + s) * h - o
+
+
+def fsq_quantize(z, levels):
+    """Quantise latent vectors z (..., len(levels)) to integer token indices.
+
+    The token matrix the paper transmits (Sec. 4.3, Sec. 6.2) holds one index
+    per latent position. Steps: bound, round half to even, digit
+    d_i = q_i + floor(L_i/2) in [0, L_i), index = sum_i d_i * B_i,
+    code_i = q_i / floor(L_i/2) in [-1, 1].
+    Returns (idx int64, codes float64, bound float64).
+    """
+    _, _, _, hw, basis = fsq_constants(levels)
+    b = fsq_bound(z, levels)
+    q = np.rint(b)  # numpy rint rounds half to even
+    d = (q + hw).astype(np.int64)
+    idx = (d * basis).sum(axis=-1)
+    codes = q / hw
+    return idx, codes, b
+
+
+def fsq_index_to_digits(idx, levels):
+    """Mixed-radix decomposition of token indices into per-channel digits."""
+    idx = np.asarray(idx, dtype=np.int64)
+    L = np.asarray(levels, dtype=np.int64)
+    _, _, _, _, basis = fsq_constants(levels)
+    return (idx[..., None] // basis) % L
+
+
+def fsq_dequantize(idx, levels):
+    """Token indices back to code vectors: code_i = (d_i - floor(L_i/2)) / floor(L_i/2)."""
+    _, _, _, hw, _ = fsq_constants(levels)
+    d = fsq_index_to_digits(idx, levels)
+    return (d - hw) / hw
+
+
+def fsq_zero_index(levels) -> int:
+    """Index of the all-zero code vector (digit floor(L_i/2) on every channel).
+
+    The receiver fills dropped tokens and lost rows with zeros (Sec. 6.2;
+    Appendix A.2); a zero code vector is this index."""
+    _, _, _, hw, basis = fsq_constants(levels)
+    return int((hw * basis).sum())
+
+
+# --------------------------------------------------------------------------
+# Counter-based random numbers and packet-drop token masking
+# --------------------------------------------------------------------------
+
+_M = np.uint64(0xFFFFFFFF)
+PHILOX_M0 = np.uint64(0xD2511F53)
+PHILOX_M1 = np.uint64(0xCD9E8D57)
+PHILOX_W0 = np.uint64(0x9E3779B9)
+PHILOX_W1 = np.uint64(0xBB67AE85)
+
+
+def philox4x32_10(c0, c1, c2, c3, k0, k1):
+    """Philox-4x32 with 10 rounds (Salmon, Moraes, Dror, Shaw, SC'11).
+
+    Each round: (hi0, lo0) = M0 * c0, (hi1, lo1) = M1 * c2 (32x32 -> 64-bit
+    products), new counter = (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0); the key
+    is bumped by the Weyl constants (W0, W1) between rounds. Inputs are
+    arrays (or scalars) of values < 2^32; returns four uint64 arrays of
+    32-bit words."""
+    c = [np.asarray(v, dtype=np.uint64) & _M for v in (c0, c1, c2, c3)]
+    k = [np.asarray(v, dtype=np.uint64) & _M for v in (k0, k1)]
+    for r in range(10):
+        if r > 0:
+            k = [(k[0] + PHILOX_W0) & _M, (k[1] + PHILOX_W1) & _M]
+        p0 = PHILOX_M0 * c[0]
+        p1 = PHILOX_M1 * c[2]
+        hi0, lo0 = p0 >> np.uint64(32), p0 & _M
+        hi1, lo1 = p1 >> np.uint64(32), p1 & _M
+        c = [hi1 ^ c[1] ^ k[0], lo1, hi0 ^ c[3] ^ k[1], lo0]
+    return c
+
+
+def drop_threshold(rate) -> int:
+    """Integer threshold for a drop probability: floor(rate * 2^32) computed
+    from the float32 rate (exact in float64), clipped to [0, 2^32]."""
+    r = float(np.float32(rate))
+    r = min(max(r, 0.0), 1.0)
+    return int(np.floor(r * 4294967296.0))
+
+
+def drop_mask(N, Tq, Hq, Wq, rate, seed, stream_id, chunk_id):
+    """Per-token Bernoulli(rate) drop decisions (True = dropped).
+
+    Models proactive token dropping / random token drop (Sec. 4.3;
+    Appendix A.2 trains with drop rates U[0, 25%]). Counter-based so that the
+    decision for a token depends only on (seed, stream, chunk, sample, token):
+    token j = (t*Hq + h)*Wq + w of sample n uses Philox counter
+    (j >> 2, n, chunk_id mod 2^32, stream_id mod 2^32), key
+    (seed mod 2^32, seed >> 32), output word j & 3; it is dropped iff that
+    word < floor(rate * 2^32)."""
+    thr = drop_threshold(rate)
+    ntok = Tq * Hq * Wq
+    j = np.arange(ntok, dtype=np.uint64)
+    out = np.zeros((N, ntok), dtype=bool)
+    seed = int(seed) & 0xFFFFFFFFFFFFFFFF
+    for n in range(N):
+        words = philox4x32_10(j >> np.uint64(2), n, int(chunk_id) & 0xFFFFFFFF,
+                              int(stream_id) & 0xFFFFFFFF, seed & 0xFFFFFFFF, seed >> 32)
+        w = np.stack(words, axis=-1)  # (ntok, 4)
+        r = w[np.arange(ntok), (j & np.uint64(3)).astype(np.int64)]
+        out[n] = r < np.uint64(thr) if thr < (1 << 32) else np.ones(ntok, dtype=bool)
+    return out.reshape(N, Tq, Hq, Wq)
+
+
+def apply_drop(idx, dropped, levels):
+    """Dropped tokens take the zero-code index (zero fill, Sec. 6.2)."""
+    out = np.array(idx, dtype=np.int64, copy=True)
+    out[dropped] = fsq_zero_index(levels)
+    return out
+
+
+def keep_bits_from_mask(dropped):
+    """Row masks of the packet header (Sec. 6.2): for every token row, a
+    W-bit vector with bit w set when token w is kept, stored as
+    ceil(W/32) little-endian 32-bit words per row."""
+    dropped = np.asarray(dropped, dtype=bool)
+    *lead, Wq = dropped.shape
+    nw = (Wq + 31) // 32
+    keep = ~dropped.reshape(-1, Wq)
+    bits = np.zeros((keep.shape[0], nw), dtype=np.uint64)
+    for w in range(Wq):
+        bits[:, w // 32] |= keep[:, w].astype(np.uint64) << np.uint64(w % 32)
+    return bits.astype(np.uint32).reshape(*lead, nw)
+
+
+def pack_rows(idx, keep_bits, Wq):
+    """Sender side of the row packetisation (Sec. 6.2): each token row
+    becomes a packet whose payload is the kept tokens in column order.
+    Returns (payload int32, row_offsets int64 of length rows+1)."""
+    idx = np.asarray(idx).reshape(-1, Wq)
+    kb = np.asarray(keep_bits).reshape(idx.shape[0], -1)
+    payload, offs = [], [0]
+    for r in range(idx.shape[0]):
+        for w in range(Wq):
+            if (int(kb[r, w // 32]) >> (w % 32)) & 1:
+                payload.append(int(idx[r, w]))
+        offs.append(len(payload))
+    return np.asarray(payload, dtype=np.int32), np.asarray(offs, dtype=np.int64)
+
+
+def unpack_rows(payload, row_offsets, keep_bits, row_received, Wq, zero_index):
+    """Receiver side (Sec. 6.2): place kept tokens at their columns, fill
+    masked positions with zeros (the zero-code index), and fill every
+    token of a lost row (row_received == 0) with zeros."""
+    kb = np.asarray(keep_bits).reshape(len(row_received), -1)
+    out = np.full((len(row_received), Wq), zero_index, dtype=np.int64)
+    for r in range(len(row_received)):
+        if not row_received[r]:
+            continue
+        k = int(row_offsets[r])
+        for w in range(Wq):
+            if (int(kb[r, w // 32]) >> (w % 32)) & 1:
+                out[r, w] = payload[k]
+                k += 1
+    return out
+
+
+# --------------------------------------------------------------------------
+# Depth-to-space and padding
+# --------------------------------------------------------------------------
+
+def depth_to_space(y, r, drop_first=None):
+    """Rearrange channels into (time, height, width) sub-positions.
+
+    y (N,T,H,W,C'*rt*rh*rw) -> (N, T*rt, H*rh, W*rw, C') with channel
+    ((a*rh + b)*rw + c)*C' + ch going to (t*rt + a, h*rh + b, w*rw + c, ch);
+    then the first ``drop_first`` frames (default rt - 1) are removed so that
+    the causal decoder emits 1 + rt*(T-1) frames, mirroring the encoder's
+    causal downsampling (Sec. 2.4: x_{0:T} <-> z_{0:T'})."""
+    rt, rh, rw = r
+    y = np.asarray(y)
+    N, T, H, W, C = y.shape
+    Co = C // (rt * rh * rw)
+    o = y.reshape(N, T, H, W, rt, rh, rw, Co).transpose(0, 1, 4, 2, 5, 3, 6, 7)
+    o = o.reshape(N, T * rt, H * rh, W * rw, Co)
+    d = rt - 1 if drop_first is None else drop_first
+    return o[:, d:]
+
+
+def space_to_depth(x, r, pad_first=None):
+    """Inverse of :func:`depth_to_space` (used only to pin it)."""
+    rt, rh, rw = r
+    x = np.asarray(x)
+    d = rt - 1 if pad_first is None else pad_first
+    N, T, H, W, Co = x.shape
+    if d:
+        x = np.concatenate([np.zeros((N, d, H, W, Co), x.dtype), x], axis=1)
+        T += d
+    o = x.reshape(N, T // rt, rt, H // rh, rh, W // rw, rw, Co).transpose(0, 1, 3, 5, 2, 4, 6, 7)
+    return o.reshape(N, T // rt, H // rh, W // rw, rt * rh * rw * Co)
+
+
+def edge_pad_to_multiple(x, m=8):
+    """Pad H and W up to multiples of m by repeating the last row/column.
+
+    Reading: the 8x spatial compression needs H and W divisible by 8
+    (e.g. 854-wide 480p); the frame is edge-extended and the decoder output
+    is cropped back."""
+    x = np.asarray(x)
+    N, T, H, W, C = x.shape
+    Hp = -(-H // m) * m
+    Wp = -(-W // m) * m
+    if Hp == H and Wp == W:
+        return x
+    return np.pad(x, ((0, 0), (0, 0), (0, Hp - H), (0, Wp - W), (0, 0)), mode="edge")

@@ -1,0 +1,241 @@
+"""Pins of the oracle's GroupNorm, SiLU, FSQ, Philox drop mask, row packets
+and depth-to-space: library routines, closed forms, invariants and the
+published Philox known-answer vectors."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+import torch.nn.functional as F
+
+from oracle import ops
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _gold(name):
+    with open(os.path.join(GOLD, name)) as f:
+        return json.load(f)
+
+
+# ---------------------------------------------------------------- GroupNorm
+
+def test_gn_matches_torch_group_norm_per_frame():
+    """Per-frame GroupNorm equals torch's group_norm applied to each frame."""
+    rng = np.random.default_rng(0)
+    x = rng.standard_normal((2, 3, 5, 6, 16)) * 3 + 1
+    g = rng.standard_normal(16)
+    b = rng.standard_normal(16)
+    y = ops.group_norm_frames(x, 8, 1e-6, g, b)
+    xt = torch.from_numpy(x).reshape(6, 5, 6, 16).permute(0, 3, 1, 2)
+    ref = F.group_norm(xt, 8, torch.from_numpy(g), torch.from_numpy(b), eps=1e-6)
+    ref = ref.permute(0, 2, 3, 1).reshape(x.shape).numpy()
+    np.testing.assert_allclose(y, ref, rtol=1e-10, atol=1e-10)
+
+
+def test_gn_moments_closed_form():
+    """Without affine, every (sample, group, frame) slice has mean 0 and
+    variance sigma^2 / (sigma^2 + eps)."""
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((1, 4, 3, 3, 8)) * np.arange(1, 9)
+    eps = 1e-2
+    y = ops.group_norm_frames(x, 4, eps)
+    xg = x.reshape(1, 4, 9, 4, 2)
+    yg = y.reshape(1, 4, 9, 4, 2)
+    var = xg.var(axis=(2, 4))
+    np.testing.assert_allclose(yg.mean(axis=(2, 4)), 0.0, atol=1e-12)
+    np.testing.assert_allclose(yg.var(axis=(2, 4)), var / (var + eps), rtol=1e-12)
+
+
+def test_gn_frames_independent():
+    rng = np.random.default_rng(2)
+    x = rng.standard_normal((1, 4, 3, 3, 8))
+    y0 = ops.group_norm_frames(x, 4)
+    x[:, 2] *= 5.0
+    x[:, 2] += 3.0
+    y1 = ops.group_norm_frames(x, 4)
+    np.testing.assert_array_equal(y0[:, :2], y1[:, :2])
+    np.testing.assert_array_equal(y0[:, 3:], y1[:, 3:])
+
+
+def test_gn_groups_reading():
+    assert ops.gn_groups(128) == 32 and ops.gn_groups(512) == 32
+    assert ops.gn_groups(16) == 8 and ops.gn_groups(32) == 16 and ops.gn_groups(64) == 32
+
+
+def test_silu_matches_torch():
+    x = np.linspace(-20, 20, 401)
+    np.testing.assert_allclose(ops.silu(x), F.silu(torch.from_numpy(x)).numpy(), rtol=1e-14, atol=1e-300)
+    assert ops.silu(np.array([0.0]))[0] == 0.0
+
+
+# ---------------------------------------------------------------------- FSQ
+
+G = _gold("fsq_8_8_8_5_5_5.json")
+LV = G["levels"]
+
+
+def test_fsq_closed_forms():
+    _, _, _, hw, basis = ops.fsq_constants(LV)
+    assert basis.tolist() == G["basis"]
+    assert int(np.prod(LV)) == G["codebook_size"]
+    assert ops.fsq_zero_index(LV) == G["zero_index"]
+    assert abs(math.log2(G["codebook_size"]) - G["bits_per_token"]) < 1e-12
+    idx, codes, b = ops.fsq_quantize(np.zeros((1, 6)), LV)
+    assert int(idx[0]) == G["zero_index"]
+    assert np.all(codes == 0.0)
+    np.testing.assert_allclose(b, 0.0, atol=1e-15)
+
+
+def test_fsq_extremes():
+    idx, _, _ = ops.fsq_quantize(np.full((1, 6), 50.0), LV)
+    assert int(idx[0]) == G["max_index"]
+    idx, codes, _ = ops.fsq_quantize(np.full((1, 6), -50.0), LV)
+    assert int(idx[0]) == 0
+    assert np.all(codes == -1.0)
+
+
+def test_fsq_bijection_exhaustive():
+    """Every one of the 64000 digit vectors maps to a distinct index in
+    [0, 64000), and index -> digits inverts it."""
+    grids = np.meshgrid(*[np.arange(l) for l in LV], indexing="ij")
+    d = np.stack([g.ravel() for g in grids], axis=-1)
+    _, _, _, _, basis = ops.fsq_constants(LV)
+    idx = (d * basis).sum(-1)
+    assert np.array_equal(np.sort(idx), np.arange(64000))
+    np.testing.assert_array_equal(ops.fsq_index_to_digits(idx, LV), d)
+
+
+def test_fsq_grid_points_fixed():
+    """Quantising the pre-image of every grid code returns that code
+    (idempotence of quantise o dequantise on the grid)."""
+    h, o, s, hw, basis = ops.fsq_constants(LV)
+    for ch, L in enumerate(LV):
+        for dgt in range(L):
+            q = dgt - L // 2
+            # the bound's range is (-h-o, h-o): the lowest even-level digit is
+            # reached only by rounding, so aim just inside the range there
+            bt = min(max(q, -h[ch] - o[ch] + 0.01), h[ch] - o[ch] - 0.01)
+            zc = np.arctanh((bt + o[ch]) / h[ch]) - s[ch]
+            z = np.zeros((1, 6))
+            z[0, ch] = zc
+            idx, codes, _ = ops.fsq_quantize(z, LV)
+            assert ops.fsq_index_to_digits(idx, LV)[0, ch] == dgt
+            assert codes[0, ch] == q / (L // 2)
+            np.testing.assert_allclose(ops.fsq_dequantize(idx, LV), codes)
+
+
+def test_fsq_monotone():
+    z = np.linspace(-6, 6, 2001)
+    for ch in range(6):
+        zz = np.zeros((z.size, 6))
+        zz[:, ch] = z
+        d = ops.fsq_index_to_digits(ops.fsq_quantize(zz, LV)[0], LV)[:, ch]
+        assert np.all(np.diff(d) >= 0)
+        assert d[0] == 0 and d[-1] == LV[ch] - 1
+
+
+def test_fsq_codes_in_range():
+    rng = np.random.default_rng(5)
+    idx, codes, _ = ops.fsq_quantize(rng.standard_normal((1000, 6)) * 3, LV)
+    assert idx.min() >= 0 and idx.max() < 64000
+    assert np.all(np.abs(codes) <= 1.0)
+
+
+# ------------------------------------------------------------ Philox + mask
+
+def test_philox_known_answers():
+    for v in _gold("philox4x32_10_kat.json")["vectors"]:
+        c = [int(a, 16) for a in v["ctr"]]
+        k = [int(a, 16) for a in v["key"]]
+        out = ops.philox4x32_10(*c, *k)
+        assert [int(o) for o in out] == [int(a, 16) for a in v["out"]]
+
+
+@pytest.mark.parametrize("rate", [0.05, 0.25, 0.3])
+def test_drop_rate_binomial(rate):
+    m = ops.drop_mask(2, 3, 45, 80, rate, seed=1234, stream_id=7, chunk_id=3)
+    n = m.size
+    k = int(m.sum())
+    sd = math.sqrt(n * rate * (1 - rate))
+    assert abs(k - n * rate) < 5 * sd
+
+
+def test_drop_rate_extremes_and_keys():
+    assert not ops.drop_mask(1, 2, 4, 5, 0.0, 1, 0, 0).any()
+    assert ops.drop_mask(1, 2, 4, 5, 1.0, 1, 0, 0).all()
+    a = ops.drop_mask(1, 1, 30, 40, 0.5, 9, 1, 2)
+    assert np.array_equal(a, ops.drop_mask(1, 1, 30, 40, 0.5, 9, 1, 2))
+    assert not np.array_equal(a, ops.drop_mask(1, 1, 30, 40, 0.5, 9, 1, 3))
+    assert not np.array_equal(a, ops.drop_mask(1, 1, 30, 40, 0.5, 9, 2, 2))
+    assert not np.array_equal(a, ops.drop_mask(1, 1, 30, 40, 0.5, 10, 1, 2))
+
+
+def test_drop_uses_philox_word():
+    """Token j of sample n takes word j&3 of Philox(counter (j>>2, n, chunk,
+    stream), key (seed lo, seed hi)) and drops iff it is below floor(rate*2^32)."""
+    seed, sid, cid, rate = (5 << 32) | 17, 3, 11, 0.4
+    m = ops.drop_mask(2, 1, 3, 5, rate, seed, sid, cid).reshape(2, -1)
+    thr = int(np.floor(float(np.float32(rate)) * 2 ** 32))
+    for n in range(2):
+        for j in range(15):
+            w = ops.philox4x32_10(j >> 2, n, cid, sid, 17, 5)[j & 3]
+            assert bool(m[n, j]) == (int(w) < thr)
+
+
+def test_packets_roundtrip_and_lost_rows():
+    rng = np.random.default_rng(6)
+    idx = rng.integers(0, 64000, size=(2, 1, 7, 37))
+    dropped = ops.drop_mask(2, 1, 7, 37, 0.3, 1, 2, 3)
+    kb = ops.keep_bits_from_mask(dropped)
+    assert kb.shape == (2, 1, 7, 2)
+    payload, offs = ops.pack_rows(idx, kb, 37)
+    assert len(payload) == int((~dropped).sum()) and offs[-1] == len(payload)
+    z = ops.fsq_zero_index(LV)
+    rows = 2 * 7
+    got = ops.unpack_rows(payload, offs, kb, np.ones(rows, bool), 37, z).reshape(idx.shape)
+    np.testing.assert_array_equal(got, ops.apply_drop(idx, dropped, LV))
+    recv = np.ones(rows, bool)
+    recv[[1, 9]] = False
+    got = ops.unpack_rows(payload, offs, kb, recv, 37, z).reshape(rows, 37)
+    assert np.all(got[[1, 9]] == z)
+    ref = ops.apply_drop(idx, dropped, LV).reshape(rows, 37)
+    np.testing.assert_array_equal(got[recv], ref[recv])
+
+
+# ----------------------------------------------------------- depth-to-space
+
+def test_d2s_channel_order_closed_form():
+    """Channel ((a*2+b)*2+c) of latent (t,h,w) lands at (2t+a-1, 2h+b, 2w+c)."""
+    y = np.arange(8, dtype=np.float64).reshape(1, 1, 1, 1, 8)
+    o = ops.depth_to_space(y, (2, 2, 2), drop_first=0)
+    for a in range(2):
+        for b in range(2):
+            for c in range(2):
+                assert o[0, a, b, c, 0] == (a * 2 + b) * 2 + c
+    o = ops.depth_to_space(y, (2, 2, 2))
+    assert o.shape == (1, 1, 2, 2, 1)
+    assert o[0, 0, :, :, 0].tolist() == [[4, 5], [6, 7]]
+
+
+def test_d2s_s2d_inverse():
+    rng = np.random.default_rng(7)
+    y = rng.standard_normal((2, 5, 3, 4, 8 * 3))
+    x = ops.depth_to_space(y, (2, 2, 2))
+    assert x.shape == (2, 9, 6, 8, 3)
+    yy = ops.space_to_depth(x, (2, 2, 2))
+    yy[:, 0, ..., :3 * 1] = y[:, 0, ..., :3]  # the dropped frame's channels are gone
+    np.testing.assert_array_equal(yy[:, 1:], y[:, 1:])
+    np.testing.assert_array_equal(ops.depth_to_space(ops.space_to_depth(x, (2, 2, 2)), (2, 2, 2)), x)
+    y2 = rng.standard_normal((1, 3, 2, 2, 12))
+    np.testing.assert_array_equal(ops.space_to_depth(ops.depth_to_space(y2, (1, 2, 2)), (1, 2, 2)), y2)
+
+
+def test_edge_pad():
+    x = np.arange(2 * 3 * 5, dtype=np.float64).reshape(1, 1, 3 * 2, 5, 1)[:, :, :3]
+    p = ops.edge_pad_to_multiple(x, 4)
+    assert p.shape == (1, 1, 4, 8, 1)
+    np.testing.assert_array_equal(p[0, 0, 3], p[0, 0, 2])
+    np.testing.assert_array_equal(p[0, 0, :, 7], p[0, 0, :, 4])
