@@ -1,0 +1,262 @@
+/*
+ * morphe-tok: C-ABI of a B300-native causal video tokenizer (sm_103a).
+ *
+ * The library implements the data-parallel hot path of a VFM-based
+ * generative video codec: the encoder f_phi that maps a clip
+ * x_{0:T} in R^{(1+T) x H x W x 3} to a latent z_{0:T'} in
+ * R^{(1+T') x H' x W' x C} with temporal factor s_T = 4 and spatial factor
+ * s_HW = 8 (paper Sec. 2.4; the 4x/8x8 setting of Sec. 4.1), a finite scalar
+ * quantiser that turns z into the integer token matrix that is transmitted
+ * (Sec. 4.3, Sec. 6.2), packet-drop masking with zero fill of dropped tokens
+ * and lost rows (Sec. 6.2; joint training with random drop, Appendix A.2),
+ * and the mirrored decoder g_theta.
+ *
+ * Conventions for every entry point:
+ *  - Tensors are channels-last, contiguous: x is (N, T, H, W, 3); latents
+ *    are (N, T', H', W', C); token indices are (N, T', H', W') int32.
+ *  - Pointers named d_* are device pointers (cudaMalloc'd or equivalent);
+ *    h_* are host pointers. The caller owns every tensor it passes.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream). Calls that take a stream are asynchronous on it: they enqueue
+ *    work and return without synchronising; outputs are valid once the
+ *    stream reaches that point.
+ *  - Return value: TOK_OK (0) or a negative-free error code below. Argument
+ *    and shape errors are detected on the host before anything is enqueued;
+ *    nothing is written in that case. Device-side errors (a bounded wait that
+ *    ran out) are recorded in the context's device status word and returned
+ *    by tok_status() and by the next call on that context.
+ *  - No entry point allocates device memory except tok_create, tok_reserve
+ *    and tok_stream_open; no C++ exception crosses the ABI.
+ */
+#ifndef MORPHE_TOK_H
+#define MORPHE_TOK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tok_ctx tok_ctx;
+typedef struct tok_stream tok_stream;
+
+enum tok_err {
+    TOK_OK = 0,
+    TOK_EINVAL = 1,    /* bad argument (null pointer, unknown name, bad enum) */
+    TOK_ESHAPE = 2,    /* shape not supported (e.g. T != 1 mod 4) */
+    TOK_ENOMEM = 3,    /* device allocation failed, or workspace too small */
+    TOK_ECUDA = 4,     /* a CUDA runtime/driver call failed */
+    TOK_ETIMEOUT = 5,  /* a device-side bounded wait ran out (kernel returned early) */
+    TOK_EDEVICE = 6,   /* no usable sm_100-family device */
+    TOK_ESTATE = 7     /* call out of order (e.g. weights not set, stream misuse) */
+};
+
+enum tok_precision { TOK_BF16 = 1, TOK_FP32 = 2 };
+enum tok_time_pad { TOK_PAD_REPLICATE = 0, TOK_PAD_ZERO = 1 };
+enum tok_arch_kind { TOK_ARCH_FULL = 0, TOK_ARCH_STAGE = 1 };
+
+/* Architecture descriptor. The paper gives no layer list (it builds on a
+ * published video tokenizer, Sec. 7); this descriptor is the reading used:
+ *  FULL : stem conv k3 stride (1,2,2) -> per level l < nlevels: `blocks`
+ *         causal residual blocks at ch[l] (GN->SiLU->conv->GN->SiLU->conv,
+ *         1x1x1 skip conv when channels change), a k3 stride-(2,2,2) conv
+ *         between levels -> GN->SiLU->conv to zdim -> FSQ. The decoder mirrors
+ *         it with k3 convs to ch[l-1]*8 channels + depth-to-space (2,2,2),
+ *         and a final conv to 3*4 channels + depth-to-space (1,2,2).
+ *  STAGE: conv k3 in->ch[0] -> conv k3 stride (1,2,2) ch[0]->ch[1] ->
+ *         GN->SiLU -> 1x1x1 conv ch[1]->zdim -> FSQ (encoder only).
+ * GroupNorm statistics are per (sample, group, frame) (causal); the group
+ * count of a C-channel norm is min(gn_groups, C/2). */
+typedef struct tok_arch {
+    int kind;            /* tok_arch_kind */
+    int in_ch;           /* pixel channels, must be 3 */
+    int nlevels;         /* FULL: 1..4 levels; STAGE: 2 */
+    int ch[4];           /* channels per level, multiples of 64 on the BF16 path */
+    int blocks;          /* residual blocks per level (FULL) */
+    int nlev;            /* number of FSQ channels = latent dim (<= 8) */
+    int levels[8];       /* FSQ levels, each 2..16 */
+    int gn_groups;       /* 32 */
+    float gn_eps;        /* 1e-6 */
+    int time_pad;        /* tok_time_pad for the causal left padding */
+} tok_arch;
+
+/* Fill `a` with the default tokenizer: FULL, ch {128,256,512}, 2 blocks per
+ * level, FSQ levels {8,8,8,5,5,5}, GroupNorm(32) eps 1e-6, replicate pad. */
+void tok_arch_default(tok_arch* a);
+
+/* Create a context on the current CUDA device. `precision` selects the
+ * compute path: TOK_BF16 (tcgen05 tensor cores, BF16 activations and
+ * weights, FP32 accumulation and norm statistics) or TOK_FP32 (CUDA-core FP32
+ * everywhere, no TF32). Allocates the weights on the device (zeros until
+ * set). Returns TOK_EDEVICE if the device is not sm_100-family. */
+int tok_create(const tok_arch* arch, int precision, tok_ctx** out);
+void tok_destroy(tok_ctx* ctx);
+
+/* Parameter list in the architecture's order: name (owned by the context,
+ * valid until tok_destroy), rank and dims. Conv weights are
+ * (Cout, kt, kh, kw, Cin); biases, GN gamma/beta are (C). */
+int tok_param_count(const tok_ctx* ctx);
+int tok_param_info(const tok_ctx* ctx, int i, const char** name, int* ndim, int64_t dims[5]);
+/* Copy one parameter from host FP32 memory (synchronous). The BF16 path
+ * rounds weights to nearest-even BF16 and re-lays them out for TMA. */
+int tok_set_param(tok_ctx* ctx, const char* name, const float* h_values, int64_t count);
+
+/* Workspace for clips of up to N x T x H x W pixels (bytes), and reserve it
+ * (allocates once; later calls with larger shapes grow it). Hot calls never
+ * allocate: tok_encode/tok_decode return TOK_ENOMEM if the reserved
+ * workspace is smaller than they need. */
+size_t tok_workspace_bytes(const tok_ctx* ctx, int N, int T, int H, int W);
+int tok_reserve(tok_ctx* ctx, int N, int T, int H, int W);
+
+/* Latent / token shape of an N x T x H x W clip: T' = 1 + (T-1)/s_T
+ * (requires T = 1 mod s_T), H' = ceil(H/s_HW), W' = ceil(W/s_HW). */
+int tok_latent_shape(const tok_ctx* ctx, int T, int H, int W, int* Tq, int* Hq, int* Wq);
+
+/* Encoder f_phi (Sec. 2.4) + FSQ.
+ * d_x    : (N,T,H,W,3) pixels in [-1,1]; bf16 on the BF16 path, fp32 on FP32.
+ *          H and W need not be multiples of 8: the frame is edge-extended.
+ * d_z    : (N,T',H',W',nlev) fp32 pre-quantisation latent, or NULL.
+ * d_idx  : (N,T',H',W') int32 token indices, or NULL.
+ * s      : NULL for a whole clip (causal padding at frame 0); a stream
+ *          handle for chunked streaming (see tok_stream_open).
+ * Errors: TOK_ESHAPE if T != 1 mod s_T in clip mode. */
+int tok_encode(tok_ctx* ctx, const void* d_x, int N, int T, int H, int W,
+               float* d_z, int32_t* d_idx, tok_stream* s, void* stream);
+
+/* Decoder g_theta (Sec. 2.4): token indices -> pixels.
+ * d_idx  : (N,Tq,Hq,Wq) int32 indices in [0, prod(levels)); the zero-code
+ *          index stands for a dropped/lost token (Sec. 6.2).
+ * d_xhat : (N, 1 + s_T*(Tq-1), H, W, 3) fp32, cropped to H x W
+ *          (H <= s_HW*Hq, W <= s_HW*Wq). */
+int tok_decode(tok_ctx* ctx, const int32_t* d_idx, int N, int Tq, int Hq, int Wq,
+               int H, int W, float* d_xhat, tok_stream* s, void* stream);
+
+/* Stand-alone FSQ (Mentzer et al. 2023): per token of nlev channels,
+ * b = tanh(z + atanh(o/h))*h - o with h = (L-1)(1-1e-3)/2, o = 0.5 for even
+ * L else 0; q = round-half-even(b); idx = sum (q + L/2) * prod_{j<i} L_j;
+ * codes = q / floor(L/2). FP32 arithmetic.
+ * d_z (ntok, nlev) fp32; h_levels host array of nlev levels (<= 8);
+ * d_idx (ntok) int32; d_codes (ntok, nlev) fp32 or NULL. */
+int tok_quantize(const float* d_z, int64_t ntok, const int* h_levels, int nlev,
+                 int32_t* d_idx, float* d_codes, void* stream);
+
+/* Index -> code vectors: codes_i = (digit_i - L_i/2) / floor(L_i/2). */
+int tok_dequantize(const int32_t* d_idx, int64_t ntok, const int* h_levels, int nlev,
+                   float* d_codes, void* stream);
+
+/* Index of the all-zero code vector (the zero-fill token of Sec. 6.2). */
+int32_t tok_zero_index(const int* h_levels, int nlev);
+
+/* Packet-drop token masking (Sec. 4.3 token dropping; Sec. 6.2 zero fill;
+ * random drop of Appendix A.2). Token j = (t*Hq + h)*Wq + w of sample n is
+ * dropped iff word (j & 3) of Philox-4x32-10(counter = (j>>2, n,
+ * chunk_id mod 2^32, stream_id mod 2^32), key = (seed mod 2^32, seed>>32))
+ * is below floor(rate * 2^32) (rate clipped to [0,1]).
+ * d_idx (N,Tq,Hq,Wq) int32 in; d_out (same) gets the zero index at dropped
+ * tokens (may alias d_idx); d_keep_bits, if not NULL, gets the row masks of
+ * the packet headers: (N,Tq,Hq, ceil(Wq/32)) uint32, bit w%32 of word w/32 set
+ * when token w of the row is kept. */
+int tok_drop_mask(const int32_t* d_idx, int N, int Tq, int Hq, int Wq, float rate,
+                  uint64_t seed, uint64_t stream_id, uint64_t chunk_id, int32_t zero_index,
+                  int32_t* d_out, uint32_t* d_keep_bits, void* stream);
+
+/* Row packetisation (Sec. 6.2). rows = N*Tq*Hq rows of Wq tokens.
+ * Sender: d_payload gets, row after row, the kept tokens of each row in
+ * column order, starting at d_row_offsets[r] = number of kept tokens in rows
+ * < r (d_row_offsets has rows+1 entries; both computed here). */
+int tok_pack_rows(const int32_t* d_idx, const uint32_t* d_keep_bits, int64_t rows, int Wq,
+                  int32_t* d_payload, int64_t* d_row_offsets, void* stream);
+/* Receiver: place the kept tokens of every received row at their columns and
+ * fill masked positions and every position of a lost row
+ * (d_row_received[r] == 0) with zero_index. */
+int tok_unpack_rows(const int32_t* d_payload, const int64_t* d_row_offsets,
+                    const uint32_t* d_keep_bits, const uint8_t* d_row_received,
+                    int64_t rows, int Wq, int32_t zero_index, int32_t* d_idx, void* stream);
+
+/* Streaming (chunked causal encode/decode with per-stream conv caches on the
+ * device; GoP-style segment coding, Sec. 4.2 and 4.3). Chunk 0 is one frame
+ * (latent 0); every later chunk is s_T frames (frames s_T*k-3 .. s_T*k ->
+ * latent k). Each causal conv keeps the last two input frames of the chunk
+ * it saw, so a stream's chunks give exactly the whole-clip result.
+ * tok_stream_bytes: device bytes one stream of H x W needs (for admission).
+ * tok_stream_open allocates them (TOK_ENOMEM when they do not fit). */
+size_t tok_stream_bytes(const tok_ctx* ctx, int H, int W);
+int tok_stream_open(tok_ctx* ctx, int H, int W, tok_stream** out);
+void tok_stream_close(tok_stream* s);
+int tok_stream_reset(tok_stream* s);
+
+/* One causal 3D convolution (the K1 building block of f_phi / g_theta,
+ * Sec. 2.4) on the selected precision path, without a context:
+ *   y[n,to,ho,wo,co] = bias[co] + sum W[co,dt,dh,dw,ci] * x[n,ti,hi,wi,ci]
+ *   ti = to*st + dt - (k-1) (frames before 0 read frame 0 under
+ *   TOK_PAD_REPLICATE, zero under TOK_PAD_ZERO), hi = ho*sh + dh - (k-1)/2,
+ *   wi = wo*sw + dw - (k-1)/2 (zero outside the frame).
+ * d_x (N,T,H,W,Cin) and d_y (N,To,Ho,Wo,Cout), To = (T-1)/st+1,
+ * Ho = (H-1)/sh+1 for k = 3 (H for k = 1), bf16 for TOK_BF16 / fp32 for
+ * TOK_FP32; d_residual (same shape as d_y) is added when not NULL.
+ * d_w (Cout,k,k,k,Cin) and d_bias (Cout) are fp32 device arrays; the BF16
+ * path rounds the weights to bf16 into the workspace.
+ * k is 1 or 3; strides are 1 or 2 with sh == sw; TOK_BF16 needs
+ * Cin % 64 == 0 and even H, W when sh == 2 (TOK_ESHAPE otherwise).
+ * d_workspace: at least tok_conv3d_workspace_bytes(...) bytes. */
+size_t tok_conv3d_workspace_bytes(int precision, int Cin, int Cout, int k);
+int tok_conv3d(int precision, const void* d_x, int N, int T, int H, int W, int Cin,
+               const float* d_w, const float* d_bias, int Cout, int k, int st, int sh, int sw,
+               int time_pad, const void* d_residual, void* d_y,
+               void* d_workspace, size_t workspace_bytes, void* stream);
+
+/* GroupNorm with statistics per (sample, group, frame) followed by SiLU
+ * (the normalisation of every causal residual block):
+ *   y = SiLU((x - mean) / sqrt(var + eps) * gamma + beta), mean/var over the
+ *   C/G channels of a group and the H*W positions of one frame (biased var).
+ * d_x, d_y (frames, HW, C) channels-last, bf16 (TOK_BF16) or fp32
+ * (TOK_FP32), may alias. gamma/beta fp32 (C) or NULL (1/0). Needs C/G >= 2,
+ * G <= 64, C a multiple of 8 (bf16) or 4 (fp32) with C/8 (C/4) a power of two
+ * <= 256. d_workspace: tok_groupnorm_workspace_bytes(...) bytes. */
+size_t tok_groupnorm_workspace_bytes(int precision, int64_t frames, int64_t HW, int C, int G);
+int tok_groupnorm_silu(int precision, const void* d_x, int64_t frames, int64_t HW, int C, int G,
+                       const float* d_gamma, const float* d_beta, float eps, void* d_y,
+                       void* d_workspace, size_t workspace_bytes, void* stream);
+
+/* Device status: synchronises the context's work, returns and clears the
+ * first device-side error recorded since the last call. */
+int tok_status(tok_ctx* ctx);
+const char* tok_strerror(int code);
+
+/* Debug/self-test: launch one kernel that waits on a device barrier nothing
+ * ever signals, with a bounded wait of `limit_ns`; the kernel gives up,
+ * records TOK_ETIMEOUT in the context's status word and returns. */
+int tok_selftest_timeout(tok_ctx* ctx, int64_t limit_ns, void* stream);
+
+/* Number of kernels the library has launched since the context was created
+ * (for launch accounting in benchmarks). */
+int64_t tok_launch_count(const tok_ctx* ctx);
+
+/* Opt-in timing of the context's kernels with CUDA events recorded on the
+ * caller's stream around every launch, grouped by kernel class, with the
+ * algorithmic work of each launch: convolutions count 2*M*N*K FLOPs
+ * (M output voxels, N output channels, K = taps * input channels, padding
+ * excluded); GroupNorm+SiLU counts one read and one write of the activation;
+ * the gathers count their output bytes. tok_profile_enable allocates the
+ * event pool (on = 1) or frees it (on = 0); tok_profile_read synchronises
+ * the recorded events, fills `out` with the sums since the previous read and
+ * resets them. */
+typedef struct tok_profile_stats {
+    int64_t conv_launches;
+    double conv_ms;
+    double conv_flop;
+    int64_t gn_launches;
+    double gn_ms;
+    double gn_bytes;
+    int64_t other_launches;
+    double other_ms;
+    double other_bytes;
+} tok_profile_stats;
+int tok_profile_enable(tok_ctx* ctx, int on);
+int tok_profile_read(tok_ctx* ctx, tok_profile_stats* out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MORPHE_TOK_H */

@@ -1,0 +1,275 @@
+"""ctypes binding of the tokenizer's C-ABI (include/tok.h): argument marshalling only.
+
+Every function here has the name of the C entry point it wraps and forwards
+plain pointers and sizes; all computation happens in the CUDA library. The
+library must have been built (``python -m paper_2602_03529_b300.build``):
+loading fails loudly otherwise, there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmorphe_tok.so")
+
+TOK_OK, TOK_EINVAL, TOK_ESHAPE, TOK_ENOMEM, TOK_ECUDA, TOK_ETIMEOUT, TOK_EDEVICE, TOK_ESTATE = range(8)
+TOK_BF16, TOK_FP32 = 1, 2
+TOK_PAD_REPLICATE, TOK_PAD_ZERO = 0, 1
+TOK_ARCH_FULL, TOK_ARCH_STAGE = 0, 1
+
+
+class tok_arch(C.Structure):
+    _fields_ = [
+        ("kind", C.c_int),
+        ("in_ch", C.c_int),
+        ("nlevels", C.c_int),
+        ("ch", C.c_int * 4),
+        ("blocks", C.c_int),
+        ("nlev", C.c_int),
+        ("levels", C.c_int * 8),
+        ("gn_groups", C.c_int),
+        ("gn_eps", C.c_float),
+        ("time_pad", C.c_int),
+    ]
+
+
+class tok_profile_stats(C.Structure):
+    _fields_ = [
+        ("conv_launches", C.c_int64), ("conv_ms", C.c_double), ("conv_flop", C.c_double),
+        ("gn_launches", C.c_int64), ("gn_ms", C.c_double), ("gn_bytes", C.c_double),
+        ("other_launches", C.c_int64), ("other_ms", C.c_double), ("other_bytes", C.c_double),
+    ]
+
+
+class TokError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {tok_strerror(code)} (code {code})")
+        self.code = code
+
+
+_lib = None
+vp, i32, i64, u64, f32, sz = C.c_void_p, C.c_int, C.c_int64, C.c_uint64, C.c_float, C.c_size_t
+
+_SIGS = {
+    "tok_arch_default": (None, [C.POINTER(tok_arch)]),
+    "tok_create": (i32, [C.POINTER(tok_arch), i32, C.POINTER(vp)]),
+    "tok_destroy": (None, [vp]),
+    "tok_param_count": (i32, [vp]),
+    "tok_param_info": (i32, [vp, i32, C.POINTER(C.c_char_p), C.POINTER(i32), C.POINTER(i64)]),
+    "tok_set_param": (i32, [vp, C.c_char_p, vp, i64]),
+    "tok_workspace_bytes": (sz, [vp, i32, i32, i32, i32]),
+    "tok_reserve": (i32, [vp, i32, i32, i32, i32]),
+    "tok_latent_shape": (i32, [vp, i32, i32, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
+    "tok_encode": (i32, [vp, vp, i32, i32, i32, i32, vp, vp, vp, vp]),
+    "tok_decode": (i32, [vp, vp, i32, i32, i32, i32, i32, i32, vp, vp, vp]),
+    "tok_quantize": (i32, [vp, i64, vp, i32, vp, vp, vp]),
+    "tok_dequantize": (i32, [vp, i64, vp, i32, vp, vp]),
+    "tok_zero_index": (i32, [vp, i32]),
+    "tok_drop_mask": (i32, [vp, i32, i32, i32, i32, f32, u64, u64, u64, i32, vp, vp, vp]),
+    "tok_pack_rows": (i32, [vp, vp, i64, i32, vp, vp, vp]),
+    "tok_unpack_rows": (i32, [vp, vp, vp, vp, i64, i32, i32, vp, vp]),
+    "tok_stream_bytes": (sz, [vp, i32, i32]),
+    "tok_stream_open": (i32, [vp, i32, i32, C.POINTER(vp)]),
+    "tok_stream_close": (None, [vp]),
+    "tok_stream_reset": (i32, [vp]),
+    "tok_conv3d_workspace_bytes": (sz, [i32, i32, i32, i32]),
+    "tok_conv3d": (i32, [i32, vp, i32, i32, i32, i32, i32, vp, vp, i32, i32, i32, i32, i32, i32, vp, vp, vp, sz,
+                         vp]),
+    "tok_groupnorm_workspace_bytes": (sz, [i32, i64, i64, i32, i32]),
+    "tok_groupnorm_silu": (i32, [i32, vp, i64, i64, i32, i32, vp, vp, f32, vp, vp, sz, vp]),
+    "tok_status": (i32, [vp]),
+    "tok_strerror": (C.c_char_p, [i32]),
+    "tok_selftest_timeout": (i32, [vp, i64, vp]),
+    "tok_launch_count": (i64, [vp]),
+    "tok_profile_enable": (i32, [vp, i32]),
+    "tok_profile_read": (i32, [vp, C.POINTER(tok_profile_stats)]),
+}
+
+
+def load():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                               "(run `python -m paper_2602_03529_b300.build`)")
+        lib = C.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def exported_names():
+    return list(_SIGS)
+
+
+def _call(name, *args):
+    return getattr(load(), name)(*args)
+
+
+def _ck(code, what):
+    if code != TOK_OK:
+        raise TokError(code, what)
+
+
+def _levels_arr(levels):
+    arr = (C.c_int * len(levels))(*levels)
+    return arr
+
+
+# --- one wrapper per entry point (same names as include/tok.h) -------------
+
+def tok_arch_default() -> tok_arch:
+    a = tok_arch()
+    _call("tok_arch_default", C.byref(a))
+    return a
+
+
+def tok_create(arch: tok_arch, precision: int) -> int:
+    h = vp()
+    _ck(_call("tok_create", C.byref(arch), precision, C.byref(h)), "tok_create")
+    return h.value
+
+
+def tok_destroy(ctx: int) -> None:
+    _call("tok_destroy", ctx)
+
+
+def tok_param_count(ctx: int) -> int:
+    return _call("tok_param_count", ctx)
+
+
+def tok_param_info(ctx: int, i: int):
+    name = C.c_char_p()
+    nd = i32()
+    dims = (i64 * 5)()
+    _ck(_call("tok_param_info", ctx, i, C.byref(name), C.byref(nd), dims), "tok_param_info")
+    return name.value.decode(), tuple(dims[k] for k in range(nd.value))
+
+
+def tok_set_param(ctx: int, name: str, host_ptr: int, count: int) -> None:
+    _ck(_call("tok_set_param", ctx, name.encode(), host_ptr, count), f"tok_set_param({name})")
+
+
+def tok_workspace_bytes(ctx: int, N: int, T: int, H: int, W: int) -> int:
+    return _call("tok_workspace_bytes", ctx, N, T, H, W)
+
+
+def tok_reserve(ctx: int, N: int, T: int, H: int, W: int) -> None:
+    _ck(_call("tok_reserve", ctx, N, T, H, W), "tok_reserve")
+
+
+def tok_latent_shape(ctx: int, T: int, H: int, W: int):
+    a, b, c = i32(), i32(), i32()
+    _ck(_call("tok_latent_shape", ctx, T, H, W, C.byref(a), C.byref(b), C.byref(c)), "tok_latent_shape")
+    return a.value, b.value, c.value
+
+
+def tok_encode(ctx, x_ptr, N, T, H, W, z_ptr, idx_ptr, stream_handle, cuda_stream) -> None:
+    _ck(_call("tok_encode", ctx, x_ptr, N, T, H, W, z_ptr, idx_ptr, stream_handle, cuda_stream), "tok_encode")
+
+
+def tok_decode(ctx, idx_ptr, N, Tq, Hq, Wq, H, W, xhat_ptr, stream_handle, cuda_stream) -> None:
+    _ck(_call("tok_decode", ctx, idx_ptr, N, Tq, Hq, Wq, H, W, xhat_ptr, stream_handle, cuda_stream),
+        "tok_decode")
+
+
+def tok_quantize(z_ptr, ntok, levels, idx_ptr, codes_ptr, cuda_stream) -> None:
+    lv = _levels_arr(levels)
+    _ck(_call("tok_quantize", z_ptr, ntok, C.cast(lv, vp), len(levels), idx_ptr, codes_ptr, cuda_stream),
+        "tok_quantize")
+
+
+def tok_dequantize(idx_ptr, ntok, levels, codes_ptr, cuda_stream) -> None:
+    lv = _levels_arr(levels)
+    _ck(_call("tok_dequantize", idx_ptr, ntok, C.cast(lv, vp), len(levels), codes_ptr, cuda_stream),
+        "tok_dequantize")
+
+
+def tok_zero_index(levels) -> int:
+    lv = _levels_arr(levels)
+    return _call("tok_zero_index", C.cast(lv, vp), len(levels))
+
+
+def tok_drop_mask(idx_ptr, N, Tq, Hq, Wq, rate, seed, stream_id, chunk_id, zero_index, out_ptr, keep_ptr,
+                  cuda_stream) -> None:
+    _ck(_call("tok_drop_mask", idx_ptr, N, Tq, Hq, Wq, rate, seed, stream_id, chunk_id, zero_index, out_ptr,
+              keep_ptr, cuda_stream), "tok_drop_mask")
+
+
+def tok_pack_rows(idx_ptr, keep_ptr, rows, Wq, payload_ptr, offs_ptr, cuda_stream) -> None:
+    _ck(_call("tok_pack_rows", idx_ptr, keep_ptr, rows, Wq, payload_ptr, offs_ptr, cuda_stream), "tok_pack_rows")
+
+
+def tok_unpack_rows(payload_ptr, offs_ptr, keep_ptr, received_ptr, rows, Wq, zero_index, idx_ptr,
+                    cuda_stream) -> None:
+    _ck(_call("tok_unpack_rows", payload_ptr, offs_ptr, keep_ptr, received_ptr, rows, Wq, zero_index, idx_ptr,
+              cuda_stream), "tok_unpack_rows")
+
+
+def tok_stream_bytes(ctx, H, W) -> int:
+    return _call("tok_stream_bytes", ctx, H, W)
+
+
+def tok_stream_open(ctx, H, W) -> int:
+    h = vp()
+    _ck(_call("tok_stream_open", ctx, H, W, C.byref(h)), "tok_stream_open")
+    return h.value
+
+
+def tok_stream_close(s) -> None:
+    _call("tok_stream_close", s)
+
+
+def tok_stream_reset(s) -> None:
+    _ck(_call("tok_stream_reset", s), "tok_stream_reset")
+
+
+def tok_conv3d_workspace_bytes(precision, Cin, Cout, k) -> int:
+    return _call("tok_conv3d_workspace_bytes", precision, Cin, Cout, k)
+
+
+def tok_conv3d(precision, x_ptr, N, T, H, W, Cin, w_ptr, b_ptr, Cout, k, st, sh, sw, time_pad, res_ptr, y_ptr,
+               ws_ptr, ws_bytes, cuda_stream) -> None:
+    _ck(_call("tok_conv3d", precision, x_ptr, N, T, H, W, Cin, w_ptr, b_ptr, Cout, k, st, sh, sw, time_pad,
+              res_ptr, y_ptr, ws_ptr, ws_bytes, cuda_stream), "tok_conv3d")
+
+
+def tok_groupnorm_workspace_bytes(precision, frames, HW, C, G) -> int:
+    return _call("tok_groupnorm_workspace_bytes", precision, frames, HW, C, G)
+
+
+def tok_groupnorm_silu(precision, x_ptr, frames, HW, C, G, g_ptr, b_ptr, eps, y_ptr, ws_ptr, ws_bytes,
+                       cuda_stream) -> None:
+    _ck(_call("tok_groupnorm_silu", precision, x_ptr, frames, HW, C, G, g_ptr, b_ptr, eps, y_ptr, ws_ptr,
+              ws_bytes, cuda_stream), "tok_groupnorm_silu")
+
+
+def tok_status(ctx) -> int:
+    return _call("tok_status", ctx)
+
+
+def tok_strerror(code: int) -> str:
+    return _call("tok_strerror", code).decode()
+
+
+def tok_selftest_timeout(ctx, limit_ns, cuda_stream) -> None:
+    _ck(_call("tok_selftest_timeout", ctx, limit_ns, cuda_stream), "tok_selftest_timeout")
+
+
+def tok_launch_count(ctx) -> int:
+    return _call("tok_launch_count", ctx)
+
+
+def tok_profile_enable(ctx, on: bool) -> None:
+    _ck(_call("tok_profile_enable", ctx, 1 if on else 0), "tok_profile_enable")
+
+
+def tok_profile_read(ctx) -> dict:
+    st = tok_profile_stats()
+    _ck(_call("tok_profile_read", ctx, C.byref(st)), "tok_profile_read")
+    return {f: getattr(st, f) for f, _ in tok_profile_stats._fields_}

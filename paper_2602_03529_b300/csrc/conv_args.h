@@ -1,0 +1,72 @@
+// Geometry and epilogue description of one causal 3D convolution launch,
+// shared by the tcgen05 (BF16) and CUDA-core (FP32) conv kernels.
+//
+// Convolution (causal in time, zero-padded in space):
+//   y[n,to,ho,wo,co] = bias[co] + sum_{dt,dh,dw,ci} W[co,dt,dh,dw,ci] * x[n,ti,hi,wi,ci]
+//   ti = to*st + dt + t_off   (clip mode: t_off = -(kt-1), the causal left pad)
+//   hi = ho*sh + dh - (kh-1)/2,  wi = wo*sw + dw - (kw-1)/2
+// A tap with ti < 0 reads, in this order of precedence: frame (hist_T + ti)
+// of the history tensor when one is given (streaming), frame 0 (replicate
+// pad) or zero (zero pad). Taps outside [0,H) x [0,W) read zero.
+//
+// Epilogue modes:
+//   OUT_PLAIN : out[n,to,ho,wo,co] = y (+ residual[n,to,ho,wo,co])
+//   OUT_D2S   : depth-to-space: channel co = ((a*rh+b)*rw+c)*oC + ch of y at
+//               (to,ho,wo) goes to out[n, to*rt + a - drop_t, ho*rh+b, wo*rw+c, ch];
+//               frames < 0 are dropped, rows/cols >= oH/oW are cropped.
+//   OUT_FSQ   : out is the fp32 latent z; idx gets the FSQ token index.
+#pragma once
+#include <stdint.h>
+
+namespace tok {
+
+enum OutMode { OUT_PLAIN = 0, OUT_D2S = 1, OUT_FSQ = 2 };
+
+struct FsqConsts {
+    int nlev;
+    int levels[8];     // L_i
+    float half_l[8];   // (L-1)(1-eps)/2
+    float offset[8];   // 0.5 for even L else 0
+    float shift[8];    // atanh(offset/half_l)
+    int half_w[8];     // L/2
+    int basis[8];      // prod_{j<i} L_j
+};
+
+struct ConvArgs {
+    // input (the chunk / clip) and optional history
+    const void* x;        // (N, Tin, Hin, Win, Cin)
+    const void* hist;     // (N, hist_T, Hin, Win, Cin) or null
+    int hist_T;
+    int N, Tin, Hin, Win, Cin;
+    // weights: (Cout_pad, Kpad) with K = taps*Cin laid out (tap, ci)
+    const void* w;
+    const float* bias;    // (Cout) fp32
+    int Cout, Cout_pad, Kpad;
+    int kt, kh, kw, st, sh, sw;
+    int t_off, pad_mode;
+    // output (pre-epilogue conv grid)
+    int Tout, Hout, Wout;
+    // epilogue
+    int mode;
+    void* out;
+    int out_fp32;         // store fp32 (else bf16 on the BF16 path)
+    int oT, oH, oW, oC;   // output tensor dims per sample
+    int rt, rh, rw, drop_t;
+    const void* residual; // same layout as out (OUT_PLAIN only) or null
+    int32_t* idx;         // OUT_FSQ
+    FsqConsts fsq;
+    // device status / bounded waits
+    int* status;
+    unsigned long long wait_ns;
+};
+
+// Geometry of the im2col gathers (pixel stem / dequantised decoder input).
+struct GatherGeo {
+    int N, Tin, H, W, Hp, Wp, Cin;  // source (H,W real extent; Hp,Wp logical padded extent)
+    int hist_T;
+    int Tout, Hout, Wout;
+    int kt, kh, kw, st, sh, sw, t_off, pad_mode;
+    int Kpad;
+};
+
+}  // namespace tok

@@ -1,0 +1,463 @@
+// BF16 causal 3D convolution on the 5th-generation tensor cores (sm_103a).
+//
+// Implicit GEMM: M = output voxels, N = output channels, K = taps x Cin.
+// One CTA per SM (persistent) walks output tiles of 128 voxels x BN channels.
+// A tile of 128 voxels is a BH x BW block of one output frame; each K block
+// is one tap (dt,dh,dw) x 64 input channels, fetched by one TMA box load of
+// the input frame at the tap's offset (boundary padding = TMA out-of-bounds
+// zero fill; stride-2 convs read a parity view of the input, see the host
+// side). The time-causal left padding is folded into the loader: a tap that
+// falls before frame 0 reads the stream's history tensor (streaming), frame 0
+// (replicate) or nothing (zero fill via an out-of-range coordinate).
+//
+// Warp roles (192 threads):
+//   warp 0      TMA producer (one lane): A (activations) and B (weights) boxes
+//               into a STAGES-deep ring of 128B-swizzled shared-memory tiles.
+//   warp 1      TMEM allocation and MMA issue (one lane): 4 x
+//               tcgen05.mma.kind::f16 (M=128, N=BN, K=16) per stage into one of
+//               two FP32 accumulators in TMEM; tcgen05.commit frees the stage.
+//   warps 2..5  epilogue: tcgen05.ld the accumulator (each warp its 32 TMEM
+//               lanes = 32 voxels), add bias and residual, round to BF16 and
+//               store; or scatter through depth-to-space; or FSQ-quantise.
+// The epilogue of tile i overlaps the MMAs of tile i+1 (double-buffered TMEM).
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+
+#include "common.cuh"
+#include "conv_args.h"
+
+namespace tok {
+
+struct TcGeo {
+    int BH, BW;              // output tile = BH rows x BW cols of one frame
+    int tiles_w, tiles_h;
+    int n_tiles;             // Cout_pad / BN
+    long long num_tiles;     // m tiles x n tiles
+    int cpt;                 // 64-channel blocks per tap
+    int nkb;                 // K blocks per tile = taps * cpt
+    int strided;             // parity view (sh = sw = 2)
+};
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int A_BYTES = BM * 128;
+
+template <int BN>
+struct Cfg {
+    static constexpr int B_BYTES = BN * 128;
+    static constexpr int STAGE = A_BYTES + B_BYTES;
+    static constexpr int STAGES = (200 * 1024 / STAGE) > 8 ? 8 : (200 * 1024 / STAGE);
+    static constexpr int TMEM_COLS = (2 * BN <= 32) ? 32 : (2 * BN <= 64) ? 64 : (2 * BN <= 128) ? 128 : (2 * BN <= 256) ? 256 : 512;
+    static constexpr int BAR_BYTES = 256;
+    static constexpr int SMEM = STAGES * STAGE + 1024 + BAR_BYTES;
+    static constexpr uint32_t IDESC = idesc_bf16_f32(BM, BN);
+};
+
+struct TileCoord {
+    int n, to, th, tw, nt;
+};
+
+__device__ __forceinline__ TileCoord decode_tile(const ConvArgs& a, const TcGeo& g, long long tile) {
+    TileCoord c;
+    c.nt = (int)(tile % g.n_tiles);
+    long long m = tile / g.n_tiles;
+    c.tw = (int)(m % g.tiles_w);
+    m /= g.tiles_w;
+    c.th = (int)(m % g.tiles_h);
+    m /= g.tiles_h;
+    c.to = (int)(m % a.Tout);
+    c.n = (int)(m / a.Tout);
+    return c;
+}
+
+__device__ __forceinline__ void store_bf16x16(__nv_bfloat16* dst, const float (&v)[16]) {
+    uint4 o0, o1;
+    o0.x = pack_bf16x2(v[0], v[1]);
+    o0.y = pack_bf16x2(v[2], v[3]);
+    o0.z = pack_bf16x2(v[4], v[5]);
+    o0.w = pack_bf16x2(v[6], v[7]);
+    o1.x = pack_bf16x2(v[8], v[9]);
+    o1.y = pack_bf16x2(v[10], v[11]);
+    o1.z = pack_bf16x2(v[12], v[13]);
+    o1.w = pack_bf16x2(v[14], v[15]);
+    reinterpret_cast<uint4*>(dst)[0] = o0;
+    reinterpret_cast<uint4*>(dst)[1] = o1;
+}
+
+__device__ __forceinline__ void add_bf16x16(const __nv_bfloat16* src, float (&v)[16]) {
+    uint4 r0 = reinterpret_cast<const uint4*>(src)[0];
+    uint4 r1 = reinterpret_cast<const uint4*>(src)[1];
+    uint32_t u[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        float2 f = unpack_bf16x2(u[i]);
+        v[2 * i] += f.x;
+        v[2 * i + 1] += f.y;
+    }
+}
+
+template <int BN>
+__global__ void __launch_bounds__(192, 1)
+    conv_tc_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_h,
+                   const __grid_constant__ CUtensorMap tm_w, const ConvArgs a, const TcGeo g) {
+    using C = Cfg<BN>;
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw_addr = smem_u32(smem_raw);
+    uint8_t* smem = smem_raw + (((raw_addr + 1023u) & ~1023u) - raw_addr);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE);
+    uint64_t* empty = full + C::STAGES;
+    uint64_t* tfull = empty + C::STAGES;
+    uint64_t* tempty = tfull + 2;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    // A context already in error skips the launch (decided once per CTA).
+    __shared__ int s_skip;
+    if (threadIdx.x == 0) s_skip = (a.status && *(volatile int*)a.status != 0) ? 1 : 0;
+    __syncthreads();
+    if (s_skip) return;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C::STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&tfull[i], 1);
+            mbar_init(&tempty[i], 4);
+        }
+        fence_mbar_init();
+    }
+    if (warp == 0 && lane == 0) {
+        tma_prefetch_desc(&tm_x);
+        tma_prefetch_desc(&tm_h);
+        tma_prefetch_desc(&tm_w);
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, C::TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ------------------------------------------------ TMA producer
+            int s = 0;
+            uint32_t ph = 0;
+            int last_ph[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) last_ph[i] = -1;
+            bool ok = true;
+            const int ph_ = (a.kh - 1) / 2, pw_ = (a.kw - 1) / 2;
+            for (long long tile = blockIdx.x; tile < g.num_tiles && ok; tile += gridDim.x) {
+                const TileCoord tc = decode_tile(a, g, tile);
+                for (int kb = 0; kb < g.nkb; ++kb) {
+                    if (!mbar_wait(&empty[s], ph ^ 1, a.status, a.wait_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    const int tap = kb / g.cpt, cb = kb - tap * g.cpt;
+                    const int dw = tap % a.kw, dh = (tap / a.kw) % a.kh, dt = tap / (a.kw * a.kh);
+                    const int ti = tc.to * a.st + dt + a.t_off;
+                    const CUtensorMap* src = &tm_x;
+                    int tcoord;
+                    if (ti >= 0) {
+                        tcoord = tc.n * a.Tin + ti;
+                    } else if (a.hist) {
+                        src = &tm_h;
+                        tcoord = tc.n * a.hist_T + a.hist_T + ti;
+                    } else if (a.pad_mode == 0) {
+                        tcoord = tc.n * a.Tin;
+                    } else {
+                        tcoord = -1;  // whole box out of range -> zeros
+                    }
+                    uint8_t* sa = smem + s * C::STAGE;
+                    uint8_t* sb = sa + A_BYTES;
+                    mbar_arrive_expect_tx(&full[s], C::STAGE);
+                    if (!g.strided) {
+                        tma_load_4d(sa, src, &full[s], cb * 64, tc.tw * g.BW + dw - pw_, tc.th * g.BH + dh - ph_,
+                                    tcoord);
+                    } else {
+                        const int pwp = (dw == 1) ? 0 : 1, php = (dh == 1) ? 0 : 1;
+                        tma_load_5d(sa, src, &full[s], pwp * a.Cin + cb * 64, tc.tw * g.BW + (dw == 0 ? -1 : 0), php,
+                                    tc.th * g.BH + (dh == 0 ? -1 : 0), tcoord);
+                    }
+                    tma_load_2d(sb, &tm_w, &full[s], tap * a.Cin + cb * 64, tc.nt * BN);
+                    last_ph[s] = (int)ph;
+                    if (++s == C::STAGES) {
+                        s = 0;
+                        ph ^= 1;
+                    }
+                }
+            }
+            // make sure no copy is still in flight before the CTA may exit
+            for (int i = 0; i < C::STAGES; ++i)
+                if (last_ph[i] >= 0) mbar_wait(&full[i], (uint32_t)last_ph[i], a.status, a.wait_ns);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ------------------------------------------------ MMA issuer
+            int s = 0;
+            uint32_t ph = 0;
+            int last_acc_ph[2] = {-1, -1};
+            bool ok = true;
+            int it = 0;
+            for (long long tile = blockIdx.x; tile < g.num_tiles && ok; tile += gridDim.x, ++it) {
+                const int acc = it & 1;
+                const uint32_t aph = (uint32_t)((it >> 1) & 1);
+                if (!mbar_wait(&tempty[acc], aph ^ 1, a.status, a.wait_ns)) break;
+                tc_fence_after();
+                const uint32_t d = tmem_base + (uint32_t)(acc * BN);
+                for (int kb = 0; kb < g.nkb; ++kb) {
+                    if (!mbar_wait(&full[s], ph, a.status, a.wait_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(smem + s * C::STAGE);
+                    const uint32_t sb = sa + A_BYTES;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        tc_mma_bf16(d, sw128_desc(sa + k * 32), sw128_desc(sb + k * 32), C::IDESC,
+                                    (kb | k) != 0 ? 1u : 0u);
+                    tc_commit(&empty[s]);
+                    if (++s == C::STAGES) {
+                        s = 0;
+                        ph ^= 1;
+                    }
+                }
+                tc_commit(&tfull[acc]);
+                last_acc_ph[acc] = (int)aph;
+            }
+            // wait for our own MMAs before TMEM can be released
+            for (int i = 0; i < 2; ++i)
+                if (last_acc_ph[i] >= 0) mbar_wait(&tfull[i], (uint32_t)last_acc_ph[i], a.status, a.wait_ns);
+        }
+    } else {
+        // ---------------------------------------------------- epilogue
+        const int q = warp & 3;  // TMEM lane quarter accessible to this warp
+        const int r = q * 32 + lane;
+        int it = 0;
+        for (long long tile = blockIdx.x; tile < g.num_tiles; tile += gridDim.x, ++it) {
+            const int acc = it & 1;
+            const uint32_t aph = (uint32_t)((it >> 1) & 1);
+            int okw = 1;
+            if (lane == 0) okw = mbar_wait(&tfull[acc], aph, a.status, a.wait_ns) ? 1 : 0;
+            okw = __shfl_sync(0xffffffffu, okw, 0);
+            if (!okw) break;
+            tc_fence_after();
+            const TileCoord tc = decode_tile(a, g, tile);
+            const int ho = tc.th * g.BH + r / g.BW;
+            const int wo = tc.tw * g.BW + r % g.BW;
+            const bool valid = ho < a.Hout && wo < a.Wout;
+            const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
+            const long long vox = (((long long)tc.n * a.Tout + tc.to) * a.Hout + ho) * a.Wout + wo;
+#pragma unroll 1
+            for (int c16 = 0; c16 < BN / 16; ++c16) {
+                float v[16];
+                tmem_ld16(tbase + (uint32_t)(c16 * 16), v);
+                const int co0 = tc.nt * BN + c16 * 16;
+                if (!valid || co0 >= a.Cout) continue;
+                if (a.bias) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v[j] += (co0 + j < a.Cout) ? a.bias[co0 + j] : 0.f;
+                }
+                if (a.mode == OUT_PLAIN) {
+                    const long long off = ((((long long)tc.n * a.oT + tc.to) * a.oH + ho) * a.oW + wo) * a.oC + co0;
+                    if (a.residual) add_bf16x16(static_cast<const __nv_bfloat16*>(a.residual) + off, v);
+                    store_bf16x16(static_cast<__nv_bfloat16*>(a.out) + off, v);
+                } else if (a.mode == OUT_D2S) {
+                    if ((a.oC & 15) == 0) {
+                        const int sub = co0 / a.oC, ch0 = co0 - sub * a.oC;
+                        const int c = sub % a.rw, b = (sub / a.rw) % a.rh, t = sub / (a.rw * a.rh);
+                        const int ot = tc.to * a.rt + t - a.drop_t, oh = ho * a.rh + b, ow = wo * a.rw + c;
+                        if (ot >= 0 && ot < a.oT && oh < a.oH && ow < a.oW) {
+                            const long long off =
+                                ((((long long)tc.n * a.oT + ot) * a.oH + oh) * a.oW + ow) * a.oC + ch0;
+                            if (a.out_fp32) {
+                                float* o = static_cast<float*>(a.out) + off;
+#pragma unroll
+                                for (int j = 0; j < 16; ++j) o[j] = v[j];
+                            } else {
+                                store_bf16x16(static_cast<__nv_bfloat16*>(a.out) + off, v);
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const int co = co0 + j;
+                            if (co >= a.Cout) break;
+                            const int sub = co / a.oC, ch = co - sub * a.oC;
+                            const int c = sub % a.rw, b = (sub / a.rw) % a.rh, t = sub / (a.rw * a.rh);
+                            const int ot = tc.to * a.rt + t - a.drop_t, oh = ho * a.rh + b, ow = wo * a.rw + c;
+                            if (ot < 0 || ot >= a.oT || oh >= a.oH || ow >= a.oW) continue;
+                            const long long off =
+                                ((((long long)tc.n * a.oT + ot) * a.oH + oh) * a.oW + ow) * a.oC + ch;
+                            if (a.out_fp32)
+                                static_cast<float*>(a.out)[off] = v[j];
+                            else
+                                static_cast<__nv_bfloat16*>(a.out)[off] = __float2bfloat16_rn(v[j]);
+                        }
+                    }
+                } else {  // OUT_FSQ: the latent z (fp32) and its token index
+                    float* z = static_cast<float*>(a.out) + vox * a.fsq.nlev;
+                    int idx = 0;
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        if (j < a.fsq.nlev) {
+                            z[j] = v[j];
+                            const float b = tanhf(v[j] + a.fsq.shift[j]) * a.fsq.half_l[j] - a.fsq.offset[j];
+                            const int d = (int)rintf(b) + a.fsq.half_w[j];
+                            idx += d * a.fsq.basis[j];
+                        }
+                    }
+                    if (a.idx) a.idx[vox] = idx;
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[acc]);
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) tmem_dealloc(tmem_base, C::TMEM_COLS);
+}
+
+// ------------------------------------------------------------------ host side
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// Activation map: plain (C, W, H, N*T) or parity view (2C, W/2, 2, H/2, N*T).
+bool encode_act_map(CUtensorMap* m, const void* base, int frames, int H, int W, int C, int BH, int BW,
+                    bool strided) {
+    auto enc = get_encode_fn();
+    if (!enc) return false;
+    const uint64_t es = 2;
+    CUresult r;
+    if (!strided) {
+        cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)frames};
+        cuuint64_t strides[3] = {C * es, (uint64_t)W * C * es, (uint64_t)H * W * C * es};
+        cuuint32_t box[4] = {64, (cuuint32_t)BW, (cuuint32_t)BH, 1};
+        cuuint32_t estr[4] = {1, 1, 1, 1};
+        r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else {
+        cuuint64_t dims[5] = {(cuuint64_t)(2 * C), (cuuint64_t)(W / 2), 2, (cuuint64_t)(H / 2),
+                              (cuuint64_t)frames};
+        cuuint64_t strides[4] = {2 * C * es, (uint64_t)W * C * es, 2ull * W * C * es, (uint64_t)H * W * C * es};
+        cuuint32_t box[5] = {64, (cuuint32_t)BW, 1, (cuuint32_t)BH, 1};
+        cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+        r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(base), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
+    return r == CUDA_SUCCESS;
+}
+
+bool encode_w_map(CUtensorMap* m, const void* base, int rows, int Kpad, int BN) {
+    auto enc = get_encode_fn();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)Kpad, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)Kpad * 2};
+    cuuint32_t box[2] = {64, (cuuint32_t)BN};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN>
+int launch_bn(const ConvArgs& a, TcGeo g, int num_sms, cudaStream_t stream) {
+    using C = Cfg<BN>;
+    CUtensorMap mx, mh, mw;
+    const bool strided = g.strided != 0;
+    if (!encode_act_map(&mx, a.x, a.N * a.Tin, a.Hin, a.Win, a.Cin, g.BH, g.BW, strided)) return -1;
+    if (a.hist) {
+        if (!encode_act_map(&mh, a.hist, a.N * a.hist_T, a.Hin, a.Win, a.Cin, g.BH, g.BW, strided)) return -1;
+    } else {
+        mh = mx;
+    }
+    if (!encode_w_map(&mw, a.w, a.Cout_pad, a.Kpad, BN)) return -1;
+    g.n_tiles = a.Cout_pad / BN;
+    const long long m_tiles = (long long)a.N * a.Tout * g.tiles_h * g.tiles_w;
+    g.num_tiles = m_tiles * g.n_tiles;
+    if (g.num_tiles == 0) return 0;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(conv_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+        attr_set = true;
+    }
+    const int grid = (int)std::min<long long>(g.num_tiles, num_sms);
+    conv_tc_kernel<BN><<<grid, 192, C::SMEM, stream>>>(mx, mh, mw, a, g);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace
+
+// Choose the output tile shape (BH x BW = 128) that covers Hout x Wout with
+// the fewest tiles; ties go to the wider tile (longer contiguous rows).
+void choose_tile(int Hout, int Wout, int* BH, int* BW) {
+    long long best = -1;
+    for (int bw : {128, 64, 32, 16, 8}) {
+        int bh = 128 / bw;
+        long long t = (long long)((Wout + bw - 1) / bw) * ((Hout + bh - 1) / bh);
+        if (best < 0 || t < best) {
+            best = t;
+            *BW = bw;
+            *BH = bh;
+        }
+    }
+}
+
+int conv_tc_bn(int Cout_pad) {
+    if (Cout_pad >= 256) return 256;
+    if (Cout_pad >= 128) return 128;
+    if (Cout_pad >= 64) return 64;
+    if (Cout_pad >= 32) return 32;
+    return 16;
+}
+
+// Requirements (checked by the caller's plan): Cin % 64 == 0, Cout_pad a
+// multiple of the chosen BN, Kpad = taps * Cin, strided convs have
+// sh == sw == 2 with even Hin and Win, bf16 tensors 16-byte aligned.
+int launch_conv_tc(const ConvArgs& a, int num_sms, cudaStream_t stream) {
+    TcGeo g;
+    choose_tile(a.Hout, a.Wout, &g.BH, &g.BW);
+    g.tiles_w = (a.Wout + g.BW - 1) / g.BW;
+    g.tiles_h = (a.Hout + g.BH - 1) / g.BH;
+    g.cpt = a.Cin / 64;
+    g.nkb = a.kt * a.kh * a.kw * g.cpt;
+    g.strided = (a.sh == 2) ? 1 : 0;
+    g.n_tiles = 0;
+    g.num_tiles = 0;
+    switch (conv_tc_bn(a.Cout_pad)) {
+        case 256: return launch_bn<256>(a, g, num_sms, stream);
+        case 128: return launch_bn<128>(a, g, num_sms, stream);
+        case 64: return launch_bn<64>(a, g, num_sms, stream);
+        case 32: return launch_bn<32>(a, g, num_sms, stream);
+        default: return launch_bn<16>(a, g, num_sms, stream);
+    }
+}
+
+}  // namespace tok

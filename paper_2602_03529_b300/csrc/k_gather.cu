@@ -1,0 +1,188 @@
+// Gather kernels feeding the tensor-core convolution where the input has too
+// few channels for 64-channel K blocks: the pixel stem (3 channels) and the
+// decoder input (the nlev FSQ code channels, dequantised on the fly). Each
+// builds the im2col matrix A (M x Kpad, BF16) of one causal conv, with
+// K = (tap, ci), zero columns up to Kpad, the time-causal pad (history frames,
+// replicate or zero), zero spatial pad, and, for pixels, edge extension of the
+// frame from H x W to the padded Hp x Wp. Also the edge pad used by the FP32
+// path. All bandwidth-bound; one thread writes 8 consecutive K entries.
+#include "common.cuh"
+#include "conv_args.h"
+
+namespace tok {
+
+namespace {
+
+// Source location of (output voxel, tap) or -1 for a zero tap.
+// Returns (frame index into `x` or into `hist` (flag), h, w).
+__device__ __forceinline__ bool gather_src(const GatherGeo& g, int n, int to, int ho, int wo, int tap,
+                                           bool* from_hist, long long* frame, int* hi, int* wi) {
+    const int dw = tap % g.kw, dh = (tap / g.kw) % g.kh, dt = tap / (g.kw * g.kh);
+    int h = ho * g.sh + dh - (g.kh - 1) / 2;
+    int w = wo * g.sw + dw - (g.kw - 1) / 2;
+    if (h < 0 || h >= g.Hp || w < 0 || w >= g.Wp) return false;
+    *hi = h < g.H ? h : g.H - 1;  // edge extension of the padded frame
+    *wi = w < g.W ? w : g.W - 1;
+    const int ti = to * g.st + dt + g.t_off;
+    *from_hist = false;
+    if (ti >= 0) {
+        *frame = (long long)n * g.Tin + ti;
+    } else if (g.hist_T > 0) {
+        *from_hist = true;
+        *frame = (long long)n * g.hist_T + g.hist_T + ti;
+    } else if (g.pad_mode == 0) {
+        *frame = (long long)n * g.Tin;
+    } else {
+        return false;
+    }
+    return true;
+}
+
+__global__ void im2col_pixels_kernel(const __nv_bfloat16* __restrict__ x, const __nv_bfloat16* __restrict__ hist,
+                                     GatherGeo g, __nv_bfloat16* __restrict__ A) {
+    const long long M = (long long)g.N * g.Tout * g.Hout * g.Wout;
+    const int kg = g.Kpad / 8;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= M * kg) return;
+    const long long m = t / kg;
+    const int k0 = (int)(t % kg) * 8;
+    long long mm = m;
+    const int wo = (int)(mm % g.Wout); mm /= g.Wout;
+    const int ho = (int)(mm % g.Hout); mm /= g.Hout;
+    const int to = (int)(mm % g.Tout);
+    const int n = (int)(mm / g.Tout);
+    const int K = g.kt * g.kh * g.kw * g.Cin;
+    float v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        v[e] = 0.f;
+        const int k = k0 + e;
+        if (k < K) {
+            bool fh;
+            long long fr;
+            int hi, wi;
+            if (gather_src(g, n, to, ho, wo, k / g.Cin, &fh, &fr, &hi, &wi)) {
+                const __nv_bfloat16* src = fh ? hist : x;
+                v[e] = __bfloat162float(src[((fr * g.H + hi) * g.W + wi) * g.Cin + (k % g.Cin)]);
+            }
+        }
+    }
+    uint4 o;
+    o.x = pack_bf16x2(v[0], v[1]);
+    o.y = pack_bf16x2(v[2], v[3]);
+    o.z = pack_bf16x2(v[4], v[5]);
+    o.w = pack_bf16x2(v[6], v[7]);
+    reinterpret_cast<uint4*>(A)[t] = o;
+}
+
+__device__ __forceinline__ float code_of(int id, const FsqConsts& f, int i) {
+    const int d = (id / f.basis[i]) % f.levels[i];
+    return (float)(d - f.half_w[i]) / (float)f.half_w[i];
+}
+
+__global__ void im2col_tokens_kernel(const int32_t* __restrict__ idx, const int32_t* __restrict__ hist, GatherGeo g,
+                                     FsqConsts f, __nv_bfloat16* __restrict__ A) {
+    const long long M = (long long)g.N * g.Tout * g.Hout * g.Wout;
+    const int kg = g.Kpad / 8;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= M * kg) return;
+    const long long m = t / kg;
+    const int k0 = (int)(t % kg) * 8;
+    long long mm = m;
+    const int wo = (int)(mm % g.Wout); mm /= g.Wout;
+    const int ho = (int)(mm % g.Hout); mm /= g.Hout;
+    const int to = (int)(mm % g.Tout);
+    const int n = (int)(mm / g.Tout);
+    const int K = g.kt * g.kh * g.kw * g.Cin;
+    float v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+        v[e] = 0.f;
+        const int k = k0 + e;
+        if (k < K) {
+            bool fh;
+            long long fr;
+            int hi, wi;
+            if (gather_src(g, n, to, ho, wo, k / g.Cin, &fh, &fr, &hi, &wi)) {
+                const int32_t* src = fh ? hist : idx;
+                v[e] = code_of(src[(fr * g.H + hi) * g.W + wi], f, k % g.Cin);
+            }
+        }
+    }
+    uint4 o;
+    o.x = pack_bf16x2(v[0], v[1]);
+    o.y = pack_bf16x2(v[2], v[3]);
+    o.z = pack_bf16x2(v[4], v[5]);
+    o.w = pack_bf16x2(v[6], v[7]);
+    reinterpret_cast<uint4*>(A)[t] = o;
+}
+
+template <typename T>
+__global__ void edge_pad_kernel(const T* __restrict__ x, long long frames, int H, int W, int Hp, int Wp, int C,
+                                T* __restrict__ y) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long total = frames * Hp * Wp * C;
+    if (t >= total) return;
+    long long r = t;
+    const int c = (int)(r % C); r /= C;
+    const int w = (int)(r % Wp); r /= Wp;
+    const int h = (int)(r % Hp);
+    const long long f = r / Hp;
+    const int hi = h < H ? h : H - 1, wi = w < W ? w : W - 1;
+    y[t] = x[((f * H + hi) * W + wi) * C + c];
+}
+
+template <typename T>
+__global__ void pack_weights_kernel(const float* __restrict__ w, int Cout, int K, int Cout_pad, int Kpad,
+                                    T* __restrict__ out) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)Cout_pad * Kpad) return;
+    const int co = (int)(t / Kpad), k = (int)(t % Kpad);
+    const float v = (co < Cout && k < K) ? w[(long long)co * K + k] : 0.f;
+    if constexpr (sizeof(T) == 2)
+        out[t] = __float2bfloat16_rn(v);
+    else
+        out[t] = v;
+}
+
+inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+}  // namespace
+
+int launch_im2col_pixels(const __nv_bfloat16* x, const __nv_bfloat16* hist, const GatherGeo& g, __nv_bfloat16* A,
+                         cudaStream_t s) {
+    const long long n = (long long)g.N * g.Tout * g.Hout * g.Wout * (g.Kpad / 8);
+    if (n <= 0) return 0;
+    im2col_pixels_kernel<<<blocks_for(n, 256), 256, 0, s>>>(x, hist, g, A);
+    return (int)cudaGetLastError();
+}
+
+int launch_im2col_tokens(const int32_t* idx, const int32_t* hist, const GatherGeo& g, const FsqConsts& f,
+                         __nv_bfloat16* A, cudaStream_t s) {
+    const long long n = (long long)g.N * g.Tout * g.Hout * g.Wout * (g.Kpad / 8);
+    if (n <= 0) return 0;
+    im2col_tokens_kernel<<<blocks_for(n, 256), 256, 0, s>>>(idx, hist, g, f, A);
+    return (int)cudaGetLastError();
+}
+
+template <typename T>
+int launch_edge_pad(const T* x, long long frames, int H, int W, int Hp, int Wp, int C, T* y, cudaStream_t s) {
+    const long long n = frames * Hp * Wp * C;
+    if (n <= 0) return 0;
+    edge_pad_kernel<T><<<blocks_for(n, 256), 256, 0, s>>>(x, frames, H, W, Hp, Wp, C, y);
+    return (int)cudaGetLastError();
+}
+template int launch_edge_pad<float>(const float*, long long, int, int, int, int, int, float*, cudaStream_t);
+template int launch_edge_pad<int32_t>(const int32_t*, long long, int, int, int, int, int, int32_t*, cudaStream_t);
+
+template <typename T>
+int launch_pack_weights(const float* w, int Cout, int K, int Cout_pad, int Kpad, T* out, cudaStream_t s) {
+    const long long n = (long long)Cout_pad * Kpad;
+    if (n <= 0) return 0;
+    pack_weights_kernel<T><<<blocks_for(n, 256), 256, 0, s>>>(w, Cout, K, Cout_pad, Kpad, out);
+    return (int)cudaGetLastError();
+}
+template int launch_pack_weights<float>(const float*, int, int, int, int, float*, cudaStream_t);
+template int launch_pack_weights<__nv_bfloat16>(const float*, int, int, int, int, __nv_bfloat16*, cudaStream_t);
+
+}  // namespace tok

@@ -1,0 +1,237 @@
+// GroupNorm (statistics per sample, group and frame) fused with SiLU.
+//
+// Three passes over channels-last activations (x: frames x HW x C):
+//   gn_partial  : every block reduces one chunk of one frame to per-group
+//                 (count, mean, M2) triples. Each thread keeps sums shifted by
+//                 the first value it saw (so E[x^2]-E[x]^2 does not cancel),
+//                 then the block merges threads with Chan's pairwise update in
+//                 a fixed tree order (deterministic, no atomics).
+//   gn_finalize : one block per frame merges the chunk triples in chunk order
+//                 into mean and 1/sqrt(var + eps) per group.
+//   gn_apply    : SiLU((x - mean) * rstd * gamma + beta), 16-byte vectors.
+// The causal tokenizer may not mix frames, hence statistics per frame.
+#include "common.cuh"
+
+namespace tok {
+
+namespace {
+
+constexpr int NT = 256;
+
+template <typename T>
+struct Vec;
+template <>
+struct Vec<float> {
+    static constexpr int N = 4;
+    __device__ static void load(const float* p, float (&v)[4]) {
+        float4 q = *reinterpret_cast<const float4*>(p);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    }
+    __device__ static void store(float* p, const float (&v)[4]) {
+        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+};
+template <>
+struct Vec<__nv_bfloat16> {
+    static constexpr int N = 8;
+    __device__ static void load(const __nv_bfloat16* p, float (&v)[8]) {
+        uint4 q = *reinterpret_cast<const uint4*>(p);
+        uint32_t u[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            float2 f = unpack_bf16x2(u[i]);
+            v[2 * i] = f.x;
+            v[2 * i + 1] = f.y;
+        }
+    }
+    __device__ static void store(__nv_bfloat16* p, const float (&v)[8]) {
+        uint4 q;
+        q.x = pack_bf16x2(v[0], v[1]);
+        q.y = pack_bf16x2(v[2], v[3]);
+        q.z = pack_bf16x2(v[4], v[5]);
+        q.w = pack_bf16x2(v[6], v[7]);
+        *reinterpret_cast<uint4*>(p) = q;
+    }
+};
+
+struct Triple {
+    float n, mean, m2;
+};
+
+__device__ __forceinline__ Triple merge(Triple a, Triple b) {
+    if (b.n == 0.f) return a;
+    if (a.n == 0.f) return b;
+    Triple r;
+    r.n = a.n + b.n;
+    const float d = b.mean - a.mean;
+    const float fb = b.n / r.n;
+    r.mean = a.mean + d * fb;
+    r.m2 = a.m2 + b.m2 + d * d * a.n * fb;
+    return r;
+}
+
+// NGV = groups covered by one vector of V channels (V / channels-per-group,
+// or 1 when a group spans one or more whole vectors).
+template <typename T, int NGV>
+__global__ void __launch_bounds__(NT) gn_partial_kernel(const T* __restrict__ x, long long vec_per_frame, int C,
+                                                        int G, int S, int vpt, Triple* __restrict__ part) {
+    constexpr int V = Vec<T>::N;
+    constexpr int EPG = V / NGV;  // elements of my vector per group slot
+    __shared__ Triple red[NT][NGV];
+    const int frame = blockIdx.y, chunk = blockIdx.x, tid = threadIdx.x;
+    const int vpv = C / V;  // vectors per voxel (a power of two dividing NT)
+    const T* base = x + (long long)frame * vec_per_frame * V;
+    float K[NGV], s[NGV], q[NGV];
+    float cnt = 0.f;
+#pragma unroll
+    for (int k = 0; k < NGV; ++k) K[k] = s[k] = q[k] = 0.f;
+    const long long v0 = (long long)chunk * NT * vpt;
+    for (int i = 0; i < vpt; ++i) {
+        const long long vi = v0 + (long long)i * NT + tid;
+        if (vi >= vec_per_frame) break;
+        float v[V];
+        Vec<T>::load(base + vi * V, v);
+        if (i == 0) {
+#pragma unroll
+            for (int k = 0; k < NGV; ++k) K[k] = v[k * EPG];
+        }
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            const float d = v[j] - K[j / EPG];
+            s[j / EPG] += d;
+            q[j / EPG] = fmaf(d, d, q[j / EPG]);
+        }
+        cnt += (float)EPG;
+    }
+#pragma unroll
+    for (int k = 0; k < NGV; ++k) {
+        Triple t;
+        t.n = cnt;
+        t.mean = cnt > 0.f ? K[k] + s[k] / cnt : 0.f;
+        t.m2 = cnt > 0.f ? fmaxf(q[k] - s[k] * s[k] / cnt, 0.f) : 0.f;
+        red[tid][k] = t;
+    }
+    __syncthreads();
+    // tree over threads holding the same channels (tid, tid + stride, ...)
+    for (int stride = NT / 2; stride >= vpv; stride >>= 1) {
+        if (tid < stride) {
+#pragma unroll
+            for (int k = 0; k < NGV; ++k) red[tid][k] = merge(red[tid][k], red[tid + stride][k]);
+        }
+        __syncthreads();
+    }
+    // red[p][k] (p < vpv) now covers channels p*V + k*EPG ... ; fold into groups
+    const int cg = C / G;
+    for (int g = tid; g < G; g += NT) {
+        Triple acc = {0.f, 0.f, 0.f};
+        if (NGV > 1) {
+            const int p = (g * cg) / V, k = ((g * cg) % V) / EPG;
+            acc = red[p][k];
+        } else {
+            const int p0 = (g * cg) / V, np = cg / V;
+            for (int p = p0; p < p0 + np; ++p) acc = merge(acc, red[p][0]);
+        }
+        part[((long long)frame * S + chunk) * G + g] = acc;
+    }
+}
+
+__global__ void gn_finalize_kernel(const Triple* __restrict__ part, int S, int G, float eps,
+                                   float2* __restrict__ stats) {
+    const int frame = blockIdx.x;
+    for (int g = threadIdx.x; g < G; g += blockDim.x) {
+        Triple acc = {0.f, 0.f, 0.f};
+        for (int c = 0; c < S; ++c) acc = merge(acc, part[((long long)frame * S + c) * G + g]);
+        stats[(long long)frame * G + g] = make_float2(acc.mean, rsqrtf(acc.m2 / fmaxf(acc.n, 1.f) + eps));
+    }
+}
+
+template <typename T, bool FAST>
+__global__ void __launch_bounds__(NT) gn_apply_kernel(const T* __restrict__ x, T* __restrict__ y,
+                                                      long long vec_per_frame, int C, int G, int vpt,
+                                                      const float2* __restrict__ stats,
+                                                      const float* __restrict__ gamma,
+                                                      const float* __restrict__ beta) {
+    constexpr int V = Vec<T>::N;
+    const int frame = blockIdx.y, chunk = blockIdx.x, tid = threadIdx.x;
+    const int cg = C / G;
+    const int vpv = C / V;
+    const int c0 = (tid % vpv) * V;
+    float sc[V], sh[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+        const int c = c0 + j;
+        const float2 st = stats[(long long)frame * G + c / cg];
+        const float ga = gamma ? gamma[c] : 1.f;
+        sc[j] = st.y * ga;
+        sh[j] = (beta ? beta[c] : 0.f) - st.x * st.y * ga;
+    }
+    const long long fo = (long long)frame * vec_per_frame * V;
+    const long long v0 = (long long)chunk * NT * vpt;
+    for (int i = 0; i < vpt; ++i) {
+        const long long vi = v0 + (long long)i * NT + tid;
+        if (vi >= vec_per_frame) break;
+        float v[V];
+        Vec<T>::load(x + fo + vi * V, v);
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            const float h = fmaf(v[j], sc[j], sh[j]);
+            v[j] = FAST ? silu_fast(h) : silu_exact(h);
+        }
+        Vec<T>::store(y + fo + vi * V, v);
+    }
+}
+
+void gn_plan(long long frames, long long vec_per_frame, int num_sms, int* vpt, int* S) {
+    const long long total = frames * vec_per_frame;
+    const long long target_blocks = 4LL * num_sms;
+    long long v = (total + (long long)NT * target_blocks - 1) / ((long long)NT * target_blocks);
+    if (v < 1) v = 1;
+    if (v > 256) v = 256;
+    *vpt = (int)v;
+    *S = (int)((vec_per_frame + (long long)NT * v - 1) / ((long long)NT * v));
+}
+
+}  // namespace
+
+size_t gn_scratch_bytes(long long frames, long long HW, int C, int G, int num_sms, int vec) {
+    int vpt, S;
+    gn_plan(frames, HW * C / vec, num_sms, &vpt, &S);
+    return (size_t)frames * S * G * sizeof(Triple) + (size_t)frames * G * sizeof(float2) + 256;
+}
+
+// x, y: (frames, HW, C) channels-last; y may alias x. scratch: at least
+// gn_scratch_bytes(...). Requirements: C % V == 0, (C/V) a power of two
+// dividing 256, C/G >= 2, 16-byte aligned tensors.
+template <typename T>
+int launch_gn_silu(const T* x, T* y, long long frames, long long HW, int C, int G, const float* gamma,
+                   const float* beta, float eps, void* scratch, int num_sms, bool fast, cudaStream_t stream) {
+    constexpr int V = Vec<T>::N;
+    const long long vpf = HW * C / V;
+    int vpt, S;
+    gn_plan(frames, vpf, num_sms, &vpt, &S);
+    Triple* part = static_cast<Triple*>(scratch);
+    float2* stats = reinterpret_cast<float2*>(
+        (reinterpret_cast<uintptr_t>(part + frames * S * G) + 15) & ~uintptr_t(15));
+    dim3 grid(S, (unsigned)frames);
+    const int cg = C / G;
+    const int ngv = cg >= V ? 1 : V / cg;
+    switch (ngv) {
+        case 1: gn_partial_kernel<T, 1><<<grid, NT, 0, stream>>>(x, vpf, C, G, S, vpt, part); break;
+        case 2: gn_partial_kernel<T, 2><<<grid, NT, 0, stream>>>(x, vpf, C, G, S, vpt, part); break;
+        case 4: gn_partial_kernel<T, 4><<<grid, NT, 0, stream>>>(x, vpf, C, G, S, vpt, part); break;
+        default: return (int)cudaErrorInvalidValue;
+    }
+    gn_finalize_kernel<<<(unsigned)frames, 64, 0, stream>>>(part, S, G, eps, stats);
+    if (fast)
+        gn_apply_kernel<T, true><<<grid, NT, 0, stream>>>(x, y, vpf, C, G, vpt, stats, gamma, beta);
+    else
+        gn_apply_kernel<T, false><<<grid, NT, 0, stream>>>(x, y, vpf, C, G, vpt, stats, gamma, beta);
+    return (int)cudaGetLastError();
+}
+
+template int launch_gn_silu<float>(const float*, float*, long long, long long, int, int, const float*, const float*,
+                                   float, void*, int, bool, cudaStream_t);
+template int launch_gn_silu<__nv_bfloat16>(const __nv_bfloat16*, __nv_bfloat16*, long long, long long, int, int,
+                                           const float*, const float*, float, void*, int, bool, cudaStream_t);
+
+}  // namespace tok

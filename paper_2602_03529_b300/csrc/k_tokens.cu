@@ -1,0 +1,217 @@
+// Token-level kernels: FSQ quantise / dequantise, Philox-4x32-10 packet-drop
+// masking with zero fill, and the row packetisation of the token matrix.
+//
+// FSQ (finite scalar quantisation, Mentzer et al. 2023) turns each latent
+// vector into one integer token (the token matrix the codec transmits,
+// Sec. 4.3 / Sec. 6.2). Dropped tokens and lost rows are filled with the
+// zero-code index (Sec. 6.2 zero fill; random drop in training, Appendix A.2).
+// All kernels are HBM- or launch-bound; one token per thread, coalesced.
+#include "common.cuh"
+#include "conv_args.h"
+
+namespace tok {
+
+namespace {
+
+// ------------------------------------------------------------------ FSQ
+
+__global__ void fsq_kernel(const float* __restrict__ z, long long ntok, FsqConsts f, int32_t* __restrict__ idx,
+                           float* __restrict__ codes) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntok) return;
+    const float* zp = z + t * f.nlev;
+    int id = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        if (i < f.nlev) {
+            const float b = tanhf(zp[i] + f.shift[i]) * f.half_l[i] - f.offset[i];
+            const float q = rintf(b);
+            id += ((int)q + f.half_w[i]) * f.basis[i];
+            if (codes) codes[t * f.nlev + i] = q / (float)f.half_w[i];
+        }
+    }
+    idx[t] = id;
+}
+
+__global__ void dequant_kernel(const int32_t* __restrict__ idx, long long ntok, FsqConsts f,
+                               float* __restrict__ codes) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntok) return;
+    const int id = idx[t];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        if (i < f.nlev) {
+            const int d = (id / f.basis[i]) % f.levels[i];
+            codes[t * f.nlev + i] = (float)(d - f.half_w[i]) / (float)f.half_w[i];
+        }
+    }
+}
+
+// ----------------------------------------------------------- Philox drop
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k.x += W0;
+            k.y += W1;
+        }
+        const uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+        const uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    }
+    return c;
+}
+
+// One warp per (row, 32-token word): each lane decides one token; the warp
+// ballot is the row mask word of the packet header.
+__global__ void drop_kernel(const int32_t* __restrict__ idx, int N, int Tq, int Hq, int Wq, unsigned long long thr,
+                            uint2 key, uint32_t chunk_lo, uint32_t stream_lo, int32_t zero_index,
+                            int32_t* __restrict__ out, uint32_t* __restrict__ keep_bits) {
+    const int nwords = (Wq + 31) / 32;
+    const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int lane = threadIdx.x % 32;
+    const long long rows = (long long)N * Tq * Hq;
+    if (gw >= rows * nwords) return;
+    const long long row = gw / nwords;
+    const int word = (int)(gw % nwords);
+    const int w = word * 32 + lane;
+    const int n = (int)(row / ((long long)Tq * Hq));
+    const long long rin = row % ((long long)Tq * Hq);  // t*Hq + h within sample n
+    bool keep = false;
+    if (w < Wq) {
+        const uint32_t j = (uint32_t)(rin * Wq + w);
+        const uint4 r = philox4x32_10(make_uint4(j >> 2, (uint32_t)n, chunk_lo, stream_lo), key);
+        const uint32_t word32 = (j & 3) == 0 ? r.x : (j & 3) == 1 ? r.y : (j & 3) == 2 ? r.z : r.w;
+        keep = !((unsigned long long)word32 < thr);
+        const long long o = row * Wq + w;
+        out[o] = keep ? idx[o] : zero_index;
+    }
+    const uint32_t mask = __ballot_sync(0xffffffffu, keep);
+    if (keep_bits && lane == 0) keep_bits[row * nwords + word] = mask;
+}
+
+// --------------------------------------------------------- row packets
+
+__global__ void row_count_kernel(const uint32_t* __restrict__ keep_bits, long long rows, int nwords,
+                                 int64_t* __restrict__ counts) {
+    const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= rows) return;
+    int c = 0;
+    for (int i = 0; i < nwords; ++i) c += __popc(keep_bits[r * nwords + i]);
+    counts[r + 1] = c;  // shifted: exclusive scan done in place afterwards
+}
+
+// Single-block exclusive scan of counts[1..rows] into offsets[0..rows].
+__global__ void scan_kernel(int64_t* __restrict__ offs, long long rows) {
+    __shared__ int64_t carry;
+    __shared__ int64_t buf[1024];
+    if (threadIdx.x == 0) {
+        carry = 0;
+        offs[0] = 0;
+    }
+    __syncthreads();
+    for (long long base = 0; base < rows; base += 1024) {
+        const long long i = base + threadIdx.x;
+        buf[threadIdx.x] = (i < rows) ? offs[i + 1] : 0;
+        __syncthreads();
+        for (int s = 1; s < 1024; s <<= 1) {
+            int64_t v = (threadIdx.x >= (unsigned)s) ? buf[threadIdx.x - s] : 0;
+            __syncthreads();
+            buf[threadIdx.x] += v;
+            __syncthreads();
+        }
+        if (i < rows) offs[i + 1] = carry + buf[threadIdx.x];
+        __syncthreads();
+        if (threadIdx.x == 1023) carry += buf[1023];
+        __syncthreads();
+    }
+}
+
+// One warp per row: compact the kept tokens (ballot + popc) into the payload.
+__global__ void pack_kernel(const int32_t* __restrict__ idx, const uint32_t* __restrict__ keep_bits, long long rows,
+                            int Wq, const int64_t* __restrict__ offs, int32_t* __restrict__ payload) {
+    const long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int lane = threadIdx.x % 32;
+    if (r >= rows) return;
+    const int nwords = (Wq + 31) / 32;
+    long long o = offs[r];
+    for (int wd = 0; wd < nwords; ++wd) {
+        const uint32_t m = keep_bits[r * nwords + wd];
+        const int w = wd * 32 + lane;
+        if ((m >> lane) & 1u) payload[o + __popc(m & ((1u << lane) - 1u))] = idx[r * Wq + w];
+        o += __popc(m);
+    }
+}
+
+__global__ void unpack_kernel(const int32_t* __restrict__ payload, const int64_t* __restrict__ offs,
+                              const uint32_t* __restrict__ keep_bits, const uint8_t* __restrict__ received,
+                              long long rows, int Wq, int32_t zero_index, int32_t* __restrict__ out) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= rows * Wq) return;
+    const long long r = t / Wq;
+    const int w = (int)(t % Wq);
+    int32_t v = zero_index;
+    if (received == nullptr || received[r]) {
+        const int nwords = (Wq + 31) / 32;
+        const uint32_t* kb = keep_bits + r * nwords;
+        const uint32_t m = kb[w / 32];
+        if ((m >> (w % 32)) & 1u) {
+            int rank = __popc(m & ((1u << (w % 32)) - 1u));
+            for (int i = 0; i < w / 32; ++i) rank += __popc(kb[i]);
+            v = payload[offs[r] + rank];
+        }
+    }
+    out[t] = v;
+}
+
+inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+}  // namespace
+
+int launch_fsq(const float* z, long long ntok, const FsqConsts& f, int32_t* idx, float* codes, cudaStream_t s) {
+    if (ntok <= 0) return 0;
+    fsq_kernel<<<blocks_for(ntok, 256), 256, 0, s>>>(z, ntok, f, idx, codes);
+    return (int)cudaGetLastError();
+}
+
+int launch_dequant(const int32_t* idx, long long ntok, const FsqConsts& f, float* codes, cudaStream_t s) {
+    if (ntok <= 0) return 0;
+    dequant_kernel<<<blocks_for(ntok, 256), 256, 0, s>>>(idx, ntok, f, codes);
+    return (int)cudaGetLastError();
+}
+
+int launch_drop(const int32_t* idx, int N, int Tq, int Hq, int Wq, unsigned long long thr, uint64_t seed,
+                uint64_t stream_id, uint64_t chunk_id, int32_t zero_index, int32_t* out, uint32_t* keep_bits,
+                cudaStream_t s) {
+    const long long rows = (long long)N * Tq * Hq;
+    const long long threads = rows * ((Wq + 31) / 32) * 32;
+    if (threads <= 0) return 0;
+    const uint2 key = make_uint2((uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32));
+    drop_kernel<<<blocks_for(threads, 256), 256, 0, s>>>(idx, N, Tq, Hq, Wq, thr, key,
+                                                         (uint32_t)(chunk_id & 0xffffffffu),
+                                                         (uint32_t)(stream_id & 0xffffffffu), zero_index, out,
+                                                         keep_bits);
+    return (int)cudaGetLastError();
+}
+
+int launch_pack(const int32_t* idx, const uint32_t* keep_bits, long long rows, int Wq, int32_t* payload,
+                int64_t* offs, cudaStream_t s) {
+    if (rows <= 0) return 0;
+    const int nwords = (Wq + 31) / 32;
+    row_count_kernel<<<blocks_for(rows, 256), 256, 0, s>>>(keep_bits, rows, nwords, offs);
+    scan_kernel<<<1, 1024, 0, s>>>(offs, rows);
+    pack_kernel<<<blocks_for(rows * 32, 256), 256, 0, s>>>(idx, keep_bits, rows, Wq, offs, payload);
+    return (int)cudaGetLastError();
+}
+
+int launch_unpack(const int32_t* payload, const int64_t* offs, const uint32_t* keep_bits, const uint8_t* received,
+                  long long rows, int Wq, int32_t zero_index, int32_t* out, cudaStream_t s) {
+    const long long n = rows * Wq;
+    if (n <= 0) return 0;
+    unpack_kernel<<<blocks_for(n, 256), 256, 0, s>>>(payload, offs, keep_bits, received, rows, Wq, zero_index, out);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace tok

@@ -1,0 +1,231 @@
+"""Torch-tensor front end of the tokenizer library (thin marshalling layer).
+
+PyTorch provides device memory and streams; every step of encode/decode runs
+in the CUDA library through the C-ABI (see ``_lib``). Tensors must be CUDA,
+contiguous, channels-last: clips (N, T, H, W, 3), latents (N, T', H', W', C),
+token indices (N, T', H', W') int32.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+PRECISIONS = {"bf16": L.TOK_BF16, "fp32": L.TOK_FP32}
+
+
+def make_arch(kind="full", ch=(128, 256, 512), blocks=2, levels=(8, 8, 8, 5, 5, 5), gn_groups=32,
+              gn_eps=1e-6, time_pad="replicate") -> L.tok_arch:
+    a = L.tok_arch_default()
+    a.kind = L.TOK_ARCH_FULL if kind == "full" else L.TOK_ARCH_STAGE
+    a.nlevels = len(ch)
+    for i in range(4):
+        a.ch[i] = ch[i] if i < len(ch) else 0
+    a.blocks = blocks
+    a.nlev = len(levels)
+    for i in range(8):
+        a.levels[i] = levels[i] if i < len(levels) else 0
+    a.gn_groups = gn_groups
+    a.gn_eps = gn_eps
+    a.time_pad = L.TOK_PAD_REPLICATE if time_pad == "replicate" else L.TOK_PAD_ZERO
+    return a
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+def _ptr(t: torch.Tensor | None):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+class Tokenizer:
+    """One tokenizer context (weights resident on the device)."""
+
+    def __init__(self, precision: str = "bf16", **arch):
+        self.precision = precision
+        self.arch_kw = arch
+        self.arch = make_arch(**arch)
+        self.levels = tuple(arch.get("levels", (8, 8, 8, 5, 5, 5)))
+        self.ctx = L.tok_create(self.arch, PRECISIONS[precision])
+        self.dtype = torch.bfloat16 if precision == "bf16" else torch.float32
+
+    # -- parameters -------------------------------------------------------
+    def param_list(self):
+        """[(name, shape)] in the architecture's order."""
+        return [L.tok_param_info(self.ctx, i) for i in range(L.tok_param_count(self.ctx))]
+
+    def param_spec(self):
+        """[(name, shape, kind)] with kind conv / bias / gn_gamma / gn_beta."""
+        out = []
+        for name, shape in self.param_list():
+            if len(shape) == 5:
+                kind = "conv"
+            elif name.endswith(".g"):
+                kind = "gn_gamma"
+            elif ".gn" in name or name.endswith("_gn.b"):
+                kind = "gn_beta"
+            else:
+                kind = "bias"
+            out.append((name, shape, kind))
+        return out
+
+    def set_params(self, params: dict):
+        for name, shape in self.param_list():
+            a = np.ascontiguousarray(params[name], dtype=np.float32)
+            if tuple(a.shape) != tuple(shape):
+                raise ValueError(f"{name}: shape {a.shape} != {shape}")
+            L.tok_set_param(self.ctx, name, a.ctypes.data_as(C.c_void_p).value, a.size)
+
+    # -- shapes / workspace ----------------------------------------------
+    def latent_shape(self, T, H, W):
+        return L.tok_latent_shape(self.ctx, T, H, W)
+
+    def reserve(self, N, T, H, W):
+        L.tok_reserve(self.ctx, N, T, H, W)
+
+    def workspace_bytes(self, N, T, H, W):
+        return L.tok_workspace_bytes(self.ctx, N, T, H, W)
+
+    # -- encode / decode --------------------------------------------------
+    def encode(self, x: torch.Tensor, z: torch.Tensor | None = None, idx: torch.Tensor | None = None,
+               stream=None, want_z=True):
+        N, T, H, W, c = x.shape
+        if x.dtype != self.dtype:
+            raise ValueError(f"x must be {self.dtype}")
+        Tq, Hq, Wq = self.latent_shape(T, H, W)
+        if z is None and want_z:
+            z = torch.empty((N, Tq, Hq, Wq, len(self.levels)), device=x.device, dtype=torch.float32)
+        if idx is None:
+            idx = torch.empty((N, Tq, Hq, Wq), device=x.device, dtype=torch.int32)
+        L.tok_encode(self.ctx, _ptr(x), N, T, H, W, _ptr(z), _ptr(idx), None, _stream_ptr(stream))
+        return z, idx
+
+    def decode(self, idx: torch.Tensor, H: int, W: int, out: torch.Tensor | None = None, stream=None):
+        N, Tq, Hq, Wq = idx.shape
+        T = 1 + (Tq - 1) * self.s_t
+        if out is None:
+            out = torch.empty((N, T, H, W, 3), device=idx.device, dtype=torch.float32)
+        L.tok_decode(self.ctx, _ptr(idx), N, Tq, Hq, Wq, H, W, _ptr(out), None, _stream_ptr(stream))
+        return out
+
+    @property
+    def s_t(self):
+        return 1 if self.arch.kind == L.TOK_ARCH_STAGE else 2 ** (self.arch.nlevels - 1)
+
+    def status(self) -> int:
+        return L.tok_status(self.ctx)
+
+    def launch_count(self) -> int:
+        return L.tok_launch_count(self.ctx)
+
+    def profile(self, on: bool = True):
+        L.tok_profile_enable(self.ctx, on)
+
+    def profile_read(self) -> dict:
+        return L.tok_profile_read(self.ctx)
+
+    def close(self):
+        if self.ctx:
+            L.tok_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# -- stand-alone token ops ----------------------------------------------------
+
+def quantize(z: torch.Tensor, levels=(8, 8, 8, 5, 5, 5), codes=False, stream=None):
+    ntok = z.numel() // len(levels)
+    idx = torch.empty(z.shape[:-1], device=z.device, dtype=torch.int32)
+    cd = torch.empty_like(z) if codes else None
+    L.tok_quantize(_ptr(z), ntok, list(levels), _ptr(idx), _ptr(cd), _stream_ptr(stream))
+    return (idx, cd) if codes else idx
+
+
+def dequantize(idx: torch.Tensor, levels=(8, 8, 8, 5, 5, 5), stream=None):
+    out = torch.empty((*idx.shape, len(levels)), device=idx.device, dtype=torch.float32)
+    L.tok_dequantize(_ptr(idx), idx.numel(), list(levels), _ptr(out), _stream_ptr(stream))
+    return out
+
+
+def zero_index(levels=(8, 8, 8, 5, 5, 5)) -> int:
+    return L.tok_zero_index(list(levels))
+
+
+def drop_mask(idx: torch.Tensor, rate: float, seed: int, stream_id: int = 0, chunk_id: int = 0,
+              levels=(8, 8, 8, 5, 5, 5), keep_bits=True, out=None, stream=None):
+    N, Tq, Hq, Wq = idx.shape
+    if out is None:
+        out = torch.empty_like(idx)
+    kb = None
+    if keep_bits:
+        kb = torch.empty((N, Tq, Hq, (Wq + 31) // 32), device=idx.device, dtype=torch.int32)
+    L.tok_drop_mask(_ptr(idx), N, Tq, Hq, Wq, float(rate), int(seed), int(stream_id), int(chunk_id),
+                    zero_index(levels), _ptr(out), _ptr(kb), _stream_ptr(stream))
+    return out, kb
+
+
+def pack_rows(idx: torch.Tensor, keep_bits: torch.Tensor, stream=None):
+    Wq = idx.shape[-1]
+    rows = idx.numel() // Wq
+    payload = torch.empty(idx.numel(), device=idx.device, dtype=torch.int32)
+    offs = torch.empty(rows + 1, device=idx.device, dtype=torch.int64)
+    L.tok_pack_rows(_ptr(idx), _ptr(keep_bits), rows, Wq, _ptr(payload), _ptr(offs), _stream_ptr(stream))
+    return payload, offs
+
+
+def unpack_rows(payload, offs, keep_bits, received, shape, levels=(8, 8, 8, 5, 5, 5), stream=None):
+    Wq = shape[-1]
+    rows = int(np.prod(shape)) // Wq
+    out = torch.empty(shape, device=payload.device, dtype=torch.int32)
+    L.tok_unpack_rows(_ptr(payload), _ptr(offs), _ptr(keep_bits), _ptr(received), rows, Wq, zero_index(levels),
+                      _ptr(out), _stream_ptr(stream))
+    return out
+
+
+def conv3d(x: torch.Tensor, w: torch.Tensor, bias: torch.Tensor | None = None, stride=(1, 1, 1),
+           time_pad="replicate", residual: torch.Tensor | None = None, stream=None):
+    """One causal conv through tok_conv3d. x (N,T,H,W,Cin) bf16 -> BF16 tensor-core path,
+    fp32 -> FP32 CUDA-core path; w (Cout,k,k,k,Cin) fp32, bias (Cout) fp32."""
+    prec = L.TOK_BF16 if x.dtype == torch.bfloat16 else L.TOK_FP32
+    N, T, H, W, Cin = x.shape
+    Cout, k = w.shape[0], w.shape[1]
+    st, sh, sw = stride
+    To = (T - 1) // st + 1
+    Ho = (H + 2 * ((k - 1) // 2) - k) // sh + 1
+    Wo = (W + 2 * ((k - 1) // 2) - k) // sw + 1
+    y = torch.empty((N, To, Ho, Wo, Cout), device=x.device, dtype=x.dtype)
+    nb = L.tok_conv3d_workspace_bytes(prec, Cin, Cout, k)
+    ws = torch.empty(nb, device=x.device, dtype=torch.uint8)
+    L.tok_conv3d(prec, _ptr(x), N, T, H, W, Cin, _ptr(w), _ptr(bias), Cout, k, st, sh, sw,
+                 L.TOK_PAD_REPLICATE if time_pad == "replicate" else L.TOK_PAD_ZERO, _ptr(residual), _ptr(y),
+                 _ptr(ws), nb, _stream_ptr(stream))
+    return y
+
+
+def groupnorm_silu(x: torch.Tensor, groups: int, gamma=None, beta=None, eps=1e-6, out=None, stream=None):
+    """GroupNorm (statistics per sample, group and frame) + SiLU of x (N,T,H,W,C)."""
+    prec = L.TOK_BF16 if x.dtype == torch.bfloat16 else L.TOK_FP32
+    N, T, H, W, Cc = x.shape
+    y = torch.empty_like(x) if out is None else out
+    nb = L.tok_groupnorm_workspace_bytes(prec, N * T, H * W, Cc, groups)
+    ws = torch.empty(nb, device=x.device, dtype=torch.uint8)
+    L.tok_groupnorm_silu(prec, _ptr(x), N * T, H * W, Cc, groups, _ptr(gamma), _ptr(beta), eps, _ptr(y), _ptr(ws),
+                         nb, _stream_ptr(stream))
+    return y

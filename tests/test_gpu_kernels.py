@@ -1,0 +1,174 @@
+"""Parity of the individual CUDA kernels against the FP64 oracle, through the C-ABI.
+
+Tolerances (stated here, derived in the design doc):
+  * conv, FP32 path: the oracle gets the same fp32 inputs; FP32 accumulation
+    of K terms plus one fp32 rounding: |gpu - ref| <= 1e-5 |ref| + 2e-6 * s,
+    s = max |ref|.
+  * conv, BF16 path: the oracle gets the bf16-rounded inputs and weights, so
+    products are exact; FP32 accumulation plus one bf16 output rounding:
+    |gpu - ref| <= 2^-8 |ref| + 2e-4 * s.
+  * GroupNorm+SiLU: FP32 statistics; fp32 output 1e-5 relative to the output
+    scale, bf16 output 2^-8 |ref| + 4e-3 (the input is bf16 already).
+  * FSQ, drop mask, packets: integer results, bit-exact (FSQ: away from a
+    rounding tie band of 2^-16 around .5, inside it counted).
+"""
+import numpy as np
+import pytest
+import torch
+
+import synthetic as S
+from oracle import ops
+
+pytestmark = pytest.mark.gpu
+LV = (8, 8, 8, 5, 5, 5)
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_2602_03529_b300 as P
+    P._lib.load()
+    return P
+
+
+def _dev(a, dtype=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dtype)
+
+
+CONV_CASES = [
+    # (N, T, H, W, Cin, Cout, k, stride, pad)
+    (1, 5, 16, 16, 64, 64, 3, (1, 1, 1), 0),
+    (1, 5, 12, 20, 64, 128, 3, (1, 1, 1), 1),          # ragged tiles in h and w
+    (2, 3, 8, 8, 128, 256, 3, (1, 1, 1), 0),            # batch, N tile 256
+    (1, 9, 16, 24, 64, 64, 3, (2, 2, 2), 0),            # strided (parity view)
+    (1, 9, 16, 24, 64, 64, 3, (2, 2, 2), 1),
+    (1, 4, 10, 12, 64, 128, 3, (1, 2, 2), 0),           # stride (1,2,2)
+    (1, 3, 7, 9, 128, 64, 1, (1, 1, 1), 0),             # 1x1x1 shortcut
+    (1, 3, 9, 40, 64, 16, 3, (1, 1, 1), 0),             # narrow N (output conv)
+    (1, 2, 6, 130, 64, 512, 3, (1, 1, 1), 0),           # W > 128, two N tiles of 256
+]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("case", CONV_CASES)
+def test_conv3d_parity(P, prec, case):
+    N, T, H, W, Cin, Cout, k, stride, pad = case
+    rng = np.random.default_rng(hash(case) % 2**32)
+    x = rng.standard_normal((N, T, H, W, Cin)).astype(np.float32)
+    w = (rng.standard_normal((Cout, k, k, k, Cin)) * np.sqrt(2.0 / (Cin * k ** 3))).astype(np.float32)
+    b = rng.standard_normal(Cout).astype(np.float32) * 0.1
+    if prec == "bf16":
+        x, w = S.to_bf16_f32(x), S.to_bf16_f32(w)
+    ref = ops.conv3d(x, w, b, stride, pad)
+    res = rng.standard_normal(ref.shape).astype(np.float32)
+    if prec == "bf16":
+        res = S.to_bf16_f32(res)
+    ref_r = ref + res
+    dt = torch.bfloat16 if prec == "bf16" else torch.float32
+    tp = "replicate" if pad == 0 else "zero"
+    y = P.conv3d(_dev(x, dt), _dev(w), _dev(b), stride, tp)
+    yr = P.conv3d(_dev(x, dt), _dev(w), _dev(b), stride, tp, residual=_dev(res, dt))
+    torch.cuda.synchronize()
+    for got, want in ((y, ref), (yr, ref_r)):
+        g = got.float().cpu().numpy().astype(np.float64)
+        s = np.abs(want).max()
+        if prec == "fp32":
+            tol = 1e-5 * np.abs(want) + 2e-6 * s
+        else:
+            tol = 2.0 ** -8 * np.abs(want) + 2e-4 * s
+        err = np.abs(g - want)
+        assert g.shape == want.shape
+        assert np.all(err <= tol), (float(err.max()), float((err / (tol + 1e-30)).max()))
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("shape,G", [((1, 3, 16, 16, 128), 32), ((2, 2, 8, 12, 256), 32),
+                                     ((1, 2, 4, 4, 512), 32), ((1, 3, 5, 7, 16), 8), ((1, 2, 9, 9, 64), 32)])
+def test_groupnorm_silu_parity(P, prec, shape, G):
+    rng = np.random.default_rng(7)
+    x = (rng.standard_normal(shape) * 2 + 0.5).astype(np.float32)
+    C = shape[-1]
+    gam = (1 + 0.1 * rng.standard_normal(C)).astype(np.float32)
+    bet = (0.1 * rng.standard_normal(C)).astype(np.float32)
+    if prec == "bf16":
+        x = S.to_bf16_f32(x)
+    ref = ops.silu(ops.group_norm_frames(x, G, 1e-6, gam, bet))
+    dt = torch.bfloat16 if prec == "bf16" else torch.float32
+    y = P.groupnorm_silu(_dev(x, dt), G, _dev(gam), _dev(bet), 1e-6)
+    torch.cuda.synchronize()
+    g = y.float().cpu().numpy()
+    err = np.abs(g - ref)
+    tol = (1e-5 * (np.abs(ref) + 1.0)) if prec == "fp32" else (2.0 ** -8 * np.abs(ref) + 4e-3)
+    assert np.all(err <= tol), float(err.max())
+
+
+def test_fsq_parity_with_tie_band(P):
+    rng = np.random.default_rng(11)
+    z = (rng.standard_normal((1 << 20, 6)) * 1.5).astype(np.float32)
+    idx_ref, codes_ref, b = ops.fsq_quantize(z.astype(np.float64), LV)
+    idx, codes = P.quantize(_dev(z), LV, codes=True)
+    torch.cuda.synchronize()
+    idx = idx.cpu().numpy()
+    near_tie = (np.abs(np.abs(b - np.floor(b)) - 0.5) <= 2.0 ** -16).any(axis=1)
+    mism = idx != idx_ref
+    assert not np.any(mism & ~near_tie)
+    assert mism.sum() <= 1e-4 * len(idx)
+    ok = ~mism
+    np.testing.assert_array_equal(codes.cpu().numpy()[ok], codes_ref[ok].astype(np.float32))
+
+
+def test_fsq_closed_forms_on_gpu(P):
+    z = torch.zeros((4, 6), device="cuda")
+    z[1] = 50.0
+    z[2] = -50.0
+    idx = P.quantize(z, LV).cpu().numpy()
+    assert idx.tolist()[:3] == [32036, 63999, 0]
+    all_idx = torch.arange(64000, device="cuda", dtype=torch.int32)
+    codes = P.dequantize(all_idx, LV).cpu().numpy()
+    np.testing.assert_array_equal(codes, ops.fsq_dequantize(np.arange(64000), LV).astype(np.float32))
+
+
+@pytest.mark.parametrize("rate", [0.0, 0.13, 0.3, 1.0])
+@pytest.mark.parametrize("shape", [(1, 5, 45, 80), (2, 1, 7, 37), (1, 3, 135, 240)])
+def test_drop_mask_bit_exact(P, rate, shape):
+    N, Tq, Hq, Wq = shape
+    rng = np.random.default_rng(3)
+    idx = rng.integers(0, 64000, size=shape).astype(np.int32)
+    seed, sid, cid = (7 << 32) | 1234, 5, 9
+    out, kb = P.drop_mask(_dev(idx, torch.int32), rate, seed, sid, cid, LV)
+    torch.cuda.synchronize()
+    dropped = ops.drop_mask(N, Tq, Hq, Wq, rate, seed, sid, cid)
+    np.testing.assert_array_equal(out.cpu().numpy(), ops.apply_drop(idx, dropped, LV))
+    np.testing.assert_array_equal(kb.cpu().numpy().view(np.uint32), ops.keep_bits_from_mask(dropped))
+
+
+def test_packets_bit_exact(P):
+    N, Tq, Hq, Wq = 1, 2, 60, 107
+    rng = np.random.default_rng(4)
+    idx = rng.integers(0, 64000, size=(N, Tq, Hq, Wq)).astype(np.int32)
+    out, kb = P.drop_mask(_dev(idx, torch.int32), 0.25, 99, 1, 2, LV)
+    payload, offs = P.pack_rows(out, kb)
+    torch.cuda.synchronize()
+    dropped = ops.drop_mask(N, Tq, Hq, Wq, 0.25, 99, 1, 2)
+    kb_ref = ops.keep_bits_from_mask(dropped)
+    pay_ref, offs_ref = ops.pack_rows(idx, kb_ref, Wq)
+    np.testing.assert_array_equal(offs.cpu().numpy(), offs_ref)
+    np.testing.assert_array_equal(payload.cpu().numpy()[:len(pay_ref)], pay_ref)
+    rows = N * Tq * Hq
+    recv = np.ones(rows, np.uint8)
+    recv[[0, 17, rows - 1]] = 0
+    got = P.unpack_rows(payload, offs, kb, _dev(recv, torch.uint8), (N, Tq, Hq, Wq), LV)
+    torch.cuda.synchronize()
+    ref = ops.unpack_rows(pay_ref, offs_ref, kb_ref, recv.astype(bool), Wq, 32036).reshape(N, Tq, Hq, Wq)
+    np.testing.assert_array_equal(got.cpu().numpy(), ref)
+
+
+def test_bounded_wait_times_out_and_context_survives(P):
+    from paper_2602_03529_b300 import _lib as L
+    tk = P.Tokenizer("bf16", kind="stage", ch=(64, 128))
+    assert tk.status() == L.TOK_OK
+    L.tok_selftest_timeout(tk.ctx, 20_000_000, torch.cuda.current_stream().cuda_stream)
+    assert tk.status() == L.TOK_ETIMEOUT
+    assert tk.status() == L.TOK_OK          # cleared once read
+    x = torch.ones(4, device="cuda")        # the CUDA context is still usable
+    assert float(x.sum()) == 4.0
+    tk.close()

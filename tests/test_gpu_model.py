@@ -1,0 +1,110 @@
+"""End-to-end parity of the tokenizer (encode -> FSQ indices, decode) against
+the FP64 oracle, through the C-ABI, on both precision paths.
+
+Index parity (per the target: bit-exact away from rounding ties): for every
+token the margin m = min_i |frac(b_i) - 0.5| of the oracle's bounded latent b
+to the nearest rounding boundary is computed; the band eps is twice the
+largest |b_gpu - b_oracle| seen; tokens with m > eps must match exactly,
+mismatches inside the band are counted and reported.
+
+Latent / reconstruction error bounds (max-abs, on [-1,1]-scale outputs):
+  FP32 path  z: 1e-3, x_hat: 1e-3       (FP32 accumulation through ~30 convs)
+  BF16 path  z: 0.15, x_hat: 0.10       (bf16 activations between layers)
+The decoder is compared on identical indices (the oracle's).
+"""
+import numpy as np
+import pytest
+import torch
+
+import synthetic as S
+from oracle import Arch, Oracle, ops, param_spec
+
+pytestmark = pytest.mark.gpu
+LV = (8, 8, 8, 5, 5, 5)
+TOL = {"fp32": {"z": 1e-3, "x": 1e-3}, "bf16": {"z": 0.15, "x": 0.10}}
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_2602_03529_b300 as P
+    P._lib.load()
+    return P
+
+
+def index_parity(idx_gpu, z_gpu, b_ref, idx_ref, levels=LV):
+    b_gpu = ops.fsq_bound(z_gpu.astype(np.float64), levels)
+    eps = 2.0 * float(np.abs(b_gpu - b_ref).max())
+    frac = b_ref - np.floor(b_ref)
+    margin = np.abs(frac - 0.5).min(axis=-1)
+    mism = idx_gpu != idx_ref
+    out_band = mism & (margin > eps)
+    return dict(eps=eps, mismatches=int(mism.sum()), out_of_band=int(out_band.sum()),
+                in_band_tokens=int((margin <= eps).sum()), tokens=int(mism.size))
+
+
+def run_case(P, prec, arch_kw, oarch, N, T, H, W, seed=0, decode=True):
+    tk = P.Tokenizer(prec, **arch_kw)
+    spec = tk.param_spec()
+    assert [(n, tuple(s)) for n, s, _ in spec] == [(n, tuple(s)) for n, s, _ in param_spec(oarch)]
+    params = S.weights_for(spec, seed=seed)
+    tk.set_params(params)
+    x = S.blurred_noise_clip(seed, N, T, H, W)
+    if prec == "bf16":
+        x = S.to_bf16_f32(x)
+        p_or = {k: S.to_bf16_f32(v) for k, v in params.items()}
+    else:
+        p_or = params
+    orc = Oracle(oarch, p_or)
+    idx_ref, z_ref, b_ref = orc.encode(x)
+    tk.reserve(N, T, H, W)
+    dt = torch.bfloat16 if prec == "bf16" else torch.float32
+    z, idx = tk.encode(torch.from_numpy(x).to("cuda", dt))
+    torch.cuda.synchronize()
+    assert tk.status() == 0
+    z = z.cpu().numpy()
+    idx = idx.cpu().numpy()
+    rep = index_parity(idx, z, b_ref, idx_ref)
+    rep["z_err"] = float(np.abs(z - z_ref).max())
+    if decode:
+        xh_ref = orc.decode(idx_ref, H, W)
+        xh = tk.decode(torch.from_numpy(idx_ref.astype(np.int32)).cuda(), H, W)
+        torch.cuda.synchronize()
+        rep["x_err"] = float(np.abs(xh.cpu().numpy() - xh_ref).max())
+        rep["x_shape_ok"] = xh.shape == xh_ref.shape
+    tk.close()
+    return rep
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_stage_cfg0(P, prec):
+    """Single encoder stage + FSQ, 1x3x9x64x64 (the plain-FP32 stage config)."""
+    rep = run_case(P, prec, dict(kind="stage", ch=(64, 128)), Arch(kind="stage", ch=(64, 128)),
+                   1, 9, 64, 64, seed=0, decode=False)
+    print(prec, rep)
+    assert rep["out_of_band"] == 0
+    assert rep["z_err"] <= TOL[prec]["z"]
+    if prec == "fp32":
+        assert rep["mismatches"] <= 1e-4 * rep["tokens"]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("shape", [(1, 9, 32, 48), (2, 5, 24, 40), (1, 5, 20, 30)])
+def test_small_tokenizer(P, prec, shape):
+    """Full architecture with narrow channels; ragged H/W (edge pad + crop)."""
+    kw = dict(ch=(64, 128, 256), blocks=1)
+    rep = run_case(P, prec, kw, Arch(ch=(64, 128, 256), blocks=1), *shape, seed=1)
+    print(prec, shape, rep)
+    assert rep["x_shape_ok"]
+    assert rep["out_of_band"] == 0
+    assert rep["z_err"] <= TOL[prec]["z"]
+    assert rep["x_err"] <= TOL[prec]["x"]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_default_tokenizer_64px(P, prec):
+    """The 128/256/512, 2-blocks-per-level tokenizer on a 1x3x9x64x64 clip."""
+    rep = run_case(P, prec, {}, Arch(), 1, 9, 64, 64, seed=2)
+    print(prec, rep)
+    assert rep["out_of_band"] == 0
+    assert rep["z_err"] <= TOL[prec]["z"]
+    assert rep["x_err"] <= TOL[prec]["x"]
