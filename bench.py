@@ -1,0 +1,318 @@
+#!/usr/bin/env python
+"""Benchmark of the tokenizer hot path on B300: encode + FSQ + drop mask + decode.
+
+One step = one pass of the whole hot path over one synthetic 720p clip
+(1 x 3 x 17 x 720 x 1280, default tokenizer: channels 128/256/512, 2 residual
+blocks per level, 4x temporal / 8x8 spatial, FSQ [8,8,8,5,5,5]):
+  tok_encode (tcgen05 convs, GroupNorm+SiLU, FSQ fused in the last conv)
+  -> tok_drop_mask (Philox Bernoulli drop, zero fill, packet row masks)
+  -> tok_decode (tcgen05 convs, depth-to-space fused in the up convs).
+Prints one JSON line (rank 0). `--impl reference` times the FP64 CPU oracle on
+a bounded sample of the same workload instead.
+
+Multi-GPU: replicas (each rank its own clip, no data-path collective); value
+is the clips of all ranks / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("tokenizer encode+decode frames/s at 720p (BF16 vs plain FP32), fwd+bwd step ms, "
+          "p99 chunk ms")
+WORKLOAD = ("tokenizer encode + FSQ + token drop (15%) + decode of a 1x3x17x720x1280 clip; channels "
+            "128/256/512, 2 causal res-blocks per level, 4x8x8 compression, FSQ [8,8,8,5,5,5], BF16 "
+            "tcgen05 convs with FP32 accumulation")
+LEVELS = (8, 8, 8, 5, 5, 5)
+FALLBACK_PEAKS = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return FALLBACK_PEAKS, "fallback"
+
+
+# ----------------------------------------------------------------- clocks
+
+CLOCK_FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    """nvidia-smi sampling every 200 ms while the timed region runs."""
+
+    def __init__(self, gpu_id: str | None):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        cmd = ["nvidia-smi", f"--query-gpu={CLOCK_FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if gpu_id:
+            cmd += ["-i", gpu_id]
+        try:
+            self.p = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [q.strip() for q in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------- our arm
+
+def gpu_arm(args):
+    import torch
+
+    import paper_2602_03529_b300 as P
+    from paper_2602_03529_b300 import replicas as R
+    import synthetic as S
+
+    R.init()
+    rank, local, world = R.world()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    N, T, H, W = 1, args.T, args.H, args.W
+    tk = P.Tokenizer("bf16")
+    params = S.weights_for(tk.param_spec(), seed=0)
+    tk.set_params(params)
+    tk.reserve(N, T, H, W)
+    Tq, Hq, Wq = tk.latent_shape(T, H, W)
+    x_host = S.to_bf16_f32(S.blurred_noise_clip(1000 + rank, N, T, H, W))
+    x = torch.from_numpy(x_host).to(dev, torch.bfloat16)
+    z = torch.empty((N, Tq, Hq, Wq, len(LEVELS)), device=dev)
+    idx = torch.empty((N, Tq, Hq, Wq), device=dev, dtype=torch.int32)
+    idx_d = torch.empty_like(idx)
+    kb = torch.empty((N, Tq, Hq, (Wq + 31) // 32), device=dev, dtype=torch.int32)
+    xh = torch.empty((N, T, H, W, 3), device=dev)
+    flush = torch.empty(256 << 20, device=dev, dtype=torch.uint8)  # > L2 (126 MB)
+    rate = 0.15
+
+    def step(i, xin=None):
+        tk.encode(x if xin is None else xin, z, idx)
+        P.drop_mask(idx, rate, seed=12345, stream_id=rank, chunk_id=i, levels=LEVELS, out=idx_d, keep_bits=kb)
+        tk.decode(idx_d, H, W, out=xh)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    assert tk.status() == 0, "device-side error during warm-up"
+
+    # ---------------- timed region: device-resident inputs, L2 flushed per step
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(local).uuid)
+    except Exception:
+        pass
+    R.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(uuid) if rank == 0 else None
+    tk.profile(True)
+    tk.profile_read()
+    l0 = tk.launch_count()
+    evs = []
+    for i in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step(args.warmup + i)
+        e1.record()
+        evs.append((e0, e1))
+    torch.cuda.synchronize()
+    R.barrier()
+    clocks = sampler.stop() if sampler else None
+    launches = tk.launch_count() - l0 + args.steps  # + one drop-mask kernel per step
+    prof = tk.profile_read()
+    tk.profile(False)
+    assert tk.status() == 0, "device-side error in the timed region"
+    total_ms = sum(a.elapsed_time(b) for a, b in evs)
+    total_ms = R.max_over_ranks(total_ms)
+    frames = world * N * T * args.steps
+    value = frames / (total_ms / 1e3)
+
+    # ---------------- end to end: pinned host clip in, decoded frames out
+    xpin = torch.from_numpy(x_host).to(torch.bfloat16).pin_memory()
+    xhpin = torch.empty((N, T, H, W, 3), dtype=torch.float32).pin_memory()
+    xdev = torch.empty_like(x)
+    e2e_steps = max(1, min(args.steps, 5))
+    R.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(e2e_steps):
+        xdev.copy_(xpin, non_blocking=True)
+        step(10_000 + i, xin=xdev)
+        xhpin.copy_(xh, non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = R.max_over_ranks(time.perf_counter() - t0)
+    e2e = {"value": world * N * T * e2e_steps / e2e_s, "unit": "frames/s",
+           "h2d_bytes_per_step": xpin.numel() * 2, "d2h_bytes_per_step": xhpin.numel() * 4}
+
+    # ---------------- the plain FP32 CUDA-core path (denominator of the 5x target)
+    fp32 = None
+    if not args.no_fp32:
+        tf = P.Tokenizer("fp32")
+        tf.set_params(params)
+        tf.reserve(N, T, H, W)
+        xf = torch.from_numpy(x_host).to(dev)
+        zf = torch.empty_like(z)
+
+        def fstep(i):
+            tf.encode(xf, zf, idx)
+            P.drop_mask(idx, rate, seed=12345, stream_id=rank, chunk_id=i, levels=LEVELS, out=idx_d,
+                        keep_bits=kb)
+            tf.decode(idx_d, H, W, out=xh)
+
+        fstep(0)
+        torch.cuda.synchronize()
+        ks = max(1, min(2, args.steps))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for i in range(ks):
+            fstep(1 + i)
+        e1.record()
+        torch.cuda.synchronize()
+        fms = R.max_over_ranks(e0.elapsed_time(e1))
+        fp32 = {"value": world * N * T * ks / (fms / 1e3), "unit": "frames/s", "ms_per_step": fms / ks}
+        assert tf.status() == 0
+        tf.close()
+
+    peaks, peak_src = load_peaks()
+    conv_tflops = prof["conv_flop"] / (prof["conv_ms"] / 1e3) / 1e12 if prof["conv_ms"] > 0 else 0.0
+    peak = float(peaks["bf16_tflops_sustained"])
+    roofline = {
+        "kernel": "conv_tc_kernel (tcgen05 implicit-GEMM causal conv, all launches)",
+        "bound": "tensor", "achieved": conv_tflops, "peak": peak, "unit": "TFLOP/s",
+        "frac": conv_tflops / peak,
+        "peak_source": f"{peak_src} bf16_tflops_sustained (kernel inside a long step)",
+        "frac_of_burst_peak": conv_tflops / float(peaks["bf16_tflops"]),
+        "traffic": None,
+        "flop_per_step": prof["conv_flop"] / args.steps, "launches_per_step": prof["conv_launches"] / args.steps,
+        "conv_ms_per_step": prof["conv_ms"] / args.steps,
+        "conv_share_of_step": prof["conv_ms"] / max(total_ms, 1e-9),
+        "groupnorm": {"ms_per_step": prof["gn_ms"] / args.steps,
+                      "achieved_gbs": prof["gn_bytes"] / (prof["gn_ms"] / 1e3) / 1e9 if prof["gn_ms"] else 0.0,
+                      "peak_gbs": float(peaks["hbm_gbs"])},
+        "other_ms_per_step": prof["other_ms"] / args.steps,
+    }
+    out = {
+        "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N, "T": T, "H": H, "W": W, "latent": [Tq, Hq, Wq],
+                   "parallelism": f"replicas x{world}", "drop_rate": rate,
+                   "l2": "256 MB buffer written before every timed step (L2 is 126 MB); activations are ~1 GB each"},
+        "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+        "fp32_path": fp32, "speedup_vs_fp32": (value / fp32["value"]) if fp32 else None,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args)
+    tk.close()
+    R.barrier()
+    R.finalize()
+    return out if rank == 0 else None
+
+
+# -------------------------------------------------------- the oracle (CPU)
+
+def oracle_sample(T, H, W, seed=0):
+    """Encode + drop + decode of one T x H x W clip by the FP64 oracle; returns seconds."""
+    import synthetic as S
+    from oracle import Arch, Oracle, ops, param_spec
+    a = Arch()
+    p = {k: S.to_bf16_f32(v) for k, v in S.weights_for(param_spec(a), seed=0).items()}
+    x = S.to_bf16_f32(S.blurred_noise_clip(seed, 1, T, H, W))
+    o = Oracle(a, p)
+    t0 = time.perf_counter()
+    idx, _, _ = o.encode(x)
+    dropped = ops.drop_mask(*idx.shape, 0.15, 12345, 0, seed)
+    o.decode(ops.apply_drop(idx, dropped, a.levels), H, W)
+    return time.perf_counter() - t0
+
+
+def cpu_baseline(args, T=5, H=128, W=192):
+    from oracle import ops
+    s = oracle_sample(T, H, W)
+    eq = T * H * W / (args.H * args.W)  # 720p-frame equivalents (work scales with pixels)
+    return {"value": eq / s, "unit": "frames/s (720p-equivalent)", "cores": ops.num_threads(), "kind": "oracle",
+            "sample": f"FP64 oracle encode+drop+decode of a 1x3x{T}x{H}x{W} crop of the same workload "
+                      f"({s:.1f} s); work scales with pixel count, so frames/s = {eq:.4f} 720p frames / time"}
+
+
+def reference_arm(args):
+    from paper_2602_03529_b300 import replicas as R
+    rank, _, world = R.world()
+    if rank != 0:
+        return None
+    from oracle import ops
+    T, H, W = 5, 64, 96
+    for i in range(args.warmup):
+        oracle_sample(T, H, W, seed=i)
+    secs = [oracle_sample(T, H, W, seed=100 + i) for i in range(args.steps)]
+    total = sum(secs)
+    eq = T * H * W / (args.H * args.W) * args.steps
+    value = eq / total
+    sample = (f"FP64 oracle encode+drop+decode of a 1x3x{T}x{H}x{W} crop per step "
+              "(720p-frame equivalents by pixel count)")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": 1, "T": args.T, "H": args.H, "W": args.W, "sample": [T, H, W]},
+            "cpu_baseline": {"value": value, "unit": "frames/s", "kind": "oracle", "cores": ops.num_threads(),
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--T", type=int, default=17)
+    ap.add_argument("--H", type=int, default=720)
+    ap.add_argument("--W", type=int, default=1280)
+    ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    out = reference_arm(args) if args.impl == "reference" else gpu_arm(args)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

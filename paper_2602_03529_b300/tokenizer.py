@@ -173,9 +173,12 @@ def drop_mask(idx: torch.Tensor, rate: float, seed: int, stream_id: int = 0, chu
     N, Tq, Hq, Wq = idx.shape
     if out is None:
         out = torch.empty_like(idx)
-    kb = None
-    if keep_bits:
+    if isinstance(keep_bits, torch.Tensor):
+        kb = keep_bits
+    elif keep_bits:
         kb = torch.empty((N, Tq, Hq, (Wq + 31) // 32), device=idx.device, dtype=torch.int32)
+    else:
+        kb = None
     L.tok_drop_mask(_ptr(idx), N, Tq, Hq, Wq, float(rate), int(seed), int(stream_id), int(chunk_id),
                     zero_index(levels), _ptr(out), _ptr(kb), _stream_ptr(stream))
     return out, kb
