@@ -219,6 +219,24 @@ int tok_groupnorm_silu(int precision, const void* d_x, int64_t frames, int64_t H
                        const float* d_gamma, const float* d_beta, float eps, void* d_y,
                        void* d_workspace, size_t workspace_bytes, void* stream);
 
+/* GroupNorm+SiLU without a workspace argument, for callers that cannot
+ * allocate device memory (a host callback or real-time thread that may not
+ * call cudaMalloc or take the allocator's locks, or an embedding with a fixed
+ * memory budget). The paper has no counterpart; this is a library
+ * convenience. Same computation and arguments as tok_groupnorm_silu, minus
+ * the workspace: the scratch lives in one fixed array of
+ * TOK_GN_NOALLOC_MAX_SCRATCH_BYTES in device global memory, held by every GPU
+ * that loads the library until the process exits. Returns TOK_ENOMEM when
+ * the problem needs more scratch than that (tok_groupnorm_workspace_bytes
+ * tells how much it needs). Allocates nothing. The first call on a device
+ * looks up the array's device address, so make that first call before any
+ * stream capture. All calls share the array: calls whose kernels overlap on
+ * the GPU (other streams, other threads) race on it; serialise them. */
+#define TOK_GN_NOALLOC_MAX_SCRATCH_BYTES (4u << 20)
+int tok_groupnorm_silu_noalloc(int precision, const void* d_x, int64_t frames, int64_t HW, int C, int G,
+                               const float* d_gamma, const float* d_beta, float eps, void* d_y,
+                               void* stream);
+
 /* Device status: synchronises the context's work, returns and clears the
  * first device-side error recorded since the last call. */
 int tok_status(tok_ctx* ctx);

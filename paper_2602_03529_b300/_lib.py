@@ -78,6 +78,7 @@ _SIGS = {
                          vp]),
     "tok_groupnorm_workspace_bytes": (sz, [i32, i64, i64, i32, i32]),
     "tok_groupnorm_silu": (i32, [i32, vp, i64, i64, i32, i32, vp, vp, f32, vp, vp, sz, vp]),
+    "tok_groupnorm_silu_noalloc": (i32, [i32, vp, i64, i64, i32, i32, vp, vp, f32, vp, vp]),
     "tok_status": (i32, [vp]),
     "tok_strerror": (C.c_char_p, [i32]),
     "tok_selftest_timeout": (i32, [vp, i64, vp]),
@@ -247,6 +248,12 @@ def tok_groupnorm_silu(precision, x_ptr, frames, HW, C, G, g_ptr, b_ptr, eps, y_
                        cuda_stream) -> None:
     _ck(_call("tok_groupnorm_silu", precision, x_ptr, frames, HW, C, G, g_ptr, b_ptr, eps, y_ptr, ws_ptr,
               ws_bytes, cuda_stream), "tok_groupnorm_silu")
+
+
+def tok_groupnorm_silu_noalloc(precision, x_ptr, frames, HW, C, G, g_ptr, b_ptr, eps, y_ptr, cuda_stream) -> None:
+    """GroupNorm+SiLU with library-owned fixed scratch (no workspace, no allocation)."""
+    _ck(_call("tok_groupnorm_silu_noalloc", precision, x_ptr, frames, HW, C, G, g_ptr, b_ptr, eps, y_ptr,
+              cuda_stream), "tok_groupnorm_silu_noalloc")
 
 
 def tok_status(ctx) -> int:
