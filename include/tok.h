@@ -180,7 +180,13 @@ int tok_unpack_rows(const int32_t* d_payload, const int64_t* d_row_offsets,
  * latent k). Each causal conv keeps the last two input frames of the chunk
  * it saw, so a stream's chunks give exactly the whole-clip result.
  * tok_stream_bytes: device bytes one stream of H x W needs (for admission).
- * tok_stream_open allocates them (TOK_ENOMEM when they do not fit). */
+ * tok_stream_open allocates them (TOK_ENOMEM when they do not fit) and
+ * tok_stream_reset starts a new video in them (chunk 0 again). A stream's
+ * chunks must be encoded (decoded) in order, one at a time, but may be run
+ * by any context with the same architecture and precision (serving lanes).
+ * Streaming chunks have N = 1; encode takes 1 frame first, then s_T frames,
+ * and returns one latent frame; decode takes one latent frame. The
+ * concatenated outputs equal the whole-clip outputs bitwise. */
 size_t tok_stream_bytes(const tok_ctx* ctx, int H, int W);
 int tok_stream_open(tok_ctx* ctx, int H, int W, tok_stream** out);
 void tok_stream_close(tok_stream* s);

@@ -43,18 +43,29 @@ struct TcGeo {
 
 namespace {
 
-constexpr int BM = 128;
-constexpr int A_BYTES = BM * 128;
-
-template <int BN>
+// Two operand arrangements of the same implicit GEMM:
+//  SWAP = false: MMA M = 128 voxels, N = BN output channels (A = activations).
+//  SWAP = true : MMA M = 128 output channels, N = 256 voxels (A = weights), for
+//                layers with exactly 128 output channels: an M128 x N256 MMA
+//                reads 12 KB of operands from shared memory per 128 tensor
+//                cycles where M128 x N128 reads 8 KB per 64, so the wide form
+//                keeps the tensor pipe fed. TMEM then holds D^T (lanes =
+//                channels, columns = voxels) and the epilogue transposes
+//                through a small per-warp staging buffer.
+template <int BN, bool SWAP>
 struct Cfg {
-    static constexpr int B_BYTES = BN * 128;
-    static constexpr int STAGE = A_BYTES + B_BYTES;
+    static constexpr int ROWS = SWAP ? 256 : 128;  // voxels per tile
+    static constexpr int ACT_BYTES = ROWS * 128;   // 64 bf16 channels per voxel row
+    static constexpr int W_BYTES = BN * 128;
+    static constexpr int STAGE = ACT_BYTES + W_BYTES;
     static constexpr int STAGES = (200 * 1024 / STAGE) > 8 ? 8 : (200 * 1024 / STAGE);
-    static constexpr int TMEM_COLS = (2 * BN <= 32) ? 32 : (2 * BN <= 64) ? 64 : (2 * BN <= 128) ? 128 : (2 * BN <= 256) ? 256 : 512;
+    static constexpr int ACC_COLS = SWAP ? ROWS : BN;  // TMEM columns per accumulator
+    static constexpr int TMEM_COLS = (2 * ACC_COLS <= 32) ? 32 : (2 * ACC_COLS <= 64) ? 64 : (2 * ACC_COLS <= 128) ? 128 : (2 * ACC_COLS <= 256) ? 256 : 512;
     static constexpr int BAR_BYTES = 256;
-    static constexpr int SMEM = STAGES * STAGE + 1024 + BAR_BYTES;
-    static constexpr uint32_t IDESC = idesc_bf16_f32(BM, BN);
+    static constexpr int EPI_STRIDE = 36;  // floats per staged voxel row (16B-aligned, bank-spread)
+    static constexpr int EPI_BYTES = SWAP ? 4 * 16 * EPI_STRIDE * 4 : 0;
+    static constexpr int SMEM = STAGES * STAGE + 1024 + BAR_BYTES + EPI_BYTES;
+    static constexpr uint32_t IDESC = SWAP ? idesc_bf16_f32(BN, ROWS) : idesc_bf16_f32(128, BN);
 };
 
 struct TileCoord {
@@ -100,11 +111,11 @@ __device__ __forceinline__ void add_bf16x16(const __nv_bfloat16* src, float (&v)
     }
 }
 
-template <int BN>
+template <int BN, bool SWAP>
 __global__ void __launch_bounds__(192, 1)
     conv_tc_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_h,
                    const __grid_constant__ CUtensorMap tm_w, const ConvArgs a, const TcGeo g) {
-    using C = Cfg<BN>;
+    using C = Cfg<BN, SWAP>;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_addr = smem_u32(smem_raw);
     uint8_t* smem = smem_raw + (((raw_addr + 1023u) & ~1023u) - raw_addr);
@@ -113,6 +124,7 @@ __global__ void __launch_bounds__(192, 1)
     uint64_t* tfull = empty + C::STAGES;
     uint64_t* tempty = tfull + 2;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+    float* epi = reinterpret_cast<float*>(smem + C::STAGES * C::STAGE + C::BAR_BYTES);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     // A context already in error skips the launch (decided once per CTA).
@@ -179,7 +191,7 @@ __global__ void __launch_bounds__(192, 1)
                         tcoord = -1;  // whole box out of range -> zeros
                     }
                     uint8_t* sa = smem + s * C::STAGE;
-                    uint8_t* sb = sa + A_BYTES;
+                    uint8_t* sb = sa + C::ACT_BYTES;
                     mbar_arrive_expect_tx(&full[s], C::STAGE);
                     if (!g.strided) {
                         tma_load_4d(sa, src, &full[s], cb * 64, tc.tw * g.BW + dw - pw_, tc.th * g.BH + dh - ph_,
@@ -214,18 +226,19 @@ __global__ void __launch_bounds__(192, 1)
                 const uint32_t aph = (uint32_t)((it >> 1) & 1);
                 if (!mbar_wait(&tempty[acc], aph ^ 1, a.status, a.wait_ns)) break;
                 tc_fence_after();
-                const uint32_t d = tmem_base + (uint32_t)(acc * BN);
+                const uint32_t d = tmem_base + (uint32_t)(acc * C::ACC_COLS);
                 for (int kb = 0; kb < g.nkb; ++kb) {
                     if (!mbar_wait(&full[s], ph, a.status, a.wait_ns)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t sa = smem_u32(smem + s * C::STAGE);
-                    const uint32_t sb = sa + A_BYTES;
+                    const uint32_t s_act = smem_u32(smem + s * C::STAGE);
+                    const uint32_t s_w = s_act + C::ACT_BYTES;
+                    const uint32_t op_a = SWAP ? s_w : s_act, op_b = SWAP ? s_act : s_w;
 #pragma unroll
                     for (int k = 0; k < 4; ++k)
-                        tc_mma_bf16(d, sw128_desc(sa + k * 32), sw128_desc(sb + k * 32), C::IDESC,
+                        tc_mma_bf16(d, sw128_desc(op_a + k * 32), sw128_desc(op_b + k * 32), C::IDESC,
                                     (kb | k) != 0 ? 1u : 0u);
                     tc_commit(&empty[s]);
                     if (++s == C::STAGES) {
@@ -254,10 +267,50 @@ __global__ void __launch_bounds__(192, 1)
             if (!okw) break;
             tc_fence_after();
             const TileCoord tc = decode_tile(a, g, tile);
+            if constexpr (SWAP) {
+                // lane = output channel co, TMEM column = voxel of the 256-voxel tile
+                const int co = tc.nt * BN + r;
+                const float bias = (a.bias && co < a.Cout) ? a.bias[co] : 0.f;
+                float* stg = epi + q * 16 * C::EPI_STRIDE;
+                const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * C::ACC_COLS);
+                const int j = lane >> 1, half = lane & 1;  // read-back role: voxel j, 16 channels
+#pragma unroll 1
+                for (int c16 = 0; c16 < C::ROWS / 16; ++c16) {
+                    float v[16];
+                    tmem_ld16(tbase + (uint32_t)(c16 * 16), v);
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) stg[i * C::EPI_STRIDE + lane] = v[i] + bias;
+                    __syncwarp();
+                    const int vv = c16 * 16 + j;
+                    const int ho = tc.th * g.BH + vv / g.BW, wo = tc.tw * g.BW + vv % g.BW;
+                    const int c0 = tc.nt * BN + q * 32 + half * 16;
+                    if (ho < a.Hout && wo < a.Wout && c0 < a.Cout) {
+                        float o[16];
+                        const float4* src = reinterpret_cast<const float4*>(stg + j * C::EPI_STRIDE + half * 16);
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const float4 f = src[i];
+                            o[4 * i] = f.x;
+                            o[4 * i + 1] = f.y;
+                            o[4 * i + 2] = f.z;
+                            o[4 * i + 3] = f.w;
+                        }
+                        const long long off =
+                            ((((long long)tc.n * a.oT + tc.to) * a.oH + ho) * a.oW + wo) * a.oC + c0;
+                        if (a.residual) add_bf16x16(static_cast<const __nv_bfloat16*>(a.residual) + off, o);
+                        store_bf16x16(static_cast<__nv_bfloat16*>(a.out) + off, o);
+                    }
+                    __syncwarp();
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[acc]);
+                continue;
+            }
             const int ho = tc.th * g.BH + r / g.BW;
             const int wo = tc.tw * g.BW + r % g.BW;
             const bool valid = ho < a.Hout && wo < a.Wout;
-            const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * BN);
+            const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * C::ACC_COLS);
             const long long vox = (((long long)tc.n * a.Tout + tc.to) * a.Hout + ho) * a.Wout + wo;
 #pragma unroll 1
             for (int c16 = 0; c16 < BN / 16; ++c16) {
@@ -387,9 +440,9 @@ bool encode_w_map(CUtensorMap* m, const void* base, int rows, int Kpad, int BN) 
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BN>
+template <int BN, bool SWAP>
 int launch_bn(const ConvArgs& a, TcGeo g, int num_sms, cudaStream_t stream) {
-    using C = Cfg<BN>;
+    using C = Cfg<BN, SWAP>;
     CUtensorMap mx, mh, mw;
     const bool strided = g.strided != 0;
     if (!encode_act_map(&mx, a.x, a.N * a.Tin, a.Hin, a.Win, a.Cin, g.BH, g.BW, strided)) return -1;
@@ -405,11 +458,11 @@ int launch_bn(const ConvArgs& a, TcGeo g, int num_sms, cudaStream_t stream) {
     if (g.num_tiles == 0) return 0;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(conv_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+        cudaFuncSetAttribute(conv_tc_kernel<BN, SWAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
         attr_set = true;
     }
     const int grid = (int)std::min<long long>(g.num_tiles, num_sms);
-    conv_tc_kernel<BN><<<grid, 192, C::SMEM, stream>>>(mx, mh, mw, a, g);
+    conv_tc_kernel<BN, SWAP><<<grid, 192, C::SMEM, stream>>>(mx, mh, mw, a, g);
     return (int)cudaGetLastError();
 }
 
@@ -417,10 +470,11 @@ int launch_bn(const ConvArgs& a, TcGeo g, int num_sms, cudaStream_t stream) {
 
 // Choose the output tile shape (BH x BW = 128) that covers Hout x Wout with
 // the fewest tiles; ties go to the wider tile (longer contiguous rows).
-void choose_tile(int Hout, int Wout, int* BH, int* BW) {
+void choose_tile(int Hout, int Wout, int rows, int* BH, int* BW) {
     long long best = -1;
-    for (int bw : {128, 64, 32, 16, 8}) {
-        int bh = 128 / bw;
+    for (int bw : {256, 128, 64, 32, 16, 8}) {
+        if (bw > rows || rows / bw > 256) continue;
+        int bh = rows / bw;
         long long t = (long long)((Wout + bw - 1) / bw) * ((Hout + bh - 1) / bh);
         if (best < 0 || t < best) {
             best = t;
@@ -443,7 +497,9 @@ int conv_tc_bn(int Cout_pad) {
 // sh == sw == 2 with even Hin and Win, bf16 tensors 16-byte aligned.
 int launch_conv_tc(const ConvArgs& a, int num_sms, cudaStream_t stream) {
     TcGeo g;
-    choose_tile(a.Hout, a.Wout, &g.BH, &g.BW);
+    // exactly 128 output channels, plain bf16 output: the wide (swapped) form
+    const bool swap = a.mode == OUT_PLAIN && !a.out_fp32 && a.Cout == 128 && a.Cout_pad == 128;
+    choose_tile(a.Hout, a.Wout, swap ? 256 : 128, &g.BH, &g.BW);
     g.tiles_w = (a.Wout + g.BW - 1) / g.BW;
     g.tiles_h = (a.Hout + g.BH - 1) / g.BH;
     g.cpt = a.Cin / 64;
@@ -451,12 +507,13 @@ int launch_conv_tc(const ConvArgs& a, int num_sms, cudaStream_t stream) {
     g.strided = (a.sh == 2) ? 1 : 0;
     g.n_tiles = 0;
     g.num_tiles = 0;
+    if (swap) return launch_bn<128, true>(a, g, num_sms, stream);
     switch (conv_tc_bn(a.Cout_pad)) {
-        case 256: return launch_bn<256>(a, g, num_sms, stream);
-        case 128: return launch_bn<128>(a, g, num_sms, stream);
-        case 64: return launch_bn<64>(a, g, num_sms, stream);
-        case 32: return launch_bn<32>(a, g, num_sms, stream);
-        default: return launch_bn<16>(a, g, num_sms, stream);
+        case 256: return launch_bn<256, false>(a, g, num_sms, stream);
+        case 128: return launch_bn<128, false>(a, g, num_sms, stream);
+        case 64: return launch_bn<64, false>(a, g, num_sms, stream);
+        case 32: return launch_bn<32, false>(a, g, num_sms, stream);
+        default: return launch_bn<16, false>(a, g, num_sms, stream);
     }
 }
 

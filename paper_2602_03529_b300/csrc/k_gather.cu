@@ -175,6 +175,19 @@ int launch_edge_pad(const T* x, long long frames, int H, int W, int Hp, int Wp, 
 template int launch_edge_pad<float>(const float*, long long, int, int, int, int, int, float*, cudaStream_t);
 template int launch_edge_pad<int32_t>(const int32_t*, long long, int, int, int, int, int, int32_t*, cudaStream_t);
 
+namespace {
+__global__ void fill_i32_kernel(int32_t* p, long long n, int32_t v) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) p[t] = v;
+}
+}  // namespace
+
+int launch_fill_i32(int32_t* p, long long n, int32_t v, cudaStream_t s) {
+    if (n <= 0) return 0;
+    fill_i32_kernel<<<blocks_for(n, 256), 256, 0, s>>>(p, n, v);
+    return (int)cudaGetLastError();
+}
+
 template <typename T>
 int launch_pack_weights(const float* w, int Cout, int K, int Cout_pad, int Kpad, T* out, cudaStream_t s) {
     const long long n = (long long)Cout_pad * Kpad;

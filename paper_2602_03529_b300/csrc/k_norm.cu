@@ -181,10 +181,14 @@ __global__ void __launch_bounds__(NT) gn_apply_kernel(const T* __restrict__ x, T
     }
 }
 
+// The chunking of a frame depends on the frame's size only (about 64 chunks
+// per frame), never on how many frames the launch holds, so that a frame's
+// statistics are summed in the same order whether it is normalised as part of
+// a whole clip or of a streaming chunk.
 void gn_plan(long long frames, long long vec_per_frame, int num_sms, int* vpt, int* S) {
-    const long long total = frames * vec_per_frame;
-    const long long target_blocks = 4LL * num_sms;
-    long long v = (total + (long long)NT * target_blocks - 1) / ((long long)NT * target_blocks);
+    (void)frames;
+    (void)num_sms;
+    long long v = (vec_per_frame + (long long)NT * 64 - 1) / ((long long)NT * 64);
     if (v < 1) v = 1;
     if (v > 256) v = 256;
     *vpt = (int)v;

@@ -38,6 +38,8 @@ int launch_edge_pad(const T* x, long long frames, int H, int W, int Hp, int Wp, 
 template <typename T>
 int launch_pack_weights(const float* w, int Cout, int K, int Cout_pad, int Kpad, T* out, cudaStream_t s);
 
+int launch_fill_i32(int32_t* p, long long n, int32_t v, cudaStream_t s);
+
 int launch_timeout_selftest(int* status, unsigned long long limit_ns, cudaStream_t s);
 
 }  // namespace tok

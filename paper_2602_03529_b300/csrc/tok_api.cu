@@ -90,9 +90,17 @@ struct tok_ctx {
     size_t esize() const { return bf16() ? 2 : 4; }
 };
 
+// One video stream's causal state: for every conv with temporal taps, the
+// last two frames of its input (the left context of the next chunk), plus
+// chunk counters for the encoder and the decoder side.
 struct tok_stream {
-    tok_ctx* ctx;
-    int H, W;
+    tok_ctx* ctx = nullptr;
+    int H = 0, W = 0;
+    int enc_chunk = 0, dec_chunk = 0;
+    char* mem = nullptr;
+    size_t bytes = 0;
+    std::map<std::string, char*> hist;        // conv name -> 2 frames
+    std::map<std::string, size_t> frame_bytes; // conv name -> bytes of one frame
 };
 
 namespace {
@@ -336,6 +344,56 @@ Work carve(tok_ctx* c, const Layout& L) {
 
 // ------------------------------------------------------------ executor
 
+int32_t zero_index_of(const tok_ctx* c) {
+    int32_t z = 0, b = 1;
+    for (int i = 0; i < c->arch.nlev; ++i) {
+        z += (c->arch.levels[i] / 2) * b;
+        b *= c->arch.levels[i];
+    }
+    return z;
+}
+
+// Every conv with temporal taps and the bytes of one frame of its input, for
+// one stream of H x W pixels (N = 1). On the BF16 path the stem and the
+// decoder input keep the raw pixels / token indices their gathers read.
+std::vector<std::pair<std::string, size_t>> stream_frames(const tok_ctx* c, int H, int W) {
+    std::vector<std::pair<std::string, size_t>> v;
+    const tok_arch& a = c->arch;
+    const Dims d = clip_dims(c, 1, H, W);
+    const size_t es = c->esize();
+    const size_t pix = c->bf16() ? (size_t)H * W * a.in_ch * 2 : (size_t)d.Hp * d.Wp * a.in_ch * 4;
+    if (a.kind == TOK_ARCH_STAGE) {
+        v.push_back({"stage.c0", pix});
+        v.push_back({"stage.c1", (size_t)d.Hp * d.Wp * a.ch[0] * es});
+        return v;
+    }
+    v.push_back({"enc.stem", pix});
+    for (int l = 0; l < a.nlevels; ++l) {
+        const size_t hw = (size_t)(d.Hp >> (l + 1)) * (d.Wp >> (l + 1));
+        const int cin = l > 0 ? a.ch[l - 1] : a.ch[0];
+        for (int b = 0; b < a.blocks; ++b) {
+            const std::string n = "enc.l" + std::to_string(l) + ".b" + std::to_string(b);
+            v.push_back({n + ".c1", hw * (b == 0 ? cin : a.ch[l]) * es});
+            v.push_back({n + ".c2", hw * a.ch[l] * es});
+        }
+        if (l < a.nlevels - 1) v.push_back({"enc.down" + std::to_string(l), hw * a.ch[l] * es});
+    }
+    const size_t hwq = (size_t)d.Hq * d.Wq;
+    v.push_back({"enc.out", hwq * a.ch[a.nlevels - 1] * es});
+    v.push_back({"dec.in", c->bf16() ? hwq * 4 : hwq * a.nlev * 4});
+    for (int l = a.nlevels - 1; l >= 0; --l) {
+        const size_t hw = (size_t)(d.Hp >> (l + 1)) * (d.Wp >> (l + 1));
+        for (int b = 0; b < a.blocks; ++b) {
+            const std::string n = "dec.l" + std::to_string(l) + ".b" + std::to_string(b);
+            v.push_back({n + ".c1", hw * a.ch[l] * es});
+            v.push_back({n + ".c2", hw * a.ch[l] * es});
+        }
+        if (l > 0) v.push_back({"dec.up" + std::to_string(l - 1), hw * a.ch[l] * es});
+    }
+    v.push_back({"dec.out", (size_t)(d.Hp >> 1) * (d.Wp >> 1) * a.ch[0] * es});
+    return v;
+}
+
 struct Act {
     void* p;
     int N, T, H, W, C;
@@ -346,6 +404,47 @@ struct Exec {
     cudaStream_t s;
     Work w;
     int err = 0;
+    tok_stream* st = nullptr;  // chunked streaming (null: whole clip)
+    bool chunk0 = true;        // first chunk of a stream: clip-mode causal padding
+
+    // Streaming: a conv with temporal taps reads its left context from the
+    // stream's history; stride-2 convs see chunks that start one frame after
+    // an output frame, hence t_off -1 instead of -2.
+    void stream_args(ConvArgs& a, const std::string& name, int k, int st_t) {
+        if (!st || k != 3 || chunk0) return;
+        a.hist = st->hist[name];
+        a.hist_T = 2;
+        if (st_t == 2) a.t_off = -1;
+    }
+
+    // After a causal conv of a stream: history <- last two frames of [history | chunk].
+    void stream_update(const std::string& name, const void* chunk, int Tc, bool zero_index_fill = false) {
+        if (!st || err) return;
+        auto it = st->hist.find(name);
+        if (it == st->hist.end()) return;
+        char* h = it->second;
+        const size_t fb = st->frame_bytes[name];
+        const char* x = static_cast<const char*>(chunk);
+        auto cp = [&](void* d, const void* src, size_t n) {
+            if (cudaMemcpyAsync(d, src, n, cudaMemcpyDeviceToDevice, s) != cudaSuccess) ck(1);
+        };
+        if (chunk0) {
+            if (c->arch.time_pad == TOK_PAD_REPLICATE) {
+                cp(h, x, fb);
+            } else if (zero_index_fill) {
+                other([&] { return launch_fill_i32(reinterpret_cast<int32_t*>(h), (long long)(fb / 4),
+                                                   zero_index_of(c), s); }, (double)fb);
+            } else if (cudaMemsetAsync(h, 0, fb, s) != cudaSuccess) {
+                ck(1);
+            }
+            cp(h + fb, x + (size_t)(Tc - 1) * fb, fb);
+        } else if (Tc >= 2) {
+            cp(h, x + (size_t)(Tc - 2) * fb, 2 * fb);
+        } else {
+            cp(h, h + fb, fb);
+            cp(h + fb, x, fb);
+        }
+    }
 
     void ck(int e) {
         if (e && !err) err = TOK_ECUDA;
@@ -418,10 +517,11 @@ struct Exec {
     }
 
     // Plain conv (optional residual) into `out`.
-    Act conv(const std::string& name, const Act& in, void* out, const void* residual = nullptr, int st = 1,
+    Act conv(const std::string& name, const Act& in, void* out, const void* residual = nullptr, int tst = 1,
              int sh = 1, int sw = 1) {
         const ConvW& cw = c->convs[c->cindex[name]];
-        ConvArgs a = base_args(cw, in, st, sh, sw);
+        ConvArgs a = base_args(cw, in, tst, sh, sw);
+        stream_args(a, name, cw.k, tst);
         a.mode = OUT_PLAIN;
         a.out = out;
         a.residual = residual;
@@ -430,6 +530,7 @@ struct Exec {
         a.oW = a.Wout;
         a.oC = cw.Cout;
         launch(a, cw);
+        stream_update(name, in.p, in.T);
         return Act{out, in.N, a.Tout, a.Hout, a.Wout, cw.Cout};
     }
 
@@ -438,18 +539,21 @@ struct Exec {
                  bool out_fp32) {
         const ConvW& cw = c->convs[c->cindex[name]];
         ConvArgs a = base_args(cw, in, 1, 1, 1);
+        stream_args(a, name, cw.k, 1);
         a.mode = OUT_D2S;
         a.out = out;
         a.out_fp32 = out_fp32 ? 1 : 0;
         a.rt = rt;
         a.rh = rh;
         a.rw = rw;
-        a.drop_t = rt - 1;
-        a.oT = a.Tout * rt - (rt - 1);
+        // the causal trim of the first rt-1 frames belongs to the clip's start only
+        a.drop_t = (st && !chunk0) ? 0 : rt - 1;
+        a.oT = a.Tout * rt - a.drop_t;
         a.oH = oH;
         a.oW = oW;
         a.oC = cw.Cout / (rt * rh * rw);
         launch(a, cw);
+        stream_update(name, in.p, in.T);
         return Act{out, in.N, a.oT, oH, oW, a.oC};
     }
 
@@ -518,9 +622,11 @@ struct Exec {
         if (ar.kind == TOK_ARCH_STAGE) {
             if (c->bf16()) {
                 GatherGeo g = gather_pixels(N, T, H, W, d.Hp, d.Wp, 1);
-                other([&] { return launch_im2col_pixels(static_cast<const __nv_bfloat16*>(x), nullptr, g,
+                const __nv_bfloat16* ph = stream_hist_pixels(g, "stage.c0");
+                other([&] { return launch_im2col_pixels(static_cast<const __nv_bfloat16*>(x), ph, g,
                                                         reinterpret_cast<__nv_bfloat16*>(w.gather), s); },
                       gather_bytes(g));
+                stream_update("stage.c0", x, T);
                 X = conv_gathered("stage.c0", N, T, d.Hp, d.Wp, w.act[0], OUT_PLAIN, nullptr);
             } else {
                 Act P = edge_pad_f32(static_cast<const float*>(x), N, T, H, W, d.Hp, d.Wp);
@@ -533,9 +639,11 @@ struct Exec {
         }
         if (c->bf16()) {
             GatherGeo g = gather_pixels(N, T, H, W, d.Hp, d.Wp, 2);
-            other([&] { return launch_im2col_pixels(static_cast<const __nv_bfloat16*>(x), nullptr, g,
+            const __nv_bfloat16* ph = stream_hist_pixels(g, "enc.stem");
+            other([&] { return launch_im2col_pixels(static_cast<const __nv_bfloat16*>(x), ph, g,
                                                     reinterpret_cast<__nv_bfloat16*>(w.gather), s); },
                   gather_bytes(g));
+            stream_update("enc.stem", x, T);
             X = conv_gathered("enc.stem", N, T, d.Hp / 2, d.Wp / 2, w.act[0], OUT_PLAIN, nullptr);
         } else {
             Act P = edge_pad_f32(static_cast<const float*>(x), N, T, H, W, d.Hp, d.Wp);
@@ -558,6 +666,7 @@ struct Exec {
     void out_conv(const std::string& name, const Act& A, float* z, int32_t* idx) {
         const ConvW& cw = c->convs[c->cindex[name]];
         ConvArgs a = base_args(cw, A, 1, 1, 1);
+        stream_args(a, name, cw.k, 1);
         a.out = z;
         a.oT = a.Tout;
         a.oH = a.Hout;
@@ -574,6 +683,7 @@ struct Exec {
             launch(a, cw);
             if (idx) other([&] { return launch_fsq(z, ntok, c->fsq, idx, nullptr, s); }, (double)ntok * (4 * cw.Cout + 4));
         }
+        stream_update(name, A.p, A.T);
     }
 
     GatherGeo gather_pixels(int N, int T, int H, int W, int Hp, int Wp, int stride_hw) {
@@ -596,6 +706,12 @@ struct Exec {
         g.pad_mode = c->arch.time_pad;
         g.Kpad = round_up(27 * g.Cin, 64);
         return g;
+    }
+
+    const __nv_bfloat16* stream_hist_pixels(GatherGeo& g, const char* name) {
+        if (!st || chunk0) return nullptr;
+        g.hist_T = 2;
+        return reinterpret_cast<const __nv_bfloat16*>(st->hist[name]);
     }
 
     static double gather_bytes(const GatherGeo& g) {
@@ -632,9 +748,15 @@ struct Exec {
             g.t_off = -2;
             g.pad_mode = ar.time_pad;
             g.Kpad = round_up(27 * ar.nlev, 64);
-            other([&] { return launch_im2col_tokens(idx, nullptr, g, c->fsq,
+            const int32_t* th = nullptr;
+            if (st && !chunk0) {
+                th = reinterpret_cast<const int32_t*>(st->hist["dec.in"]);
+                g.hist_T = 2;
+            }
+            other([&] { return launch_im2col_tokens(idx, th, g, c->fsq,
                                                     reinterpret_cast<__nv_bfloat16*>(w.gather), s); },
                   gather_bytes(g));
+            stream_update("dec.in", idx, Tq, true);
             X = conv_gathered("dec.in", N, Tq, Hq, Wq, w.act[0], OUT_PLAIN, nullptr);
         } else {
             float* codes = reinterpret_cast<float*>(w.zbuf);
@@ -656,6 +778,12 @@ struct Exec {
         conv_d2s("dec.out", A, xhat, 1, 2, 2, H, W, true);
     }
 };
+
+// A stream's caches may be advanced by any context with the same architecture
+// and precision (a serving loop runs chunks of one stream on several lanes).
+bool compatible(const tok_ctx* a, const tok_ctx* b) {
+    return a == b || (a && b && a->precision == b->precision && memcmp(&a->arch, &b->arch, sizeof(tok_arch)) == 0);
+}
 
 int check_cuda_device(int* num_sms) {
     int dev = 0;
@@ -831,15 +959,25 @@ int tok_latent_shape(const tok_ctx* c, int T, int H, int W, int* Tq, int* Hq, in
 int tok_encode(tok_ctx* c, const void* x, int N, int T, int H, int W, float* z, int32_t* idx, tok_stream* st,
                void* stream) {
     if (!c || !x || N < 1 || T < 1 || H < 1 || W < 1) return TOK_EINVAL;
-    if (st) return TOK_ESTATE;  // chunked streaming: see tok_stream_open
-    if ((T - 1) % c->s_t != 0) return TOK_ESHAPE;
-    const Layout L = layout_for(c, N, T, H, W);
-    if (L.total > c->arena_bytes) return TOK_ENOMEM;
     Exec ex;
     ex.c = c;
     ex.s = static_cast<cudaStream_t>(stream);
+    Layout L;
+    if (st) {
+        // one chunk of a stream: frame 0 alone, then s_T frames per chunk
+        if (!compatible(st->ctx, c) || N != 1 || H != st->H || W != st->W) return TOK_EINVAL;
+        if (T != (st->enc_chunk == 0 ? 1 : c->s_t)) return TOK_ESHAPE;
+        L = layout_for(c, 1, c->s_t, H, W);
+        ex.st = st;
+        ex.chunk0 = st->enc_chunk == 0;
+    } else {
+        if ((T - 1) % c->s_t != 0) return TOK_ESHAPE;
+        L = layout_for(c, N, T, H, W);
+    }
+    if (L.total > c->arena_bytes) return TOK_ENOMEM;
     ex.w = carve(c, L);
     ex.encode(x, N, T, H, W, z, idx);
+    if (st && !ex.err) st->enc_chunk++;
     return ex.err;
 }
 
@@ -847,16 +985,27 @@ int tok_decode(tok_ctx* c, const int32_t* idx, int N, int Tq, int Hq, int Wq, in
                tok_stream* st, void* stream) {
     if (!c || !idx || !xhat || N < 1 || Tq < 1 || Hq < 1 || Wq < 1 || H < 1 || W < 1) return TOK_EINVAL;
     if (c->arch.kind != TOK_ARCH_FULL) return TOK_ESTATE;
-    if (st) return TOK_ESTATE;
     if (H > Hq * c->s_hw || W > Wq * c->s_hw) return TOK_ESHAPE;
-    const int T = 1 + c->s_t * (Tq - 1);
-    const Layout L = layout_for(c, N, T, Hq * c->s_hw, Wq * c->s_hw);
-    if (L.total > c->arena_bytes) return TOK_ENOMEM;
     Exec ex;
     ex.c = c;
     ex.s = static_cast<cudaStream_t>(stream);
+    Layout L;
+    if (st) {
+        // one latent frame of a stream -> 1 frame (chunk 0) or s_T frames
+        if (!compatible(st->ctx, c) || N != 1 || Tq != 1) return TOK_EINVAL;
+        const Dims d = clip_dims(c, 1, st->H, st->W);
+        if (H != st->H || W != st->W || Hq != d.Hq || Wq != d.Wq) return TOK_ESHAPE;
+        L = layout_for(c, 1, c->s_t, Hq * c->s_hw, Wq * c->s_hw);
+        ex.st = st;
+        ex.chunk0 = st->dec_chunk == 0;
+    } else {
+        const int T = 1 + c->s_t * (Tq - 1);
+        L = layout_for(c, N, T, Hq * c->s_hw, Wq * c->s_hw);
+    }
+    if (L.total > c->arena_bytes) return TOK_ENOMEM;
     ex.w = carve(c, L);
     ex.decode(idx, N, Tq, Hq, Wq, H, W, xhat);
+    if (st && !ex.err) st->dec_chunk++;
     return ex.err;
 }
 
@@ -914,23 +1063,48 @@ int tok_unpack_rows(const int32_t* payload, const int64_t* row_offsets, const ui
 }
 
 size_t tok_stream_bytes(const tok_ctx* c, int H, int W) {
-    (void)c;
-    (void)H;
-    (void)W;
-    return 0;
+    if (!c || H < 1 || W < 1) return 0;
+    size_t total = 0;
+    for (const auto& kv : stream_frames(c, H, W)) total += align256(2 * kv.second);
+    return total;
 }
 
 int tok_stream_open(tok_ctx* c, int H, int W, tok_stream** out) {
-    (void)c;
-    (void)H;
-    (void)W;
-    if (out) *out = nullptr;
-    return TOK_ESTATE;
+    if (!c || !out || H < 1 || W < 1) return TOK_EINVAL;
+    *out = nullptr;
+    const size_t bytes = tok_stream_bytes(c, H, W);
+    tok_stream* st = new tok_stream();
+    st->ctx = c;
+    st->H = H;
+    st->W = W;
+    if (cudaMalloc(&st->mem, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        delete st;
+        return TOK_ENOMEM;
+    }
+    st->bytes = bytes;
+    char* p = st->mem;
+    for (const auto& kv : stream_frames(c, H, W)) {
+        st->hist[kv.first] = p;
+        st->frame_bytes[kv.first] = kv.second;
+        p += align256(2 * kv.second);
+    }
+    *out = st;
+    return TOK_OK;
 }
 
-void tok_stream_close(tok_stream* s) { delete s; }
+void tok_stream_close(tok_stream* s) {
+    if (!s) return;
+    if (s->mem) cudaFree(s->mem);
+    delete s;
+}
 
-int tok_stream_reset(tok_stream* s) { return s ? TOK_OK : TOK_EINVAL; }
+int tok_stream_reset(tok_stream* s) {
+    if (!s) return TOK_EINVAL;
+    s->enc_chunk = 0;
+    s->dec_chunk = 0;
+    return TOK_OK;
+}
 
 size_t tok_conv3d_workspace_bytes(int precision, int Cin, int Cout, int k) {
     if ((precision != TOK_BF16 && precision != TOK_FP32) || Cin < 1 || Cout < 1 || (k != 1 && k != 3)) return 0;

@@ -100,25 +100,51 @@ class Tokenizer:
 
     # -- encode / decode --------------------------------------------------
     def encode(self, x: torch.Tensor, z: torch.Tensor | None = None, idx: torch.Tensor | None = None,
-               stream=None, want_z=True):
+               stream=None, want_z=True, video=None):
+        """Encode a clip, or (``video`` = a handle from stream_open) the next chunk of a video:
+        1 frame for its first chunk, s_T frames after that, giving one latent frame."""
         N, T, H, W, c = x.shape
         if x.dtype != self.dtype:
             raise ValueError(f"x must be {self.dtype}")
-        Tq, Hq, Wq = self.latent_shape(T, H, W)
+        if video is not None:
+            Tq, Hq, Wq = (1,) + self.latent_shape(1, H, W)[1:]
+        else:
+            Tq, Hq, Wq = self.latent_shape(T, H, W)
         if z is None and want_z:
             z = torch.empty((N, Tq, Hq, Wq, len(self.levels)), device=x.device, dtype=torch.float32)
         if idx is None:
             idx = torch.empty((N, Tq, Hq, Wq), device=x.device, dtype=torch.int32)
-        L.tok_encode(self.ctx, _ptr(x), N, T, H, W, _ptr(z), _ptr(idx), None, _stream_ptr(stream))
+        L.tok_encode(self.ctx, _ptr(x), N, T, H, W, _ptr(z), _ptr(idx), video, _stream_ptr(stream))
         return z, idx
 
-    def decode(self, idx: torch.Tensor, H: int, W: int, out: torch.Tensor | None = None, stream=None):
+    def decode(self, idx: torch.Tensor, H: int, W: int, out: torch.Tensor | None = None, stream=None,
+               video=None, first_chunk=None):
+        """Decode token indices; with ``video`` one latent frame of a stream (``first_chunk``
+        tells whether it is the stream's first, which yields 1 frame instead of s_T)."""
         N, Tq, Hq, Wq = idx.shape
-        T = 1 + (Tq - 1) * self.s_t
+        if video is not None:
+            T = 1 if first_chunk else self.s_t
+        else:
+            T = 1 + (Tq - 1) * self.s_t
         if out is None:
             out = torch.empty((N, T, H, W, 3), device=idx.device, dtype=torch.float32)
-        L.tok_decode(self.ctx, _ptr(idx), N, Tq, Hq, Wq, H, W, _ptr(out), None, _stream_ptr(stream))
+        L.tok_decode(self.ctx, _ptr(idx), N, Tq, Hq, Wq, H, W, _ptr(out), video, _stream_ptr(stream))
         return out
+
+    # -- streaming -----------------------------------------------------------
+    def stream_bytes(self, H, W) -> int:
+        return L.tok_stream_bytes(self.ctx, H, W)
+
+    def stream_open(self, H, W) -> int:
+        """Per-video causal state on the device (the conv caches); reserves the chunk workspace."""
+        self.reserve(1, self.s_t, H, W)
+        return L.tok_stream_open(self.ctx, H, W)
+
+    def stream_close(self, handle) -> None:
+        L.tok_stream_close(handle)
+
+    def stream_reset(self, handle) -> None:
+        L.tok_stream_reset(handle)
 
     @property
     def s_t(self):
