@@ -225,6 +225,40 @@ int tok_groupnorm_silu(int precision, const void* d_x, int64_t frames, int64_t H
                        const float* d_gamma, const float* d_beta, float eps, void* d_y,
                        void* d_workspace, size_t workspace_bytes, void* stream);
 
+/* Training: joint encoder/decoder optimisation through the masked decode
+ * (Sec. 7, codec training; Appendix A.2, Eq. 7: tokens are dropped at random
+ * and zero filled, and gradients reach the encoder through the decoder). The
+ * paper's losses (L1 + optical flow + adversarial, Eq. 5-6) need networks and
+ * data that are not available here; the objective is
+ * L = mean((x_hat - x)^2). FSQ rounding is passed straight through:
+ * d code_i / d z_i = h_i (1 - tanh^2(z_i + s_i)) / floor(L_i/2), and 0 at
+ * dropped tokens. Only residual-block inputs are kept; the activations inside
+ * a block are recomputed in the backward. FULL architecture, H and W
+ * multiples of s_HW, T = 1 mod s_T.
+ *
+ * Parameters as one flat FP32 vector in the order of tok_param_info
+ * (tok_param_total floats). tok_get_params copies the context's parameters
+ * out, tok_set_params_device loads them from device memory (both enqueued on
+ * `stream`). tok_train_forward runs encode -> drop (Bernoulli(drop_rate),
+ * Philox key seed, counter step) -> decode, writes x_hat (N,T,H,W,3) fp32, the
+ * loss (one fp32 on the device) and dL/dx_hat (N,T,H,W,3) fp32, and keeps what
+ * the backward needs; d_x must stay valid until tok_backward. A non-NULL
+ * d_keep_bits (row masks in the layout tok_drop_mask writes) replaces the
+ * random drop: tokens whose bit is 0 are dropped (e.g. a similarity-based
+ * token selection, Sec. 4.3 Eq. 3, or lost packets). tok_backward
+ * writes dL/dparams (flat FP32, every entry written) for the most recent
+ * tok_train_forward, given dL/dx_hat. tok_sgd: params -= lr * grads. */
+int64_t tok_param_total(const tok_ctx* ctx);
+int tok_get_params(tok_ctx* ctx, float* d_flat, void* stream);
+int tok_set_params_device(tok_ctx* ctx, const float* d_flat, void* stream);
+size_t tok_train_workspace_bytes(const tok_ctx* ctx, int N, int T, int H, int W);
+int tok_reserve_train(tok_ctx* ctx, int N, int T, int H, int W);
+int tok_train_forward(tok_ctx* ctx, const void* d_x, int N, int T, int H, int W, float drop_rate,
+                      uint64_t seed, uint64_t step, const uint32_t* d_keep_bits, float* d_xhat,
+                      float* d_loss, float* d_dxhat, void* stream);
+int tok_backward(tok_ctx* ctx, const float* d_dxhat, float* d_dparams, void* stream);
+int tok_sgd(float* d_params, const float* d_grads, int64_t n, float lr, void* stream);
+
 /* GroupNorm+SiLU without a workspace argument, for callers that cannot
  * allocate device memory (a host callback or real-time thread that may not
  * call cudaMalloc or take the allocator's locks, or an embedding with a fixed

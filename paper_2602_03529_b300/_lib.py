@@ -78,6 +78,14 @@ _SIGS = {
                          vp]),
     "tok_groupnorm_workspace_bytes": (sz, [i32, i64, i64, i32, i32]),
     "tok_groupnorm_silu": (i32, [i32, vp, i64, i64, i32, i32, vp, vp, f32, vp, vp, sz, vp]),
+    "tok_param_total": (i64, [vp]),
+    "tok_get_params": (i32, [vp, vp, vp]),
+    "tok_set_params_device": (i32, [vp, vp, vp]),
+    "tok_train_workspace_bytes": (sz, [vp, i32, i32, i32, i32]),
+    "tok_reserve_train": (i32, [vp, i32, i32, i32, i32]),
+    "tok_train_forward": (i32, [vp, vp, i32, i32, i32, i32, f32, u64, u64, vp, vp, vp, vp, vp]),
+    "tok_backward": (i32, [vp, vp, vp, vp]),
+    "tok_sgd": (i32, [vp, vp, i64, f32, vp]),
     "tok_groupnorm_silu_noalloc": (i32, [i32, vp, i64, i64, i32, i32, vp, vp, f32, vp, vp]),
     "tok_status": (i32, [vp]),
     "tok_strerror": (C.c_char_p, [i32]),
@@ -280,3 +288,37 @@ def tok_profile_read(ctx) -> dict:
     st = tok_profile_stats()
     _ck(_call("tok_profile_read", ctx, C.byref(st)), "tok_profile_read")
     return {f: getattr(st, f) for f, _ in tok_profile_stats._fields_}
+
+
+def tok_param_total(ctx) -> int:
+    return _call("tok_param_total", ctx)
+
+
+def tok_get_params(ctx, d_flat, cuda_stream) -> None:
+    _ck(_call("tok_get_params", ctx, d_flat, cuda_stream), "tok_get_params")
+
+
+def tok_set_params_device(ctx, d_flat, cuda_stream) -> None:
+    _ck(_call("tok_set_params_device", ctx, d_flat, cuda_stream), "tok_set_params_device")
+
+
+def tok_train_workspace_bytes(ctx, N, T, H, W) -> int:
+    return _call("tok_train_workspace_bytes", ctx, N, T, H, W)
+
+
+def tok_reserve_train(ctx, N, T, H, W) -> None:
+    _ck(_call("tok_reserve_train", ctx, N, T, H, W), "tok_reserve_train")
+
+
+def tok_train_forward(ctx, x_ptr, N, T, H, W, rate, seed, step, keep_ptr, xhat_ptr, loss_ptr, dxhat_ptr,
+                      cuda_stream) -> None:
+    _ck(_call("tok_train_forward", ctx, x_ptr, N, T, H, W, rate, seed, step, keep_ptr, xhat_ptr, loss_ptr,
+              dxhat_ptr, cuda_stream), "tok_train_forward")
+
+
+def tok_backward(ctx, dxhat_ptr, dparams_ptr, cuda_stream) -> None:
+    _ck(_call("tok_backward", ctx, dxhat_ptr, dparams_ptr, cuda_stream), "tok_backward")
+
+
+def tok_sgd(p_ptr, g_ptr, n, lr, cuda_stream) -> None:
+    _ck(_call("tok_sgd", p_ptr, g_ptr, n, lr, cuda_stream), "tok_sgd")

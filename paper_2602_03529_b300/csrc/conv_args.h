@@ -7,7 +7,8 @@
 //   hi = ho*sh + dh - (kh-1)/2,  wi = wo*sw + dw - (kw-1)/2
 // A tap with ti < 0 reads, in this order of precedence: frame (hist_T + ti)
 // of the history tensor when one is given (streaming), frame 0 (replicate
-// pad) or zero (zero pad). Taps outside [0,H) x [0,W) read zero.
+// pad) or zero (zero pad). A tap with ti >= Tin (only the adjoint convs of the
+// backward read ahead) and taps outside [0,H) x [0,W) read zero.
 //
 // Epilogue modes:
 //   OUT_PLAIN : out[n,to,ho,wo,co] = y (+ residual[n,to,ho,wo,co])
@@ -67,6 +68,17 @@ struct GatherGeo {
     int Tout, Hout, Wout;
     int kt, kh, kw, st, sh, sw, t_off, pad_mode;
     int Kpad;
+};
+
+// One weight-gradient problem: dY of a conv (N,Tout,Hout,Wout,Cdy) against its input
+// (N,Tin,Hin,Win,Cin); same tap rule as the forward conv.
+struct WgradArgs {
+    int N, Tin, Hin, Win, Cin;
+    int Tout, Hout, Wout, Cout, Cdy;  // Cdy: channel stride of dY (>= Cout)
+    int kt, kh, kw, st, sh, sw, t_off, pad_mode;
+    int K;                            // taps * Cin
+    long long V;                      // N * Tout * Hout * Wout
+    long long vchunk;                 // voxels per split
 };
 
 }  // namespace tok

@@ -1,0 +1,594 @@
+// Backward kernels of the tokenizer's training step (joint encoder/decoder
+// training through the masked decode, Sec. 7 / Appendix A.2; MSE objective,
+// straight-through FSQ):
+//   wgrad        dW[co][tap][ci] = sum_v dY[v][co] * X_tap(v)[ci] and
+//                db[co] = sum_v dY[v][co]: split-K over voxels into FP32
+//                partials, then a fixed-order reduction (deterministic).
+//   GN+SiLU bwd  three passes: per (frame, chunk) partial sums of
+//                g = dy*SiLU'(h)*gamma and g*xhat (and per-channel dgamma,
+//                dbeta), fixed-order finalize, then
+//                dx = rstd * (g - mean(g) - xhat * mean(g*xhat)) (+ a skip term).
+//   STE bwd      dz_i = dcode_i * h_i (1 - tanh^2(z_i + s_i)) / floor(L_i/2) at
+//                kept tokens, 0 at dropped ones.
+//   s2d          adjoint of depth-to-space (zeros for the trimmed frames).
+//   zero insert  adjoint of a stride-2 conv as a stride-1 one over dY spread
+//                onto the input grid.
+//   MSE          loss = mean((xhat - x)^2) and d loss / d xhat.
+//   weight packs flipped / transposed weights for the adjoint convs.
+//   SGD          p -= lr * g.
+// All are bandwidth-bound except wgrad (CUDA-core FP32 FMA).
+#include "common.cuh"
+#include "conv_args.h"
+
+#include <algorithm>
+
+namespace tok {
+
+namespace {
+
+template <typename T>
+__device__ __forceinline__ float ldf(const T* p) {
+    if constexpr (sizeof(T) == 2)
+        return __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(p));
+    else
+        return *p;
+}
+
+template <typename T>
+__device__ __forceinline__ void stf(T* p, float v) {
+    if constexpr (sizeof(T) == 2)
+        *reinterpret_cast<__nv_bfloat16*>(p) = __float2bfloat16_rn(v);
+    else
+        *p = v;
+}
+
+inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+// ------------------------------------------------------------------ wgrad
+
+constexpr int WB = 64;  // co tile and k tile
+constexpr int WV = 16;  // voxels per step
+
+template <typename T>
+__global__ void __launch_bounds__(256) wgrad_kernel(const T* __restrict__ dy, const T* __restrict__ x, WgradArgs a,
+                                                    float* __restrict__ part, float* __restrict__ dbpart) {
+    __shared__ __align__(16) float dyS[WV][WB];
+    __shared__ __align__(16) float xS[WV][WB];
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    const int co0 = blockIdx.x * WB, k0 = blockIdx.y * WB, split = blockIdx.z;
+    const long long v_begin = (long long)split * a.vchunk;
+    const long long v_end = min(a.V, v_begin + a.vchunk);
+    float acc[4][4] = {};
+    float dbacc[4] = {};
+    const bool do_db = blockIdx.y == 0 && tx == 0;
+    // loader role: voxel lv (0..15), 4 consecutive columns lc
+    const int lv = tid / 16, lc = (tid % 16) * 4;
+    for (long long v0 = v_begin; v0 < v_end; v0 += WV) {
+        const long long v = v0 + lv;
+        float dyv[4] = {0.f, 0.f, 0.f, 0.f}, xv[4] = {0.f, 0.f, 0.f, 0.f};
+        if (v < v_end) {
+            const T* dp = dy + v * a.Cdy;
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+                if (co0 + lc + e < a.Cout) dyv[e] = ldf(dp + co0 + lc + e);
+            long long m = v;
+            const int wo = (int)(m % a.Wout); m /= a.Wout;
+            const int ho = (int)(m % a.Hout); m /= a.Hout;
+            const int to = (int)(m % a.Tout);
+            const int n = (int)(m / a.Tout);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const int k = k0 + lc + e;
+                if (k >= a.K) continue;
+                const int tap = k / a.Cin, ci = k - tap * a.Cin;
+                const int dw = tap % a.kw, dh = (tap / a.kw) % a.kh, dt = tap / (a.kw * a.kh);
+                const int hi = ho * a.sh + dh - (a.kh - 1) / 2, wi = wo * a.sw + dw - (a.kw - 1) / 2;
+                if (hi < 0 || hi >= a.Hin || wi < 0 || wi >= a.Win) continue;
+                int ti = to * a.st + dt + a.t_off;
+                if (ti < 0) {
+                    if (a.pad_mode != 0) continue;
+                    ti = 0;
+                }
+                if (ti >= a.Tin) continue;
+                xv[e] = ldf(x + ((((long long)n * a.Tin + ti) * a.Hin + hi) * a.Win + wi) * a.Cin + ci);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            dyS[lv][lc + e] = dyv[e];
+            xS[lv][lc + e] = xv[e];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int vv = 0; vv < WV; ++vv) {
+            const float4 d4 = *reinterpret_cast<const float4*>(&dyS[vv][ty * 4]);
+            const float4 x4 = *reinterpret_cast<const float4*>(&xS[vv][tx * 4]);
+            const float dv[4] = {d4.x, d4.y, d4.z, d4.w}, xw[4] = {x4.x, x4.y, x4.z, x4.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(dv[i], xw[j], acc[i][j]);
+            if (do_db) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) dbacc[i] += dv[i];
+            }
+        }
+    }
+    float* P = part + (long long)split * a.Cout * a.K;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int co = co0 + ty * 4 + i;
+        if (co >= a.Cout) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int k = k0 + tx * 4 + j;
+            if (k < a.K) P[(long long)co * a.K + k] = acc[i][j];
+        }
+        if (do_db) dbpart[(long long)split * a.Cout + co] = dbacc[i];
+    }
+}
+
+__global__ void wgrad_reduce_kernel(const float* __restrict__ part, const float* __restrict__ dbpart, int S, int Cout,
+                                    int K, float* __restrict__ dw, float* __restrict__ db) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long n = (long long)Cout * K;
+    if (t < n) {
+        float s = 0.f;
+        for (int i = 0; i < S; ++i) s += part[(long long)i * n + t];
+        dw[t] = s;
+    }
+    if (db && t < Cout) {
+        float s = 0.f;
+        for (int i = 0; i < S; ++i) s += dbpart[(long long)i * Cout + t];
+        db[t] = s;
+    }
+}
+
+// ------------------------------------------------------------ GN+SiLU bwd
+
+constexpr int NT = 256;
+
+template <typename T>
+struct V8;
+template <>
+struct V8<float> {
+    static constexpr int N = 4;
+};
+template <>
+struct V8<__nv_bfloat16> {
+    static constexpr int N = 8;
+};
+
+// per (frame, chunk, group): (sum g, sum g*xhat); per (frame*S + chunk, channel): (sum dh*xhat, sum dh)
+template <typename T>
+__global__ void __launch_bounds__(NT) gn_bwd_reduce_kernel(const T* __restrict__ x, const T* __restrict__ dy,
+                                                           const float2* __restrict__ stats,
+                                                           const float* __restrict__ gamma,
+                                                           const float* __restrict__ beta, long long vpf, int C,
+                                                           int G, int S, int vpt, float2* __restrict__ pg,
+                                                           float2* __restrict__ pc) {
+    constexpr int V = V8<T>::N;
+    __shared__ float2 redc[NT][V];
+    __shared__ float2 redg[NT][V];
+    const int frame = blockIdx.y, chunk = blockIdx.x, tid = threadIdx.x;
+    const int vpv = C / V, cg = C / G;
+    const int c0 = (tid % vpv) * V;
+    float mu[V], rs[V], ga[V], be[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+        const float2 st = stats[(long long)frame * G + (c0 + j) / cg];
+        mu[j] = st.x;
+        rs[j] = st.y;
+        ga[j] = gamma ? gamma[c0 + j] : 1.f;
+        be[j] = beta ? beta[c0 + j] : 0.f;
+    }
+    float sdx[V] = {}, sd[V] = {}, sg[V] = {}, sgx[V] = {};
+    const long long base = (long long)frame * vpf * V;
+    const long long v0 = (long long)chunk * NT * vpt;
+    for (int i = 0; i < vpt; ++i) {
+        const long long vi = v0 + (long long)i * NT + tid;
+        if (vi >= vpf) break;
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            const float xv = ldf(x + base + vi * V + j);
+            const float gv = ldf(dy + base + vi * V + j);
+            const float xh = (xv - mu[j]) * rs[j];
+            const float h = xh * ga[j] + be[j];
+            const float s = 1.f / (1.f + expf(-h));
+            const float dh = gv * s * (1.f + h * (1.f - s));
+            sdx[j] += dh * xh;
+            sd[j] += dh;
+            const float g = dh * ga[j];
+            sg[j] += g;
+            sgx[j] += g * xh;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+        redc[tid][j] = make_float2(sdx[j], sd[j]);
+        redg[tid][j] = make_float2(sg[j], sgx[j]);
+    }
+    __syncthreads();
+    for (int stride = NT / 2; stride >= vpv; stride >>= 1) {
+        if (tid < stride) {
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                redc[tid][j].x += redc[tid + stride][j].x;
+                redc[tid][j].y += redc[tid + stride][j].y;
+                redg[tid][j].x += redg[tid + stride][j].x;
+                redg[tid][j].y += redg[tid + stride][j].y;
+            }
+        }
+        __syncthreads();
+    }
+    // per channel
+    for (int c = tid; c < C; c += NT) pc[((long long)frame * S + chunk) * C + c] = redc[c / V][c % V];
+    // per group: the channels of group g are c in [g*cg, (g+1)*cg)
+    for (int g = tid; g < G; g += NT) {
+        float2 acc = make_float2(0.f, 0.f);
+        for (int c = g * cg; c < (g + 1) * cg; ++c) {
+            acc.x += redg[c / V][c % V].x;
+            acc.y += redg[c / V][c % V].y;
+        }
+        pg[((long long)frame * S + chunk) * G + g] = acc;
+    }
+}
+
+__global__ void gn_bwd_finalize_kernel(const float2* __restrict__ pg, int S, int G, float inv_n,
+                                       float2* __restrict__ gstat) {
+    const int frame = blockIdx.x;
+    for (int g = threadIdx.x; g < G; g += blockDim.x) {
+        float a = 0.f, b = 0.f;
+        for (int c = 0; c < S; ++c) {
+            const float2 v = pg[((long long)frame * S + c) * G + g];
+            a += v.x;
+            b += v.y;
+        }
+        gstat[(long long)frame * G + g] = make_float2(a * inv_n, b * inv_n);
+    }
+}
+
+__global__ void gn_bwd_channel_kernel(const float2* __restrict__ pc, long long rows, int C, float* __restrict__ dgamma,
+                                      float* __restrict__ dbeta) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    float a = 0.f, b = 0.f;
+    for (long long r = 0; r < rows; ++r) {
+        const float2 v = pc[r * C + c];
+        a += v.x;
+        b += v.y;
+    }
+    if (dgamma) dgamma[c] = a;
+    if (dbeta) dbeta[c] = b;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) gn_bwd_apply_kernel(const T* __restrict__ x, const T* __restrict__ dy,
+                                                          const float2* __restrict__ stats,
+                                                          const float2* __restrict__ gstat,
+                                                          const float* __restrict__ gamma,
+                                                          const float* __restrict__ beta, const T* __restrict__ add,
+                                                          long long vpf, int C, int G, int vpt, T* __restrict__ dx) {
+    constexpr int V = V8<T>::N;
+    const int frame = blockIdx.y, chunk = blockIdx.x, tid = threadIdx.x;
+    const int vpv = C / V, cg = C / G;
+    const int c0 = (tid % vpv) * V;
+    float mu[V], rs[V], ga[V], be[V], m1[V], m2[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+        const int g = (c0 + j) / cg;
+        const float2 st = stats[(long long)frame * G + g];
+        const float2 gs = gstat[(long long)frame * G + g];
+        mu[j] = st.x;
+        rs[j] = st.y;
+        m1[j] = gs.x;
+        m2[j] = gs.y;
+        ga[j] = gamma ? gamma[c0 + j] : 1.f;
+        be[j] = beta ? beta[c0 + j] : 0.f;
+    }
+    const long long base = (long long)frame * vpf * V;
+    const long long v0 = (long long)chunk * NT * vpt;
+    for (int i = 0; i < vpt; ++i) {
+        const long long vi = v0 + (long long)i * NT + tid;
+        if (vi >= vpf) break;
+#pragma unroll
+        for (int j = 0; j < V; ++j) {
+            const long long o = base + vi * V + j;
+            const float xh = (ldf(x + o) - mu[j]) * rs[j];
+            const float h = xh * ga[j] + be[j];
+            const float s = 1.f / (1.f + expf(-h));
+            const float g = ldf(dy + o) * s * (1.f + h * (1.f - s)) * ga[j];
+            float r = rs[j] * (g - m1[j] - xh * m2[j]);
+            if (add) r += ldf(add + o);
+            stf(dx + o, r);
+        }
+    }
+}
+
+// ------------------------------------------------------------- STE / mask
+
+template <typename T>
+__global__ void ste_bwd_kernel(const T* __restrict__ dcodes, int Cd, const float* __restrict__ z,
+                               const uint32_t* __restrict__ keep_bits, long long ntok, int Wq, FsqConsts f,
+                               T* __restrict__ dz, int Co) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntok) return;
+    bool keep = true;
+    if (keep_bits) {
+        const int nwords = (Wq + 31) / 32;
+        const long long row = t / Wq;
+        const int w = (int)(t % Wq);
+        keep = (keep_bits[row * nwords + w / 32] >> (w % 32)) & 1u;
+    }
+    for (int c = 0; c < Co; ++c) {
+        float v = 0.f;
+        if (c < f.nlev && keep) {
+            const float th = tanhf(z[t * f.nlev + c] + f.shift[c]);
+            v = ldf(dcodes + t * Cd + c) * f.half_l[c] * (1.f - th * th) / (float)f.half_w[c];
+        }
+        stf(dz + t * Co + c, v);
+    }
+}
+
+// Dequantised codes with dropped tokens zeroed (the decoder input of a training step).
+template <typename T>
+__global__ void codes_kernel(const int32_t* __restrict__ idx, long long ntok, FsqConsts f, T* __restrict__ codes) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntok) return;
+    const int id = idx[t];
+    for (int i = 0; i < f.nlev; ++i) {
+        const int d = (id / f.basis[i]) % f.levels[i];
+        stf(codes + t * f.nlev + i, (float)(d - f.half_w[i]) / (float)f.half_w[i]);
+    }
+}
+
+// ------------------------------------------------------------------ s2d
+
+template <typename Ti, typename To>
+__global__ void s2d_kernel(const Ti* __restrict__ d, int N, int oT, int oH, int oW, int C, int rt, int rh, int rw,
+                           int drop_t, int T, int H, int W, int Cpad, To* __restrict__ out) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long total = (long long)N * T * H * W * Cpad;
+    if (t >= total) return;
+    long long r = t;
+    const int co = (int)(r % Cpad); r /= Cpad;
+    const int w = (int)(r % W); r /= W;
+    const int h = (int)(r % H); r /= H;
+    const int tt = (int)(r % T);
+    const int n = (int)(r / T);
+    float v = 0.f;
+    if (co < C * rt * rh * rw) {
+        const int ch = co % C, sub = co / C;
+        const int c = sub % rw, b = (sub / rw) % rh, a = sub / (rw * rh);
+        const int ot = tt * rt + a - drop_t, oh = h * rh + b, ow = w * rw + c;
+        if (ot >= 0 && ot < oT && oh < oH && ow < oW)
+            v = ldf(d + ((((long long)n * oT + ot) * oH + oh) * oW + ow) * C + ch);
+    }
+    stf(out + t, v);
+}
+
+template <typename T>
+__global__ void zero_insert_kernel(const T* __restrict__ dy, int N, int To, int Ho, int Wo, int C, int Tin, int Hin,
+                                   int Win, int st, int sh, int sw, T* __restrict__ out) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long total = (long long)N * Tin * Hin * Win * C;
+    if (t >= total) return;
+    long long r = t;
+    const int c = (int)(r % C); r /= C;
+    const int w = (int)(r % Win); r /= Win;
+    const int h = (int)(r % Hin); r /= Hin;
+    const int tt = (int)(r % Tin);
+    const int n = (int)(r / Tin);
+    float v = 0.f;
+    if (tt % st == 0 && h % sh == 0 && w % sw == 0) {
+        const int a = tt / st, b = h / sh, e = w / sw;
+        if (a < To && b < Ho && e < Wo) v = ldf(dy + ((((long long)n * To + a) * Ho + b) * Wo + e) * C + c);
+    }
+    stf(out + t, v);
+}
+
+// ------------------------------------------------------------------ MSE
+
+template <typename T>
+__global__ void mse_partial_kernel(const float* __restrict__ xh, const T* __restrict__ x, long long n, float scale,
+                                   float* __restrict__ dxh, float* __restrict__ part) {
+    __shared__ float red[256];
+    float s = 0.f;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float d = xh[i] - ldf(x + i);
+        s += d * d;
+        if (dxh) dxh[i] = scale * d;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = 128; k > 0; k >>= 1) {
+        if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void mse_final_kernel(const float* __restrict__ part, int nb, float inv_n, float* __restrict__ loss) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < nb; ++i) s += part[i];
+        *loss = (float)(s * inv_n);
+    }
+}
+
+// ---------------------------------------------------------- weight packs
+
+// Adjoint-conv weights: Wf[ci][tap'][co] with tap' the spatio-temporal flip
+// of tap (k = 3) or identity (k = 1); rows padded to rows_pad, the co axis to
+// cpad per tap. `corr` selects the replicate-pad correction weights (k = 3):
+// two temporal taps d'' with V[0] = W[dt=0] + W[dt=1], V[1] = W[dt=0], both
+// spatially flipped.
+template <typename T>
+__global__ void pack_adjoint_kernel(const float* __restrict__ w, int Cout, int Cin, int k, int rows_pad, int cpad,
+                                    int corr, T* __restrict__ out) {
+    const int taps_out = corr ? 2 * k * k : k * k * k;
+    const long long total = (long long)rows_pad * taps_out * cpad;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= total) return;
+    const int co = (int)(t % cpad);
+    const int tap = (int)((t / cpad) % taps_out);
+    const int ci = (int)(t / ((long long)cpad * taps_out));
+    float v = 0.f;
+    if (ci < Cin && co < Cout) {
+        const int k2 = k * k;
+        const int dwp = tap % k, dhp = (tap / k) % k, dtp = tap / k2;
+        const int dh = k - 1 - dhp, dw = k - 1 - dwp;
+        auto W = [&](int dt) { return w[(((long long)co * k + dt) * k2 + dh * k + dw) * Cin + ci]; };
+        if (!corr) {
+            v = W(k - 1 - dtp);
+        } else {
+            v = (dtp == 0) ? W(0) + W(1) : W(0);
+        }
+    }
+    stf(out + t, v);
+}
+
+__global__ void sgd_kernel(float* __restrict__ p, const float* __restrict__ g, long long n, float lr) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) p[t] -= lr * g[t];
+}
+
+}  // namespace
+
+// ======================================================================= host
+
+size_t wgrad_partial_floats(int Cout, int K, int S) { return (size_t)S * Cout * K + (size_t)S * Cout; }
+
+int wgrad_splits(const WgradArgs& a, int num_sms, size_t max_partial_floats) {
+    const long long tiles = (long long)((a.Cout + WB - 1) / WB) * ((a.K + WB - 1) / WB);
+    long long S = (4LL * num_sms + tiles - 1) / tiles;
+    S = std::max(1LL, std::min(S, (a.V + 255) / 256));
+    while (S > 1 && wgrad_partial_floats(a.Cout, a.K, (int)S) > max_partial_floats) --S;
+    return (int)std::min(S, 256LL);
+}
+
+template <typename T>
+int launch_wgrad(const T* dy, const T* x, WgradArgs a, int S, float* part, float* dw, float* db, cudaStream_t s) {
+    if (a.V <= 0) return 0;
+    a.vchunk = ((a.V + S - 1) / S + WV - 1) / WV * WV;
+    float* dbpart = part + (size_t)S * a.Cout * a.K;
+    dim3 grid((a.Cout + WB - 1) / WB, (a.K + WB - 1) / WB, S);
+    wgrad_kernel<T><<<grid, 256, 0, s>>>(dy, x, a, part, dbpart);
+    const long long n = std::max<long long>((long long)a.Cout * a.K, a.Cout);
+    wgrad_reduce_kernel<<<blocks_for(n, 256), 256, 0, s>>>(part, dbpart, S, a.Cout, a.K, dw, db);
+    return (int)cudaGetLastError();
+}
+template int launch_wgrad<float>(const float*, const float*, WgradArgs, int, float*, float*, float*, cudaStream_t);
+template int launch_wgrad<__nv_bfloat16>(const __nv_bfloat16*, const __nv_bfloat16*, WgradArgs, int, float*, float*,
+                                         float*, cudaStream_t);
+
+// Scratch layout of the GN backward: pg[frames*S*G], pc[frames*S*C], gstat[frames*G] (float2 each).
+size_t gn_bwd_scratch_bytes(long long frames, int S, int C, int G) {
+    return ((size_t)frames * S * G + (size_t)frames * S * C + (size_t)frames * G) * sizeof(float2) + 256;
+}
+
+// stats: (mean, rstd) per (frame, group) from the forward statistics pass.
+template <typename T>
+int launch_gn_silu_bwd(const T* x, const T* dy, const float2* stats, const float* gamma, const float* beta,
+                       const T* add, long long frames, long long HW, int C, int G, int vpt, int S, void* scratch,
+                       float* dgamma, float* dbeta, T* dx, cudaStream_t s) {
+    constexpr int V = V8<T>::N;
+    const long long vpf = HW * C / V;
+    float2* pg = static_cast<float2*>(scratch);
+    float2* pc = pg + frames * S * G;
+    float2* gstat = pc + frames * S * C;
+    dim3 grid(S, (unsigned)frames);
+    gn_bwd_reduce_kernel<T><<<grid, NT, 0, s>>>(x, dy, stats, gamma, beta, vpf, C, G, S, vpt, pg, pc);
+    gn_bwd_finalize_kernel<<<(unsigned)frames, 64, 0, s>>>(pg, S, G, 1.f / (float)(HW * (C / G)), gstat);
+    gn_bwd_channel_kernel<<<(C + 127) / 128, 128, 0, s>>>(pc, frames * S, C, dgamma, dbeta);
+    gn_bwd_apply_kernel<T><<<grid, NT, 0, s>>>(x, dy, stats, gstat, gamma, beta, add, vpf, C, G, vpt, dx);
+    return (int)cudaGetLastError();
+}
+template int launch_gn_silu_bwd<float>(const float*, const float*, const float2*, const float*, const float*,
+                                       const float*, long long, long long, int, int, int, int, void*, float*, float*,
+                                       float*, cudaStream_t);
+template int launch_gn_silu_bwd<__nv_bfloat16>(const __nv_bfloat16*, const __nv_bfloat16*, const float2*,
+                                               const float*, const float*, const __nv_bfloat16*, long long, long long,
+                                               int, int, int, int, void*, float*, float*, __nv_bfloat16*,
+                                               cudaStream_t);
+
+template <typename T>
+int launch_ste_bwd(const T* dcodes, int Cd, const float* z, const uint32_t* keep_bits, long long ntok, int Wq,
+                   const FsqConsts& f, T* dz, int Co, cudaStream_t s) {
+    if (ntok <= 0) return 0;
+    ste_bwd_kernel<T><<<blocks_for(ntok, 256), 256, 0, s>>>(dcodes, Cd, z, keep_bits, ntok, Wq, f, dz, Co);
+    return (int)cudaGetLastError();
+}
+template int launch_ste_bwd<float>(const float*, int, const float*, const uint32_t*, long long, int, const FsqConsts&,
+                                   float*, int, cudaStream_t);
+template int launch_ste_bwd<__nv_bfloat16>(const __nv_bfloat16*, int, const float*, const uint32_t*, long long, int,
+                                           const FsqConsts&, __nv_bfloat16*, int, cudaStream_t);
+
+template <typename T>
+int launch_codes(const int32_t* idx, long long ntok, const FsqConsts& f, T* codes, cudaStream_t s) {
+    if (ntok <= 0) return 0;
+    codes_kernel<T><<<blocks_for(ntok, 256), 256, 0, s>>>(idx, ntok, f, codes);
+    return (int)cudaGetLastError();
+}
+template int launch_codes<float>(const int32_t*, long long, const FsqConsts&, float*, cudaStream_t);
+template int launch_codes<__nv_bfloat16>(const int32_t*, long long, const FsqConsts&, __nv_bfloat16*, cudaStream_t);
+
+template <typename Ti, typename To>
+int launch_s2d(const Ti* d, int N, int oT, int oH, int oW, int C, int rt, int rh, int rw, int drop_t, int T, int H,
+               int W, int Cpad, To* out, cudaStream_t s) {
+    const long long n = (long long)N * T * H * W * Cpad;
+    if (n <= 0) return 0;
+    s2d_kernel<Ti, To><<<blocks_for(n, 256), 256, 0, s>>>(d, N, oT, oH, oW, C, rt, rh, rw, drop_t, T, H, W, Cpad, out);
+    return (int)cudaGetLastError();
+}
+template int launch_s2d<float, float>(const float*, int, int, int, int, int, int, int, int, int, int, int, int, int,
+                                      float*, cudaStream_t);
+template int launch_s2d<float, __nv_bfloat16>(const float*, int, int, int, int, int, int, int, int, int, int, int, int,
+                                              int, __nv_bfloat16*, cudaStream_t);
+template int launch_s2d<__nv_bfloat16, __nv_bfloat16>(const __nv_bfloat16*, int, int, int, int, int, int, int, int,
+                                                      int, int, int, int, int, __nv_bfloat16*, cudaStream_t);
+
+template <typename T>
+int launch_zero_insert(const T* dy, int N, int To, int Ho, int Wo, int C, int Tin, int Hin, int Win, int st, int sh,
+                       int sw, T* out, cudaStream_t s) {
+    const long long n = (long long)N * Tin * Hin * Win * C;
+    if (n <= 0) return 0;
+    zero_insert_kernel<T><<<blocks_for(n, 256), 256, 0, s>>>(dy, N, To, Ho, Wo, C, Tin, Hin, Win, st, sh, sw, out);
+    return (int)cudaGetLastError();
+}
+template int launch_zero_insert<float>(const float*, int, int, int, int, int, int, int, int, int, int, int, float*,
+                                       cudaStream_t);
+template int launch_zero_insert<__nv_bfloat16>(const __nv_bfloat16*, int, int, int, int, int, int, int, int, int, int,
+                                               int, __nv_bfloat16*, cudaStream_t);
+
+template <typename T>
+int launch_mse(const float* xh, const T* x, long long n, float* dxh, float* loss, float* scratch, cudaStream_t s) {
+    const int nb = 592;
+    mse_partial_kernel<T><<<nb, 256, 0, s>>>(xh, x, n, 2.f / (float)n, dxh, scratch);
+    mse_final_kernel<<<1, 32, 0, s>>>(scratch, nb, 1.f / (float)n, loss);
+    return (int)cudaGetLastError();
+}
+template int launch_mse<float>(const float*, const float*, long long, float*, float*, float*, cudaStream_t);
+template int launch_mse<__nv_bfloat16>(const float*, const __nv_bfloat16*, long long, float*, float*, float*,
+                                       cudaStream_t);
+
+template <typename T>
+int launch_pack_adjoint(const float* w, int Cout, int Cin, int k, int rows_pad, int cpad, int corr, T* out,
+                        cudaStream_t s) {
+    const int taps_out = corr ? 2 * k * k : k * k * k;
+    const long long n = (long long)rows_pad * taps_out * cpad;
+    pack_adjoint_kernel<T><<<blocks_for(n, 256), 256, 0, s>>>(w, Cout, Cin, k, rows_pad, cpad, corr, out);
+    return (int)cudaGetLastError();
+}
+template int launch_pack_adjoint<float>(const float*, int, int, int, int, int, int, float*, cudaStream_t);
+template int launch_pack_adjoint<__nv_bfloat16>(const float*, int, int, int, int, int, int, __nv_bfloat16*,
+                                                cudaStream_t);
+
+int launch_sgd(float* p, const float* g, long long n, float lr, cudaStream_t s) {
+    if (n <= 0) return 0;
+    sgd_kernel<<<blocks_for(n, 256), 256, 0, s>>>(p, g, n, lr);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace tok

@@ -41,6 +41,7 @@ __device__ __forceinline__ const float* src_ptr(const ConvArgs& a, const RowGeo&
     int wi = g.wo * a.sw + dw - (a.kw - 1) / 2;
     if (hi < 0 || hi >= a.Hin || wi < 0 || wi >= a.Win) return nullptr;
     int ti = g.to * a.st + dt + a.t_off;
+    if (ti >= a.Tin) return nullptr;  // past the last frame (adjoint convs read ahead): zeros
     const float* base = static_cast<const float*>(a.x);
     long long frame;
     if (ti < 0) {

@@ -180,7 +180,9 @@ __global__ void __launch_bounds__(192, 1)
                     const int ti = tc.to * a.st + dt + a.t_off;
                     const CUtensorMap* src = &tm_x;
                     int tcoord;
-                    if (ti >= 0) {
+                    if (ti >= a.Tin) {
+                        tcoord = -1;  // past the last frame (adjoint convs read ahead): zeros
+                    } else if (ti >= 0) {
                         tcoord = tc.n * a.Tin + ti;
                     } else if (a.hist) {
                         src = &tm_h;

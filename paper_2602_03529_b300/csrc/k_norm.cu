@@ -233,6 +233,36 @@ int launch_gn_silu(const T* x, T* y, long long frames, long long HW, int C, int 
     return (int)cudaGetLastError();
 }
 
+template <typename T>
+int launch_gn_stats(const T* x, long long frames, long long HW, int C, int G, float eps, void* scratch, int num_sms,
+                    cudaStream_t stream, float2** stats_out, int* vpt_out, int* S_out) {
+    constexpr int V = Vec<T>::N;
+    const long long vpf = HW * C / V;
+    int vpt, S;
+    gn_plan(frames, vpf, num_sms, &vpt, &S);
+    Triple* part = static_cast<Triple*>(scratch);
+    float2* stats = reinterpret_cast<float2*>(
+        (reinterpret_cast<uintptr_t>(part + frames * S * G) + 15) & ~uintptr_t(15));
+    dim3 grid(S, (unsigned)frames);
+    const int cg = C / G;
+    const int ngv = cg >= V ? 1 : V / cg;
+    switch (ngv) {
+        case 1: gn_partial_kernel<T, 1><<<grid, NT, 0, stream>>>(x, vpf, C, G, S, vpt, part); break;
+        case 2: gn_partial_kernel<T, 2><<<grid, NT, 0, stream>>>(x, vpf, C, G, S, vpt, part); break;
+        case 4: gn_partial_kernel<T, 4><<<grid, NT, 0, stream>>>(x, vpf, C, G, S, vpt, part); break;
+        default: return (int)cudaErrorInvalidValue;
+    }
+    gn_finalize_kernel<<<(unsigned)frames, 64, 0, stream>>>(part, S, G, eps, stats);
+    *stats_out = stats;
+    *vpt_out = vpt;
+    *S_out = S;
+    return (int)cudaGetLastError();
+}
+template int launch_gn_stats<float>(const float*, long long, long long, int, int, float, void*, int, cudaStream_t,
+                                    float2**, int*, int*);
+template int launch_gn_stats<__nv_bfloat16>(const __nv_bfloat16*, long long, long long, int, int, float, void*, int,
+                                            cudaStream_t, float2**, int*, int*);
+
 template int launch_gn_silu<float>(const float*, float*, long long, long long, int, int, const float*, const float*,
                                    float, void*, int, bool, cudaStream_t);
 template int launch_gn_silu<__nv_bfloat16>(const __nv_bfloat16*, __nv_bfloat16*, long long, long long, int, int,

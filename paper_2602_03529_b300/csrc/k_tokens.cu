@@ -166,9 +166,28 @@ __global__ void unpack_kernel(const int32_t* __restrict__ payload, const int64_t
     out[t] = v;
 }
 
+// Zero fill of the tokens a caller's row masks mark as dropped.
+__global__ void apply_keep_kernel(const int32_t* __restrict__ idx, const uint32_t* __restrict__ keep_bits,
+                                  long long ntok, int Wq, int32_t zero_index, int32_t* __restrict__ out) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= ntok) return;
+    const int nwords = (Wq + 31) / 32;
+    const long long row = t / Wq;
+    const int w = (int)(t % Wq);
+    const bool keep = (keep_bits[row * nwords + w / 32] >> (w % 32)) & 1u;
+    out[t] = keep ? idx[t] : zero_index;
+}
+
 inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
 }  // namespace
+
+int launch_apply_keep(const int32_t* idx, const uint32_t* keep_bits, long long ntok, int Wq, int32_t zero_index,
+                      int32_t* out, cudaStream_t s) {
+    if (ntok <= 0) return 0;
+    apply_keep_kernel<<<blocks_for(ntok, 256), 256, 0, s>>>(idx, keep_bits, ntok, Wq, zero_index, out);
+    return (int)cudaGetLastError();
+}
 
 int launch_fsq(const float* z, long long ntok, const FsqConsts& f, int32_t* idx, float* codes, cudaStream_t s) {
     if (ntok <= 0) return 0;

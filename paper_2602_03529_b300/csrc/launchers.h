@@ -25,6 +25,8 @@ int launch_drop(const int32_t* idx, int N, int Tq, int Hq, int Wq, unsigned long
                 cudaStream_t s);
 int launch_pack(const int32_t* idx, const uint32_t* keep_bits, long long rows, int Wq, int32_t* payload,
                 int64_t* offs, cudaStream_t s);
+int launch_apply_keep(const int32_t* idx, const uint32_t* keep_bits, long long ntok, int Wq, int32_t zero_index,
+                      int32_t* out, cudaStream_t s);
 int launch_unpack(const int32_t* payload, const int64_t* offs, const uint32_t* keep_bits, const uint8_t* received,
                   long long rows, int Wq, int32_t zero_index, int32_t* out, cudaStream_t s);
 
@@ -39,6 +41,40 @@ template <typename T>
 int launch_pack_weights(const float* w, int Cout, int K, int Cout_pad, int Kpad, T* out, cudaStream_t s);
 
 int launch_fill_i32(int32_t* p, long long n, int32_t v, cudaStream_t s);
+
+// GroupNorm statistics only: (mean, rstd) per (frame, group) written at *stats
+// (inside scratch); vpt / S report the chunking used.
+template <typename T>
+int launch_gn_stats(const T* x, long long frames, long long HW, int C, int G, float eps, void* scratch, int num_sms,
+                    cudaStream_t s, float2** stats, int* vpt, int* S);
+
+// backward kernels (k_backward.cu)
+size_t wgrad_partial_floats(int Cout, int K, int S);
+int wgrad_splits(const WgradArgs& a, int num_sms, size_t max_partial_floats);
+template <typename T>
+int launch_wgrad(const T* dy, const T* x, WgradArgs a, int S, float* part, float* dw, float* db, cudaStream_t s);
+size_t gn_bwd_scratch_bytes(long long frames, int S, int C, int G);
+template <typename T>
+int launch_gn_silu_bwd(const T* x, const T* dy, const float2* stats, const float* gamma, const float* beta,
+                       const T* add, long long frames, long long HW, int C, int G, int vpt, int S, void* scratch,
+                       float* dgamma, float* dbeta, T* dx, cudaStream_t s);
+template <typename T>
+int launch_ste_bwd(const T* dcodes, int Cd, const float* z, const uint32_t* keep_bits, long long ntok, int Wq,
+                   const FsqConsts& f, T* dz, int Co, cudaStream_t s);
+template <typename T>
+int launch_codes(const int32_t* idx, long long ntok, const FsqConsts& f, T* codes, cudaStream_t s);
+template <typename Ti, typename To>
+int launch_s2d(const Ti* d, int N, int oT, int oH, int oW, int C, int rt, int rh, int rw, int drop_t, int T, int H,
+               int W, int Cpad, To* out, cudaStream_t s);
+template <typename T>
+int launch_zero_insert(const T* dy, int N, int To, int Ho, int Wo, int C, int Tin, int Hin, int Win, int st, int sh,
+                       int sw, T* out, cudaStream_t s);
+template <typename T>
+int launch_mse(const float* xh, const T* x, long long n, float* dxh, float* loss, float* scratch, cudaStream_t s);
+template <typename T>
+int launch_pack_adjoint(const float* w, int Cout, int Cin, int k, int rows_pad, int cpad, int corr, T* out,
+                        cudaStream_t s);
+int launch_sgd(float* p, const float* g, long long n, float lr, cudaStream_t s);
 
 int launch_timeout_selftest(int* status, unsigned long long limit_ns, cudaStream_t s);
 

@@ -11,790 +11,7 @@
 //         stand-alone FSQ / dequantisation.
 // All work is enqueued on the caller's stream; nothing here synchronises
 // except tok_set_param / tok_status / allocation calls.
-#include <cuda_bf16.h>
-#include <cuda_runtime.h>
-
-#include <algorithm>
-#include <cmath>
-#include <cstdio>
-#include <cstring>
-#include <map>
-#include <string>
-#include <vector>
-
-#include "../../include/tok.h"
-#include "launchers.h"
-
-using namespace tok;
-
-namespace {
-
-constexpr unsigned long long kWaitNs = 2000000000ull;  // bounded device waits: 2 s
-
-struct ParamInfo {
-    std::string name;
-    int ndim;
-    int64_t dims[5];
-    int64_t count;
-};
-
-struct ConvW {
-    std::string name;
-    int Cin, Cout, k;
-    int im2col;     // BF16 path: input is gathered to (M, Kpad) and the conv runs as 1x1x1
-    int Cout_pad, Kpad;
-    void* w = nullptr;
-    float* b = nullptr;
-};
-
-struct GnW {
-    std::string name;
-    int C, G;
-    float* g = nullptr;
-    float* b = nullptr;
-};
-
-inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
-inline size_t align256(size_t a) { return (a + 255) & ~size_t(255); }
-
-}  // namespace
-
-struct tok_ctx {
-    tok_arch arch;
-    int precision;
-    int device = 0, num_sms = 148;
-    std::vector<ParamInfo> params;
-    std::map<std::string, int> pindex;
-    std::vector<std::vector<float>> host;
-    std::vector<ConvW> convs;
-    std::map<std::string, int> cindex;
-    std::vector<GnW> gns;
-    std::map<std::string, int> gindex;
-    FsqConsts fsq;
-    int* d_status = nullptr;
-    char* arena = nullptr;
-    size_t arena_bytes = 0;
-    int64_t launches = 0;
-    int s_t = 1, s_hw = 1;
-    // opt-in event timing (tok_profile_enable)
-    struct ProfRec {
-        int cls;
-        double work;
-        int ev;
-    };
-    bool prof = false;
-    std::vector<cudaEvent_t> events;
-    std::vector<ProfRec> recs;
-    int ev_used = 0;
-    bool bf16() const { return precision == TOK_BF16; }
-    size_t esize() const { return bf16() ? 2 : 4; }
-};
-
-// One video stream's causal state: for every conv with temporal taps, the
-// last two frames of its input (the left context of the next chunk), plus
-// chunk counters for the encoder and the decoder side.
-struct tok_stream {
-    tok_ctx* ctx = nullptr;
-    int H = 0, W = 0;
-    int enc_chunk = 0, dec_chunk = 0;
-    char* mem = nullptr;
-    size_t bytes = 0;
-    std::map<std::string, char*> hist;        // conv name -> 2 frames
-    std::map<std::string, size_t> frame_bytes; // conv name -> bytes of one frame
-};
-
-namespace {
-
-// ------------------------------------------------------------ layer list
-
-void add_param(tok_ctx* c, const std::string& name, std::vector<int64_t> dims) {
-    ParamInfo p;
-    p.name = name;
-    p.ndim = (int)dims.size();
-    p.count = 1;
-    for (int i = 0; i < 5; ++i) p.dims[i] = i < p.ndim ? dims[i] : 0;
-    for (auto d : dims) p.count *= d;
-    c->pindex[name] = (int)c->params.size();
-    c->params.push_back(p);
-    c->host.emplace_back((size_t)p.count, 0.f);
-}
-
-void add_conv(tok_ctx* c, const std::string& name, int cout, int cin, int k, bool im2col_in) {
-    add_param(c, name + ".w", {cout, k, k, k, cin});
-    add_param(c, name + ".b", {cout});
-    ConvW cw;
-    cw.name = name;
-    cw.Cin = cin;
-    cw.Cout = cout;
-    cw.k = k;
-    const int taps = k * k * k;
-    if (c->bf16()) {
-        cw.im2col = (im2col_in || cin % 64 != 0) ? 1 : 0;
-        cw.Kpad = cw.im2col ? round_up(taps * cin, 64) : taps * cin;
-        const int c16 = round_up(cout, 16);
-        cw.Cout_pad = round_up(c16, conv_tc_bn(c16));
-    } else {
-        cw.im2col = 0;
-        cw.Kpad = round_up(taps * cin, 8);
-        cw.Cout_pad = round_up(cout, 16);
-    }
-    c->cindex[name] = (int)c->convs.size();
-    c->convs.push_back(cw);
-}
-
-void add_gn(tok_ctx* c, const std::string& name, int C) {
-    add_param(c, name + ".g", {C});
-    add_param(c, name + ".b", {C});
-    GnW g;
-    g.name = name;
-    g.C = C;
-    g.G = std::max(1, std::min(c->arch.gn_groups, C / 2));
-    c->gindex[name] = (int)c->gns.size();
-    c->gns.push_back(g);
-}
-
-void add_block(tok_ctx* c, const std::string& name, int cin, int cout) {
-    add_gn(c, name + ".gn1", cin);
-    add_conv(c, name + ".c1", cout, cin, 3, false);
-    add_gn(c, name + ".gn2", cout);
-    add_conv(c, name + ".c2", cout, cout, 3, false);
-    if (cin != cout) add_conv(c, name + ".sc", cout, cin, 1, false);
-}
-
-void build_layers(tok_ctx* c) {
-    const tok_arch& a = c->arch;
-    const int* ch = a.ch;
-    if (a.kind == TOK_ARCH_STAGE) {
-        add_conv(c, "stage.c0", ch[0], a.in_ch, 3, true);
-        add_conv(c, "stage.c1", ch[1], ch[0], 3, false);
-        add_gn(c, "stage.gn", ch[1]);
-        add_conv(c, "stage.out", a.nlev, ch[1], 1, false);
-        c->s_t = 1;
-        c->s_hw = 2;
-        return;
-    }
-    add_conv(c, "enc.stem", ch[0], a.in_ch, 3, true);
-    for (int l = 0; l < a.nlevels; ++l) {
-        const int cin = l > 0 ? ch[l - 1] : ch[0];
-        for (int b = 0; b < a.blocks; ++b)
-            add_block(c, "enc.l" + std::to_string(l) + ".b" + std::to_string(b), b == 0 ? cin : ch[l], ch[l]);
-        if (l < a.nlevels - 1) add_conv(c, "enc.down" + std::to_string(l), ch[l], ch[l], 3, false);
-    }
-    add_gn(c, "enc.out_gn", ch[a.nlevels - 1]);
-    add_conv(c, "enc.out", a.nlev, ch[a.nlevels - 1], 3, false);
-    add_conv(c, "dec.in", ch[a.nlevels - 1], a.nlev, 3, true);
-    for (int l = a.nlevels - 1; l >= 0; --l) {
-        for (int b = 0; b < a.blocks; ++b)
-            add_block(c, "dec.l" + std::to_string(l) + ".b" + std::to_string(b), ch[l], ch[l]);
-        if (l > 0) add_conv(c, "dec.up" + std::to_string(l - 1), ch[l - 1] * 8, ch[l], 3, false);
-    }
-    add_gn(c, "dec.out_gn", ch[0]);
-    add_conv(c, "dec.out", a.in_ch * 4, ch[0], 3, false);
-    c->s_t = 1 << (a.nlevels - 1);
-    c->s_hw = 1 << a.nlevels;
-}
-
-FsqConsts make_fsq(const int* levels, int nlev) {
-    FsqConsts f;
-    memset(&f, 0, sizeof(f));
-    f.nlev = nlev;
-    int basis = 1;
-    for (int i = 0; i < nlev; ++i) {
-        const int L = levels[i];
-        const double h = (L - 1) * (1.0 - 1e-3) / 2.0;
-        const double o = (L % 2 == 0) ? 0.5 : 0.0;
-        f.levels[i] = L;
-        f.half_l[i] = (float)h;
-        f.offset[i] = (float)o;
-        f.shift[i] = (float)std::atanh(o / h);
-        f.half_w[i] = L / 2;
-        f.basis[i] = basis;
-        basis *= L;
-    }
-    return f;
-}
-
-bool valid_levels(const int* levels, int nlev) {
-    if (!levels || nlev < 1 || nlev > 8) return false;
-    long long prod = 1;
-    for (int i = 0; i < nlev; ++i) {
-        if (levels[i] < 2 || levels[i] > 16) return false;
-        prod *= levels[i];
-    }
-    return prod < (1LL << 31);
-}
-
-// Upload one conv's weights (device layout [Cout_pad][Kpad]) and bias.
-int upload_conv(tok_ctx* c, ConvW& cw) {
-    const std::vector<float>& w = c->host[c->pindex[cw.name + ".w"]];
-    const std::vector<float>& b = c->host[c->pindex[cw.name + ".b"]];
-    const int K = cw.k * cw.k * cw.k * cw.Cin;
-    const size_t n = (size_t)cw.Cout_pad * cw.Kpad;
-    if (c->bf16()) {
-        std::vector<__nv_bfloat16> hw(n, __float2bfloat16_rn(0.f));
-        for (int co = 0; co < cw.Cout; ++co)
-            for (int k = 0; k < K; ++k) hw[(size_t)co * cw.Kpad + k] = __float2bfloat16_rn(w[(size_t)co * K + k]);
-        if (cudaMemcpy(cw.w, hw.data(), n * 2, cudaMemcpyHostToDevice) != cudaSuccess) return TOK_ECUDA;
-    } else {
-        std::vector<float> hw(n, 0.f);
-        for (int co = 0; co < cw.Cout; ++co)
-            for (int k = 0; k < K; ++k) hw[(size_t)co * cw.Kpad + k] = w[(size_t)co * K + k];
-        if (cudaMemcpy(cw.w, hw.data(), n * 4, cudaMemcpyHostToDevice) != cudaSuccess) return TOK_ECUDA;
-    }
-    if (cudaMemcpy(cw.b, b.data(), b.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) return TOK_ECUDA;
-    return TOK_OK;
-}
-
-int upload_gn(tok_ctx* c, GnW& g) {
-    const std::vector<float>& ga = c->host[c->pindex[g.name + ".g"]];
-    const std::vector<float>& be = c->host[c->pindex[g.name + ".b"]];
-    if (cudaMemcpy(g.g, ga.data(), ga.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) return TOK_ECUDA;
-    if (cudaMemcpy(g.b, be.data(), be.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) return TOK_ECUDA;
-    return TOK_OK;
-}
-
-// ------------------------------------------------------------ workspace
-
-struct Layout {
-    size_t act;       // bytes per activation buffer
-    size_t gather;    // im2col (BF16) / edge-padded pixels + codes (FP32)
-    size_t zbuf;      // latent when the caller passes no z
-    size_t gn;        // GroupNorm scratch
-    size_t total;
-};
-
-struct Dims {
-    int Hp, Wp, Tq, Hq, Wq;
-};
-
-Dims clip_dims(const tok_ctx* c, int T, int H, int W) {
-    Dims d;
-    d.Hp = round_up(H, c->s_hw);
-    d.Wp = round_up(W, c->s_hw);
-    d.Tq = (T - 1) / c->s_t + 1;
-    d.Hq = d.Hp / c->s_hw;
-    d.Wq = d.Wp / c->s_hw;
-    return d;
-}
-
-Layout layout_for(const tok_ctx* c, int N, int T, int H, int W) {
-    Layout L;
-    const Dims d = clip_dims(c, T, H, W);
-    const tok_arch& a = c->arch;
-    const size_t es = c->esize();
-    size_t act = 0, gn = 0;
-    auto gn_need = [&](long long frames, long long HW, int C) {
-        const int G = std::max(1, std::min(a.gn_groups, C / 2));
-        gn = std::max(gn, gn_scratch_bytes(frames, HW, C, G, c->num_sms, c->bf16() ? 8 : 4));
-    };
-    if (a.kind == TOK_ARCH_STAGE) {
-        act = std::max<size_t>((size_t)N * T * d.Hp * d.Wp * a.ch[0], (size_t)N * T * (d.Hp / 2) * (d.Wp / 2) * a.ch[1]) * es;
-        gn_need((long long)N * T, (long long)(d.Hp / 2) * (d.Wp / 2), a.ch[1]);
-    } else {
-        int Tl = T;
-        for (int l = 0; l < a.nlevels; ++l) {
-            const long long Hl = d.Hp >> (l + 1), Wl = d.Wp >> (l + 1);
-            const int cmax = std::max(a.ch[l], l > 0 ? a.ch[l - 1] : a.ch[0]);
-            act = std::max<size_t>(act, (size_t)N * Tl * Hl * Wl * cmax * es);
-            gn_need((long long)N * Tl, Hl * Wl, a.ch[l]);
-            if (l > 0) gn_need((long long)N * Tl, Hl * Wl, a.ch[l - 1]);
-            Tl = (Tl - 1) / 2 + 1;
-        }
-    }
-    L.act = align256(act);
-    size_t g = 0;
-    const long long ntok = (long long)N * d.Tq * d.Hq * d.Wq;
-    if (c->bf16()) {
-        // stem / stage.c0 im2col and dec.in im2col
-        const long long m0 = a.kind == TOK_ARCH_STAGE ? (long long)N * T * d.Hp * d.Wp
-                                                       : (long long)N * T * (d.Hp / 2) * (d.Wp / 2);
-        g = (size_t)m0 * round_up(27 * a.in_ch, 64) * 2;
-        g = std::max(g, (size_t)ntok * round_up(27 * a.nlev, 64) * 2);
-    } else {
-        g = align256((size_t)N * T * d.Hp * d.Wp * a.in_ch * 4) + align256((size_t)ntok * a.nlev * 4);
-    }
-    L.gather = align256(g);
-    L.zbuf = align256((size_t)ntok * a.nlev * 4);
-    L.gn = align256(gn);
-    L.total = 5 * L.act + L.gather + L.zbuf + L.gn;
-    return L;
-}
-
-struct Work {
-    char* act[5];
-    char* gather;
-    char* zbuf;
-    char* gn;
-};
-
-Work carve(tok_ctx* c, const Layout& L) {
-    Work w;
-    char* p = c->arena;
-    for (int i = 0; i < 5; ++i) {
-        w.act[i] = p;
-        p += L.act;
-    }
-    w.gather = p;
-    p += L.gather;
-    w.zbuf = p;
-    p += L.zbuf;
-    w.gn = p;
-    return w;
-}
-
-// ------------------------------------------------------------ executor
-
-int32_t zero_index_of(const tok_ctx* c) {
-    int32_t z = 0, b = 1;
-    for (int i = 0; i < c->arch.nlev; ++i) {
-        z += (c->arch.levels[i] / 2) * b;
-        b *= c->arch.levels[i];
-    }
-    return z;
-}
-
-// Every conv with temporal taps and the bytes of one frame of its input, for
-// one stream of H x W pixels (N = 1). On the BF16 path the stem and the
-// decoder input keep the raw pixels / token indices their gathers read.
-std::vector<std::pair<std::string, size_t>> stream_frames(const tok_ctx* c, int H, int W) {
-    std::vector<std::pair<std::string, size_t>> v;
-    const tok_arch& a = c->arch;
-    const Dims d = clip_dims(c, 1, H, W);
-    const size_t es = c->esize();
-    const size_t pix = c->bf16() ? (size_t)H * W * a.in_ch * 2 : (size_t)d.Hp * d.Wp * a.in_ch * 4;
-    if (a.kind == TOK_ARCH_STAGE) {
-        v.push_back({"stage.c0", pix});
-        v.push_back({"stage.c1", (size_t)d.Hp * d.Wp * a.ch[0] * es});
-        return v;
-    }
-    v.push_back({"enc.stem", pix});
-    for (int l = 0; l < a.nlevels; ++l) {
-        const size_t hw = (size_t)(d.Hp >> (l + 1)) * (d.Wp >> (l + 1));
-        const int cin = l > 0 ? a.ch[l - 1] : a.ch[0];
-        for (int b = 0; b < a.blocks; ++b) {
-            const std::string n = "enc.l" + std::to_string(l) + ".b" + std::to_string(b);
-            v.push_back({n + ".c1", hw * (b == 0 ? cin : a.ch[l]) * es});
-            v.push_back({n + ".c2", hw * a.ch[l] * es});
-        }
-        if (l < a.nlevels - 1) v.push_back({"enc.down" + std::to_string(l), hw * a.ch[l] * es});
-    }
-    const size_t hwq = (size_t)d.Hq * d.Wq;
-    v.push_back({"enc.out", hwq * a.ch[a.nlevels - 1] * es});
-    v.push_back({"dec.in", c->bf16() ? hwq * 4 : hwq * a.nlev * 4});
-    for (int l = a.nlevels - 1; l >= 0; --l) {
-        const size_t hw = (size_t)(d.Hp >> (l + 1)) * (d.Wp >> (l + 1));
-        for (int b = 0; b < a.blocks; ++b) {
-            const std::string n = "dec.l" + std::to_string(l) + ".b" + std::to_string(b);
-            v.push_back({n + ".c1", hw * a.ch[l] * es});
-            v.push_back({n + ".c2", hw * a.ch[l] * es});
-        }
-        if (l > 0) v.push_back({"dec.up" + std::to_string(l - 1), hw * a.ch[l] * es});
-    }
-    v.push_back({"dec.out", (size_t)(d.Hp >> 1) * (d.Wp >> 1) * a.ch[0] * es});
-    return v;
-}
-
-struct Act {
-    void* p;
-    int N, T, H, W, C;
-};
-
-struct Exec {
-    tok_ctx* c;
-    cudaStream_t s;
-    Work w;
-    int err = 0;
-    tok_stream* st = nullptr;  // chunked streaming (null: whole clip)
-    bool chunk0 = true;        // first chunk of a stream: clip-mode causal padding
-
-    // Streaming: a conv with temporal taps reads its left context from the
-    // stream's history; stride-2 convs see chunks that start one frame after
-    // an output frame, hence t_off -1 instead of -2.
-    void stream_args(ConvArgs& a, const std::string& name, int k, int st_t) {
-        if (!st || k != 3 || chunk0) return;
-        a.hist = st->hist[name];
-        a.hist_T = 2;
-        if (st_t == 2) a.t_off = -1;
-    }
-
-    // After a causal conv of a stream: history <- last two frames of [history | chunk].
-    void stream_update(const std::string& name, const void* chunk, int Tc, bool zero_index_fill = false) {
-        if (!st || err) return;
-        auto it = st->hist.find(name);
-        if (it == st->hist.end()) return;
-        char* h = it->second;
-        const size_t fb = st->frame_bytes[name];
-        const char* x = static_cast<const char*>(chunk);
-        auto cp = [&](void* d, const void* src, size_t n) {
-            if (cudaMemcpyAsync(d, src, n, cudaMemcpyDeviceToDevice, s) != cudaSuccess) ck(1);
-        };
-        if (chunk0) {
-            if (c->arch.time_pad == TOK_PAD_REPLICATE) {
-                cp(h, x, fb);
-            } else if (zero_index_fill) {
-                other([&] { return launch_fill_i32(reinterpret_cast<int32_t*>(h), (long long)(fb / 4),
-                                                   zero_index_of(c), s); }, (double)fb);
-            } else if (cudaMemsetAsync(h, 0, fb, s) != cudaSuccess) {
-                ck(1);
-            }
-            cp(h + fb, x + (size_t)(Tc - 1) * fb, fb);
-        } else if (Tc >= 2) {
-            cp(h, x + (size_t)(Tc - 2) * fb, 2 * fb);
-        } else {
-            cp(h, h + fb, fb);
-            cp(h + fb, x, fb);
-        }
-    }
-
-    void ck(int e) {
-        if (e && !err) err = TOK_ECUDA;
-    }
-
-    // profiling: record an event pair around a launch (class 0 conv, 1 GN, 2 other)
-    int pbegin() {
-        if (!c->prof || c->ev_used + 2 > (int)c->events.size()) return -1;
-        const int e = c->ev_used;
-        c->ev_used += 2;
-        cudaEventRecord(c->events[e], s);
-        return e;
-    }
-    void pend(int e, int cls, double work) {
-        if (e < 0) return;
-        cudaEventRecord(c->events[e + 1], s);
-        c->recs.push_back({cls, work, e});
-    }
-
-    ConvArgs base_args(const ConvW& cw, const Act& in, int st, int sh, int sw) {
-        ConvArgs a;
-        memset(&a, 0, sizeof(a));
-        a.x = in.p;
-        a.N = in.N;
-        a.Tin = in.T;
-        a.Hin = in.H;
-        a.Win = in.W;
-        a.Cin = in.C;
-        a.w = cw.w;
-        a.bias = cw.b;
-        a.Cout = cw.Cout;
-        a.Cout_pad = cw.Cout_pad;
-        a.Kpad = cw.Kpad;
-        a.kt = a.kh = a.kw = cw.k;
-        a.st = st;
-        a.sh = sh;
-        a.sw = sw;
-        a.t_off = -(cw.k - 1);
-        a.pad_mode = c->arch.time_pad;
-        a.Tout = (in.T - 1) / st + 1;
-        a.Hout = (in.H + 2 * ((cw.k - 1) / 2) - cw.k) / sh + 1;
-        a.Wout = (in.W + 2 * ((cw.k - 1) / 2) - cw.k) / sw + 1;
-        a.status = c->d_status;
-        a.wait_ns = kWaitNs;
-        a.fsq = c->fsq;
-        return a;
-    }
-
-    void launch(ConvArgs& a, const ConvW& cw) {
-        if (err) return;
-        const double flop = 2.0 * (double)a.N * a.Tout * a.Hout * a.Wout * cw.Cout * (double)(cw.k * cw.k * cw.k) *
-                            cw.Cin;
-        const int e = pbegin();
-        if (c->bf16())
-            ck(launch_conv_tc(a, c->num_sms, s));
-        else
-            ck(launch_conv_simt(a, s));
-        pend(e, 0, flop);
-        c->launches += 1;
-    }
-
-    // Other (bandwidth-bound) kernels: bytes of algorithmic traffic.
-    template <typename F>
-    void other(F&& f, double bytes, int nk = 1) {
-        if (err) return;
-        const int e = pbegin();
-        ck(f());
-        pend(e, 2, bytes);
-        c->launches += nk;
-    }
-
-    // Plain conv (optional residual) into `out`.
-    Act conv(const std::string& name, const Act& in, void* out, const void* residual = nullptr, int tst = 1,
-             int sh = 1, int sw = 1) {
-        const ConvW& cw = c->convs[c->cindex[name]];
-        ConvArgs a = base_args(cw, in, tst, sh, sw);
-        stream_args(a, name, cw.k, tst);
-        a.mode = OUT_PLAIN;
-        a.out = out;
-        a.residual = residual;
-        a.oT = a.Tout;
-        a.oH = a.Hout;
-        a.oW = a.Wout;
-        a.oC = cw.Cout;
-        launch(a, cw);
-        stream_update(name, in.p, in.T);
-        return Act{out, in.N, a.Tout, a.Hout, a.Wout, cw.Cout};
-    }
-
-    // Conv followed by depth-to-space (r = (rt, rh, rw)), cropped to oH x oW.
-    Act conv_d2s(const std::string& name, const Act& in, void* out, int rt, int rh, int rw, int oH, int oW,
-                 bool out_fp32) {
-        const ConvW& cw = c->convs[c->cindex[name]];
-        ConvArgs a = base_args(cw, in, 1, 1, 1);
-        stream_args(a, name, cw.k, 1);
-        a.mode = OUT_D2S;
-        a.out = out;
-        a.out_fp32 = out_fp32 ? 1 : 0;
-        a.rt = rt;
-        a.rh = rh;
-        a.rw = rw;
-        // the causal trim of the first rt-1 frames belongs to the clip's start only
-        a.drop_t = (st && !chunk0) ? 0 : rt - 1;
-        a.oT = a.Tout * rt - a.drop_t;
-        a.oH = oH;
-        a.oW = oW;
-        a.oC = cw.Cout / (rt * rh * rw);
-        launch(a, cw);
-        stream_update(name, in.p, in.T);
-        return Act{out, in.N, a.oT, oH, oW, a.oC};
-    }
-
-    // Conv whose input is first gathered into an im2col matrix (BF16 path):
-    // runs as a 1x1x1 conv over (N, Tout, Hout, Wout, Kpad).
-    Act conv_gathered(const std::string& name, int N, int Tout, int Hout, int Wout, void* out, int mode,
-                      int32_t* idx_out) {
-        const ConvW& cw = c->convs[c->cindex[name]];
-        Act in{w.gather, N, Tout, Hout, Wout, cw.Kpad};
-        ConvArgs a = base_args(cw, in, 1, 1, 1);
-        a.Cin = cw.Kpad;
-        a.kt = a.kh = a.kw = 1;
-        a.t_off = 0;
-        a.mode = mode;
-        a.out = out;
-        a.idx = idx_out;
-        a.oT = Tout;
-        a.oH = Hout;
-        a.oW = Wout;
-        a.oC = cw.Cout;
-        launch(a, cw);
-        return Act{out, N, Tout, Hout, Wout, cw.Cout};
-    }
-
-    Act gn_silu(const std::string& name, const Act& in, void* out) {
-        const GnW& g = c->gns[c->gindex[name]];
-        if (err) return Act{out, in.N, in.T, in.H, in.W, in.C};
-        const long long frames = (long long)in.N * in.T, HW = (long long)in.H * in.W;
-        const int e = pbegin();
-        if (c->bf16())
-            ck(launch_gn_silu<__nv_bfloat16>(static_cast<const __nv_bfloat16*>(in.p), static_cast<__nv_bfloat16*>(out),
-                                             frames, HW, in.C, g.G, g.g, g.b, c->arch.gn_eps, w.gn, c->num_sms, true,
-                                             s));
-        else
-            ck(launch_gn_silu<float>(static_cast<const float*>(in.p), static_cast<float*>(out), frames, HW, in.C, g.G,
-                                     g.g, g.b, c->arch.gn_eps, w.gn, c->num_sms, false, s));
-        pend(e, 1, 2.0 * (double)frames * HW * in.C * c->esize());
-        c->launches += 3;
-        return Act{out, in.N, in.T, in.H, in.W, in.C};
-    }
-
-    // Residual block; X is the stream. Uses act slots: ix (X), and three temps.
-    int block(const std::string& name, int ix, Act& X) {
-        int t[4], k = 0;
-        for (int i = 0; i < 5 && k < 4; ++i)
-            if (i != ix) t[k++] = i;
-        const int iA = t[0], iH = t[1], iS = t[2], iY = t[3];
-        Act A = gn_silu(name + ".gn1", X, w.act[iA]);
-        Act H = conv(name + ".c1", A, w.act[iH]);
-        Act A2 = gn_silu(name + ".gn2", H, w.act[iA]);
-        const void* res = X.p;
-        if (c->cindex.count(name + ".sc")) res = conv(name + ".sc", X, w.act[iS]).p;
-        X = conv(name + ".c2", A2, w.act[iY], res);
-        return iY;
-    }
-
-    int other(int ix) { return ix == 0 ? 1 : 0; }
-
-    // ---------------------------------------------------------------- encode
-    void encode(const void* x, int N, int T, int H, int W, float* z, int32_t* idx) {
-        const tok_arch& ar = c->arch;
-        const Dims d = clip_dims(c, T, H, W);
-        float* zo = z ? z : reinterpret_cast<float*>(w.zbuf);
-        int ix = 0;
-        Act X;
-        if (ar.kind == TOK_ARCH_STAGE) {
-            if (c->bf16()) {
-                GatherGeo g = gather_pixels(N, T, H, W, d.Hp, d.Wp, 1);
-                const __nv_bfloat16* ph = stream_hist_pixels(g, "stage.c0");
-                other([&] { return launch_im2col_pixels(static_cast<const __nv_bfloat16*>(x), ph, g,
-                                                        reinterpret_cast<__nv_bfloat16*>(w.gather), s); },
-                      gather_bytes(g));
-                stream_update("stage.c0", x, T);
-                X = conv_gathered("stage.c0", N, T, d.Hp, d.Wp, w.act[0], OUT_PLAIN, nullptr);
-            } else {
-                Act P = edge_pad_f32(static_cast<const float*>(x), N, T, H, W, d.Hp, d.Wp);
-                X = conv("stage.c0", P, w.act[0]);
-            }
-            Act Y = conv("stage.c1", X, w.act[1], nullptr, 1, 2, 2);
-            Act A = gn_silu("stage.gn", Y, w.act[2]);
-            out_conv("stage.out", A, zo, idx);
-            return;
-        }
-        if (c->bf16()) {
-            GatherGeo g = gather_pixels(N, T, H, W, d.Hp, d.Wp, 2);
-            const __nv_bfloat16* ph = stream_hist_pixels(g, "enc.stem");
-            other([&] { return launch_im2col_pixels(static_cast<const __nv_bfloat16*>(x), ph, g,
-                                                    reinterpret_cast<__nv_bfloat16*>(w.gather), s); },
-                  gather_bytes(g));
-            stream_update("enc.stem", x, T);
-            X = conv_gathered("enc.stem", N, T, d.Hp / 2, d.Wp / 2, w.act[0], OUT_PLAIN, nullptr);
-        } else {
-            Act P = edge_pad_f32(static_cast<const float*>(x), N, T, H, W, d.Hp, d.Wp);
-            X = conv("enc.stem", P, w.act[0], nullptr, 1, 2, 2);
-        }
-        for (int l = 0; l < ar.nlevels; ++l) {
-            for (int b = 0; b < ar.blocks; ++b) ix = block("enc.l" + std::to_string(l) + ".b" + std::to_string(b), ix, X);
-            if (l < ar.nlevels - 1) {
-                const int iy = other(ix);
-                X = conv("enc.down" + std::to_string(l), X, w.act[iy], nullptr, 2, 2, 2);
-                ix = iy;
-            }
-        }
-        const int ia = other(ix);
-        Act A = gn_silu("enc.out_gn", X, w.act[ia]);
-        out_conv("enc.out", A, zo, idx);
-    }
-
-    // Last encoder conv: latent z (fp32) and FSQ token indices.
-    void out_conv(const std::string& name, const Act& A, float* z, int32_t* idx) {
-        const ConvW& cw = c->convs[c->cindex[name]];
-        ConvArgs a = base_args(cw, A, 1, 1, 1);
-        stream_args(a, name, cw.k, 1);
-        a.out = z;
-        a.oT = a.Tout;
-        a.oH = a.Hout;
-        a.oW = a.Wout;
-        a.oC = cw.Cout;
-        const long long ntok = (long long)A.N * a.Tout * a.Hout * a.Wout;
-        if (c->bf16()) {
-            a.mode = OUT_FSQ;
-            a.idx = idx;
-            launch(a, cw);
-        } else {
-            a.mode = OUT_PLAIN;
-            a.out_fp32 = 1;
-            launch(a, cw);
-            if (idx) other([&] { return launch_fsq(z, ntok, c->fsq, idx, nullptr, s); }, (double)ntok * (4 * cw.Cout + 4));
-        }
-        stream_update(name, A.p, A.T);
-    }
-
-    GatherGeo gather_pixels(int N, int T, int H, int W, int Hp, int Wp, int stride_hw) {
-        GatherGeo g;
-        g.N = N;
-        g.Tin = T;
-        g.H = H;
-        g.W = W;
-        g.Hp = Hp;
-        g.Wp = Wp;
-        g.Cin = c->arch.in_ch;
-        g.hist_T = 0;
-        g.Tout = T;
-        g.Hout = Hp / stride_hw;
-        g.Wout = Wp / stride_hw;
-        g.kt = g.kh = g.kw = 3;
-        g.st = 1;
-        g.sh = g.sw = stride_hw;
-        g.t_off = -2;
-        g.pad_mode = c->arch.time_pad;
-        g.Kpad = round_up(27 * g.Cin, 64);
-        return g;
-    }
-
-    const __nv_bfloat16* stream_hist_pixels(GatherGeo& g, const char* name) {
-        if (!st || chunk0) return nullptr;
-        g.hist_T = 2;
-        return reinterpret_cast<const __nv_bfloat16*>(st->hist[name]);
-    }
-
-    static double gather_bytes(const GatherGeo& g) {
-        return (double)g.N * g.Tout * g.Hout * g.Wout * g.Kpad * 2;
-    }
-
-    Act edge_pad_f32(const float* x, int N, int T, int H, int W, int Hp, int Wp) {
-        float* P = reinterpret_cast<float*>(w.gather);
-        if (Hp == H && Wp == W) return Act{const_cast<float*>(x), N, T, H, W, c->arch.in_ch};
-        other([&] { return launch_edge_pad<float>(x, (long long)N * T, H, W, Hp, Wp, c->arch.in_ch, P, s); },
-              (double)N * T * (H * W + Hp * Wp) * c->arch.in_ch * 4);
-        return Act{P, N, T, Hp, Wp, c->arch.in_ch};
-    }
-
-    // ---------------------------------------------------------------- decode
-    void decode(const int32_t* idx, int N, int Tq, int Hq, int Wq, int H, int W, float* xhat) {
-        const tok_arch& ar = c->arch;
-        const int* ch = ar.ch;
-        int ix = 0;
-        Act X;
-        if (c->bf16()) {
-            GatherGeo g;
-            g.N = N;
-            g.Tin = Tq;
-            g.H = g.Hp = Hq;
-            g.W = g.Wp = Wq;
-            g.Cin = ar.nlev;
-            g.hist_T = 0;
-            g.Tout = Tq;
-            g.Hout = Hq;
-            g.Wout = Wq;
-            g.kt = g.kh = g.kw = 3;
-            g.st = g.sh = g.sw = 1;
-            g.t_off = -2;
-            g.pad_mode = ar.time_pad;
-            g.Kpad = round_up(27 * ar.nlev, 64);
-            const int32_t* th = nullptr;
-            if (st && !chunk0) {
-                th = reinterpret_cast<const int32_t*>(st->hist["dec.in"]);
-                g.hist_T = 2;
-            }
-            other([&] { return launch_im2col_tokens(idx, th, g, c->fsq,
-                                                    reinterpret_cast<__nv_bfloat16*>(w.gather), s); },
-                  gather_bytes(g));
-            stream_update("dec.in", idx, Tq, true);
-            X = conv_gathered("dec.in", N, Tq, Hq, Wq, w.act[0], OUT_PLAIN, nullptr);
-        } else {
-            float* codes = reinterpret_cast<float*>(w.zbuf);
-            const long long nt = (long long)N * Tq * Hq * Wq;
-            other([&] { return launch_dequant(idx, nt, c->fsq, codes, s); }, (double)nt * (4 + 4 * ar.nlev));
-            X = conv("dec.in", Act{codes, N, Tq, Hq, Wq, ar.nlev}, w.act[0]);
-        }
-        for (int l = ar.nlevels - 1; l >= 0; --l) {
-            for (int b = 0; b < ar.blocks; ++b) ix = block("dec.l" + std::to_string(l) + ".b" + std::to_string(b), ix, X);
-            if (l > 0) {
-                const int iy = other(ix);
-                X = conv_d2s("dec.up" + std::to_string(l - 1), X, w.act[iy], 2, 2, 2, X.H * 2, X.W * 2, false);
-                ix = iy;
-            }
-        }
-        (void)ch;
-        const int ia = other(ix);
-        Act A = gn_silu("dec.out_gn", X, w.act[ia]);
-        conv_d2s("dec.out", A, xhat, 1, 2, 2, H, W, true);
-    }
-};
-
-// A stream's caches may be advanced by any context with the same architecture
-// and precision (a serving loop runs chunks of one stream on several lanes).
-bool compatible(const tok_ctx* a, const tok_ctx* b) {
-    return a == b || (a && b && a->precision == b->precision && memcmp(&a->arch, &b->arch, sizeof(tok_arch)) == 0);
-}
-
-int check_cuda_device(int* num_sms) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return TOK_EDEVICE;
-    cudaDeviceProp p;
-    if (cudaGetDeviceProperties(&p, dev) != cudaSuccess) return TOK_EDEVICE;
-    *num_sms = p.multiProcessorCount;
-    return (p.major == 10) ? TOK_OK : TOK_EDEVICE;
-}
-
-}  // namespace
+#include "tok_internal.h"
 
 // ======================================================================= C ABI
 
@@ -862,17 +79,20 @@ int tok_create(const tok_arch* arch, int precision, tok_ctx** out) {
     for (auto& g : c->gns) std::fill(c->host[c->pindex[g.name + ".g"]].begin(), c->host[c->pindex[g.name + ".g"]].end(), 1.f);
     bool ok = cudaMalloc(&c->d_status, sizeof(int)) == cudaSuccess;
     if (ok) ok = cudaMemset(c->d_status, 0, sizeof(int)) == cudaSuccess;
+    if (ok) ok = cudaMalloc(&c->d_master, (size_t)c->param_total * 4) == cudaSuccess;
+    for (size_t i = 0; ok && i < c->params.size(); ++i)
+        ok = cudaMemcpy(c->d_master + c->params[i].offset, c->host[i].data(), c->params[i].count * 4,
+                        cudaMemcpyHostToDevice) == cudaSuccess;
     for (auto& cw : c->convs) {
         if (!ok) break;
-        ok = cudaMalloc(&cw.w, (size_t)cw.Cout_pad * cw.Kpad * c->esize()) == cudaSuccess &&
-             cudaMalloc(&cw.b, (size_t)cw.Cout * 4) == cudaSuccess;
+        ok = cudaMalloc(&cw.w, (size_t)cw.Cout_pad * cw.Kpad * c->esize()) == cudaSuccess;
         if (ok) ok = upload_conv(c, cw) == TOK_OK;
     }
     for (auto& g : c->gns) {
         if (!ok) break;
-        ok = cudaMalloc(&g.g, (size_t)g.C * 4) == cudaSuccess && cudaMalloc(&g.b, (size_t)g.C * 4) == cudaSuccess;
-        if (ok) ok = upload_gn(c, g) == TOK_OK;
+        ok = upload_gn(c, g) == TOK_OK;
     }
+    if (ok) ok = cudaDeviceSynchronize() == cudaSuccess;
     if (!ok) {
         tok_destroy(c);
         return TOK_ENOMEM;
@@ -885,12 +105,11 @@ void tok_destroy(tok_ctx* c) {
     if (!c) return;
     for (auto& cw : c->convs) {
         if (cw.w) cudaFree(cw.w);
-        if (cw.b) cudaFree(cw.b);
+        if (cw.wt) cudaFree(cw.wt);
+        if (cw.wc) cudaFree(cw.wc);
     }
-    for (auto& g : c->gns) {
-        if (g.g) cudaFree(g.g);
-        if (g.b) cudaFree(g.b);
-    }
+    if (c->d_master) cudaFree(c->d_master);
+    if (c->tarena) cudaFree(c->tarena);
     if (c->d_status) cudaFree(c->d_status);
     if (c->arena) cudaFree(c->arena);
     for (auto e : c->events) cudaEventDestroy(e);
@@ -916,11 +135,15 @@ int tok_set_param(tok_ctx* c, const char* name, const float* h, int64_t count) {
     const ParamInfo& p = c->params[it->second];
     if (count != p.count) return TOK_ESHAPE;
     std::copy(h, h + count, c->host[it->second].begin());
+    if (cudaMemcpy(c->d_master + p.offset, h, count * 4, cudaMemcpyHostToDevice) != cudaSuccess) return TOK_ECUDA;
+    c->adjoint_dirty = true;
     std::string n(name);
     const std::string layer = n.substr(0, n.rfind('.'));
-    if (c->cindex.count(layer)) return upload_conv(c, c->convs[c->cindex[layer]]);
-    if (c->gindex.count(layer)) return upload_gn(c, c->gns[c->gindex[layer]]);
-    return TOK_EINVAL;
+    int e = TOK_EINVAL;
+    if (c->cindex.count(layer)) e = upload_conv(c, c->convs[c->cindex[layer]]);
+    if (c->gindex.count(layer)) e = upload_gn(c, c->gns[c->gindex[layer]]);
+    if (e == TOK_OK && cudaDeviceSynchronize() != cudaSuccess) e = TOK_ECUDA;
+    return e;
 }
 
 size_t tok_workspace_bytes(const tok_ctx* c, int N, int T, int H, int W) {

@@ -1,0 +1,128 @@
+"""The hand-written backward on the GPU against the FP64 oracle's gradient.
+
+Same weights, same input, same drop mask (Philox, so identical on both
+sides); the oracle runs the rounded (training) forward. Tolerances on the
+relative Frobenius error per parameter tensor:
+  FP32 path: 1e-4 (FP32 accumulation through ~40 convs, forward and backward)
+  BF16 path: 5e-2 (bf16 activations and activation gradients)
+plus the loss itself (FP32: 1e-5 relative; BF16: 2e-2).
+"""
+import numpy as np
+import pytest
+import torch
+
+import synthetic as S
+from oracle import Arch, ops, param_spec
+from oracle.grad import OracleTrain
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_2602_03529_b300 as P
+    P._lib.load()
+    return P
+
+
+def _params(arch, seed):
+    rng = np.random.default_rng(seed)
+    p = S.weights_for(param_spec(arch), seed=seed)
+    for n, shape, kind in param_spec(arch):
+        if kind in ("bias", "gn_beta"):
+            p[n] = (0.1 * rng.standard_normal(shape)).astype(np.float32)
+        elif kind == "gn_gamma":
+            p[n] = (1 + 0.1 * rng.standard_normal(shape)).astype(np.float32)
+    return p
+
+
+def _run(P, prec, ch, shape, rate=0.2, seed=7, step=3, margin_keep=None):
+    from paper_2602_03529_b300.train import Trainer
+    arch = Arch(ch=ch, blocks=1)
+    p = _params(arch, 11)
+    if prec == "bf16":
+        p = {k: S.to_bf16_f32(v) for k, v in p.items()}
+    N, T, H, W = shape
+    x = S.blurred_noise_clip(5, N, T, H, W)
+    if prec == "bf16":
+        x = S.to_bf16_f32(x)
+    tk = P.Tokenizer(prec, ch=ch, blocks=1)
+    tk.set_params(p)
+    tr = Trainer(tk, N, T, H, W)
+    dt = torch.bfloat16 if prec == "bf16" else torch.float32
+    xd = torch.from_numpy(x).to("cuda", dt)
+    Tq, Hq, Wq = tk.latent_shape(T, H, W)
+    o = OracleTrain(arch, p, surrogate=False)
+    kb = None
+    if margin_keep is not None:
+        # keep only tokens whose every channel is at least `margin_keep` away from a
+        # rounding boundary in the oracle, so that both sides quantise them alike
+        _, _, b = o.encode(x)
+        margin = np.abs((b - np.floor(b)) - 0.5).min(axis=-1)
+        dropped = margin < margin_keep
+        kb = torch.from_numpy(ops.keep_bits_from_mask(dropped).view(np.int32)).cuda()
+    else:
+        dropped = ops.drop_mask(N, Tq, Hq, Wq, rate, seed, 0, step)
+    loss = float(tr.forward(xd, rate, seed, step, keep_bits=kb).item())
+    g = tr.backward().cpu().numpy().astype(np.float64)
+    torch.cuda.synchronize()
+    assert tk.status() == 0
+    loss_ref, _, saved = o.forward_train(x, dropped)
+    gref, _ = o.backward(saved)
+    off, rel = 0, {}
+    for name, shp in tk.param_list():
+        n = int(np.prod(shp))
+        gg = g[off:off + n].reshape(shp)
+        off += n
+        ref = gref[name]
+        rel[name] = float(np.linalg.norm(gg - ref) / max(np.linalg.norm(ref), 1e-30))
+    tk.close()
+    return loss, loss_ref, rel
+
+
+def test_fp32_gradient_matches_oracle(P):
+    loss, loss_ref, rel = _run(P, "fp32", (16, 32, 64), (1, 5, 32, 32))
+    worst = max(rel.items(), key=lambda kv: kv[1])
+    print("fp32 loss", loss, loss_ref, "worst", worst)
+    assert abs(loss - loss_ref) <= 1e-5 * abs(loss_ref)
+    assert worst[1] <= 1e-4, worst
+
+
+def test_bf16_gradient_matches_oracle(P):
+    """Tokens near a rounding tie are dropped on both sides (a caller mask), so
+    the BF16 forward quantises every kept token like the FP64 oracle."""
+    loss, loss_ref, rel = _run(P, "bf16", (64, 128, 256), (1, 5, 64, 64), margin_keep=0.12)
+    worst = max(rel.items(), key=lambda kv: kv[1])
+    print("bf16 loss", loss, loss_ref, "worst", worst, "median", float(np.median(list(rel.values()))))
+    assert abs(loss - loss_ref) <= 2e-2 * abs(loss_ref)
+    assert worst[1] <= 5e-2, worst
+
+
+def test_bf16_decoder_gradient_all_dropped(P):
+    """With every token dropped the decoder sees only zero codes on both sides:
+    decoder gradients match, encoder gradients are exactly zero."""
+    loss, loss_ref, rel = _run(P, "bf16", (64, 128, 256), (1, 5, 32, 32), rate=1.0)
+    dec = {k: v for k, v in rel.items() if k.startswith("dec.")}
+    worst = max(dec.items(), key=lambda kv: kv[1])
+    print("bf16 all-dropped loss", loss, loss_ref, "worst decoder", worst)
+    assert abs(loss - loss_ref) <= 2e-2 * abs(loss_ref)
+    assert worst[1] <= 5e-2, worst
+
+
+def test_sgd_reduces_loss_and_autograd_node(P):
+    from paper_2602_03529_b300.train import Trainer, TokenizerLoss
+    tk = P.Tokenizer("bf16", ch=(64, 128, 256), blocks=1)
+    tk.set_params(S.weights_for(tk.param_spec(), seed=3))
+    N, T, H, W = 1, 5, 32, 32
+    tr = Trainer(tk, N, T, H, W)
+    x = torch.from_numpy(S.blurred_noise_clip(9, N, T, H, W)).to("cuda", torch.bfloat16)
+    losses = [float(tr.step(x, 0.0, 1, i, lr=0.05).item()) for i in range(6)]
+    assert losses[-1] < losses[0], losses
+    params = tr.params.clone().requires_grad_(True)
+    loss = TokenizerLoss.apply(params, x, tr, 0.1, 1, 99)
+    loss.backward()
+    g2 = tr.backward().clone()
+    torch.cuda.synchronize()
+    assert torch.equal(params.grad, g2)
+    assert tk.status() == 0
+    tk.close()
