@@ -31,6 +31,9 @@
 
 namespace tok {
 
+bool encode_act_map(CUtensorMap* m, const void* base, int frames, int H, int W, int C, int BH, int BW, bool strided);
+bool encode_w_map(CUtensorMap* m, const void* base, int rows, int Kpad, int BN);
+
 struct TcGeo {
     int BH, BW;              // output tile = BH rows x BW cols of one frame
     int tiles_w, tiles_h;
@@ -388,7 +391,36 @@ __global__ void __launch_bounds__(192, 1)
     if (warp == 1) tmem_dealloc(tmem_base, C::TMEM_COLS);
 }
 
+template <int BN, bool SWAP>
+int launch_bn(const ConvArgs& a, TcGeo g, int num_sms, cudaStream_t stream) {
+    using C = Cfg<BN, SWAP>;
+    CUtensorMap mx, mh, mw;
+    const bool strided = g.strided != 0;
+    if (!encode_act_map(&mx, a.x, a.N * a.Tin, a.Hin, a.Win, a.Cin, g.BH, g.BW, strided)) return -1;
+    if (a.hist) {
+        if (!encode_act_map(&mh, a.hist, a.N * a.hist_T, a.Hin, a.Win, a.Cin, g.BH, g.BW, strided)) return -1;
+    } else {
+        mh = mx;
+    }
+    if (!encode_w_map(&mw, a.w, a.Cout_pad, a.Kpad, BN)) return -1;
+    g.n_tiles = a.Cout_pad / BN;
+    const long long m_tiles = (long long)a.N * a.Tout * g.tiles_h * g.tiles_w;
+    g.num_tiles = m_tiles * g.n_tiles;
+    if (g.num_tiles == 0) return 0;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(conv_tc_kernel<BN, SWAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+        attr_set = true;
+    }
+    const int grid = (int)std::min<long long>(g.num_tiles, num_sms);
+    conv_tc_kernel<BN, SWAP><<<grid, 192, C::SMEM, stream>>>(mx, mh, mw, a, g);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace
+
 // ------------------------------------------------------------------ host side
+// (tensor-map encoders are shared with the tensor-core wgrad kernel)
 
 PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -441,34 +473,6 @@ bool encode_w_map(CUtensorMap* m, const void* base, int rows, int Kpad, int BN) 
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
-
-template <int BN, bool SWAP>
-int launch_bn(const ConvArgs& a, TcGeo g, int num_sms, cudaStream_t stream) {
-    using C = Cfg<BN, SWAP>;
-    CUtensorMap mx, mh, mw;
-    const bool strided = g.strided != 0;
-    if (!encode_act_map(&mx, a.x, a.N * a.Tin, a.Hin, a.Win, a.Cin, g.BH, g.BW, strided)) return -1;
-    if (a.hist) {
-        if (!encode_act_map(&mh, a.hist, a.N * a.hist_T, a.Hin, a.Win, a.Cin, g.BH, g.BW, strided)) return -1;
-    } else {
-        mh = mx;
-    }
-    if (!encode_w_map(&mw, a.w, a.Cout_pad, a.Kpad, BN)) return -1;
-    g.n_tiles = a.Cout_pad / BN;
-    const long long m_tiles = (long long)a.N * a.Tout * g.tiles_h * g.tiles_w;
-    g.num_tiles = m_tiles * g.n_tiles;
-    if (g.num_tiles == 0) return 0;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(conv_tc_kernel<BN, SWAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
-        attr_set = true;
-    }
-    const int grid = (int)std::min<long long>(g.num_tiles, num_sms);
-    conv_tc_kernel<BN, SWAP><<<grid, 192, C::SMEM, stream>>>(mx, mh, mw, a, g);
-    return (int)cudaGetLastError();
-}
-
-}  // namespace
 
 // Choose the output tile shape (BH x BW = 128) that covers Hout x Wout with
 // the fewest tiles; ties go to the wider tile (longer contiguous rows).

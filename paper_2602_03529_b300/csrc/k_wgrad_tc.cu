@@ -1,0 +1,297 @@
+// Weight gradient of a stride-1 causal conv on the tensor cores (BF16 -> FP32).
+//
+//   dW[co][tap][ci] = sum_v dY[v][co] * X[v + off(tap)][ci]
+//
+// GEMM with M = output channels (128 per tile), N = input channels (BN = 128
+// or 256 per tile), K = voxels, one tap per CTA, split-K over voxel tiles
+// (deterministic: every split writes its own FP32 partial, a fixed-order
+// reduction follows). A K step is one tile of 64 output voxels (BH x BW of one
+// frame): TMA loads the dY box {64 channels x 64 voxels} and the tap-shifted X
+// box with the same voxel order. Such a box lands in shared memory as 64
+// rows (voxels = K) of 128 bytes (64 channels = M or N) with 128B swizzle,
+// which is the MN-major canonical layout of tcgen05: rows of 64 MN-contiguous
+// elements, 8-row groups 1024 B apart along K (stride byte offset), and
+// 64-element MN blocks one box apart (leading byte offset). Out-of-frame taps
+// read zeros (TMA out-of-bounds fill); taps before frame 0 read frame 0
+// (replicate) or nothing (zero padding); voxels past the frame edge of a
+// ragged tile read zero dY and so contribute nothing.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "conv_args.h"
+
+namespace tok {
+
+bool encode_act_map(CUtensorMap* m, const void* base, int frames, int H, int W, int C, int BH, int BW, bool strided);
+
+namespace {
+
+constexpr int KV = 64;  // voxels per K step
+
+struct WtcGeo {
+    int BH, BW, tiles_h, tiles_w;
+    long long vtiles;   // voxel tiles (K steps) in total
+    int m_tiles, n_tiles, taps, S;
+};
+
+__device__ __forceinline__ uint64_t mn_sw128_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1u << 46;
+    d |= (uint64_t)2u << 61;
+    return d;
+}
+
+__host__ __device__ constexpr uint32_t idesc_bf16_mn(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+template <int BN>
+struct WCfg {
+    static constexpr int A_BYTES = 2 * KV * 128;          // 128 output channels = two 64-channel boxes
+    static constexpr int B_BYTES = (BN / 64) * KV * 128;  // BN input channels
+    static constexpr int STAGE = A_BYTES + B_BYTES;
+    static constexpr int STAGES = (200 * 1024 / STAGE) > 8 ? 8 : (200 * 1024 / STAGE);
+    static constexpr int TMEM_COLS = BN;
+    static constexpr int SMEM = STAGES * STAGE + 1024 + 256;
+    static constexpr uint32_t IDESC = idesc_bf16_mn(128, BN);
+};
+
+template <int BN>
+__global__ void __launch_bounds__(192, 1)
+    wgrad_tc_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constant__ CUtensorMap tm_x,
+                    const WgradArgs a, const WtcGeo g, float* __restrict__ part, int* status,
+                    unsigned long long wait_ns) {
+    using C = WCfg<BN>;
+    extern __shared__ uint8_t smem_raw[];
+    const uint32_t raw_addr = smem_u32(smem_raw);
+    uint8_t* smem = smem_raw + (((raw_addr + 1023u) & ~1023u) - raw_addr);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE);
+    uint64_t* empty = full + C::STAGES;
+    uint64_t* tdone = empty + C::STAGES;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tdone + 1);
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+
+    // tile: (split, tap, n tile, m tile) with m fastest
+    long long t = blockIdx.x;
+    const int mt = (int)(t % g.m_tiles);
+    t /= g.m_tiles;
+    const int nt = (int)(t % g.n_tiles);
+    t /= g.n_tiles;
+    const int tap = (int)(t % g.taps);
+    const int split = (int)(t / g.taps);
+    const long long v_begin = (long long)split * g.vtiles / g.S, v_end = (long long)(split + 1) * g.vtiles / g.S;
+    const int dw = tap % a.kw, dh = (tap / a.kw) % a.kh, dt = tap / (a.kw * a.kh);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C::STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(tdone, 1);
+        fence_mbar_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, C::TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    bool ok = true;
+
+    if (warp == 0 && lane == 0) {
+        int s = 0;
+        uint32_t ph = 0;
+        int last_ph[8];
+        for (int i = 0; i < 8; ++i) last_ph[i] = -1;
+        for (long long vt = v_begin; vt < v_end; ++vt) {
+            if (!mbar_wait(&empty[s], ph ^ 1, status, wait_ns)) break;
+            long long m = vt;
+            const int tw = (int)(m % g.tiles_w); m /= g.tiles_w;
+            const int th = (int)(m % g.tiles_h); m /= g.tiles_h;
+            const int to = (int)(m % a.Tout);
+            const int n = (int)(m / a.Tout);
+            int ti = to + dt + a.t_off;
+            int tcoord;
+            if (ti >= 0) tcoord = n * a.Tin + ti;
+            else if (a.pad_mode == 0) tcoord = n * a.Tin;
+            else tcoord = -1;
+            uint8_t* sa = smem + s * C::STAGE;
+            uint8_t* sb = sa + C::A_BYTES;
+            mbar_arrive_expect_tx(&full[s], C::STAGE);
+            const int ycoord = n * a.Tout + to;
+            for (int j = 0; j < 2; ++j)
+                tma_load_4d(sa + j * KV * 128, &tm_dy, &full[s], mt * 128 + j * 64, tw * g.BW, th * g.BH, ycoord);
+            for (int j = 0; j < BN / 64; ++j)
+                tma_load_4d(sb + j * KV * 128, &tm_x, &full[s], nt * BN + j * 64, tw * g.BW + dw - (a.kw - 1) / 2,
+                            th * g.BH + dh - (a.kh - 1) / 2, tcoord);
+            last_ph[s] = (int)ph;
+            if (++s == C::STAGES) {
+                s = 0;
+                ph ^= 1;
+            }
+        }
+        for (int i = 0; i < C::STAGES; ++i)
+            if (last_ph[i] >= 0) mbar_wait(&full[i], (uint32_t)last_ph[i], status, wait_ns);
+    } else if (warp == 1 && lane == 0) {
+        int s = 0;
+        uint32_t ph = 0;
+        bool any = false;
+        for (long long vt = v_begin; vt < v_end; ++vt) {
+            if (!mbar_wait(&full[s], ph, status, wait_ns)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const uint32_t sa = smem_u32(smem + s * C::STAGE);
+            const uint32_t sb = sa + C::A_BYTES;
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+                tc_mma_bf16(tmem_base, mn_sw128_desc(sa + k * 2048, KV * 128, 1024),
+                            mn_sw128_desc(sb + k * 2048, KV * 128, 1024), C::IDESC, (any || k) ? 1u : 0u);
+            any = true;
+            tc_commit(&empty[s]);
+            if (++s == C::STAGES) {
+                s = 0;
+                ph ^= 1;
+            }
+        }
+        tc_commit(tdone);
+        if (!any) {
+            // empty split (more splits than voxel tiles): nothing was accumulated
+        }
+        mbar_wait(tdone, 0, status, wait_ns);
+    } else if (warp >= 2) {
+        const int q = warp & 3;
+        int okw = 1;
+        if (lane == 0) okw = mbar_wait(tdone, 0, status, wait_ns) ? 1 : 0;
+        okw = __shfl_sync(0xffffffffu, okw, 0);
+        if (okw) {
+            tc_fence_after();
+            const int co = mt * 128 + q * 32 + lane;
+            float* P = part + ((long long)split * a.Cout + co) * a.K + (long long)tap * a.Cin + nt * BN;
+            const bool empty_range = v_end <= v_begin;
+#pragma unroll 1
+            for (int c16 = 0; c16 < BN / 16; ++c16) {
+                float v[16];
+                tmem_ld16(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(c16 * 16), v);
+                if (co < a.Cout) {
+                    float4* dst = reinterpret_cast<float4*>(P + c16 * 16);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i)
+                        dst[i] = empty_range ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                             : make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                }
+            }
+            tc_fence_before();
+        }
+    }
+    (void)ok;
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) tmem_dealloc(tmem_base, C::TMEM_COLS);
+}
+
+__global__ void colsum_kernel(const __nv_bfloat16* __restrict__ dy, long long V, int Cdy, int Cout, long long vchunk,
+                              float* __restrict__ out) {
+    const int co = blockIdx.x * blockDim.x + threadIdx.x;
+    const int chunk = blockIdx.y;
+    if (co >= Cout) return;
+    const long long v0 = chunk * vchunk, v1 = min(V, v0 + vchunk);
+    float s = 0.f;
+    for (long long v = v0; v < v1; ++v) s += __bfloat162float(dy[v * Cdy + co]);
+    out[(long long)chunk * Cout + co] = s;
+}
+
+__global__ void partial_reduce_kernel(const float* __restrict__ part, int S, long long n, float* __restrict__ out) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    float s = 0.f;
+    for (int i = 0; i < S; ++i) s += part[(long long)i * n + t];
+    out[t] = s;
+}
+
+void choose_vtile(int Hout, int Wout, int* BH, int* BW) {
+    long long best = -1;
+    for (int bw : {64, 32, 16, 8}) {
+        const int bh = KV / bw;
+        const long long tiles = (long long)((Wout + bw - 1) / bw) * ((Hout + bh - 1) / bh);
+        if (best < 0 || tiles < best) {
+            best = tiles;
+            *BW = bw;
+            *BH = bh;
+        }
+    }
+}
+
+template <int BN>
+int launch_bn(const __nv_bfloat16* dy, const __nv_bfloat16* x, const WgradArgs& a, WtcGeo g, float* part,
+              int* status, unsigned long long wait_ns, cudaStream_t s) {
+    using C = WCfg<BN>;
+    CUtensorMap mdy, mx;
+    if (!encode_act_map(&mdy, dy, a.N * a.Tout, a.Hout, a.Wout, a.Cdy, g.BH, g.BW, false)) return -1;
+    if (!encode_act_map(&mx, x, a.N * a.Tin, a.Hin, a.Win, a.Cin, g.BH, g.BW, false)) return -1;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(wgrad_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+        attr = true;
+    }
+    const long long grid = (long long)g.m_tiles * g.n_tiles * g.taps * g.S;
+    wgrad_tc_kernel<BN><<<(unsigned)grid, 192, C::SMEM, s>>>(mdy, mx, a, g, part, status, wait_ns);
+    return (int)cudaGetLastError();
+}
+
+inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+}  // namespace
+
+// Eligible: BF16, stride 1, Cin % 128 == 0, Cout % 128 == 0, dY channel stride a multiple of 64.
+bool wgrad_tc_ok(const WgradArgs& a) {
+    return a.st == 1 && a.sh == 1 && a.sw == 1 && a.Cin % 128 == 0 && a.Cout % 128 == 0 && a.Cdy % 64 == 0 &&
+           a.Cdy >= a.Cout;
+}
+
+// dw (Cout x K) and db (Cout) in FP32; `part` holds the split partials (at
+// most max_floats floats).
+int launch_wgrad_tc(const __nv_bfloat16* dy, const __nv_bfloat16* x, const WgradArgs& a, float* part,
+                    size_t max_floats, float* dw, float* db, int num_sms, int* status, unsigned long long wait_ns,
+                    cudaStream_t s) {
+    WtcGeo g;
+    choose_vtile(a.Hout, a.Wout, &g.BH, &g.BW);
+    g.tiles_w = (a.Wout + g.BW - 1) / g.BW;
+    g.tiles_h = (a.Hout + g.BH - 1) / g.BH;
+    g.vtiles = (long long)a.N * a.Tout * g.tiles_h * g.tiles_w;
+    const int BN = (a.Cin % 256 == 0) ? 256 : 128;
+    g.m_tiles = a.Cout / 128;
+    g.n_tiles = a.Cin / BN;
+    g.taps = a.kt * a.kh * a.kw;
+    const long long out_tiles = (long long)g.m_tiles * g.n_tiles * g.taps;
+    long long S = std::max(1LL, (2LL * num_sms + out_tiles - 1) / out_tiles);
+    S = std::min(S, std::max(1LL, g.vtiles / 4));
+    while (S > 1 && (size_t)S * a.Cout * a.K > max_floats) --S;
+    if ((size_t)S * a.Cout * a.K > max_floats) return -1;
+    g.S = (int)S;
+    int e = (BN == 256) ? launch_bn<256>(dy, x, a, g, part, status, wait_ns, s)
+                        : launch_bn<128>(dy, x, a, g, part, status, wait_ns, s);
+    if (e) return e;
+    const long long n = (long long)a.Cout * a.K;
+    partial_reduce_kernel<<<blocks_for(n, 256), 256, 0, s>>>(part, g.S, n, dw);
+    if (db) {
+        // column sums of dY, reusing the (now consumed) partial buffer
+        const int chunks = (int)std::min<long long>(256, std::max<long long>(1, a.V / 1024));
+        const long long vchunk = (a.V + chunks - 1) / chunks;
+        colsum_kernel<<<dim3((a.Cout + 127) / 128, chunks), 128, 0, s>>>(dy, a.V, a.Cdy, a.Cout, vchunk, part);
+        partial_reduce_kernel<<<blocks_for(a.Cout, 256), 256, 0, s>>>(part, chunks, a.Cout, db);
+    }
+    return (int)cudaGetLastError();
+}
+
+}  // namespace tok

@@ -48,6 +48,12 @@ template <typename T>
 int launch_gn_stats(const T* x, long long frames, long long HW, int C, int G, float eps, void* scratch, int num_sms,
                     cudaStream_t s, float2** stats, int* vpt, int* S);
 
+// tensor-core weight gradient (k_wgrad_tc.cu)
+bool wgrad_tc_ok(const WgradArgs& a);
+int launch_wgrad_tc(const __nv_bfloat16* dy, const __nv_bfloat16* x, const WgradArgs& a, float* part,
+                    size_t max_floats, float* dw, float* db, int num_sms, int* status, unsigned long long wait_ns,
+                    cudaStream_t s);
+
 // backward kernels (k_backward.cu)
 size_t wgrad_partial_floats(int Cout, int K, int S);
 int wgrad_splits(const WgradArgs& a, int num_sms, size_t max_partial_floats);

@@ -246,7 +246,11 @@ struct TrainExec : Exec {
         const int S = wgrad_splits(a, c->num_sms, b.wpart_floats);
         const double flop = 2.0 * (double)a.V * a.Cout * a.K;
         const int e = pbegin();
-        if (c->bf16())
+        if (c->bf16() && wgrad_tc_ok(a))
+            ck(launch_wgrad_tc(static_cast<const __nv_bfloat16*>(dy.p), static_cast<const __nv_bfloat16*>(xin.p), a,
+                               b.wpart, b.wpart_floats, grads + cw.ow, grads + cw.ob, c->num_sms, c->d_status,
+                               kWaitNs, s));
+        else if (c->bf16())
             ck(launch_wgrad<__nv_bfloat16>(static_cast<const __nv_bfloat16*>(dy.p),
                                            static_cast<const __nv_bfloat16*>(xin.p), a, S, b.wpart, grads + cw.ow,
                                            grads + cw.ob, s));
