@@ -240,6 +240,8 @@ def gpu_arm(args):
         "fp32_path": fp32, "speedup_vs_fp32": (value / fp32["value"]) if fp32 else None,
     }
     tk.close()
+    if not args.no_train:
+        out["training"] = training(args, params)
     if not args.no_serve:
         cap = value / world * args.H * args.W * 3.94e6  # algorithmic FLOP/s one GPU sustains
         out["serving"] = serving(args, params, cap, rank, world)
@@ -248,6 +250,46 @@ def gpu_arm(args):
     R.barrier()
     R.finalize()
     return out if rank == 0 else None
+
+
+# ------------------------------------------------------------- training
+
+def training(args, params, N=2, T=17, H=256, W=256, steps=5, warmup=2):
+    """Joint training step (forward with drop + MSE + hand-written backward + SGD) of the
+    default tokenizer on a 2x3x17x256x256 BF16 batch."""
+    import torch
+
+    import paper_2602_03529_b300 as P
+    from paper_2602_03529_b300.train import Trainer
+    import synthetic as S
+
+    tk = P.Tokenizer("bf16")
+    tk.set_params(params)
+    tr = Trainer(tk, N, T, H, W)
+    x = torch.from_numpy(S.blurred_noise_clip(7, N, T, H, W)).to("cuda", torch.bfloat16)
+    for i in range(warmup):
+        tr.step(x, 0.1, 1, i, lr=1e-5)
+    torch.cuda.synchronize()
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+    for i in range(steps):
+        e = ev[i]
+        e[0].record()
+        tr.forward(x, 0.1, 1, 100 + i)
+        e[1].record()
+        tr.backward()
+        e[2].record()
+        tr.sgd(1e-5)
+        e[3].record()
+    torch.cuda.synchronize()
+    assert tk.status() == 0, "device-side error in the training step"
+    fwd = sum(e[0].elapsed_time(e[1]) for e in ev) / steps
+    bwd = sum(e[1].elapsed_time(e[2]) for e in ev) / steps
+    upd = sum(e[2].elapsed_time(e[3]) for e in ev) / steps
+    loss = float(tr.loss.item())
+    tk.close()
+    return {"workload": f"fwd+bwd step, batch {N}x3x{T}x{H}x{W}, BF16, MSE, STE, drop 10%, per-block recompute",
+            "step_ms": fwd + bwd + upd, "fwd_ms": fwd, "bwd_ms": bwd, "sgd_ms": upd, "loss": loss,
+            "steps": steps, "warmup": warmup}
 
 
 # ------------------------------------------------------------- serving
@@ -359,10 +401,11 @@ def main():
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-train", action="store_true")
     ap.add_argument("--serve-streams", type=int, default=64)
     ap.add_argument("--serve-horizon", type=float, default=20.0)
-    ap.add_argument("--serve-chunks", type=int, default=31)
-    ap.add_argument("--serve-lanes", type=int, default=4)
+    ap.add_argument("--serve-chunks", type=int, default=16)
+    ap.add_argument("--serve-lanes", type=int, default=2)
     ap.add_argument("--serve-load", type=float, default=0.6)
     args = ap.parse_args()
     out = reference_arm(args) if args.impl == "reference" else gpu_arm(args)
