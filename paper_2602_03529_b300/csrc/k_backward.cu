@@ -160,7 +160,48 @@ struct V8<__nv_bfloat16> {
     static constexpr int N = 8;
 };
 
-// per (frame, chunk, group): (sum g, sum g*xhat); per (frame*S + chunk, channel): (sum dh*xhat, sum dh)
+template <typename T>
+__device__ __forceinline__ void ldv(const T* p, float (&v)[V8<T>::N]) {
+    if constexpr (sizeof(T) == 2) {
+        const uint4 q = *reinterpret_cast<const uint4*>(p);
+        const uint32_t u[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float2 f = unpack_bf16x2(u[i]);
+            v[2 * i] = f.x;
+            v[2 * i + 1] = f.y;
+        }
+    } else {
+        const float4 q = *reinterpret_cast<const float4*>(p);
+        v[0] = q.x;
+        v[1] = q.y;
+        v[2] = q.z;
+        v[3] = q.w;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ void stv(T* p, const float (&v)[V8<T>::N]) {
+    if constexpr (sizeof(T) == 2) {
+        uint4 q;
+        q.x = pack_bf16x2(v[0], v[1]);
+        q.y = pack_bf16x2(v[2], v[3]);
+        q.z = pack_bf16x2(v[4], v[5]);
+        q.w = pack_bf16x2(v[6], v[7]);
+        *reinterpret_cast<uint4*>(p) = q;
+    } else {
+        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    }
+}
+
+// GN + SiLU backward, with h = xhat * gamma + beta and y = SiLU(h):
+//   dh   = dy * s * (1 + h * (1 - s)),  s = sigmoid(h)
+//   g    = dh * gamma
+//   dx   = rstd * (g - mean_group(g) - xhat * mean_group(g * xhat))
+//   dgamma = sum dh * xhat,  dbeta = sum dh   (over frames and voxels)
+//
+// Pass 1 (per frame and chunk): per group (sum g, sum g*xhat) and per channel
+// (sum dh*xhat, sum dh), combined over the block in a fixed tree order.
 template <typename T>
 __global__ void __launch_bounds__(NT) gn_bwd_reduce_kernel(const T* __restrict__ x, const T* __restrict__ dy,
                                                            const float2* __restrict__ stats,
@@ -189,14 +230,15 @@ __global__ void __launch_bounds__(NT) gn_bwd_reduce_kernel(const T* __restrict__
     for (int i = 0; i < vpt; ++i) {
         const long long vi = v0 + (long long)i * NT + tid;
         if (vi >= vpf) break;
+        float xv[V], gv[V];
+        ldv(x + base + vi * V, xv);
+        ldv(dy + base + vi * V, gv);
 #pragma unroll
         for (int j = 0; j < V; ++j) {
-            const float xv = ldf(x + base + vi * V + j);
-            const float gv = ldf(dy + base + vi * V + j);
-            const float xh = (xv - mu[j]) * rs[j];
+            const float xh = (xv[j] - mu[j]) * rs[j];
             const float h = xh * ga[j] + be[j];
-            const float s = 1.f / (1.f + expf(-h));
-            const float dh = gv * s * (1.f + h * (1.f - s));
+            const float sg1 = 1.f / (1.f + (sizeof(T) == 2 ? __expf(-h) : expf(-h)));
+            const float dh = gv[j] * sg1 * (1.f + h * (1.f - sg1));
             sdx[j] += dh * xh;
             sd[j] += dh;
             const float g = dh * ga[j];
@@ -222,9 +264,7 @@ __global__ void __launch_bounds__(NT) gn_bwd_reduce_kernel(const T* __restrict__
         }
         __syncthreads();
     }
-    // per channel
     for (int c = tid; c < C; c += NT) pc[((long long)frame * S + chunk) * C + c] = redc[c / V][c % V];
-    // per group: the channels of group g are c in [g*cg, (g+1)*cg)
     for (int g = tid; g < G; g += NT) {
         float2 acc = make_float2(0.f, 0.f);
         for (int c = g * cg; c < (g + 1) * cg; ++c) {
@@ -235,34 +275,80 @@ __global__ void __launch_bounds__(NT) gn_bwd_reduce_kernel(const T* __restrict__
     }
 }
 
-__global__ void gn_bwd_finalize_kernel(const float2* __restrict__ pg, int S, int G, float inv_n,
+// Pass 2a: per (frame, group) the chunk sums, one warp each (lanes take
+// chunks lane, lane + 32, ...; a fixed shuffle tree combines them).
+__global__ void gn_bwd_finalize_kernel(const float2* __restrict__ pg, long long frames, int S, int G, float inv_n,
                                        float2* __restrict__ gstat) {
-    const int frame = blockIdx.x;
-    for (int g = threadIdx.x; g < G; g += blockDim.x) {
-        float a = 0.f, b = 0.f;
-        for (int c = 0; c < S; ++c) {
-            const float2 v = pg[((long long)frame * S + c) * G + g];
-            a += v.x;
-            b += v.y;
-        }
-        gstat[(long long)frame * G + g] = make_float2(a * inv_n, b * inv_n);
-    }
-}
-
-__global__ void gn_bwd_channel_kernel(const float2* __restrict__ pc, long long rows, int C, float* __restrict__ dgamma,
-                                      float* __restrict__ dbeta) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= C) return;
+    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int lane = threadIdx.x % 32;
+    if (wid >= frames * G) return;
+    const long long frame = wid / G;
+    const int g = (int)(wid % G);
     float a = 0.f, b = 0.f;
-    for (long long r = 0; r < rows; ++r) {
-        const float2 v = pc[r * C + c];
+    for (int c = lane; c < S; c += 32) {
+        const float2 v = pg[(frame * S + c) * G + g];
         a += v.x;
         b += v.y;
     }
-    if (dgamma) dgamma[c] = a;
-    if (dbeta) dbeta[c] = b;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) gstat[wid] = make_float2(a * inv_n, b * inv_n);
 }
 
+// Pass 2b: per channel over all (frame, chunk) rows, in two steps: blocks of
+// 32 channels x 8 row lanes sum a band of rows into q[band][C], then one warp
+// per channel sums the bands.
+constexpr int GN_BANDS = 128;
+
+__global__ void __launch_bounds__(256) gn_bwd_channel_kernel(const float2* __restrict__ pc, long long rows, int C,
+                                                             float2* __restrict__ q) {
+    __shared__ float2 red[8][32];
+    const int cx = threadIdx.x % 32, ry = threadIdx.x / 32;
+    const int c = blockIdx.x * 32 + cx, band = blockIdx.y;
+    const long long r0 = rows * band / GN_BANDS, r1 = rows * (band + 1) / GN_BANDS;
+    float a = 0.f, b = 0.f;
+    if (c < C)
+        for (long long r = r0 + ry; r < r1; r += 8) {
+            const float2 v = pc[r * C + c];
+            a += v.x;
+            b += v.y;
+        }
+    red[ry][cx] = make_float2(a, b);
+    __syncthreads();
+    if (ry == 0 && c < C) {
+        float2 t = red[0][cx];
+        for (int l = 1; l < 8; ++l) {
+            t.x += red[l][cx].x;
+            t.y += red[l][cx].y;
+        }
+        q[(long long)band * C + c] = t;
+    }
+}
+
+__global__ void gn_bwd_channel_final_kernel(const float2* __restrict__ q, int C, float* __restrict__ dgamma,
+                                            float* __restrict__ dbeta) {
+    const int c = (blockIdx.x * blockDim.x + threadIdx.x) / 32, lane = threadIdx.x % 32;
+    if (c >= C) return;
+    float a = 0.f, b = 0.f;
+    for (int i = lane; i < GN_BANDS; i += 32) {
+        a += q[(long long)i * C + c].x;
+        b += q[(long long)i * C + c].y;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) {
+        if (dgamma) dgamma[c] = a;
+        if (dbeta) dbeta[c] = b;
+    }
+}
+
+// Pass 3: dx (+ add), 16-byte vectors.
 template <typename T>
 __global__ void __launch_bounds__(NT) gn_bwd_apply_kernel(const T* __restrict__ x, const T* __restrict__ dy,
                                                           const float2* __restrict__ stats,
@@ -292,17 +378,21 @@ __global__ void __launch_bounds__(NT) gn_bwd_apply_kernel(const T* __restrict__ 
     for (int i = 0; i < vpt; ++i) {
         const long long vi = v0 + (long long)i * NT + tid;
         if (vi >= vpf) break;
+        const long long o = base + vi * V;
+        float xv[V], gv[V], av[V], r[V];
+        ldv(x + o, xv);
+        ldv(dy + o, gv);
+        if (add) ldv(add + o, av);
 #pragma unroll
         for (int j = 0; j < V; ++j) {
-            const long long o = base + vi * V + j;
-            const float xh = (ldf(x + o) - mu[j]) * rs[j];
+            const float xh = (xv[j] - mu[j]) * rs[j];
             const float h = xh * ga[j] + be[j];
-            const float s = 1.f / (1.f + expf(-h));
-            const float g = ldf(dy + o) * s * (1.f + h * (1.f - s)) * ga[j];
-            float r = rs[j] * (g - m1[j] - xh * m2[j]);
-            if (add) r += ldf(add + o);
-            stf(dx + o, r);
+            const float sg1 = 1.f / (1.f + (sizeof(T) == 2 ? __expf(-h) : expf(-h)));
+            const float g = gv[j] * sg1 * (1.f + h * (1.f - sg1)) * ga[j];
+            r[j] = rs[j] * (g - m1[j] - xh * m2[j]);
+            if (add) r[j] += av[j];
         }
+        stv(dx + o, r);
     }
 }
 
@@ -483,9 +573,12 @@ template int launch_wgrad<float>(const float*, const float*, WgradArgs, int, flo
 template int launch_wgrad<__nv_bfloat16>(const __nv_bfloat16*, const __nv_bfloat16*, WgradArgs, int, float*, float*,
                                          float*, cudaStream_t);
 
-// Scratch layout of the GN backward: pg[frames*S*G], pc[frames*S*C], gstat[frames*G] (float2 each).
+// Scratch layout of the GN backward (float2 each): pg[frames*S*G],
+// pc[frames*S*C], gstat[frames*G], q[GN_BANDS*C]; S = chunks per frame.
 size_t gn_bwd_scratch_bytes(long long frames, int S, int C, int G) {
-    return ((size_t)frames * S * G + (size_t)frames * S * C + (size_t)frames * G) * sizeof(float2) + 256;
+    return ((size_t)frames * S * G + (size_t)frames * S * C + (size_t)frames * G + (size_t)GN_BANDS * C) *
+               sizeof(float2) +
+           256;
 }
 
 // stats: (mean, rstd) per (frame, group) from the forward statistics pass.
@@ -498,10 +591,13 @@ int launch_gn_silu_bwd(const T* x, const T* dy, const float2* stats, const float
     float2* pg = static_cast<float2*>(scratch);
     float2* pc = pg + frames * S * G;
     float2* gstat = pc + frames * S * C;
+    float2* q = gstat + frames * G;
     dim3 grid(S, (unsigned)frames);
     gn_bwd_reduce_kernel<T><<<grid, NT, 0, s>>>(x, dy, stats, gamma, beta, vpf, C, G, S, vpt, pg, pc);
-    gn_bwd_finalize_kernel<<<(unsigned)frames, 64, 0, s>>>(pg, S, G, 1.f / (float)(HW * (C / G)), gstat);
-    gn_bwd_channel_kernel<<<(C + 127) / 128, 128, 0, s>>>(pc, frames * S, C, dgamma, dbeta);
+    gn_bwd_finalize_kernel<<<blocks_for(frames * G * 32, 256), 256, 0, s>>>(pg, frames, S, G,
+                                                                           1.f / (float)(HW * (C / G)), gstat);
+    gn_bwd_channel_kernel<<<dim3((C + 31) / 32, GN_BANDS), 256, 0, s>>>(pc, frames * S, C, q);
+    gn_bwd_channel_final_kernel<<<blocks_for((long long)C * 32, 256), 256, 0, s>>>(q, C, dgamma, dbeta);
     gn_bwd_apply_kernel<T><<<grid, NT, 0, s>>>(x, dy, stats, gstat, gamma, beta, add, vpf, C, G, vpt, dx);
     return (int)cudaGetLastError();
 }

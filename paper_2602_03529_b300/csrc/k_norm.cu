@@ -6,8 +6,8 @@
 //                 the first value it saw (so E[x^2]-E[x]^2 does not cancel),
 //                 then the block merges threads with Chan's pairwise update in
 //                 a fixed tree order (deterministic, no atomics).
-//   gn_finalize : one block per frame merges the chunk triples in chunk order
-//                 into mean and 1/sqrt(var + eps) per group.
+//   gn_finalize : one warp per (frame, group) merges the chunk triples in a
+//                 fixed order into mean and 1/sqrt(var + eps).
 //   gn_apply    : SiLU((x - mean) * rstd * gamma + beta), 16-byte vectors.
 // The causal tokenizer may not mix frames, hence statistics per frame.
 #include "common.cuh"
@@ -135,14 +135,27 @@ __global__ void __launch_bounds__(NT) gn_partial_kernel(const T* __restrict__ x,
     }
 }
 
-__global__ void gn_finalize_kernel(const Triple* __restrict__ part, int S, int G, float eps,
+// One warp per (frame, group): lanes merge chunks lane, lane + 32, ... in
+// chunk order, then a fixed shuffle tree merges the lanes (lane i takes lane
+// i + o), so the statistics are the same on every run.
+__global__ void gn_finalize_kernel(const Triple* __restrict__ part, long long frames, int S, int G, float eps,
                                    float2* __restrict__ stats) {
-    const int frame = blockIdx.x;
-    for (int g = threadIdx.x; g < G; g += blockDim.x) {
-        Triple acc = {0.f, 0.f, 0.f};
-        for (int c = 0; c < S; ++c) acc = merge(acc, part[((long long)frame * S + c) * G + g]);
-        stats[(long long)frame * G + g] = make_float2(acc.mean, rsqrtf(acc.m2 / fmaxf(acc.n, 1.f) + eps));
+    const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    const int lane = threadIdx.x % 32;
+    if (wid >= frames * G) return;
+    const long long frame = wid / G;
+    const int g = (int)(wid % G);
+    Triple acc = {0.f, 0.f, 0.f};
+    for (int c = lane; c < S; c += 32) acc = merge(acc, part[(frame * S + c) * G + g]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        Triple b;
+        b.n = __shfl_down_sync(0xffffffffu, acc.n, o);
+        b.mean = __shfl_down_sync(0xffffffffu, acc.mean, o);
+        b.m2 = __shfl_down_sync(0xffffffffu, acc.m2, o);
+        if (lane + o < 32) acc = merge(acc, b);
     }
+    if (lane == 0) stats[wid] = make_float2(acc.mean, rsqrtf(acc.m2 / fmaxf(acc.n, 1.f) + eps));
 }
 
 template <typename T, bool FAST>
@@ -197,6 +210,12 @@ void gn_plan(long long frames, long long vec_per_frame, int num_sms, int* vpt, i
 
 }  // namespace
 
+int gn_chunks_per_frame(long long HW, int C, int vec) {
+    int vpt, S;
+    gn_plan(1, HW * C / vec, 0, &vpt, &S);
+    return S;
+}
+
 size_t gn_scratch_bytes(long long frames, long long HW, int C, int G, int num_sms, int vec) {
     int vpt, S;
     gn_plan(frames, HW * C / vec, num_sms, &vpt, &S);
@@ -225,7 +244,7 @@ int launch_gn_silu(const T* x, T* y, long long frames, long long HW, int C, int 
         case 4: gn_partial_kernel<T, 4><<<grid, NT, 0, stream>>>(x, vpf, C, G, S, vpt, part); break;
         default: return (int)cudaErrorInvalidValue;
     }
-    gn_finalize_kernel<<<(unsigned)frames, 64, 0, stream>>>(part, S, G, eps, stats);
+    gn_finalize_kernel<<<(unsigned)((frames * G * 32 + 255) / 256), 256, 0, stream>>>(part, frames, S, G, eps, stats);
     if (fast)
         gn_apply_kernel<T, true><<<grid, NT, 0, stream>>>(x, y, vpf, C, G, vpt, stats, gamma, beta);
     else
@@ -252,7 +271,7 @@ int launch_gn_stats(const T* x, long long frames, long long HW, int C, int G, fl
         case 4: gn_partial_kernel<T, 4><<<grid, NT, 0, stream>>>(x, vpf, C, G, S, vpt, part); break;
         default: return (int)cudaErrorInvalidValue;
     }
-    gn_finalize_kernel<<<(unsigned)frames, 64, 0, stream>>>(part, S, G, eps, stats);
+    gn_finalize_kernel<<<(unsigned)((frames * G * 32 + 255) / 256), 256, 0, stream>>>(part, frames, S, G, eps, stats);
     *stats_out = stats;
     *vpt_out = vpt;
     *S_out = S;

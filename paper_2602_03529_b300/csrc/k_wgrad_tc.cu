@@ -1,4 +1,4 @@
-// Weight gradient of a stride-1 causal conv on the tensor cores (BF16 -> FP32).
+// Weight gradient of a causal conv on the tensor cores (BF16 -> FP32).
 //
 //   dW[co][tap][ci] = sum_v dY[v][co] * X[v + off(tap)][ci]
 //
@@ -15,6 +15,14 @@
 // read zeros (TMA out-of-bounds fill); taps before frame 0 read frame 0
 // (replicate) or nothing (zero padding); voxels past the frame edge of a
 // ragged tile read zero dY and so contribute nothing.
+//
+// Stride-2 convs (h and w) read X through the parity view
+// (2C, W/2, 2, H/2, frames) that the forward conv uses: input column
+// 2w + dw - 1 is parity (dw + 1) % 2 at half-column w - (dw == 0), so a tap
+// is again one box per 64 channels. Output channels past Cout (a narrow
+// layer such as the 12-channel pixel head) and input channels past Cin (an
+// im2col matrix of 192 columns) are neither loaded nor stored: row m of the
+// product depends on row m of A only, column n on column n of B only.
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -34,6 +42,7 @@ struct WtcGeo {
     int BH, BW, tiles_h, tiles_w;
     long long vtiles;   // voxel tiles (K steps) in total
     int m_tiles, n_tiles, taps, S;
+    int strided;        // X read through the parity view (stride 2 in h and w)
 };
 
 __device__ __forceinline__ uint64_t mn_sw128_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
@@ -87,6 +96,9 @@ __global__ void __launch_bounds__(192, 1)
     const int split = (int)(t / g.taps);
     const long long v_begin = (long long)split * g.vtiles / g.S, v_end = (long long)(split + 1) * g.vtiles / g.S;
     const int dw = tap % a.kw, dh = (tap / a.kw) % a.kh, dt = tap / (a.kw * a.kh);
+    const int a_boxes = (mt * 128 + 64 < a.Cout) ? 2 : 1;
+    const int b_boxes = min(BN / 64, (a.Cin - nt * BN) / 64);
+    const uint32_t tx_bytes = (uint32_t)(a_boxes + b_boxes) * KV * 128;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::STAGES; ++s) {
@@ -111,27 +123,49 @@ __global__ void __launch_bounds__(192, 1)
         uint32_t ph = 0;
         int last_ph[8];
         for (int i = 0; i < 8; ++i) last_ph[i] = -1;
+        // voxel tile vt = ((n * Tout + to) * tiles_h + th) * tiles_w + tw, decoded once and then stepped
+        int tw, th, to, n;
+        {
+            long long m = v_begin;
+            tw = (int)(m % g.tiles_w); m /= g.tiles_w;
+            th = (int)(m % g.tiles_h); m /= g.tiles_h;
+            to = (int)(m % a.Tout);
+            n = (int)(m / a.Tout);
+        }
         for (long long vt = v_begin; vt < v_end; ++vt) {
+            if (vt != v_begin && ++tw == g.tiles_w) {
+                tw = 0;
+                if (++th == g.tiles_h) {
+                    th = 0;
+                    if (++to == a.Tout) {
+                        to = 0;
+                        ++n;
+                    }
+                }
+            }
             if (!mbar_wait(&empty[s], ph ^ 1, status, wait_ns)) break;
-            long long m = vt;
-            const int tw = (int)(m % g.tiles_w); m /= g.tiles_w;
-            const int th = (int)(m % g.tiles_h); m /= g.tiles_h;
-            const int to = (int)(m % a.Tout);
-            const int n = (int)(m / a.Tout);
-            int ti = to + dt + a.t_off;
+            int ti = to * a.st + dt + a.t_off;
             int tcoord;
-            if (ti >= 0) tcoord = n * a.Tin + ti;
+            if (ti >= a.Tin) tcoord = -1;
+            else if (ti >= 0) tcoord = n * a.Tin + ti;
             else if (a.pad_mode == 0) tcoord = n * a.Tin;
             else tcoord = -1;
             uint8_t* sa = smem + s * C::STAGE;
             uint8_t* sb = sa + C::A_BYTES;
-            mbar_arrive_expect_tx(&full[s], C::STAGE);
+            mbar_arrive_expect_tx(&full[s], tx_bytes);
             const int ycoord = n * a.Tout + to;
-            for (int j = 0; j < 2; ++j)
+            for (int j = 0; j < a_boxes; ++j)
                 tma_load_4d(sa + j * KV * 128, &tm_dy, &full[s], mt * 128 + j * 64, tw * g.BW, th * g.BH, ycoord);
-            for (int j = 0; j < BN / 64; ++j)
-                tma_load_4d(sb + j * KV * 128, &tm_x, &full[s], nt * BN + j * 64, tw * g.BW + dw - (a.kw - 1) / 2,
-                            th * g.BH + dh - (a.kh - 1) / 2, tcoord);
+            if (!g.strided) {
+                for (int j = 0; j < b_boxes; ++j)
+                    tma_load_4d(sb + j * KV * 128, &tm_x, &full[s], nt * BN + j * 64,
+                                tw * g.BW + dw - (a.kw - 1) / 2, th * g.BH + dh - (a.kh - 1) / 2, tcoord);
+            } else {
+                const int pw = (dw == 1) ? 0 : 1, ph = (dh == 1) ? 0 : 1;
+                for (int j = 0; j < b_boxes; ++j)
+                    tma_load_5d(sb + j * KV * 128, &tm_x, &full[s], pw * a.Cin + nt * BN + j * 64,
+                                tw * g.BW - (dw == 0 ? 1 : 0), ph, th * g.BH - (dh == 0 ? 1 : 0), tcoord);
+            }
             last_ph[s] = (int)ph;
             if (++s == C::STAGES) {
                 s = 0;
@@ -182,7 +216,7 @@ __global__ void __launch_bounds__(192, 1)
             for (int c16 = 0; c16 < BN / 16; ++c16) {
                 float v[16];
                 tmem_ld16(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(c16 * 16), v);
-                if (co < a.Cout) {
+                if (co < a.Cout && nt * BN + c16 * 16 < a.Cin) {
                     float4* dst = reinterpret_cast<float4*>(P + c16 * 16);
 #pragma unroll
                     for (int i = 0; i < 4; ++i)
@@ -200,15 +234,54 @@ __global__ void __launch_bounds__(192, 1)
     if (warp == 1) tmem_dealloc(tmem_base, C::TMEM_COLS);
 }
 
-__global__ void colsum_kernel(const __nv_bfloat16* __restrict__ dy, long long V, int Cdy, int Cout, long long vchunk,
-                              float* __restrict__ out) {
-    const int co = blockIdx.x * blockDim.x + threadIdx.x;
+// Column sums of dY (V rows of Cdy channels, the first Cout summed) into
+// per-chunk partials out[chunk][Cout]. A block covers CGT groups of 8
+// channels (16-byte loads) and 256 / CGT voxel lanes; lanes are combined in
+// a fixed order, so the result does not depend on scheduling.
+__global__ void __launch_bounds__(256) colsum_kernel(const __nv_bfloat16* __restrict__ dy, long long V, int Cdy,
+                                                     int Cout, long long vchunk, float* __restrict__ out) {
+    __shared__ float red[256 * 8];
+    const int CG = (Cout + 7) / 8, CGT = min(CG, 32), lanes = 256 / CGT;
+    const int tx = threadIdx.x % CGT, ty = threadIdx.x / CGT;
+    const int cg = blockIdx.x * CGT + tx;
     const int chunk = blockIdx.y;
-    if (co >= Cout) return;
     const long long v0 = chunk * vchunk, v1 = min(V, v0 + vchunk);
+    float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (ty < lanes && cg < CG) {
+        for (long long v = v0 + ty; v < v1; v += lanes) {
+            const uint4 q = *reinterpret_cast<const uint4*>(dy + v * Cdy + cg * 8);
+            const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&q);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float2 f = __bfloat1622float2(h[i]);
+                acc[2 * i] += f.x;
+                acc[2 * i + 1] += f.y;
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) red[threadIdx.x * 8 + i] = acc[i];
+    __syncthreads();
+    if (ty == 0 && cg < CG) {
+        float t[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int l = 0; l < lanes; ++l)
+#pragma unroll
+            for (int i = 0; i < 8; ++i) t[i] += red[(l * CGT + tx) * 8 + i];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            if (cg * 8 + i < Cout) out[(long long)chunk * Cout + cg * 8 + i] = t[i];
+    }
+}
+
+// db[co] = sum over chunks of part[chunk][co]; one warp per column, fixed order.
+__global__ void colsum_reduce_kernel(const float* __restrict__ part, int chunks, int Cout, float* __restrict__ db) {
+    const int co = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32, lane = threadIdx.x % 32;
+    if (co >= Cout) return;
     float s = 0.f;
-    for (long long v = v0; v < v1; ++v) s += __bfloat162float(dy[v * Cdy + co]);
-    out[(long long)chunk * Cout + co] = s;
+    for (int i = lane; i < chunks; i += 32) s += part[(long long)i * Cout + co];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) db[co] = s;
 }
 
 __global__ void partial_reduce_kernel(const float* __restrict__ part, int S, long long n, float* __restrict__ out) {
@@ -216,6 +289,17 @@ __global__ void partial_reduce_kernel(const float* __restrict__ part, int S, lon
     if (t >= n) return;
     float s = 0.f;
     for (int i = 0; i < S; ++i) s += part[(long long)i * n + t];
+    out[t] = s;
+}
+
+// Same, keeping the first kv of every K columns (an im2col layer whose K is padded).
+__global__ void partial_reduce_crop_kernel(const float* __restrict__ part, int S, int rows, int K, int kv,
+                                           float* __restrict__ out) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)rows * kv) return;
+    const long long r = t / kv, k = t % kv, n = (long long)rows * K;
+    float s = 0.f;
+    for (int i = 0; i < S; ++i) s += part[(long long)i * n + r * K + k];
     out[t] = s;
 }
 
@@ -238,7 +322,7 @@ int launch_bn(const __nv_bfloat16* dy, const __nv_bfloat16* x, const WgradArgs& 
     using C = WCfg<BN>;
     CUtensorMap mdy, mx;
     if (!encode_act_map(&mdy, dy, a.N * a.Tout, a.Hout, a.Wout, a.Cdy, g.BH, g.BW, false)) return -1;
-    if (!encode_act_map(&mx, x, a.N * a.Tin, a.Hin, a.Win, a.Cin, g.BH, g.BW, false)) return -1;
+    if (!encode_act_map(&mx, x, a.N * a.Tin, a.Hin, a.Win, a.Cin, g.BH, g.BW, g.strided != 0)) return -1;
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(wgrad_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
@@ -253,43 +337,67 @@ inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1)
 
 }  // namespace
 
-// Eligible: BF16, stride 1, Cin % 128 == 0, Cout % 128 == 0, dY channel stride a multiple of 64.
+// Eligible: BF16; Cin a multiple of 64; dY channel stride a multiple of 64
+// holding all Cout channels; stride 1 or 2 in time; stride 1 in h and w, or 2
+// with a 3x3 spatial kernel over an even input frame.
 bool wgrad_tc_ok(const WgradArgs& a) {
-    return a.st == 1 && a.sh == 1 && a.sw == 1 && a.Cin % 128 == 0 && a.Cout % 128 == 0 && a.Cdy % 64 == 0 &&
+    const bool hw_ok = (a.sh == 1 && a.sw == 1) ||
+                       (a.sh == 2 && a.sw == 2 && a.kh == 3 && a.kw == 3 && a.Hin % 2 == 0 && a.Win % 2 == 0 &&
+                        a.Hout == a.Hin / 2 && a.Wout == a.Win / 2);
+    return (a.st == 1 || a.st == 2) && hw_ok && a.Cin % 64 == 0 && a.Cin > 0 && a.Cout > 0 && a.Cdy % 64 == 0 &&
            a.Cdy >= a.Cout;
 }
 
-// dw (Cout x K) and db (Cout) in FP32; `part` holds the split partials (at
-// most max_floats floats).
+// dw (Cout x K, or Cout x k_valid when 0 < k_valid < K) and db (Cout) in
+// FP32; `part` holds the split partials (at most max_floats floats).
 int launch_wgrad_tc(const __nv_bfloat16* dy, const __nv_bfloat16* x, const WgradArgs& a, float* part,
                     size_t max_floats, float* dw, float* db, int num_sms, int* status, unsigned long long wait_ns,
-                    cudaStream_t s) {
+                    cudaStream_t s, int k_valid) {
     WtcGeo g;
+    g.strided = (a.sh == 2) ? 1 : 0;
     choose_vtile(a.Hout, a.Wout, &g.BH, &g.BW);
     g.tiles_w = (a.Wout + g.BW - 1) / g.BW;
     g.tiles_h = (a.Hout + g.BH - 1) / g.BH;
     g.vtiles = (long long)a.N * a.Tout * g.tiles_h * g.tiles_w;
     const int BN = (a.Cin % 256 == 0) ? 256 : 128;
-    g.m_tiles = a.Cout / 128;
-    g.n_tiles = a.Cin / BN;
+    g.m_tiles = (a.Cout + 127) / 128;
+    g.n_tiles = (a.Cin + BN - 1) / BN;
     g.taps = a.kt * a.kh * a.kw;
     const long long out_tiles = (long long)g.m_tiles * g.n_tiles * g.taps;
-    long long S = std::max(1LL, (2LL * num_sms + out_tiles - 1) / out_tiles);
-    S = std::min(S, std::max(1LL, g.vtiles / 4));
-    while (S > 1 && (size_t)S * a.Cout * a.K > max_floats) --S;
+    // split count: at least 4 voxel tiles per split, partials within max_floats,
+    // and the grid (one CTA per SM) filling its last wave as fully as possible
+    const long long s_max = std::max(1LL, std::min(g.vtiles / 4, (long long)(max_floats / ((size_t)a.Cout * a.K))));
+    const long long s_cap = std::min(s_max, std::max(1LL, (4LL * num_sms + out_tiles - 1) / out_tiles));
+    long long S = 1;
+    double best = -1.0;
+    for (long long sc = 1; sc <= s_cap; ++sc) {
+        const long long ctas = out_tiles * sc, waves = (ctas + num_sms - 1) / num_sms;
+        // time ~ waves / sc (work per CTA shrinks with sc); small bonus for fewer partials
+        const double score = (double)sc / (double)waves - 1e-3 * (double)sc;
+        if (score > best) {
+            best = score;
+            S = sc;
+        }
+    }
     if ((size_t)S * a.Cout * a.K > max_floats) return -1;
     g.S = (int)S;
     int e = (BN == 256) ? launch_bn<256>(dy, x, a, g, part, status, wait_ns, s)
                         : launch_bn<128>(dy, x, a, g, part, status, wait_ns, s);
     if (e) return e;
     const long long n = (long long)a.Cout * a.K;
-    partial_reduce_kernel<<<blocks_for(n, 256), 256, 0, s>>>(part, g.S, n, dw);
+    if (k_valid > 0 && k_valid < a.K)
+        partial_reduce_crop_kernel<<<blocks_for((long long)a.Cout * k_valid, 256), 256, 0, s>>>(part, g.S, a.Cout,
+                                                                                               a.K, k_valid, dw);
+    else
+        partial_reduce_kernel<<<blocks_for(n, 256), 256, 0, s>>>(part, g.S, n, dw);
     if (db) {
         // column sums of dY, reusing the (now consumed) partial buffer
-        const int chunks = (int)std::min<long long>(256, std::max<long long>(1, a.V / 1024));
+        const int cgt = std::min((a.Cout + 7) / 8, 32);
+        const int gx = ((a.Cout + 7) / 8 + cgt - 1) / cgt;
+        const int chunks = (int)std::max<long long>(1, std::min<long long>(4LL * num_sms / gx, a.V / 256));
         const long long vchunk = (a.V + chunks - 1) / chunks;
-        colsum_kernel<<<dim3((a.Cout + 127) / 128, chunks), 128, 0, s>>>(dy, a.V, a.Cdy, a.Cout, vchunk, part);
-        partial_reduce_kernel<<<blocks_for(a.Cout, 256), 256, 0, s>>>(part, chunks, a.Cout, db);
+        colsum_kernel<<<dim3(gx, chunks), 256, 0, s>>>(dy, a.V, a.Cdy, a.Cout, vchunk, part);
+        colsum_reduce_kernel<<<(a.Cout + 7) / 8, 256, 0, s>>>(part, chunks, a.Cout, db);
     }
     return (int)cudaGetLastError();
 }

@@ -52,7 +52,7 @@ int launch_gn_stats(const T* x, long long frames, long long HW, int C, int G, fl
 bool wgrad_tc_ok(const WgradArgs& a);
 int launch_wgrad_tc(const __nv_bfloat16* dy, const __nv_bfloat16* x, const WgradArgs& a, float* part,
                     size_t max_floats, float* dw, float* db, int num_sms, int* status, unsigned long long wait_ns,
-                    cudaStream_t s);
+                    cudaStream_t s, int k_valid = 0);
 
 // backward kernels (k_backward.cu)
 size_t wgrad_partial_floats(int Cout, int K, int S);
@@ -60,6 +60,7 @@ int wgrad_splits(const WgradArgs& a, int num_sms, size_t max_partial_floats);
 template <typename T>
 int launch_wgrad(const T* dy, const T* x, WgradArgs a, int S, float* part, float* dw, float* db, cudaStream_t s);
 size_t gn_bwd_scratch_bytes(long long frames, int S, int C, int G);
+int gn_chunks_per_frame(long long HW, int C, int vec);  // k_norm.cu
 template <typename T>
 int launch_gn_silu_bwd(const T* x, const T* dy, const float2* stats, const float* gamma, const float* beta,
                        const T* add, long long frames, long long HW, int C, int G, int vpt, int S, void* scratch,

@@ -78,7 +78,12 @@ TrainBufs train_layout(const tok_ctx* c, int N, int T, int H, int W, char* base)
         const int G = std::max(1, std::min(a.gn_groups, a.ch[l] / 2));
         gn = std::max(gn, gn_scratch_bytes((long long)N * Tl[l], (long long)(H >> (l + 1)) * (W >> (l + 1)),
                                            a.ch[l], G, c->num_sms, c->bf16() ? 8 : 4));
-        gn = std::max(gn, gn_bwd_scratch_bytes((long long)N * Tl[l], 64, std::max(a.ch[l], cin0), G));
+        {
+            const long long hw = (long long)(H >> (l + 1)) * (W >> (l + 1));
+            const int cmax = std::max(a.ch[l], cin0), vec = c->bf16() ? 8 : 4;
+            const int smax = std::max(gn_chunks_per_frame(hw, a.ch[l], vec), gn_chunks_per_frame(hw, cin0, vec));
+            gn = std::max(gn, gn_bwd_scratch_bytes((long long)N * Tl[l], smax, cmax, std::max(a.gn_groups, 1)));
+        }
         if (l > 0) {
             const int G2 = std::max(1, std::min(a.gn_groups, cin0 / 2));
             gn = std::max(gn, gn_scratch_bytes((long long)N * Tl[l], (long long)(H >> (l + 1)) * (W >> (l + 1)),
@@ -176,21 +181,7 @@ struct TrainExec : Exec {
             other([&] { return launch_codes<__nv_bfloat16>(b.idx_d, ntok, c->fsq,
                                                            reinterpret_cast<__nv_bfloat16*>(b.codes), s); },
                   (double)ntok * (4 + 2 * ar.nlev));
-            GatherGeo g;
-            g.N = N;
-            g.Tin = Tq;
-            g.H = g.Hp = Hq;
-            g.W = g.Wp = Wq;
-            g.Cin = ar.nlev;
-            g.hist_T = 0;
-            g.Tout = Tq;
-            g.Hout = Hq;
-            g.Wout = Wq;
-            g.kt = g.kh = g.kw = 3;
-            g.st = g.sh = g.sw = 1;
-            g.t_off = -2;
-            g.pad_mode = ar.time_pad;
-            g.Kpad = round_up(27 * ar.nlev, 64);
+            const GatherGeo g = dec_in_geo(N, Tq, Hq, Wq);
             other([&] { return launch_im2col_tokens(b.idx_d, nullptr, g, c->fsq,
                                                     reinterpret_cast<__nv_bfloat16*>(w.gather), s); },
                   gather_bytes(g));
@@ -219,7 +210,63 @@ struct TrainExec : Exec {
                   (double)n * 12, 2);
     }
 
+    // im2col geometry of the decoder input conv (3x3x3 over the token codes)
+    GatherGeo dec_in_geo(int N, int Tq, int Hq, int Wq) const {
+        GatherGeo g;
+        memset(&g, 0, sizeof(g));
+        g.N = N;
+        g.Tin = Tq;
+        g.H = g.Hp = Hq;
+        g.W = g.Wp = Wq;
+        g.Cin = c->arch.nlev;
+        g.hist_T = 0;
+        g.Tout = Tq;
+        g.Hout = Hq;
+        g.Wout = Wq;
+        g.kt = g.kh = g.kw = 3;
+        g.st = g.sh = g.sw = 1;
+        g.t_off = -2;
+        g.pad_mode = c->arch.time_pad;
+        g.Kpad = round_up(27 * c->arch.nlev, 64);
+        return g;
+    }
+
     // ------------------------------------------------------------ backward
+
+    // Weight gradient of a layer whose forward ran on an im2col matrix (BF16
+    // stem and decoder input): the same matrix is rebuilt in the gather
+    // buffer and the gradient is that of a 1x1x1 conv over its Kpad columns,
+    // of which the first 27 * Cin are the weights.
+    void wgrad_gathered(const std::string& name, const Act& dy, int Cdy, int Kpad) {
+        if (err) return;
+        const ConvW& cw = c->convs[c->cindex[name]];
+        WgradArgs a;
+        memset(&a, 0, sizeof(a));
+        a.N = dy.N;
+        a.Tin = a.Tout = dy.T;
+        a.Hin = a.Hout = dy.H;
+        a.Win = a.Wout = dy.W;
+        a.Cin = Kpad;
+        a.Cout = cw.Cout;
+        a.Cdy = Cdy;
+        a.kt = a.kh = a.kw = 1;
+        a.st = a.sh = a.sw = 1;
+        a.t_off = 0;
+        a.pad_mode = c->arch.time_pad;
+        a.K = Kpad;
+        a.V = (long long)dy.N * dy.T * dy.H * dy.W;
+        const int kv = cw.k * cw.k * cw.k * cw.Cin;
+        if (!wgrad_tc_ok(a) || kv > Kpad) {
+            ck(TOK_ESHAPE);
+            return;
+        }
+        const int e = pbegin();
+        ck(launch_wgrad_tc(static_cast<const __nv_bfloat16*>(dy.p), reinterpret_cast<const __nv_bfloat16*>(w.gather),
+                           a, b.wpart, b.wpart_floats, grads + cw.ow, grads + cw.ob, c->num_sms, c->d_status, kWaitNs,
+                           s, kv));
+        pend(e, 0, 2.0 * (double)a.V * a.Cout * kv);
+        c->launches += 4;
+    }
 
     void wgrad(const std::string& name, const Act& dy, int Cdy, const Act& xin, int tst, int ss) {
         if (err) return;
@@ -246,7 +293,8 @@ struct TrainExec : Exec {
         const int S = wgrad_splits(a, c->num_sms, b.wpart_floats);
         const double flop = 2.0 * (double)a.V * a.Cout * a.K;
         const int e = pbegin();
-        if (c->bf16() && wgrad_tc_ok(a))
+        const bool tc = c->bf16() && wgrad_tc_ok(a);
+        if (tc)
             ck(launch_wgrad_tc(static_cast<const __nv_bfloat16*>(dy.p), static_cast<const __nv_bfloat16*>(xin.p), a,
                                b.wpart, b.wpart_floats, grads + cw.ow, grads + cw.ob, c->num_sms, c->d_status,
                                kWaitNs, s));
@@ -258,7 +306,7 @@ struct TrainExec : Exec {
             ck(launch_wgrad<float>(static_cast<const float*>(dy.p), static_cast<const float*>(xin.p), a, S, b.wpart,
                                    grads + cw.ow, grads + cw.ob, s));
         pend(e, 0, flop);
-        c->launches += 2;
+        c->launches += tc ? 4 : 2;
     }
 
     // Input gradient of a stride-1 conv: the adjoint conv over dY (cpad
@@ -417,7 +465,15 @@ struct TrainExec : Exec {
         const int Tq = Tl[L - 1], Hq = H >> L, Wq = W >> L;
         const long long ntok = (long long)N * Tq * Hq * Wq;
         Act codes{b.codes, N, Tq, Hq, Wq, ar.nlev};
-        wgrad("dec.in", G, G.C, codes, 1, 1);
+        if (c->bf16()) {
+            const GatherGeo g = dec_in_geo(N, Tq, Hq, Wq);
+            other([&] { return launch_im2col_tokens(b.idx_d, nullptr, g, c->fsq,
+                                                    reinterpret_cast<__nv_bfloat16*>(w.gather), s); },
+                  gather_bytes(g));
+            wgrad_gathered("dec.in", G, G.C, g.Kpad);
+        } else {
+            wgrad("dec.in", G, G.C, codes, 1, 1);
+        }
         const ConvW& di = c->convs[c->cindex["dec.in"]];
         dgrad("dec.in", G, b.dcodes);
         // straight-through FSQ and the drop mask
@@ -467,7 +523,15 @@ struct TrainExec : Exec {
         }
         // stem (stride (1,2,2)) from the pixels
         Act xin{const_cast<void*>(c->train_x), N, T, H, W, ar.in_ch};
-        wgrad("enc.stem", G, G.C, xin, 1, 2);
+        if (c->bf16()) {
+            const GatherGeo g = gather_pixels(N, T, H, W, H, W, 2);
+            other([&] { return launch_im2col_pixels(static_cast<const __nv_bfloat16*>(xin.p), nullptr, g,
+                                                    reinterpret_cast<__nv_bfloat16*>(w.gather), s); },
+                  gather_bytes(g));
+            wgrad_gathered("enc.stem", G, G.C, g.Kpad);
+        } else {
+            wgrad("enc.stem", G, G.C, xin, 1, 2);
+        }
     }
 };
 

@@ -94,9 +94,14 @@ def test_bf16_gradient_matches_oracle(P):
     loss, loss_ref, rel = _run(P, "bf16", (64, 128, 256), (1, 5, 64, 64), margin_keep=0.12, blocks=2)
     worst = max(rel.items(), key=lambda kv: kv[1])
     print("bf16 loss", loss, loss_ref, "worst", worst, "median", float(np.median(list(rel.values()))))
-    # weights whose gradient the tensor-core wgrad computes (Cin, Cout multiples of 128, stride 1)
-    tc = ["enc.l1.b1.c1.w", "enc.l2.b0.c2.w", "enc.l2.b0.sc.w", "dec.l2.b0.c1.w", "dec.up1.w", "dec.up0.w"]
-    print("tensor-core wgrad tensors", {k: round(rel[k], 5) for k in tc if k in rel})
+    # every BF16 weight gradient runs on the tensor cores; these are the layer kinds
+    # with their own operand handling: im2col (stem, dec.in), stride 2 (down),
+    # narrow output (enc.out, dec.out), 64 input channels
+    kinds = ["enc.stem.w", "enc.down0.w", "enc.down1.w", "enc.out.w", "dec.in.w", "dec.out.w",
+             "enc.l0.b0.c1.w", "dec.up0.w"]
+    print("per-kind weight gradient error", {k: round(rel[k], 5) for k in kinds if k in rel})
+    for k in kinds:
+        assert rel[k] <= 5e-2, (k, rel[k])
     assert abs(loss - loss_ref) <= 2e-2 * abs(loss_ref)
     assert worst[1] <= 5e-2, worst
 
