@@ -132,6 +132,40 @@ int tok_encode(tok_ctx* ctx, const void* d_x, int N, int T, int H, int W,
 int tok_decode(tok_ctx* ctx, const int32_t* d_idx, int N, int Tq, int Hq, int Wq,
                int H, int W, float* d_xhat, tok_stream* s, void* stream);
 
+/* Grouped encode / decode (one launch per layer over several inputs).
+ * A batch holds 1 .. TOK_MAX_BATCH items of any sizes: whole clips, chunks of
+ * streams (each stream at most once per batch), or both. Every convolution
+ * of a layer runs as one tensor-core launch over all items, every
+ * GroupNorm+SiLU as one grouped pass; tiles never span items, so each
+ * item's result is the one its own tok_encode / tok_decode call gives.
+ * Item fields mean what the arguments of tok_encode / tok_decode mean; the
+ * workspace is the sum of the items' workspaces, laid out item after item
+ * (tok_reserve_batch; a stream chunk counts as N = 1, T = s_T). Errors: the
+ * first argument error of any item, before anything is launched; TOK_ENOMEM
+ * if the reserved workspace is too small. Not in the paper: a serving and
+ * throughput device for mixed-resolution inputs. */
+#define TOK_MAX_BATCH 8
+typedef struct tok_shape {
+    int N, T, H, W;
+} tok_shape;
+typedef struct tok_enc_item {
+    const void* d_x;
+    int N, T, H, W;
+    float* d_z;      /* or NULL */
+    int32_t* d_idx;  /* or NULL */
+    tok_stream* s;   /* NULL: a whole clip */
+} tok_enc_item;
+typedef struct tok_dec_item {
+    const int32_t* d_idx;
+    int N, Tq, Hq, Wq, H, W;
+    float* d_xhat;
+    tok_stream* s;   /* NULL: a whole clip */
+} tok_dec_item;
+size_t tok_batch_workspace_bytes(const tok_ctx* ctx, const tok_shape* h_shapes, int count);
+int tok_reserve_batch(tok_ctx* ctx, const tok_shape* h_shapes, int count);
+int tok_encode_batch(tok_ctx* ctx, const tok_enc_item* h_items, int count, void* stream);
+int tok_decode_batch(tok_ctx* ctx, const tok_dec_item* h_items, int count, void* stream);
+
 /* Stand-alone FSQ (Mentzer et al. 2023): per token of nlev channels,
  * b = tanh(z + atanh(o/h))*h - o with h = (L-1)(1-1e-3)/2, o = 0.5 for even
  * L else 0; q = round-half-even(b); idx = sum (q + L/2) * prod_{j<i} L_j;

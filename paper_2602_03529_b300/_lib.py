@@ -42,6 +42,23 @@ class tok_profile_stats(C.Structure):
     ]
 
 
+TOK_MAX_BATCH = 8
+
+
+class tok_shape(C.Structure):
+    _fields_ = [("N", C.c_int), ("T", C.c_int), ("H", C.c_int), ("W", C.c_int)]
+
+
+class tok_enc_item(C.Structure):
+    _fields_ = [("d_x", C.c_void_p), ("N", C.c_int), ("T", C.c_int), ("H", C.c_int), ("W", C.c_int),
+                ("d_z", C.c_void_p), ("d_idx", C.c_void_p), ("s", C.c_void_p)]
+
+
+class tok_dec_item(C.Structure):
+    _fields_ = [("d_idx", C.c_void_p), ("N", C.c_int), ("Tq", C.c_int), ("Hq", C.c_int), ("Wq", C.c_int),
+                ("H", C.c_int), ("W", C.c_int), ("d_xhat", C.c_void_p), ("s", C.c_void_p)]
+
+
 class TokError(RuntimeError):
     def __init__(self, code: int, what: str):
         super().__init__(f"{what}: {tok_strerror(code)} (code {code})")
@@ -63,6 +80,10 @@ _SIGS = {
     "tok_latent_shape": (i32, [vp, i32, i32, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
     "tok_encode": (i32, [vp, vp, i32, i32, i32, i32, vp, vp, vp, vp]),
     "tok_decode": (i32, [vp, vp, i32, i32, i32, i32, i32, i32, vp, vp, vp]),
+    "tok_batch_workspace_bytes": (sz, [vp, C.POINTER(tok_shape), i32]),
+    "tok_reserve_batch": (i32, [vp, C.POINTER(tok_shape), i32]),
+    "tok_encode_batch": (i32, [vp, C.POINTER(tok_enc_item), i32, vp]),
+    "tok_decode_batch": (i32, [vp, C.POINTER(tok_dec_item), i32, vp]),
     "tok_quantize": (i32, [vp, i64, vp, i32, vp, vp, vp]),
     "tok_dequantize": (i32, [vp, i64, vp, i32, vp, vp]),
     "tok_zero_index": (i32, [vp, i32]),
@@ -185,6 +206,38 @@ def tok_encode(ctx, x_ptr, N, T, H, W, z_ptr, idx_ptr, stream_handle, cuda_strea
 def tok_decode(ctx, idx_ptr, N, Tq, Hq, Wq, H, W, xhat_ptr, stream_handle, cuda_stream) -> None:
     _ck(_call("tok_decode", ctx, idx_ptr, N, Tq, Hq, Wq, H, W, xhat_ptr, stream_handle, cuda_stream),
         "tok_decode")
+
+
+def _shapes(shapes):
+    arr = (tok_shape * len(shapes))()
+    for i, (N, T, H, W) in enumerate(shapes):
+        arr[i] = tok_shape(N, T, H, W)
+    return arr
+
+
+def tok_batch_workspace_bytes(ctx, shapes) -> int:
+    """shapes: list of (N, T, H, W)."""
+    return int(_call("tok_batch_workspace_bytes", ctx, _shapes(shapes), len(shapes)))
+
+
+def tok_reserve_batch(ctx, shapes) -> None:
+    _ck(_call("tok_reserve_batch", ctx, _shapes(shapes), len(shapes)), "tok_reserve_batch")
+
+
+def tok_encode_batch(ctx, items, cuda_stream) -> None:
+    """items: list of (x_ptr, N, T, H, W, z_ptr, idx_ptr, stream_handle)."""
+    arr = (tok_enc_item * len(items))()
+    for i, it in enumerate(items):
+        arr[i] = tok_enc_item(*it)
+    _ck(_call("tok_encode_batch", ctx, arr, len(items), cuda_stream), "tok_encode_batch")
+
+
+def tok_decode_batch(ctx, items, cuda_stream) -> None:
+    """items: list of (idx_ptr, N, Tq, Hq, Wq, H, W, xhat_ptr, stream_handle)."""
+    arr = (tok_dec_item * len(items))()
+    for i, it in enumerate(items):
+        arr[i] = tok_dec_item(*it)
+    _ck(_call("tok_decode_batch", ctx, arr, len(items), cuda_stream), "tok_decode_batch")
 
 
 def tok_quantize(z_ptr, ntok, levels, idx_ptr, codes_ptr, cuda_stream) -> None:

@@ -23,6 +23,9 @@ namespace tok {
 
 enum OutMode { OUT_PLAIN = 0, OUT_D2S = 1, OUT_FSQ = 2 };
 
+// Most inputs one grouped conv launch takes (clips or stream chunks of one layer).
+constexpr int kMaxConvGroup = 8;
+
 struct FsqConsts {
     int nlev;
     int levels[8];     // L_i

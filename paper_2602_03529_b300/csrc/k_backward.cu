@@ -21,6 +21,7 @@
 #include "conv_args.h"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace tok {
 
@@ -180,6 +181,34 @@ __device__ __forceinline__ void ldv(const T* p, float (&v)[V8<T>::N]) {
     }
 }
 
+// Raw 16-byte vectors, loaded ahead of use and unpacked when consumed.
+template <typename T>
+struct Raw {
+    using type = typename std::conditional<sizeof(T) == 2, uint4, float4>::type;
+};
+template <typename T>
+__device__ __forceinline__ typename Raw<T>::type ldraw(const T* p) {
+    return *reinterpret_cast<const typename Raw<T>::type*>(p);
+}
+template <typename T>
+__device__ __forceinline__ void unpack(const typename Raw<T>::type& q, float (&v)[V8<T>::N]) {
+    if constexpr (sizeof(T) == 2) {
+        const uint32_t u[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const float2 f = unpack_bf16x2(u[i]);
+            v[2 * i] = f.x;
+            v[2 * i + 1] = f.y;
+        }
+    } else {
+        v[0] = q.x;
+        v[1] = q.y;
+        v[2] = q.z;
+        v[3] = q.w;
+    }
+}
+constexpr int GN_PREFETCH = 4;  // vectors of x and dy in flight per thread
+
 template <typename T>
 __device__ __forceinline__ void stv(T* p, const float (&v)[V8<T>::N]) {
     if constexpr (sizeof(T) == 2) {
@@ -210,8 +239,9 @@ __global__ void __launch_bounds__(NT) gn_bwd_reduce_kernel(const T* __restrict__
                                                            int G, int S, int vpt, float2* __restrict__ pg,
                                                            float2* __restrict__ pc) {
     constexpr int V = V8<T>::N;
-    __shared__ float2 redc[NT][V];
-    __shared__ float2 redg[NT][V];
+    // [channel slot][thread]: consecutive threads hit consecutive banks
+    __shared__ float2 redc[V][NT];
+    __shared__ float2 redg[V][NT];
     const int frame = blockIdx.y, chunk = blockIdx.x, tid = threadIdx.x;
     const int vpv = C / V, cg = C / G;
     const int c0 = (tid % vpv) * V;
@@ -227,17 +257,28 @@ __global__ void __launch_bounds__(NT) gn_bwd_reduce_kernel(const T* __restrict__
     float sdx[V] = {}, sd[V] = {}, sg[V] = {}, sgx[V] = {};
     const long long base = (long long)frame * vpf * V;
     const long long v0 = (long long)chunk * NT * vpt;
-    for (int i = 0; i < vpt; ++i) {
-        const long long vi = v0 + (long long)i * NT + tid;
-        if (vi >= vpf) break;
+    for (int i0 = 0; i0 < vpt; i0 += GN_PREFETCH) {
+        typename Raw<T>::type rx[GN_PREFETCH], rg[GN_PREFETCH];
+#pragma unroll
+        for (int u = 0; u < GN_PREFETCH; ++u) {
+            const long long vi = v0 + (long long)(i0 + u) * NT + tid;
+            if (i0 + u < vpt && vi < vpf) {
+                rx[u] = ldraw(x + base + vi * V);
+                rg[u] = ldraw(dy + base + vi * V);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < GN_PREFETCH; ++u) {
+        const long long vi = v0 + (long long)(i0 + u) * NT + tid;
+        if (i0 + u >= vpt || vi >= vpf) break;
         float xv[V], gv[V];
-        ldv(x + base + vi * V, xv);
-        ldv(dy + base + vi * V, gv);
+        unpack<T>(rx[u], xv);
+        unpack<T>(rg[u], gv);
 #pragma unroll
         for (int j = 0; j < V; ++j) {
             const float xh = (xv[j] - mu[j]) * rs[j];
             const float h = xh * ga[j] + be[j];
-            const float sg1 = 1.f / (1.f + (sizeof(T) == 2 ? __expf(-h) : expf(-h)));
+            const float sg1 = sizeof(T) == 2 ? __fdividef(1.f, 1.f + __expf(-h)) : 1.f / (1.f + expf(-h));
             const float dh = gv[j] * sg1 * (1.f + h * (1.f - sg1));
             sdx[j] += dh * xh;
             sd[j] += dh;
@@ -245,31 +286,32 @@ __global__ void __launch_bounds__(NT) gn_bwd_reduce_kernel(const T* __restrict__
             sg[j] += g;
             sgx[j] += g * xh;
         }
+        }
     }
 #pragma unroll
     for (int j = 0; j < V; ++j) {
-        redc[tid][j] = make_float2(sdx[j], sd[j]);
-        redg[tid][j] = make_float2(sg[j], sgx[j]);
+        redc[j][tid] = make_float2(sdx[j], sd[j]);
+        redg[j][tid] = make_float2(sg[j], sgx[j]);
     }
     __syncthreads();
     for (int stride = NT / 2; stride >= vpv; stride >>= 1) {
         if (tid < stride) {
 #pragma unroll
             for (int j = 0; j < V; ++j) {
-                redc[tid][j].x += redc[tid + stride][j].x;
-                redc[tid][j].y += redc[tid + stride][j].y;
-                redg[tid][j].x += redg[tid + stride][j].x;
-                redg[tid][j].y += redg[tid + stride][j].y;
+                redc[j][tid].x += redc[j][tid + stride].x;
+                redc[j][tid].y += redc[j][tid + stride].y;
+                redg[j][tid].x += redg[j][tid + stride].x;
+                redg[j][tid].y += redg[j][tid + stride].y;
             }
         }
         __syncthreads();
     }
-    for (int c = tid; c < C; c += NT) pc[((long long)frame * S + chunk) * C + c] = redc[c / V][c % V];
+    for (int c = tid; c < C; c += NT) pc[((long long)frame * S + chunk) * C + c] = redc[c % V][c / V];
     for (int g = tid; g < G; g += NT) {
         float2 acc = make_float2(0.f, 0.f);
         for (int c = g * cg; c < (g + 1) * cg; ++c) {
-            acc.x += redg[c / V][c % V].x;
-            acc.y += redg[c / V][c % V].y;
+            acc.x += redg[c % V][c / V].x;
+            acc.y += redg[c % V][c / V].y;
         }
         pg[((long long)frame * S + chunk) * G + g] = acc;
     }
@@ -375,24 +417,36 @@ __global__ void __launch_bounds__(NT) gn_bwd_apply_kernel(const T* __restrict__ 
     }
     const long long base = (long long)frame * vpf * V;
     const long long v0 = (long long)chunk * NT * vpt;
-    for (int i = 0; i < vpt; ++i) {
-        const long long vi = v0 + (long long)i * NT + tid;
-        if (vi >= vpf) break;
+    for (int i0 = 0; i0 < vpt; i0 += GN_PREFETCH) {
+        typename Raw<T>::type rx[GN_PREFETCH], rg[GN_PREFETCH];
+#pragma unroll
+        for (int u = 0; u < GN_PREFETCH; ++u) {
+            const long long vi = v0 + (long long)(i0 + u) * NT + tid;
+            if (i0 + u < vpt && vi < vpf) {
+                rx[u] = ldraw(x + base + vi * V);
+                rg[u] = ldraw(dy + base + vi * V);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < GN_PREFETCH; ++u) {
+        const long long vi = v0 + (long long)(i0 + u) * NT + tid;
+        if (i0 + u >= vpt || vi >= vpf) break;
         const long long o = base + vi * V;
         float xv[V], gv[V], av[V], r[V];
-        ldv(x + o, xv);
-        ldv(dy + o, gv);
+        unpack<T>(rx[u], xv);
+        unpack<T>(rg[u], gv);
         if (add) ldv(add + o, av);
 #pragma unroll
         for (int j = 0; j < V; ++j) {
             const float xh = (xv[j] - mu[j]) * rs[j];
             const float h = xh * ga[j] + be[j];
-            const float sg1 = 1.f / (1.f + (sizeof(T) == 2 ? __expf(-h) : expf(-h)));
+            const float sg1 = sizeof(T) == 2 ? __fdividef(1.f, 1.f + __expf(-h)) : 1.f / (1.f + expf(-h));
             const float g = gv[j] * sg1 * (1.f + h * (1.f - sg1)) * ga[j];
             r[j] = rs[j] * (g - m1[j] - xh * m2[j]);
             if (add) r[j] += av[j];
         }
         stv(dx + o, r);
+        }
     }
 }
 
@@ -515,28 +569,31 @@ __global__ void mse_final_kernel(const float* __restrict__ part, int nb, float i
 // two temporal taps d'' with V[0] = W[dt=0] + W[dt=1], V[1] = W[dt=0], both
 // spatially flipped.
 template <typename T>
-__global__ void pack_adjoint_kernel(const float* __restrict__ w, int Cout, int Cin, int k, int rows_pad, int cpad,
-                                    int corr, T* __restrict__ out) {
+__global__ void __launch_bounds__(256) pack_adjoint_kernel(const float* __restrict__ w, int Cout, int Cin, int k,
+                                                           int rows_pad, int cpad, int corr, T* __restrict__ out) {
+    // one output tap, 32 input channels (rows) x 32 output channels (columns),
+    // transposed through shared memory so reads run along ci and writes along co
+    __shared__ float tile[32][33];
     const int taps_out = corr ? 2 * k * k : k * k * k;
-    const long long total = (long long)rows_pad * taps_out * cpad;
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= total) return;
-    const int co = (int)(t % cpad);
-    const int tap = (int)((t / cpad) % taps_out);
-    const int ci = (int)(t / ((long long)cpad * taps_out));
-    float v = 0.f;
-    if (ci < Cin && co < Cout) {
-        const int k2 = k * k;
-        const int dwp = tap % k, dhp = (tap / k) % k, dtp = tap / k2;
-        const int dh = k - 1 - dhp, dw = k - 1 - dwp;
-        auto W = [&](int dt) { return w[(((long long)co * k + dt) * k2 + dh * k + dw) * Cin + ci]; };
-        if (!corr) {
-            v = W(k - 1 - dtp);
-        } else {
-            v = (dtp == 0) ? W(0) + W(1) : W(0);
-        }
+    const int tap = blockIdx.z, co0 = blockIdx.x * 32, ci0 = blockIdx.y * 32;
+    const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+    const int k2 = k * k;
+    const int dwp = tap % k, dhp = (tap / k) % k, dtp = tap / k2;
+    const int dh = k - 1 - dhp, dw = k - 1 - dwp;
+    auto W = [&](int co, int dt, int ci) { return w[(((long long)co * k + dt) * k2 + dh * k + dw) * Cin + ci]; };
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int co = co0 + ty + 8 * i, ci = ci0 + tx;
+        float v = 0.f;
+        if (co < Cout && ci < Cin) v = !corr ? W(co, k - 1 - dtp, ci) : (dtp == 0 ? W(co, 0, ci) + W(co, 1, ci) : W(co, 0, ci));
+        tile[ty + 8 * i][tx] = v;
     }
-    stf(out + t, v);
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int ci = ci0 + ty + 8 * i, co = co0 + tx;
+        if (ci < rows_pad && co < cpad) stf(out + ((long long)ci * taps_out + tap) * cpad + co, tile[tx][ty + 8 * i]);
+    }
 }
 
 __global__ void sgd_kernel(float* __restrict__ p, const float* __restrict__ g, long long n, float lr) {
@@ -673,8 +730,8 @@ template <typename T>
 int launch_pack_adjoint(const float* w, int Cout, int Cin, int k, int rows_pad, int cpad, int corr, T* out,
                         cudaStream_t s) {
     const int taps_out = corr ? 2 * k * k : k * k * k;
-    const long long n = (long long)rows_pad * taps_out * cpad;
-    pack_adjoint_kernel<T><<<blocks_for(n, 256), 256, 0, s>>>(w, Cout, Cin, k, rows_pad, cpad, corr, out);
+    dim3 grid((cpad + 31) / 32, (rows_pad + 31) / 32, taps_out);
+    pack_adjoint_kernel<T><<<grid, 256, 0, s>>>(w, Cout, Cin, k, rows_pad, cpad, corr, out);
     return (int)cudaGetLastError();
 }
 template int launch_pack_adjoint<float>(const float*, int, int, int, int, int, int, float*, cudaStream_t);

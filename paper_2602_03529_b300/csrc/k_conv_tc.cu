@@ -44,6 +44,22 @@ struct TcGeo {
     int strided;             // parity view (sh = sw = 2)
 };
 
+// A grouped launch: up to MAXP inputs of one layer (clips or stream chunks of
+// different sizes), one weight tensor. Tiles are numbered problem after
+// problem (tile_end holds the running totals) and a tile never spans two
+// problems; the persistent CTAs stride over all of them.
+template <int MAXP>
+struct TcBatch {
+    CUtensorMap tm_w;
+    CUtensorMap tm_x[MAXP];
+    CUtensorMap tm_h[MAXP];
+    ConvArgs a[MAXP];
+    TcGeo g[MAXP];
+    long long tile_end[MAXP];
+    long long num_tiles;
+    int count;
+};
+
 namespace {
 
 // Two operand arrangements of the same implicit GEMM:
@@ -114,11 +130,21 @@ __device__ __forceinline__ void add_bf16x16(const __nv_bfloat16* src, float (&v)
     }
 }
 
-template <int BN, bool SWAP>
-__global__ void __launch_bounds__(192, 1)
-    conv_tc_kernel(const __grid_constant__ CUtensorMap tm_x, const __grid_constant__ CUtensorMap tm_h,
-                   const __grid_constant__ CUtensorMap tm_w, const ConvArgs a, const TcGeo g) {
+// Problem of a global tile index and the tile's index within that problem.
+template <int MAXP>
+__device__ __forceinline__ int problem_of(const TcBatch<MAXP>& B, long long tile, long long* local) {
+    int p = 0;
+    if constexpr (MAXP > 1)
+        while (p + 1 < B.count && tile >= B.tile_end[p]) ++p;
+    *local = p ? tile - B.tile_end[p - 1] : tile;
+    return p;
+}
+
+template <int BN, bool SWAP, int MAXP>
+__global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__ TcBatch<MAXP> B) {
     using C = Cfg<BN, SWAP>;
+    int* const status = B.a[0].status;
+    const unsigned long long wait_ns = B.a[0].wait_ns;
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_addr = smem_u32(smem_raw);
     uint8_t* smem = smem_raw + (((raw_addr + 1023u) & ~1023u) - raw_addr);
@@ -132,7 +158,7 @@ __global__ void __launch_bounds__(192, 1)
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     // A context already in error skips the launch (decided once per CTA).
     __shared__ int s_skip;
-    if (threadIdx.x == 0) s_skip = (a.status && *(volatile int*)a.status != 0) ? 1 : 0;
+    if (threadIdx.x == 0) s_skip = (status && *(volatile int*)status != 0) ? 1 : 0;
     __syncthreads();
     if (s_skip) return;
 
@@ -147,10 +173,10 @@ __global__ void __launch_bounds__(192, 1)
         }
         fence_mbar_init();
     }
-    if (warp == 0 && lane == 0) {
-        tma_prefetch_desc(&tm_x);
-        tma_prefetch_desc(&tm_h);
-        tma_prefetch_desc(&tm_w);
+    if (warp == 0 && lane < B.count) {
+        tma_prefetch_desc(&B.tm_x[lane]);
+        if (B.a[lane].hist) tma_prefetch_desc(&B.tm_h[lane]);
+        if (lane == 0) tma_prefetch_desc(&B.tm_w);
     }
     if (warp == 1) {
         tmem_alloc(tmem_slot, C::TMEM_COLS);
@@ -170,25 +196,29 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
             for (int i = 0; i < 8; ++i) last_ph[i] = -1;
             bool ok = true;
-            const int ph_ = (a.kh - 1) / 2, pw_ = (a.kw - 1) / 2;
-            for (long long tile = blockIdx.x; tile < g.num_tiles && ok; tile += gridDim.x) {
-                const TileCoord tc = decode_tile(a, g, tile);
+            for (long long tile = blockIdx.x; tile < B.num_tiles && ok; tile += gridDim.x) {
+                long long lt;
+                const int p = problem_of(B, tile, &lt);
+                const ConvArgs& a = B.a[p];
+                const TcGeo& g = B.g[p];
+                const int ph_ = (a.kh - 1) / 2, pw_ = (a.kw - 1) / 2;
+                const TileCoord tc = decode_tile(a, g, lt);
                 for (int kb = 0; kb < g.nkb; ++kb) {
-                    if (!mbar_wait(&empty[s], ph ^ 1, a.status, a.wait_ns)) {
+                    if (!mbar_wait(&empty[s], ph ^ 1, status, wait_ns)) {
                         ok = false;
                         break;
                     }
                     const int tap = kb / g.cpt, cb = kb - tap * g.cpt;
                     const int dw = tap % a.kw, dh = (tap / a.kw) % a.kh, dt = tap / (a.kw * a.kh);
                     const int ti = tc.to * a.st + dt + a.t_off;
-                    const CUtensorMap* src = &tm_x;
+                    const CUtensorMap* src = &B.tm_x[p];
                     int tcoord;
                     if (ti >= a.Tin) {
                         tcoord = -1;  // past the last frame (adjoint convs read ahead): zeros
                     } else if (ti >= 0) {
                         tcoord = tc.n * a.Tin + ti;
                     } else if (a.hist) {
-                        src = &tm_h;
+                        src = &B.tm_h[p];
                         tcoord = tc.n * a.hist_T + a.hist_T + ti;
                     } else if (a.pad_mode == 0) {
                         tcoord = tc.n * a.Tin;
@@ -206,7 +236,7 @@ __global__ void __launch_bounds__(192, 1)
                         tma_load_5d(sa, src, &full[s], pwp * a.Cin + cb * 64, tc.tw * g.BW + (dw == 0 ? -1 : 0), php,
                                     tc.th * g.BH + (dh == 0 ? -1 : 0), tcoord);
                     }
-                    tma_load_2d(sb, &tm_w, &full[s], tap * a.Cin + cb * 64, tc.nt * BN);
+                    tma_load_2d(sb, &B.tm_w, &full[s], tap * a.Cin + cb * 64, tc.nt * BN);
                     last_ph[s] = (int)ph;
                     if (++s == C::STAGES) {
                         s = 0;
@@ -216,7 +246,7 @@ __global__ void __launch_bounds__(192, 1)
             }
             // make sure no copy is still in flight before the CTA may exit
             for (int i = 0; i < C::STAGES; ++i)
-                if (last_ph[i] >= 0) mbar_wait(&full[i], (uint32_t)last_ph[i], a.status, a.wait_ns);
+                if (last_ph[i] >= 0) mbar_wait(&full[i], (uint32_t)last_ph[i], status, wait_ns);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -226,14 +256,16 @@ __global__ void __launch_bounds__(192, 1)
             int last_acc_ph[2] = {-1, -1};
             bool ok = true;
             int it = 0;
-            for (long long tile = blockIdx.x; tile < g.num_tiles && ok; tile += gridDim.x, ++it) {
+            for (long long tile = blockIdx.x; tile < B.num_tiles && ok; tile += gridDim.x, ++it) {
+                long long lt;
+                const int nkb = B.g[problem_of(B, tile, &lt)].nkb;
                 const int acc = it & 1;
                 const uint32_t aph = (uint32_t)((it >> 1) & 1);
-                if (!mbar_wait(&tempty[acc], aph ^ 1, a.status, a.wait_ns)) break;
+                if (!mbar_wait(&tempty[acc], aph ^ 1, status, wait_ns)) break;
                 tc_fence_after();
                 const uint32_t d = tmem_base + (uint32_t)(acc * C::ACC_COLS);
-                for (int kb = 0; kb < g.nkb; ++kb) {
-                    if (!mbar_wait(&full[s], ph, a.status, a.wait_ns)) {
+                for (int kb = 0; kb < nkb; ++kb) {
+                    if (!mbar_wait(&full[s], ph, status, wait_ns)) {
                         ok = false;
                         break;
                     }
@@ -256,22 +288,26 @@ __global__ void __launch_bounds__(192, 1)
             }
             // wait for our own MMAs before TMEM can be released
             for (int i = 0; i < 2; ++i)
-                if (last_acc_ph[i] >= 0) mbar_wait(&tfull[i], (uint32_t)last_acc_ph[i], a.status, a.wait_ns);
+                if (last_acc_ph[i] >= 0) mbar_wait(&tfull[i], (uint32_t)last_acc_ph[i], status, wait_ns);
         }
     } else {
         // ---------------------------------------------------- epilogue
         const int q = warp & 3;  // TMEM lane quarter accessible to this warp
         const int r = q * 32 + lane;
         int it = 0;
-        for (long long tile = blockIdx.x; tile < g.num_tiles; tile += gridDim.x, ++it) {
+        for (long long tile = blockIdx.x; tile < B.num_tiles; tile += gridDim.x, ++it) {
             const int acc = it & 1;
             const uint32_t aph = (uint32_t)((it >> 1) & 1);
             int okw = 1;
-            if (lane == 0) okw = mbar_wait(&tfull[acc], aph, a.status, a.wait_ns) ? 1 : 0;
+            if (lane == 0) okw = mbar_wait(&tfull[acc], aph, status, wait_ns) ? 1 : 0;
             okw = __shfl_sync(0xffffffffu, okw, 0);
             if (!okw) break;
             tc_fence_after();
-            const TileCoord tc = decode_tile(a, g, tile);
+            long long lt;
+            const int p = problem_of(B, tile, &lt);
+            const ConvArgs& a = B.a[p];
+            const TcGeo& g = B.g[p];
+            const TileCoord tc = decode_tile(a, g, lt);
             if constexpr (SWAP) {
                 // lane = output channel co, TMEM column = voxel of the 256-voxel tile
                 const int co = tc.nt * BN + r;
@@ -391,30 +427,48 @@ __global__ void __launch_bounds__(192, 1)
     if (warp == 1) tmem_dealloc(tmem_base, C::TMEM_COLS);
 }
 
-template <int BN, bool SWAP>
-int launch_bn(const ConvArgs& a, TcGeo g, int num_sms, cudaStream_t stream) {
+template <int BN, bool SWAP, int MAXP>
+int launch_bn(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, cudaStream_t stream) {
     using C = Cfg<BN, SWAP>;
-    CUtensorMap mx, mh, mw;
-    const bool strided = g.strided != 0;
-    if (!encode_act_map(&mx, a.x, a.N * a.Tin, a.Hin, a.Win, a.Cin, g.BH, g.BW, strided)) return -1;
-    if (a.hist) {
-        if (!encode_act_map(&mh, a.hist, a.N * a.hist_T, a.Hin, a.Win, a.Cin, g.BH, g.BW, strided)) return -1;
-    } else {
-        mh = mx;
+    TcBatch<MAXP> B;
+    memset(&B, 0, sizeof(B));
+    if (!encode_w_map(&B.tm_w, as[0].w, as[0].Cout_pad, as[0].Kpad, BN)) return -1;
+    long long total = 0;
+    for (int p = 0; p < count; ++p) {
+        const ConvArgs& a = as[p];
+        TcGeo g = gs[p];
+        const bool strided = g.strided != 0;
+        if (!encode_act_map(&B.tm_x[p], a.x, a.N * a.Tin, a.Hin, a.Win, a.Cin, g.BH, g.BW, strided)) return -1;
+        if (a.hist) {
+            if (!encode_act_map(&B.tm_h[p], a.hist, a.N * a.hist_T, a.Hin, a.Win, a.Cin, g.BH, g.BW, strided))
+                return -1;
+        } else {
+            B.tm_h[p] = B.tm_x[p];
+        }
+        g.n_tiles = a.Cout_pad / BN;
+        g.num_tiles = (long long)a.N * a.Tout * g.tiles_h * g.tiles_w * g.n_tiles;
+        total += g.num_tiles;
+        B.a[p] = a;
+        B.g[p] = g;
+        B.tile_end[p] = total;
     }
-    if (!encode_w_map(&mw, a.w, a.Cout_pad, a.Kpad, BN)) return -1;
-    g.n_tiles = a.Cout_pad / BN;
-    const long long m_tiles = (long long)a.N * a.Tout * g.tiles_h * g.tiles_w;
-    g.num_tiles = m_tiles * g.n_tiles;
-    if (g.num_tiles == 0) return 0;
+    B.count = count;
+    B.num_tiles = total;
+    if (total == 0) return 0;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(conv_tc_kernel<BN, SWAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+        cudaFuncSetAttribute(conv_tc_kernel<BN, SWAP, MAXP>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
         attr_set = true;
     }
-    const int grid = (int)std::min<long long>(g.num_tiles, num_sms);
-    conv_tc_kernel<BN, SWAP><<<grid, 192, C::SMEM, stream>>>(mx, mh, mw, a, g);
+    const int grid = (int)std::min<long long>(total, num_sms);
+    conv_tc_kernel<BN, SWAP, MAXP><<<grid, 192, C::SMEM, stream>>>(B);
     return (int)cudaGetLastError();
+}
+
+template <int BN, bool SWAP>
+int launch_bn_any(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, cudaStream_t stream) {
+    return count == 1 ? launch_bn<BN, SWAP, 1>(as, gs, 1, num_sms, stream)
+                      : launch_bn<BN, SWAP, kMaxConvGroup>(as, gs, count, num_sms, stream);
 }
 
 }  // namespace
@@ -501,26 +555,43 @@ int conv_tc_bn(int Cout_pad) {
 // Requirements (checked by the caller's plan): Cin % 64 == 0, Cout_pad a
 // multiple of the chosen BN, Kpad = taps * Cin, strided convs have
 // sh == sw == 2 with even Hin and Win, bf16 tensors 16-byte aligned.
-int launch_conv_tc(const ConvArgs& a, int num_sms, cudaStream_t stream) {
-    TcGeo g;
+// A group shares the layer: weights, Cin, Cout, kernel, strides and epilogue
+// mode; inputs, outputs, sizes and histories are per problem.
+int launch_conv_tc_group(const ConvArgs* as, int count, int num_sms, cudaStream_t stream) {
+    if (count < 1 || count > kMaxConvGroup) return -1;
+    const ConvArgs& a0 = as[0];
+    for (int p = 1; p < count; ++p)
+        if (as[p].w != a0.w || as[p].Cin != a0.Cin || as[p].Cout_pad != a0.Cout_pad || as[p].Kpad != a0.Kpad ||
+            as[p].kt != a0.kt || as[p].kh != a0.kh || as[p].kw != a0.kw || as[p].sh != a0.sh || as[p].mode != a0.mode ||
+            as[p].out_fp32 != a0.out_fp32)
+            return -1;
     // exactly 128 output channels, plain bf16 output: the wide (swapped) form
-    const bool swap = a.mode == OUT_PLAIN && !a.out_fp32 && a.Cout == 128 && a.Cout_pad == 128;
-    choose_tile(a.Hout, a.Wout, swap ? 256 : 128, &g.BH, &g.BW);
-    g.tiles_w = (a.Wout + g.BW - 1) / g.BW;
-    g.tiles_h = (a.Hout + g.BH - 1) / g.BH;
-    g.cpt = a.Cin / 64;
-    g.nkb = a.kt * a.kh * a.kw * g.cpt;
-    g.strided = (a.sh == 2) ? 1 : 0;
-    g.n_tiles = 0;
-    g.num_tiles = 0;
-    if (swap) return launch_bn<128, true>(a, g, num_sms, stream);
-    switch (conv_tc_bn(a.Cout_pad)) {
-        case 256: return launch_bn<256, false>(a, g, num_sms, stream);
-        case 128: return launch_bn<128, false>(a, g, num_sms, stream);
-        case 64: return launch_bn<64, false>(a, g, num_sms, stream);
-        case 32: return launch_bn<32, false>(a, g, num_sms, stream);
-        default: return launch_bn<16, false>(a, g, num_sms, stream);
+    const bool swap = a0.mode == OUT_PLAIN && !a0.out_fp32 && a0.Cout == 128 && a0.Cout_pad == 128;
+    TcGeo gs[kMaxConvGroup];
+    for (int p = 0; p < count; ++p) {
+        TcGeo& g = gs[p];
+        const ConvArgs& a = as[p];
+        choose_tile(a.Hout, a.Wout, swap ? 256 : 128, &g.BH, &g.BW);
+        g.tiles_w = (a.Wout + g.BW - 1) / g.BW;
+        g.tiles_h = (a.Hout + g.BH - 1) / g.BH;
+        g.cpt = a.Cin / 64;
+        g.nkb = a.kt * a.kh * a.kw * g.cpt;
+        g.strided = (a.sh == 2) ? 1 : 0;
+        g.n_tiles = 0;
+        g.num_tiles = 0;
     }
+    if (swap) return launch_bn_any<128, true>(as, gs, count, num_sms, stream);
+    switch (conv_tc_bn(a0.Cout_pad)) {
+        case 256: return launch_bn_any<256, false>(as, gs, count, num_sms, stream);
+        case 128: return launch_bn_any<128, false>(as, gs, count, num_sms, stream);
+        case 64: return launch_bn_any<64, false>(as, gs, count, num_sms, stream);
+        case 32: return launch_bn_any<32, false>(as, gs, count, num_sms, stream);
+        default: return launch_bn_any<16, false>(as, gs, count, num_sms, stream);
+    }
+}
+
+int launch_conv_tc(const ConvArgs& a, int num_sms, cudaStream_t stream) {
+    return launch_conv_tc_group(&a, 1, num_sms, stream);
 }
 
 }  // namespace tok

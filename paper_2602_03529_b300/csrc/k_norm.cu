@@ -10,7 +10,11 @@
 //                 fixed order into mean and 1/sqrt(var + eps).
 //   gn_apply    : SiLU((x - mean) * rstd * gamma + beta), 16-byte vectors.
 // The causal tokenizer may not mix frames, hence statistics per frame.
+#include <cstring>
+
 #include "common.cuh"
+#include "conv_args.h"
+#include "launchers.h"
 
 namespace tok {
 
@@ -70,17 +74,50 @@ __device__ __forceinline__ Triple merge(Triple a, Triple b) {
     return r;
 }
 
+// One input of a grouped GroupNorm launch (clips or stream chunks of one
+// layer). Blocks are numbered problem after problem (blk_end: running totals
+// of frames * S), finalize warps likewise over (frame, group) rows.
+template <typename T>
+struct GnProb {
+    const T* x;
+    T* y;
+    long long frames, vpf;  // frames, 16-byte vectors per frame
+    int vpt, S;             // vectors per thread, chunks per frame
+    Triple* part;           // (frames, S, G)
+    float2* stats;          // (frames, G): mean, rstd
+    long long blk_end, row_end;
+};
+
+template <typename T, int MAXP>
+struct GnBatch {
+    GnProb<T> p[MAXP];
+    int count;
+};
+
+template <typename T, int MAXP>
+__device__ __forceinline__ int gn_block_problem(const GnBatch<T, MAXP>& B, long long b, long long* local) {
+    int p = 0;
+    if constexpr (MAXP > 1)
+        while (p + 1 < B.count && b >= B.p[p].blk_end) ++p;
+    *local = p ? b - B.p[p - 1].blk_end : b;
+    return p;
+}
+
 // NGV = groups covered by one vector of V channels (V / channels-per-group,
 // or 1 when a group spans one or more whole vectors).
-template <typename T, int NGV>
-__global__ void __launch_bounds__(NT) gn_partial_kernel(const T* __restrict__ x, long long vec_per_frame, int C,
-                                                        int G, int S, int vpt, Triple* __restrict__ part) {
+template <typename T, int NGV, int MAXP>
+__global__ void __launch_bounds__(NT) gn_partial_kernel(const __grid_constant__ GnBatch<T, MAXP> B, int C, int G) {
     constexpr int V = Vec<T>::N;
     constexpr int EPG = V / NGV;  // elements of my vector per group slot
     __shared__ Triple red[NT][NGV];
-    const int frame = blockIdx.y, chunk = blockIdx.x, tid = threadIdx.x;
+    long long lb;
+    const GnProb<T>& P = B.p[gn_block_problem(B, blockIdx.x, &lb)];
+    const long long vec_per_frame = P.vpf;
+    const int S = P.S, vpt = P.vpt;
+    const int frame = (int)(lb / S), chunk = (int)(lb % S), tid = threadIdx.x;
+    Triple* __restrict__ part = P.part;
     const int vpv = C / V;  // vectors per voxel (a power of two dividing NT)
-    const T* base = x + (long long)frame * vec_per_frame * V;
+    const T* base = P.x + (long long)frame * vec_per_frame * V;
     float K[NGV], s[NGV], q[NGV];
     float cnt = 0.f;
 #pragma unroll
@@ -138,15 +175,20 @@ __global__ void __launch_bounds__(NT) gn_partial_kernel(const T* __restrict__ x,
 // One warp per (frame, group): lanes merge chunks lane, lane + 32, ... in
 // chunk order, then a fixed shuffle tree merges the lanes (lane i takes lane
 // i + o), so the statistics are the same on every run.
-__global__ void gn_finalize_kernel(const Triple* __restrict__ part, long long frames, int S, int G, float eps,
-                                   float2* __restrict__ stats) {
+template <typename T, int MAXP>
+__global__ void gn_finalize_kernel(const __grid_constant__ GnBatch<T, MAXP> B, int G, float eps) {
     const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
     const int lane = threadIdx.x % 32;
-    if (wid >= frames * G) return;
-    const long long frame = wid / G;
-    const int g = (int)(wid % G);
+    int p = 0;
+    if constexpr (MAXP > 1)
+        while (p + 1 < B.count && wid >= B.p[p].row_end) ++p;
+    if (wid >= B.p[p].row_end) return;
+    const GnProb<T>& P = B.p[p];
+    const long long row = p ? wid - B.p[p - 1].row_end : wid;
+    const long long frame = row / G;
+    const int g = (int)(row % G), S = P.S;
     Triple acc = {0.f, 0.f, 0.f};
-    for (int c = lane; c < S; c += 32) acc = merge(acc, part[(frame * S + c) * G + g]);
+    for (int c = lane; c < S; c += 32) acc = merge(acc, P.part[(frame * S + c) * G + g]);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         Triple b;
@@ -155,17 +197,21 @@ __global__ void gn_finalize_kernel(const Triple* __restrict__ part, long long fr
         b.m2 = __shfl_down_sync(0xffffffffu, acc.m2, o);
         if (lane + o < 32) acc = merge(acc, b);
     }
-    if (lane == 0) stats[wid] = make_float2(acc.mean, rsqrtf(acc.m2 / fmaxf(acc.n, 1.f) + eps));
+    if (lane == 0) P.stats[row] = make_float2(acc.mean, rsqrtf(acc.m2 / fmaxf(acc.n, 1.f) + eps));
 }
 
-template <typename T, bool FAST>
-__global__ void __launch_bounds__(NT) gn_apply_kernel(const T* __restrict__ x, T* __restrict__ y,
-                                                      long long vec_per_frame, int C, int G, int vpt,
-                                                      const float2* __restrict__ stats,
+template <typename T, bool FAST, int MAXP>
+__global__ void __launch_bounds__(NT) gn_apply_kernel(const __grid_constant__ GnBatch<T, MAXP> B, int C, int G,
                                                       const float* __restrict__ gamma,
                                                       const float* __restrict__ beta) {
     constexpr int V = Vec<T>::N;
-    const int frame = blockIdx.y, chunk = blockIdx.x, tid = threadIdx.x;
+    long long lb;
+    const GnProb<T>& P = B.p[gn_block_problem(B, blockIdx.x, &lb)];
+    const long long vec_per_frame = P.vpf;
+    const int vpt = P.vpt;
+    const int frame = (int)(lb / P.S), chunk = (int)(lb % P.S), tid = threadIdx.x;
+    const T* __restrict__ x = P.x;
+    T* __restrict__ y = P.y;
     const int cg = C / G;
     const int vpv = C / V;
     const int c0 = (tid % vpv) * V;
@@ -173,7 +219,7 @@ __global__ void __launch_bounds__(NT) gn_apply_kernel(const T* __restrict__ x, T
 #pragma unroll
     for (int j = 0; j < V; ++j) {
         const int c = c0 + j;
-        const float2 st = stats[(long long)frame * G + c / cg];
+        const float2 st = P.stats[(long long)frame * G + c / cg];
         const float ga = gamma ? gamma[c] : 1.f;
         sc[j] = st.y * ga;
         sh[j] = (beta ? beta[c] : 0.f) - st.x * st.y * ga;
@@ -222,59 +268,100 @@ size_t gn_scratch_bytes(long long frames, long long HW, int C, int G, int num_sm
     return (size_t)frames * S * G * sizeof(Triple) + (size_t)frames * G * sizeof(float2) + 256;
 }
 
-// x, y: (frames, HW, C) channels-last; y may alias x. scratch: at least
-// gn_scratch_bytes(...). Requirements: C % V == 0, (C/V) a power of two
-// dividing 256, C/G >= 2, 16-byte aligned tensors.
-template <typename T>
-int launch_gn_silu(const T* x, T* y, long long frames, long long HW, int C, int G, const float* gamma,
-                   const float* beta, float eps, void* scratch, int num_sms, bool fast, cudaStream_t stream) {
+namespace {
+
+// Plan a batch: per-problem chunking, scratch carving, block numbering.
+template <typename T, int MAXP>
+bool gn_batch(const GnItem<T>* items, int count, int C, int G, GnBatch<T, MAXP>* B, long long* blocks,
+              long long* rows) {
     constexpr int V = Vec<T>::N;
-    const long long vpf = HW * C / V;
-    int vpt, S;
-    gn_plan(frames, vpf, num_sms, &vpt, &S);
-    Triple* part = static_cast<Triple*>(scratch);
-    float2* stats = reinterpret_cast<float2*>(
-        (reinterpret_cast<uintptr_t>(part + frames * S * G) + 15) & ~uintptr_t(15));
-    dim3 grid(S, (unsigned)frames);
+    memset(B, 0, sizeof(*B));
+    B->count = count;
+    long long nb = 0, nr = 0;
+    for (int p = 0; p < count; ++p) {
+        GnProb<T>& P = B->p[p];
+        P.x = items[p].x;
+        P.y = items[p].y;
+        P.frames = items[p].frames;
+        P.vpf = items[p].HW * C / V;
+        gn_plan(P.frames, P.vpf, 0, &P.vpt, &P.S);
+        P.part = static_cast<Triple*>(items[p].scratch);
+        P.stats = reinterpret_cast<float2*>(
+            (reinterpret_cast<uintptr_t>(P.part + P.frames * P.S * G) + 15) & ~uintptr_t(15));
+        nb += P.frames * P.S;
+        nr += P.frames * G;
+        P.blk_end = nb;
+        P.row_end = nr;
+    }
+    *blocks = nb;
+    *rows = nr;
+    return nb > 0;
+}
+
+template <typename T, int MAXP>
+int gn_stats_batch(const GnBatch<T, MAXP>& B, long long blocks, long long rows, int C, int G, float eps,
+                   cudaStream_t stream) {
+    constexpr int V = Vec<T>::N;
     const int cg = C / G;
     const int ngv = cg >= V ? 1 : V / cg;
     switch (ngv) {
-        case 1: gn_partial_kernel<T, 1><<<grid, NT, 0, stream>>>(x, vpf, C, G, S, vpt, part); break;
-        case 2: gn_partial_kernel<T, 2><<<grid, NT, 0, stream>>>(x, vpf, C, G, S, vpt, part); break;
-        case 4: gn_partial_kernel<T, 4><<<grid, NT, 0, stream>>>(x, vpf, C, G, S, vpt, part); break;
+        case 1: gn_partial_kernel<T, 1, MAXP><<<(unsigned)blocks, NT, 0, stream>>>(B, C, G); break;
+        case 2: gn_partial_kernel<T, 2, MAXP><<<(unsigned)blocks, NT, 0, stream>>>(B, C, G); break;
+        case 4: gn_partial_kernel<T, 4, MAXP><<<(unsigned)blocks, NT, 0, stream>>>(B, C, G); break;
         default: return (int)cudaErrorInvalidValue;
     }
-    gn_finalize_kernel<<<(unsigned)((frames * G * 32 + 255) / 256), 256, 0, stream>>>(part, frames, S, G, eps, stats);
+    gn_finalize_kernel<T, MAXP><<<(unsigned)((rows * 32 + 255) / 256), 256, 0, stream>>>(B, G, eps);
+    return 0;
+}
+
+template <typename T, int MAXP>
+int gn_silu_batch(const GnItem<T>* items, int count, int C, int G, const float* gamma, const float* beta, float eps,
+                  bool fast, cudaStream_t stream) {
+    GnBatch<T, MAXP> B;
+    long long blocks, rows;
+    if (!gn_batch(items, count, C, G, &B, &blocks, &rows)) return 0;
+    if (const int e = gn_stats_batch(B, blocks, rows, C, G, eps, stream)) return e;
     if (fast)
-        gn_apply_kernel<T, true><<<grid, NT, 0, stream>>>(x, y, vpf, C, G, vpt, stats, gamma, beta);
+        gn_apply_kernel<T, true, MAXP><<<(unsigned)blocks, NT, 0, stream>>>(B, C, G, gamma, beta);
     else
-        gn_apply_kernel<T, false><<<grid, NT, 0, stream>>>(x, y, vpf, C, G, vpt, stats, gamma, beta);
+        gn_apply_kernel<T, false, MAXP><<<(unsigned)blocks, NT, 0, stream>>>(B, C, G, gamma, beta);
     return (int)cudaGetLastError();
+}
+
+}  // namespace
+
+// Every item: x, y (frames, HW, C) channels-last, y may alias x; scratch of at
+// least gn_scratch_bytes(...) for that item. Requirements: C % V == 0, (C/V)
+// a power of two dividing 256, C/G >= 2, 16-byte aligned tensors. One launch
+// per pass over all items (at most kMaxConvGroup).
+template <typename T>
+int launch_gn_silu_group(const GnItem<T>* items, int count, int C, int G, const float* gamma, const float* beta,
+                         float eps, bool fast, cudaStream_t stream) {
+    if (count < 1 || count > kMaxConvGroup) return (int)cudaErrorInvalidValue;
+    return count == 1 ? gn_silu_batch<T, 1>(items, 1, C, G, gamma, beta, eps, fast, stream)
+                      : gn_silu_batch<T, kMaxConvGroup>(items, count, C, G, gamma, beta, eps, fast, stream);
+}
+
+template <typename T>
+int launch_gn_silu(const T* x, T* y, long long frames, long long HW, int C, int G, const float* gamma,
+                   const float* beta, float eps, void* scratch, int num_sms, bool fast, cudaStream_t stream) {
+    (void)num_sms;
+    GnItem<T> it{x, y, frames, HW, scratch};
+    return launch_gn_silu_group<T>(&it, 1, C, G, gamma, beta, eps, fast, stream);
 }
 
 template <typename T>
 int launch_gn_stats(const T* x, long long frames, long long HW, int C, int G, float eps, void* scratch, int num_sms,
                     cudaStream_t stream, float2** stats_out, int* vpt_out, int* S_out) {
-    constexpr int V = Vec<T>::N;
-    const long long vpf = HW * C / V;
-    int vpt, S;
-    gn_plan(frames, vpf, num_sms, &vpt, &S);
-    Triple* part = static_cast<Triple*>(scratch);
-    float2* stats = reinterpret_cast<float2*>(
-        (reinterpret_cast<uintptr_t>(part + frames * S * G) + 15) & ~uintptr_t(15));
-    dim3 grid(S, (unsigned)frames);
-    const int cg = C / G;
-    const int ngv = cg >= V ? 1 : V / cg;
-    switch (ngv) {
-        case 1: gn_partial_kernel<T, 1><<<grid, NT, 0, stream>>>(x, vpf, C, G, S, vpt, part); break;
-        case 2: gn_partial_kernel<T, 2><<<grid, NT, 0, stream>>>(x, vpf, C, G, S, vpt, part); break;
-        case 4: gn_partial_kernel<T, 4><<<grid, NT, 0, stream>>>(x, vpf, C, G, S, vpt, part); break;
-        default: return (int)cudaErrorInvalidValue;
-    }
-    gn_finalize_kernel<<<(unsigned)((frames * G * 32 + 255) / 256), 256, 0, stream>>>(part, frames, S, G, eps, stats);
-    *stats_out = stats;
-    *vpt_out = vpt;
-    *S_out = S;
+    (void)num_sms;
+    GnItem<T> it{x, nullptr, frames, HW, scratch};
+    GnBatch<T, 1> B;
+    long long blocks, rows;
+    if (!gn_batch(&it, 1, C, G, &B, &blocks, &rows)) return 0;
+    if (const int e = gn_stats_batch(B, blocks, rows, C, G, eps, stream)) return e;
+    *stats_out = B.p[0].stats;
+    *vpt_out = B.p[0].vpt;
+    *S_out = B.p[0].S;
     return (int)cudaGetLastError();
 }
 template int launch_gn_stats<float>(const float*, long long, long long, int, int, float, void*, int, cudaStream_t,
@@ -286,5 +373,9 @@ template int launch_gn_silu<float>(const float*, float*, long long, long long, i
                                    float, void*, int, bool, cudaStream_t);
 template int launch_gn_silu<__nv_bfloat16>(const __nv_bfloat16*, __nv_bfloat16*, long long, long long, int, int,
                                            const float*, const float*, float, void*, int, bool, cudaStream_t);
+template int launch_gn_silu_group<float>(const GnItem<float>*, int, int, int, const float*, const float*, float, bool,
+                                         cudaStream_t);
+template int launch_gn_silu_group<__nv_bfloat16>(const GnItem<__nv_bfloat16>*, int, int, int, const float*,
+                                                 const float*, float, bool, cudaStream_t);
 
 }  // namespace tok

@@ -10,10 +10,23 @@
 namespace tok {
 
 int launch_conv_tc(const ConvArgs& a, int num_sms, cudaStream_t stream);
+// one launch over up to kMaxConvGroup inputs of the same layer (k_conv_tc.cu)
+int launch_conv_tc_group(const ConvArgs* as, int count, int num_sms, cudaStream_t stream);
 int conv_tc_bn(int cout_pad16);
 int launch_conv_simt(const ConvArgs& a, cudaStream_t stream);
 
 size_t gn_scratch_bytes(long long frames, long long HW, int C, int G, int num_sms, int vec);
+// One input of a grouped GroupNorm+SiLU launch (k_norm.cu).
+template <typename T>
+struct GnItem {
+    const T* x;
+    T* y;
+    long long frames, HW;
+    void* scratch;  // gn_scratch_bytes(frames, HW, ...) bytes
+};
+template <typename T>
+int launch_gn_silu_group(const GnItem<T>* items, int count, int C, int G, const float* gamma, const float* beta,
+                         float eps, bool fast, cudaStream_t stream);
 template <typename T>
 int launch_gn_silu(const T* x, T* y, long long frames, long long HW, int C, int G, const float* gamma,
                    const float* beta, float eps, void* scratch, int num_sms, bool fast, cudaStream_t stream);

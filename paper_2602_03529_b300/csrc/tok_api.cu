@@ -11,7 +11,7 @@
 //         stand-alone FSQ / dequantisation.
 // All work is enqueued on the caller's stream; nothing here synchronises
 // except tok_set_param / tok_status / allocation calls.
-#include "tok_internal.h"
+#include "exec_group.h"
 
 // ======================================================================= C ABI
 
@@ -151,9 +151,41 @@ size_t tok_workspace_bytes(const tok_ctx* c, int N, int T, int H, int W) {
     return layout_for(c, N, T, H, W).total;
 }
 
+static int reserve_bytes(tok_ctx* c, size_t need);
+
 int tok_reserve(tok_ctx* c, int N, int T, int H, int W) {
     if (!c || N < 1 || T < 1 || H < 1 || W < 1) return TOK_EINVAL;
-    const size_t need = layout_for(c, N, T, H, W).total;
+    return reserve_bytes(c, layout_for(c, N, T, H, W).total);
+}
+
+int tok_latent_shape(const tok_ctx* c, int T, int H, int W, int* Tq, int* Hq, int* Wq) {
+    if (!c || T < 1 || H < 1 || W < 1) return TOK_EINVAL;
+    if ((T - 1) % c->s_t != 0) return TOK_ESHAPE;
+    const Dims d = clip_dims(c, T, H, W);
+    if (Tq) *Tq = d.Tq;
+    if (Hq) *Hq = d.Hq;
+    if (Wq) *Wq = d.Wq;
+    return TOK_OK;
+}
+
+static_assert(TOK_MAX_BATCH == tok::kMaxConvGroup, "batch size of the ABI and of the grouped launch");
+
+// Workspace of one batch item: a clip (N, T, H, W), or one chunk of a stream
+// (sized as N = 1 with s_T frames).
+static size_t item_bytes(const tok_ctx* c, const tok_shape& sh) { return layout_for(c, sh.N, sh.T, sh.H, sh.W).total; }
+
+size_t tok_batch_workspace_bytes(const tok_ctx* c, const tok_shape* shapes, int count) {
+    if (!c || !shapes || count < 1 || count > TOK_MAX_BATCH) return 0;
+    size_t t = 0;
+    for (int p = 0; p < count; ++p) {
+        const tok_shape& sh = shapes[p];
+        if (sh.N < 1 || sh.T < 1 || sh.H < 1 || sh.W < 1) return 0;
+        t += item_bytes(c, sh);
+    }
+    return t;
+}
+
+static int reserve_bytes(tok_ctx* c, size_t need) {
     if (need <= c->arena_bytes) return TOK_OK;
     if (c->arena) {
         cudaDeviceSynchronize();
@@ -169,67 +201,120 @@ int tok_reserve(tok_ctx* c, int N, int T, int H, int W) {
     return TOK_OK;
 }
 
-int tok_latent_shape(const tok_ctx* c, int T, int H, int W, int* Tq, int* Hq, int* Wq) {
-    if (!c || T < 1 || H < 1 || W < 1) return TOK_EINVAL;
-    if ((T - 1) % c->s_t != 0) return TOK_ESHAPE;
-    const Dims d = clip_dims(c, T, H, W);
-    if (Tq) *Tq = d.Tq;
-    if (Hq) *Hq = d.Hq;
-    if (Wq) *Wq = d.Wq;
-    return TOK_OK;
+int tok_reserve_batch(tok_ctx* c, const tok_shape* shapes, int count) {
+    const size_t need = tok_batch_workspace_bytes(c, shapes, count);
+    if (!need) return TOK_EINVAL;
+    return reserve_bytes(c, need);
+}
+
+int tok_encode_batch(tok_ctx* c, const tok_enc_item* items, int count, void* stream) {
+    if (!c || !items || count < 1 || count > TOK_MAX_BATCH) return TOK_EINVAL;
+    GroupExec ex;
+    ex.c = c;
+    ex.s = static_cast<cudaStream_t>(stream);
+    ex.P = count;
+    const void* x[kMaxConvGroup];
+    int N[kMaxConvGroup], T[kMaxConvGroup], H[kMaxConvGroup], W[kMaxConvGroup];
+    float* z[kMaxConvGroup];
+    int32_t* idx[kMaxConvGroup];
+    size_t off = 0;
+    for (int p = 0; p < count; ++p) {
+        const tok_enc_item& it = items[p];
+        if (!it.d_x || it.N < 1 || it.T < 1 || it.H < 1 || it.W < 1) return TOK_EINVAL;
+        tok_shape sh{it.N, it.T, it.H, it.W};
+        if (tok_stream* st = it.s) {
+            // one chunk of a stream: frame 0 alone, then s_T frames per chunk
+            if (!compatible(st->ctx, c) || it.N != 1 || it.H != st->H || it.W != st->W) return TOK_EINVAL;
+            for (int q = 0; q < p; ++q)
+                if (items[q].s == st) return TOK_EINVAL;
+            if (it.T != (st->enc_chunk == 0 ? 1 : c->s_t)) return TOK_ESHAPE;
+            sh = tok_shape{1, c->s_t, it.H, it.W};
+            ex.pr[p].st = st;
+            ex.pr[p].chunk0 = st->enc_chunk == 0;
+        } else if ((it.T - 1) % c->s_t != 0) {
+            return TOK_ESHAPE;
+        }
+        const Layout L = layout_for(c, sh.N, sh.T, sh.H, sh.W);
+        ex.pr[p].w = carve(c, L, off);
+        off += L.total;
+        x[p] = it.d_x;
+        N[p] = it.N;
+        T[p] = it.T;
+        H[p] = it.H;
+        W[p] = it.W;
+        z[p] = it.d_z;
+        idx[p] = it.d_idx;
+    }
+    if (off > c->arena_bytes) return TOK_ENOMEM;
+    ex.encode(x, N, T, H, W, z, idx);
+    if (!ex.err)
+        for (int p = 0; p < count; ++p)
+            if (items[p].s) items[p].s->enc_chunk++;
+    return ex.err;
+}
+
+int tok_decode_batch(tok_ctx* c, const tok_dec_item* items, int count, void* stream) {
+    if (!c || !items || count < 1 || count > TOK_MAX_BATCH) return TOK_EINVAL;
+    if (c->arch.kind != TOK_ARCH_FULL) return TOK_ESTATE;
+    GroupExec ex;
+    ex.c = c;
+    ex.s = static_cast<cudaStream_t>(stream);
+    ex.P = count;
+    const int32_t* idx[kMaxConvGroup];
+    int N[kMaxConvGroup], Tq[kMaxConvGroup], Hq[kMaxConvGroup], Wq[kMaxConvGroup], H[kMaxConvGroup],
+        W[kMaxConvGroup];
+    float* xhat[kMaxConvGroup];
+    size_t off = 0;
+    for (int p = 0; p < count; ++p) {
+        const tok_dec_item& it = items[p];
+        if (!it.d_idx || !it.d_xhat || it.N < 1 || it.Tq < 1 || it.Hq < 1 || it.Wq < 1 || it.H < 1 || it.W < 1)
+            return TOK_EINVAL;
+        if (it.H > it.Hq * c->s_hw || it.W > it.Wq * c->s_hw) return TOK_ESHAPE;
+        Layout L;
+        if (tok_stream* st = it.s) {
+            // one latent frame of a stream -> 1 frame (chunk 0) or s_T frames
+            if (!compatible(st->ctx, c) || it.N != 1 || it.Tq != 1) return TOK_EINVAL;
+            for (int q = 0; q < p; ++q)
+                if (items[q].s == st) return TOK_EINVAL;
+            const Dims d = clip_dims(c, 1, st->H, st->W);
+            if (it.H != st->H || it.W != st->W || it.Hq != d.Hq || it.Wq != d.Wq) return TOK_ESHAPE;
+            L = layout_for(c, 1, c->s_t, it.Hq * c->s_hw, it.Wq * c->s_hw);
+            ex.pr[p].st = st;
+            ex.pr[p].chunk0 = st->dec_chunk == 0;
+        } else {
+            L = layout_for(c, it.N, 1 + c->s_t * (it.Tq - 1), it.Hq * c->s_hw, it.Wq * c->s_hw);
+        }
+        ex.pr[p].w = carve(c, L, off);
+        off += L.total;
+        idx[p] = it.d_idx;
+        N[p] = it.N;
+        Tq[p] = it.Tq;
+        Hq[p] = it.Hq;
+        Wq[p] = it.Wq;
+        H[p] = it.H;
+        W[p] = it.W;
+        xhat[p] = it.d_xhat;
+    }
+    if (off > c->arena_bytes) return TOK_ENOMEM;
+    ex.decode(idx, N, Tq, Hq, Wq, H, W, xhat);
+    if (!ex.err)
+        for (int p = 0; p < count; ++p)
+            if (items[p].s) items[p].s->dec_chunk++;
+    return ex.err;
 }
 
 int tok_encode(tok_ctx* c, const void* x, int N, int T, int H, int W, float* z, int32_t* idx, tok_stream* st,
                void* stream) {
     if (!c || !x || N < 1 || T < 1 || H < 1 || W < 1) return TOK_EINVAL;
-    Exec ex;
-    ex.c = c;
-    ex.s = static_cast<cudaStream_t>(stream);
-    Layout L;
-    if (st) {
-        // one chunk of a stream: frame 0 alone, then s_T frames per chunk
-        if (!compatible(st->ctx, c) || N != 1 || H != st->H || W != st->W) return TOK_EINVAL;
-        if (T != (st->enc_chunk == 0 ? 1 : c->s_t)) return TOK_ESHAPE;
-        L = layout_for(c, 1, c->s_t, H, W);
-        ex.st = st;
-        ex.chunk0 = st->enc_chunk == 0;
-    } else {
-        if ((T - 1) % c->s_t != 0) return TOK_ESHAPE;
-        L = layout_for(c, N, T, H, W);
-    }
-    if (L.total > c->arena_bytes) return TOK_ENOMEM;
-    ex.w = carve(c, L);
-    ex.encode(x, N, T, H, W, z, idx);
-    if (st && !ex.err) st->enc_chunk++;
-    return ex.err;
+    const tok_enc_item it{x, N, T, H, W, z, idx, st};
+    return tok_encode_batch(c, &it, 1, stream);
 }
 
 int tok_decode(tok_ctx* c, const int32_t* idx, int N, int Tq, int Hq, int Wq, int H, int W, float* xhat,
                tok_stream* st, void* stream) {
     if (!c || !idx || !xhat || N < 1 || Tq < 1 || Hq < 1 || Wq < 1 || H < 1 || W < 1) return TOK_EINVAL;
-    if (c->arch.kind != TOK_ARCH_FULL) return TOK_ESTATE;
-    if (H > Hq * c->s_hw || W > Wq * c->s_hw) return TOK_ESHAPE;
-    Exec ex;
-    ex.c = c;
-    ex.s = static_cast<cudaStream_t>(stream);
-    Layout L;
-    if (st) {
-        // one latent frame of a stream -> 1 frame (chunk 0) or s_T frames
-        if (!compatible(st->ctx, c) || N != 1 || Tq != 1) return TOK_EINVAL;
-        const Dims d = clip_dims(c, 1, st->H, st->W);
-        if (H != st->H || W != st->W || Hq != d.Hq || Wq != d.Wq) return TOK_ESHAPE;
-        L = layout_for(c, 1, c->s_t, Hq * c->s_hw, Wq * c->s_hw);
-        ex.st = st;
-        ex.chunk0 = st->dec_chunk == 0;
-    } else {
-        const int T = 1 + c->s_t * (Tq - 1);
-        L = layout_for(c, N, T, Hq * c->s_hw, Wq * c->s_hw);
-    }
-    if (L.total > c->arena_bytes) return TOK_ENOMEM;
-    ex.w = carve(c, L);
-    ex.decode(idx, N, Tq, Hq, Wq, H, W, xhat);
-    if (st && !ex.err) st->dec_chunk++;
-    return ex.err;
+    const tok_dec_item it{idx, N, Tq, Hq, Wq, H, W, xhat, st};
+    return tok_decode_batch(c, &it, 1, stream);
 }
 
 int tok_quantize(const float* z, int64_t ntok, const int* levels, int nlev, int32_t* idx, float* codes,

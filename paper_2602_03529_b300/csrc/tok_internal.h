@@ -335,9 +335,10 @@ struct Work {
     char* gn;
 };
 
-Work carve(tok_ctx* c, const Layout& L) {
+// Carve one problem's workspace out of the arena, starting `off` bytes in.
+Work carve(tok_ctx* c, const Layout& L, size_t off = 0) {
     Work w;
-    char* p = c->arena;
+    char* p = c->arena + off;
     for (int i = 0; i < 5; ++i) {
         w.act[i] = p;
         p += L.act;
@@ -412,48 +413,6 @@ struct Exec {
     cudaStream_t s;
     Work w;
     int err = 0;
-    tok_stream* st = nullptr;  // chunked streaming (null: whole clip)
-    bool chunk0 = true;        // first chunk of a stream: clip-mode causal padding
-
-    // Streaming: a conv with temporal taps reads its left context from the
-    // stream's history; stride-2 convs see chunks that start one frame after
-    // an output frame, hence t_off -1 instead of -2.
-    void stream_args(ConvArgs& a, const std::string& name, int k, int st_t) {
-        if (!st || k != 3 || chunk0) return;
-        a.hist = st->hist[name];
-        a.hist_T = 2;
-        if (st_t == 2) a.t_off = -1;
-    }
-
-    // After a causal conv of a stream: history <- last two frames of [history | chunk].
-    void stream_update(const std::string& name, const void* chunk, int Tc, bool zero_index_fill = false) {
-        if (!st || err) return;
-        auto it = st->hist.find(name);
-        if (it == st->hist.end()) return;
-        char* h = it->second;
-        const size_t fb = st->frame_bytes[name];
-        const char* x = static_cast<const char*>(chunk);
-        auto cp = [&](void* d, const void* src, size_t n) {
-            if (cudaMemcpyAsync(d, src, n, cudaMemcpyDeviceToDevice, s) != cudaSuccess) ck(1);
-        };
-        if (chunk0) {
-            if (c->arch.time_pad == TOK_PAD_REPLICATE) {
-                cp(h, x, fb);
-            } else if (zero_index_fill) {
-                other([&] { return launch_fill_i32(reinterpret_cast<int32_t*>(h), (long long)(fb / 4),
-                                                   zero_index_of(c), s); }, (double)fb);
-            } else if (cudaMemsetAsync(h, 0, fb, s) != cudaSuccess) {
-                ck(1);
-            }
-            cp(h + fb, x + (size_t)(Tc - 1) * fb, fb);
-        } else if (Tc >= 2) {
-            cp(h, x + (size_t)(Tc - 2) * fb, 2 * fb);
-        } else {
-            cp(h, h + fb, fb);
-            cp(h + fb, x, fb);
-        }
-    }
-
     void ck(int e) {
         if (e && !err) err = TOK_ECUDA;
     }
@@ -529,7 +488,6 @@ struct Exec {
              int sh = 1, int sw = 1) {
         const ConvW& cw = c->convs[c->cindex[name]];
         ConvArgs a = base_args(cw, in, tst, sh, sw);
-        stream_args(a, name, cw.k, tst);
         a.mode = OUT_PLAIN;
         a.out = out;
         a.residual = residual;
@@ -538,7 +496,6 @@ struct Exec {
         a.oW = a.Wout;
         a.oC = cw.Cout;
         launch(a, cw);
-        stream_update(name, in.p, in.T);
         return Act{out, in.N, a.Tout, a.Hout, a.Wout, cw.Cout};
     }
 
@@ -547,21 +504,18 @@ struct Exec {
                  bool out_fp32) {
         const ConvW& cw = c->convs[c->cindex[name]];
         ConvArgs a = base_args(cw, in, 1, 1, 1);
-        stream_args(a, name, cw.k, 1);
         a.mode = OUT_D2S;
         a.out = out;
         a.out_fp32 = out_fp32 ? 1 : 0;
         a.rt = rt;
         a.rh = rh;
         a.rw = rw;
-        // the causal trim of the first rt-1 frames belongs to the clip's start only
-        a.drop_t = (st && !chunk0) ? 0 : rt - 1;
+        a.drop_t = rt - 1;  // causal trim of the clip's first rt-1 frames
         a.oT = a.Tout * rt - a.drop_t;
         a.oH = oH;
         a.oW = oW;
         a.oC = cw.Cout / (rt * rh * rw);
         launch(a, cw);
-        stream_update(name, in.p, in.T);
         return Act{out, in.N, a.oT, oH, oW, a.oC};
     }
 
@@ -603,78 +557,10 @@ struct Exec {
         return Act{out, in.N, in.T, in.H, in.W, in.C};
     }
 
-    // Residual block; X is the stream. Uses act slots: ix (X), and three temps.
-    int block(const std::string& name, int ix, Act& X) {
-        int t[4], k = 0;
-        for (int i = 0; i < 5 && k < 4; ++i)
-            if (i != ix) t[k++] = i;
-        const int iA = t[0], iH = t[1], iS = t[2], iY = t[3];
-        Act A = gn_silu(name + ".gn1", X, w.act[iA]);
-        Act H = conv(name + ".c1", A, w.act[iH]);
-        Act A2 = gn_silu(name + ".gn2", H, w.act[iA]);
-        const void* res = X.p;
-        if (c->cindex.count(name + ".sc")) res = conv(name + ".sc", X, w.act[iS]).p;
-        X = conv(name + ".c2", A2, w.act[iY], res);
-        return iY;
-    }
-
-    int other(int ix) { return ix == 0 ? 1 : 0; }
-
-    // ---------------------------------------------------------------- encode
-    void encode(const void* x, int N, int T, int H, int W, float* z, int32_t* idx) {
-        const tok_arch& ar = c->arch;
-        const Dims d = clip_dims(c, T, H, W);
-        float* zo = z ? z : reinterpret_cast<float*>(w.zbuf);
-        int ix = 0;
-        Act X;
-        if (ar.kind == TOK_ARCH_STAGE) {
-            if (c->bf16()) {
-                GatherGeo g = gather_pixels(N, T, H, W, d.Hp, d.Wp, 1);
-                const __nv_bfloat16* ph = stream_hist_pixels(g, "stage.c0");
-                other([&] { return launch_im2col_pixels(static_cast<const __nv_bfloat16*>(x), ph, g,
-                                                        reinterpret_cast<__nv_bfloat16*>(w.gather), s); },
-                      gather_bytes(g));
-                stream_update("stage.c0", x, T);
-                X = conv_gathered("stage.c0", N, T, d.Hp, d.Wp, w.act[0], OUT_PLAIN, nullptr);
-            } else {
-                Act P = edge_pad_f32(static_cast<const float*>(x), N, T, H, W, d.Hp, d.Wp);
-                X = conv("stage.c0", P, w.act[0]);
-            }
-            Act Y = conv("stage.c1", X, w.act[1], nullptr, 1, 2, 2);
-            Act A = gn_silu("stage.gn", Y, w.act[2]);
-            out_conv("stage.out", A, zo, idx);
-            return;
-        }
-        if (c->bf16()) {
-            GatherGeo g = gather_pixels(N, T, H, W, d.Hp, d.Wp, 2);
-            const __nv_bfloat16* ph = stream_hist_pixels(g, "enc.stem");
-            other([&] { return launch_im2col_pixels(static_cast<const __nv_bfloat16*>(x), ph, g,
-                                                    reinterpret_cast<__nv_bfloat16*>(w.gather), s); },
-                  gather_bytes(g));
-            stream_update("enc.stem", x, T);
-            X = conv_gathered("enc.stem", N, T, d.Hp / 2, d.Wp / 2, w.act[0], OUT_PLAIN, nullptr);
-        } else {
-            Act P = edge_pad_f32(static_cast<const float*>(x), N, T, H, W, d.Hp, d.Wp);
-            X = conv("enc.stem", P, w.act[0], nullptr, 1, 2, 2);
-        }
-        for (int l = 0; l < ar.nlevels; ++l) {
-            for (int b = 0; b < ar.blocks; ++b) ix = block("enc.l" + std::to_string(l) + ".b" + std::to_string(b), ix, X);
-            if (l < ar.nlevels - 1) {
-                const int iy = other(ix);
-                X = conv("enc.down" + std::to_string(l), X, w.act[iy], nullptr, 2, 2, 2);
-                ix = iy;
-            }
-        }
-        const int ia = other(ix);
-        Act A = gn_silu("enc.out_gn", X, w.act[ia]);
-        out_conv("enc.out", A, zo, idx);
-    }
-
     // Last encoder conv: latent z (fp32) and FSQ token indices.
     void out_conv(const std::string& name, const Act& A, float* z, int32_t* idx) {
         const ConvW& cw = c->convs[c->cindex[name]];
         ConvArgs a = base_args(cw, A, 1, 1, 1);
-        stream_args(a, name, cw.k, 1);
         a.out = z;
         a.oT = a.Tout;
         a.oH = a.Hout;
@@ -691,7 +577,6 @@ struct Exec {
             launch(a, cw);
             if (idx) other([&] { return launch_fsq(z, ntok, c->fsq, idx, nullptr, s); }, (double)ntok * (4 * cw.Cout + 4));
         }
-        stream_update(name, A.p, A.T);
     }
 
     GatherGeo gather_pixels(int N, int T, int H, int W, int Hp, int Wp, int stride_hw) {
@@ -716,74 +601,8 @@ struct Exec {
         return g;
     }
 
-    const __nv_bfloat16* stream_hist_pixels(GatherGeo& g, const char* name) {
-        if (!st || chunk0) return nullptr;
-        g.hist_T = 2;
-        return reinterpret_cast<const __nv_bfloat16*>(st->hist[name]);
-    }
-
     static double gather_bytes(const GatherGeo& g) {
         return (double)g.N * g.Tout * g.Hout * g.Wout * g.Kpad * 2;
-    }
-
-    Act edge_pad_f32(const float* x, int N, int T, int H, int W, int Hp, int Wp) {
-        float* P = reinterpret_cast<float*>(w.gather);
-        if (Hp == H && Wp == W) return Act{const_cast<float*>(x), N, T, H, W, c->arch.in_ch};
-        other([&] { return launch_edge_pad<float>(x, (long long)N * T, H, W, Hp, Wp, c->arch.in_ch, P, s); },
-              (double)N * T * (H * W + Hp * Wp) * c->arch.in_ch * 4);
-        return Act{P, N, T, Hp, Wp, c->arch.in_ch};
-    }
-
-    // ---------------------------------------------------------------- decode
-    void decode(const int32_t* idx, int N, int Tq, int Hq, int Wq, int H, int W, float* xhat) {
-        const tok_arch& ar = c->arch;
-        const int* ch = ar.ch;
-        int ix = 0;
-        Act X;
-        if (c->bf16()) {
-            GatherGeo g;
-            g.N = N;
-            g.Tin = Tq;
-            g.H = g.Hp = Hq;
-            g.W = g.Wp = Wq;
-            g.Cin = ar.nlev;
-            g.hist_T = 0;
-            g.Tout = Tq;
-            g.Hout = Hq;
-            g.Wout = Wq;
-            g.kt = g.kh = g.kw = 3;
-            g.st = g.sh = g.sw = 1;
-            g.t_off = -2;
-            g.pad_mode = ar.time_pad;
-            g.Kpad = round_up(27 * ar.nlev, 64);
-            const int32_t* th = nullptr;
-            if (st && !chunk0) {
-                th = reinterpret_cast<const int32_t*>(st->hist["dec.in"]);
-                g.hist_T = 2;
-            }
-            other([&] { return launch_im2col_tokens(idx, th, g, c->fsq,
-                                                    reinterpret_cast<__nv_bfloat16*>(w.gather), s); },
-                  gather_bytes(g));
-            stream_update("dec.in", idx, Tq, true);
-            X = conv_gathered("dec.in", N, Tq, Hq, Wq, w.act[0], OUT_PLAIN, nullptr);
-        } else {
-            float* codes = reinterpret_cast<float*>(w.zbuf);
-            const long long nt = (long long)N * Tq * Hq * Wq;
-            other([&] { return launch_dequant(idx, nt, c->fsq, codes, s); }, (double)nt * (4 + 4 * ar.nlev));
-            X = conv("dec.in", Act{codes, N, Tq, Hq, Wq, ar.nlev}, w.act[0]);
-        }
-        for (int l = ar.nlevels - 1; l >= 0; --l) {
-            for (int b = 0; b < ar.blocks; ++b) ix = block("dec.l" + std::to_string(l) + ".b" + std::to_string(b), ix, X);
-            if (l > 0) {
-                const int iy = other(ix);
-                X = conv_d2s("dec.up" + std::to_string(l - 1), X, w.act[iy], 2, 2, 2, X.H * 2, X.W * 2, false);
-                ix = iy;
-            }
-        }
-        (void)ch;
-        const int ia = other(ix);
-        Act A = gn_silu("dec.out_gn", X, w.act[ia]);
-        conv_d2s("dec.out", A, xhat, 1, 2, 2, H, W, true);
     }
 };
 

@@ -131,6 +131,47 @@ class Tokenizer:
         L.tok_decode(self.ctx, _ptr(idx), N, Tq, Hq, Wq, H, W, _ptr(out), video, _stream_ptr(stream))
         return out
 
+    # -- grouped (one launch per layer over several inputs) --------------------
+    def reserve_batch(self, shapes):
+        """shapes: list of (N, T, H, W); a stream chunk counts as (1, s_T, H, W)."""
+        L.tok_reserve_batch(self.ctx, list(shapes))
+
+    def batch_workspace_bytes(self, shapes) -> int:
+        return L.tok_batch_workspace_bytes(self.ctx, list(shapes))
+
+    def encode_batch(self, xs, videos=None, stream=None, want_z=True):
+        """Encode several clips (or stream chunks, ``videos[i]`` a handle or None) of
+        any sizes in one grouped pass; returns lists of z (or None) and idx."""
+        videos = videos or [None] * len(xs)
+        zs, idxs, items = [], [], []
+        for x, v in zip(xs, videos):
+            N, T, H, W, _ = x.shape
+            if x.dtype != self.dtype:
+                raise ValueError(f"x must be {self.dtype}")
+            Tq, Hq, Wq = (1,) + self.latent_shape(1, H, W)[1:] if v is not None else self.latent_shape(T, H, W)
+            z = torch.empty((N, Tq, Hq, Wq, len(self.levels)), device=x.device, dtype=torch.float32) \
+                if want_z else None
+            idx = torch.empty((N, Tq, Hq, Wq), device=x.device, dtype=torch.int32)
+            zs.append(z)
+            idxs.append(idx)
+            items.append((_ptr(x), N, T, H, W, _ptr(z), _ptr(idx), v))
+        L.tok_encode_batch(self.ctx, items, _stream_ptr(stream))
+        return zs, idxs
+
+    def decode_batch(self, idxs, sizes, videos=None, first_chunks=None, stream=None):
+        """Decode several token tensors in one grouped pass; ``sizes[i]`` = (H, W)."""
+        videos = videos or [None] * len(idxs)
+        first_chunks = first_chunks or [None] * len(idxs)
+        outs, items = [], []
+        for idx, (H, W), v, f in zip(idxs, sizes, videos, first_chunks):
+            N, Tq, Hq, Wq = idx.shape
+            T = (1 if f else self.s_t) if v is not None else 1 + (Tq - 1) * self.s_t
+            out = torch.empty((N, T, H, W, 3), device=idx.device, dtype=torch.float32)
+            outs.append(out)
+            items.append((_ptr(idx), N, Tq, Hq, Wq, H, W, _ptr(out), v))
+        L.tok_decode_batch(self.ctx, items, _stream_ptr(stream))
+        return outs
+
     # -- streaming -----------------------------------------------------------
     def stream_bytes(self, H, W) -> int:
         return L.tok_stream_bytes(self.ctx, H, W)
