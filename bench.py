@@ -242,6 +242,8 @@ def gpu_arm(args):
     tk.close()
     if not args.no_train:
         out["training"] = training(args, params)
+    if not args.no_group:
+        out["grouped"] = grouped(args, params, roofline["peak"])
     if not args.no_serve:
         cap = value / world * args.H * args.W * 3.94e6  # algorithmic FLOP/s one GPU sustains
         out["serving"] = serving(args, params, cap, rank, world)
@@ -292,6 +294,76 @@ def training(args, params, N=2, T=17, H=256, W=256, steps=5, warmup=2):
             "steps": steps, "warmup": warmup}
 
 
+# ------------------------------------------------------------- grouped
+
+GROUP_RES = [(360, 640), (480, 854), (720, 1280), (1080, 1920)]
+
+
+def grouped(args, params, peak_tflops, steps=3, warmup=2, T=17):
+    """One grouped forward (encode + decode) over four 17-frame clips at 360p, 480p,
+    720p and 1080p: every conv of a layer is one tensor-core launch over the four
+    clips. Timed beside the same four clips run one after another."""
+    import torch
+
+    import paper_2602_03529_b300 as P
+    import synthetic as S
+
+    tk = P.Tokenizer("bf16")
+    tk.set_params(params)
+    shapes = [(1, T, h, w) for h, w in GROUP_RES]
+    tk.reserve_batch(shapes)
+    xs = [torch.from_numpy(S.to_bf16_f32(S.moving_rects_clip(i, T, h, w)[None])).to("cuda", torch.bfloat16)
+          for i, (h, w) in enumerate(GROUP_RES)]
+    flush = torch.empty(256 << 20, device="cuda", dtype=torch.uint8)
+
+    def batch():
+        _, ids = tk.encode_batch(xs, want_z=False)
+        return tk.decode_batch(ids, GROUP_RES)
+
+    def single():
+        for x, (h, w) in zip(xs, GROUP_RES):
+            _, idx = tk.encode(x, want_z=False)
+            tk.decode(idx, h, w)
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        ms = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+        return ms / steps
+
+    l0 = tk.launch_count()
+    batch()
+    launches = tk.launch_count() - l0
+    batch_ms = timed(batch)
+    single_ms = timed(single)
+    tk.profile(True)
+    tk.profile_read()
+    batch()
+    torch.cuda.synchronize()
+    prof = tk.profile_read()
+    tk.profile(False)
+    assert tk.status() == 0, "device-side error in the grouped forward"
+    tk.close()
+    frames = T * len(GROUP_RES)
+    conv_tf = prof["conv_flop"] / (prof["conv_ms"] / 1e3) / 1e12 if prof["conv_ms"] > 0 else None
+    return {"workload": "encode + decode of 4 clips x 17 frames at 360x640, 480x854, 720x1280, 1080x1920 "
+                        "(moving rectangles over smooth noise), BF16, one grouped launch per layer",
+            "ms": batch_ms, "frames_per_s": frames / (batch_ms / 1e3), "launches": launches,
+            "conv_tflop": prof["conv_flop"] / 1e12, "conv_ms": prof["conv_ms"],
+            "conv_tflops": conv_tf, "conv_frac": (conv_tf / peak_tflops) if conv_tf else None,
+            "peak_tflops": peak_tflops, "sequential_ms": single_ms,
+            "speedup_vs_sequential": single_ms / batch_ms, "steps": steps, "warmup": warmup}
+
+
 # ------------------------------------------------------------- serving
 
 SERVE_RES = [(480, 854), (720, 1280), (1080, 1920)]
@@ -320,19 +392,31 @@ def serving(args, params, capacity_flops, rank, world):
         return torch.roll(clips[((spec.H, spec.W), spec.sid % 2)], shifts=spec.sid % 9, dims=0)
 
     slots = {SERVE_RES[0]: 8, SERVE_RES[1]: 8, SERVE_RES[2]: 4}
-    ex = GpuExecutor(args.serve_lanes, params, slots, content_fn=content)
+    mb = args.serve_batch
+    ex = GpuExecutor(args.serve_lanes, params, slots, content_fn=content, max_batch=mb, priorities=True)
     budget = args.serve_load * capacity_flops
-    # warm-up: every lane, every resolution
-    warm = [StreamSpec(10_000 + i, *SERVE_RES[i % 3], start=0.0, n_chunks=2) for i in range(6)]
-    Server(ex, args.serve_lanes, slots, 1e30, stall_timeout=5.0).run(warm, horizon=1.0)
+
+    # chunk time of each resolution alone on the urgent lane, with 25% for sharing the GPU
+    alone = ex.calibrate()
+
+    def service_time(spec):
+        return 1.25 * alone[(spec.H, spec.W)]
+
+    # warm-up: every lane, every resolution, batches of every size
+    warm = [StreamSpec(10_000 + i, *SERVE_RES[i % 3], start=0.0, n_chunks=2) for i in range(12)]
+    Server(ex, args.serve_lanes, slots, 1e30, stall_timeout=5.0, max_batch=mb).run(warm, horizon=1.0)
     torch.cuda.synchronize()
-    rep = Server(ex, args.serve_lanes, slots, budget, target_latency=0.033, stall_timeout=1.0).run(
+    rep = Server(ex, args.serve_lanes, slots, budget, target_latency=0.033, stall_timeout=1.0,
+                 service_time=service_time, max_batch=mb, align_phases=not args.serve_no_align).run(
         mine, horizon=args.serve_horizon)
     torch.cuda.synchronize()
     assert all(s == 0 for s in ex.status()), "device-side error while serving"
     ex.close()
     rep.pop("admission_wait_s", None)  # per-stream detail; the p50 stays
-    rep.update({"lanes": args.serve_lanes, "slots": {f"{h}x{w}": k for (h, w), k in slots.items()},
+    rep.update({"lanes": args.serve_lanes, "max_batch": mb, "phase_aligned": not args.serve_no_align,
+                "urgent": {f"{h}x{w}": service_time(StreamSpec(0, h, w, 0.0, 1)) <= 0.033 for h, w in SERVE_RES},
+                "service_ms": {f"{h}x{w}": 1e3 * service_time(StreamSpec(0, h, w, 0.0, 1)) for h, w in SERVE_RES},
+                "slots": {f"{h}x{w}": k for (h, w), k in slots.items()},
                 "budget_tflops": budget / 1e12, "load_factor": args.serve_load,
                 "stream_chunks": args.serve_chunks, "arrival_horizon_s": args.serve_horizon,
                 "drop_rate": "U[0, 0.30] per chunk", "target_ms": 33.0})
@@ -402,11 +486,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-train", action="store_true")
+    ap.add_argument("--no-group", action="store_true")
     ap.add_argument("--serve-streams", type=int, default=64)
     ap.add_argument("--serve-horizon", type=float, default=20.0)
     ap.add_argument("--serve-chunks", type=int, default=16)
     ap.add_argument("--serve-lanes", type=int, default=2)
     ap.add_argument("--serve-load", type=float, default=0.6)
+    ap.add_argument("--serve-batch", type=int, default=4)
+    ap.add_argument("--serve-no-align", action="store_true")
     args = ap.parse_args()
     out = reference_arm(args) if args.impl == "reference" else gpu_arm(args)
     if out is not None:

@@ -132,6 +132,15 @@ int tok_encode(tok_ctx* ctx, const void* d_x, int N, int T, int H, int W,
 int tok_decode(tok_ctx* ctx, const int32_t* d_idx, int N, int Tq, int Hq, int Wq,
                int H, int W, float* d_xhat, tok_stream* s, void* stream);
 
+/* Lifetime of the conv CTAs of this context's tok_encode / tok_decode
+ * launches: 0 (default) one persistent CTA per SM that loops over all tiles
+ * of a layer; n > 0 at most n output tiles per CTA. A context whose work runs
+ * on a low-priority CUDA stream beside latency-critical work on a
+ * high-priority stream sets a small n, so that the critical kernels get SMs
+ * as soon as a short CTA ends rather than after a whole layer. Results do
+ * not depend on n. Not in the paper: a serving control. */
+int tok_set_cta_tiles(tok_ctx* ctx, int tiles);
+
 /* Grouped encode / decode (one launch per layer over several inputs).
  * A batch holds 1 .. TOK_MAX_BATCH items of any sizes: whole clips, chunks of
  * streams (each stream at most once per batch), or both. Every convolution

@@ -80,6 +80,7 @@ _SIGS = {
     "tok_latent_shape": (i32, [vp, i32, i32, i32, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32)]),
     "tok_encode": (i32, [vp, vp, i32, i32, i32, i32, vp, vp, vp, vp]),
     "tok_decode": (i32, [vp, vp, i32, i32, i32, i32, i32, i32, vp, vp, vp]),
+    "tok_set_cta_tiles": (i32, [vp, i32]),
     "tok_batch_workspace_bytes": (sz, [vp, C.POINTER(tok_shape), i32]),
     "tok_reserve_batch": (i32, [vp, C.POINTER(tok_shape), i32]),
     "tok_encode_batch": (i32, [vp, C.POINTER(tok_enc_item), i32, vp]),
@@ -206,6 +207,10 @@ def tok_encode(ctx, x_ptr, N, T, H, W, z_ptr, idx_ptr, stream_handle, cuda_strea
 def tok_decode(ctx, idx_ptr, N, Tq, Hq, Wq, H, W, xhat_ptr, stream_handle, cuda_stream) -> None:
     _ck(_call("tok_decode", ctx, idx_ptr, N, Tq, Hq, Wq, H, W, xhat_ptr, stream_handle, cuda_stream),
         "tok_decode")
+
+
+def tok_set_cta_tiles(ctx, tiles: int) -> None:
+    _ck(_call("tok_set_cta_tiles", ctx, tiles), "tok_set_cta_tiles")
 
 
 def _shapes(shapes):

@@ -428,7 +428,7 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
 }
 
 template <int BN, bool SWAP, int MAXP>
-int launch_bn(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, cudaStream_t stream) {
+int launch_bn(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int cta_tiles, cudaStream_t stream) {
     using C = Cfg<BN, SWAP>;
     TcBatch<MAXP> B;
     memset(&B, 0, sizeof(B));
@@ -460,15 +460,17 @@ int launch_bn(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, cudaS
         cudaFuncSetAttribute(conv_tc_kernel<BN, SWAP, MAXP>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
         attr_set = true;
     }
-    const int grid = (int)std::min<long long>(total, num_sms);
-    conv_tc_kernel<BN, SWAP, MAXP><<<grid, 192, C::SMEM, stream>>>(B);
+    // persistent (one CTA per SM), or CTAs of at most cta_tiles tiles each
+    long long grid = std::min<long long>(total, num_sms);
+    if (cta_tiles > 0) grid = std::max(grid, std::min<long long>((total + cta_tiles - 1) / cta_tiles, 1LL << 30));
+    conv_tc_kernel<BN, SWAP, MAXP><<<(unsigned)grid, 192, C::SMEM, stream>>>(B);
     return (int)cudaGetLastError();
 }
 
 template <int BN, bool SWAP>
-int launch_bn_any(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, cudaStream_t stream) {
-    return count == 1 ? launch_bn<BN, SWAP, 1>(as, gs, 1, num_sms, stream)
-                      : launch_bn<BN, SWAP, kMaxConvGroup>(as, gs, count, num_sms, stream);
+int launch_bn_any(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int cta_tiles, cudaStream_t stream) {
+    return count == 1 ? launch_bn<BN, SWAP, 1>(as, gs, 1, num_sms, cta_tiles, stream)
+                      : launch_bn<BN, SWAP, kMaxConvGroup>(as, gs, count, num_sms, cta_tiles, stream);
 }
 
 }  // namespace
@@ -556,8 +558,11 @@ int conv_tc_bn(int Cout_pad) {
 // multiple of the chosen BN, Kpad = taps * Cin, strided convs have
 // sh == sw == 2 with even Hin and Win, bf16 tensors 16-byte aligned.
 // A group shares the layer: weights, Cin, Cout, kernel, strides and epilogue
-// mode; inputs, outputs, sizes and histories are per problem.
-int launch_conv_tc_group(const ConvArgs* as, int count, int num_sms, cudaStream_t stream) {
+// mode; inputs, outputs, sizes and histories are per problem. cta_tiles = 0
+// launches one persistent CTA per SM; n > 0 gives every CTA at most n tiles,
+// so that a kernel on a higher-priority CUDA stream gets SMs within one short
+// CTA lifetime instead of after the whole layer.
+int launch_conv_tc_group(const ConvArgs* as, int count, int num_sms, cudaStream_t stream, int cta_tiles) {
     if (count < 1 || count > kMaxConvGroup) return -1;
     const ConvArgs& a0 = as[0];
     for (int p = 1; p < count; ++p)
@@ -580,18 +585,18 @@ int launch_conv_tc_group(const ConvArgs* as, int count, int num_sms, cudaStream_
         g.n_tiles = 0;
         g.num_tiles = 0;
     }
-    if (swap) return launch_bn_any<128, true>(as, gs, count, num_sms, stream);
+    if (swap) return launch_bn_any<128, true>(as, gs, count, num_sms, cta_tiles, stream);
     switch (conv_tc_bn(a0.Cout_pad)) {
-        case 256: return launch_bn_any<256, false>(as, gs, count, num_sms, stream);
-        case 128: return launch_bn_any<128, false>(as, gs, count, num_sms, stream);
-        case 64: return launch_bn_any<64, false>(as, gs, count, num_sms, stream);
-        case 32: return launch_bn_any<32, false>(as, gs, count, num_sms, stream);
-        default: return launch_bn_any<16, false>(as, gs, count, num_sms, stream);
+        case 256: return launch_bn_any<256, false>(as, gs, count, num_sms, cta_tiles, stream);
+        case 128: return launch_bn_any<128, false>(as, gs, count, num_sms, cta_tiles, stream);
+        case 64: return launch_bn_any<64, false>(as, gs, count, num_sms, cta_tiles, stream);
+        case 32: return launch_bn_any<32, false>(as, gs, count, num_sms, cta_tiles, stream);
+        default: return launch_bn_any<16, false>(as, gs, count, num_sms, cta_tiles, stream);
     }
 }
 
 int launch_conv_tc(const ConvArgs& a, int num_sms, cudaStream_t stream) {
-    return launch_conv_tc_group(&a, 1, num_sms, stream);
+    return launch_conv_tc_group(&a, 1, num_sms, stream, 0);
 }
 
 }  // namespace tok

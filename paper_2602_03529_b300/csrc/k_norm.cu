@@ -10,6 +10,7 @@
 //                 fixed order into mean and 1/sqrt(var + eps).
 //   gn_apply    : SiLU((x - mean) * rstd * gamma + beta), 16-byte vectors.
 // The causal tokenizer may not mix frames, hence statistics per frame.
+#include <algorithm>
 #include <cstring>
 
 #include "common.cuh"
@@ -240,18 +241,17 @@ __global__ void __launch_bounds__(NT) gn_apply_kernel(const __grid_constant__ Gn
     }
 }
 
-// The chunking of a frame depends on the frame's size only (about 64 chunks
-// per frame), never on how many frames the launch holds, so that a frame's
-// statistics are summed in the same order whether it is normalised as part of
-// a whole clip or of a streaming chunk.
+// A block covers NT x 16 vectors of one frame (64 KB of BF16): the number of
+// chunks of a frame grows with the frame's size and never depends on how many
+// frames the launch holds, so a frame's statistics are summed in the same
+// order whether it is normalised as part of a whole clip or of a streaming
+// chunk, and a 4-frame chunk still fills the GPU with blocks.
+constexpr int GN_VPT = 16;
 void gn_plan(long long frames, long long vec_per_frame, int num_sms, int* vpt, int* S) {
     (void)frames;
     (void)num_sms;
-    long long v = (vec_per_frame + (long long)NT * 64 - 1) / ((long long)NT * 64);
-    if (v < 1) v = 1;
-    if (v > 256) v = 256;
-    *vpt = (int)v;
-    *S = (int)((vec_per_frame + (long long)NT * v - 1) / ((long long)NT * v));
+    *vpt = GN_VPT;
+    *S = (int)std::max<long long>(1, (vec_per_frame + (long long)NT * GN_VPT - 1) / ((long long)NT * GN_VPT));
 }
 
 }  // namespace

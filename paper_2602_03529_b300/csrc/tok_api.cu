@@ -303,6 +303,12 @@ int tok_decode_batch(tok_ctx* c, const tok_dec_item* items, int count, void* str
     return ex.err;
 }
 
+int tok_set_cta_tiles(tok_ctx* c, int tiles) {
+    if (!c || tiles < 0) return TOK_EINVAL;
+    c->cta_tiles = tiles;
+    return TOK_OK;
+}
+
 int tok_encode(tok_ctx* c, const void* x, int N, int T, int H, int W, float* z, int32_t* idx, tok_stream* st,
                void* stream) {
     if (!c || !x || N < 1 || T < 1 || H < 1 || W < 1) return TOK_EINVAL;

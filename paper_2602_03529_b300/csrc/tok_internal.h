@@ -65,6 +65,7 @@ struct tok_ctx {
     tok_arch arch;
     int precision;
     int device = 0, num_sms = 148;
+    int cta_tiles = 0;  // conv launches: 0 persistent, n > 0 at most n tiles per CTA
     std::vector<ParamInfo> params;
     std::map<std::string, int> pindex;
     std::vector<std::vector<float>> host;

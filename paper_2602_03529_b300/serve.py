@@ -9,10 +9,28 @@ minus the time its last frame arrived.
 
 Scheduling:
   * lanes: L executors (tokenizer contexts with their own workspace and CUDA
-    stream). A lane runs one chunk at a time; chunks of different streams on
-    different lanes overlap on the GPU. Requests that arrive while others run
-    take a lane as soon as one frees up (continuous batching), never waiting
-    for a "batch" to fill.
+    stream). A lane runs one batch at a time: up to `max_batch` chunks of
+    different streams in one grouped pass (one conv launch per layer over all
+    of them); chunks on different lanes overlap on the GPU. Requests that
+    arrive while others run take a lane as soon as one frees up (continuous
+    batching), never waiting for a batch to fill.
+  * priority classes (when a per-chunk service-time estimate is given): a
+    chunk that can meet the latency target on its own is urgent; the others
+    (a resolution too large for the target) are background. Lane 0 runs
+    urgent chunks only, on the highest-priority CUDA stream, so an urgent
+    chunk waits at most for one background kernel, never for a whole
+    background chunk; it batches urgent chunks only while the batch still
+    meets every member's deadline. The other lanes run background chunks at
+    low priority. Without an estimate every lane takes any chunk.
+  * phase alignment (`align_phases`): urgent streams are periodic (a chunk
+    every 4/fps s), and a stream's source starts sending when the server
+    admits it, so admission may choose the start within one period: the
+    earliest offset whose chunk window [offset, offset + service) does not
+    overlap the windows of the urgent streams already admitted (modulo the
+    period). An urgent stream for which no such window exists waits for
+    admission, like one that finds no free slot. The offset is part of the
+    reported admission wait; chunk latencies are still counted from each
+    chunk's last frame.
   * admission: a stream is admitted when a cache slot of its resolution is
     free (memory: tok_stream_bytes per slot, preallocated) and its compute
     demand (FLOP/s at its frame rate) fits the compute budget; otherwise it
@@ -65,14 +83,23 @@ class StreamState:
     done: bool = False
     timed_out: bool = False
     latencies: list = dataclasses.field(default_factory=list)
+    waits: list = dataclasses.field(default_factory=list)   # ready -> dispatched
+    runs: list = dataclasses.field(default_factory=list)    # dispatched -> done
 
 
 class Server:
     def __init__(self, executor, n_lanes: int, slots_per_res: dict, budget_flops: float,
                  target_latency: float = 0.033, stall_timeout: float = 0.5,
-                 clock: Callable[[], float] | None = None, sleep: Callable[[float], None] | None = None):
+                 clock: Callable[[], float] | None = None, sleep: Callable[[float], None] | None = None,
+                 service_time: Callable[[StreamSpec], float] | None = None, max_batch: int = 1,
+                 align_phases: bool = False, guard_s: float = 0.002):
         self.ex = executor
         self.n_lanes = n_lanes
+        self.service_time = service_time
+        self.max_batch = max(1, max_batch)
+        self.align = align_phases and service_time is not None
+        self.guard = guard_s
+        self.windows: dict[int, tuple[float, float, float]] = {}  # sid -> (start, length, period)
         self.free_slots = {res: list(range(n)) for res, n in slots_per_res.items()}
         self.budget = budget_flops
         self.target = target_latency
@@ -88,7 +115,7 @@ class Server:
         ai = 0
         waiting: list[StreamState] = []
         active: list[StreamState] = []
-        lanes: list = [None] * self.n_lanes      # (state, chunk, ready_t) or None
+        lanes: list = [None] * self.n_lanes      # list of (state, chunk, ready_t) or None
         used = 0.0
         max_admitted = 0
         admitted_total = 0
@@ -96,17 +123,19 @@ class Server:
         while True:
             t = now()
             # 1. completions
-            for li, job in enumerate(lanes):
-                if job is None:
+            for li, jobs in enumerate(lanes):
+                if jobs is None or not self.ex.done(li):
                     continue
-                st, k, ready = job
-                if self.ex.done(li):
-                    st.latencies.append(now() - ready)
+                tdone = now()
+                for st, k, ready, tsub in jobs:
+                    st.latencies.append(tdone - ready)
+                    st.waits.append(tsub - ready)
+                    st.runs.append(tdone - tsub)
                     st.in_flight = False
                     st.next_chunk = k + 1
-                    lanes[li] = None
                     if st.next_chunk >= st.spec.n_chunks:
                         st.done = True
+                lanes[li] = None
             # 2. retire finished / stalled streams
             for st in list(active):
                 if st.in_flight:
@@ -117,6 +146,7 @@ class Server:
                     st.timed_out = stalled
                     st.done = True
                     active.remove(st)
+                    self.windows.pop(st.spec.sid, None)
                     used -= st.spec.demand_flops()
                     self.free_slots[(st.spec.H, st.spec.W)].append(st.slot)
                     self.ex.release(st.spec, st.slot)
@@ -129,10 +159,13 @@ class Server:
                 res = (st.spec.H, st.spec.W)
                 if not self.free_slots.get(res) or used + st.spec.demand_flops() > self.budget:
                     break
+                off = self._offset(st.spec, t)
+                if off is None:
+                    break
                 waiting.pop(0)
                 st.slot = self.free_slots[res].pop()
                 self.ex.attach(st.spec, st.slot)
-                st.admitted_at = t
+                st.admitted_at = t + off
                 used += st.spec.demand_flops()
                 active.append(st)
                 admitted_total += 1
@@ -148,12 +181,19 @@ class Server:
                 rt = st.spec.ready_time(k, st.admitted_at)
                 if rt <= t:
                     heapq.heappush(ready, (rt + self.target, st.spec.sid, st, k, rt))
+            ready.sort(key=lambda e: (e[0], e[1]))
             for li in range(self.n_lanes):
-                if lanes[li] is None and ready:
-                    _, _, st, k, rt = heapq.heappop(ready)
-                    st.in_flight = True
-                    lanes[li] = (st, k, rt)
-                    self.ex.submit(li, st.spec, st.slot, k)
+                if lanes[li] is not None or not ready:
+                    continue
+                batch = self._pick(li, ready, t)
+                if not batch:
+                    continue
+                picked = {id(e) for e in batch}
+                ready = [e for e in ready if id(e) not in picked]
+                for e in batch:
+                    e[2].in_flight = True
+                lanes[li] = [(e[2], e[3], e[4], t) for e in batch]
+                self.ex.submit(li, [(e[2].spec, e[2].slot, e[3]) for e in batch])
             # 5. termination
             idle = all(j is None for j in lanes)
             if ai >= len(arrivals) and not waiting and not active and idle:
@@ -165,12 +205,60 @@ class Server:
             self.sleep(poll_s)
         return self._report(states, max_admitted, admitted_total, now())
 
+    def _offset(self, spec, t) -> float | None:
+        """Start offset (s) of a newly admitted stream: 0 unless phases are aligned; then
+        the earliest offset in [0, period) whose window avoids every admitted urgent
+        stream's window, or None when there is none (the stream waits)."""
+        if not self.align or not self.urgent(spec):
+            return 0.0
+        period = 4.0 / spec.fps
+        d = self.service_time(spec) + self.guard
+
+        def clear(a0):
+            for b0, db, pb in self.windows.values():
+                if abs(pb - period) > 1e-9:
+                    continue
+                if (b0 - a0) % period < d or (a0 - b0) % period < db:
+                    return False
+            return True
+
+        cands = sorted({0.0} | {(b0 + db - t) % period for b0, db, _ in self.windows.values()})
+        off = next((c for c in cands if clear(t + c)), None)
+        if off is not None:
+            self.windows[spec.sid] = (t + off, d, period)
+        return off
+
+    def urgent(self, spec) -> bool:
+        """A chunk that can meet the latency target when it runs alone."""
+        return self.service_time is None or self.service_time(spec) <= self.target
+
+    def _pick(self, li, ready, t):
+        """Chunks (EDF-sorted entries of `ready`) for free lane li."""
+        if self.service_time is None or self.n_lanes == 1:
+            return ready[:self.max_batch]
+        if li == 0:
+            # urgent lane: EDF, batched only while every member still meets its deadline
+            batch, total = [], 0.0
+            for e in ready:
+                if not self.urgent(e[2].spec):
+                    continue
+                d = self.service_time(e[2].spec)
+                if batch and (len(batch) >= self.max_batch or t + total + d > min(x[0] for x in batch)):
+                    break
+                batch.append(e)
+                total += d
+            return batch
+        return [e for e in ready if not self.urgent(e[2].spec)][:self.max_batch]
+
     def _report(self, states, max_admitted, admitted_total, elapsed):
         import statistics as stats
         lat_all = [x for s in states.values() for x in s.latencies]
-        by_res = {}
+        by_res, waits, runs = {}, {}, {}
         for s in states.values():
-            by_res.setdefault(f"{s.spec.H}x{s.spec.W}", []).extend(s.latencies)
+            r = f"{s.spec.H}x{s.spec.W}"
+            by_res.setdefault(r, []).extend(s.latencies)
+            waits.setdefault(r, []).extend(s.waits)
+            runs.setdefault(r, []).extend(s.runs)
 
         def pct(v, q):
             if not v:
@@ -189,7 +277,14 @@ class Server:
             "p99_ms": 1e3 * pct(lat_all, 0.99) if lat_all else None,
             "mean_ms": 1e3 * stats.fmean(lat_all) if lat_all else None,
             "by_resolution": {r: {"chunks": len(v), "p50_ms": 1e3 * pct(v, 0.5) if v else None,
-                                  "p99_ms": 1e3 * pct(v, 0.99) if v else None} for r, v in by_res.items()},
+                                  "p90_ms": 1e3 * pct(v, 0.9) if v else None,
+                                  "p99_ms": 1e3 * pct(v, 0.99) if v else None,
+                                  "over_target": sum(1 for x in v if x > self.target),
+                                  "wait_p50_ms": 1e3 * pct(waits[r], 0.5) if waits[r] else None,
+                                  "wait_p99_ms": 1e3 * pct(waits[r], 0.99) if waits[r] else None,
+                                  "run_p50_ms": 1e3 * pct(runs[r], 0.5) if runs[r] else None,
+                                  "run_p99_ms": 1e3 * pct(runs[r], 0.99) if runs[r] else None}
+                              for r, v in by_res.items()},
             "admission_wait_s": {s.spec.sid: (s.admitted_at - s.spec.start) for s in states.values()
                                  if s.admitted_at is not None},
             "admission_wait_p50_s": pct([s.admitted_at - s.spec.start for s in states.values()
@@ -198,75 +293,121 @@ class Server:
 
 
 class GpuExecutor:
-    """Runs chunks through the CUDA library: one tokenizer context + CUDA stream per lane,
-    preallocated stream-cache slots per resolution, one content loop per stream."""
+    """Runs chunks through the CUDA library: one tokenizer context + CUDA stream per lane
+    (lane 0 on the highest stream priority when `priorities`), preallocated stream-cache
+    slots per resolution, one content loop per stream. A submitted batch is one grouped
+    encode, a drop mask per chunk and one grouped decode."""
 
     def __init__(self, n_lanes: int, params: dict, slots_per_res: dict, drop_seed: int = 1000,
                  drop_range=(0.0, 0.30), content_frames: int = 9, keep_outputs: bool = False,
-                 arch: dict | None = None, content_fn=None):
+                 arch: dict | None = None, content_fn=None, max_batch: int = 1, priorities: bool = False):
         import numpy as np
         import torch
 
+        from . import _lib
         from . import tokenizer as tkz
         self.torch = torch
         self.tkz = tkz
+        self.lib = _lib
         arch = arch or {}
         self.lanes = []
-        for _ in range(n_lanes):
+        for li in range(n_lanes):
             tk = tkz.Tokenizer("bf16", **arch)
             tk.set_params(params)
-            self.lanes.append({"tk": tk, "stream": torch.cuda.Stream(), "event": None, "bufs": {}})
+            # lower number = higher priority; out-of-range values map to the nearest valid one
+            prio = -100 if (priorities and li == 0) else 0
+            if priorities and li > 0:
+                tk.set_cta_tiles(1)  # background conv CTAs of one tile: SMs free up every few tens of us
+            self.lanes.append({"tk": tk, "stream": torch.cuda.Stream(priority=prio), "event": None})
         tk0 = self.lanes[0]["tk"]
         self.levels = tk0.levels
         self.s_t = tk0.s_t
         self.slots = {}
+        self.max_batch = max(1, max_batch)
+        big = max(slots_per_res, key=lambda r: r[0] * r[1])
+        for lane in self.lanes:
+            lane["tk"].reserve_batch([(1, self.s_t, *big)] * min(self.max_batch, sum(slots_per_res.values())))
         for (H, W), n in slots_per_res.items():
-            for lane in self.lanes:
-                lane["tk"].reserve(1, self.s_t, H, W)
             self.slots[(H, W)] = [tk0.stream_open(H, W) for _ in range(n)]
+        self.bufs = {}
         self.drop_seed = drop_seed
         self.drop_range = drop_range
         self.content_frames = content_frames
         self.content_fn = content_fn
         self.content = {}
+        self.content_ready = {}
+        self.side = torch.cuda.Stream()  # content preparation, off the lanes and off the host
         self.keep = keep_outputs
         self.outputs = {}
         self.tokens = {}
         self._np = np
 
     def _content(self, spec):
+        """The stream's source frames on the device, made on a side stream (an event marks
+        them ready; the lanes wait for it on the device, the host never blocks)."""
         key = spec.sid
         if key not in self.content:
-            if self.content_fn is not None:
-                clip = self.content_fn(spec)
-            else:
-                import synthetic as S
-                clip = S.moving_rects_clip(100 + spec.sid, self.content_frames, spec.H, spec.W)
-            if not isinstance(clip, self.torch.Tensor):
-                clip = self.torch.from_numpy(clip)
-            self.content[key] = clip.to("cuda", self.torch.bfloat16)
+            torch = self.torch
+            with torch.cuda.stream(self.side):
+                if self.content_fn is not None:
+                    clip = self.content_fn(spec)
+                else:
+                    import synthetic as S
+                    clip = S.moving_rects_clip(100 + spec.sid, self.content_frames, spec.H, spec.W)
+                if not isinstance(clip, torch.Tensor):
+                    clip = torch.from_numpy(clip)
+                clip = clip.to("cuda", torch.bfloat16, non_blocking=True)
+                ev = torch.cuda.Event()
+                ev.record(self.side)
+            self.content[key] = clip
+            self.content_ready[key] = ev
         return self.content[key]
 
     def attach(self, spec, slot):
         self._content(spec)
-        self.torch.cuda.current_stream().synchronize()  # content is on the device before lanes read it
         self.lanes[0]["tk"].stream_reset(self.slots[(spec.H, spec.W)][slot])
 
     def release(self, spec, slot):
         self.content.pop(spec.sid, None)
+        self.content_ready.pop(spec.sid, None)
 
-    def _bufs(self, lane, H, W):
-        key = (H, W)
-        if key not in lane["bufs"]:
+    def _bufs(self, H, W, slot):
+        """Token and output buffers of one stream slot (one chunk of a stream is in flight
+        at a time, so a slot's buffers are never shared by two running chunks)."""
+        key = (H, W, slot)
+        if key not in self.bufs:
             torch = self.torch
-            Tq, Hq, Wq = lane["tk"].latent_shape(1, H, W)
-            lane["bufs"][key] = {
+            Tq, Hq, Wq = self.lanes[0]["tk"].latent_shape(1, H, W)
+            self.bufs[key] = {
                 "idx": torch.empty((1, 1, Hq, Wq), device="cuda", dtype=torch.int32),
                 "idx_d": torch.empty((1, 1, Hq, Wq), device="cuda", dtype=torch.int32),
                 "kb": torch.empty((1, 1, Hq, (Wq + 31) // 32), device="cuda", dtype=torch.int32),
                 "xh": torch.empty((1, self.s_t, H, W, 3), device="cuda", dtype=torch.float32),
+                "xh1": torch.empty((1, 1, H, W, 3), device="cuda", dtype=torch.float32),
             }
-        return lane["bufs"][key]
+        return self.bufs[key]
+
+    def calibrate(self, reps: int = 5) -> dict:
+        """Seconds one chunk of each slot resolution takes alone on lane 0 (median of
+        `reps` steady-state chunks through a stream slot, which is reset afterwards)."""
+        torch = self.torch
+        out = {}
+        for (H, W) in self.slots:
+            spec = StreamSpec(-1 - len(out), H, W, 0.0, reps + 1)
+            self.attach(spec, 0)
+            times = []
+            for k in range(reps + 1):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(self.lanes[0]["stream"])
+                self.submit(0, [(spec, 0, k)])
+                e1.record(self.lanes[0]["stream"])
+                e1.synchronize()
+                if k > 0:
+                    times.append(e0.elapsed_time(e1) / 1e3)
+            self.release(spec, 0)
+            self.lanes[0]["tk"].stream_reset(self.slots[(H, W)][0])
+            out[(H, W)] = sorted(times)[len(times) // 2]
+        return out
 
     def chunk_frames(self, spec, k):
         clip = self._content(spec)
@@ -277,28 +418,41 @@ class GpuExecutor:
             ids = [(4 * k - 3 + i) % n for i in range(4)]
         return clip[ids][None].contiguous()
 
-    def submit(self, li, spec, slot, k):
+    def submit(self, li, jobs):
+        """jobs: list of (spec, slot, chunk index) of distinct streams, run as one batch."""
         torch = self.torch
         lane = self.lanes[li]
         tk = lane["tk"]
-        vid = self.slots[(spec.H, spec.W)][slot]
-        b = self._bufs(lane, spec.H, spec.W)
-        rate = float(self._np.random.default_rng([self.drop_seed + spec.sid, k]).uniform(*self.drop_range))
-        with torch.cuda.stream(lane["stream"]):
-            x = self.chunk_frames(spec, k)
-            tk.encode(x, idx=b["idx"], want_z=False, video=vid, stream=lane["stream"])
-            self.tkz.drop_mask(b["idx"], rate, seed=self.drop_seed + spec.sid, stream_id=spec.sid, chunk_id=k,
-                               levels=self.levels, out=b["idx_d"], keep_bits=b["kb"], stream=lane["stream"])
-            T = 1 if k == 0 else self.s_t
-            xh = b["xh"][:, :T]
-            tk.decode(b["idx_d"], spec.H, spec.W, out=xh if T == self.s_t else b["xh"][:, :1].contiguous(),
-                      video=vid, first_chunk=(k == 0), stream=lane["stream"])
+        st = lane["stream"]
+        L = self.lib
+        with torch.cuda.stream(st):
+            enc, dec, drops = [], [], []
+            for spec, _, _ in jobs:
+                self._content(spec)
+                st.wait_event(self.content_ready[spec.sid])
+            for spec, slot, k in jobs:
+                vid = self.slots[(spec.H, spec.W)][slot]
+                b = self._bufs(spec.H, spec.W, slot)
+                x = self.chunk_frames(spec, k)
+                b["x"] = x  # keep the chunk alive until the batch has run
+                T = x.shape[1]
+                enc.append((x.data_ptr(), 1, T, spec.H, spec.W, None, b["idx"].data_ptr(), vid))
+                Tq, Hq, Wq = b["idx"].shape[1:]
+                xh = b["xh"] if k > 0 else b["xh1"]
+                dec.append((b["idx_d"].data_ptr(), 1, Tq, Hq, Wq, spec.H, spec.W, xh.data_ptr(), vid))
+                drops.append((spec, k, b))
+            L.tok_encode_batch(tk.ctx, enc, st.cuda_stream)
+            for spec, k, b in drops:
+                rate = float(self._np.random.default_rng([self.drop_seed + spec.sid, k]).uniform(*self.drop_range))
+                self.tkz.drop_mask(b["idx"], rate, seed=self.drop_seed + spec.sid, stream_id=spec.sid, chunk_id=k,
+                                   levels=self.levels, out=b["idx_d"], keep_bits=b["kb"], stream=st)
+            L.tok_decode_batch(tk.ctx, dec, st.cuda_stream)
             if self.keep:
-                out = b["xh"][:, :T].clone()
-                self.outputs.setdefault(spec.sid, []).append(out)
-                self.tokens.setdefault(spec.sid, []).append(b["idx_d"].clone())
+                for spec, k, b in drops:
+                    self.outputs.setdefault(spec.sid, []).append((b["xh"] if k > 0 else b["xh1"]).clone())
+                    self.tokens.setdefault(spec.sid, []).append(b["idx_d"].clone())
             ev = torch.cuda.Event()
-            ev.record(lane["stream"])
+            ev.record(st)
         lane["event"] = ev
 
     def done(self, li):

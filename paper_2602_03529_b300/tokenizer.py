@@ -131,6 +131,11 @@ class Tokenizer:
         L.tok_decode(self.ctx, _ptr(idx), N, Tq, Hq, Wq, H, W, _ptr(out), video, _stream_ptr(stream))
         return out
 
+    def set_cta_tiles(self, tiles: int):
+        """0: persistent conv CTAs; n > 0: at most n tiles per CTA (yields SMs quickly to
+        work on higher-priority CUDA streams; results are unchanged)."""
+        L.tok_set_cta_tiles(self.ctx, tiles)
+
     # -- grouped (one launch per layer over several inputs) --------------------
     def reserve_batch(self, shapes):
         """shapes: list of (N, T, H, W); a stream chunk counts as (1, s_T, H, W)."""

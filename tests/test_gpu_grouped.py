@@ -150,3 +150,22 @@ def test_batch_argument_errors(P):
     assert tk.status() == 0
     tk.stream_close(v)
     tk.close()
+
+
+@pytest.mark.parametrize("tiles", [1, 3])
+def test_short_lived_ctas_give_the_same_result(P, tiles):
+    """Conv CTAs of at most `tiles` tiles (a context that yields SMs to higher-priority
+    work) compute every tile exactly as the persistent CTAs do."""
+    tk = _tok(P, "bf16")
+    xs = _clips("bf16", SHAPES[:2])
+    tk.reserve_batch(SHAPES[:2])
+    zr, ir = tk.encode_batch(xs)
+    xr = tk.decode_batch(ir, [(H, W) for (_, _, H, W) in SHAPES[:2]])
+    tk.set_cta_tiles(tiles)
+    zt, it = tk.encode_batch(xs)
+    xt = tk.decode_batch(it, [(H, W) for (_, _, H, W) in SHAPES[:2]])
+    torch.cuda.synchronize()
+    assert tk.status() == 0
+    for a, b in zip(zr + ir + xr, zt + it + xt):
+        assert torch.equal(a, b)
+    tk.close()

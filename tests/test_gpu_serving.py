@@ -1,6 +1,8 @@
 """The streaming server on the GPU: continuous batching over several lanes with
-chunks of different streams in flight together, and every stream's tokens and
-decoded frames bitwise the same when it is served alone and in the mix."""
+chunks of different streams in flight together (and, in the second form,
+grouped into one launch per layer, with an urgent lane on the highest stream
+priority), and every stream's tokens and decoded frames bitwise the same when
+it is served alone and in the mix."""
 import pytest
 import torch
 
@@ -11,11 +13,17 @@ ARCH = dict(ch=(64, 128, 256), blocks=1)
 RES = [(48, 64), (64, 96), (40, 56)]
 
 
-def _run(specs, lanes, params):
+def _svc(spec):
+    # pretend the 64x96 streams are too large for the target: background class
+    return 0.050 if (spec.H, spec.W) == RES[1] else 0.001
+
+
+def _run(specs, lanes, params, max_batch=1, classes=False):
     from paper_2602_03529_b300.serve import GpuExecutor, Server
     slots = {r: 2 for r in RES}
-    ex = GpuExecutor(lanes, params, slots, keep_outputs=True, arch=ARCH)
-    rep = Server(ex, lanes, slots, 1e30, stall_timeout=5.0).run(specs, horizon=2.0)
+    ex = GpuExecutor(lanes, params, slots, keep_outputs=True, arch=ARCH, max_batch=max_batch, priorities=classes)
+    rep = Server(ex, lanes, slots, 1e30, stall_timeout=5.0, service_time=_svc if classes else None,
+                 max_batch=max_batch).run(specs, horizon=2.0)
     torch.cuda.synchronize()
     assert all(s == 0 for s in ex.status())
     outs = {k: torch.cat(v, 1) for k, v in ex.outputs.items()}
@@ -24,14 +32,15 @@ def _run(specs, lanes, params):
     return rep, outs, toks
 
 
-def test_alone_equals_mix():
+@pytest.mark.parametrize("max_batch,classes", [(1, False), (3, True)])
+def test_alone_equals_mix(max_batch, classes):
     import paper_2602_03529_b300 as P
     from paper_2602_03529_b300.serve import StreamSpec
     tk = P.Tokenizer("bf16", **ARCH)
     params = S.weights_for(tk.param_spec(), seed=5)
     tk.close()
     specs = [StreamSpec(i, *RES[i % 3], start=0.004 * i, n_chunks=4) for i in range(6)]
-    rep, out_mix, tok_mix = _run(specs, 3, params)
+    rep, out_mix, tok_mix = _run(specs, 3 if not classes else 2, params, max_batch, classes)
     assert rep["chunks"] == 24 and rep["admitted_total"] == 6 and rep["timed_out"] == 0
     assert rep["max_concurrent"] >= 2
     for s in specs:

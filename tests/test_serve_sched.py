@@ -1,8 +1,9 @@
 """Host-side scheduling of the streaming server, on the CPU with a fake executor
 and a virtual clock: continuous admission as slots and compute free up,
-earliest-deadline-first dispatch, in-order chunks per stream, and the stall
-timeout that releases a stream whose source stopped (failure detection on the
-host, no GPU involved)."""
+earliest-deadline-first dispatch, in-order chunks per stream, urgent and
+background lanes, deadline-bounded batching, and the stall timeout that
+releases a stream whose source stopped (failure detection on the host, no GPU
+involved)."""
 from paper_2602_03529_b300.serve import Server, StreamSpec
 
 
@@ -18,12 +19,14 @@ class Clock:
 
 
 class FakeExec:
-    """Each chunk takes `dur[(H, W)]` seconds; lanes run in parallel."""
+    """Each chunk takes `dur[(H, W)]` seconds, a batch the sum of its chunks; lanes run
+    in parallel."""
 
     def __init__(self, clock, dur):
         self.clock, self.dur = clock, dur
         self.finish = {}
         self.log = []
+        self.batches = []
         self.attached = []
 
     def attach(self, spec, slot):
@@ -32,17 +35,20 @@ class FakeExec:
     def release(self, spec, slot):
         pass
 
-    def submit(self, li, spec, slot, k):
-        self.finish[li] = self.clock() + self.dur[(spec.H, spec.W)]
-        self.log.append((self.clock(), spec.sid, k, li))
+    def submit(self, li, jobs):
+        self.finish[li] = self.clock() + sum(self.dur[(spec.H, spec.W)] for spec, _, _ in jobs)
+        for spec, slot, k in jobs:
+            self.log.append((self.clock(), spec.sid, k, li))
+        self.batches.append((li, [spec.sid for spec, _, _ in jobs]))
 
     def done(self, li):
         return self.clock() >= self.finish.get(li, 0.0)
 
 
-def _server(clock, ex, lanes=2, slots=None, budget=1e30):
+def _server(clock, ex, lanes=2, slots=None, budget=1e30, service_time=None, max_batch=1, align=False):
     return Server(ex, lanes, slots or {(8, 8): 4}, budget, target_latency=0.033, stall_timeout=0.2,
-                  clock=clock, sleep=clock.sleep)
+                  clock=clock, sleep=clock.sleep, service_time=service_time, max_batch=max_batch,
+                  align_phases=align)
 
 
 def test_all_chunks_in_order_and_latency_alone():
@@ -95,3 +101,83 @@ def test_stalled_source_times_out_and_frees_its_slot():
     assert rep["admitted_total"] == 2           # the second stream got the freed slot
     assert [k for _, sid, k, _ in ex.log if sid == 0] == [0, 1]
     assert [k for _, sid, k, _ in ex.log if sid == 1] == [0, 1]
+
+
+def test_urgent_lane_takes_only_chunks_that_can_meet_the_target():
+    """Small streams (10 ms a chunk) are urgent and run on lane 0; large ones (50 ms,
+    above the 33 ms target) run on the background lane and never delay lane 0."""
+    c = Clock()
+    dur = {(8, 8): 0.010, (16, 16): 0.050}
+    ex = FakeExec(c, dur)
+    svc = lambda spec: dur[(spec.H, spec.W)]  # noqa: E731
+    specs = [StreamSpec(0, 16, 16, start=0.0, n_chunks=4), StreamSpec(1, 8, 8, start=0.001, n_chunks=4),
+             StreamSpec(2, 16, 16, start=0.002, n_chunks=4), StreamSpec(3, 8, 8, start=0.003, n_chunks=4)]
+    rep = _server(c, ex, lanes=2, slots={(8, 8): 2, (16, 16): 2}, service_time=svc, max_batch=4).run(
+        specs, horizon=2.0, poll_s=1e-3)
+    assert rep["chunks"] == 16
+    for _, sid, _, li in ex.log:
+        assert li == (0 if sid in (1, 3) else 1)
+    small = rep["by_resolution"]["8x8"]
+    assert small["p99_ms"] <= 33.0          # never queued behind a 50 ms chunk
+    assert rep["by_resolution"]["16x16"]["chunks"] == 8
+
+
+def test_urgent_batches_keep_every_deadline():
+    """Three urgent chunks ready together, 12 ms each: a batch of three would end at
+    36 ms, past the first deadline (33 ms), so lane 0 runs two, then one."""
+    c = Clock()
+    dur = {(8, 8): 0.012, (16, 16): 0.050}
+    ex = FakeExec(c, dur)
+    svc = lambda spec: dur[(spec.H, spec.W)]  # noqa: E731
+    specs = [StreamSpec(i, 8, 8, start=0.0, n_chunks=1) for i in range(3)]
+    _server(c, ex, lanes=2, slots={(8, 8): 3, (16, 16): 1}, service_time=svc, max_batch=8).run(
+        specs, horizon=1.0, poll_s=1e-3)
+    assert [len(b) for _, b in ex.batches] == [2, 1]
+    assert all(li == 0 for li, _ in ex.batches)
+
+
+def test_background_lane_batches_up_to_max_batch():
+    c = Clock()
+    dur = {(8, 8): 0.005, (16, 16): 0.050}
+    ex = FakeExec(c, dur)
+    svc = lambda spec: dur[(spec.H, spec.W)]  # noqa: E731
+    specs = [StreamSpec(i, 16, 16, start=0.0, n_chunks=1) for i in range(5)]
+    _server(c, ex, lanes=2, slots={(8, 8): 1, (16, 16): 5}, service_time=svc, max_batch=3).run(
+        specs, horizon=1.0, poll_s=1e-3)
+    assert [len(b) for _, b in ex.batches] == [3, 2]
+    assert all(li == 1 for li, _ in ex.batches)
+
+
+def test_phase_alignment_removes_collisions_between_urgent_streams():
+    """Four urgent streams of 20 ms chunks arriving together: unaligned, their chunks
+    queue behind each other on the urgent lane (up to 80 ms); aligned, each stream
+    starts in its own 20 ms window of the 133 ms period and no chunk waits."""
+    dur = {(8, 8): 0.020, (16, 16): 0.050}
+    svc = lambda spec: dur[(spec.H, spec.W)]  # noqa: E731
+    reps = {}
+    for align in (False, True):
+        c = Clock()
+        ex = FakeExec(c, dur)
+        specs = [StreamSpec(i, 8, 8, start=0.0005 * i, n_chunks=6) for i in range(4)]
+        reps[align] = _server(c, ex, lanes=2, slots={(8, 8): 4, (16, 16): 1}, service_time=svc,
+                              align=align).run(specs, horizon=3.0, poll_s=5e-4)
+    assert reps[False]["p99_ms"] > 60.0
+    assert reps[True]["p99_ms"] <= 22.0 and reps[True]["chunks"] == 24
+    waits = sorted(reps[True]["admission_wait_s"].values())
+    assert waits[-1] < 4 / 30.0                 # every offset is within one period
+    assert min(b - a for a, b in zip(waits, waits[1:])) >= 0.020   # disjoint windows
+
+
+def test_urgent_stream_without_a_free_window_waits_for_admission():
+    """Seven urgent streams of 20 ms chunks: only six disjoint 22 ms windows fit in
+    the 133 ms period, so the seventh waits until a stream retires."""
+    c = Clock()
+    dur = {(8, 8): 0.020, (16, 16): 0.050}
+    ex = FakeExec(c, dur)
+    svc = lambda spec: dur[(spec.H, spec.W)]  # noqa: E731
+    specs = [StreamSpec(i, 8, 8, start=0.0, n_chunks=3) for i in range(7)]
+    rep = _server(c, ex, lanes=2, slots={(8, 8): 7, (16, 16): 1}, service_time=svc, align=True).run(
+        specs, horizon=3.0, poll_s=5e-4)
+    assert rep["chunks"] == 21 and rep["p99_ms"] <= 22.0
+    waits = sorted(rep["admission_wait_s"].values())
+    assert waits[5] < 4 / 30.0 and waits[6] > 0.2   # the 7th waited for a retirement
