@@ -315,6 +315,105 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                 float* stg = epi + q * 16 * C::EPI_STRIDE;
                 const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * C::ACC_COLS);
                 const int j = lane >> 1, half = lane & 1;  // read-back role: voxel j, 16 channels
+                if (a.Cout <= 32) {
+                    // narrow layer (pixel head, latent head): only TMEM lanes 0..Cout-1 hold
+                    // channels, all in the warp of quarter 0; the others have nothing to store
+                    if (q == 0) {
+                        // layer and tile constants in registers, the lane's channel decomposed once
+                        const int Hout = a.Hout, Wout = a.Wout, BW = g.BW, BH = g.BH, mode = a.mode;
+                        const int oT = a.oT, oH = a.oH, oW = a.oW, oC = a.oC;
+                        const bool f32 = a.out_fp32 != 0, lane_ok = co < a.Cout;
+                        void* const out = a.out;
+                        const __nv_bfloat16* const resid = static_cast<const __nv_bfloat16*>(a.residual);
+                        int cc = 0, bb = 0, ot = tc.to, ch = co, rw = 1;
+                        if (mode == OUT_D2S) {
+                            const int sub = co / oC;
+                            ch = co - sub * oC;
+                            rw = a.rw;
+                            cc = sub % a.rw;
+                            bb = (sub / a.rw) % a.rh;
+                            ot = tc.to * a.rt + sub / (a.rw * a.rh) - a.drop_t;
+                        }
+                        const int rh = mode == OUT_D2S ? a.rh : 1;
+                        const bool t_ok = ot >= 0 && ot < oT;
+                        const long long fbase = ((long long)tc.n * oT + ot) * oH;
+#pragma unroll 1
+                        for (int c16 = 0; c16 < C::ROWS / 16; ++c16) {
+                            float v[16];
+                            tmem_ld16(tbase + (uint32_t)(c16 * 16), v);
+                            const int vv0 = c16 * 16;
+                            if (mode == OUT_FSQ) {
+                                // gather each voxel's nlev channels through the staging buffer
+#pragma unroll
+                                for (int i2 = 0; i2 < 16; ++i2) stg[i2 * C::EPI_STRIDE + lane] = v[i2] + bias;
+                                __syncwarp();
+                                if (lane < 16) {
+                                    const int vv = vv0 + lane;
+                                    const int ho = tc.th * BH + vv / BW, wo = tc.tw * BW + vv % BW;
+                                    if (ho < Hout && wo < Wout) {
+                                        const long long vox =
+                                            (((long long)tc.n * a.Tout + tc.to) * Hout + ho) * Wout + wo;
+                                        float* z = static_cast<float*>(out) + vox * a.fsq.nlev;
+                                        int idx = 0;
+#pragma unroll
+                                        for (int c = 0; c < 8; ++c) {
+                                            if (c < a.fsq.nlev) {
+                                                const float x = stg[lane * C::EPI_STRIDE + c];
+                                                z[c] = x;
+                                                const float b =
+                                                    tanhf(x + a.fsq.shift[c]) * a.fsq.half_l[c] - a.fsq.offset[c];
+                                                idx += ((int)rintf(b) + a.fsq.half_w[c]) * a.fsq.basis[c];
+                                            }
+                                        }
+                                        if (a.idx) a.idx[vox] = idx;
+                                    }
+                                }
+                                __syncwarp();
+                                continue;
+                            }
+                            if (!lane_ok || !t_ok) continue;
+                            if ((BW & 15) == 0) {
+                                // the 16 voxels lie in one tile row: one row base, stride rw * oC
+                                const int ho = tc.th * BH + vv0 / BW, wo0 = tc.tw * BW + vv0 % BW;
+                                const int oh = ho * rh + bb;
+                                if (ho >= Hout || oh >= oH) continue;
+                                const long long rowoff = (fbase + oh) * oW;
+                                const int nv = min(16, Wout - wo0);
+#pragma unroll
+                                for (int i2 = 0; i2 < 16; ++i2) {
+                                    const int ow = (wo0 + i2) * rw + cc;
+                                    if (i2 >= nv || ow >= oW) continue;
+                                    const long long off = (rowoff + ow) * oC + ch;
+                                    float x = v[i2] + bias;
+                                    if (resid) x += __bfloat162float(resid[off]);
+                                    if (f32)
+                                        static_cast<float*>(out)[off] = x;
+                                    else
+                                        static_cast<__nv_bfloat16*>(out)[off] = __float2bfloat16_rn(x);
+                                }
+                                continue;
+                            }
+#pragma unroll
+                            for (int i2 = 0; i2 < 16; ++i2) {
+                                const int vv = vv0 + i2;
+                                const int ho = tc.th * BH + vv / BW, wo = tc.tw * BW + vv % BW;
+                                const int oh = ho * rh + bb, ow = wo * rw + cc;
+                                if (ho >= Hout || wo >= Wout || oh >= oH || ow >= oW) continue;
+                                const long long off = ((fbase + oh) * oW + ow) * oC + ch;
+                                float x = v[i2] + bias;
+                                if (resid) x += __bfloat162float(resid[off]);
+                                if (f32)
+                                    static_cast<float*>(out)[off] = x;
+                                else
+                                    static_cast<__nv_bfloat16*>(out)[off] = __float2bfloat16_rn(x);
+                            }
+                        }
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&tempty[acc]);
+                    continue;
+                }
 #pragma unroll 1
                 for (int c16 = 0; c16 < C::ROWS / 16; ++c16) {
                     float v[16];
@@ -554,6 +653,15 @@ int conv_tc_bn(int Cout_pad) {
     return 16;
 }
 
+// Padded output channels of a BF16 conv's packed weights: layers of at most
+// 32 channels are padded to 128 and run in the swapped (weights as A) form.
+int conv_tc_cout_pad(int Cout) {
+    const int c16 = (Cout + 15) / 16 * 16;
+    if (c16 <= 32) return 128;
+    const int bn = conv_tc_bn(c16);
+    return (c16 + bn - 1) / bn * bn;
+}
+
 // Requirements (checked by the caller's plan): Cin % 64 == 0, Cout_pad a
 // multiple of the chosen BN, Kpad = taps * Cin, strided convs have
 // sh == sw == 2 with even Hin and Win, bf16 tensors 16-byte aligned.
@@ -570,8 +678,10 @@ int launch_conv_tc_group(const ConvArgs* as, int count, int num_sms, cudaStream_
             as[p].kt != a0.kt || as[p].kh != a0.kh || as[p].kw != a0.kw || as[p].sh != a0.sh || as[p].mode != a0.mode ||
             as[p].out_fp32 != a0.out_fp32)
             return -1;
-    // exactly 128 output channels, plain bf16 output: the wide (swapped) form
-    const bool swap = a0.mode == OUT_PLAIN && !a0.out_fp32 && a0.Cout == 128 && a0.Cout_pad == 128;
+    // the wide (swapped) form: exactly 128 output channels with plain bf16 output,
+    // or a narrow layer (at most 32 channels, weights padded to 128 rows)
+    const bool swap = a0.Cout_pad == 128 &&
+                      ((a0.mode == OUT_PLAIN && !a0.out_fp32 && a0.Cout == 128) || a0.Cout <= 32);
     TcGeo gs[kMaxConvGroup];
     for (int p = 0; p < count; ++p) {
         TcGeo& g = gs[p];

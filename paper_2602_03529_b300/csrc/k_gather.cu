@@ -117,6 +117,57 @@ __global__ void im2col_tokens_kernel(const int32_t* __restrict__ idx, const int3
     reinterpret_cast<uint4*>(A)[t] = o;
 }
 
+// Row-per-thread form of the pixel gather for the stem's shape (3x3x3 taps,
+// CIN channels, KQ 16-byte groups per row): each thread resolves a tap's
+// source once and emits its CIN values in order, so the register buffer
+// indices are compile-time; the block stages its rows in shared memory and
+// writes them out as contiguous 16-byte stores.
+constexpr int ROWS_PER_BLOCK = 128;
+
+template <int CIN, int KQ>
+__global__ void __launch_bounds__(ROWS_PER_BLOCK) im2col_rows_kernel(const __nv_bfloat16* __restrict__ src,
+                                                                     const __nv_bfloat16* __restrict__ hist,
+                                                                     GatherGeo g, __nv_bfloat16* __restrict__ A) {
+    __shared__ uint4 stage[ROWS_PER_BLOCK][KQ + 1];
+    const long long M = (long long)g.N * g.Tout * g.Hout * g.Wout;
+    const long long m0 = (long long)blockIdx.x * ROWS_PER_BLOCK;
+    const long long m = m0 + threadIdx.x;
+    if (m < M) {
+        long long mm = m;
+        const int wo = (int)(mm % g.Wout); mm /= g.Wout;
+        const int ho = (int)(mm % g.Hout); mm /= g.Hout;
+        const int to = (int)(mm % g.Tout);
+        const int n = (int)(mm / g.Tout);
+        float buf[KQ * 8];
+#pragma unroll
+        for (int tap = 0; tap < 27; ++tap) {
+            bool fh;
+            long long fr;
+            int hi, wi;
+            const bool ok = gather_src(g, n, to, ho, wo, tap, &fh, &fr, &hi, &wi);
+            const long long pix = ok ? (fr * g.H + hi) * g.W + wi : 0;
+            const __nv_bfloat16* s16 = fh ? hist : src;
+#pragma unroll
+            for (int c = 0; c < CIN; ++c) buf[tap * CIN + c] = ok ? __bfloat162float(s16[pix * CIN + c]) : 0.f;
+        }
+#pragma unroll
+        for (int k = 27 * CIN; k < KQ * 8; ++k) buf[k] = 0.f;
+#pragma unroll
+        for (int q = 0; q < KQ; ++q) {
+            uint4 o;
+            o.x = pack_bf16x2(buf[8 * q + 0], buf[8 * q + 1]);
+            o.y = pack_bf16x2(buf[8 * q + 2], buf[8 * q + 3]);
+            o.z = pack_bf16x2(buf[8 * q + 4], buf[8 * q + 5]);
+            o.w = pack_bf16x2(buf[8 * q + 6], buf[8 * q + 7]);
+            stage[threadIdx.x][q] = o;
+        }
+    }
+    __syncthreads();
+    uint4* out = reinterpret_cast<uint4*>(A) + m0 * KQ;
+    const long long rows = M - m0 < ROWS_PER_BLOCK ? M - m0 : ROWS_PER_BLOCK;
+    for (int i = threadIdx.x; i < rows * KQ; i += ROWS_PER_BLOCK) out[i] = stage[i / KQ][i % KQ];
+}
+
 template <typename T>
 __global__ void edge_pad_kernel(const T* __restrict__ x, long long frames, int H, int W, int Hp, int Wp, int C,
                                 T* __restrict__ y) {
@@ -149,19 +200,25 @@ inline unsigned blocks_for(long long n, int bs) { return (unsigned)((n + bs - 1)
 
 }  // namespace
 
+static bool taps27(const GatherGeo& g) { return g.kt == 3 && g.kh == 3 && g.kw == 3; }
+
 int launch_im2col_pixels(const __nv_bfloat16* x, const __nv_bfloat16* hist, const GatherGeo& g, __nv_bfloat16* A,
                          cudaStream_t s) {
-    const long long n = (long long)g.N * g.Tout * g.Hout * g.Wout * (g.Kpad / 8);
-    if (n <= 0) return 0;
-    im2col_pixels_kernel<<<blocks_for(n, 256), 256, 0, s>>>(x, hist, g, A);
+    const long long M = (long long)g.N * g.Tout * g.Hout * g.Wout;
+    if (M <= 0) return 0;
+    if (taps27(g) && g.Cin == 3 && g.Kpad == 128) {
+        im2col_rows_kernel<3, 16><<<blocks_for(M, ROWS_PER_BLOCK), ROWS_PER_BLOCK, 0, s>>>(x, hist, g, A);
+    } else {
+        im2col_pixels_kernel<<<blocks_for(M * (g.Kpad / 8), 256), 256, 0, s>>>(x, hist, g, A);
+    }
     return (int)cudaGetLastError();
 }
 
 int launch_im2col_tokens(const int32_t* idx, const int32_t* hist, const GatherGeo& g, const FsqConsts& f,
                          __nv_bfloat16* A, cudaStream_t s) {
-    const long long n = (long long)g.N * g.Tout * g.Hout * g.Wout * (g.Kpad / 8);
-    if (n <= 0) return 0;
-    im2col_tokens_kernel<<<blocks_for(n, 256), 256, 0, s>>>(idx, hist, g, f, A);
+    const long long M = (long long)g.N * g.Tout * g.Hout * g.Wout;
+    if (M <= 0) return 0;
+    im2col_tokens_kernel<<<blocks_for(M * (g.Kpad / 8), 256), 256, 0, s>>>(idx, hist, g, f, A);
     return (int)cudaGetLastError();
 }
 

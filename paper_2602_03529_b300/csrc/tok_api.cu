@@ -425,7 +425,7 @@ size_t tok_conv3d_workspace_bytes(int precision, int Cin, int Cout, int k) {
     const int taps = k * k * k;
     if (precision == TOK_BF16) {
         const int c16 = round_up(Cout, 16);
-        const int cp = round_up(c16, conv_tc_bn(c16));
+        const int cp = conv_tc_cout_pad(c16);
         return align256((size_t)cp * taps * Cin * 2);
     }
     return align256((size_t)round_up(Cout, 16) * round_up(taps * Cin, 8) * 4);
@@ -452,7 +452,7 @@ int tok_conv3d(int precision, const void* x, int N, int T, int H, int W, int Cin
     memset(&a, 0, sizeof(a));
     if (bf) {
         const int c16 = round_up(Cout, 16);
-        a.Cout_pad = round_up(c16, conv_tc_bn(c16));
+        a.Cout_pad = conv_tc_cout_pad(c16);
         a.Kpad = taps * Cin;
         if (launch_pack_weights<__nv_bfloat16>(w, Cout, taps * Cin, a.Cout_pad, a.Kpad,
                                                static_cast<__nv_bfloat16*>(ws), s))

@@ -148,7 +148,7 @@ void add_conv(tok_ctx* c, const std::string& name, int cout, int cin, int k, boo
         cw.im2col = (im2col_in || cin % 64 != 0) ? 1 : 0;
         cw.Kpad = cw.im2col ? round_up(taps * cin, 64) : taps * cin;
         const int c16 = round_up(cout, 16);
-        cw.Cout_pad = round_up(c16, conv_tc_bn(c16));
+        cw.Cout_pad = conv_tc_cout_pad(c16);
     } else {
         cw.im2col = 0;
         cw.Kpad = round_up(taps * cin, 8);

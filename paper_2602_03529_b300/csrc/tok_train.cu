@@ -46,7 +46,7 @@ int adj_cpad(const tok_ctx* c, int Cout) { return c->bf16() ? round_up(Cout, 64)
 int adj_rows(const tok_ctx* c, int Cin) {
     if (!c->bf16()) return round_up(Cin, 16);
     const int c16 = round_up(Cin, 16);
-    return round_up(c16, conv_tc_bn(c16));
+    return conv_tc_cout_pad(c16);
 }
 
 // Bump layout of the training workspace; base == nullptr only sizes it.
