@@ -36,6 +36,11 @@ LEVELS = (8, 8, 8, 5, 5, 5)
 FALLBACK_PEAKS = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}
 
 
+# ncu dram__bytes_read.sum + dram__bytes_write.sum over the conv launches of one
+# 1x3x17x720x1280 encode + decode (40.62 GB + 12.88 GB); re-measure when the conv kernel changes
+CONV_DRAM_BYTES_PER_STEP = 53.50e9
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -220,7 +225,10 @@ def gpu_arm(args):
         "frac": conv_tflops / peak,
         "peak_source": f"{peak_src} bf16_tflops_sustained (kernel inside a long step)",
         "frac_of_burst_peak": conv_tflops / float(peaks["bf16_tflops"]),
-        "traffic": None,
+        # DRAM bytes (read + write) of the 34 conv launches of one step, from the ncu
+        # capture summarised in profiles/conv_dram_tokenizer_720p_bf16.md (same kernels)
+        "traffic": CONV_DRAM_BYTES_PER_STEP, "traffic_unit": "bytes per step (34 launches)",
+        "traffic_algorithmic": 28.40e9,
         "flop_per_step": prof["conv_flop"] / args.steps, "launches_per_step": prof["conv_launches"] / args.steps,
         "conv_ms_per_step": prof["conv_ms"] / args.steps,
         "conv_share_of_step": prof["conv_ms"] / max(total_ms, 1e-9),
