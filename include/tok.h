@@ -141,6 +141,13 @@ int tok_decode(tok_ctx* ctx, const int32_t* d_idx, int N, int Tq, int Hq, int Wq
  * not depend on n. Not in the paper: a serving control. */
 int tok_set_cta_tiles(tok_ctx* ctx, int tiles);
 
+/* Whether this context's conv launches may run as clusters of two CTAs that
+ * share every weight box by TMA multicast (off by default: measured 3-4%
+ * slower, the conv mainloop is not held by L2 bandwidth for weights; used
+ * for layers with at least one wave of tiles and persistent CTAs). Results
+ * do not depend on it. Not in the paper: a performance control. */
+int tok_set_conv_pairs(tok_ctx* ctx, int on);
+
 /* Grouped encode / decode (one launch per layer over several inputs).
  * A batch holds 1 .. TOK_MAX_BATCH items of any sizes: whole clips, chunks of
  * streams (each stream at most once per batch), or both. Every convolution

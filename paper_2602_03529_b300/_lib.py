@@ -81,6 +81,7 @@ _SIGS = {
     "tok_encode": (i32, [vp, vp, i32, i32, i32, i32, vp, vp, vp, vp]),
     "tok_decode": (i32, [vp, vp, i32, i32, i32, i32, i32, i32, vp, vp, vp]),
     "tok_set_cta_tiles": (i32, [vp, i32]),
+    "tok_set_conv_pairs": (i32, [vp, i32]),
     "tok_batch_workspace_bytes": (sz, [vp, C.POINTER(tok_shape), i32]),
     "tok_reserve_batch": (i32, [vp, C.POINTER(tok_shape), i32]),
     "tok_encode_batch": (i32, [vp, C.POINTER(tok_enc_item), i32, vp]),
@@ -211,6 +212,10 @@ def tok_decode(ctx, idx_ptr, N, Tq, Hq, Wq, H, W, xhat_ptr, stream_handle, cuda_
 
 def tok_set_cta_tiles(ctx, tiles: int) -> None:
     _ck(_call("tok_set_cta_tiles", ctx, tiles), "tok_set_cta_tiles")
+
+
+def tok_set_conv_pairs(ctx, on: bool) -> None:
+    _ck(_call("tok_set_conv_pairs", ctx, 1 if on else 0), "tok_set_conv_pairs")
 
 
 def _shapes(shapes):

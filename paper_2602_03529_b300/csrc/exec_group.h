@@ -75,7 +75,7 @@ struct GroupExec : Exec {
                     (double)(cw.k * cw.k * cw.k) * cw.Cin;
         const int e = pbegin();
         if (c->bf16()) {
-            ck(launch_conv_tc_group(as, P, c->num_sms, s, c->cta_tiles));
+            ck(launch_conv_tc_group(as, P, c->num_sms, s, c->cta_tiles, c->conv_pairs != 0));
             c->launches += 1;
         } else {
             for (int p = 0; p < P; ++p) ck(launch_conv_simt(as[p], s));

@@ -42,12 +42,17 @@ struct TcGeo {
     int cpt;                 // 64-channel blocks per tap
     int nkb;                 // K blocks per tile = taps * cpt
     int strided;             // parity view (sh = sw = 2)
+    long long m_tiles;       // voxel tiles
 };
 
 // A grouped launch: up to MAXP inputs of one layer (clips or stream chunks of
 // different sizes), one weight tensor. Tiles are numbered problem after
 // problem (tile_end holds the running totals) and a tile never spans two
 // problems; the persistent CTAs stride over all of them.
+//
+// Work is handed out in units: a unit is one tile, or (CTA pairs) two voxel
+// tiles of the same weight tile, one per CTA of the cluster; unit_end holds
+// the running totals of units per problem.
 template <int MAXP>
 struct TcBatch {
     CUtensorMap tm_w;
@@ -55,8 +60,8 @@ struct TcBatch {
     CUtensorMap tm_h[MAXP];
     ConvArgs a[MAXP];
     TcGeo g[MAXP];
-    long long tile_end[MAXP];
-    long long num_tiles;
+    long long unit_end[MAXP];
+    long long num_units;
     int count;
 };
 
@@ -91,16 +96,20 @@ struct TileCoord {
     int n, to, th, tw, nt;
 };
 
+// Voxel tiles are numbered with the output frame fastest: the CTAs working at
+// the same time cover a few spatial blocks across all frames, so an input
+// frame is fetched into L2 once and read there by the three output frames
+// whose temporal taps need it, instead of again after a whole frame of tiles.
 __device__ __forceinline__ TileCoord decode_tile(const ConvArgs& a, const TcGeo& g, long long tile) {
     TileCoord c;
     c.nt = (int)(tile % g.n_tiles);
     long long m = tile / g.n_tiles;
+    c.to = (int)(m % a.Tout);
+    m /= a.Tout;
     c.tw = (int)(m % g.tiles_w);
     m /= g.tiles_w;
     c.th = (int)(m % g.tiles_h);
-    m /= g.tiles_h;
-    c.to = (int)(m % a.Tout);
-    c.n = (int)(m / a.Tout);
+    c.n = (int)(m / g.tiles_h);
     return c;
 }
 
@@ -130,19 +139,44 @@ __device__ __forceinline__ void add_bf16x16(const __nv_bfloat16* src, float (&v)
     }
 }
 
-// Problem of a global tile index and the tile's index within that problem.
+// Problem of a global unit index and the unit's index within that problem.
 template <int MAXP>
-__device__ __forceinline__ int problem_of(const TcBatch<MAXP>& B, long long tile, long long* local) {
+__device__ __forceinline__ int problem_of(const TcBatch<MAXP>& B, long long unit, long long* local) {
     int p = 0;
     if constexpr (MAXP > 1)
-        while (p + 1 < B.count && tile >= B.tile_end[p]) ++p;
-    *local = p ? tile - B.tile_end[p - 1] : tile;
+        while (p + 1 < B.count && unit >= B.unit_end[p]) ++p;
+    *local = p ? unit - B.unit_end[p - 1] : unit;
     return p;
 }
 
-template <int BN, bool SWAP, int MAXP>
+// Tile of CTA `rank` in a unit. With CTA pairs a unit is (pair of voxel tiles,
+// weight tile); the second CTA of a pair whose second voxel tile does not
+// exist recomputes the first one and stores nothing (phantom), so that both
+// CTAs always run the same K loop.
+template <int CL>
+__device__ __forceinline__ long long unit_tile(const TcGeo& g, long long lu, uint32_t rank, bool* phantom) {
+    if constexpr (CL == 1) {
+        *phantom = false;
+        return lu;
+    } else {
+        const long long nt = lu % g.n_tiles, mp = lu / g.n_tiles;
+        long long m = 2 * mp + rank;
+        *phantom = m >= g.m_tiles;
+        if (*phantom) m = 2 * mp;
+        return m * g.n_tiles + nt;
+    }
+}
+
+// CL = 1: one CTA per unit. CL = 2: clusters of two CTAs on two voxel tiles of
+// the same weight tile; each CTA loads half of every weight box and multicasts
+// it to both, and each stage is released only when both CTAs' MMAs have read
+// it (the empty barrier counts one commit from each CTA).
+template <int BN, bool SWAP, int MAXP, int CL>
 __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__ TcBatch<MAXP> B) {
     using C = Cfg<BN, SWAP>;
+    static_assert(CL == 1 || CL == 2, "CTA pairs at most");
+    constexpr uint32_t HALF_W = C::W_BYTES / 2;  // one CTA's share of a weight box
+    static_assert(CL == 1 || HALF_W % 1024 == 0, "weight halves must start on a swizzle atom");
     int* const status = B.a[0].status;
     const unsigned long long wait_ns = B.a[0].wait_ns;
     extern __shared__ uint8_t smem_raw[];
@@ -156,22 +190,38 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
     float* epi = reinterpret_cast<float*>(smem + C::STAGES * C::STAGE + C::BAR_BYTES);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    // A context already in error skips the launch (decided once per CTA).
+    const uint32_t rank = CL > 1 ? cluster_ctarank() : 0;
+    const long long cid = blockIdx.x / CL, ncl = gridDim.x / CL;
+    // A context already in error skips the launch (decided once per CTA, or
+    // once per cluster: both CTAs of a pair take the same path).
     __shared__ int s_skip;
     if (threadIdx.x == 0) s_skip = (status && *(volatile int*)status != 0) ? 1 : 0;
-    __syncthreads();
-    if (s_skip) return;
+    if constexpr (CL == 1) {
+        __syncthreads();
+        if (s_skip) return;
+    }
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::STAGES; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+            mbar_init(&empty[s], CL);
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(&tfull[i], 1);
             mbar_init(&tempty[i], 4);
         }
         fence_mbar_init();
+    }
+    if constexpr (CL > 1) {
+        // the peer's barriers exist before any multicast reaches them
+        cluster_sync();
+        __shared__ int s_skip_pair;
+        if (threadIdx.x == 0) s_skip_pair = s_skip | (int)ld_peer_u32(&s_skip, rank ^ 1u);
+        __syncthreads();
+        if (s_skip_pair) {
+            cluster_sync();
+            return;
+        }
     }
     if (warp == 0 && lane < B.count) {
         tma_prefetch_desc(&B.tm_x[lane]);
@@ -196,13 +246,14 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
 #pragma unroll
             for (int i = 0; i < 8; ++i) last_ph[i] = -1;
             bool ok = true;
-            for (long long tile = blockIdx.x; tile < B.num_tiles && ok; tile += gridDim.x) {
-                long long lt;
-                const int p = problem_of(B, tile, &lt);
+            for (long long u = cid; u < B.num_units && ok; u += ncl) {
+                long long lu;
+                const int p = problem_of(B, u, &lu);
                 const ConvArgs& a = B.a[p];
                 const TcGeo& g = B.g[p];
                 const int ph_ = (a.kh - 1) / 2, pw_ = (a.kw - 1) / 2;
-                const TileCoord tc = decode_tile(a, g, lt);
+                bool phantom;
+                const TileCoord tc = decode_tile(a, g, unit_tile<CL>(g, lu, rank, &phantom));
                 for (int kb = 0; kb < g.nkb; ++kb) {
                     if (!mbar_wait(&empty[s], ph ^ 1, status, wait_ns)) {
                         ok = false;
@@ -236,7 +287,11 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                         tma_load_5d(sa, src, &full[s], pwp * a.Cin + cb * 64, tc.tw * g.BW + (dw == 0 ? -1 : 0), php,
                                     tc.th * g.BH + (dh == 0 ? -1 : 0), tcoord);
                     }
-                    tma_load_2d(sb, &B.tm_w, &full[s], tap * a.Cin + cb * 64, tc.nt * BN);
+                    if constexpr (CL == 1)
+                        tma_load_2d(sb, &B.tm_w, &full[s], tap * a.Cin + cb * 64, tc.nt * BN);
+                    else
+                        tma_load_2d_mc(sb + rank * HALF_W, &B.tm_w, &full[s], tap * a.Cin + cb * 64,
+                                       tc.nt * BN + (int)rank * (BN / 2), (uint16_t)0x3);
                     last_ph[s] = (int)ph;
                     if (++s == C::STAGES) {
                         s = 0;
@@ -244,9 +299,21 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                     }
                 }
             }
-            // make sure no copy is still in flight before the CTA may exit
-            for (int i = 0; i < C::STAGES; ++i)
-                if (last_ph[i] >= 0) mbar_wait(&full[i], (uint32_t)last_ph[i], status, wait_ns);
+            if constexpr (CL == 1) {
+                // make sure no copy is still in flight before the CTA may exit
+                for (int i = 0; i < C::STAGES; ++i)
+                    if (last_ph[i] >= 0) mbar_wait(&full[i], (uint32_t)last_ph[i], status, wait_ns);
+            } else {
+                // producer tail: wait until both CTAs' MMAs have released every stage, so
+                // that no copy into this CTA and no arrival on its barriers is in flight
+                for (int i = 0; i < C::STAGES; ++i) {
+                    if (!mbar_wait(&empty[s], ph ^ 1, status, wait_ns)) break;
+                    if (++s == C::STAGES) {
+                        s = 0;
+                        ph ^= 1;
+                    }
+                }
+            }
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -256,9 +323,9 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
             int last_acc_ph[2] = {-1, -1};
             bool ok = true;
             int it = 0;
-            for (long long tile = blockIdx.x; tile < B.num_tiles && ok; tile += gridDim.x, ++it) {
-                long long lt;
-                const int nkb = B.g[problem_of(B, tile, &lt)].nkb;
+            for (long long u = cid; u < B.num_units && ok; u += ncl, ++it) {
+                long long lu;
+                const int nkb = B.g[problem_of(B, u, &lu)].nkb;
                 const int acc = it & 1;
                 const uint32_t aph = (uint32_t)((it >> 1) & 1);
                 if (!mbar_wait(&tempty[acc], aph ^ 1, status, wait_ns)) break;
@@ -277,7 +344,10 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                     for (int k = 0; k < 4; ++k)
                         tc_mma_bf16(d, sw128_desc(op_a + k * 32), sw128_desc(op_b + k * 32), C::IDESC,
                                     (kb | k) != 0 ? 1u : 0u);
-                    tc_commit(&empty[s]);
+                    if constexpr (CL == 1)
+                        tc_commit(&empty[s]);
+                    else
+                        tc_commit_mc(&empty[s], (uint16_t)0x3);
                     if (++s == C::STAGES) {
                         s = 0;
                         ph ^= 1;
@@ -295,7 +365,7 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
         const int q = warp & 3;  // TMEM lane quarter accessible to this warp
         const int r = q * 32 + lane;
         int it = 0;
-        for (long long tile = blockIdx.x; tile < B.num_tiles; tile += gridDim.x, ++it) {
+        for (long long u = cid; u < B.num_units; u += ncl, ++it) {
             const int acc = it & 1;
             const uint32_t aph = (uint32_t)((it >> 1) & 1);
             int okw = 1;
@@ -303,11 +373,19 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
             okw = __shfl_sync(0xffffffffu, okw, 0);
             if (!okw) break;
             tc_fence_after();
-            long long lt;
-            const int p = problem_of(B, tile, &lt);
+            long long lu;
+            const int p = problem_of(B, u, &lu);
             const ConvArgs& a = B.a[p];
             const TcGeo& g = B.g[p];
-            const TileCoord tc = decode_tile(a, g, lt);
+            bool phantom;
+            const TileCoord tc = decode_tile(a, g, unit_tile<CL>(g, lu, rank, &phantom));
+            if (phantom) {
+                // the pair's missing tile: computed for the K loop's sake, not stored
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&tempty[acc]);
+                continue;
+            }
             if constexpr (SWAP) {
                 // lane = output channel co, TMEM column = voxel of the 256-voxel tile
                 const int co = tc.nt * BN + r;
@@ -524,14 +602,17 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
     __syncthreads();
     tc_fence_after();
     if (warp == 1) tmem_dealloc(tmem_base, C::TMEM_COLS);
+    if constexpr (CL > 1) cluster_sync();  // neither CTA leaves while its peer may still address it
 }
 
-template <int BN, bool SWAP, int MAXP>
+template <int BN, bool SWAP, int MAXP, int CL>
 int launch_bn(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int cta_tiles, cudaStream_t stream) {
     using C = Cfg<BN, SWAP>;
+    auto kern = conv_tc_kernel<BN, SWAP, MAXP, CL>;
     TcBatch<MAXP> B;
     memset(&B, 0, sizeof(B));
-    if (!encode_w_map(&B.tm_w, as[0].w, as[0].Cout_pad, as[0].Kpad, BN)) return -1;
+    // with CTA pairs each CTA loads half of the weight box (BN / 2 rows)
+    if (!encode_w_map(&B.tm_w, as[0].w, as[0].Cout_pad, as[0].Kpad, BN / CL)) return -1;
     long long total = 0;
     for (int p = 0; p < count; ++p) {
         const ConvArgs& a = as[p];
@@ -545,31 +626,78 @@ int launch_bn(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int c
             B.tm_h[p] = B.tm_x[p];
         }
         g.n_tiles = a.Cout_pad / BN;
-        g.num_tiles = (long long)a.N * a.Tout * g.tiles_h * g.tiles_w * g.n_tiles;
-        total += g.num_tiles;
+        g.m_tiles = (long long)a.N * a.Tout * g.tiles_h * g.tiles_w;
+        g.num_tiles = g.m_tiles * g.n_tiles;
+        total += CL == 1 ? g.num_tiles : (g.m_tiles + 1) / 2 * g.n_tiles;
         B.a[p] = a;
         B.g[p] = g;
-        B.tile_end[p] = total;
+        B.unit_end[p] = total;
     }
     B.count = count;
-    B.num_tiles = total;
+    B.num_units = total;
     if (total == 0) return 0;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(conv_tc_kernel<BN, SWAP, MAXP>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
-        attr_set = true;
+    static int max_clusters = -1;
+    if (max_clusters < 0) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+        max_clusters = num_sms / CL;
+        if (CL > 1) {
+            cudaLaunchConfig_t q = {};
+            q.gridDim = dim3((unsigned)(CL * max_clusters));
+            q.blockDim = dim3(192);
+            q.dynamicSmemBytes = C::SMEM;
+            cudaLaunchAttribute at;
+            at.id = cudaLaunchAttributeClusterDimension;
+            at.val.clusterDim.x = CL;
+            at.val.clusterDim.y = 1;
+            at.val.clusterDim.z = 1;
+            q.attrs = &at;
+            q.numAttrs = 1;
+            int n = 0;
+            if (cudaOccupancyMaxActiveClusters(&n, kern, &q) == cudaSuccess && n > 0) max_clusters = n;
+            cudaGetLastError();
+        }
     }
-    // persistent (one CTA per SM), or CTAs of at most cta_tiles tiles each
-    long long grid = std::min<long long>(total, num_sms);
-    if (cta_tiles > 0) grid = std::max(grid, std::min<long long>((total + cta_tiles - 1) / cta_tiles, 1LL << 30));
-    conv_tc_kernel<BN, SWAP, MAXP><<<(unsigned)grid, 192, C::SMEM, stream>>>(B);
+    if constexpr (CL == 1) {
+        // persistent (one CTA per SM), or CTAs of at most cta_tiles tiles each
+        long long grid = std::min<long long>(total, num_sms);
+        if (cta_tiles > 0)
+            grid = std::max(grid, std::min<long long>((total + cta_tiles - 1) / cta_tiles, 1LL << 30));
+        kern<<<(unsigned)grid, 192, C::SMEM, stream>>>(B);
+    } else {
+        const long long clusters = std::min<long long>(total, max_clusters);
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(CL * clusters));
+        cfg.blockDim = dim3(192);
+        cfg.dynamicSmemBytes = C::SMEM;
+        cfg.stream = stream;
+        cudaLaunchAttribute at;
+        at.id = cudaLaunchAttributeClusterDimension;
+        at.val.clusterDim.x = CL;
+        at.val.clusterDim.y = 1;
+        at.val.clusterDim.z = 1;
+        cfg.attrs = &at;
+        cfg.numAttrs = 1;
+        if (cudaLaunchKernelEx(&cfg, kern, B) != cudaSuccess) return -1;
+    }
     return (int)cudaGetLastError();
 }
 
+// CTA pairs for layers with at least one wave of tiles (weight halves of 64+
+// rows), single CTAs otherwise and whenever CTA lifetimes are bounded.
 template <int BN, bool SWAP>
-int launch_bn_any(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int cta_tiles, cudaStream_t stream) {
-    return count == 1 ? launch_bn<BN, SWAP, 1>(as, gs, 1, num_sms, cta_tiles, stream)
-                      : launch_bn<BN, SWAP, kMaxConvGroup>(as, gs, count, num_sms, cta_tiles, stream);
+int launch_bn_any(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int cta_tiles, bool pairs,
+                  cudaStream_t stream) {
+    long long tiles = 0;
+    for (int p = 0; p < count; ++p) {
+        const TcGeo& g = gs[p];
+        tiles += (long long)as[p].N * as[p].Tout * g.tiles_h * g.tiles_w * (as[p].Cout_pad / BN);
+    }
+    const bool pair = pairs && cta_tiles == 0 && (SWAP || BN >= 128) && tiles >= num_sms;
+    if (pair)
+        return count == 1 ? launch_bn<BN, SWAP, 1, 2>(as, gs, 1, num_sms, 0, stream)
+                          : launch_bn<BN, SWAP, kMaxConvGroup, 2>(as, gs, count, num_sms, 0, stream);
+    return count == 1 ? launch_bn<BN, SWAP, 1, 1>(as, gs, 1, num_sms, cta_tiles, stream)
+                      : launch_bn<BN, SWAP, kMaxConvGroup, 1>(as, gs, count, num_sms, cta_tiles, stream);
 }
 
 }  // namespace
@@ -669,8 +797,10 @@ int conv_tc_cout_pad(int Cout) {
 // mode; inputs, outputs, sizes and histories are per problem. cta_tiles = 0
 // launches one persistent CTA per SM; n > 0 gives every CTA at most n tiles,
 // so that a kernel on a higher-priority CUDA stream gets SMs within one short
-// CTA lifetime instead of after the whole layer.
-int launch_conv_tc_group(const ConvArgs* as, int count, int num_sms, cudaStream_t stream, int cta_tiles) {
+// CTA lifetime instead of after the whole layer. pairs allows clusters of two
+// CTAs sharing each weight box by multicast (results are the same either way).
+int launch_conv_tc_group(const ConvArgs* as, int count, int num_sms, cudaStream_t stream, int cta_tiles,
+                         bool pairs) {
     if (count < 1 || count > kMaxConvGroup) return -1;
     const ConvArgs& a0 = as[0];
     for (int p = 1; p < count; ++p)
@@ -695,18 +825,18 @@ int launch_conv_tc_group(const ConvArgs* as, int count, int num_sms, cudaStream_
         g.n_tiles = 0;
         g.num_tiles = 0;
     }
-    if (swap) return launch_bn_any<128, true>(as, gs, count, num_sms, cta_tiles, stream);
+    if (swap) return launch_bn_any<128, true>(as, gs, count, num_sms, cta_tiles, pairs, stream);
     switch (conv_tc_bn(a0.Cout_pad)) {
-        case 256: return launch_bn_any<256, false>(as, gs, count, num_sms, cta_tiles, stream);
-        case 128: return launch_bn_any<128, false>(as, gs, count, num_sms, cta_tiles, stream);
-        case 64: return launch_bn_any<64, false>(as, gs, count, num_sms, cta_tiles, stream);
-        case 32: return launch_bn_any<32, false>(as, gs, count, num_sms, cta_tiles, stream);
-        default: return launch_bn_any<16, false>(as, gs, count, num_sms, cta_tiles, stream);
+        case 256: return launch_bn_any<256, false>(as, gs, count, num_sms, cta_tiles, pairs, stream);
+        case 128: return launch_bn_any<128, false>(as, gs, count, num_sms, cta_tiles, pairs, stream);
+        case 64: return launch_bn_any<64, false>(as, gs, count, num_sms, cta_tiles, pairs, stream);
+        case 32: return launch_bn_any<32, false>(as, gs, count, num_sms, cta_tiles, pairs, stream);
+        default: return launch_bn_any<16, false>(as, gs, count, num_sms, cta_tiles, pairs, stream);
     }
 }
 
 int launch_conv_tc(const ConvArgs& a, int num_sms, cudaStream_t stream) {
-    return launch_conv_tc_group(&a, 1, num_sms, stream, 0);
+    return launch_conv_tc_group(&a, 1, num_sms, stream, 0, true);
 }
 
 }  // namespace tok

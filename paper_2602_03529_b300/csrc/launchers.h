@@ -11,7 +11,8 @@ namespace tok {
 
 int launch_conv_tc(const ConvArgs& a, int num_sms, cudaStream_t stream);
 // one launch over up to kMaxConvGroup inputs of the same layer (k_conv_tc.cu)
-int launch_conv_tc_group(const ConvArgs* as, int count, int num_sms, cudaStream_t stream, int cta_tiles = 0);
+int launch_conv_tc_group(const ConvArgs* as, int count, int num_sms, cudaStream_t stream, int cta_tiles = 0,
+                         bool pairs = true);
 int conv_tc_bn(int cout_pad16);
 int conv_tc_cout_pad(int Cout);  // packed weight rows of a BF16 conv
 int launch_conv_simt(const ConvArgs& a, cudaStream_t stream);

@@ -309,6 +309,12 @@ int tok_set_cta_tiles(tok_ctx* c, int tiles) {
     return TOK_OK;
 }
 
+int tok_set_conv_pairs(tok_ctx* c, int on) {
+    if (!c) return TOK_EINVAL;
+    c->conv_pairs = on ? 1 : 0;
+    return TOK_OK;
+}
+
 int tok_encode(tok_ctx* c, const void* x, int N, int T, int H, int W, float* z, int32_t* idx, tok_stream* st,
                void* stream) {
     if (!c || !x || N < 1 || T < 1 || H < 1 || W < 1) return TOK_EINVAL;

@@ -66,6 +66,7 @@ struct tok_ctx {
     int precision;
     int device = 0, num_sms = 148;
     int cta_tiles = 0;  // conv launches: 0 persistent, n > 0 at most n tiles per CTA
+    int conv_pairs = 0;  // conv launches may use CTA pairs with weight multicast (measured slower)
     std::vector<ParamInfo> params;
     std::map<std::string, int> pindex;
     std::vector<std::vector<float>> host;
@@ -467,7 +468,7 @@ struct Exec {
                             cw.Cin;
         const int e = pbegin();
         if (c->bf16())
-            ck(launch_conv_tc(a, c->num_sms, s));
+            ck(launch_conv_tc_group(&a, 1, c->num_sms, s, 0, c->conv_pairs != 0));
         else
             ck(launch_conv_simt(a, s));
         pend(e, 0, flop);

@@ -136,6 +136,11 @@ class Tokenizer:
         work on higher-priority CUDA streams; results are unchanged)."""
         L.tok_set_cta_tiles(self.ctx, tiles)
 
+    def set_conv_pairs(self, on: bool):
+        """Allow (default) or forbid conv launches as CTA pairs sharing weight boxes by
+        TMA multicast; results are unchanged."""
+        L.tok_set_conv_pairs(self.ctx, on)
+
     # -- grouped (one launch per layer over several inputs) --------------------
     def reserve_batch(self, shapes):
         """shapes: list of (N, T, H, W); a stream chunk counts as (1, s_T, H, W)."""
