@@ -294,6 +294,64 @@ def apply_drop(idx, dropped, levels):
     return out
 
 
+# --------------------------------------------------------------------------
+# Similarity-based token selection (Sec. 6.3, Eq. 3)
+# --------------------------------------------------------------------------
+
+def token_similarity(idx_p, idx_i, levels):
+    """Per-position cosine similarity between P-frame and I-frame tokens (Eq. 3).
+
+    S = <p, q> / (|p| |q|) for the code vectors p, q of the two indices at the
+    same (sample, h, w); the I tokens (N, 1, H', W') are compared with every
+    P latent frame. Reading: S = 0 where either code vector is zero (a zero
+    vector has no direction; this is also the convention of a cosine with the
+    norm product clamped from below). The selection is decided on these
+    values, so they are computed in float32: dot product and both squared
+    norms summed over channels in order, and the product of the squared norms
+    (all exact: codes are multiples of 1/floor(L/2)), then one correctly
+    rounded square root of that product and one correctly rounded division
+    (so parallel codes give exactly +-1); -0 is returned as +0. The kernel
+    computes the same float32 operations."""
+    cp = fsq_dequantize(idx_p, levels).astype(np.float32)
+    ci = fsq_dequantize(idx_i, levels).astype(np.float32)
+    ci = np.broadcast_to(ci, cp.shape)
+    dot = np.zeros(cp.shape[:-1], dtype=np.float32)
+    sp = np.zeros_like(dot)
+    si = np.zeros_like(dot)
+    for c in range(cp.shape[-1]):
+        dot = dot + cp[..., c] * ci[..., c]
+        sp = sp + cp[..., c] * cp[..., c]
+        si = si + ci[..., c] * ci[..., c]
+    den = np.sqrt(sp * si)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        S = np.where(den > 0, dot / np.where(den > 0, den, np.float32(1)), np.float32(0)).astype(np.float32)
+    return S + np.float32(0.0)
+
+
+def similarity_drop(idx_p, idx_i, levels, rate):
+    """Drop decisions (True = dropped) of the similarity-based selection.
+
+    Per sample and P latent frame of H' x W' tokens, the tokens with S > tau
+    are dropped, tau chosen for the available bandwidth (Sec. 6.3). Reading:
+    tau is the (1 - rate)-quantile of S over the frame, i.e. exactly
+    k = floor(rate * H'W') tokens are dropped, those with the largest S, and
+    among equal S the lower linear index (h * W' + w) goes first. rate is the
+    float32 value, k computed in float64 and clipped to [0, H'W']."""
+    S = token_similarity(idx_p, idx_i, levels)
+    N, Tp, Hq, Wq = S.shape
+    n = Hq * Wq
+    k = int(np.floor(float(np.float32(rate)) * n))
+    k = min(max(k, 0), n)
+    out = np.zeros((N, Tp, n), dtype=bool)
+    order_idx = np.arange(n)
+    for b in range(N):
+        for t in range(Tp):
+            s = S[b, t].reshape(-1)
+            order = np.lexsort((order_idx, -s))  # S descending, then index ascending
+            out[b, t, order[:k]] = True
+    return out.reshape(N, Tp, Hq, Wq)
+
+
 def keep_bits_from_mask(dropped):
     """Row masks of the packet header (Sec. 6.2): for every token row, a
     W-bit vector with bit w set when token w is kept, stored as

@@ -239,3 +239,75 @@ def test_edge_pad():
     assert p.shape == (1, 1, 4, 8, 1)
     np.testing.assert_array_equal(p[0, 0, 3], p[0, 0, 2])
     np.testing.assert_array_equal(p[0, 0, :, 7], p[0, 0, :, 4])
+
+
+# ------------------------------------------------- similarity-based selection (Eq. 3)
+
+LV = [8, 8, 8, 5, 5, 5]
+
+
+def _idx_of_digits(d, levels=LV):
+    _, _, _, _, basis = ops.fsq_constants(levels)
+    return int((np.asarray(d) * basis).sum())
+
+
+def test_similarity_closed_forms():
+    """Identical codes give 1, opposite codes -1, orthogonal codes 0, a zero code 0."""
+    hw = [4, 4, 4, 2, 2, 2]
+    a = [hw[0] + 2, hw[1], hw[2], hw[3] + 1, hw[4], hw[5]]          # code (0.5, 0, 0, 0.5, 0, 0)
+    neg = [hw[0] - 2, hw[1], hw[2], hw[3] - 1, hw[4], hw[5]]        # (-0.5, 0, 0, -0.5, 0, 0)
+    orth = [hw[0], hw[1] + 3, hw[2], hw[3], hw[4], hw[5] + 2]        # (0, 0.75, 0, 0, 0, 1)
+    zero = hw
+    I = np.array([[[[_idx_of_digits(a)]]]])
+    P = np.array([[[[_idx_of_digits(a)]], [[_idx_of_digits(neg)]], [[_idx_of_digits(orth)]],
+                   [[_idx_of_digits(zero)]]]])
+    S = ops.token_similarity(P, I, LV)
+    assert S.reshape(-1).tolist() == [1.0, -1.0, 0.0, 0.0]
+    assert ops.fsq_zero_index(LV) == _idx_of_digits(zero)
+    # a zero reference makes every similarity 0
+    S0 = ops.token_similarity(P, np.array([[[[_idx_of_digits(zero)]]]]), LV)
+    assert not S0.any()
+
+
+def test_similarity_matches_a_float64_cosine():
+    """The float32 similarity is the cosine of the two code vectors (independent fp64
+    formula through numpy.linalg), to float32 rounding."""
+    rng = np.random.default_rng(3)
+    P = rng.integers(0, 64000, (2, 3, 6, 9))
+    I = rng.integers(0, 64000, (2, 1, 6, 9))
+    p = ops.fsq_dequantize(P, LV)
+    q = np.broadcast_to(ops.fsq_dequantize(I, LV), p.shape)
+    num = np.einsum("...c,...c->...", p, q)
+    den = np.linalg.norm(p, axis=-1) * np.linalg.norm(q, axis=-1)
+    ref = np.where(den > 0, num / np.where(den > 0, den, 1), 0)
+    S = ops.token_similarity(P, I, LV)
+    assert np.abs(S - ref).max() <= 2 ** -22
+
+
+def test_similarity_drop_counts_order_and_ties():
+    rng = np.random.default_rng(5)
+    P = rng.integers(0, 64000, (2, 4, 7, 11))
+    I = rng.integers(0, 64000, (2, 1, 7, 11))
+    S = ops.token_similarity(P, I, LV)
+    n = 7 * 11
+    for rate in (0.0, 0.1, 0.25, 0.5, 1.0):
+        d = ops.similarity_drop(P, I, LV, rate)
+        k = min(n, int(np.floor(float(np.float32(rate)) * n)))
+        assert (d.sum(axis=(2, 3)) == k).all()
+        for b in range(2):
+            for t in range(4):
+                s, m = S[b, t], d[b, t]
+                if 0 < k < n:
+                    assert s[m].min() >= s[~m].max()    # tau separates dropped from kept
+    # all similarities equal (P = I everywhere): the lowest linear indices go first
+    P2 = np.repeat(I, 3, axis=1)
+    d2 = ops.similarity_drop(P2, I, LV, 0.3)
+    k = int(np.floor(float(np.float32(0.3)) * n))
+    flat = d2.reshape(2, 3, n)
+    assert (flat[..., :k]).all() and not (flat[..., k:]).any()
+    # among equal S at the threshold, the lower index is dropped, the higher kept
+    s = S[0, 0].reshape(-1).copy()
+    P3 = P.copy()
+    P3[0, 0].reshape(-1)[[10, 20]] = I[0, 0].reshape(-1)[[10, 20]]   # two tokens with S = 1
+    d3 = ops.similarity_drop(P3, I, LV, 1.0 / n + 1e-7)             # k = 1
+    assert d3[0, 0].reshape(-1)[10] and not d3[0, 0].reshape(-1)[20]
