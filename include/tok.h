@@ -211,6 +211,27 @@ int tok_drop_mask(const int32_t* d_idx, int N, int Tq, int Hq, int Wq, float rat
                   uint64_t seed, uint64_t stream_id, uint64_t chunk_id, int32_t zero_index,
                   int32_t* d_out, uint32_t* d_keep_bits, void* stream);
 
+/* Similarity-based token selection (Sec. 6.3, Eq. 3). For every P-frame
+ * token, S = <p, q> / (|p| |q|) between its code vector p and the code vector
+ * q of the I-frame token at the same (sample, h, w) (S = 0 where either is
+ * the zero vector); per sample and P latent frame the k = floor(rate * Hq*Wq)
+ * tokens with the largest S are dropped (rate clipped to [0,1]; among equal S
+ * the lower linear index h*Wq + w first), i.e. the threshold tau of Eq. 3 is
+ * the (1 - rate)-quantile of S. S is computed in float32 with the rounding
+ * steps of the definition (exact dot and squared norms, one rounded square
+ * root of the squared-norm product, one rounded division), so the selection
+ * is a deterministic function of the indices.
+ * d_idx_p (N,Tp,Hq,Wq) int32 P tokens; d_idx_i (N,1,Hq,Wq) int32 I tokens;
+ * d_out (N,Tp,Hq,Wq) int32 (zero index at dropped tokens; may alias
+ * d_idx_p); d_keep_bits (N,Tp,Hq,ceil(Wq/32)) uint32 row masks as in
+ * tok_drop_mask, or NULL; d_sim (N,Tp,Hq,Wq) fp32 similarities, or NULL;
+ * d_ws device workspace of tok_similarity_workspace_bytes(...) bytes.
+ * Errors: TOK_EINVAL (arguments, levels), TOK_ENOMEM (workspace too small). */
+size_t tok_similarity_workspace_bytes(int N, int Tp, int Hq, int Wq);
+int tok_similarity_mask(const int32_t* d_idx_p, const int32_t* d_idx_i, int N, int Tp, int Hq, int Wq,
+                        const int* h_levels, int nlev, float rate, int32_t* d_out, uint32_t* d_keep_bits,
+                        float* d_sim, void* d_ws, size_t ws_bytes, void* stream);
+
 /* Row packetisation (Sec. 6.2). rows = N*Tq*Hq rows of Wq tokens.
  * Sender: d_payload gets, row after row, the kept tokens of each row in
  * column order, starting at d_row_offsets[r] = number of kept tokens in rows

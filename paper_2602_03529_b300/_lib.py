@@ -81,6 +81,8 @@ _SIGS = {
     "tok_encode": (i32, [vp, vp, i32, i32, i32, i32, vp, vp, vp, vp]),
     "tok_decode": (i32, [vp, vp, i32, i32, i32, i32, i32, i32, vp, vp, vp]),
     "tok_set_cta_tiles": (i32, [vp, i32]),
+    "tok_similarity_workspace_bytes": (sz, [i32, i32, i32, i32]),
+    "tok_similarity_mask": (i32, [vp, vp, i32, i32, i32, i32, C.POINTER(i32), i32, f32, vp, vp, vp, vp, sz, vp]),
     "tok_set_conv_pairs": (i32, [vp, i32]),
     "tok_batch_workspace_bytes": (sz, [vp, C.POINTER(tok_shape), i32]),
     "tok_reserve_batch": (i32, [vp, C.POINTER(tok_shape), i32]),
@@ -208,6 +210,17 @@ def tok_encode(ctx, x_ptr, N, T, H, W, z_ptr, idx_ptr, stream_handle, cuda_strea
 def tok_decode(ctx, idx_ptr, N, Tq, Hq, Wq, H, W, xhat_ptr, stream_handle, cuda_stream) -> None:
     _ck(_call("tok_decode", ctx, idx_ptr, N, Tq, Hq, Wq, H, W, xhat_ptr, stream_handle, cuda_stream),
         "tok_decode")
+
+
+def tok_similarity_workspace_bytes(N, Tp, Hq, Wq) -> int:
+    return int(_call("tok_similarity_workspace_bytes", N, Tp, Hq, Wq))
+
+
+def tok_similarity_mask(idx_p, idx_i, N, Tp, Hq, Wq, levels, rate, out, keep_bits, sim, ws, ws_bytes,
+                        cuda_stream) -> None:
+    lv = (i32 * len(levels))(*levels)
+    _ck(_call("tok_similarity_mask", idx_p, idx_i, N, Tp, Hq, Wq, lv, len(levels), float(rate), out, keep_bits,
+              sim, ws, ws_bytes, cuda_stream), "tok_similarity_mask")
 
 
 def tok_set_cta_tiles(ctx, tiles: int) -> None:

@@ -69,6 +69,12 @@ int launch_wgrad_tc(const __nv_bfloat16* dy, const __nv_bfloat16* x, const Wgrad
                     size_t max_floats, float* dw, float* db, int num_sms, int* status, unsigned long long wait_ns,
                     cudaStream_t s, int k_valid = 0);
 
+// similarity-based token selection (k_select.cu)
+size_t similarity_workspace_bytes(long long N, int Tp, long long HW);
+int launch_similarity_mask(const int32_t* idx_p, const int32_t* idx_i, long long N, int Tp, int Hq, int Wq,
+                           const FsqConsts& f, long long k, int32_t zero_index, int32_t* out, uint32_t* keep_bits,
+                           float* sim, void* ws, cudaStream_t s);
+
 // backward kernels (k_backward.cu)
 size_t wgrad_partial_floats(int Cout, int K, int S);
 int wgrad_splits(const WgradArgs& a, int num_sms, size_t max_partial_floats);

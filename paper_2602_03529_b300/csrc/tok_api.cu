@@ -364,6 +364,30 @@ int tok_drop_mask(const int32_t* idx, int N, int Tq, int Hq, int Wq, float rate,
                : TOK_OK;
 }
 
+size_t tok_similarity_workspace_bytes(int N, int Tp, int Hq, int Wq) {
+    if (N < 0 || Tp < 0 || Hq < 0 || Wq < 0) return 0;
+    return similarity_workspace_bytes(N, Tp, (long long)Hq * Wq);
+}
+
+int tok_similarity_mask(const int32_t* idx_p, const int32_t* idx_i, int N, int Tp, int Hq, int Wq,
+                        const int* levels, int nlev, float rate, int32_t* out, uint32_t* keep_bits, float* sim,
+                        void* ws, size_t ws_bytes, void* stream) {
+    if (!idx_p || !idx_i || !out || !ws || N < 0 || Tp < 0 || Hq < 0 || Wq < 0 || !(rate == rate) ||
+        !valid_levels(levels, nlev))
+        return TOK_EINVAL;
+    if (ws_bytes < similarity_workspace_bytes(N, Tp, (long long)Hq * Wq)) return TOK_ENOMEM;
+    const FsqConsts f = make_fsq(levels, nlev);
+    double r = (double)rate;
+    r = r < 0.0 ? 0.0 : (r > 1.0 ? 1.0 : r);
+    const long long HW = (long long)Hq * Wq;
+    long long k = (long long)std::floor(r * (double)HW);
+    k = k < 0 ? 0 : (k > HW ? HW : k);
+    return launch_similarity_mask(idx_p, idx_i, N, Tp, Hq, Wq, f, k, tok_zero_index(levels, nlev), out, keep_bits,
+                                  sim, ws, static_cast<cudaStream_t>(stream))
+               ? TOK_ECUDA
+               : TOK_OK;
+}
+
 int tok_pack_rows(const int32_t* idx, const uint32_t* keep_bits, int64_t rows, int Wq, int32_t* payload,
                   int64_t* row_offsets, void* stream) {
     if (!idx || !keep_bits || !payload || !row_offsets || rows < 0 || Wq < 1) return TOK_EINVAL;

@@ -261,6 +261,26 @@ def drop_mask(idx: torch.Tensor, rate: float, seed: int, stream_id: int = 0, chu
     return out, kb
 
 
+def similarity_mask(idx_p: torch.Tensor, idx_i: torch.Tensor, rate: float, levels=(8, 8, 8, 5, 5, 5),
+                    keep_bits=True, want_sim=False, out=None, workspace=None, stream=None):
+    """Similarity-based token selection (Eq. 3): drop the floor(rate * Hq*Wq) P tokens of
+    every latent frame most similar (cosine of code vectors) to the I token at the same
+    position. idx_p (N, Tp, Hq, Wq), idx_i (N, 1, Hq, Wq). Returns (out, keep_bits, sim)."""
+    N, Tp, Hq, Wq = idx_p.shape
+    if tuple(idx_i.shape) != (N, 1, Hq, Wq):
+        raise ValueError("idx_i must be (N, 1, Hq, Wq)")
+    if out is None:
+        out = torch.empty_like(idx_p)
+    kb = torch.empty((N, Tp, Hq, (Wq + 31) // 32), device=idx_p.device, dtype=torch.int32) if keep_bits else None
+    sim = torch.empty((N, Tp, Hq, Wq), device=idx_p.device, dtype=torch.float32) if want_sim else None
+    need = L.tok_similarity_workspace_bytes(N, Tp, Hq, Wq)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, device=idx_p.device, dtype=torch.uint8)
+    L.tok_similarity_mask(_ptr(idx_p), _ptr(idx_i), N, Tp, Hq, Wq, list(levels), rate, _ptr(out), _ptr(kb),
+                          _ptr(sim), _ptr(workspace), workspace.numel(), _stream_ptr(stream))
+    return out, kb, sim
+
+
 def pack_rows(idx: torch.Tensor, keep_bits: torch.Tensor, stream=None):
     Wq = idx.shape[-1]
     rows = idx.numel() // Wq
