@@ -352,6 +352,72 @@ def similarity_drop(idx_p, idx_i, levels, rate):
     return out.reshape(N, Tp, Hq, Wq)
 
 
+# --------------------------------------------------------------------------
+# Pixel residuals (Sec. 6.3, Eq. 4)
+# --------------------------------------------------------------------------
+
+def residual_windows(T, window):
+    """Frame windows of a clip: [0, w), [w, 2w), ...; the last may be shorter."""
+    return [(a, min(a + window, T)) for a in range(0, T, window)]
+
+
+def residual_mean(x, xhat, window, theta):
+    """Window-averaged, thresholded pixel residual (Sec. 6.3; Eq. 4).
+
+    r = x - x_hat per pixel and channel, averaged over each window of
+    consecutive frames: r_c(h,w,c) = (1/T) sum_t r(h,w,c,t), T the window's
+    frame count; then elements with |r_c| < theta are zeroed. The zeroing is a
+    decision on these values, so they are computed in float32 in the order of
+    the definition: each difference rounded, summed over t in order, one
+    division by T. x, x_hat: (N, T, H, W, C); returns (N, n_windows, H, W, C)."""
+    x = np.asarray(x, dtype=np.float32)
+    xh = np.asarray(xhat, dtype=np.float32)
+    N, T = x.shape[:2]
+    wins = residual_windows(T, window)
+    out = np.zeros((N, len(wins)) + x.shape[2:], dtype=np.float32)
+    th = np.float32(theta)
+    for k, (a, b) in enumerate(wins):
+        s = np.zeros((N,) + x.shape[2:], dtype=np.float32)
+        for t in range(a, b):
+            s = s + (x[:, t] - xh[:, t])
+        r = s / np.float32(b - a)
+        out[:, k] = np.where(np.abs(r) < th, np.float32(0), r)
+    return out
+
+
+def residual_sparse(r):
+    """Sparse form of a thresholded residual: per (sample, window) segment, the
+    nonzero elements in position order, position = (h*W + w)*C + c.
+    Returns (positions int32, values float32, segment offsets int64 of length
+    N*n_windows + 1)."""
+    N, K = r.shape[:2]
+    flat = r.reshape(N * K, -1)
+    pos, val, offs = [], [], [0]
+    for seg in flat:
+        nz = np.nonzero(seg)[0]
+        pos.append(nz.astype(np.int32))
+        val.append(seg[nz])
+        offs.append(offs[-1] + len(nz))
+    return np.concatenate(pos), np.concatenate(val).astype(np.float32), np.asarray(offs, dtype=np.int64)
+
+
+def residual_apply(xhat, pos, val, offs, window):
+    """Receiver side (Sec. 6.3): every frame of a window gets that window's
+    residual added (float32): x_hat[n, t] += r_c[n, window(t)]."""
+    xh = np.array(xhat, dtype=np.float32, copy=True)
+    N, T = xh.shape[:2]
+    wins = residual_windows(T, window)
+    flat = xh.reshape(N, T, -1)
+    for n in range(N):
+        for k, (a, b) in enumerate(wins):
+            seg = n * len(wins) + k
+            p = pos[offs[seg]:offs[seg + 1]]
+            v = val[offs[seg]:offs[seg + 1]]
+            for t in range(a, b):
+                flat[n, t, p] = flat[n, t, p] + v
+    return flat.reshape(xh.shape)
+
+
 def keep_bits_from_mask(dropped):
     """Row masks of the packet header (Sec. 6.2): for every token row, a
     W-bit vector with bit w set when token w is kept, stored as

@@ -311,3 +311,46 @@ def test_similarity_drop_counts_order_and_ties():
     P3[0, 0].reshape(-1)[[10, 20]] = I[0, 0].reshape(-1)[[10, 20]]   # two tokens with S = 1
     d3 = ops.similarity_drop(P3, I, LV, 1.0 / n + 1e-7)             # k = 1
     assert d3[0, 0].reshape(-1)[10] and not d3[0, 0].reshape(-1)[20]
+
+
+# ------------------------------------------------------------- pixel residuals (Eq. 4)
+
+def test_residual_mean_closed_forms():
+    """A residual constant in time averages to itself; a residual linear in t averages to
+    its value at the window's mid-time; windows tile the clip with a shorter last one;
+    |r| < theta is zeroed and |r| >= theta kept."""
+    rng = np.random.default_rng(0)
+    N, T, H, W, C = 2, 7, 3, 5, 3
+    xh = rng.standard_normal((N, T, H, W, C)).astype(np.float32)
+    c = (rng.integers(-8, 9, (N, 1, H, W, C)) / 8).astype(np.float32)          # exact in float32
+    r = ops.residual_mean(xh + c, xh, 3, 0.0)
+    assert ops.residual_windows(7, 3) == [(0, 3), (3, 6), (6, 7)]
+    assert r.shape == (N, 3, H, W, C)
+    assert np.abs(r - c).max() <= 1e-6
+    ramp = (np.arange(T, dtype=np.float32)[None, :, None, None, None] * 0.25).astype(np.float32)
+    r2 = ops.residual_mean(xh * 0 + ramp, xh * 0, 4, 0.0)                      # windows [0,4), [4,7)
+    assert np.allclose(r2[:, 0], 0.25 * 1.5) and np.allclose(r2[:, 1], 0.25 * 5.0)
+    r3 = ops.residual_mean(xh * 0 + ramp, xh * 0, 4, 0.375)
+    assert (r3[:, 0] == 0.375).all() and (r3[:, 1] == 1.25).all()
+    r4 = ops.residual_mean(xh * 0 + ramp, xh * 0, 4, 0.376)
+    assert (r4[:, 0] == 0).all()
+
+
+def test_residual_sparse_round_trip_and_apply():
+    """dense -> sparse -> apply: every frame of a window gets its residual; with theta 0
+    and a residual constant over time the receiver recovers x exactly."""
+    rng = np.random.default_rng(1)
+    N, T, H, W, C = 2, 6, 4, 5, 3
+    xh = (rng.integers(-64, 64, (N, T, H, W, C)) / 32).astype(np.float32)
+    c = (rng.integers(-8, 9, (N, 1, H, W, C)) / 8).astype(np.float32)
+    c[rng.random(c.shape) < 0.5] = 0
+    x = xh + c
+    r = ops.residual_mean(x, xh, 3, 0.0)
+    pos, val, offs = ops.residual_sparse(r)
+    assert offs[-1] == len(pos) == np.count_nonzero(r)
+    dense = np.zeros(r.reshape(N * 2, -1).shape, dtype=np.float32)
+    for s in range(N * 2):
+        dense[s, pos[offs[s]:offs[s + 1]]] = val[offs[s]:offs[s + 1]]
+    assert np.array_equal(dense.reshape(r.shape), r)
+    assert (np.diff(pos[offs[0]:offs[1]]) > 0).all()
+    assert np.array_equal(ops.residual_apply(xh, pos, val, offs, 3), x)
