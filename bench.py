@@ -247,6 +247,7 @@ def gpu_arm(args):
         "roofline": roofline, "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
         "fp32_path": fp32, "speedup_vs_fp32": (value / fp32["value"]) if fp32 else None,
     }
+    out["residuals"] = residuals(x, xh, roofline["groupnorm"]["peak_gbs"])
     tk.close()
     if not args.no_train:
         out["training"] = training(args, params)
@@ -421,6 +422,53 @@ def selection(args, hbm_gbs, streams=256, Tp=4, Hq=90, Wq=160, rate=0.25, steps=
                     "frame (about 77 us for a 90x160 frame), not by HBM"}
 
 
+# ------------------------------------------------------------- pixel residuals
+
+def residuals(x, xh, hbm_gbs, window=4, theta=0.05, steps=10, warmup=3):
+    """Pixel residual path (Eq. 4) on the 720p clip and its reconstruction from the timed
+    step: window means of x - x_hat with theta zeroing, the sparse form, and the
+    receiver-side add. HBM-bound; algorithmic bytes per stage as listed."""
+    import torch
+
+    import paper_2602_03529_b300 as P
+
+    N, T, H, W, C = x.shape
+    r = P.residual(x, xh, window, theta)
+    pos, val, offs = P.residual_sparse(r)
+    xr = xh.clone()
+    for _ in range(warmup):
+        r = P.residual(x, xh, window, theta)
+        pos, val, offs = P.residual_sparse(r)
+        P.residual_apply(xr, window, pos, val, offs)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    t = [0.0, 0.0, 0.0]
+    for _ in range(steps):
+        ev[0].record()
+        r = P.residual(x, xh, window, theta)
+        ev[1].record()
+        pos, val, offs = P.residual_sparse(r)
+        ev[2].record()
+        P.residual_apply(xr, window, pos, val, offs)
+        ev[3].record()
+        torch.cuda.synchronize()
+        for i in range(3):
+            t[i] += ev[i].elapsed_time(ev[i + 1]) / steps
+    nnz = int(offs[-1].item())
+    E = H * W * C
+    nwin = (T + window - 1) // window
+    b_mean = N * T * E * (x.element_size() + 4) + N * nwin * E * 4
+    b_sparse = 2 * N * nwin * E * 4 + nnz * 8
+    b_apply = nnz * 8 + 2 * nnz * window * 4
+    return {"workload": f"{N}x{T}x{H}x{W}x{C} clip and its reconstruction, {window}-frame windows, "
+                        f"theta {theta}", "nonzeros": nnz, "density": nnz / (N * nwin * E),
+            "mean_ms": t[0], "mean_gbs": b_mean / (t[0] / 1e3) / 1e9, "mean_frac": b_mean / (t[0] / 1e3) / 1e9 / hbm_gbs,
+            "sparse_ms": t[1], "sparse_gbs": b_sparse / (t[1] / 1e3) / 1e9,
+            "apply_ms": t[2], "apply_gbs": b_apply / (t[2] / 1e3) / 1e9 if t[2] > 0 else None,
+            "peak_gbs": hbm_gbs}
+
+
+# ------------------------------------------------------------- serving
 # ------------------------------------------------------------- serving
 # ------------------------------------------------------------- serving
 

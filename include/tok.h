@@ -232,6 +232,32 @@ int tok_similarity_mask(const int32_t* d_idx_p, const int32_t* d_idx_i, int N, i
                         const int* h_levels, int nlev, float rate, int32_t* d_out, uint32_t* d_keep_bits,
                         float* d_sim, void* d_ws, size_t ws_bytes, void* stream);
 
+/* Pixel residuals (Sec. 6.3, Eq. 4). Sender: r = x - x_hat per pixel and
+ * channel (x_hat a reconstruction of x, e.g. tok_decode(tok_encode(x))),
+ * averaged over windows of `window` consecutive frames ([0,w), [w,2w), ...;
+ * the last may be shorter): r_c = (1/T_w) sum_t r, then zeroed where
+ * |r_c| < theta. float32 with the definition's rounding steps (differences
+ * summed in frame order, one division), since theta decides which elements
+ * are sent. precision: TOK_BF16 or TOK_FP32 for d_x (N,T,H,W,C); d_xhat
+ * (N,T,H,W,C) fp32; d_r (N, ceil(T/window), H, W, C) fp32.
+ * The arithmetic coding of the sparse residual (Sec. 6.3) is not part of this
+ * library. */
+int tok_residual(int precision, const void* d_x, const float* d_xhat, int N, int T, int H, int W, int C,
+                 int window, float theta, float* d_r, void* stream);
+/* Sparse form of d_r: per (sample, window) segment s = n*n_windows + k, the
+ * nonzero elements in position order, position = (h*W + w)*C + c;
+ * d_pos int32 / d_val fp32 hold up to N*n_windows*H*W*C entries (caller
+ * allocates the worst case); d_seg_offsets int64 (N*n_windows + 1): segment s
+ * occupies [off[s], off[s+1]). d_ws: tok_residual_sparse_workspace_bytes. */
+size_t tok_residual_sparse_workspace_bytes(int N, int n_windows, int H, int W, int C);
+int tok_residual_sparse(const float* d_r, int N, int n_windows, int H, int W, int C, int32_t* d_pos,
+                        float* d_val, int64_t* d_seg_offsets, void* d_ws, size_t ws_bytes, void* stream);
+/* Receiver: every frame t of window k gets that window's residual added,
+ * d_xhat[n,t] += r_c[n,k] (fp32, in place). capacity = the length of
+ * d_pos / d_val (entries past d_seg_offsets[N*n_windows] are ignored). */
+int tok_residual_apply(float* d_xhat, int N, int T, int H, int W, int C, int window, const int32_t* d_pos,
+                       const float* d_val, const int64_t* d_seg_offsets, int64_t capacity, void* stream);
+
 /* Row packetisation (Sec. 6.2). rows = N*Tq*Hq rows of Wq tokens.
  * Sender: d_payload gets, row after row, the kept tokens of each row in
  * column order, starting at d_row_offsets[r] = number of kept tokens in rows

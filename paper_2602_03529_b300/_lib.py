@@ -81,6 +81,10 @@ _SIGS = {
     "tok_encode": (i32, [vp, vp, i32, i32, i32, i32, vp, vp, vp, vp]),
     "tok_decode": (i32, [vp, vp, i32, i32, i32, i32, i32, i32, vp, vp, vp]),
     "tok_set_cta_tiles": (i32, [vp, i32]),
+    "tok_residual": (i32, [i32, vp, vp, i32, i32, i32, i32, i32, i32, f32, vp, vp]),
+    "tok_residual_sparse_workspace_bytes": (sz, [i32, i32, i32, i32, i32]),
+    "tok_residual_sparse": (i32, [vp, i32, i32, i32, i32, i32, vp, vp, vp, vp, sz, vp]),
+    "tok_residual_apply": (i32, [vp, i32, i32, i32, i32, i32, i32, vp, vp, vp, i64, vp]),
     "tok_similarity_workspace_bytes": (sz, [i32, i32, i32, i32]),
     "tok_similarity_mask": (i32, [vp, vp, i32, i32, i32, i32, C.POINTER(i32), i32, f32, vp, vp, vp, vp, sz, vp]),
     "tok_set_conv_pairs": (i32, [vp, i32]),
@@ -221,6 +225,25 @@ def tok_similarity_mask(idx_p, idx_i, N, Tp, Hq, Wq, levels, rate, out, keep_bit
     lv = (i32 * len(levels))(*levels)
     _ck(_call("tok_similarity_mask", idx_p, idx_i, N, Tp, Hq, Wq, lv, len(levels), float(rate), out, keep_bits,
               sim, ws, ws_bytes, cuda_stream), "tok_similarity_mask")
+
+
+def tok_residual(precision, x, xhat, N, T, H, W, C, window, theta, r, cuda_stream) -> None:
+    _ck(_call("tok_residual", precision, x, xhat, N, T, H, W, C, window, float(theta), r, cuda_stream),
+        "tok_residual")
+
+
+def tok_residual_sparse_workspace_bytes(N, nwin, H, W, C) -> int:
+    return int(_call("tok_residual_sparse_workspace_bytes", N, nwin, H, W, C))
+
+
+def tok_residual_sparse(r, N, nwin, H, W, C, pos, val, seg_off, ws, ws_bytes, cuda_stream) -> None:
+    _ck(_call("tok_residual_sparse", r, N, nwin, H, W, C, pos, val, seg_off, ws, ws_bytes, cuda_stream),
+        "tok_residual_sparse")
+
+
+def tok_residual_apply(xhat, N, T, H, W, C, window, pos, val, seg_off, capacity, cuda_stream) -> None:
+    _ck(_call("tok_residual_apply", xhat, N, T, H, W, C, window, pos, val, seg_off, capacity, cuda_stream),
+        "tok_residual_apply")
 
 
 def tok_set_cta_tiles(ctx, tiles: int) -> None:

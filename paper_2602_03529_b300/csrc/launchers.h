@@ -75,6 +75,15 @@ int launch_similarity_mask(const int32_t* idx_p, const int32_t* idx_i, long long
                            const FsqConsts& f, long long k, int32_t zero_index, int32_t* out, uint32_t* keep_bits,
                            float* sim, void* ws, cudaStream_t s);
 
+// pixel residuals (k_residual.cu)
+int launch_residual_mean(bool bf16, const void* x, const float* xh, long long N, int Tf, long long E, int window,
+                         float theta, float* r, cudaStream_t s);
+size_t residual_sparse_workspace_bytes(long long nseg, long long E);
+int launch_residual_sparse(const float* r, long long nseg, long long E, int32_t* pos, float* val, int64_t* seg_off,
+                           void* ws, cudaStream_t s);
+int launch_residual_apply(float* xh, long long N, int Tf, long long E, int window, const int32_t* pos,
+                          const float* val, const int64_t* seg_off, long long cap, cudaStream_t s);
+
 // backward kernels (k_backward.cu)
 size_t wgrad_partial_floats(int Cout, int K, int S);
 int wgrad_splits(const WgradArgs& a, int num_sms, size_t max_partial_floats);

@@ -388,6 +388,43 @@ int tok_similarity_mask(const int32_t* idx_p, const int32_t* idx_i, int N, int T
                : TOK_OK;
 }
 
+int tok_residual(int precision, const void* x, const float* xhat, int N, int T, int H, int W, int C, int window,
+                 float theta, float* r, void* stream) {
+    if (!x || !xhat || !r || N < 0 || T < 0 || H < 0 || W < 0 || C < 1 || window < 1 || !(theta == theta))
+        return TOK_EINVAL;
+    if (precision != TOK_BF16 && precision != TOK_FP32) return TOK_EINVAL;
+    return launch_residual_mean(precision == TOK_BF16, x, xhat, N, T, (long long)H * W * C, window, theta, r,
+                                static_cast<cudaStream_t>(stream))
+               ? TOK_ECUDA
+               : TOK_OK;
+}
+
+size_t tok_residual_sparse_workspace_bytes(int N, int nwin, int H, int W, int C) {
+    if (N < 0 || nwin < 0 || H < 0 || W < 0 || C < 0) return 0;
+    return residual_sparse_workspace_bytes((long long)N * nwin, (long long)H * W * C);
+}
+
+int tok_residual_sparse(const float* r, int N, int nwin, int H, int W, int C, int32_t* pos, float* val,
+                        int64_t* seg_off, void* ws, size_t ws_bytes, void* stream) {
+    if (!r || !pos || !val || !seg_off || !ws || N < 0 || nwin < 0 || H < 0 || W < 0 || C < 1) return TOK_EINVAL;
+    const long long E = (long long)H * W * C;
+    if (E > 0x7fffffffLL) return TOK_ESHAPE;
+    if (ws_bytes < residual_sparse_workspace_bytes((long long)N * nwin, E)) return TOK_ENOMEM;
+    return launch_residual_sparse(r, (long long)N * nwin, E, pos, val, seg_off, ws, static_cast<cudaStream_t>(stream))
+               ? TOK_ECUDA
+               : TOK_OK;
+}
+
+int tok_residual_apply(float* xhat, int N, int T, int H, int W, int C, int window, const int32_t* pos,
+                       const float* val, const int64_t* seg_off, int64_t capacity, void* stream) {
+    if (!xhat || !pos || !val || !seg_off || N < 0 || T < 0 || H < 0 || W < 0 || C < 1 || window < 1 || capacity < 0)
+        return TOK_EINVAL;
+    return launch_residual_apply(xhat, N, T, (long long)H * W * C, window, pos, val, seg_off, capacity,
+                                 static_cast<cudaStream_t>(stream))
+               ? TOK_ECUDA
+               : TOK_OK;
+}
+
 int tok_pack_rows(const int32_t* idx, const uint32_t* keep_bits, int64_t rows, int Wq, int32_t* payload,
                   int64_t* row_offsets, void* stream) {
     if (!idx || !keep_bits || !payload || !row_offsets || rows < 0 || Wq < 1) return TOK_EINVAL;

@@ -281,6 +281,40 @@ def similarity_mask(idx_p: torch.Tensor, idx_i: torch.Tensor, rate: float, level
     return out, kb, sim
 
 
+def residual(x: torch.Tensor, xhat: torch.Tensor, window: int, theta: float, stream=None):
+    """Window-averaged, thresholded pixel residual (Eq. 4): x (N,T,H,W,C) bf16 or fp32,
+    xhat fp32 of the same shape -> (N, ceil(T/window), H, W, C) fp32."""
+    N, T, H, W, C = x.shape
+    prec = L.TOK_BF16 if x.dtype == torch.bfloat16 else L.TOK_FP32
+    r = torch.empty((N, (T + window - 1) // window, H, W, C), device=x.device, dtype=torch.float32)
+    L.tok_residual(prec, _ptr(x), _ptr(xhat), N, T, H, W, C, window, theta, _ptr(r), _stream_ptr(stream))
+    return r
+
+
+def residual_sparse(r: torch.Tensor, stream=None):
+    """Sparse form of a thresholded residual: (positions int32, values fp32, segment
+    offsets int64 (N*n_windows + 1)); the arrays hold the worst case, the first
+    offsets[-1] entries are used."""
+    N, K, H, W, C = r.shape
+    cap = r.numel()
+    pos = torch.empty(cap, device=r.device, dtype=torch.int32)
+    val = torch.empty(cap, device=r.device, dtype=torch.float32)
+    offs = torch.empty(N * K + 1, device=r.device, dtype=torch.int64)
+    need = L.tok_residual_sparse_workspace_bytes(N, K, H, W, C)
+    ws = torch.empty(max(need, 1), device=r.device, dtype=torch.uint8)
+    L.tok_residual_sparse(_ptr(r), N, K, H, W, C, _ptr(pos), _ptr(val), _ptr(offs), _ptr(ws), need,
+                          _stream_ptr(stream))
+    return pos, val, offs
+
+
+def residual_apply(xhat: torch.Tensor, window: int, pos, val, offs, stream=None):
+    """Receiver side: adds each window's residual to every frame of the window (in place)."""
+    N, T, H, W, C = xhat.shape
+    L.tok_residual_apply(_ptr(xhat), N, T, H, W, C, window, _ptr(pos), _ptr(val), _ptr(offs), pos.numel(),
+                         _stream_ptr(stream))
+    return xhat
+
+
 def pack_rows(idx: torch.Tensor, keep_bits: torch.Tensor, stream=None):
     Wq = idx.shape[-1]
     rows = idx.numel() // Wq

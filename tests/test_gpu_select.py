@@ -101,3 +101,13 @@ def test_argument_errors(P):
         L.tok_similarity_mask(dp.data_ptr(), di.data_ptr(), 1, 2, 4, 4, [8, 1], 0.5, out.data_ptr(), None, None,
                               ws.data_ptr(), 10 ** 6, None)
     assert e.value.code == L.TOK_EINVAL
+
+
+def test_large_frames_take_the_three_kernel_form(P):
+    """Frames above the fused kernel's shared-memory budget (240 x 256 = 61440 tokens)."""
+    rng = np.random.default_rng(9)
+    N, Tp, H, W = 1, 2, 240, 256
+    ii = rng.integers(0, 64000, (N, 1, H, W))
+    ip = np.where(rng.random((N, Tp, H, W)) < 0.3, np.repeat(ii, Tp, axis=1), rng.integers(0, 64000, (N, Tp, H, W)))
+    for rate in (0.0, 0.2, 1.0):
+        _check(P, ip, ii, rate)
