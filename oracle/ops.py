@@ -418,6 +418,44 @@ def residual_apply(xhat, pos, val, offs, window):
     return flat.reshape(xh.shape)
 
 
+# --------------------------------------------------------------------------
+# GoP boundary smoothing (Sec. 6.1, Eq. 1 and 2)
+# --------------------------------------------------------------------------
+
+def gop_blend(xhat_prev, xhat_curr, n):
+    """Boundary blending (Eq. 2): for i = 1..n, frame i of the current GoP
+    becomes a_i * prev[T-n+i] + (1 - a_i) * curr[i] with a_i = (n - i) / n
+    (1-based frame numbers; T the previous GoP's frame count); the other
+    frames are unchanged. Arrays (N, T, H, W, C), float64."""
+    prev = np.asarray(xhat_prev, dtype=np.float64)
+    out = np.array(xhat_curr, dtype=np.float64, copy=True)
+    T = prev.shape[1]
+    for i in range(1, n + 1):
+        a = (n - i) / n
+        out[:, i - 1] = a * prev[:, T - n + i - 1] + (1 - a) * out[:, i - 1]
+    return out
+
+
+def temporal_loss(xhat_curr, x_prev, n):
+    """Boundary loss (Eq. 1): L = (1/n) sum_{i=1..n} || xhat_curr[i] - x_prev[T-n+i] ||,
+    averaged over the batch. Reading (the norm is not specified): the
+    Euclidean norm of the whole frame difference (all pixels and channels).
+    Returns (L, dL/dxhat_curr) with the gradient (1/(N n)) d / ||d|| on the
+    first n frames (0 where ||d|| = 0) and 0 elsewhere; float64."""
+    xc = np.asarray(xhat_curr, dtype=np.float64)
+    xp = np.asarray(x_prev, dtype=np.float64)
+    N, T = xp.shape[:2]
+    L = 0.0
+    g = np.zeros_like(xc)
+    for i in range(1, n + 1):
+        d = xc[:, i - 1] - xp[:, T - n + i - 1]
+        nrm = np.sqrt((d.reshape(N, -1) ** 2).sum(axis=1))
+        L += nrm.sum() / (N * n)
+        scale = np.where(nrm > 0, 1.0 / (N * n * np.where(nrm > 0, nrm, 1.0)), 0.0)
+        g[:, i - 1] = d * scale.reshape((N,) + (1,) * (d.ndim - 1))
+    return L, g
+
+
 def keep_bits_from_mask(dropped):
     """Row masks of the packet header (Sec. 6.2): for every token row, a
     W-bit vector with bit w set when token w is kept, stored as

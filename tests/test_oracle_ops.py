@@ -354,3 +354,42 @@ def test_residual_sparse_round_trip_and_apply():
     assert np.array_equal(dense.reshape(r.shape), r)
     assert (np.diff(pos[offs[0]:offs[1]]) > 0).all()
     assert np.array_equal(ops.residual_apply(xh, pos, val, offs, 3), x)
+
+
+# ------------------------------------------------------- GoP boundary smoothing (Eq. 1, 2)
+
+def test_gop_blend_weights():
+    """a_i = (n - i)/n: frame n is the current frame unchanged, frame 1 is mostly the
+    previous GoP's frame T-n+1; weights sum to one (blending equal frames is the identity);
+    frames past n are untouched."""
+    rng = np.random.default_rng(0)
+    N, T, H, W, C, n = 2, 6, 3, 4, 3, 3
+    prev = rng.standard_normal((N, T, H, W, C))
+    curr = rng.standard_normal((N, T, H, W, C))
+    out = ops.gop_blend(prev, curr, n)
+    assert np.array_equal(out[:, n - 1], curr[:, n - 1])
+    assert np.allclose(out[:, 0], (2 / 3) * prev[:, T - 3] + (1 / 3) * curr[:, 0])
+    assert np.allclose(out[:, 1], (1 / 3) * prev[:, T - 2] + (2 / 3) * curr[:, 1])
+    assert np.array_equal(out[:, n:], curr[:, n:])
+    same = np.repeat(curr[:, :1], T, axis=1)
+    assert np.allclose(ops.gop_blend(same, same, n), same)
+
+
+def test_temporal_loss_closed_form_and_finite_differences():
+    rng = np.random.default_rng(1)
+    N, T, H, W, C, n = 2, 5, 3, 4, 3, 2
+    xp = rng.standard_normal((N, T, H, W, C))
+    c = 0.5
+    xc = np.zeros((N, T, H, W, C))
+    xc[:, :n] = xp[:, T - n:] + c                     # every boundary difference is c
+    L, g = ops.temporal_loss(xc, xp, n)
+    assert abs(L - c * np.sqrt(H * W * C)) < 1e-12
+    assert not g[:, n:].any()
+    xc = rng.standard_normal((N, T, H, W, C))
+    L, g = ops.temporal_loss(xc, xp, n)
+    h = 1e-6
+    for idx in [(0, 0, 1, 2, 1), (1, 1, 2, 0, 0), (0, 1, 0, 3, 2), (1, 3, 1, 1, 1)]:
+        e = np.zeros_like(xc)
+        e[idx] = h
+        fd = (ops.temporal_loss(xc + e, xp, n)[0] - ops.temporal_loss(xc - e, xp, n)[0]) / (2 * h)
+        assert abs(fd - g[idx]) <= 1e-7 + 1e-6 * abs(g[idx])
