@@ -254,6 +254,7 @@ def gpu_arm(args):
     if not args.no_group:
         out["grouped"] = grouped(args, params, roofline["peak"])
     out["selection"] = selection(args, roofline["groupnorm"]["peak_gbs"])
+    out["gop_smoothing"] = gop_smoothing(roofline["groupnorm"]["peak_gbs"])
     if not args.no_serve:
         cap = value / world * args.H * args.W * 3.94e6  # algorithmic FLOP/s one GPU sustains
         out["serving"] = serving(args, params, cap, rank, world)
@@ -468,6 +469,44 @@ def residuals(x, xh, hbm_gbs, window=4, theta=0.05, steps=10, warmup=3):
             "peak_gbs": hbm_gbs}
 
 
+# ------------------------------------------------------------- GoP boundary smoothing
+
+def gop_smoothing(hbm_gbs, N=8, T=9, H=720, W=1280, n=4, steps=10, warmup=3):
+    """Eq. 2 blending and the Eq. 1 boundary loss with its gradient on 8 consecutive 9-frame
+    720p GoP reconstructions (fp32 frames). HBM-bound: blend reads n previous + T current
+    frames and writes T frames; the loss reads 2n frames, the gradient pass 2n frames and
+    writes T frames."""
+    import torch
+
+    import paper_2602_03529_b300 as P
+
+    g = torch.Generator(device="cuda").manual_seed(3)
+    prev = torch.rand((N, T, H, W, 3), device="cuda", generator=g) * 2 - 1
+    curr = torch.rand((N, T, H, W, 3), device="cuda", generator=g) * 2 - 1
+    out = torch.empty_like(curr)
+    for _ in range(warmup):
+        P.gop_blend(prev, curr, n, out=out)
+        P.temporal_loss(curr, prev, n)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record()
+    for _ in range(steps):
+        P.gop_blend(prev, curr, n, out=out)
+    ev[1].record()
+    for _ in range(steps):
+        P.temporal_loss(curr, prev, n)
+    ev[2].record()
+    torch.cuda.synchronize()
+    tb, tl = ev[0].elapsed_time(ev[1]) / steps, ev[1].elapsed_time(ev[2]) / steps
+    fb = H * W * 3 * 4
+    bb = N * fb * (n + 2 * T)
+    bl = N * fb * (2 * n + 2 * n + T)
+    return {"workload": f"{N} GoPs x {T} frames at {H}x{W}, n = {n} boundary frames", "blend_ms": tb,
+            "blend_gbs": bb / (tb / 1e3) / 1e9, "blend_frac": bb / (tb / 1e3) / 1e9 / hbm_gbs,
+            "loss_and_grad_ms": tl, "loss_and_grad_gbs": bl / (tl / 1e3) / 1e9, "peak_gbs": hbm_gbs}
+
+
+# ------------------------------------------------------------- serving
 # ------------------------------------------------------------- serving
 # ------------------------------------------------------------- serving
 # ------------------------------------------------------------- serving

@@ -258,6 +258,24 @@ int tok_residual_sparse(const float* d_r, int N, int n_windows, int H, int W, in
 int tok_residual_apply(float* d_xhat, int N, int T, int H, int W, int C, int window, const int32_t* d_pos,
                        const float* d_val, const int64_t* d_seg_offsets, int64_t capacity, void* stream);
 
+/* GoP boundary blending (Sec. 6.1, Eq. 2): for i = 1..n, frame i of the
+ * current GoP becomes a_i * prev[T_prev-n+i] + (1 - a_i) * curr[i] with
+ * a_i = (n - i)/n (1-based frame numbers); the other frames are copied.
+ * d_prev (N,T_prev,H,W,C), d_curr and d_out (N,T,H,W,C) fp32 (d_out may
+ * alias d_curr); 0 <= n <= min(T_prev, T). */
+int tok_gop_blend(const float* d_prev, int T_prev, const float* d_curr, float* d_out, int N, int T, int H, int W,
+                  int C, int n, void* stream);
+/* GoP boundary loss (Sec. 6.1, Eq. 1): L = (1/n) sum_{i=1..n}
+ * ||xhat_curr[i] - x_prev[T_prev-n+i]||, averaged over the batch, the norm
+ * being the Euclidean norm of the whole frame difference (the paper leaves it
+ * open). d_loss: one fp32; d_grad (N,T_curr,H,W,C) fp32 dL/dxhat_curr or NULL
+ * (zero outside the first n frames; add it to the reconstruction gradient
+ * given to tok_backward). Deterministic (fixed-order FP64 sums). d_ws:
+ * tok_temporal_loss_workspace_bytes. */
+size_t tok_temporal_loss_workspace_bytes(int N, int n, int H, int W, int C);
+int tok_temporal_loss(const float* d_xhat_curr, const float* d_x_prev, int N, int T_curr, int T_prev, int H, int W,
+                      int C, int n, float* d_loss, float* d_grad, void* d_ws, size_t ws_bytes, void* stream);
+
 /* Row packetisation (Sec. 6.2). rows = N*Tq*Hq rows of Wq tokens.
  * Sender: d_payload gets, row after row, the kept tokens of each row in
  * column order, starting at d_row_offsets[r] = number of kept tokens in rows

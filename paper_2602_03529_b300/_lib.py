@@ -81,6 +81,9 @@ _SIGS = {
     "tok_encode": (i32, [vp, vp, i32, i32, i32, i32, vp, vp, vp, vp]),
     "tok_decode": (i32, [vp, vp, i32, i32, i32, i32, i32, i32, vp, vp, vp]),
     "tok_set_cta_tiles": (i32, [vp, i32]),
+    "tok_gop_blend": (i32, [vp, i32, vp, vp, i32, i32, i32, i32, i32, i32, vp]),
+    "tok_temporal_loss_workspace_bytes": (sz, [i32, i32, i32, i32, i32]),
+    "tok_temporal_loss": (i32, [vp, vp, i32, i32, i32, i32, i32, i32, i32, vp, vp, vp, sz, vp]),
     "tok_residual": (i32, [i32, vp, vp, i32, i32, i32, i32, i32, i32, f32, vp, vp]),
     "tok_residual_sparse_workspace_bytes": (sz, [i32, i32, i32, i32, i32]),
     "tok_residual_sparse": (i32, [vp, i32, i32, i32, i32, i32, vp, vp, vp, vp, sz, vp]),
@@ -244,6 +247,19 @@ def tok_residual_sparse(r, N, nwin, H, W, C, pos, val, seg_off, ws, ws_bytes, cu
 def tok_residual_apply(xhat, N, T, H, W, C, window, pos, val, seg_off, capacity, cuda_stream) -> None:
     _ck(_call("tok_residual_apply", xhat, N, T, H, W, C, window, pos, val, seg_off, capacity, cuda_stream),
         "tok_residual_apply")
+
+
+def tok_gop_blend(prev, Tp, curr, out, N, T, H, W, C, n, cuda_stream) -> None:
+    _ck(_call("tok_gop_blend", prev, Tp, curr, out, N, T, H, W, C, n, cuda_stream), "tok_gop_blend")
+
+
+def tok_temporal_loss_workspace_bytes(N, n, H, W, C) -> int:
+    return int(_call("tok_temporal_loss_workspace_bytes", N, n, H, W, C))
+
+
+def tok_temporal_loss(xc, xp, N, Tc, Tp, H, W, C, n, loss, grad, ws, ws_bytes, cuda_stream) -> None:
+    _ck(_call("tok_temporal_loss", xc, xp, N, Tc, Tp, H, W, C, n, loss, grad, ws, ws_bytes, cuda_stream),
+        "tok_temporal_loss")
 
 
 def tok_set_cta_tiles(ctx, tiles: int) -> None:

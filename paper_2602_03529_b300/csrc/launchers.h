@@ -84,6 +84,13 @@ int launch_residual_sparse(const float* r, long long nseg, long long E, int32_t*
 int launch_residual_apply(float* xh, long long N, int Tf, long long E, int window, const int32_t* pos,
                           const float* val, const int64_t* seg_off, long long cap, cudaStream_t s);
 
+// GoP boundary smoothing (k_gop.cu)
+int launch_gop_blend(const float* prev, int Tp, const float* curr, float* out, long long N, int T, long long E, int n,
+                     cudaStream_t s);
+size_t temporal_loss_workspace_bytes(long long N, int n, long long E);
+int launch_temporal_loss(const float* xc, const float* xp, long long N, int Tc, int Tp, long long E, int n,
+                         float* loss, float* grad, void* ws, cudaStream_t s);
+
 // backward kernels (k_backward.cu)
 size_t wgrad_partial_floats(int Cout, int K, int S);
 int wgrad_splits(const WgradArgs& a, int num_sms, size_t max_partial_floats);

@@ -425,6 +425,32 @@ int tok_residual_apply(float* xhat, int N, int T, int H, int W, int C, int windo
                : TOK_OK;
 }
 
+int tok_gop_blend(const float* prev, int Tp, const float* curr, float* out, int N, int T, int H, int W, int C, int n,
+                  void* stream) {
+    if (!prev || !curr || !out || N < 0 || T < 0 || Tp < 0 || H < 0 || W < 0 || C < 1 || n < 0 || n > T || n > Tp)
+        return TOK_EINVAL;
+    return launch_gop_blend(prev, Tp, curr, out, N, T, (long long)H * W * C, n, static_cast<cudaStream_t>(stream))
+               ? TOK_ECUDA
+               : TOK_OK;
+}
+
+size_t tok_temporal_loss_workspace_bytes(int N, int n, int H, int W, int C) {
+    if (N < 0 || n < 0 || H < 0 || W < 0 || C < 0) return 0;
+    return temporal_loss_workspace_bytes(N, n, (long long)H * W * C);
+}
+
+int tok_temporal_loss(const float* xc, const float* xp, int N, int Tc, int Tp, int H, int W, int C, int n,
+                      float* loss, float* grad, void* ws, size_t ws_bytes, void* stream) {
+    if (!xc || !xp || !loss || !ws || N < 1 || Tc < 0 || Tp < 0 || H < 1 || W < 1 || C < 1 || n < 1 || n > Tc ||
+        n > Tp)
+        return TOK_EINVAL;
+    if (ws_bytes < temporal_loss_workspace_bytes(N, n, (long long)H * W * C)) return TOK_ENOMEM;
+    return launch_temporal_loss(xc, xp, N, Tc, Tp, (long long)H * W * C, n, loss, grad, ws,
+                                static_cast<cudaStream_t>(stream))
+               ? TOK_ECUDA
+               : TOK_OK;
+}
+
 int tok_pack_rows(const int32_t* idx, const uint32_t* keep_bits, int64_t rows, int Wq, int32_t* payload,
                   int64_t* row_offsets, void* stream) {
     if (!idx || !keep_bits || !payload || !row_offsets || rows < 0 || Wq < 1) return TOK_EINVAL;

@@ -315,6 +315,28 @@ def residual_apply(xhat: torch.Tensor, window: int, pos, val, offs, stream=None)
     return xhat
 
 
+def gop_blend(xhat_prev: torch.Tensor, xhat_curr: torch.Tensor, n: int, out=None, stream=None):
+    """Eq. 2: blend the first n frames of the current GoP with the last n of the previous one."""
+    N, T, H, W, C = xhat_curr.shape
+    if out is None:
+        out = torch.empty_like(xhat_curr)
+    L.tok_gop_blend(_ptr(xhat_prev), xhat_prev.shape[1], _ptr(xhat_curr), _ptr(out), N, T, H, W, C, n,
+                    _stream_ptr(stream))
+    return out
+
+
+def temporal_loss(xhat_curr: torch.Tensor, x_prev: torch.Tensor, n: int, grad=True, stream=None):
+    """Eq. 1: (loss (1-element fp32 tensor), dL/dxhat_curr or None)."""
+    N, Tc, H, W, C = xhat_curr.shape
+    loss = torch.empty(1, device=xhat_curr.device, dtype=torch.float32)
+    g = torch.empty_like(xhat_curr) if grad else None
+    need = L.tok_temporal_loss_workspace_bytes(N, n, H, W, C)
+    ws = torch.empty(need, device=xhat_curr.device, dtype=torch.uint8)
+    L.tok_temporal_loss(_ptr(xhat_curr), _ptr(x_prev), N, Tc, x_prev.shape[1], H, W, C, n, _ptr(loss), _ptr(g),
+                        _ptr(ws), need, _stream_ptr(stream))
+    return loss, g
+
+
 def pack_rows(idx: torch.Tensor, keep_bits: torch.Tensor, stream=None):
     Wq = idx.shape[-1]
     rows = idx.numel() // Wq
