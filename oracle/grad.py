@@ -126,7 +126,7 @@ class OracleTrain(Oracle):
         x = np.asarray(x, dtype=np.float64)
         assert x.shape[2] % a.s_hw == 0 and x.shape[3] % a.s_hw == 0, "training needs H, W multiples of 8"
         tape = []
-        h = self._conv(tape, "enc.stem", x, (1, 2, 2))
+        h = self._conv(tape, "enc.stem", x, (a.t_stem, 2, 2))
         for l in range(a.nlevels):
             for b in range(a.blocks):
                 h = self._block(tape, f"enc.l{l}.b{b}", h)
@@ -146,8 +146,8 @@ class OracleTrain(Oracle):
                 h = ops.depth_to_space(self._conv(tape, f"dec.up{l - 1}", h), (2, 2, 2))
                 tape.append(("d2s", (2, 2, 2)))
         y = self._conv(tape, "dec.out", self._gn(tape, "dec.out_gn", h))
-        xh = ops.depth_to_space(y, (1, 2, 2))
-        tape.append(("d2s", (1, 2, 2)))
+        xh = ops.depth_to_space(y, (a.t_stem, 2, 2))
+        tape.append(("d2s", (a.t_stem, 2, 2)))
         loss = float(np.mean((xh - x) ** 2))
         return loss, xh, (tape, x, xh, z)
 

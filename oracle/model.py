@@ -11,14 +11,19 @@ two standard settings (Sec. 4.1) built from causal residual blocks (Sec. 1,
 C2). The paper gives no layer list; the one here follows the workload
 description the implementation is measured on:
 
-  encoder: stem conv k3 stride (1,2,2) -> per level l: ``blocks`` causal
+  encoder: stem conv k3 stride (t_stem,2,2) -> per level l: ``blocks`` causal
   residual blocks (GN -> SiLU -> conv -> GN -> SiLU -> conv, plus a skip that is
   a 1x1x1 conv when channels change) -> between levels a k3 conv with stride
   (2,2,2) -> GN -> SiLU -> conv to the latent dim -> FSQ.
   decoder (mirror): conv from the code vectors -> per level (deepest first)
   ``blocks`` residual blocks -> a k3 conv to C_{l-1} * 8 channels followed by
-  depth-to-space (2,2,2) -> ... -> GN -> SiLU -> conv to 3*4 channels ->
-  depth-to-space (1,2,2) -> crop.
+  depth-to-space (2,2,2) -> ... -> GN -> SiLU -> conv to 3*4*t_stem channels ->
+  depth-to-space (t_stem,2,2) -> crop.
+
+t_stem = 1 gives the 4x temporal / 8x8 spatial setting; t_stem = 2 adds a
+third temporal halving in the stem: the paper's own asymmetric 8x temporal,
+8x8 spatial setting (Sec. 4.1), whose 9-frame GoP is one I frame coded only
+spatially plus 8 P frames coded jointly (Sec. 6.3).
 
 The single-stage variant ("stage") is: conv k3 in->c0 (no activation) ->
 conv k3 stride (1,2,2) c0->c1 -> GN -> SiLU -> 1x1x1 conv c1->zdim -> FSQ.
@@ -42,6 +47,7 @@ class Arch:
     gn_groups: int = 32
     gn_eps: float = 1e-6
     time_pad: int = ops.PAD_REPLICATE
+    t_stem: int = 1                    # temporal stride of the stem: 1 (4x8x8) or 2 (8x8x8)
 
     @property
     def zdim(self) -> int:
@@ -53,8 +59,8 @@ class Arch:
 
     @property
     def s_t(self) -> int:
-        """Temporal compression: one stride-2 per level transition."""
-        return 1 if self.kind == "stage" else 2 ** (self.nlevels - 1)
+        """Temporal compression: the stem's temporal stride times one stride-2 per level transition."""
+        return 1 if self.kind == "stage" else self.t_stem * 2 ** (self.nlevels - 1)
 
     @property
     def s_hw(self) -> int:
@@ -99,7 +105,7 @@ def param_spec(arch: Arch):
             s += _block_spec(f"dec.l{l}.b{b}", c[l], c[l])
         if l > 0:
             s += _conv_spec(f"dec.up{l - 1}", c[l - 1] * 8, c[l])
-    s += _gn_spec("dec.out_gn", c[0]) + _conv_spec("dec.out", arch.in_ch * 4, c[0])
+    s += _gn_spec("dec.out_gn", c[0]) + _conv_spec("dec.out", arch.in_ch * 4 * arch.t_stem, c[0])
     return s
 
 
@@ -140,7 +146,7 @@ class Oracle:
             h = self.conv("stage.c0", x)
             h = self.conv("stage.c1", h, (1, 2, 2))
             return self.conv("stage.out", self.gn_silu("stage.gn", h))
-        h = self.conv("enc.stem", x, (1, 2, 2))
+        h = self.conv("enc.stem", x, (a.t_stem, 2, 2))
         for l in range(a.nlevels):
             for b in range(a.blocks):
                 h = self.block(f"enc.l{l}.b{b}", h)
@@ -165,7 +171,7 @@ class Oracle:
             if l > 0:
                 h = ops.depth_to_space(self.conv(f"dec.up{l - 1}", h), (2, 2, 2))
         y = self.conv("dec.out", self.gn_silu("dec.out_gn", h))
-        y = ops.depth_to_space(y, (1, 2, 2))
+        y = ops.depth_to_space(y, (a.t_stem, 2, 2))
         return y[:, :, :H, :W, :]
 
     def decode(self, idx, H, W):

@@ -119,3 +119,31 @@ def test_rounded_forward_has_same_gradient_structure():
     r = 2 * (xh - x) / xh.size
     ref = ops.space_to_depth(r, (1, 2, 2)).sum(axis=(0, 1, 2, 3))
     np.testing.assert_allclose(gb, ref, rtol=1e-10, atol=1e-14)
+
+
+def test_888_gradient_finite_differences():
+    """The 8x8x8 setting (stem with temporal stride 2, (2,2,2) pixel head)."""
+    a = Arch(ch=(16, 32, 64), blocks=1, t_stem=2)
+    rng = np.random.default_rng(7)
+    p = {k: np.asarray(v, dtype=np.float64) for k, v in S.weights_for(param_spec(a), seed=5).items()}
+    for n, shape, kind in param_spec(a):
+        if kind in ("bias", "gn_beta"):
+            p[n] = 0.1 * rng.standard_normal(shape)
+    x = S.blurred_noise_clip(4, 1, 9, 32, 32).astype(np.float64)
+    dropped = rng.random((1, 2, 4, 4)) < 0.2
+    o = OracleTrain(a, p, surrogate=True)
+    loss, _, saved = o.forward_train(x, dropped)
+    grads, dx = o.backward(saved)
+    for name in ["enc.stem.w", "enc.l0.b0.c1.w", "dec.out.w", "dec.out.b", "dec.up0.w"]:
+        g = grads[name]
+        for _ in range(2):
+            i = tuple(int(rng.integers(0, s)) for s in g.shape)
+            h = 1e-6 * max(1.0, abs(p[name][i]))
+            pp = dict(p)
+            pp[name] = p[name].copy()
+            pp[name][i] += h
+            lp = OracleTrain(a, pp, surrogate=True).forward_train(x, dropped)[0]
+            pp[name][i] -= 2 * h
+            lm = OracleTrain(a, pp, surrogate=True).forward_train(x, dropped)[0]
+            fd = (lp - lm) / (2 * h)
+            assert abs(fd - g[i]) <= 1e-5 * max(abs(g[i]), 1e-3 * np.abs(g).max()), (name, i, fd, g[i])

@@ -203,3 +203,65 @@ def test_crop_and_pad_shapes(H, W):
     assert idx.shape == latent_shape(SMALL, 1, 5, H, W)
     y = o.decode(idx, H, W)
     assert y.shape == (1, 5, H, W, 3)
+
+
+# --- the paper's 8x temporal, 8x8 spatial setting (stem with temporal stride 2) ---
+
+SMALL8 = Arch(ch=(8, 16, 32), blocks=1, t_stem=2)
+
+
+def test_888_shapes_and_params():
+    a = Arch(t_stem=2)
+    assert a.s_t == 8 and a.s_hw == 8
+    assert latent_shape(a, 1, 9, 720, 1280) == (1, 2, 90, 160)   # a 9-frame GoP: 1 I + 8 P frames
+    assert latent_shape(a, 1, 17, 256, 256) == (1, 3, 32, 32)
+    spec = {n: s for n, s, _ in param_spec(a)}
+    assert spec["dec.out.w"] == (24, 3, 3, 3, 128)                # 3 channels x (2,2,2) depth-to-space
+
+
+def test_888_encoder_decoder_causal():
+    """Latent t depends only on frames <= 8t; decoded frame f only on latents <= ceil(f/8)."""
+    o = Oracle(SMALL8, _small_params(SMALL8, seed=6))
+    x = S.blurred_noise_clip(3, 1, 17, 16, 16)
+    z0 = o.encode_latent(x)
+    assert z0.shape == (1, 3, 2, 2, 6)
+    rng = np.random.default_rng(0)
+    for t in range(3):
+        x2 = x.copy()
+        x2[:, 8 * t + 1:] = rng.uniform(-1, 1, x2[:, 8 * t + 1:].shape)
+        z1 = o.encode_latent(x2)
+        np.testing.assert_array_equal(z0[:, :t + 1], z1[:, :t + 1])
+    codes = rng.uniform(-1, 1, (1, 3, 2, 2, 6))
+    y0 = o.decode_codes(codes, 16, 16)
+    assert y0.shape == (1, 17, 16, 16, 3)
+    for k in (1, 2):
+        c2 = codes.copy()
+        c2[:, k] += 0.5
+        y1 = o.decode_codes(c2, 16, 16)
+        np.testing.assert_array_equal(y0[:, :8 * (k - 1) + 1], y1[:, :8 * (k - 1) + 1])
+        assert not np.array_equal(y0[:, 8 * (k - 1) + 1:], y1[:, 8 * (k - 1) + 1:])
+
+
+def test_888_model_matches_torch_fp64():
+    a = SMALL8
+    p = _small_params(a, seed=8)
+    x = S.blurred_noise_clip(2, 1, 9, 16, 24)
+    o = Oracle(a, p)
+    z = o.encode_latent(x)
+    h = _tconv(_t(x).permute(0, 4, 1, 2, 3), p, "enc.stem", (2, 2, 2))
+    for l in range(3):
+        h = _tblock(h, p, f"enc.l{l}.b0")
+        if l < 2:
+            h = _tconv(h, p, f"enc.down{l}", (2, 2, 2))
+    zt = _tconv(_tgn(h, p, "enc.out_gn"), p, "enc.out")
+    np.testing.assert_allclose(z, zt.permute(0, 2, 3, 4, 1).numpy(), rtol=1e-9, atol=1e-9)
+    codes = np.random.default_rng(5).uniform(-1, 1, z.shape)
+    y = o.decode_codes(codes, 16, 24)
+    assert y.shape[1] == 9
+    h = _tconv(_t(codes).permute(0, 4, 1, 2, 3), p, "dec.in")
+    for l in (2, 1, 0):
+        h = _tblock(h, p, f"dec.l{l}.b0")
+        if l > 0:
+            h = _td2s(_tconv(h, p, f"dec.up{l - 1}"), (2, 2, 2))
+    yt = _td2s(_tconv(_tgn(h, p, "dec.out_gn"), p, "dec.out"), (2, 2, 2))
+    np.testing.assert_allclose(y, yt.permute(0, 2, 3, 4, 1).numpy(), rtol=1e-9, atol=1e-9)
