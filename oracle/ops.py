@@ -456,6 +456,67 @@ def temporal_loss(xhat_curr, x_prev, n):
     return L, g
 
 
+# --------------------------------------------------------------------------
+# Resolution Scaling Accelerator: pre-encode downsampling (Sec. 5)
+# --------------------------------------------------------------------------
+
+def round_to_bf16(x):
+    """float32 -> nearest bfloat16 (ties to even), returned as float32 values.
+
+    bfloat16 keeps the upper 16 bits of the IEEE binary32 pattern; rounding
+    adds 0x7FFF plus the lowest kept bit to the pattern before truncation, so
+    that a dropped half-way remainder goes to the even neighbour. NaNs stay
+    NaN (quietened)."""
+    f = np.ascontiguousarray(x, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    keep_lsb = (u >> 16) & 1
+    r = ((u + 0x7FFF + keep_lsb) >> 16) << 16
+    nan = np.isnan(f)
+    r = np.where(nan, (u | 0x00400000) >> 16 << 16, r)
+    return (r & 0xFFFFFFFF).astype(np.uint32).view(np.float32).reshape(f.shape)
+
+
+def box_downsample(x, s, out_bf16=False):
+    """Downsampling by an integer factor s (the resolution control of Sec. 5,
+    2x or 3x of 1080p in the paper's training and evaluation).
+
+    Reading (the paper says the frames are "linearly" downsampled and gives no
+    filter): every output pixel is the mean of the s x s block of input pixels
+    it covers, blocks anchored at the top-left corner, output size floor(H/s)
+    x floor(W/s) (trailing rows and columns dropped) -- the area filter, which
+    for s = 2 coincides with bilinear sampling at the block centres.
+
+    x: (F, H, W, C) frames, channels last, either uint8 (0..255) or float32
+    values. The mean is computed in float32 in a fixed order, since the
+    result is quantised to its output type: for float input, the s*s values
+    summed row by row, left to right, each addition rounded, then one division
+    by s*s; for uint8 input, the exact integer sum, one division by s*s, then
+    the map to [-1, 1] as m / 127.5 - 1 (each step rounded to float32).
+    out_bf16 rounds the float32 result to bfloat16 (ties to even).
+    Returns float32 (F, H//s, W//s, C)."""
+    x = np.asarray(x)
+    F, H, W, C = x.shape
+    Ho, Wo = H // s, W // s
+    out = np.zeros((F, Ho, Wo, C), dtype=np.float32)
+    ss = np.float32(s * s)
+    if x.dtype == np.uint8:
+        acc = np.zeros((F, Ho, Wo, C), dtype=np.int64)
+        for i in range(s):
+            for j in range(s):
+                acc += x[:, i:Ho * s:s, j:Wo * s:s, :].astype(np.int64)
+        m = acc.astype(np.float32) / ss
+        out = m / np.float32(127.5) - np.float32(1.0)
+    else:
+        xf = x.astype(np.float32)
+        acc = np.zeros((F, Ho, Wo, C), dtype=np.float32)
+        for i in range(s):
+            for j in range(s):
+                acc = acc + xf[:, i:Ho * s:s, j:Wo * s:s, :]
+        out = acc / ss
+    out = out.astype(np.float32)
+    return round_to_bf16(out) if out_bf16 else out
+
+
 def keep_bits_from_mask(dropped):
     """Row masks of the packet header (Sec. 6.2): for every token row, a
     W-bit vector with bit w set when token w is kept, stored as

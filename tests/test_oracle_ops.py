@@ -393,3 +393,78 @@ def test_temporal_loss_closed_form_and_finite_differences():
         e[idx] = h
         fd = (ops.temporal_loss(xc + e, xp, n)[0] - ops.temporal_loss(xc - e, xp, n)[0]) / (2 * h)
         assert abs(fd - g[idx]) <= 1e-7 + 1e-6 * abs(g[idx])
+
+
+# ---------------------------------------------------------------- RSA resize (Sec. 5)
+
+def test_round_to_bf16_matches_torch_cast():
+    """The oracle's bfloat16 rounding against torch's CPU float32 -> bfloat16 cast,
+    on random values, exact half-way ties (both parities), and special values."""
+    rng = np.random.default_rng(0)
+    v = (rng.standard_normal(20000) * 10.0 ** rng.integers(-30, 30, 20000)).astype(np.float32)
+    base = rng.integers(0, 2 ** 31, 4000, dtype=np.uint64).astype(np.uint32)
+    ties = ((base & np.uint32(0xFFFF0000)) | np.uint32(0x8000)).view(np.float32)   # remainder exactly 1/2
+    near = ((base & np.uint32(0xFFFF0000)) | np.uint32(0x7FFF)).view(np.float32)
+    special = np.array([0.0, -0.0, np.inf, -np.inf, 3.4028235e38, -3.4028235e38, 1e-40, -1e-45,
+                        1.0, 1.00390625, 1.005859375], dtype=np.float32)
+    x = np.concatenate([v, ties, near, special])
+    x = x[np.isfinite(x) | np.isinf(x)]
+    ref = torch.from_numpy(x).to(torch.bfloat16).to(torch.float32).numpy()
+    got = ops.round_to_bf16(x)
+    assert np.array_equal(got.view(np.uint32), ref.view(np.uint32))
+    assert np.isnan(ops.round_to_bf16(np.array([np.nan], np.float32))).all()
+
+
+def test_box_downsample_hand_example():
+    x = np.arange(16, dtype=np.float32).reshape(1, 4, 4, 1)
+    y = ops.box_downsample(x, 2)
+    assert np.array_equal(y[0, :, :, 0], np.array([[2.5, 4.5], [10.5, 12.5]], np.float32))
+    y3 = ops.box_downsample(np.arange(81, dtype=np.float32).reshape(1, 9, 9, 1), 3)
+    # block means of a 9x9 ramp: the centre values 10, 13, 16 / 37, 40, 43 / 64, 67, 70
+    assert np.array_equal(y3[0, :, :, 0], np.array([[10, 13, 16], [37, 40, 43], [64, 67, 70]], np.float32))
+
+
+@pytest.mark.parametrize("s", [1, 2, 3])
+def test_box_downsample_against_avg_pool(s):
+    """Float input: equal to torch's avg_pool2d (kernel = stride = s, floor mode) in float64,
+    up to float32 rounding; trailing rows / columns take no part."""
+    rng = np.random.default_rng(s)
+    x = rng.uniform(-1, 1, (3, 20, 31, 3)).astype(np.float32)
+    y = ops.box_downsample(x, s)
+    ref = F.avg_pool2d(torch.from_numpy(x.astype(np.float64)).permute(0, 3, 1, 2), s, s).permute(0, 2, 3, 1).numpy()
+    assert y.shape == (3, 20 // s, 31 // s, 3)
+    assert np.abs(y - ref).max() <= 4e-7 * s * s
+    if s == 1:
+        assert np.array_equal(y, x)
+    x2 = x.copy()
+    x2[:, (20 // s) * s:] = 99.0
+    x2[:, :, (31 // s) * s:] = -99.0
+    assert np.array_equal(ops.box_downsample(x2, s), y)
+
+
+def test_box_downsample_linear_ramp_and_constants():
+    """The mean of a linear function over a block is its value at the block centre."""
+    s = 3
+    h, w = np.meshgrid(np.arange(12), np.arange(15), indexing="ij")
+    x = (0.25 * h - 0.125 * w + 0.5).astype(np.float32)[None, :, :, None]
+    y = ops.box_downsample(x, s)[0, :, :, 0]
+    ho, wo = np.meshgrid(np.arange(4), np.arange(5), indexing="ij")
+    ref = 0.25 * (s * ho + 1) - 0.125 * (s * wo + 1) + 0.5
+    assert np.abs(y - ref).max() <= 1e-6
+    c = np.full((2, 9, 9, 3), 0.3, np.float32)
+    assert np.array_equal(ops.box_downsample(c, 3, out_bf16=True), np.full((2, 3, 3, 3), ops.round_to_bf16(
+        np.float32(0.3 * 9) / np.float32(9)), np.float32))
+
+
+def test_box_downsample_u8_mapping():
+    """uint8 input: the block mean mapped to [-1, 1] (m / 127.5 - 1): 0 -> -1, 255 -> 1,
+    a 2x2 block {0, 255, 255, 0} -> 0; random blocks against the float64 definition."""
+    assert np.array_equal(ops.box_downsample(np.zeros((1, 4, 4, 3), np.uint8), 2), np.full((1, 2, 2, 3), -1, np.float32))
+    assert np.array_equal(ops.box_downsample(np.full((1, 6, 6, 3), 255, np.uint8), 3), np.ones((1, 2, 2, 3), np.float32))
+    b = np.array([[0, 255], [255, 0]], np.uint8)[None, :, :, None]
+    assert ops.box_downsample(b, 2)[0, 0, 0, 0] == 0.0
+    rng = np.random.default_rng(4)
+    x = rng.integers(0, 256, (2, 30, 33, 3), dtype=np.uint8)
+    for s in (2, 3):
+        ref = F.avg_pool2d(torch.from_numpy(x.astype(np.float64)).permute(0, 3, 1, 2), s, s).permute(0, 2, 3, 1).numpy()
+        assert np.abs(ops.box_downsample(x, s) - (ref / 127.5 - 1)).max() <= 3e-7
