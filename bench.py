@@ -255,6 +255,11 @@ def gpu_arm(args):
         out["grouped"] = grouped(args, params, roofline["peak"])
     out["selection"] = selection(args, roofline["groupnorm"]["peak_gbs"])
     out["gop_smoothing"] = gop_smoothing(roofline["groupnorm"]["peak_gbs"])
+    if not args.no_rsa:
+        tk8 = P.Tokenizer("bf16", t_stem=2)
+        p8 = S.weights_for(tk8.param_spec(), seed=0)
+        tk8.close()
+        out["rsa_8x8x8"] = rsa_8x8x8(p8, roofline["groupnorm"]["peak_gbs"])
     if not args.no_serve:
         cap = value / world * args.H * args.W * 3.94e6  # algorithmic FLOP/s one GPU sustains
         out["serving"] = serving(args, params, cap, rank, world)
@@ -506,9 +511,71 @@ def gop_smoothing(hbm_gbs, N=8, T=9, H=720, W=1280, n=4, steps=10, warmup=3):
             "loss_and_grad_ms": tl, "loss_and_grad_gbs": bl / (tl / 1e3) / 1e9, "peak_gbs": hbm_gbs}
 
 
-# ------------------------------------------------------------- serving
-# ------------------------------------------------------------- serving
-# ------------------------------------------------------------- serving
+# ------------------------------------------------------------- resolution control + 8x8x8
+
+def rsa_8x8x8(params8, hbm_gbs, N=4, T=17, steps=3, warmup=2):
+    """Sec. 5 resolution control feeding the paper's 8x temporal / 8x8 spatial tokenizer
+    (Sec. 4.1): N clips of T 1080p uint8 frames are downsampled 3x (640x360) or 2x (960x540)
+    to bf16 in [-1, 1], encoded, 15% of tokens dropped, and decoded at the reduced size
+    (the learned super-resolution stage is not part of this path). Encoder and decoder
+    frames/s are reported apart, as in the paper's scaling table; the downsample kernel
+    against HBM (it reads the 1080p frames once and writes the small bf16 frames)."""
+    import numpy as np
+    import torch
+
+    import paper_2602_03529_b300 as P
+
+    tk = P.Tokenizer("bf16", t_stem=2)
+    tk.set_params(params8)
+    rng = np.random.default_rng(8)
+    x8 = torch.from_numpy(rng.integers(0, 256, (N, T, 1080, 1920, 3), dtype=np.uint8)).cuda()
+    flush = torch.empty(256 << 20, device="cuda", dtype=torch.uint8)
+    out = {"workload": f"{N} clips x {T} frames of 1080p uint8 -> s x s area downsample -> 8x8x8 tokenizer "
+                       "(channels 128/256/512, 2 blocks per level, FSQ [8,8,8,5,5,5]), 15% drop",
+           "peak_gbs": hbm_gbs}
+    for s in (3, 2):
+        H, W = 1080 // s, 1920 // s
+        tk.reserve(N, T, H, W)
+        Tq, Hq, Wq = tk.latent_shape(T, H, W)
+        xs = torch.empty((N, T, H, W, 3), device="cuda", dtype=torch.bfloat16)
+        z = torch.empty((N, Tq, Hq, Wq, len(LEVELS)), device="cuda")
+        idx = torch.empty((N, Tq, Hq, Wq), device="cuda", dtype=torch.int32)
+        idx_d = torch.empty_like(idx)
+        xh = torch.empty((N, T, H, W, 3), device="cuda")
+        for i in range(warmup):
+            P.downsample(x8, s, torch.bfloat16, out=xs)
+            tk.encode(xs, z, idx)
+            P.drop_mask(idx, 0.15, seed=5, stream_id=0, chunk_id=i, levels=LEVELS, out=idx_d)
+            tk.decode(idx_d, H, W, out=xh)
+        torch.cuda.synchronize()
+        t_ds = t_enc = t_dec = 0.0
+        for i in range(steps):
+            flush.zero_()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[0].record()
+            P.downsample(x8, s, torch.bfloat16, out=xs)
+            ev[1].record()
+            tk.encode(xs, z, idx)
+            P.drop_mask(idx, 0.15, seed=5, stream_id=0, chunk_id=100 + i, levels=LEVELS, out=idx_d)
+            ev[2].record()
+            tk.decode(idx_d, H, W, out=xh)
+            ev[3].record()
+            torch.cuda.synchronize()
+            t_ds += ev[0].elapsed_time(ev[1])
+            t_enc += ev[1].elapsed_time(ev[2])
+            t_dec += ev[2].elapsed_time(ev[3])
+        assert tk.status() == 0
+        frames = N * T * steps
+        ds_bytes = N * T * (1080 * 1920 * 3 + H * W * 3 * 2)
+        out[f"{s}x"] = {"H": H, "W": W, "latent": [Tq, Hq, Wq],
+                        "encoder_fps": frames / ((t_ds + t_enc) / 1e3), "decoder_fps": frames / (t_dec / 1e3),
+                        "codec_fps": frames / ((t_ds + t_enc + t_dec) / 1e3),
+                        "downsample_ms": t_ds / steps, "downsample_gbs": ds_bytes / (t_ds / steps / 1e3) / 1e9,
+                        "downsample_frac": ds_bytes / (t_ds / steps / 1e3) / 1e9 / hbm_gbs}
+    tk.close()
+    return out
+
+
 # ------------------------------------------------------------- serving
 
 SERVE_RES = [(480, 854), (720, 1280), (1080, 1920)]
@@ -632,6 +699,7 @@ def main():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-train", action="store_true")
     ap.add_argument("--no-group", action="store_true")
+    ap.add_argument("--no-rsa", action="store_true", help="skip the downsample + 8x8x8 tokenizer section")
     ap.add_argument("--serve-streams", type=int, default=64)
     ap.add_argument("--serve-horizon", type=float, default=20.0)
     ap.add_argument("--serve-chunks", type=int, default=16)

@@ -55,15 +55,20 @@ enum tok_err {
 enum tok_precision { TOK_BF16 = 1, TOK_FP32 = 2 };
 enum tok_time_pad { TOK_PAD_REPLICATE = 0, TOK_PAD_ZERO = 1 };
 enum tok_arch_kind { TOK_ARCH_FULL = 0, TOK_ARCH_STAGE = 1 };
+/* pixel element types of tok_downsample's input (bf16 / fp32 match tok_precision) */
+enum tok_pixel_type { TOK_PIX_U8 = 0, TOK_PIX_BF16 = 1, TOK_PIX_FP32 = 2 };
 
 /* Architecture descriptor. The paper gives no layer list (it builds on a
  * published video tokenizer, Sec. 7); this descriptor is the reading used:
- *  FULL : stem conv k3 stride (1,2,2) -> per level l < nlevels: `blocks`
+ *  FULL : stem conv k3 stride (t_stem,2,2) -> per level l < nlevels: `blocks`
  *         causal residual blocks at ch[l] (GN->SiLU->conv->GN->SiLU->conv,
  *         1x1x1 skip conv when channels change), a k3 stride-(2,2,2) conv
  *         between levels -> GN->SiLU->conv to zdim -> FSQ. The decoder mirrors
  *         it with k3 convs to ch[l-1]*8 channels + depth-to-space (2,2,2),
- *         and a final conv to 3*4 channels + depth-to-space (1,2,2).
+ *         and a final conv to 3*4*t_stem channels + depth-to-space
+ *         (t_stem,2,2). t_stem = 1 is the 4x temporal / 8x8 spatial setting
+ *         with 3 levels; t_stem = 2 the 8x temporal / 8x8 spatial one (Sec. 4.1),
+ *         which makes s_T = t_stem * 2^(nlevels-1) frames per latent frame.
  *  STAGE: conv k3 in->ch[0] -> conv k3 stride (1,2,2) ch[0]->ch[1] ->
  *         GN->SiLU -> 1x1x1 conv ch[1]->zdim -> FSQ (encoder only).
  * GroupNorm statistics are per (sample, group, frame) (causal); the group
@@ -79,6 +84,7 @@ typedef struct tok_arch {
     int gn_groups;       /* 32 */
     float gn_eps;        /* 1e-6 */
     int time_pad;        /* tok_time_pad for the causal left padding */
+    int t_stem;          /* FULL: temporal stride of the stem, 1 or 2 (default 1) */
 } tok_arch;
 
 /* Fill `a` with the default tokenizer: FULL, ch {128,256,512}, 2 blocks per
@@ -257,6 +263,21 @@ int tok_residual_sparse(const float* d_r, int N, int n_windows, int H, int W, in
  * d_pos / d_val (entries past d_seg_offsets[N*n_windows] are ignored). */
 int tok_residual_apply(float* d_xhat, int N, int T, int H, int W, int C, int window, const int32_t* d_pos,
                        const float* d_val, const int64_t* d_seg_offsets, int64_t capacity, void* stream);
+
+/* Resolution control (Sec. 5): downsampling of frames by an integer factor
+ * s before encoding (the paper uses 2x and 3x of 1080p). Reading: each output
+ * pixel is the mean of the s x s input block it covers (area filter, blocks
+ * anchored at the top-left corner); Ho = H/s, Wo = W/s rounded down, trailing
+ * rows and columns unused. The mean is float32 in a fixed order (float input:
+ * summed row by row, left to right, then one division by s*s; uint8 input:
+ * exact integer sum, division by s*s, then m / 127.5 - 1 into [-1, 1]) and
+ * rounded to the output type (bf16: to nearest, ties to even).
+ * d_x (F,H,W,C) channels-last frames of in_type (tok_pixel_type); d_y
+ * (F,Ho,Wo,C) of out_precision (TOK_BF16 or TOK_FP32). 1 <= s <= 8; F = 0
+ * is a no-op (the pointers may then be NULL).
+ * Errors: TOK_EINVAL (pointers, types, s), TOK_ESHAPE (H < s or W < s). */
+int tok_downsample(int in_type, const void* d_x, int F, int H, int W, int C, int s, int out_precision, void* d_y,
+                   void* stream);
 
 /* GoP boundary blending (Sec. 6.1, Eq. 2): for i = 1..n, frame i of the
  * current GoP becomes a_i * prev[T_prev-n+i] + (1 - a_i) * curr[i] with

@@ -8,5 +8,5 @@ been built.
 """
 from . import _lib  # noqa: F401
 from .tokenizer import (Tokenizer, conv3d, dequantize, groupnorm_silu, drop_mask, make_arch, pack_rows, quantize,  # noqa: F401
-                        similarity_mask, residual, residual_sparse, residual_apply, gop_blend, temporal_loss,
+                        similarity_mask, residual, residual_sparse, residual_apply, gop_blend, temporal_loss, downsample,
                         unpack_rows, zero_index)

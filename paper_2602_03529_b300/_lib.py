@@ -17,6 +17,7 @@ TOK_OK, TOK_EINVAL, TOK_ESHAPE, TOK_ENOMEM, TOK_ECUDA, TOK_ETIMEOUT, TOK_EDEVICE
 TOK_BF16, TOK_FP32 = 1, 2
 TOK_PAD_REPLICATE, TOK_PAD_ZERO = 0, 1
 TOK_ARCH_FULL, TOK_ARCH_STAGE = 0, 1
+TOK_PIX_U8, TOK_PIX_BF16, TOK_PIX_FP32 = 0, 1, 2
 
 
 class tok_arch(C.Structure):
@@ -31,6 +32,7 @@ class tok_arch(C.Structure):
         ("gn_groups", C.c_int),
         ("gn_eps", C.c_float),
         ("time_pad", C.c_int),
+        ("t_stem", C.c_int),
     ]
 
 
@@ -81,6 +83,7 @@ _SIGS = {
     "tok_encode": (i32, [vp, vp, i32, i32, i32, i32, vp, vp, vp, vp]),
     "tok_decode": (i32, [vp, vp, i32, i32, i32, i32, i32, i32, vp, vp, vp]),
     "tok_set_cta_tiles": (i32, [vp, i32]),
+    "tok_downsample": (i32, [i32, vp, i32, i32, i32, i32, i32, i32, vp, vp]),
     "tok_gop_blend": (i32, [vp, i32, vp, vp, i32, i32, i32, i32, i32, i32, vp]),
     "tok_temporal_loss_workspace_bytes": (sz, [i32, i32, i32, i32, i32]),
     "tok_temporal_loss": (i32, [vp, vp, i32, i32, i32, i32, i32, i32, i32, vp, vp, vp, sz, vp]),
@@ -247,6 +250,10 @@ def tok_residual_sparse(r, N, nwin, H, W, C, pos, val, seg_off, ws, ws_bytes, cu
 def tok_residual_apply(xhat, N, T, H, W, C, window, pos, val, seg_off, capacity, cuda_stream) -> None:
     _ck(_call("tok_residual_apply", xhat, N, T, H, W, C, window, pos, val, seg_off, capacity, cuda_stream),
         "tok_residual_apply")
+
+
+def tok_downsample(in_type, x, F, H, W, C, s, out_precision, y, cuda_stream) -> None:
+    _ck(_call("tok_downsample", in_type, x, F, H, W, C, s, out_precision, y, cuda_stream), "tok_downsample")
 
 
 def tok_gop_blend(prev, Tp, curr, out, N, T, H, W, C, n, cuda_stream) -> None:

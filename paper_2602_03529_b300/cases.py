@@ -5,6 +5,9 @@
     python -m paper_2602_03529_b300.cases train [--N 2 --T 17 --H 256 --W 256]
         one training step (forward with 10% drop, MSE, backward, SGD), then one
         more forward + backward
+    python -m paper_2602_03529_b300.cases downsample [--N 4 --T 17 --H 1080 --W 1920 --s 3]
+        three s x s area downsamples of seeded uint8 frames to bf16 (the
+        resolution control of the 1080p encoder input)
 
 Inputs come from the seeded generators in `synthetic`; weights are He-normal
 from seed 0. Both exit non-zero if the library's device status word reports
@@ -54,17 +57,35 @@ def train(N: int, T: int, H: int, W: int) -> None:
     print("train ok", N, T, H, W)
 
 
+def downsample(N: int, T: int, H: int, W: int, s: int) -> None:
+    import numpy as np
+    import torch
+
+    from . import downsample as ds
+
+    x = torch.from_numpy(np.random.default_rng(8).integers(0, 256, (N, T, H, W, 3), dtype=np.uint8)).cuda()
+    y = ds(x, s, torch.bfloat16)
+    for _ in range(2):
+        ds(x, s, torch.bfloat16, out=y)
+    torch.cuda.synchronize()
+    print("downsample ok", tuple(y.shape))
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["clip", "train"])
+    ap.add_argument("case", choices=["clip", "train", "downsample"])
     ap.add_argument("--N", type=int)
     ap.add_argument("--T", type=int)
     ap.add_argument("--H", type=int)
     ap.add_argument("--W", type=int)
+    ap.add_argument("--s", type=int, default=3)
     a = ap.parse_args()
-    dflt = {"clip": (1, 5, 720, 1280), "train": (2, 17, 256, 256)}[a.case]
+    dflt = {"clip": (1, 5, 720, 1280), "train": (2, 17, 256, 256), "downsample": (4, 17, 1080, 1920)}[a.case]
     shape = [v if v is not None else d for v, d in zip((a.N, a.T, a.H, a.W), dflt)]
-    (clip if a.case == "clip" else train)(*shape)
+    if a.case == "downsample":
+        downsample(*shape, a.s)
+    else:
+        (clip if a.case == "clip" else train)(*shape)
 
 
 if __name__ == "__main__":

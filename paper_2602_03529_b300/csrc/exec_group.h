@@ -227,20 +227,25 @@ struct GroupExec : Exec {
     }
 
     // Pixel input of the first conv: the BF16 path gathers the im2col matrix
-    // (stride_hw 2 for the stem, 1 for the single stage); the FP32 path edge-pads.
+    // (stride (t_stem, 2, 2) for the stem, 1 for the single stage); the FP32
+    // path edge-pads. A stem with temporal stride 2 sees a stream's later
+    // chunks start one frame after an output frame, as the stride-2 convs do.
     MAct first_input(const char* name, const void* const* x, const int* N, const int* T, const int* H, const int* W,
-                     int stride_hw) {
+                     int stride_hw, int stride_t) {
         MAct dims;
         for (int p = 0; p < P; ++p) {
             const Dims d = clip_dims(c, T[p], H[p], W[p]);
             if (c->bf16()) {
                 GatherGeo g = gather_pixels(N[p], T[p], H[p], W[p], d.Hp, d.Wp, stride_hw);
+                g.st = stride_t;
+                g.Tout = (T[p] - 1) / stride_t + 1;
                 const __nv_bfloat16* ph = stream_hist_pixels(p, g, name);
+                if (ph && stride_t == 2) g.t_off = -1;
                 other([&] { return launch_im2col_pixels(static_cast<const __nv_bfloat16*>(x[p]), ph, g,
                                                         reinterpret_cast<__nv_bfloat16*>(pr[p].w.gather), s); },
                       gather_bytes(g));
                 stream_update(p, name, x[p], T[p]);
-                dims[p] = Act{nullptr, N[p], T[p], d.Hp / stride_hw, d.Wp / stride_hw, 0};
+                dims[p] = Act{nullptr, N[p], g.Tout, d.Hp / stride_hw, d.Wp / stride_hw, 0};
             } else {
                 float* P_ = reinterpret_cast<float*>(pr[p].w.gather);
                 const float* xs = static_cast<const float*>(x[p]);
@@ -300,7 +305,7 @@ struct GroupExec : Exec {
         int ix = 0;
         MAct X;
         if (ar.kind == TOK_ARCH_STAGE) {
-            MAct in = first_input("stage.c0", x, N, T, H, W, 1);
+            MAct in = first_input("stage.c0", x, N, T, H, W, 1, 1);
             if (c->bf16())
                 X = conv_gathered("stage.c0", in, s0, OUT_PLAIN, nullptr);
             else
@@ -310,11 +315,11 @@ struct GroupExec : Exec {
             out_conv("stage.out", A, z, idx);
             return;
         }
-        MAct in = first_input("enc.stem", x, N, T, H, W, 2);
+        MAct in = first_input("enc.stem", x, N, T, H, W, 2, ar.t_stem);
         if (c->bf16())
             X = conv_gathered("enc.stem", in, s0, OUT_PLAIN, nullptr);
         else
-            X = conv("enc.stem", in, s0, nullptr, 1, 2, 2);
+            X = conv("enc.stem", in, s0, nullptr, ar.t_stem, 2, 2);
         for (int l = 0; l < ar.nlevels; ++l) {
             for (int b = 0; b < ar.blocks; ++b) ix = block("enc.l" + std::to_string(l) + ".b" + std::to_string(b), ix, X);
             if (l < ar.nlevels - 1) {
@@ -394,7 +399,7 @@ struct GroupExec : Exec {
         MAct A = gn_silu("dec.out_gn", X, other_slot(ix));
         void* o[kMaxConvGroup];
         for (int p = 0; p < P; ++p) o[p] = xhat[p];
-        conv_d2s("dec.out", A, o, 1, 2, 2, H, W, true);
+        conv_d2s("dec.out", A, o, ar.t_stem, 2, 2, H, W, true);
     }
 };
 

@@ -84,6 +84,10 @@ int launch_residual_sparse(const float* r, long long nseg, long long E, int32_t*
 int launch_residual_apply(float* xh, long long N, int Tf, long long E, int window, const int32_t* pos,
                           const float* val, const int64_t* seg_off, long long cap, cudaStream_t s);
 
+// resolution-control downsampling (k_resize.cu); in_type 0 uint8, 1 bf16, 2 fp32
+int launch_downsample(int in_type, const void* x, long long F, int H, int W, int C, int s, bool out_bf16, void* y,
+                      cudaStream_t st);
+
 // GoP boundary smoothing (k_gop.cu)
 int launch_gop_blend(const float* prev, int Tp, const float* curr, float* out, long long N, int T, long long E, int n,
                      cudaStream_t s);

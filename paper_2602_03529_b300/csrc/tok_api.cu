@@ -33,6 +33,7 @@ void tok_arch_default(tok_arch* a) {
     a->gn_groups = 32;
     a->gn_eps = 1e-6f;
     a->time_pad = TOK_PAD_REPLICATE;
+    a->t_stem = 1;
 }
 
 const char* tok_strerror(int code) {
@@ -56,6 +57,7 @@ int tok_create(const tok_arch* arch, int precision, tok_ctx** out) {
     if (arch->in_ch != 3 || !valid_levels(arch->levels, arch->nlev)) return TOK_EINVAL;
     if (arch->kind == TOK_ARCH_FULL) {
         if (arch->nlevels < 1 || arch->nlevels > 4 || arch->blocks < 0) return TOK_EINVAL;
+        if (arch->t_stem != 1 && arch->t_stem != 2) return TOK_EINVAL;
     } else if (arch->kind != TOK_ARCH_STAGE) {
         return TOK_EINVAL;
     }
@@ -421,6 +423,20 @@ int tok_residual_apply(float* xhat, int N, int T, int H, int W, int C, int windo
         return TOK_EINVAL;
     return launch_residual_apply(xhat, N, T, (long long)H * W * C, window, pos, val, seg_off, capacity,
                                  static_cast<cudaStream_t>(stream))
+               ? TOK_ECUDA
+               : TOK_OK;
+}
+
+int tok_downsample(int in_type, const void* x, int F, int H, int W, int C, int s, int out_precision, void* y,
+                   void* stream) {
+    if (F < 0 || H < 1 || W < 1 || C < 1 || s < 1 || s > 8) return TOK_EINVAL;
+    if (in_type != TOK_PIX_U8 && in_type != TOK_PIX_BF16 && in_type != TOK_PIX_FP32) return TOK_EINVAL;
+    if (out_precision != TOK_BF16 && out_precision != TOK_FP32) return TOK_EINVAL;
+    if (H < s || W < s) return TOK_ESHAPE;
+    if (F == 0) return TOK_OK;
+    if (!x || !y) return TOK_EINVAL;
+    return launch_downsample(in_type, x, F, H, W, C, s, out_precision == TOK_BF16, y,
+                             static_cast<cudaStream_t>(stream))
                ? TOK_ECUDA
                : TOK_OK;
 }

@@ -208,8 +208,8 @@ void build_layers(tok_ctx* c) {
         if (l > 0) add_conv(c, "dec.up" + std::to_string(l - 1), ch[l - 1] * 8, ch[l], 3, false);
     }
     add_gn(c, "dec.out_gn", ch[0]);
-    add_conv(c, "dec.out", a.in_ch * 4, ch[0], 3, false);
-    c->s_t = 1 << (a.nlevels - 1);
+    add_conv(c, "dec.out", a.in_ch * 4 * a.t_stem, ch[0], 3, false);
+    c->s_t = a.t_stem << (a.nlevels - 1);
     c->s_hw = 1 << a.nlevels;
 }
 
@@ -287,6 +287,13 @@ Dims clip_dims(const tok_ctx* c, int T, int H, int W) {
     return d;
 }
 
+// Frames out of the stem for T input frames (a whole clip or its first
+// chunk); a later chunk of s_T frames gives s_T / t_stem.
+int stem_frames(const tok_ctx* c, int T) {
+    const int ts = c->arch.kind == TOK_ARCH_FULL ? c->arch.t_stem : 1;
+    return (T - 1) / ts + 1;
+}
+
 Layout layout_for(const tok_ctx* c, int N, int T, int H, int W) {
     Layout L;
     const Dims d = clip_dims(c, T, H, W);
@@ -301,7 +308,7 @@ Layout layout_for(const tok_ctx* c, int N, int T, int H, int W) {
         act = std::max<size_t>((size_t)N * T * d.Hp * d.Wp * a.ch[0], (size_t)N * T * (d.Hp / 2) * (d.Wp / 2) * a.ch[1]) * es;
         gn_need((long long)N * T, (long long)(d.Hp / 2) * (d.Wp / 2), a.ch[1]);
     } else {
-        int Tl = T;
+        int Tl = stem_frames(c, T);
         for (int l = 0; l < a.nlevels; ++l) {
             const long long Hl = d.Hp >> (l + 1), Wl = d.Wp >> (l + 1);
             const int cmax = std::max(a.ch[l], l > 0 ? a.ch[l - 1] : a.ch[0]);
@@ -317,7 +324,7 @@ Layout layout_for(const tok_ctx* c, int N, int T, int H, int W) {
     if (c->bf16()) {
         // stem / stage.c0 im2col and dec.in im2col
         const long long m0 = a.kind == TOK_ARCH_STAGE ? (long long)N * T * d.Hp * d.Wp
-                                                       : (long long)N * T * (d.Hp / 2) * (d.Wp / 2);
+                                                       : (long long)N * stem_frames(c, T) * (d.Hp / 2) * (d.Wp / 2);
         g = (size_t)m0 * round_up(27 * a.in_ch, 64) * 2;
         g = std::max(g, (size_t)ntok * round_up(27 * a.nlev, 64) * 2);
     } else {

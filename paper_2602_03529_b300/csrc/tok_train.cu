@@ -62,7 +62,7 @@ TrainBufs train_layout(const tok_ctx* c, int N, int T, int H, int W, char* base)
     const size_t es = c->esize();
     const int L = a.nlevels;
     int Tl[4];
-    Tl[0] = T;
+    Tl[0] = stem_frames(c, T);
     for (int l = 1; l < L; ++l) Tl[l] = (Tl[l - 1] - 1) / 2 + 1;
     auto vox = [&](int l) { return (size_t)N * Tl[l] * (H >> (l + 1)) * (W >> (l + 1)); };
     size_t work = 0, gn = 0;
@@ -90,7 +90,7 @@ TrainBufs train_layout(const tok_ctx* c, int N, int T, int H, int W, char* base)
                                                cin0, G2, c->num_sms, c->bf16() ? 8 : 4));
         }
     }
-    work = std::max(work, vox(0) * (size_t)adj_cpad(c, 3 * 4) * es);
+    work = std::max(work, vox(0) * (size_t)adj_cpad(c, a.in_ch * 4 * a.t_stem) * es);
     const size_t ntok = (size_t)N * Tl[L - 1] * (H >> L) * (W >> L);
     b.z = reinterpret_cast<float*>(take(ntok * a.nlev * 4));
     b.idx = reinterpret_cast<int32_t*>(take(ntok * 4));
@@ -107,7 +107,7 @@ TrainBufs train_layout(const tok_ctx* c, int N, int T, int H, int W, char* base)
     b.G3 = take(work);
     b.G4 = take(work);
     b.Z = take(work);
-    size_t g = (size_t)N * T * (H / 2) * (W / 2) * round_up(27 * a.in_ch, 64) * 2;
+    size_t g = (size_t)N * Tl[0] * (H / 2) * (W / 2) * round_up(27 * a.in_ch, 64) * 2;
     g = std::max(g, ntok * (size_t)round_up(27 * a.nlev, 64) * 2);
     b.gather = take(c->bf16() ? g : 256);
     b.gn = take(gn);
@@ -146,13 +146,14 @@ struct TrainExec : Exec {
         const int L = ar.nlevels;
         Act X;
         if (c->bf16()) {
-            GatherGeo g = gather_pixels(N, T, H, W, H, W, 2);
+            const GatherGeo g = stem_geo(N, T, H, W);
             other([&] { return launch_im2col_pixels(static_cast<const __nv_bfloat16*>(x), nullptr, g,
                                                     reinterpret_cast<__nv_bfloat16*>(w.gather), s); },
                   gather_bytes(g));
-            X = conv_gathered("enc.stem", N, T, H / 2, W / 2, b.enc[0][0], OUT_PLAIN, nullptr);
+            X = conv_gathered("enc.stem", N, g.Tout, H / 2, W / 2, b.enc[0][0], OUT_PLAIN, nullptr);
         } else {
-            X = conv("enc.stem", Act{const_cast<void*>(x), N, T, H, W, ar.in_ch}, b.enc[0][0], nullptr, 1, 2, 2);
+            X = conv("enc.stem", Act{const_cast<void*>(x), N, T, H, W, ar.in_ch}, b.enc[0][0], nullptr, ar.t_stem, 2,
+                     2);
         }
         for (int l = 0; l < L; ++l) {
             for (int k = 0; k < ar.blocks; ++k)
@@ -199,7 +200,7 @@ struct TrainExec : Exec {
                                     false);
         }
         A = gn_silu("dec.out_gn", X, b.R1);
-        conv_d2s("dec.out", A, xhat, 1, 2, 2, H, W, true);
+        conv_d2s("dec.out", A, xhat, ar.t_stem, 2, 2, H, W, true);
         const long long n = (long long)N * T * H * W * ar.in_ch;
         if (c->bf16())
             other([&] { return launch_mse<__nv_bfloat16>(xhat, static_cast<const __nv_bfloat16*>(x), n, dxhat, loss,
@@ -208,6 +209,14 @@ struct TrainExec : Exec {
         else
             other([&] { return launch_mse<float>(xhat, static_cast<const float*>(x), n, dxhat, loss, b.mse, s); },
                   (double)n * 12, 2);
+    }
+
+    // im2col geometry of the stem (3x3x3, stride (t_stem, 2, 2) over the pixels)
+    GatherGeo stem_geo(int N, int T, int H, int W) {
+        GatherGeo g = gather_pixels(N, T, H, W, H, W, 2);
+        g.st = c->arch.t_stem;
+        g.Tout = stem_frames(c, T);
+        return g;
     }
 
     // im2col geometry of the decoder input conv (3x3x3 over the token codes)
@@ -411,21 +420,23 @@ struct TrainExec : Exec {
         const int L = ar.nlevels;
         const int N = c->train_N, T = c->train_T, H = c->train_H, W = c->train_W;
         int Tl[4];
-        Tl[0] = T;
+        Tl[0] = stem_frames(c, T);
         for (int l = 1; l < L; ++l) Tl[l] = (Tl[l - 1] - 1) / 2 + 1;
         auto lev = [&](int l, void* p, int C) { return Act{p, N, Tl[l], H >> (l + 1), W >> (l + 1), C}; };
         char* gcur = b.GA;
         char* galt = b.GB;
-        // dec.out: depth-to-space (1,2,2) adjoint of dL/dx_hat
+        // dec.out: depth-to-space (t_stem,2,2) adjoint of dL/dx_hat (the trimmed
+        // first t_stem-1 frames come back as zeros)
         const ConvW& co = c->convs[c->cindex["dec.out"]];
+        const int ts = ar.t_stem;
         if (c->bf16())
-            other([&] { return launch_s2d<float, __nv_bfloat16>(dxhat, N, T, H, W, ar.in_ch, 1, 2, 2, 0, T, H / 2,
-                                                                W / 2, co.cpad, reinterpret_cast<__nv_bfloat16*>(b.Z),
-                                                                s); },
+            other([&] { return launch_s2d<float, __nv_bfloat16>(dxhat, N, T, H, W, ar.in_ch, ts, 2, 2, ts - 1, Tl[0],
+                                                                H / 2, W / 2, co.cpad,
+                                                                reinterpret_cast<__nv_bfloat16*>(b.Z), s); },
                   (double)N * T * H * W * 6);
         else
-            other([&] { return launch_s2d<float, float>(dxhat, N, T, H, W, ar.in_ch, 1, 2, 2, 0, T, H / 2, W / 2,
-                                                        co.cpad, reinterpret_cast<float*>(b.Z), s); },
+            other([&] { return launch_s2d<float, float>(dxhat, N, T, H, W, ar.in_ch, ts, 2, 2, ts - 1, Tl[0], H / 2,
+                                                        W / 2, co.cpad, reinterpret_cast<float*>(b.Z), s); },
                   (double)N * T * H * W * 8);
         Act dY = lev(0, b.Z, co.cpad);
         Act X0 = lev(0, b.dec[0][ar.blocks], ar.ch[0]);
@@ -521,16 +532,16 @@ struct TrainExec : Exec {
                 G = lev(l - 1, gcur, ar.ch[l - 1]);
             }
         }
-        // stem (stride (1,2,2)) from the pixels
+        // stem (stride (t_stem,2,2)) from the pixels
         Act xin{const_cast<void*>(c->train_x), N, T, H, W, ar.in_ch};
         if (c->bf16()) {
-            const GatherGeo g = gather_pixels(N, T, H, W, H, W, 2);
+            const GatherGeo g = stem_geo(N, T, H, W);
             other([&] { return launch_im2col_pixels(static_cast<const __nv_bfloat16*>(xin.p), nullptr, g,
                                                     reinterpret_cast<__nv_bfloat16*>(w.gather), s); },
                   gather_bytes(g));
             wgrad_gathered("enc.stem", G, G.C, g.Kpad);
         } else {
-            wgrad("enc.stem", G, G.C, xin, 1, 2);
+            wgrad("enc.stem", G, G.C, xin, ts, 2);
         }
     }
 };

@@ -18,7 +18,9 @@ PRECISIONS = {"bf16": L.TOK_BF16, "fp32": L.TOK_FP32}
 
 
 def make_arch(kind="full", ch=(128, 256, 512), blocks=2, levels=(8, 8, 8, 5, 5, 5), gn_groups=32,
-              gn_eps=1e-6, time_pad="replicate") -> L.tok_arch:
+              gn_eps=1e-6, time_pad="replicate", t_stem=1) -> L.tok_arch:
+    """Architecture descriptor; ``t_stem`` = 2 gives the 8x temporal / 8x8 spatial setting
+    (Sec. 4.1) with three levels, 1 the 4x / 8x8 one."""
     a = L.tok_arch_default()
     a.kind = L.TOK_ARCH_FULL if kind == "full" else L.TOK_ARCH_STAGE
     a.nlevels = len(ch)
@@ -31,6 +33,7 @@ def make_arch(kind="full", ch=(128, 256, 512), blocks=2, levels=(8, 8, 8, 5, 5, 
     a.gn_groups = gn_groups
     a.gn_eps = gn_eps
     a.time_pad = L.TOK_PAD_REPLICATE if time_pad == "replicate" else L.TOK_PAD_ZERO
+    a.t_stem = t_stem
     return a
 
 
@@ -199,7 +202,7 @@ class Tokenizer:
 
     @property
     def s_t(self):
-        return 1 if self.arch.kind == L.TOK_ARCH_STAGE else 2 ** (self.arch.nlevels - 1)
+        return 1 if self.arch.kind == L.TOK_ARCH_STAGE else self.arch.t_stem * 2 ** (self.arch.nlevels - 1)
 
     def status(self) -> int:
         return L.tok_status(self.ctx)
@@ -313,6 +316,27 @@ def residual_apply(xhat: torch.Tensor, window: int, pos, val, offs, stream=None)
     L.tok_residual_apply(_ptr(xhat), N, T, H, W, C, window, _ptr(pos), _ptr(val), _ptr(offs), pos.numel(),
                          _stream_ptr(stream))
     return xhat
+
+
+_PIX = {torch.uint8: L.TOK_PIX_U8, torch.bfloat16: L.TOK_PIX_BF16, torch.float32: L.TOK_PIX_FP32}
+
+
+def downsample(x: torch.Tensor, s: int, out_dtype=torch.bfloat16, out=None, stream=None):
+    """Sec. 5 resolution control: s x s area-mean downsampling of frames (..., H, W, C);
+    uint8 input is mapped to [-1, 1]. Returns (..., H//s, W//s, C) of out_dtype."""
+    if x.dtype not in _PIX:
+        raise ValueError("x must be uint8, bfloat16 or float32")
+    if out_dtype not in (torch.bfloat16, torch.float32):
+        raise ValueError("out_dtype must be bfloat16 or float32")
+    *lead, H, W, C = x.shape
+    F = 1
+    for d in lead:
+        F *= d
+    if out is None:
+        out = torch.empty((*lead, H // s, W // s, C), device=x.device, dtype=out_dtype)
+    L.tok_downsample(_PIX[x.dtype], _ptr(x), F, H, W, C, s, PRECISIONS["bf16" if out_dtype == torch.bfloat16
+                                                                      else "fp32"], _ptr(out), _stream_ptr(stream))
+    return out
 
 
 def gop_blend(xhat_prev: torch.Tensor, xhat_curr: torch.Tensor, n: int, out=None, stream=None):

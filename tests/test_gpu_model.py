@@ -108,3 +108,31 @@ def test_default_tokenizer_64px(P, prec):
     assert rep["out_of_band"] == 0
     assert rep["z_err"] <= TOL[prec]["z"]
     assert rep["x_err"] <= TOL[prec]["x"]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("shape", [(1, 17, 32, 48), (2, 9, 24, 40)])
+def test_8x8x8_tokenizer(P, prec, shape):
+    """The 8x temporal / 8x8 spatial setting (Sec. 4.1): stem stride (2,2,2), pixel head
+    with depth-to-space (2,2,2); 8 frames per latent frame, ragged H/W."""
+    kw = dict(ch=(64, 128, 256), blocks=1, t_stem=2)
+    rep = run_case(P, prec, kw, Arch(ch=(64, 128, 256), blocks=1, t_stem=2), *shape, seed=5)
+    print(prec, shape, rep)
+    assert rep["x_shape_ok"]
+    assert rep["out_of_band"] == 0
+    assert rep["z_err"] <= TOL[prec]["z"]
+    assert rep["x_err"] <= TOL[prec]["x"]
+
+
+def test_t_stem_validation(P):
+    from paper_2602_03529_b300 import _lib as L
+    with pytest.raises(L.TokError) as e:
+        P.Tokenizer("bf16", ch=(64, 128, 256), blocks=1, t_stem=3)
+    assert e.value.code == L.TOK_EINVAL
+    tk = P.Tokenizer("bf16", ch=(64, 128, 256), blocks=1, t_stem=2)
+    assert tk.s_t == 8
+    assert tuple(tk.latent_shape(17, 64, 64)) == (3, 8, 8)
+    with pytest.raises(L.TokError) as e:
+        tk.latent_shape(13, 64, 64)        # a clip's T - 1 must be a multiple of 8
+    assert e.value.code == L.TOK_ESHAPE
+    tk.close()

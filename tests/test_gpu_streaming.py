@@ -1,8 +1,9 @@
 """Chunked streaming equals the whole clip, bitwise (the conv caches carry the
 causal left context across chunks; GoP-style segment coding of Sec. 4.2/4.3).
 
-Chunk 0 is frame 0 (latent 0); chunk k >= 1 is frames 4k-3..4k (latent k).
-Decoding latent k of a stream gives frame 0 (k = 0) or frames 4k-3..4k.
+Chunk 0 is frame 0 (latent 0); chunk k >= 1 is frames s(k-1)+1..sk (latent k),
+s = 4 frames per latent frame (8 with the temporal-stride-2 stem). Decoding
+latent k of a stream gives frame 0 (k = 0) or frames s(k-1)+1..sk.
 Every convolution computes each output with the same sequence of tensor-core
 (or FMA) operations whatever frames share its launch, and GroupNorm's
 per-frame reduction order does not depend on the frame count, so the
@@ -34,7 +35,8 @@ def _run(P, prec, kw, T, H, W, seed=0):
     xh_c = tk.decode(idx_c, H, W)
     vid = tk.stream_open(H, W)
     assert tk.stream_bytes(H, W) > 0
-    bounds = [(0, 1)] + [(4 * k - 3, 4 * k + 1) for k in range(1, (T - 1) // 4 + 1)]
+    st = tk.s_t
+    bounds = [(0, 1)] + [(st * (k - 1) + 1, st * k + 1) for k in range(1, (T - 1) // st + 1)]
     zs, ids = [], []
     for a, b in bounds:
         z, idx = tk.encode(x[:, a:b].contiguous(), video=vid)
@@ -53,6 +55,16 @@ def _run(P, prec, kw, T, H, W, seed=0):
 @pytest.mark.parametrize("pad", ["replicate", "zero"])
 def test_stream_equals_clip_small(P, prec, pad):
     out = _run(P, prec, dict(ch=(64, 128, 256), blocks=1, time_pad=pad), 13, 40, 56, seed=3)
+    for k, (s, c) in out.items():
+        assert s.shape == c.shape, k
+        assert torch.equal(s, c), (k, float((s.float() - c.float()).abs().max()))
+
+
+@pytest.mark.parametrize("prec", ["bf16", "fp32"])
+@pytest.mark.parametrize("pad", ["replicate", "zero"])
+def test_stream_equals_clip_8x8x8(P, prec, pad):
+    """8 frames per chunk: the stem's stride-2 taps reach one frame back into the cache."""
+    out = _run(P, prec, dict(ch=(64, 128, 256), blocks=1, time_pad=pad, t_stem=2), 25, 40, 56, seed=6)
     for k, (s, c) in out.items():
         assert s.shape == c.shape, k
         assert torch.equal(s, c), (k, float((s.float() - c.float()).abs().max()))

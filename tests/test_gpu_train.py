@@ -36,9 +36,9 @@ def _params(arch, seed):
     return p
 
 
-def _run(P, prec, ch, shape, rate=0.2, seed=7, step=3, margin_keep=None, blocks=1):
+def _run(P, prec, ch, shape, rate=0.2, seed=7, step=3, margin_keep=None, blocks=1, t_stem=1):
     from paper_2602_03529_b300.train import Trainer
-    arch = Arch(ch=ch, blocks=blocks)
+    arch = Arch(ch=ch, blocks=blocks, t_stem=t_stem)
     p = _params(arch, 11)
     if prec == "bf16":
         p = {k: S.to_bf16_f32(v) for k, v in p.items()}
@@ -46,7 +46,7 @@ def _run(P, prec, ch, shape, rate=0.2, seed=7, step=3, margin_keep=None, blocks=
     x = S.blurred_noise_clip(5, N, T, H, W)
     if prec == "bf16":
         x = S.to_bf16_f32(x)
-    tk = P.Tokenizer(prec, ch=ch, blocks=blocks)
+    tk = P.Tokenizer(prec, ch=ch, blocks=blocks, t_stem=t_stem)
     tk.set_params(p)
     tr = Trainer(tk, N, T, H, W)
     dt = torch.bfloat16 if prec == "bf16" else torch.float32
@@ -102,6 +102,24 @@ def test_bf16_gradient_matches_oracle(P):
     print("per-kind weight gradient error", {k: round(rel[k], 5) for k in kinds if k in rel})
     for k in kinds:
         assert rel[k] <= 5e-2, (k, rel[k])
+    assert abs(loss - loss_ref) <= 2e-2 * abs(loss_ref)
+    assert worst[1] <= 5e-2, worst
+
+
+def test_fp32_gradient_8x8x8(P):
+    """Temporal-stride-2 stem and (2,2,2) pixel head: the stem's weight gradient over the
+    strided taps and the depth-to-space adjoint with its trimmed first frame."""
+    loss, loss_ref, rel = _run(P, "fp32", (16, 32, 64), (1, 9, 32, 32), t_stem=2)
+    worst = max(rel.items(), key=lambda kv: kv[1])
+    print("fp32 8x8x8 loss", loss, loss_ref, "worst", worst)
+    assert abs(loss - loss_ref) <= 1e-5 * abs(loss_ref)
+    assert worst[1] <= 1e-4, worst
+
+
+def test_bf16_gradient_8x8x8(P):
+    loss, loss_ref, rel = _run(P, "bf16", (64, 128, 256), (1, 9, 64, 64), margin_keep=0.12, t_stem=2)
+    worst = max(rel.items(), key=lambda kv: kv[1])
+    print("bf16 8x8x8 loss", loss, loss_ref, "worst", worst, {k: round(rel[k], 5) for k in ("enc.stem.w", "dec.out.w")})
     assert abs(loss - loss_ref) <= 2e-2 * abs(loss_ref)
     assert worst[1] <= 5e-2, worst
 
