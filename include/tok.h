@@ -449,6 +449,19 @@ typedef struct tok_profile_stats {
 } tok_profile_stats;
 int tok_profile_enable(tok_ctx* ctx, int on);
 int tok_profile_read(tok_ctx* ctx, tok_profile_stats* out);
+/* The individual launches recorded since the last tok_profile_read, in launch
+ * order (a trace): class (0 conv, 1 GroupNorm+SiLU, 2 other), device time,
+ * algorithmic work as above, and the layer name (".dgrad" / ".wgrad" / ".bwd"
+ * suffixes for the training backward) or a kernel label. Synchronises the
+ * events; writes at most `cap` records; *count receives the number recorded.
+ * Does not reset them (tok_profile_read does). */
+typedef struct tok_profile_record {
+    int cls;
+    float ms;
+    double work;
+    char name[40];
+} tok_profile_record;
+int tok_profile_records(tok_ctx* ctx, tok_profile_record* out, int cap, int* count);
 
 #ifdef __cplusplus
 }

@@ -44,6 +44,10 @@ class tok_profile_stats(C.Structure):
     ]
 
 
+class tok_profile_record(C.Structure):
+    _fields_ = [("cls", C.c_int), ("ms", C.c_float), ("work", C.c_double), ("name", C.c_char * 40)]
+
+
 TOK_MAX_BATCH = 8
 
 
@@ -127,6 +131,7 @@ _SIGS = {
     "tok_selftest_timeout": (i32, [vp, i64, vp]),
     "tok_launch_count": (i64, [vp]),
     "tok_profile_enable": (i32, [vp, i32]),
+    "tok_profile_records": (i32, [vp, vp, i32, C.POINTER(i32)]),
     "tok_profile_read": (i32, [vp, C.POINTER(tok_profile_stats)]),
 }
 
@@ -410,6 +415,14 @@ def tok_profile_read(ctx) -> dict:
     st = tok_profile_stats()
     _ck(_call("tok_profile_read", ctx, C.byref(st)), "tok_profile_read")
     return {f: getattr(st, f) for f, _ in tok_profile_stats._fields_}
+
+
+def tok_profile_records(ctx) -> list:
+    n = i32()
+    _ck(_call("tok_profile_records", ctx, None, 0, C.byref(n)), "tok_profile_records")
+    arr = (tok_profile_record * max(n.value, 1))()
+    _ck(_call("tok_profile_records", ctx, C.cast(arr, C.c_void_p), n.value, C.byref(n)), "tok_profile_records")
+    return [{"cls": r.cls, "ms": r.ms, "work": r.work, "name": r.name.decode()} for r in arr[:n.value]]
 
 
 def tok_param_total(ctx) -> int:

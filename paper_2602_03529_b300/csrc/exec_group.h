@@ -81,7 +81,7 @@ struct GroupExec : Exec {
             for (int p = 0; p < P; ++p) ck(launch_conv_simt(as[p], s));
             c->launches += P;
         }
-        pend(e, 0, flop);
+        pend(e, 0, flop, cw.name);
     }
 
     void slot(int i, void** out) const {
@@ -198,7 +198,7 @@ struct GroupExec : Exec {
                          (long long)in[p].N * in[p].T, (long long)in[p].H * in[p].W, pr[p].w.gn};
             ck(launch_gn_silu_group<float>(it, P, in[0].C, g.G, g.g, g.b, c->arch.gn_eps, false, s));
         }
-        pend(e, 1, bytes);
+        pend(e, 1, bytes, name);
         c->launches += 3;
         return out;
     }

@@ -43,6 +43,7 @@ struct TcGeo {
     int nkb;                 // K blocks per tile = taps * cpt
     int strided;             // parity view (sh = sw = 2)
     long long m_tiles;       // voxel tiles
+    int halo;                // K blocks are (dt, dw, channel block) groups of three dh taps
 };
 
 // A grouped launch: up to MAXP inputs of one layer (clips or stream chunks of
@@ -76,11 +77,21 @@ namespace {
 //                keeps the tensor pipe fed. TMEM then holds D^T (lanes =
 //                channels, columns = voxels) and the epilogue transposes
 //                through a small per-warp staging buffer.
-template <int BN, bool SWAP>
+//  HALO        : stride-1 3x3x3 layers load, per (dt, dw, 64-channel block),
+//                one box of BH + 2 input rows that serves the three dh taps:
+//                tap dh reads the box from row dh * BW on, a whole number of
+//                1 KB swizzle atoms for BW = 16, 32, 64, so the operand
+//                descriptor simply starts there. Three weight boxes (one per
+//                dh) go into the same stage. The activation bytes per K block
+//                drop from ROWS to (ROWS + 2 BW) / 3 voxel rows.
+constexpr int HALO_BW_MAX = 64;
+
+template <int BN, bool SWAP, bool HALO = false>
 struct Cfg {
     static constexpr int ROWS = SWAP ? 256 : 128;  // voxels per tile
-    static constexpr int ACT_BYTES = ROWS * 128;   // 64 bf16 channels per voxel row
-    static constexpr int W_BYTES = BN * 128;
+    static constexpr int ACT_BYTES = (ROWS + (HALO ? 2 * HALO_BW_MAX : 0)) * 128;  // 64 bf16 channels per row
+    static constexpr int W_TAP_BYTES = BN * 128;
+    static constexpr int W_BYTES = (HALO ? 3 : 1) * W_TAP_BYTES;
     static constexpr int STAGE = ACT_BYTES + W_BYTES;
     static constexpr int STAGES = (200 * 1024 / STAGE) > 8 ? 8 : (200 * 1024 / STAGE);
     static constexpr int ACC_COLS = SWAP ? ROWS : BN;  // TMEM columns per accumulator
@@ -171,10 +182,11 @@ __device__ __forceinline__ long long unit_tile(const TcGeo& g, long long lu, uin
 // the same weight tile; each CTA loads half of every weight box and multicasts
 // it to both, and each stage is released only when both CTAs' MMAs have read
 // it (the empty barrier counts one commit from each CTA).
-template <int BN, bool SWAP, int MAXP, int CL>
+template <int BN, bool SWAP, int MAXP, int CL, bool HALO>
 __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__ TcBatch<MAXP> B) {
-    using C = Cfg<BN, SWAP>;
+    using C = Cfg<BN, SWAP, HALO>;
     static_assert(CL == 1 || CL == 2, "CTA pairs at most");
+    static_assert(!HALO || CL == 1, "halo boxes with single CTAs");
     constexpr uint32_t HALF_W = C::W_BYTES / 2;  // one CTA's share of a weight box
     static_assert(CL == 1 || HALF_W % 1024 == 0, "weight halves must start on a swizzle atom");
     int* const status = B.a[0].status;
@@ -259,8 +271,11 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                         ok = false;
                         break;
                     }
+                    // plain: kb = (tap, cb); halo: kb = (dt, dw, cb) with the three dh taps inside
                     const int tap = kb / g.cpt, cb = kb - tap * g.cpt;
-                    const int dw = tap % a.kw, dh = (tap / a.kw) % a.kh, dt = tap / (a.kw * a.kh);
+                    const int dw = HALO ? tap % 3 : tap % a.kw;
+                    const int dh = HALO ? 0 : (tap / a.kw) % a.kh;
+                    const int dt = HALO ? tap / 3 : tap / (a.kw * a.kh);
                     const int ti = tc.to * a.st + dt + a.t_off;
                     const CUtensorMap* src = &B.tm_x[p];
                     int tcoord;
@@ -278,6 +293,21 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                     }
                     uint8_t* sa = smem + s * C::STAGE;
                     uint8_t* sb = sa + C::ACT_BYTES;
+                    if constexpr (HALO) {
+                        // rows th*BH - 1 .. th*BH + BH of the input frame (zeros outside)
+                        mbar_arrive_expect_tx(&full[s], (uint32_t)((g.BH + 2) * g.BW * 128 + C::W_BYTES));
+                        tma_load_4d(sa, src, &full[s], cb * 64, tc.tw * g.BW + dw - 1, tc.th * g.BH - 1, tcoord);
+#pragma unroll
+                        for (int d = 0; d < 3; ++d)
+                            tma_load_2d(sb + d * C::W_TAP_BYTES, &B.tm_w, &full[s],
+                                        ((dt * 3 + d) * 3 + dw) * a.Cin + cb * 64, tc.nt * BN);
+                        last_ph[s] = (int)ph;
+                        if (++s == C::STAGES) {
+                            s = 0;
+                            ph ^= 1;
+                        }
+                        continue;
+                    }
                     mbar_arrive_expect_tx(&full[s], C::STAGE);
                     if (!g.strided) {
                         tma_load_4d(sa, src, &full[s], cb * 64, tc.tw * g.BW + dw - pw_, tc.th * g.BH + dh - ph_,
@@ -325,7 +355,9 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
             int it = 0;
             for (long long u = cid; u < B.num_units && ok; u += ncl, ++it) {
                 long long lu;
-                const int nkb = B.g[problem_of(B, u, &lu)].nkb;
+                const TcGeo& gu = B.g[problem_of(B, u, &lu)];
+                const int nkb = gu.nkb;
+                const uint32_t row_step = (uint32_t)gu.BW * 128u;  // one input row of the halo box
                 const int acc = it & 1;
                 const uint32_t aph = (uint32_t)((it >> 1) & 1);
                 if (!mbar_wait(&tempty[acc], aph ^ 1, status, wait_ns)) break;
@@ -339,11 +371,23 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                     tc_fence_after();
                     const uint32_t s_act = smem_u32(smem + s * C::STAGE);
                     const uint32_t s_w = s_act + C::ACT_BYTES;
-                    const uint32_t op_a = SWAP ? s_w : s_act, op_b = SWAP ? s_act : s_w;
+                    if constexpr (HALO) {
 #pragma unroll
-                    for (int k = 0; k < 4; ++k)
-                        tc_mma_bf16(d, sw128_desc(op_a + k * 32), sw128_desc(op_b + k * 32), C::IDESC,
-                                    (kb | k) != 0 ? 1u : 0u);
+                        for (int dh = 0; dh < 3; ++dh) {
+                            const uint32_t xa = s_act + (uint32_t)dh * row_step, wa = s_w + (uint32_t)(dh * C::W_TAP_BYTES);
+                            const uint32_t op_a = SWAP ? wa : xa, op_b = SWAP ? xa : wa;
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+                                tc_mma_bf16(d, sw128_desc(op_a + k * 32), sw128_desc(op_b + k * 32), C::IDESC,
+                                            (kb | dh | k) != 0 ? 1u : 0u);
+                        }
+                    } else {
+                        const uint32_t op_a = SWAP ? s_w : s_act, op_b = SWAP ? s_act : s_w;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k)
+                            tc_mma_bf16(d, sw128_desc(op_a + k * 32), sw128_desc(op_b + k * 32), C::IDESC,
+                                        (kb | k) != 0 ? 1u : 0u);
+                    }
                     if constexpr (CL == 1)
                         tc_commit(&empty[s]);
                     else
@@ -513,10 +557,22 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                             o[4 * i + 2] = f.z;
                             o[4 * i + 3] = f.w;
                         }
-                        const long long off =
-                            ((((long long)tc.n * a.oT + tc.to) * a.oH + ho) * a.oW + wo) * a.oC + c0;
-                        if (a.residual) add_bf16x16(static_cast<const __nv_bfloat16*>(a.residual) + off, o);
-                        store_bf16x16(static_cast<__nv_bfloat16*>(a.out) + off, o);
+                        // plain: voxel (to, ho, wo); depth-to-space (oC % 16 == 0): the 16 channels
+                        // lie in one sub-position (t, b, c) of the output block
+                        int ot = tc.to, oh = ho, ow = wo, ch0 = c0;
+                        if (a.mode == OUT_D2S) {
+                            const int sub = c0 / a.oC;
+                            ch0 = c0 - sub * a.oC;
+                            ow = wo * a.rw + sub % a.rw;
+                            oh = ho * a.rh + (sub / a.rw) % a.rh;
+                            ot = tc.to * a.rt + sub / (a.rw * a.rh) - a.drop_t;
+                        }
+                        if (ot >= 0 && ot < a.oT && oh < a.oH && ow < a.oW) {
+                            const long long off =
+                                ((((long long)tc.n * a.oT + ot) * a.oH + oh) * a.oW + ow) * a.oC + ch0;
+                            if (a.residual) add_bf16x16(static_cast<const __nv_bfloat16*>(a.residual) + off, o);
+                            store_bf16x16(static_cast<__nv_bfloat16*>(a.out) + off, o);
+                        }
                     }
                     __syncwarp();
                 }
@@ -542,8 +598,22 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                 }
                 if (a.mode == OUT_PLAIN) {
                     const long long off = ((((long long)tc.n * a.oT + tc.to) * a.oH + ho) * a.oW + wo) * a.oC + co0;
-                    if (a.residual) add_bf16x16(static_cast<const __nv_bfloat16*>(a.residual) + off, v);
-                    store_bf16x16(static_cast<__nv_bfloat16*>(a.out) + off, v);
+                    if (co0 + 16 <= a.Cout && (a.oC & 7) == 0 && !a.out_fp32) {
+                        if (a.residual) add_bf16x16(static_cast<const __nv_bfloat16*>(a.residual) + off, v);
+                        store_bf16x16(static_cast<__nv_bfloat16*>(a.out) + off, v);
+                    } else {
+                        // a partial group of 16 channels (narrow or ragged layers), or fp32 output
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            if (co0 + j >= a.Cout) break;
+                            float x = v[j];
+                            if (a.residual) x += __bfloat162float(static_cast<const __nv_bfloat16*>(a.residual)[off + j]);
+                            if (a.out_fp32)
+                                static_cast<float*>(a.out)[off + j] = x;
+                            else
+                                static_cast<__nv_bfloat16*>(a.out)[off + j] = __float2bfloat16_rn(x);
+                        }
+                    }
                 } else if (a.mode == OUT_D2S) {
                     if ((a.oC & 15) == 0) {
                         const int sub = co0 / a.oC, ch0 = co0 - sub * a.oC;
@@ -605,10 +675,10 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
     if constexpr (CL > 1) cluster_sync();  // neither CTA leaves while its peer may still address it
 }
 
-template <int BN, bool SWAP, int MAXP, int CL>
+template <int BN, bool SWAP, int MAXP, int CL, bool HALO = false>
 int launch_bn(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int cta_tiles, cudaStream_t stream) {
-    using C = Cfg<BN, SWAP>;
-    auto kern = conv_tc_kernel<BN, SWAP, MAXP, CL>;
+    using C = Cfg<BN, SWAP, HALO>;
+    auto kern = conv_tc_kernel<BN, SWAP, MAXP, CL, HALO>;
     TcBatch<MAXP> B;
     memset(&B, 0, sizeof(B));
     // with CTA pairs each CTA loads half of the weight box (BN / 2 rows)
@@ -618,14 +688,16 @@ int launch_bn(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int c
         const ConvArgs& a = as[p];
         TcGeo g = gs[p];
         const bool strided = g.strided != 0;
-        if (!encode_act_map(&B.tm_x[p], a.x, a.N * a.Tin, a.Hin, a.Win, a.Cin, g.BH, g.BW, strided)) return -1;
+        const int box_h = HALO ? g.BH + 2 : g.BH;  // the halo box: one input row above and below
+        if (!encode_act_map(&B.tm_x[p], a.x, a.N * a.Tin, a.Hin, a.Win, a.Cin, box_h, g.BW, strided)) return -1;
         if (a.hist) {
-            if (!encode_act_map(&B.tm_h[p], a.hist, a.N * a.hist_T, a.Hin, a.Win, a.Cin, g.BH, g.BW, strided))
+            if (!encode_act_map(&B.tm_h[p], a.hist, a.N * a.hist_T, a.Hin, a.Win, a.Cin, box_h, g.BW, strided))
                 return -1;
         } else {
             B.tm_h[p] = B.tm_x[p];
         }
-        g.n_tiles = a.Cout_pad / BN;
+        // weight tiles that hold output channels (narrow layers have padded weight rows)
+        g.n_tiles = std::min(a.Cout_pad, (a.Cout + BN - 1) / BN * BN) / BN;
         g.m_tiles = (long long)a.N * a.Tout * g.tiles_h * g.tiles_w;
         g.num_tiles = g.m_tiles * g.n_tiles;
         total += CL == 1 ? g.num_tiles : (g.m_tiles + 1) / 2 * g.n_tiles;
@@ -684,6 +756,12 @@ int launch_bn(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int c
 
 // CTA pairs for layers with at least one wave of tiles (weight halves of 64+
 // rows), single CTAs otherwise and whenever CTA lifetimes are bounded.
+template <int BN, bool SWAP>
+int launch_bn_halo(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int cta_tiles, cudaStream_t stream) {
+    return count == 1 ? launch_bn<BN, SWAP, 1, 1, true>(as, gs, 1, num_sms, cta_tiles, stream)
+                      : launch_bn<BN, SWAP, kMaxConvGroup, 1, true>(as, gs, count, num_sms, cta_tiles, stream);
+}
+
 template <int BN, bool SWAP>
 int launch_bn_any(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int cta_tiles, bool pairs,
                   cudaStream_t stream) {
@@ -773,6 +851,23 @@ void choose_tile(int Hout, int Wout, int rows, int* BH, int* BW) {
     }
 }
 
+// Halo tiles: BW in {16, 32, 64} (the dh offset is a whole number of swizzle
+// atoms and the box fits the stage); fewest tiles, then fewest halo rows.
+void choose_tile_halo(int Hout, int Wout, int rows, int* BH, int* BW) {
+    long long best = -1, best_rows = 0;
+    for (int bw : {16, 32, 64}) {
+        const int bh = rows / bw;
+        const long long t = (long long)((Wout + bw - 1) / bw) * ((Hout + bh - 1) / bh);
+        const long long hr = t * (bh + 2) * bw;
+        if (best < 0 || t < best || (t == best && hr < best_rows)) {
+            best = t;
+            best_rows = hr;
+            *BW = bw;
+            *BH = bh;
+        }
+    }
+}
+
 int conv_tc_bn(int Cout_pad) {
     if (Cout_pad >= 256) return 256;
     if (Cout_pad >= 128) return 128;
@@ -810,20 +905,41 @@ int launch_conv_tc_group(const ConvArgs* as, int count, int num_sms, cudaStream_
             return -1;
     // the wide (swapped) form: exactly 128 output channels with plain bf16 output,
     // or a narrow layer (at most 32 channels, weights padded to 128 rows)
-    const bool swap = a0.Cout_pad == 128 &&
-                      ((a0.mode == OUT_PLAIN && !a0.out_fp32 && a0.Cout == 128) || a0.Cout <= 32);
+    // stride-1 3x3x3 layers share each input box among the three dh taps (halo form); a
+    // narrow halo layer (at most 32 channels) runs unswapped with 16 or 32 weight rows
+    const bool taps3 = a0.kh == 3 && a0.kw == 3 && a0.sh == 1 && a0.sw == 1;
+    const bool narrow = a0.Cout <= 32;
+    // wide layers of 128k channels with bf16 output: plain, or depth-to-space whose
+    // 16-channel groups stay within one sub-position
+    const bool wide = a0.Cout % 128 == 0 && a0.Cout_pad % 128 == 0 && !a0.out_fp32 &&
+                      (a0.mode == OUT_PLAIN || (a0.mode == OUT_D2S && a0.oC % 16 == 0));
+    const bool swap = (a0.Cout_pad == 128 &&
+                       ((a0.mode == OUT_PLAIN && !a0.out_fp32 && a0.Cout == 128) || (narrow && !taps3))) ||
+                      (taps3 && wide);
+    const bool halo = taps3 && (swap || narrow);
     TcGeo gs[kMaxConvGroup];
     for (int p = 0; p < count; ++p) {
         TcGeo& g = gs[p];
         const ConvArgs& a = as[p];
-        choose_tile(a.Hout, a.Wout, swap ? 256 : 128, &g.BH, &g.BW);
+        if (halo)
+            choose_tile_halo(a.Hout, a.Wout, swap ? 256 : 128, &g.BH, &g.BW);
+        else
+            choose_tile(a.Hout, a.Wout, swap ? 256 : 128, &g.BH, &g.BW);
         g.tiles_w = (a.Wout + g.BW - 1) / g.BW;
         g.tiles_h = (a.Hout + g.BH - 1) / g.BH;
         g.cpt = a.Cin / 64;
-        g.nkb = a.kt * a.kh * a.kw * g.cpt;
+        g.nkb = (halo ? a.kt * a.kw : a.kt * a.kh * a.kw) * g.cpt;
         g.strided = (a.sh == 2) ? 1 : 0;
+        g.halo = halo ? 1 : 0;
         g.n_tiles = 0;
         g.num_tiles = 0;
+    }
+    if (halo) {
+        if (swap) return launch_bn_halo<128, true>(as, gs, count, num_sms, cta_tiles, stream);
+        if (narrow) {
+            if (a0.Cout <= 16) return launch_bn_halo<16, false>(as, gs, count, num_sms, cta_tiles, stream);
+            return launch_bn_halo<32, false>(as, gs, count, num_sms, cta_tiles, stream);
+        }
     }
     if (swap) return launch_bn_any<128, true>(as, gs, count, num_sms, cta_tiles, pairs, stream);
     switch (conv_tc_bn(a0.Cout_pad)) {

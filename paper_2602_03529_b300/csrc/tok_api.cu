@@ -598,7 +598,6 @@ int tok_conv3d(int precision, const void* x, int N, int T, int H, int W, int Cin
     a.oW = a.Wout;
     a.oC = Cout;
     a.wait_ns = kWaitNs;
-    if (bf && Cout % 16 != 0) return TOK_ESHAPE;  // 16-channel vector epilogue
     const int e = bf ? launch_conv_tc(a, nsm, s) : launch_conv_simt(a, s);
     return e ? TOK_ECUDA : TOK_OK;
 }
@@ -668,6 +667,22 @@ int tok_profile_enable(tok_ctx* c, int on) {
     c->prof = on != 0;
     c->recs.clear();
     c->ev_used = 0;
+    return TOK_OK;
+}
+
+int tok_profile_records(tok_ctx* c, tok_profile_record* out, int cap, int* count) {
+    if (!c || !count || cap < 0 || (cap > 0 && !out)) return TOK_EINVAL;
+    *count = (int)c->recs.size();
+    for (int i = 0; i < (int)c->recs.size() && i < cap; ++i) {
+        const auto& r = c->recs[i];
+        if (cudaEventSynchronize(c->events[r.ev + 1]) != cudaSuccess) return TOK_ECUDA;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->events[r.ev], c->events[r.ev + 1]);
+        out[i].cls = r.cls;
+        out[i].ms = ms;
+        out[i].work = r.work;
+        memcpy(out[i].name, r.name, sizeof(out[i].name));
+    }
     return TOK_OK;
 }
 

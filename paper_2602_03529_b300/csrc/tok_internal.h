@@ -94,6 +94,7 @@ struct tok_ctx {
         int cls;
         double work;
         int ev;
+        char name[40];  // layer name (convs, GroupNorms) or kernel label
     };
     bool prof = false;
     std::vector<cudaEvent_t> events;
@@ -434,10 +435,15 @@ struct Exec {
         cudaEventRecord(c->events[e], s);
         return e;
     }
-    void pend(int e, int cls, double work) {
+    void pend(int e, int cls, double work, const std::string& name = std::string()) {
         if (e < 0) return;
         cudaEventRecord(c->events[e + 1], s);
-        c->recs.push_back({cls, work, e});
+        tok_ctx::ProfRec r;
+        r.cls = cls;
+        r.work = work;
+        r.ev = e;
+        snprintf(r.name, sizeof(r.name), "%s", name.c_str());
+        c->recs.push_back(r);
     }
 
     ConvArgs base_args(const ConvW& cw, const Act& in, int st, int sh, int sw) {
@@ -478,17 +484,17 @@ struct Exec {
             ck(launch_conv_tc_group(&a, 1, c->num_sms, s, 0, c->conv_pairs != 0));
         else
             ck(launch_conv_simt(a, s));
-        pend(e, 0, flop);
+        pend(e, 0, flop, cw.name);
         c->launches += 1;
     }
 
     // Other (bandwidth-bound) kernels: bytes of algorithmic traffic.
     template <typename F>
-    void other(F&& f, double bytes, int nk = 1) {
+    void other(F&& f, double bytes, int nk = 1, const char* label = "other") {
         if (err) return;
         const int e = pbegin();
         ck(f());
-        pend(e, 2, bytes);
+        pend(e, 2, bytes, label);
         c->launches += nk;
     }
 
@@ -561,7 +567,7 @@ struct Exec {
         else
             ck(launch_gn_silu<float>(static_cast<const float*>(in.p), static_cast<float*>(out), frames, HW, in.C, g.G,
                                      g.g, g.b, c->arch.gn_eps, w.gn, c->num_sms, false, s));
-        pend(e, 1, 2.0 * (double)frames * HW * in.C * c->esize());
+        pend(e, 1, 2.0 * (double)frames * HW * in.C * c->esize(), name);
         c->launches += 3;
         return Act{out, in.N, in.T, in.H, in.W, in.C};
     }

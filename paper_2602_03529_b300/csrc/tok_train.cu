@@ -273,7 +273,7 @@ struct TrainExec : Exec {
         ck(launch_wgrad_tc(static_cast<const __nv_bfloat16*>(dy.p), reinterpret_cast<const __nv_bfloat16*>(w.gather),
                            a, b.wpart, b.wpart_floats, grads + cw.ow, grads + cw.ob, c->num_sms, c->d_status, kWaitNs,
                            s, kv));
-        pend(e, 0, 2.0 * (double)a.V * a.Cout * kv);
+        pend(e, 0, 2.0 * (double)a.V * a.Cout * kv, name + ".wgrad");
         c->launches += 4;
     }
 
@@ -314,7 +314,7 @@ struct TrainExec : Exec {
         else
             ck(launch_wgrad<float>(static_cast<const float*>(dy.p), static_cast<const float*>(xin.p), a, S, b.wpart,
                                    grads + cw.ow, grads + cw.ob, s));
-        pend(e, 0, flop);
+        pend(e, 0, flop, name + ".wgrad");
         c->launches += tc ? 4 : 2;
     }
 
@@ -354,6 +354,7 @@ struct TrainExec : Exec {
         ConvW shadow = cw;
         shadow.Cin = cw.cpad;
         shadow.Cout = cw.rows_pad;
+        shadow.name = name + ".dgrad";
         launch(a, shadow);
         if (cw.k == 3 && c->arch.time_pad == TOK_PAD_REPLICATE) {
             // taps of output frames 0 (dt = 0, 1) and 1 (dt = 0) that were clamped to frame 0
@@ -364,6 +365,7 @@ struct TrainExec : Exec {
             b2.Tout = 1;
             b2.residual = out;
             ConvW sh2 = shadow;
+            sh2.name = name + ".dgrad0";
             launch(b2, sh2);
         }
         return Act{out, dy.N, dy.T, dy.H, dy.W, cw.rows_pad};
@@ -391,7 +393,7 @@ struct TrainExec : Exec {
                                          g.b, static_cast<const float*>(add), frames, HW, x.C, g.G, vpt, S, b.gnb,
                                          grads + g.og, grads + g.ob, static_cast<float*>(dx), s));
         }
-        pend(e, 1, 4.0 * (double)frames * HW * x.C * c->esize());
+        pend(e, 1, 4.0 * (double)frames * HW * x.C * c->esize(), name + ".bwd");
         c->launches += 6;
     }
 

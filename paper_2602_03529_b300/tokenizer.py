@@ -216,6 +216,10 @@ class Tokenizer:
     def profile_read(self) -> dict:
         return L.tok_profile_read(self.ctx)
 
+    def profile_records(self) -> list:
+        """Per-launch trace since the last profile_read: [{cls, ms, work, name}] in launch order."""
+        return L.tok_profile_records(self.ctx)
+
     def close(self):
         if self.ctx:
             L.tok_destroy(self.ctx)

@@ -45,6 +45,14 @@ CONV_CASES = [
     (1, 3, 7, 9, 128, 64, 1, (1, 1, 1), 0),             # 1x1x1 shortcut
     (1, 3, 9, 40, 64, 16, 3, (1, 1, 1), 0),             # narrow N (output conv)
     (1, 2, 6, 130, 64, 512, 3, (1, 1, 1), 0),           # W > 128, two N tiles of 256
+    # stride-1 3x3x3 layers of 128 channels and narrow heads share one input box among
+    # the three dh taps (halo tiles of width 16, 32 and 64, ragged edges)
+    (1, 3, 10, 70, 128, 128, 3, (1, 1, 1), 0),          # halo tile 16 x 16
+    (1, 3, 5, 130, 128, 128, 3, (1, 1, 1), 1),          # halo tile 8 x 32
+    (1, 2, 4, 128, 64, 128, 3, (1, 1, 1), 0),           # halo tile 4 x 64
+    (1, 3, 9, 40, 128, 12, 3, (1, 1, 1), 0),            # narrow head, 16 weight rows
+    (1, 3, 11, 37, 64, 24, 3, (1, 1, 1), 1),            # narrow head, 32 weight rows
+    (1, 3, 7, 9, 128, 6, 1, (1, 1, 1), 0),              # narrow 1x1x1 (swapped form)
 ]
 
 
