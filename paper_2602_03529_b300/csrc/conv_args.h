@@ -36,6 +36,12 @@ struct FsqConsts {
     int basis[8];      // prod_{j<i} L_j
 };
 
+// Partial GroupNorm statistics of a set of values: count, mean and the sum of
+// squared deviations from the mean (merged with Chan's pairwise update).
+struct GnTriple {
+    float n, mean, m2;
+};
+
 struct ConvArgs {
     // input (the chunk / clip) and optional history
     const void* x;        // (N, Tin, Hin, Win, Cin)
@@ -59,9 +65,20 @@ struct ConvArgs {
     const void* residual; // same layout as out (OUT_PLAIN only) or null
     int32_t* idx;         // OUT_FSQ
     FsqConsts fsq;
+    // GroupNorm statistics of the stored output (bf16 values after the residual),
+    // for the GroupNorm that reads it next: per (frame, slot, group) triples, a slot
+    // being a spatial tile (times the rh x rw sub-positions for OUT_D2S); groups of
+    // gn_cg consecutive channels. Null: none. Only the swapped wide form writes them.
+    GnTriple* gn_part;
+    int gn_cg;
     // device status / bounded waits
     int* status;
     unsigned long long wait_ns;
+};
+
+// The tensor-core kernel form of a BF16 conv (see conv_route).
+struct ConvRoute {
+    bool taps3, narrow, swap, halo;
 };
 
 // Geometry of the im2col gathers (pixel stem / dequantised decoder input).

@@ -105,7 +105,9 @@ struct GroupExec : Exec {
             a.oH = a.Hout;
             a.oW = a.Wout;
             a.oC = cw.Cout;
+            want_gn_stats(a, pr[p].w, cw.Cout);
             out[p] = Act{outs[p], in[p].N, a.Tout, a.Hout, a.Wout, cw.Cout};
+            tag_gn_stats(out[p], a);
         }
         launch_group(as, cw);
         for (int p = 0; p < P; ++p) stream_update(p, name, in[p].p, in[p].T);
@@ -140,7 +142,9 @@ struct GroupExec : Exec {
             a.oH = oH[p];
             a.oW = oW[p];
             a.oC = cw.Cout / (rt * rh * rw);
+            if (!out_fp32) want_gn_stats(a, pr[p].w, a.oC);
             out[p] = Act{outs[p], in[p].N, a.oT, oH[p], oW[p], a.oC};
+            tag_gn_stats(out[p], a);
         }
         launch_group(as, cw);
         for (int p = 0; p < P; ++p) stream_update(p, name, in[p].p, in[p].T);
@@ -168,7 +172,9 @@ struct GroupExec : Exec {
             a.oH = d.H;
             a.oW = d.W;
             a.oC = cw.Cout;
+            if (mode == OUT_PLAIN) want_gn_stats(a, pr[p].w, cw.Cout);
             out[p] = Act{outs[p], d.N, d.T, d.H, d.W, cw.Cout};
+            tag_gn_stats(out[p], a);
         }
         launch_group(as, cw);
         return out;
@@ -181,6 +187,8 @@ struct GroupExec : Exec {
         for (int p = 0; p < P; ++p) {
             out[p] = in[p];
             out[p].p = pr[p].w.act[i];
+            out[p].part = nullptr;
+            out[p].part_S = 0;
             bytes += 2.0 * (double)in[p].N * in[p].T * in[p].H * in[p].W * in[p].C * c->esize();
         }
         if (err) return out;
@@ -189,7 +197,8 @@ struct GroupExec : Exec {
             GnItem<__nv_bfloat16> it[kMaxConvGroup];
             for (int p = 0; p < P; ++p)
                 it[p] = {static_cast<const __nv_bfloat16*>(in[p].p), static_cast<__nv_bfloat16*>(out[p].p),
-                         (long long)in[p].N * in[p].T, (long long)in[p].H * in[p].W, pr[p].w.gn};
+                         (long long)in[p].N * in[p].T, (long long)in[p].H * in[p].W, pr[p].w.gn, in[p].part,
+                         in[p].part_S};
             ck(launch_gn_silu_group<__nv_bfloat16>(it, P, in[0].C, g.G, g.g, g.b, c->arch.gn_eps, true, s));
         } else {
             GnItem<float> it[kMaxConvGroup];

@@ -150,6 +150,26 @@ __device__ __forceinline__ void add_bf16x16(const __nv_bfloat16* src, float (&v)
     }
 }
 
+__device__ __forceinline__ GnTriple gn_merge(GnTriple a, GnTriple b) {
+    if (b.n == 0.f) return a;
+    if (a.n == 0.f) return b;
+    GnTriple r;
+    r.n = a.n + b.n;
+    const float d = b.mean - a.mean;
+    const float fb = b.n / r.n;
+    r.mean = a.mean + d * fb;
+    r.m2 = a.m2 + b.m2 + d * d * a.n * fb;
+    return r;
+}
+
+__device__ __forceinline__ GnTriple gn_shfl_down(GnTriple t, int o) {
+    GnTriple b;
+    b.n = __shfl_down_sync(0xffffffffu, t.n, o);
+    b.mean = __shfl_down_sync(0xffffffffu, t.mean, o);
+    b.m2 = __shfl_down_sync(0xffffffffu, t.m2, o);
+    return b;
+}
+
 // Problem of a global unit index and the unit's index within that problem.
 template <int MAXP>
 __device__ __forceinline__ int problem_of(const TcBatch<MAXP>& B, long long unit, long long* local) {
@@ -536,6 +556,11 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                     if (lane == 0) mbar_arrive(&tempty[acc]);
                     continue;
                 }
+                // GroupNorm statistics of the stored values: this thread's 16 channels as four
+                // quads of 4 (shifted sums, the shift being the quad's first stored value)
+                const bool gstat = a.gn_part != nullptr;
+                float gK[4] = {0.f, 0.f, 0.f, 0.f}, gs[4] = {0.f, 0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};
+                float gcnt = 0.f;
 #pragma unroll 1
                 for (int c16 = 0; c16 < C::ROWS / 16; ++c16) {
                     float v[16];
@@ -571,10 +596,78 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                             const long long off =
                                 ((((long long)tc.n * a.oT + ot) * a.oH + oh) * a.oW + ow) * a.oC + ch0;
                             if (a.residual) add_bf16x16(static_cast<const __nv_bfloat16*>(a.residual) + off, o);
-                            store_bf16x16(static_cast<__nv_bfloat16*>(a.out) + off, o);
+                            uint32_t w8[8];
+#pragma unroll
+                            for (int i = 0; i < 8; ++i) w8[i] = pack_bf16x2(o[2 * i], o[2 * i + 1]);
+                            uint4* dst = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(a.out) + off);
+                            dst[0] = make_uint4(w8[0], w8[1], w8[2], w8[3]);
+                            dst[1] = make_uint4(w8[4], w8[5], w8[6], w8[7]);
+                            if (gstat) {
+                                float r[16];
+#pragma unroll
+                                for (int i = 0; i < 8; ++i) {
+                                    const float2 f = unpack_bf16x2(w8[i]);
+                                    r[2 * i] = f.x;
+                                    r[2 * i + 1] = f.y;
+                                }
+                                if (gcnt == 0.f) {
+#pragma unroll
+                                    for (int k = 0; k < 4; ++k) gK[k] = r[4 * k];
+                                }
+#pragma unroll
+                                for (int i = 0; i < 16; ++i) {
+                                    const float d = r[i] - gK[i / 4];
+                                    gs[i / 4] += d;
+                                    gq[i / 4] = fmaf(d, d, gq[i / 4]);
+                                }
+                                gcnt += 4.f;
+                            }
                         }
                     }
                     __syncwarp();
+                }
+                if (gstat) {
+                    // quads -> triples, merged over the 16 lanes holding the same channels
+                    // (lane i takes lane i + o: a fixed order), then into groups of gn_cg channels
+                    GnTriple t[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        t[k].n = gcnt;
+                        t[k].mean = gcnt > 0.f ? gK[k] + gs[k] / gcnt : 0.f;
+                        t[k].m2 = gcnt > 0.f ? fmaxf(gq[k] - gs[k] * gs[k] / gcnt, 0.f) : 0.f;
+                    }
+#pragma unroll
+                    for (int o = 16; o >= 2; o >>= 1)
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const GnTriple b = gn_shfl_down(t[k], o);
+                            if (lane + o < 32) t[k] = gn_merge(t[k], b);
+                        }
+                    const int cg = a.gn_cg;
+                    if (cg >= 8) {
+                        t[0] = gn_merge(t[0], t[1]);
+                        t[1] = gn_merge(t[2], t[3]);
+                    }
+                    if (cg == 16) t[0] = gn_merge(t[0], t[1]);
+                    const int c0 = tc.nt * BN + q * 32 + lane * 16;  // lanes 0, 1: the two halves
+                    if (lane < 2 && c0 < a.Cout) {
+                        int ch0 = c0, fr = tc.to, slot = tc.th * g.tiles_w + tc.tw, S = g.tiles_h * g.tiles_w;
+                        if (a.mode == OUT_D2S) {
+                            const int sub = c0 / a.oC;
+                            ch0 = c0 - sub * a.oC;
+                            fr = tc.to * a.rt + sub / (a.rw * a.rh) - a.drop_t;
+                            slot = (slot * a.rh + (sub / a.rw) % a.rh) * a.rw + sub % a.rw;
+                            S *= a.rh * a.rw;
+                        }
+                        if (fr >= 0 && fr < a.oT) {
+                            const int G = a.oC / cg;
+                            GnTriple* dst = a.gn_part + (((long long)tc.n * a.oT + fr) * S + slot) * G + ch0 / cg;
+                            const int ng = 16 / cg;
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+                                if (k < ng) dst[k] = t[k];
+                        }
+                    }
                 }
                 tc_fence_before();
                 __syncwarp();
@@ -885,6 +978,46 @@ int conv_tc_cout_pad(int Cout) {
     return (c16 + bn - 1) / bn * bn;
 }
 
+// The kernel form a layer runs in. Stride-1 3x3x3 layers share each input box
+// among the three dh taps (halo form); a narrow halo layer (at most 32
+// channels) runs unswapped with 16 or 32 weight rows. Wide layers of 128k
+// channels with bf16 output (plain, or depth-to-space whose 16-channel groups
+// stay within one sub-position) and other 128-channel plain layers run
+// swapped; narrow layers without halo run swapped with padded weights.
+ConvRoute conv_route(const ConvArgs& a0) {
+    ConvRoute r;
+    r.taps3 = a0.kh == 3 && a0.kw == 3 && a0.sh == 1 && a0.sw == 1;
+    r.narrow = a0.Cout <= 32;
+    const bool wide = a0.Cout % 128 == 0 && a0.Cout_pad % 128 == 0 && !a0.out_fp32 &&
+                      (a0.mode == OUT_PLAIN || (a0.mode == OUT_D2S && a0.oC % 16 == 0));
+    r.swap = (a0.Cout_pad == 128 &&
+              ((a0.mode == OUT_PLAIN && !a0.out_fp32 && a0.Cout == 128) || (r.narrow && !r.taps3))) ||
+             (r.taps3 && wide);
+    r.halo = r.taps3 && (r.swap || r.narrow);
+    return r;
+}
+
+// GroupNorm statistics come from the swapped wide epilogue (plain or
+// depth-to-space, bf16), for groups of 4, 8 or 16 channels.
+bool conv_tc_gn_fusable(const ConvArgs& a) {
+    const ConvRoute r = conv_route(a);
+    return r.swap && !r.narrow && (a.mode == OUT_PLAIN || a.mode == OUT_D2S) && !a.out_fp32 &&
+           (a.gn_cg == 4 || a.gn_cg == 8 || a.gn_cg == 16);
+}
+
+// Statistics slots per output frame: the spatial tiles of the launch (times
+// the rh x rw sub-positions of a depth-to-space output).
+int conv_tc_gn_slots(const ConvArgs& a) {
+    const ConvRoute r = conv_route(a);
+    int BH = 1, BW = 1;
+    if (r.halo)
+        choose_tile_halo(a.Hout, a.Wout, r.swap ? 256 : 128, &BH, &BW);
+    else
+        choose_tile(a.Hout, a.Wout, r.swap ? 256 : 128, &BH, &BW);
+    const int tiles = ((a.Hout + BH - 1) / BH) * ((a.Wout + BW - 1) / BW);
+    return a.mode == OUT_D2S ? tiles * a.rh * a.rw : tiles;
+}
+
 // Requirements (checked by the caller's plan): Cin % 64 == 0, Cout_pad a
 // multiple of the chosen BN, Kpad = taps * Cin, strided convs have
 // sh == sw == 2 with even Hin and Win, bf16 tensors 16-byte aligned.
@@ -905,18 +1038,10 @@ int launch_conv_tc_group(const ConvArgs* as, int count, int num_sms, cudaStream_
             return -1;
     // the wide (swapped) form: exactly 128 output channels with plain bf16 output,
     // or a narrow layer (at most 32 channels, weights padded to 128 rows)
-    // stride-1 3x3x3 layers share each input box among the three dh taps (halo form); a
-    // narrow halo layer (at most 32 channels) runs unswapped with 16 or 32 weight rows
-    const bool taps3 = a0.kh == 3 && a0.kw == 3 && a0.sh == 1 && a0.sw == 1;
-    const bool narrow = a0.Cout <= 32;
-    // wide layers of 128k channels with bf16 output: plain, or depth-to-space whose
-    // 16-channel groups stay within one sub-position
-    const bool wide = a0.Cout % 128 == 0 && a0.Cout_pad % 128 == 0 && !a0.out_fp32 &&
-                      (a0.mode == OUT_PLAIN || (a0.mode == OUT_D2S && a0.oC % 16 == 0));
-    const bool swap = (a0.Cout_pad == 128 &&
-                       ((a0.mode == OUT_PLAIN && !a0.out_fp32 && a0.Cout == 128) || (narrow && !taps3))) ||
-                      (taps3 && wide);
-    const bool halo = taps3 && (swap || narrow);
+    const ConvRoute rt = conv_route(a0);
+    const bool narrow = rt.narrow, swap = rt.swap, halo = rt.halo;
+    for (int p = 0; p < count; ++p)
+        if (as[p].gn_part && (!conv_tc_gn_fusable(as[p]) || as[p].gn_cg != a0.gn_cg)) return -1;
     TcGeo gs[kMaxConvGroup];
     for (int p = 0; p < count; ++p) {
         TcGeo& g = gs[p];

@@ -28,6 +28,10 @@ struct Vec;
 template <>
 struct Vec<float> {
     static constexpr int N = 4;
+    __device__ static uint4 raw(const float* p) { return *reinterpret_cast<const uint4*>(p); }
+    __device__ static void cvt(uint4 q, float (&v)[4]) {
+        v[0] = __uint_as_float(q.x); v[1] = __uint_as_float(q.y); v[2] = __uint_as_float(q.z); v[3] = __uint_as_float(q.w);
+    }
     __device__ static void load(const float* p, float (&v)[4]) {
         float4 q = *reinterpret_cast<const float4*>(p);
         v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
@@ -39,6 +43,16 @@ struct Vec<float> {
 template <>
 struct Vec<__nv_bfloat16> {
     static constexpr int N = 8;
+    __device__ static uint4 raw(const __nv_bfloat16* p) { return *reinterpret_cast<const uint4*>(p); }
+    __device__ static void cvt(uint4 q, float (&v)[8]) {
+        uint32_t u[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            float2 f = unpack_bf16x2(u[i]);
+            v[2 * i] = f.x;
+            v[2 * i + 1] = f.y;
+        }
+    }
     __device__ static void load(const __nv_bfloat16* p, float (&v)[8]) {
         uint4 q = *reinterpret_cast<const uint4*>(p);
         uint32_t u[4] = {q.x, q.y, q.z, q.w};
@@ -59,9 +73,7 @@ struct Vec<__nv_bfloat16> {
     }
 };
 
-struct Triple {
-    float n, mean, m2;
-};
+using Triple = GnTriple;
 
 __device__ __forceinline__ Triple merge(Triple a, Triple b) {
     if (b.n == 0.f) return a;
@@ -83,8 +95,9 @@ struct GnProb {
     const T* x;
     T* y;
     long long frames, vpf;  // frames, 16-byte vectors per frame
-    int vpt, S;             // vectors per thread, chunks per frame
-    Triple* part;           // (frames, S, G)
+    int vpt, S;             // vectors per thread, chunks per frame (apply and statistics passes)
+    Triple* part;           // (frames, Sp, G) statistics slots
+    int Sp;                 // slots per frame: S, or those of the producing conv
     float2* stats;          // (frames, G): mean, rstd
     long long blk_end, row_end;
 };
@@ -187,7 +200,7 @@ __global__ void gn_finalize_kernel(const __grid_constant__ GnBatch<T, MAXP> B, i
     const GnProb<T>& P = B.p[p];
     const long long row = p ? wid - B.p[p - 1].row_end : wid;
     const long long frame = row / G;
-    const int g = (int)(row % G), S = P.S;
+    const int g = (int)(row % G), S = P.Sp;
     Triple acc = {0.f, 0.f, 0.f};
     for (int c = lane; c < S; c += 32) acc = merge(acc, P.part[(frame * S + c) * G + g]);
 #pragma unroll
@@ -271,9 +284,10 @@ size_t gn_scratch_bytes(long long frames, long long HW, int C, int G, int num_sm
 namespace {
 
 // Plan a batch: per-problem chunking, scratch carving, block numbering.
+// pre: every item has precomputed statistics (used instead of the statistics pass)
 template <typename T, int MAXP>
 bool gn_batch(const GnItem<T>* items, int count, int C, int G, GnBatch<T, MAXP>* B, long long* blocks,
-              long long* rows) {
+              long long* rows, bool pre = false) {
     constexpr int V = Vec<T>::N;
     memset(B, 0, sizeof(*B));
     B->count = count;
@@ -285,9 +299,11 @@ bool gn_batch(const GnItem<T>* items, int count, int C, int G, GnBatch<T, MAXP>*
         P.frames = items[p].frames;
         P.vpf = items[p].HW * C / V;
         gn_plan(P.frames, P.vpf, 0, &P.vpt, &P.S);
-        P.part = static_cast<Triple*>(items[p].scratch);
+        Triple* own = static_cast<Triple*>(items[p].scratch);
+        P.part = pre ? const_cast<Triple*>(items[p].part) : own;
+        P.Sp = pre ? items[p].part_S : P.S;
         P.stats = reinterpret_cast<float2*>(
-            (reinterpret_cast<uintptr_t>(P.part + P.frames * P.S * G) + 15) & ~uintptr_t(15));
+            (reinterpret_cast<uintptr_t>(own + P.frames * P.S * G) + 15) & ~uintptr_t(15));
         nb += P.frames * P.S;
         nr += P.frames * G;
         P.blk_end = nb;
@@ -300,11 +316,11 @@ bool gn_batch(const GnItem<T>* items, int count, int C, int G, GnBatch<T, MAXP>*
 
 template <typename T, int MAXP>
 int gn_stats_batch(const GnBatch<T, MAXP>& B, long long blocks, long long rows, int C, int G, float eps,
-                   cudaStream_t stream) {
+                   cudaStream_t stream, bool pre = false) {
     constexpr int V = Vec<T>::N;
     const int cg = C / G;
     const int ngv = cg >= V ? 1 : V / cg;
-    switch (ngv) {
+    if (!pre) switch (ngv) {
         case 1: gn_partial_kernel<T, 1, MAXP><<<(unsigned)blocks, NT, 0, stream>>>(B, C, G); break;
         case 2: gn_partial_kernel<T, 2, MAXP><<<(unsigned)blocks, NT, 0, stream>>>(B, C, G); break;
         case 4: gn_partial_kernel<T, 4, MAXP><<<(unsigned)blocks, NT, 0, stream>>>(B, C, G); break;
@@ -319,8 +335,10 @@ int gn_silu_batch(const GnItem<T>* items, int count, int C, int G, const float* 
                   bool fast, cudaStream_t stream) {
     GnBatch<T, MAXP> B;
     long long blocks, rows;
-    if (!gn_batch(items, count, C, G, &B, &blocks, &rows)) return 0;
-    if (const int e = gn_stats_batch(B, blocks, rows, C, G, eps, stream)) return e;
+    bool pre = true;
+    for (int p = 0; p < count; ++p) pre = pre && items[p].part != nullptr && items[p].part_S > 0;
+    if (!gn_batch(items, count, C, G, &B, &blocks, &rows, pre)) return 0;
+    if (const int e = gn_stats_batch(B, blocks, rows, C, G, eps, stream, pre)) return e;
     if (fast)
         gn_apply_kernel<T, true, MAXP><<<(unsigned)blocks, NT, 0, stream>>>(B, C, G, gamma, beta);
     else

@@ -11,6 +11,11 @@ namespace tok {
 
 int launch_conv_tc(const ConvArgs& a, int num_sms, cudaStream_t stream);
 // one launch over up to kMaxConvGroup inputs of the same layer (k_conv_tc.cu)
+ConvRoute conv_route(const ConvArgs& a);
+// The launch writes GroupNorm statistics into a.gn_part (a.gn_cg channels per
+// group) only where this holds; conv_tc_gn_slots gives the slots per frame.
+bool conv_tc_gn_fusable(const ConvArgs& a);
+int conv_tc_gn_slots(const ConvArgs& a);
 int launch_conv_tc_group(const ConvArgs* as, int count, int num_sms, cudaStream_t stream, int cta_tiles = 0,
                          bool pairs = true);
 int conv_tc_bn(int cout_pad16);
@@ -25,6 +30,10 @@ struct GnItem {
     T* y;
     long long frames, HW;
     void* scratch;  // gn_scratch_bytes(frames, HW, ...) bytes
+    // statistics already reduced by the producing conv: (frames, part_S, G) triples;
+    // used when every item of a launch has them, else the statistics pass runs
+    const GnTriple* part = nullptr;
+    int part_S = 0;
 };
 template <typename T>
 int launch_gn_silu_group(const GnItem<T>* items, int count, int C, int G, const float* gamma, const float* beta,

@@ -271,6 +271,7 @@ struct Layout {
     size_t gather;    // im2col (BF16) / edge-padded pixels + codes (FP32)
     size_t zbuf;      // latent when the caller passes no z
     size_t gn;        // GroupNorm scratch
+    size_t gnpart;    // GroupNorm statistics reduced by the producing conv (BF16)
     size_t total;
 };
 
@@ -293,6 +294,30 @@ Dims clip_dims(const tok_ctx* c, int T, int H, int W) {
 int stem_frames(const tok_ctx* c, int T) {
     const int ts = c->arch.kind == TOK_ARCH_FULL ? c->arch.t_stem : 1;
     return (T - 1) / ts + 1;
+}
+
+// Upper bound on the GroupNorm statistics slots of an Hout x Wout conv output:
+// tiles of 256 voxels (BH x BW, BW >= 8) cover it in at most
+// HW/256 + Hout + Wout/8 + 1 tiles.
+inline long long gn_slot_bound(long long Ho, long long Wo) { return Ho * Wo / 256 + Ho + Wo / 8 + 2; }
+
+// Bytes of the statistics triples the largest conv output of the walk needs:
+// plain outputs at every level, and depth-to-space outputs (4 sub-positions per
+// tile of the up conv's input).
+size_t gnpart_bytes(const tok_ctx* c, int N, int T, int Hp, int Wp) {
+    const tok_arch& a = c->arch;
+    if (!c->bf16() || a.kind != TOK_ARCH_FULL) return 0;
+    size_t m = 0;
+    int Tl = stem_frames(c, T), Tprev = Tl;
+    for (int l = 0; l < a.nlevels; ++l) {
+        const long long Hl = Hp >> (l + 1), Wl = Wp >> (l + 1);
+        m = std::max<size_t>(m, (size_t)N * Tl * gn_slot_bound(Hl, Wl) * a.gn_groups * sizeof(GnTriple));
+        if (l > 0)
+            m = std::max<size_t>(m, (size_t)N * Tprev * 4 * gn_slot_bound(Hl, Wl) * a.gn_groups * sizeof(GnTriple));
+        Tprev = Tl;
+        Tl = (Tl - 1) / 2 + 1;
+    }
+    return m;
 }
 
 Layout layout_for(const tok_ctx* c, int N, int T, int H, int W) {
@@ -334,7 +359,8 @@ Layout layout_for(const tok_ctx* c, int N, int T, int H, int W) {
     L.gather = align256(g);
     L.zbuf = align256((size_t)ntok * a.nlev * 4);
     L.gn = align256(gn);
-    L.total = 5 * L.act + L.gather + L.zbuf + L.gn;
+    L.gnpart = align256(gnpart_bytes(c, N, T, d.Hp, d.Wp));
+    L.total = 5 * L.act + L.gather + L.zbuf + L.gn + L.gnpart;
     return L;
 }
 
@@ -343,6 +369,8 @@ struct Work {
     char* gather;
     char* zbuf;
     char* gn;
+    char* gnpart = nullptr;
+    size_t gnpart_bytes = 0;
 };
 
 // Carve one problem's workspace out of the arena, starting `off` bytes in.
@@ -358,6 +386,9 @@ Work carve(tok_ctx* c, const Layout& L, size_t off = 0) {
     w.zbuf = p;
     p += L.zbuf;
     w.gn = p;
+    p += L.gn;
+    w.gnpart = L.gnpart ? p : nullptr;
+    w.gnpart_bytes = L.gnpart;
     return w;
 }
 
@@ -416,6 +447,8 @@ std::vector<std::pair<std::string, size_t>> stream_frames(const tok_ctx* c, int 
 struct Act {
     void* p;
     int N, T, H, W, C;
+    const GnTriple* part = nullptr;  // GroupNorm statistics the producing conv reduced
+    int part_S = 0;                  // their slots per frame
 };
 
 struct Exec {
@@ -475,6 +508,32 @@ struct Exec {
         return a;
     }
 
+    // Ask a BF16 conv for the GroupNorm statistics of its output (Cgn channels)
+    // when its kernel form reduces them and the workspace region holds them.
+    void want_gn_stats(ConvArgs& a, const Work& wk, int Cgn) {
+        a.gn_part = nullptr;
+        a.gn_cg = 0;
+        if (!c->bf16() || !wk.gnpart) return;
+        const int G = std::max(1, std::min(c->arch.gn_groups, Cgn / 2));
+        if (Cgn % G) return;
+        a.gn_cg = Cgn / G;
+        if (!conv_tc_gn_fusable(a)) {
+            a.gn_cg = 0;
+            return;
+        }
+        const size_t need = (size_t)a.N * a.oT * conv_tc_gn_slots(a) * G * sizeof(GnTriple);
+        if (need <= wk.gnpart_bytes)
+            a.gn_part = reinterpret_cast<GnTriple*>(wk.gnpart);
+        else
+            a.gn_cg = 0;
+    }
+    static void tag_gn_stats(Act& o, const ConvArgs& a) {
+        if (a.gn_part) {
+            o.part = a.gn_part;
+            o.part_S = conv_tc_gn_slots(a);
+        }
+    }
+
     void launch(ConvArgs& a, const ConvW& cw) {
         if (err) return;
         const double flop = 2.0 * (double)a.N * a.Tout * a.Hout * a.Wout * cw.Cout * (double)(cw.k * cw.k * cw.k) *
@@ -510,8 +569,11 @@ struct Exec {
         a.oH = a.Hout;
         a.oW = a.Wout;
         a.oC = cw.Cout;
+        want_gn_stats(a, w, cw.Cout);
         launch(a, cw);
-        return Act{out, in.N, a.Tout, a.Hout, a.Wout, cw.Cout};
+        Act o{out, in.N, a.Tout, a.Hout, a.Wout, cw.Cout};
+        tag_gn_stats(o, a);
+        return o;
     }
 
     // Conv followed by depth-to-space (r = (rt, rh, rw)), cropped to oH x oW.
@@ -530,8 +592,11 @@ struct Exec {
         a.oH = oH;
         a.oW = oW;
         a.oC = cw.Cout / (rt * rh * rw);
+        if (!out_fp32) want_gn_stats(a, w, a.oC);
         launch(a, cw);
-        return Act{out, in.N, a.oT, oH, oW, a.oC};
+        Act o{out, in.N, a.oT, oH, oW, a.oC};
+        tag_gn_stats(o, a);
+        return o;
     }
 
     // Conv whose input is first gathered into an im2col matrix (BF16 path):
@@ -551,8 +616,11 @@ struct Exec {
         a.oH = Hout;
         a.oW = Wout;
         a.oC = cw.Cout;
+        if (mode == OUT_PLAIN) want_gn_stats(a, w, cw.Cout);
         launch(a, cw);
-        return Act{out, N, Tout, Hout, Wout, cw.Cout};
+        Act o{out, N, Tout, Hout, Wout, cw.Cout};
+        tag_gn_stats(o, a);
+        return o;
     }
 
     Act gn_silu(const std::string& name, const Act& in, void* out) {
@@ -560,11 +628,11 @@ struct Exec {
         if (err) return Act{out, in.N, in.T, in.H, in.W, in.C};
         const long long frames = (long long)in.N * in.T, HW = (long long)in.H * in.W;
         const int e = pbegin();
-        if (c->bf16())
-            ck(launch_gn_silu<__nv_bfloat16>(static_cast<const __nv_bfloat16*>(in.p), static_cast<__nv_bfloat16*>(out),
-                                             frames, HW, in.C, g.G, g.g, g.b, c->arch.gn_eps, w.gn, c->num_sms, true,
-                                             s));
-        else
+        if (c->bf16()) {
+            GnItem<__nv_bfloat16> it{static_cast<const __nv_bfloat16*>(in.p), static_cast<__nv_bfloat16*>(out), frames,
+                                     HW, w.gn, in.part, in.part_S};
+            ck(launch_gn_silu_group<__nv_bfloat16>(&it, 1, in.C, g.G, g.g, g.b, c->arch.gn_eps, true, s));
+        } else
             ck(launch_gn_silu<float>(static_cast<const float*>(in.p), static_cast<float*>(out), frames, HW, in.C, g.G,
                                      g.g, g.b, c->arch.gn_eps, w.gn, c->num_sms, false, s));
         pend(e, 1, 2.0 * (double)frames * HW * in.C * c->esize(), name);

@@ -34,6 +34,8 @@ struct TrainBufs {
     char* gather = nullptr;
     char* gn = nullptr;
     char* gnb = nullptr;
+    char* gnpart = nullptr;  // GroupNorm statistics reduced by the forward convs
+    size_t gnpart_bytes = 0;
     float* wpart = nullptr;
     size_t wpart_floats = 0;
     float* mse = nullptr;
@@ -112,6 +114,8 @@ TrainBufs train_layout(const tok_ctx* c, int N, int T, int H, int W, char* base)
     b.gather = take(c->bf16() ? g : 256);
     b.gn = take(gn);
     b.gnb = take(gn);
+    b.gnpart_bytes = gnpart_bytes(c, N, T, H, W);
+    b.gnpart = b.gnpart_bytes ? take(b.gnpart_bytes) : nullptr;
     b.wpart_floats = kMaxWgradPartialFloats;
     b.wpart = reinterpret_cast<float*>(take(b.wpart_floats * 4));
     b.mse = reinterpret_cast<float*>(take(4096));
@@ -126,6 +130,8 @@ struct TrainExec : Exec {
     void set_work() {
         w.gather = b.gather;
         w.gn = b.gn;
+        w.gnpart = b.gnpart;
+        w.gnpart_bytes = b.gnpart_bytes;
         w.zbuf = b.codes;
         for (int i = 0; i < 5; ++i) w.act[i] = nullptr;
     }
