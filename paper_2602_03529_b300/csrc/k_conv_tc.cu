@@ -57,6 +57,7 @@ struct TcGeo {
 template <int MAXP>
 struct TcBatch {
     CUtensorMap tm_w;
+    int w_rows;  // rows of each weight box: BN (/ CL), or the 16/32 real rows of a narrow halo layer
     CUtensorMap tm_x[MAXP];
     CUtensorMap tm_h[MAXP];
     ConvArgs a[MAXP];
@@ -84,14 +85,20 @@ namespace {
 //                descriptor simply starts there. Three weight boxes (one per
 //                dh) go into the same stage. The activation bytes per K block
 //                drop from ROWS to (ROWS + 2 BW) / 3 voxel rows.
+//                BW = 16, 32 or 64. Halo layers run swapped; a narrow layer (at
+//                most 32 channels) loads only its 16 or 32 weight rows per tap
+//                into weight slots whose other rows stay zero.
 constexpr int HALO_BW_MAX = 64;
 
-template <int BN, bool SWAP, bool HALO = false>
+//                HALO = number of 64-channel blocks per stage (0: no halo).
+template <int BN, bool SWAP, int HALO = 0>
 struct Cfg {
     static constexpr int ROWS = SWAP ? 256 : 128;  // voxels per tile
-    static constexpr int ACT_BYTES = (ROWS + (HALO ? 2 * HALO_BW_MAX : 0)) * 128;  // 64 bf16 channels per row
+    static constexpr int HALO_BW = HALO_BW_MAX;
+    static constexpr int SUB_ACT = (ROWS + (HALO ? 2 * HALO_BW : 0)) * 128;  // one channel block's box
+    static constexpr int ACT_BYTES = (HALO ? HALO : 1) * SUB_ACT;  // 64 bf16 channels per row
     static constexpr int W_TAP_BYTES = BN * 128;
-    static constexpr int W_BYTES = (HALO ? 3 : 1) * W_TAP_BYTES;
+    static constexpr int W_BYTES = (HALO ? 3 * HALO : 1) * W_TAP_BYTES;
     static constexpr int STAGE = ACT_BYTES + W_BYTES;
     static constexpr int STAGES = (200 * 1024 / STAGE) > 8 ? 8 : (200 * 1024 / STAGE);
     static constexpr int ACC_COLS = SWAP ? ROWS : BN;  // TMEM columns per accumulator
@@ -101,6 +108,9 @@ struct Cfg {
     static constexpr int EPI_BYTES = SWAP ? 4 * 16 * EPI_STRIDE * 4 : 0;
     static constexpr int SMEM = STAGES * STAGE + 1024 + BAR_BYTES + EPI_BYTES;
     static constexpr uint32_t IDESC = SWAP ? idesc_bf16_f32(BN, ROWS) : idesc_bf16_f32(128, BN);
+    // narrow swapped layers of at most 16 channels: an M = 64 MMA (half the padded
+    // rows); output channel r < 16 stays in TMEM lane r
+    static constexpr uint32_t IDESC_M64 = idesc_bf16_f32(64, ROWS);
 };
 
 struct TileCoord {
@@ -202,7 +212,7 @@ __device__ __forceinline__ long long unit_tile(const TcGeo& g, long long lu, uin
 // the same weight tile; each CTA loads half of every weight box and multicasts
 // it to both, and each stage is released only when both CTAs' MMAs have read
 // it (the empty barrier counts one commit from each CTA).
-template <int BN, bool SWAP, int MAXP, int CL, bool HALO>
+template <int BN, bool SWAP, int MAXP, int CL, int HALO>
 __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__ TcBatch<MAXP> B) {
     using C = Cfg<BN, SWAP, HALO>;
     static_assert(CL == 1 || CL == 2, "CTA pairs at most");
@@ -255,6 +265,17 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
             return;
         }
     }
+    if constexpr (HALO > 0) {
+        // narrow layer: the weight boxes fill only the first w_rows rows of each
+        // 128-row weight slot; the others are zero for the whole launch
+        if (B.w_rows < BN) {
+            for (int st = 0; st < C::STAGES; ++st) {
+                uint4* wz = reinterpret_cast<uint4*>(smem + st * C::STAGE + C::ACT_BYTES);
+                for (int i = threadIdx.x; i < C::W_BYTES / 16; i += blockDim.x) wz[i] = make_uint4(0u, 0u, 0u, 0u);
+            }
+            fence_proxy_async_smem();
+        }
+    }
     if (warp == 0 && lane < B.count) {
         tma_prefetch_desc(&B.tm_x[lane]);
         if (B.a[lane].hist) tma_prefetch_desc(&B.tm_h[lane]);
@@ -291,8 +312,10 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                         ok = false;
                         break;
                     }
-                    // plain: kb = (tap, cb); halo: kb = (dt, dw, cb) with the three dh taps inside
-                    const int tap = kb / g.cpt, cb = kb - tap * g.cpt;
+                    // plain: kb = (tap, cb); halo: kb = (dt, dw, block group) with the three dh taps
+                    // and HALO channel blocks inside
+                    const int cpg = HALO ? g.cpt / HALO : g.cpt;
+                    const int tap = kb / cpg, cb = kb - tap * cpg;
                     const int dw = HALO ? tap % 3 : tap % a.kw;
                     const int dh = HALO ? 0 : (tap / a.kw) % a.kh;
                     const int dt = HALO ? tap / 3 : tap / (a.kw * a.kh);
@@ -313,14 +336,20 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                     }
                     uint8_t* sa = smem + s * C::STAGE;
                     uint8_t* sb = sa + C::ACT_BYTES;
-                    if constexpr (HALO) {
-                        // rows th*BH - 1 .. th*BH + BH of the input frame (zeros outside)
-                        mbar_arrive_expect_tx(&full[s], (uint32_t)((g.BH + 2) * g.BW * 128 + C::W_BYTES));
-                        tma_load_4d(sa, src, &full[s], cb * 64, tc.tw * g.BW + dw - 1, tc.th * g.BH - 1, tcoord);
+                    if constexpr (HALO > 0) {
+                        // rows th*BH - 1 .. th*BH + BH of the input frame (zeros outside), per block
+                        mbar_arrive_expect_tx(&full[s],
+                                              (uint32_t)(HALO * ((g.BH + 2) * g.BW * 128 + 3 * B.w_rows * 128)));
 #pragma unroll
-                        for (int d = 0; d < 3; ++d)
-                            tma_load_2d(sb + d * C::W_TAP_BYTES, &B.tm_w, &full[s],
-                                        ((dt * 3 + d) * 3 + dw) * a.Cin + cb * 64, tc.nt * BN);
+                        for (int c = 0; c < HALO; ++c) {
+                            const int ci = (cb * HALO + c) * 64;
+                            tma_load_4d(sa + c * C::SUB_ACT, src, &full[s], ci, tc.tw * g.BW + dw - 1,
+                                        tc.th * g.BH - 1, tcoord);
+#pragma unroll
+                            for (int d = 0; d < 3; ++d)
+                                tma_load_2d(sb + (c * 3 + d) * C::W_TAP_BYTES, &B.tm_w, &full[s],
+                                            ((dt * 3 + d) * 3 + dw) * a.Cin + ci, tc.nt * BN);
+                        }
                         last_ph[s] = (int)ph;
                         if (++s == C::STAGES) {
                             s = 0;
@@ -391,16 +420,20 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                     tc_fence_after();
                     const uint32_t s_act = smem_u32(smem + s * C::STAGE);
                     const uint32_t s_w = s_act + C::ACT_BYTES;
-                    if constexpr (HALO) {
+                    if constexpr (HALO > 0) {
+                        const uint32_t idesc = (SWAP && B.w_rows <= 16) ? C::IDESC_M64 : C::IDESC;
 #pragma unroll
-                        for (int dh = 0; dh < 3; ++dh) {
-                            const uint32_t xa = s_act + (uint32_t)dh * row_step, wa = s_w + (uint32_t)(dh * C::W_TAP_BYTES);
-                            const uint32_t op_a = SWAP ? wa : xa, op_b = SWAP ? xa : wa;
+                        for (int c = 0; c < HALO; ++c)
 #pragma unroll
-                            for (int k = 0; k < 4; ++k)
-                                tc_mma_bf16(d, sw128_desc(op_a + k * 32), sw128_desc(op_b + k * 32), C::IDESC,
-                                            (kb | dh | k) != 0 ? 1u : 0u);
-                        }
+                            for (int dh = 0; dh < 3; ++dh) {
+                                const uint32_t xa = s_act + (uint32_t)(c * C::SUB_ACT) + (uint32_t)dh * row_step;
+                                const uint32_t wa = s_w + (uint32_t)((c * 3 + dh) * C::W_TAP_BYTES);
+                                const uint32_t op_a = SWAP ? wa : xa, op_b = SWAP ? xa : wa;
+#pragma unroll
+                                for (int k = 0; k < 4; ++k)
+                                    tc_mma_bf16(d, sw128_desc(op_a + k * 32), sw128_desc(op_b + k * 32), idesc,
+                                                (kb | c | dh | k) != 0 ? 1u : 0u);
+                            }
                     } else {
                         const uint32_t op_a = SWAP ? s_w : s_act, op_b = SWAP ? s_act : s_w;
 #pragma unroll
@@ -768,14 +801,16 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
     if constexpr (CL > 1) cluster_sync();  // neither CTA leaves while its peer may still address it
 }
 
-template <int BN, bool SWAP, int MAXP, int CL, bool HALO = false>
+template <int BN, bool SWAP, int MAXP, int CL, int HALO = 0>
 int launch_bn(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int cta_tiles, cudaStream_t stream) {
     using C = Cfg<BN, SWAP, HALO>;
     auto kern = conv_tc_kernel<BN, SWAP, MAXP, CL, HALO>;
     TcBatch<MAXP> B;
     memset(&B, 0, sizeof(B));
-    // with CTA pairs each CTA loads half of the weight box (BN / 2 rows)
-    if (!encode_w_map(&B.tm_w, as[0].w, as[0].Cout_pad, as[0].Kpad, BN / CL)) return -1;
+    // with CTA pairs each CTA loads half of the weight box (BN / 2 rows); a narrow halo
+    // layer loads its real rows only
+    B.w_rows = (HALO > 0 && SWAP && as[0].Cout <= 32) ? (as[0].Cout + 15) / 16 * 16 : BN / CL;
+    if (!encode_w_map(&B.tm_w, as[0].w, as[0].Cout_pad, as[0].Kpad, B.w_rows)) return -1;
     long long total = 0;
     for (int p = 0; p < count; ++p) {
         const ConvArgs& a = as[p];
@@ -849,10 +884,10 @@ int launch_bn(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int c
 
 // CTA pairs for layers with at least one wave of tiles (weight halves of 64+
 // rows), single CTAs otherwise and whenever CTA lifetimes are bounded.
-template <int BN, bool SWAP>
+template <int BN, bool SWAP, int NCB>
 int launch_bn_halo(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int cta_tiles, cudaStream_t stream) {
-    return count == 1 ? launch_bn<BN, SWAP, 1, 1, true>(as, gs, 1, num_sms, cta_tiles, stream)
-                      : launch_bn<BN, SWAP, kMaxConvGroup, 1, true>(as, gs, count, num_sms, cta_tiles, stream);
+    return count == 1 ? launch_bn<BN, SWAP, 1, 1, NCB>(as, gs, 1, num_sms, cta_tiles, stream)
+                      : launch_bn<BN, SWAP, kMaxConvGroup, 1, NCB>(as, gs, count, num_sms, cta_tiles, stream);
 }
 
 template <int BN, bool SWAP>
@@ -990,10 +1025,9 @@ ConvRoute conv_route(const ConvArgs& a0) {
     r.narrow = a0.Cout <= 32;
     const bool wide = a0.Cout % 128 == 0 && a0.Cout_pad % 128 == 0 && !a0.out_fp32 &&
                       (a0.mode == OUT_PLAIN || (a0.mode == OUT_D2S && a0.oC % 16 == 0));
-    r.swap = (a0.Cout_pad == 128 &&
-              ((a0.mode == OUT_PLAIN && !a0.out_fp32 && a0.Cout == 128) || (r.narrow && !r.taps3))) ||
+    r.swap = (a0.Cout_pad == 128 && ((a0.mode == OUT_PLAIN && !a0.out_fp32 && a0.Cout == 128) || r.narrow)) ||
              (r.taps3 && wide);
-    r.halo = r.taps3 && (r.swap || r.narrow);
+    r.halo = r.taps3 && r.swap;
     return r;
 }
 
@@ -1039,7 +1073,7 @@ int launch_conv_tc_group(const ConvArgs* as, int count, int num_sms, cudaStream_
     // the wide (swapped) form: exactly 128 output channels with plain bf16 output,
     // or a narrow layer (at most 32 channels, weights padded to 128 rows)
     const ConvRoute rt = conv_route(a0);
-    const bool narrow = rt.narrow, swap = rt.swap, halo = rt.halo;
+    const bool swap = rt.swap, halo = rt.halo;
     for (int p = 0; p < count; ++p)
         if (as[p].gn_part && (!conv_tc_gn_fusable(as[p]) || as[p].gn_cg != a0.gn_cg)) return -1;
     TcGeo gs[kMaxConvGroup];
@@ -1053,19 +1087,13 @@ int launch_conv_tc_group(const ConvArgs* as, int count, int num_sms, cudaStream_
         g.tiles_w = (a.Wout + g.BW - 1) / g.BW;
         g.tiles_h = (a.Hout + g.BH - 1) / g.BH;
         g.cpt = a.Cin / 64;
-        g.nkb = (halo ? a.kt * a.kw : a.kt * a.kh * a.kw) * g.cpt;
+        g.nkb = halo ? a.kt * a.kw * g.cpt : a.kt * a.kh * a.kw * g.cpt;
         g.strided = (a.sh == 2) ? 1 : 0;
         g.halo = halo ? 1 : 0;
         g.n_tiles = 0;
         g.num_tiles = 0;
     }
-    if (halo) {
-        if (swap) return launch_bn_halo<128, true>(as, gs, count, num_sms, cta_tiles, stream);
-        if (narrow) {
-            if (a0.Cout <= 16) return launch_bn_halo<16, false>(as, gs, count, num_sms, cta_tiles, stream);
-            return launch_bn_halo<32, false>(as, gs, count, num_sms, cta_tiles, stream);
-        }
-    }
+    if (halo) return launch_bn_halo<128, true, 1>(as, gs, count, num_sms, cta_tiles, stream);
     if (swap) return launch_bn_any<128, true>(as, gs, count, num_sms, cta_tiles, pairs, stream);
     switch (conv_tc_bn(a0.Cout_pad)) {
         case 256: return launch_bn_any<256, false>(as, gs, count, num_sms, cta_tiles, pairs, stream);
