@@ -1032,10 +1032,13 @@ ConvRoute conv_route(const ConvArgs& a0) {
 }
 
 // GroupNorm statistics come from the swapped wide epilogue (plain or
-// depth-to-space, bf16), for groups of 4, 8 or 16 channels.
+// depth-to-space, bf16), for groups of 4, 8 or 16 channels, of 3x3x3 layers:
+// a layer with a short K loop (1x1x1, the stem over its im2col matrix) is
+// bound by its epilogue, where the extra work costs more than the statistics
+// pass it would save.
 bool conv_tc_gn_fusable(const ConvArgs& a) {
     const ConvRoute r = conv_route(a);
-    return r.swap && !r.narrow && (a.mode == OUT_PLAIN || a.mode == OUT_D2S) && !a.out_fp32 &&
+    return r.swap && !r.narrow && a.kh == 3 && (a.mode == OUT_PLAIN || a.mode == OUT_D2S) && !a.out_fp32 &&
            (a.gn_cg == 4 || a.gn_cg == 8 || a.gn_cg == 16);
 }
 

@@ -168,6 +168,99 @@ __global__ void __launch_bounds__(ROWS_PER_BLOCK) im2col_rows_kernel(const __nv_
     for (int i = threadIdx.x; i < rows * KQ; i += ROWS_PER_BLOCK) out[i] = stage[i / KQ][i % KQ];
 }
 
+// The stem's pixel gather (3x3x3 taps, 3 channels, stride 2 in h and w, Kpad
+// = 128): a block forms the im2col rows of STEM_VOX consecutive output voxels
+// of one output row. It first stages the input it reads -- 3 frames x 3 rows
+// x (2 * STEM_VOX + 1) pixels, with the causal time padding, the edge
+// extension of the frame and zero padding applied -- in shared memory with
+// coalesced loads; then thread t forms the 16-byte chunk t % 16 (K = 8q ..
+// 8q+7, its 8 shared-memory offsets fixed per thread) of successive rows, so
+// every warp stores 512 contiguous bytes.
+constexpr int STEM_VOX = 128;
+constexpr int STEM_PX = 2 * STEM_VOX + 1;  // input pixels of a row segment
+
+__global__ void __launch_bounds__(128) im2col_stem_kernel(const __nv_bfloat16* __restrict__ x,
+                                                          const __nv_bfloat16* __restrict__ hist, GatherGeo g,
+                                                          __nv_bfloat16* __restrict__ A) {
+    __shared__ __nv_bfloat16 tile[9 * STEM_PX * 3];
+    const int wo0 = blockIdx.x * STEM_VOX, ho = blockIdx.y;
+    const int nto = blockIdx.z;  // n * Tout + to
+    const int n = nto / g.Tout, to = nto - n * g.Tout;
+    const int tid = threadIdx.x;
+    // 1. stage the input: row r = dt * 3 + dh, pixel p <-> w = 2 * wo0 - 1 + p. Per row, the
+    //    source frame (or none) is decided once; the loads go out in batches of 8 per thread.
+    const uint16_t* rsrc[9];
+#pragma unroll
+    for (int r = 0; r < 9; ++r) {
+        const int dt = r / 3, dh = r - dt * 3;
+        const int h = ho * g.sh + dh - 1, ti = to * g.st + dt + g.t_off;
+        const __nv_bfloat16* src = nullptr;
+        long long fr = 0;
+        if (h >= 0 && h < g.Hp) {
+            if (ti >= 0) {
+                src = x;
+                fr = (long long)n * g.Tin + ti;
+            } else if (g.hist_T > 0) {
+                src = hist;
+                fr = (long long)n * g.hist_T + g.hist_T + ti;
+            } else if (g.pad_mode == 0) {
+                src = x;
+                fr = (long long)n * g.Tin;
+            }
+        }
+        const int hi = h < g.H ? h : g.H - 1;
+        rsrc[r] = src ? reinterpret_cast<const uint16_t*>(src) + (fr * g.H + hi) * g.W * 3 : nullptr;
+    }
+    // Interior blocks (all 2 * STEM_VOX + 1 pixels inside the frame) copy each row segment as
+    // it lies in memory; edge blocks apply the zero padding and edge extension per element.
+    uint16_t* t16w = reinterpret_cast<uint16_t*>(tile);
+    const int w_first = wo0 * g.sw - 1;
+    const bool interior = w_first >= 0 && w_first + STEM_PX - 1 < g.W;
+#pragma unroll
+    for (int r = 0; r < 9; ++r) {
+        uint16_t* dst = t16w + r * STEM_PX * 3;
+        const uint16_t* rs = rsrc[r];
+        if (!rs) {
+            for (int e = tid; e < STEM_PX * 3; e += blockDim.x) dst[e] = 0;
+        } else if (interior) {
+            const uint16_t* seg = rs + w_first * 3;
+            for (int e = tid; e < STEM_PX * 3; e += blockDim.x) dst[e] = __ldg(seg + e);
+        } else {
+            for (int e = tid; e < STEM_PX * 3; e += blockDim.x) {
+                const int px = e / 3, c = e - px * 3;
+                const int w = w_first + px;
+                dst[e] = (w >= 0 && w < g.Wp) ? __ldg(rs + (w < g.W ? w : g.W - 1) * 3 + c) : (uint16_t)0;
+            }
+        }
+    }
+    __syncthreads();
+    // 2. rows: thread t forms chunk q = t % 16 (K = 8q + j, j < 8) of voxels v = t / 16 + 8 i
+    const int q = tid & 15;
+    int off[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int k = 8 * q + j;
+        if (k < 81) {
+            const int tap = k / 3, c = k - tap * 3;
+            const int dt = tap / 9, dh = (tap / 3) % 3, dw = tap % 3;
+            off[j] = ((dt * 3 + dh) * STEM_PX + dw) * 3 + c;
+        } else {
+            off[j] = -1;
+        }
+    }
+    const long long m0 = ((long long)nto * g.Hout + ho) * g.Wout + wo0;
+    const int nv = min(STEM_VOX, g.Wout - wo0);
+    const uint16_t* t16 = reinterpret_cast<const uint16_t*>(tile);
+    uint4* out = reinterpret_cast<uint4*>(A);
+    for (int v = tid >> 4; v < nv; v += blockDim.x >> 4) {
+        uint32_t u[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) u[j] = off[j] >= 0 ? t16[off[j] + 6 * v] : 0u;
+        out[(m0 + v) * 16 + q] = make_uint4(u[0] | (u[1] << 16), u[2] | (u[3] << 16), u[4] | (u[5] << 16),
+                                            u[6] | (u[7] << 16));
+    }
+}
+
 template <typename T>
 __global__ void edge_pad_kernel(const T* __restrict__ x, long long frames, int H, int W, int Hp, int Wp, int C,
                                 T* __restrict__ y) {
@@ -206,7 +299,11 @@ int launch_im2col_pixels(const __nv_bfloat16* x, const __nv_bfloat16* hist, cons
                          cudaStream_t s) {
     const long long M = (long long)g.N * g.Tout * g.Hout * g.Wout;
     if (M <= 0) return 0;
-    if (taps27(g) && g.Cin == 3 && g.Kpad == 128) {
+    if (taps27(g) && g.Cin == 3 && g.Kpad == 128 && g.sh == 2 && g.sw == 2 && g.N * g.Tout <= 65535 &&
+        g.Hout <= 65535) {
+        const dim3 grid((unsigned)((g.Wout + STEM_VOX - 1) / STEM_VOX), (unsigned)g.Hout, (unsigned)(g.N * g.Tout));
+        im2col_stem_kernel<<<grid, 128, 0, s>>>(x, hist, g, A);
+    } else if (taps27(g) && g.Cin == 3 && g.Kpad == 128) {
         im2col_rows_kernel<3, 16><<<blocks_for(M, ROWS_PER_BLOCK), ROWS_PER_BLOCK, 0, s>>>(x, hist, g, A);
     } else {
         im2col_pixels_kernel<<<blocks_for(M * (g.Kpad / 8), 256), 256, 0, s>>>(x, hist, g, A);
