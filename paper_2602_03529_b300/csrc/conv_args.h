@@ -50,6 +50,9 @@ struct ConvArgs {
     int N, Tin, Hin, Win, Cin;
     // weights: (Cout_pad, Kpad) with K = taps*Cin laid out (tap, ci)
     const void* w;
+    // weights for the tiles of output frame 0 (same layout), or null: the adjoint of
+    // a replicate-padded conv, where input frame 0 also stood in for the padded frames
+    const void* w0;
     const float* bias;    // (Cout) fp32
     int Cout, Cout_pad, Kpad;
     int kt, kh, kw, st, sh, sw;

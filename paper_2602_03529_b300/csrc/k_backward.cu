@@ -512,6 +512,83 @@ __global__ void s2d_kernel(const Ti* __restrict__ d, int N, int oT, int oH, int 
     stf(out + t, v);
 }
 
+// 16-byte forms of the two gradient reshapes (bf16, channel counts multiples of
+// 8): a thread moves 8 consecutive channels, which share one sub-position.
+__global__ void s2d_vec8_kernel(const uint4* __restrict__ d, int N, int oT, int oH, int oW, int C, int rt, int rh,
+                                int rw, int drop_t, int T, int H, int W, int Cpad, uint4* __restrict__ out) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int G = Cpad / 8;
+    const long long total = (long long)N * T * H * W * G;
+    if (t >= total) return;
+    long long r = t / G;
+    const int co0 = (int)(t - r * G) * 8;
+    const int w = (int)(r % W); r /= W;
+    const int h = (int)(r % H); r /= H;
+    const int tt = (int)(r % T);
+    const int n = (int)(r / T);
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (co0 < C * rt * rh * rw) {
+        const int sub = co0 / C, ch0 = co0 - sub * C;
+        const int c = sub % rw, b = (sub / rw) % rh, a = sub / (rw * rh);
+        const int ot = tt * rt + a - drop_t, oh = h * rh + b, ow = w * rw + c;
+        if (ot >= 0 && ot < oT && oh < oH && ow < oW)
+            v = d[(((((long long)n * oT + ot) * oH + oh) * oW + ow) * C + ch0) / 8];
+    }
+    out[t] = v;
+}
+
+__global__ void zero_insert_vec8_kernel(const uint4* __restrict__ dy, int N, int To, int Ho, int Wo, int C, int Tin,
+                                        int Hin, int Win, int st, int sh, int sw, uint4* __restrict__ out) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int G = C / 8;
+    const long long total = (long long)N * Tin * Hin * Win * G;
+    if (t >= total) return;
+    long long r = t / G;
+    const int g = (int)(t - r * G);
+    const int w = (int)(r % Win); r /= Win;
+    const int h = (int)(r % Hin); r /= Hin;
+    const int tt = (int)(r % Tin);
+    const int n = (int)(r / Tin);
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (tt % st == 0 && h % sh == 0 && w % sw == 0) {
+        const int a = tt / st, b = h / sh, e = w / sw;
+        if (a < To && b < Ho && e < Wo) v = dy[((((long long)n * To + a) * Ho + b) * Wo + e) * G + g];
+    }
+    out[t] = v;
+}
+
+// The pixel head's gradient (fp32 frames -> bf16 rows of Cpad channels): one
+// thread per output voxel writes its row in 16-byte pieces.
+__global__ void s2d_head_kernel(const float* __restrict__ d, int N, int oT, int oH, int oW, int C, int rt, int rh,
+                                int rw, int drop_t, int T, int H, int W, int Cpad, uint4* __restrict__ out) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long total = (long long)N * T * H * W;
+    if (t >= total) return;
+    long long r = t;
+    const int w = (int)(r % W); r /= W;
+    const int h = (int)(r % H); r /= H;
+    const int tt = (int)(r % T);
+    const int n = (int)(r / T);
+    const int used = C * rt * rh * rw;
+    for (int co0 = 0; co0 < Cpad; co0 += 8) {
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const int co = co0 + j;
+            v[j] = 0.f;
+            if (co < used) {
+                const int sub = co / C, ch = co - sub * C;
+                const int c = sub % rw, b = (sub / rw) % rh, a = sub / (rw * rh);
+                const int ot = tt * rt + a - drop_t, oh = h * rh + b, ow = w * rw + c;
+                if (ot >= 0 && ot < oT && oh < oH && ow < oW)
+                    v[j] = d[((((long long)n * oT + ot) * oH + oh) * oW + ow) * C + ch];
+            }
+        }
+        out[t * (Cpad / 8) + co0 / 8] = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]),
+                                                   pack_bf16x2(v[4], v[5]), pack_bf16x2(v[6], v[7]));
+    }
+}
+
 template <typename T>
 __global__ void zero_insert_kernel(const T* __restrict__ dy, int N, int To, int Ho, int Wo, int C, int Tin, int Hin,
                                    int Win, int st, int sh, int sw, T* __restrict__ out) {
@@ -574,7 +651,9 @@ __global__ void __launch_bounds__(256) pack_adjoint_kernel(const float* __restri
     // one output tap, 32 input channels (rows) x 32 output channels (columns),
     // transposed through shared memory so reads run along ci and writes along co
     __shared__ float tile[32][33];
-    const int taps_out = corr ? 2 * k * k : k * k * k;
+    // corr 0: the adjoint taps; 1: the frame-0 correction (2 taps); 2: the adjoint taps of
+    // output frame 0, where the correction is folded in (sum of W over dt <= k-1-dtp)
+    const int taps_out = corr == 1 ? 2 * k * k : k * k * k;
     const int tap = blockIdx.z, co0 = blockIdx.x * 32, ci0 = blockIdx.y * 32;
     const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
     const int k2 = k * k;
@@ -585,7 +664,15 @@ __global__ void __launch_bounds__(256) pack_adjoint_kernel(const float* __restri
     for (int i = 0; i < 4; ++i) {
         const int co = co0 + ty + 8 * i, ci = ci0 + tx;
         float v = 0.f;
-        if (co < Cout && ci < Cin) v = !corr ? W(co, k - 1 - dtp, ci) : (dtp == 0 ? W(co, 0, ci) + W(co, 1, ci) : W(co, 0, ci));
+        if (co < Cout && ci < Cin) {
+            if (corr == 0) {
+                v = W(co, k - 1 - dtp, ci);
+            } else if (corr == 1) {
+                v = dtp == 0 ? W(co, 0, ci) + W(co, 1, ci) : W(co, 0, ci);
+            } else {
+                for (int dt = 0; dt <= k - 1 - dtp; ++dt) v += W(co, dt, ci);
+            }
+        }
         tile[ty + 8 * i][tx] = v;
     }
     __syncthreads();
@@ -692,6 +779,21 @@ int launch_s2d(const Ti* d, int N, int oT, int oH, int oW, int C, int rt, int rh
                int W, int Cpad, To* out, cudaStream_t s) {
     const long long n = (long long)N * T * H * W * Cpad;
     if (n <= 0) return 0;
+    if constexpr (sizeof(Ti) == 2 && sizeof(To) == 2) {
+        if (C % 8 == 0 && Cpad % 8 == 0) {
+            s2d_vec8_kernel<<<blocks_for(n / 8, 256), 256, 0, s>>>(reinterpret_cast<const uint4*>(d), N, oT, oH, oW,
+                                                                    C, rt, rh, rw, drop_t, T, H, W, Cpad,
+                                                                    reinterpret_cast<uint4*>(out));
+            return (int)cudaGetLastError();
+        }
+    }
+    if constexpr (sizeof(Ti) == 4 && sizeof(To) == 2) {
+        if (Cpad % 8 == 0) {
+            s2d_head_kernel<<<blocks_for(n / Cpad, 128), 128, 0, s>>>(d, N, oT, oH, oW, C, rt, rh, rw, drop_t, T, H,
+                                                                      W, Cpad, reinterpret_cast<uint4*>(out));
+            return (int)cudaGetLastError();
+        }
+    }
     s2d_kernel<Ti, To><<<blocks_for(n, 256), 256, 0, s>>>(d, N, oT, oH, oW, C, rt, rh, rw, drop_t, T, H, W, Cpad, out);
     return (int)cudaGetLastError();
 }
@@ -707,6 +809,12 @@ int launch_zero_insert(const T* dy, int N, int To, int Ho, int Wo, int C, int Ti
                        int sw, T* out, cudaStream_t s) {
     const long long n = (long long)N * Tin * Hin * Win * C;
     if (n <= 0) return 0;
+    if (sizeof(T) == 2 && C % 8 == 0) {
+        zero_insert_vec8_kernel<<<blocks_for(n / 8, 256), 256, 0, s>>>(reinterpret_cast<const uint4*>(dy), N, To, Ho,
+                                                                        Wo, C, Tin, Hin, Win, st, sh, sw,
+                                                                        reinterpret_cast<uint4*>(out));
+        return (int)cudaGetLastError();
+    }
     zero_insert_kernel<T><<<blocks_for(n, 256), 256, 0, s>>>(dy, N, To, Ho, Wo, C, Tin, Hin, Win, st, sh, sw, out);
     return (int)cudaGetLastError();
 }
@@ -729,7 +837,7 @@ template int launch_mse<__nv_bfloat16>(const float*, const __nv_bfloat16*, long 
 template <typename T>
 int launch_pack_adjoint(const float* w, int Cout, int Cin, int k, int rows_pad, int cpad, int corr, T* out,
                         cudaStream_t s) {
-    const int taps_out = corr ? 2 * k * k : k * k * k;
+    const int taps_out = corr == 1 ? 2 * k * k : k * k * k;
     dim3 grid((cpad + 31) / 32, (rows_pad + 31) / 32, taps_out);
     pack_adjoint_kernel<T><<<grid, 256, 0, s>>>(w, Cout, Cin, k, rows_pad, cpad, corr, out);
     return (int)cudaGetLastError();

@@ -57,6 +57,7 @@ struct TcGeo {
 template <int MAXP>
 struct TcBatch {
     CUtensorMap tm_w;
+    CUtensorMap tm_w0;  // weights of the output-frame-0 tiles (a.w0), else a copy of tm_w
     int w_rows;  // rows of each weight box: BN (/ CL), or the 16/32 real rows of a narrow halo layer
     CUtensorMap tm_x[MAXP];
     CUtensorMap tm_h[MAXP];
@@ -336,6 +337,7 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                     }
                     uint8_t* sa = smem + s * C::STAGE;
                     uint8_t* sb = sa + C::ACT_BYTES;
+                    const CUtensorMap* wmap = (tc.to == 0) ? &B.tm_w0 : &B.tm_w;
                     if constexpr (HALO > 0) {
                         // rows th*BH - 1 .. th*BH + BH of the input frame (zeros outside), per block
                         mbar_arrive_expect_tx(&full[s],
@@ -347,7 +349,7 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                                         tc.th * g.BH - 1, tcoord);
 #pragma unroll
                             for (int d = 0; d < 3; ++d)
-                                tma_load_2d(sb + (c * 3 + d) * C::W_TAP_BYTES, &B.tm_w, &full[s],
+                                tma_load_2d(sb + (c * 3 + d) * C::W_TAP_BYTES, wmap, &full[s],
                                             ((dt * 3 + d) * 3 + dw) * a.Cin + ci, tc.nt * BN);
                         }
                         last_ph[s] = (int)ph;
@@ -367,9 +369,9 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                                     tc.th * g.BH + (dh == 0 ? -1 : 0), tcoord);
                     }
                     if constexpr (CL == 1)
-                        tma_load_2d(sb, &B.tm_w, &full[s], tap * a.Cin + cb * 64, tc.nt * BN);
+                        tma_load_2d(sb, wmap, &full[s], tap * a.Cin + cb * 64, tc.nt * BN);
                     else
-                        tma_load_2d_mc(sb + rank * HALF_W, &B.tm_w, &full[s], tap * a.Cin + cb * 64,
+                        tma_load_2d_mc(sb + rank * HALF_W, wmap, &full[s], tap * a.Cin + cb * 64,
                                        tc.nt * BN + (int)rank * (BN / 2), (uint16_t)0x3);
                     last_ph[s] = (int)ph;
                     if (++s == C::STAGES) {
@@ -811,6 +813,11 @@ int launch_bn(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int c
     // layer loads its real rows only
     B.w_rows = (HALO > 0 && SWAP && as[0].Cout <= 32) ? (as[0].Cout + 15) / 16 * 16 : BN / CL;
     if (!encode_w_map(&B.tm_w, as[0].w, as[0].Cout_pad, as[0].Kpad, B.w_rows)) return -1;
+    if (as[0].w0) {
+        if (!encode_w_map(&B.tm_w0, as[0].w0, as[0].Cout_pad, as[0].Kpad, B.w_rows)) return -1;
+    } else {
+        B.tm_w0 = B.tm_w;
+    }
     long long total = 0;
     for (int p = 0; p < count; ++p) {
         const ConvArgs& a = as[p];
@@ -1069,7 +1076,7 @@ int launch_conv_tc_group(const ConvArgs* as, int count, int num_sms, cudaStream_
     if (count < 1 || count > kMaxConvGroup) return -1;
     const ConvArgs& a0 = as[0];
     for (int p = 1; p < count; ++p)
-        if (as[p].w != a0.w || as[p].Cin != a0.Cin || as[p].Cout_pad != a0.Cout_pad || as[p].Kpad != a0.Kpad ||
+        if (as[p].w != a0.w || as[p].w0 != a0.w0 || as[p].Cin != a0.Cin || as[p].Cout_pad != a0.Cout_pad || as[p].Kpad != a0.Kpad ||
             as[p].kt != a0.kt || as[p].kh != a0.kh || as[p].kw != a0.kw || as[p].sh != a0.sh || as[p].mode != a0.mode ||
             as[p].out_fp32 != a0.out_fp32)
             return -1;

@@ -211,26 +211,26 @@ __global__ void __launch_bounds__(128) im2col_stem_kernel(const __nv_bfloat16* _
         const int hi = h < g.H ? h : g.H - 1;
         rsrc[r] = src ? reinterpret_cast<const uint16_t*>(src) + (fr * g.H + hi) * g.W * 3 : nullptr;
     }
-    // Interior blocks (all 2 * STEM_VOX + 1 pixels inside the frame) copy each row segment as
-    // it lies in memory; edge blocks apply the zero padding and edge extension per element.
+    // Each row segment: the pixels inside the frame, [p_lo, p_hi), are copied as they lie in
+    // memory; pixels left of the frame are zero, those right of it repeat the last column
+    // (edge extension) up to the padded width and are zero beyond.
     uint16_t* t16w = reinterpret_cast<uint16_t*>(tile);
     const int w_first = wo0 * g.sw - 1;
-    const bool interior = w_first >= 0 && w_first + STEM_PX - 1 < g.W;
+    const int p_lo = max(0, -w_first);
+    const int p_hi = max(p_lo, min(STEM_PX, g.W - w_first));
 #pragma unroll
     for (int r = 0; r < 9; ++r) {
         uint16_t* dst = t16w + r * STEM_PX * 3;
         const uint16_t* rs = rsrc[r];
         if (!rs) {
             for (int e = tid; e < STEM_PX * 3; e += blockDim.x) dst[e] = 0;
-        } else if (interior) {
-            const uint16_t* seg = rs + w_first * 3;
-            for (int e = tid; e < STEM_PX * 3; e += blockDim.x) dst[e] = __ldg(seg + e);
-        } else {
-            for (int e = tid; e < STEM_PX * 3; e += blockDim.x) {
-                const int px = e / 3, c = e - px * 3;
-                const int w = w_first + px;
-                dst[e] = (w >= 0 && w < g.Wp) ? __ldg(rs + (w < g.W ? w : g.W - 1) * 3 + c) : (uint16_t)0;
-            }
+            continue;
+        }
+        for (int e = 3 * p_lo + tid; e < 3 * p_hi; e += blockDim.x) dst[e] = __ldg(rs + (long long)w_first * 3 + e);
+        for (int e = tid; e < 3 * p_lo; e += blockDim.x) dst[e] = 0;
+        for (int e = 3 * p_hi + tid; e < 3 * STEM_PX; e += blockDim.x) {
+            const int px = e / 3, c = e - px * 3;
+            dst[e] = (w_first + px < g.Wp) ? __ldg(rs + (long long)(g.W - 1) * 3 + c) : (uint16_t)0;
         }
     }
     __syncthreads();

@@ -23,6 +23,13 @@
 // layer such as the 12-channel pixel head) and input channels past Cin (an
 // im2col matrix of 192 columns) are neither loaded nor stored: row m of the
 // product depends on row m of A only, column n on column n of B only.
+//
+// Halo form (stride-1 3x3x3 layers, BN = 128): a CTA accumulates the three dh
+// taps of one (dt, dw) in three TMEM accumulators. Per K step it loads the dY
+// box and one X box of BH + 2 rows (BW = 8 or 16); tap dh reads the X box from
+// voxel row dh * BW on, a whole number of 8-row (1 KB) groups, so its operand
+// descriptor starts there and the two 64-channel halves of X lie one halo box
+// apart (the leading byte offset). X bytes per MMA drop about 2.4-fold.
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -41,9 +48,11 @@ constexpr int KV = 64;  // voxels per K step
 struct WtcGeo {
     int BH, BW, tiles_h, tiles_w;
     long long vtiles;   // voxel tiles (K steps) in total
-    int m_tiles, n_tiles, taps, S;
+    int m_tiles, n_tiles, taps, S;  // taps: CTA tap slots (dt, dw groups in the halo form)
     int strided;        // X read through the parity view (stride 2 in h and w)
 };
+
+constexpr int HALO_ROWS_MAX = (KV / 16 + 2) * 16;  // X box rows of the widest halo tile (BW = 16)
 
 __device__ __forceinline__ uint64_t mn_sw128_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
     uint64_t d = 0;
@@ -60,23 +69,25 @@ __host__ __device__ constexpr uint32_t idesc_bf16_mn(int M, int N) {
            ((uint32_t)(M >> 4) << 24);
 }
 
-template <int BN>
+template <int BN, bool HT = false>
 struct WCfg {
     static constexpr int A_BYTES = 2 * KV * 128;          // 128 output channels = two 64-channel boxes
-    static constexpr int B_BYTES = (BN / 64) * KV * 128;  // BN input channels
+    static constexpr int B_BOX = (HT ? HALO_ROWS_MAX : KV) * 128;
+    static constexpr int B_BYTES = (BN / 64) * B_BOX;     // BN input channels
     static constexpr int STAGE = A_BYTES + B_BYTES;
     static constexpr int STAGES = (200 * 1024 / STAGE) > 8 ? 8 : (200 * 1024 / STAGE);
-    static constexpr int TMEM_COLS = BN;
+    static constexpr int TMEM_COLS = HT ? 512 : BN;
     static constexpr int SMEM = STAGES * STAGE + 1024 + 256;
     static constexpr uint32_t IDESC = idesc_bf16_mn(128, BN);
 };
 
-template <int BN>
+template <int BN, bool HT>
 __global__ void __launch_bounds__(192, 1)
     wgrad_tc_kernel(const __grid_constant__ CUtensorMap tm_dy, const __grid_constant__ CUtensorMap tm_x,
                     const WgradArgs a, const WtcGeo g, float* __restrict__ part, int* status,
                     unsigned long long wait_ns) {
-    using C = WCfg<BN>;
+    using C = WCfg<BN, HT>;
+    static_assert(!HT || BN == 128, "three accumulators of 128 columns");
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_addr = smem_u32(smem_raw);
     uint8_t* smem = smem_raw + (((raw_addr + 1023u) & ~1023u) - raw_addr);
@@ -95,10 +106,14 @@ __global__ void __launch_bounds__(192, 1)
     const int tap = (int)(t % g.taps);
     const int split = (int)(t / g.taps);
     const long long v_begin = (long long)split * g.vtiles / g.S, v_end = (long long)(split + 1) * g.vtiles / g.S;
-    const int dw = tap % a.kw, dh = (tap / a.kw) % a.kh, dt = tap / (a.kw * a.kh);
+    // halo form: `tap` is the (dt, dw) slot; dh = 0, 1, 2 are the three accumulators
+    const int dw = HT ? tap % 3 : tap % a.kw;
+    const int dh = HT ? 0 : (tap / a.kw) % a.kh;
+    const int dt = HT ? tap / 3 : tap / (a.kw * a.kh);
     const int a_boxes = (mt * 128 + 64 < a.Cout) ? 2 : 1;
     const int b_boxes = min(BN / 64, (a.Cin - nt * BN) / 64);
-    const uint32_t tx_bytes = (uint32_t)(a_boxes + b_boxes) * KV * 128;
+    const int xrows = HT ? (g.BH + 2) * g.BW : KV;  // rows of one X box
+    const uint32_t tx_bytes = (uint32_t)(a_boxes * KV + b_boxes * xrows) * 128;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::STAGES; ++s) {
@@ -156,7 +171,12 @@ __global__ void __launch_bounds__(192, 1)
             const int ycoord = n * a.Tout + to;
             for (int j = 0; j < a_boxes; ++j)
                 tma_load_4d(sa + j * KV * 128, &tm_dy, &full[s], mt * 128 + j * 64, tw * g.BW, th * g.BH, ycoord);
-            if (!g.strided) {
+            if (HT) {
+                // rows th*BH - 1 .. th*BH + BH of the input frame (zeros outside)
+                for (int j = 0; j < b_boxes; ++j)
+                    tma_load_4d(sb + j * C::B_BOX, &tm_x, &full[s], nt * BN + j * 64, tw * g.BW + dw - 1,
+                                th * g.BH - 1, tcoord);
+            } else if (!g.strided) {
                 for (int j = 0; j < b_boxes; ++j)
                     tma_load_4d(sb + j * KV * 128, &tm_x, &full[s], nt * BN + j * 64,
                                 tw * g.BW + dw - (a.kw - 1) / 2, th * g.BH + dh - (a.kh - 1) / 2, tcoord);
@@ -186,10 +206,21 @@ __global__ void __launch_bounds__(192, 1)
             tc_fence_after();
             const uint32_t sa = smem_u32(smem + s * C::STAGE);
             const uint32_t sb = sa + C::A_BYTES;
+            if constexpr (HT) {
+                const uint32_t shift = (uint32_t)g.BW * 128u;  // one input row of the halo box
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-                tc_mma_bf16(tmem_base, mn_sw128_desc(sa + k * 2048, KV * 128, 1024),
-                            mn_sw128_desc(sb + k * 2048, KV * 128, 1024), C::IDESC, (any || k) ? 1u : 0u);
+                for (int d = 0; d < 3; ++d)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
+                        tc_mma_bf16(tmem_base + (uint32_t)(d * BN), mn_sw128_desc(sa + k * 2048, KV * 128, 1024),
+                                    mn_sw128_desc(sb + d * shift + k * 2048, C::B_BOX, 1024), C::IDESC,
+                                    (any || k) ? 1u : 0u);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    tc_mma_bf16(tmem_base, mn_sw128_desc(sa + k * 2048, KV * 128, 1024),
+                                mn_sw128_desc(sb + k * 2048, KV * 128, 1024), C::IDESC, (any || k) ? 1u : 0u);
+            }
             any = true;
             tc_commit(&empty[s]);
             if (++s == C::STAGES) {
@@ -210,18 +241,22 @@ __global__ void __launch_bounds__(192, 1)
         if (okw) {
             tc_fence_after();
             const int co = mt * 128 + q * 32 + lane;
-            float* P = part + ((long long)split * a.Cout + co) * a.K + (long long)tap * a.Cin + nt * BN;
             const bool empty_range = v_end <= v_begin;
 #pragma unroll 1
-            for (int c16 = 0; c16 < BN / 16; ++c16) {
-                float v[16];
-                tmem_ld16(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(c16 * 16), v);
-                if (co < a.Cout && nt * BN + c16 * 16 < a.Cin) {
-                    float4* dst = reinterpret_cast<float4*>(P + c16 * 16);
+            for (int d = 0; d < (HT ? 3 : 1); ++d) {
+                const int tp = HT ? (dt * 3 + d) * 3 + dw : tap;  // the conv tap of accumulator d
+                float* P = part + ((long long)split * a.Cout + co) * a.K + (long long)tp * a.Cin + nt * BN;
+#pragma unroll 1
+                for (int c16 = 0; c16 < BN / 16; ++c16) {
+                    float v[16];
+                    tmem_ld16(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * BN + c16 * 16), v);
+                    if (co < a.Cout && nt * BN + c16 * 16 < a.Cin) {
+                        float4* dst = reinterpret_cast<float4*>(P + c16 * 16);
 #pragma unroll
-                    for (int i = 0; i < 4; ++i)
-                        dst[i] = empty_range ? make_float4(0.f, 0.f, 0.f, 0.f)
-                                             : make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                        for (int i = 0; i < 4; ++i)
+                            dst[i] = empty_range ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                                 : make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+                    }
                 }
             }
             tc_fence_before();
@@ -316,20 +351,37 @@ void choose_vtile(int Hout, int Wout, int* BH, int* BW) {
     }
 }
 
-template <int BN>
+// Halo tiles: BW = 8 or 16 (BH = 8 or 4), fewest tiles, then fewest X rows.
+void choose_vtile_halo(int Hout, int Wout, int* BH, int* BW) {
+    long long best = -1, best_rows = 0;
+    for (int bw : {8, 16}) {
+        const int bh = KV / bw;
+        const long long tiles = (long long)((Wout + bw - 1) / bw) * ((Hout + bh - 1) / bh);
+        const long long rows = tiles * (bh + 2) * bw;
+        if (best < 0 || tiles < best || (tiles == best && rows < best_rows)) {
+            best = tiles;
+            best_rows = rows;
+            *BW = bw;
+            *BH = bh;
+        }
+    }
+}
+
+template <int BN, bool HT>
 int launch_bn(const __nv_bfloat16* dy, const __nv_bfloat16* x, const WgradArgs& a, WtcGeo g, float* part,
               int* status, unsigned long long wait_ns, cudaStream_t s) {
-    using C = WCfg<BN>;
+    using C = WCfg<BN, HT>;
     CUtensorMap mdy, mx;
     if (!encode_act_map(&mdy, dy, a.N * a.Tout, a.Hout, a.Wout, a.Cdy, g.BH, g.BW, false)) return -1;
-    if (!encode_act_map(&mx, x, a.N * a.Tin, a.Hin, a.Win, a.Cin, g.BH, g.BW, g.strided != 0)) return -1;
+    if (!encode_act_map(&mx, x, a.N * a.Tin, a.Hin, a.Win, a.Cin, HT ? g.BH + 2 : g.BH, g.BW, g.strided != 0))
+        return -1;
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(wgrad_tc_kernel<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+        cudaFuncSetAttribute(wgrad_tc_kernel<BN, HT>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
         attr = true;
     }
     const long long grid = (long long)g.m_tiles * g.n_tiles * g.taps * g.S;
-    wgrad_tc_kernel<BN><<<(unsigned)grid, 192, C::SMEM, s>>>(mdy, mx, a, g, part, status, wait_ns);
+    wgrad_tc_kernel<BN, HT><<<(unsigned)grid, 192, C::SMEM, s>>>(mdy, mx, a, g, part, status, wait_ns);
     return (int)cudaGetLastError();
 }
 
@@ -355,14 +407,19 @@ int launch_wgrad_tc(const __nv_bfloat16* dy, const __nv_bfloat16* x, const Wgrad
                     cudaStream_t s, int k_valid) {
     WtcGeo g;
     g.strided = (a.sh == 2) ? 1 : 0;
-    choose_vtile(a.Hout, a.Wout, &g.BH, &g.BW);
+    // stride-1 3x3 spatial taps: the halo form with 128 input channels per tile
+    const bool ht = a.sh == 1 && a.sw == 1 && a.kh == 3 && a.kw == 3;
+    if (ht)
+        choose_vtile_halo(a.Hout, a.Wout, &g.BH, &g.BW);
+    else
+        choose_vtile(a.Hout, a.Wout, &g.BH, &g.BW);
     g.tiles_w = (a.Wout + g.BW - 1) / g.BW;
     g.tiles_h = (a.Hout + g.BH - 1) / g.BH;
     g.vtiles = (long long)a.N * a.Tout * g.tiles_h * g.tiles_w;
-    const int BN = (a.Cin % 256 == 0) ? 256 : 128;
+    const int BN = (!ht && a.Cin % 256 == 0) ? 256 : 128;
     g.m_tiles = (a.Cout + 127) / 128;
     g.n_tiles = (a.Cin + BN - 1) / BN;
-    g.taps = a.kt * a.kh * a.kw;
+    g.taps = ht ? a.kt * a.kw : a.kt * a.kh * a.kw;
     const long long out_tiles = (long long)g.m_tiles * g.n_tiles * g.taps;
     // split count: at least 4 voxel tiles per split, partials within max_floats,
     // and the grid (one CTA per SM) filling its last wave as fully as possible
@@ -381,8 +438,9 @@ int launch_wgrad_tc(const __nv_bfloat16* dy, const __nv_bfloat16* x, const Wgrad
     }
     if ((size_t)S * a.Cout * a.K > max_floats) return -1;
     g.S = (int)S;
-    int e = (BN == 256) ? launch_bn<256>(dy, x, a, g, part, status, wait_ns, s)
-                        : launch_bn<128>(dy, x, a, g, part, status, wait_ns, s);
+    int e = ht ? launch_bn<128, true>(dy, x, a, g, part, status, wait_ns, s)
+               : (BN == 256) ? launch_bn<256, false>(dy, x, a, g, part, status, wait_ns, s)
+                             : launch_bn<128, false>(dy, x, a, g, part, status, wait_ns, s);
     if (e) return e;
     const long long n = (long long)a.Cout * a.K;
     if (k_valid > 0 && k_valid < a.K)

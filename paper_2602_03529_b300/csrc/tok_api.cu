@@ -109,6 +109,7 @@ void tok_destroy(tok_ctx* c) {
         if (cw.w) cudaFree(cw.w);
         if (cw.wt) cudaFree(cw.wt);
         if (cw.wc) cudaFree(cw.wc);
+        if (cw.wf0) cudaFree(cw.wf0);
     }
     if (c->d_master) cudaFree(c->d_master);
     if (c->tarena) cudaFree(c->tarena);

@@ -45,6 +45,7 @@ struct ConvW {
     // and for k = 3 the replicate-pad correction [rows_pad][2*k*k][cpad]
     void* wt = nullptr;
     void* wc = nullptr;
+    void* wf0 = nullptr;  // BF16: adjoint taps of output frame 0 with the correction folded in
     int rows_pad = 0, cpad = 0;
 };
 

@@ -361,8 +361,12 @@ struct TrainExec : Exec {
         shadow.Cin = cw.cpad;
         shadow.Cout = cw.rows_pad;
         shadow.name = name + ".dgrad";
+        // BF16: the tiles of output frame 0 read their own taps, which fold in the
+        // replicate-pad correction (input frame 0 stood for the two padded frames)
+        const bool fold = c->bf16() && cw.k == 3 && c->arch.time_pad == TOK_PAD_REPLICATE && cw.wf0;
+        if (fold) a.w0 = cw.wf0;
         launch(a, shadow);
-        if (cw.k == 3 && c->arch.time_pad == TOK_PAD_REPLICATE) {
+        if (!fold && cw.k == 3 && c->arch.time_pad == TOK_PAD_REPLICATE) {
             // taps of output frames 0 (dt = 0, 1) and 1 (dt = 0) that were clamped to frame 0
             ConvArgs b2 = a;
             b2.w = cw.wc;
@@ -565,8 +569,11 @@ int pack_adjoints(tok_ctx* c, cudaStream_t s) {
         if (!cw.wt) {
             const size_t kp = c->bf16() ? (size_t)taps * cw.cpad : (size_t)round_up(taps * cw.cpad, 8);
             if (cudaMalloc(&cw.wt, (size_t)cw.rows_pad * kp * es) != cudaSuccess) return TOK_ENOMEM;
-            if (cw.k == 3) {
-                const size_t kc = c->bf16() ? (size_t)18 * cw.cpad : (size_t)round_up(18 * cw.cpad, 8);
+            if (cw.k == 3 && c->bf16()) {
+                // output frame 0 takes its own taps (the replicate-pad correction folded in)
+                if (cudaMalloc(&cw.wf0, (size_t)cw.rows_pad * kp * es) != cudaSuccess) return TOK_ENOMEM;
+            } else if (cw.k == 3) {
+                const size_t kc = (size_t)round_up(18 * cw.cpad, 8);
                 if (cudaMalloc(&cw.wc, (size_t)cw.rows_pad * kc * es) != cudaSuccess) return TOK_ENOMEM;
             }
         }
@@ -575,9 +582,9 @@ int pack_adjoints(tok_ctx* c, cudaStream_t s) {
         if (c->bf16()) {
             e = launch_pack_adjoint<__nv_bfloat16>(w, cw.Cout, cw.Cin, cw.k, cw.rows_pad, cw.cpad, 0,
                                                    static_cast<__nv_bfloat16*>(cw.wt), s);
-            if (!e && cw.wc)
-                e = launch_pack_adjoint<__nv_bfloat16>(w, cw.Cout, cw.Cin, cw.k, cw.rows_pad, cw.cpad, 1,
-                                                       static_cast<__nv_bfloat16*>(cw.wc), s);
+            if (!e && cw.wf0)
+                e = launch_pack_adjoint<__nv_bfloat16>(w, cw.Cout, cw.Cin, cw.k, cw.rows_pad, cw.cpad, 2,
+                                                       static_cast<__nv_bfloat16*>(cw.wf0), s);
         } else {
             e = launch_pack_adjoint<float>(w, cw.Cout, cw.Cin, cw.k, cw.rows_pad, cw.cpad, 0,
                                            static_cast<float*>(cw.wt), s);
