@@ -275,6 +275,16 @@ int gn_chunks_per_frame(long long HW, int C, int vec) {
     return S;
 }
 
+// Where a forward launch left the (mean, rstd) of every (frame, group) in its scratch.
+float2* gn_stats_of_scratch(void* scratch, long long frames, long long HW, int C, int G, int vec) {
+    int vpt, S;
+    gn_plan(frames, HW * C / vec, 0, &vpt, &S);
+    Triple* own = static_cast<Triple*>(scratch);
+    return reinterpret_cast<float2*>((reinterpret_cast<uintptr_t>(own + frames * S * G) + 15) & ~uintptr_t(15));
+}
+
+int gn_vectors_per_thread() { return GN_VPT; }
+
 size_t gn_scratch_bytes(long long frames, long long HW, int C, int G, int num_sms, int vec) {
     int vpt, S;
     gn_plan(frames, HW * C / vec, num_sms, &vpt, &S);

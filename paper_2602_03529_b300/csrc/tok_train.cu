@@ -9,6 +9,8 @@
 // ahead in time; stride-2 convs see dY spread onto their input grid; under
 // replicate padding a two-tap correction adds the clamped taps into frame 0.
 // Weight gradients use the split-K kernel of k_backward.cu.
+#include <array>
+
 #include "tok_internal.h"
 
 namespace {
@@ -36,6 +38,12 @@ struct TrainBufs {
     char* gnb = nullptr;
     char* gnpart = nullptr;  // GroupNorm statistics reduced by the forward convs
     size_t gnpart_bytes = 0;
+    // kept from the forward for the backward: per residual block its GN1 output,
+    // first conv output and GN2 output; the output GroupNorms' outputs; and every
+    // GroupNorm's scratch, which holds the (mean, rstd) its backward reuses
+    std::map<std::string, std::array<char*, 3>> blk;
+    std::map<std::string, char*> gn_out;
+    std::map<std::string, char*> gn_sc;
     float* wpart = nullptr;
     size_t wpart_floats = 0;
     float* mse = nullptr;
@@ -93,6 +101,29 @@ TrainBufs train_layout(const tok_ctx* c, int N, int T, int H, int W, char* base)
         }
     }
     work = std::max(work, vox(0) * (size_t)adj_cpad(c, a.in_ch * 4 * a.t_stem) * es);
+    // per-layer keeps of the forward
+    {
+        const int vec = c->bf16() ? 8 : 4;
+        auto gn_keep = [&](const std::string& name, int l, int C) {
+            const int G = std::max(1, std::min(a.gn_groups, C / 2));
+            b.gn_sc[name] = take(gn_scratch_bytes((long long)N * Tl[l], (long long)(H >> (l + 1)) * (W >> (l + 1)), C,
+                                                  G, c->num_sms, vec));
+        };
+        for (int side = 0; side < 2; ++side)
+            for (int l = 0; l < L; ++l)
+                for (int k = 0; k < a.blocks; ++k) {
+                    const std::string nm = std::string(side ? "dec.l" : "enc.l") + std::to_string(l) + ".b" +
+                                           std::to_string(k);
+                    const int cin = (!side && k == 0) ? (l > 0 ? a.ch[l - 1] : a.ch[0]) : a.ch[l];
+                    b.blk[nm] = {take(vox(l) * cin * es), take(vox(l) * a.ch[l] * es), take(vox(l) * a.ch[l] * es)};
+                    gn_keep(nm + ".gn1", l, cin);
+                    gn_keep(nm + ".gn2", l, a.ch[l]);
+                }
+        b.gn_out["enc.out_gn"] = take(vox(L - 1) * a.ch[L - 1] * es);
+        gn_keep("enc.out_gn", L - 1, a.ch[L - 1]);
+        b.gn_out["dec.out_gn"] = take(vox(0) * a.ch[0] * es);
+        gn_keep("dec.out_gn", 0, a.ch[0]);
+    }
     const size_t ntok = (size_t)N * Tl[L - 1] * (H >> L) * (W >> L);
     b.z = reinterpret_cast<float*>(take(ntok * a.nlev * 4));
     b.idx = reinterpret_cast<int32_t*>(take(ntok * 4));
@@ -136,11 +167,21 @@ struct TrainExec : Exec {
         for (int i = 0; i < 5; ++i) w.act[i] = nullptr;
     }
 
-    // Residual block forward into `out` (temporaries R1..R3).
+    // GroupNorm+SiLU whose scratch (and so its statistics) is kept for the backward.
+    Act gn_kept(const std::string& name, const Act& X, void* out) {
+        char* keep = w.gn;
+        w.gn = b.gn_sc.at(name);
+        Act A = gn_silu(name, X, out);
+        w.gn = keep;
+        return A;
+    }
+
+    // Residual block forward into `out`; GN1 output, first conv output and GN2 output kept.
     Act block_fwd(const std::string& name, const Act& X, void* out) {
-        Act A1 = gn_silu(name + ".gn1", X, b.R1);
-        Act H = conv(name + ".c1", A1, b.R2);
-        Act A2 = gn_silu(name + ".gn2", H, b.R1);
+        const auto& kb = b.blk.at(name);
+        Act A1 = gn_kept(name + ".gn1", X, kb[0]);
+        Act H = conv(name + ".c1", A1, kb[1]);
+        Act A2 = gn_kept(name + ".gn2", H, kb[2]);
         const void* res = X.p;
         if (c->cindex.count(name + ".sc")) res = conv(name + ".sc", X, b.R3).p;
         return conv(name + ".c2", A2, out, res);
@@ -167,7 +208,7 @@ struct TrainExec : Exec {
             if (ar.blocks == 0) X.p = b.enc[l][0];
             if (l < L - 1) X = conv("enc.down" + std::to_string(l), X, b.enc[l + 1][0], nullptr, 2, 2, 2);
         }
-        Act A = gn_silu("enc.out_gn", X, b.R1);
+        Act A = gn_kept("enc.out_gn", X, b.gn_out.at("enc.out_gn"));
         out_conv("enc.out", A, b.z, b.idx);
         const int Tq = X.T, Hq = X.H, Wq = X.W;
         const long long ntok = (long long)N * Tq * Hq * Wq;
@@ -205,7 +246,7 @@ struct TrainExec : Exec {
             if (l > 0) X = conv_d2s("dec.up" + std::to_string(l - 1), X, b.dec[l - 1][0], 2, 2, 2, X.H * 2, X.W * 2,
                                     false);
         }
-        A = gn_silu("dec.out_gn", X, b.R1);
+        A = gn_kept("dec.out_gn", X, b.gn_out.at("dec.out_gn"));
         conv_d2s("dec.out", A, xhat, ar.t_stem, 2, 2, H, W, true);
         const long long n = (long long)N * T * H * W * ar.in_ch;
         if (c->bf16())
@@ -386,32 +427,32 @@ struct TrainExec : Exec {
         if (err) return;
         const GnW& g = c->gns[c->gindex[name]];
         const long long frames = (long long)x.N * x.T, HW = (long long)x.H * x.W;
-        float2* stats = nullptr;
-        int vpt = 0, S = 0;
+        // the forward's statistics, kept in this GroupNorm's scratch
+        const int vec = c->bf16() ? 8 : 4;
+        const float2* stats = gn_stats_of_scratch(b.gn_sc.at(name), frames, HW, x.C, g.G, vec);
+        const int vpt = gn_vectors_per_thread(), S = gn_chunks_per_frame(HW, x.C, vec);
         const int e = pbegin();
         if (c->bf16()) {
-            ck(launch_gn_stats<__nv_bfloat16>(static_cast<const __nv_bfloat16*>(x.p), frames, HW, x.C, g.G,
-                                              c->arch.gn_eps, b.gn, c->num_sms, s, &stats, &vpt, &S));
             ck(launch_gn_silu_bwd<__nv_bfloat16>(
                 static_cast<const __nv_bfloat16*>(x.p), static_cast<const __nv_bfloat16*>(dy), stats, g.g, g.b,
                 static_cast<const __nv_bfloat16*>(add), frames, HW, x.C, g.G, vpt, S, b.gnb, grads + g.og,
                 grads + g.ob, static_cast<__nv_bfloat16*>(dx), s));
         } else {
-            ck(launch_gn_stats<float>(static_cast<const float*>(x.p), frames, HW, x.C, g.G, c->arch.gn_eps, b.gn,
-                                      c->num_sms, s, &stats, &vpt, &S));
             ck(launch_gn_silu_bwd<float>(static_cast<const float*>(x.p), static_cast<const float*>(dy), stats, g.g,
                                          g.b, static_cast<const float*>(add), frames, HW, x.C, g.G, vpt, S, b.gnb,
                                          grads + g.og, grads + g.ob, static_cast<float*>(dx), s));
         }
         pend(e, 1, 4.0 * (double)frames * HW * x.C * c->esize(), name + ".bwd");
-        c->launches += 6;
+        c->launches += 5;
     }
 
     // Block backward; the block-output gradient G is replaced by the block-input gradient.
     void block_bwd(const std::string& name, const Act& X, Act& G) {
-        Act A1 = gn_silu(name + ".gn1", X, b.R1);
-        Act H = conv(name + ".c1", A1, b.R2);
-        Act A2 = gn_silu(name + ".gn2", H, b.R3);
+        const auto& kb = b.blk.at(name);
+        const int Ch = c->convs[c->cindex[name + ".c1"]].Cout;
+        Act A1{kb[0], X.N, X.T, X.H, X.W, X.C};
+        Act H{kb[1], X.N, X.T, X.H, X.W, Ch};
+        Act A2{kb[2], X.N, X.T, X.H, X.W, Ch};
         wgrad(name + ".c2", G, G.C, A2, 1, 1);
         Act dA2 = dgrad(name + ".c2", G, b.G3);
         gn_bwd(name + ".gn2", H, dA2.p, nullptr, b.G4);
@@ -452,7 +493,7 @@ struct TrainExec : Exec {
                   (double)N * T * H * W * 8);
         Act dY = lev(0, b.Z, co.cpad);
         Act X0 = lev(0, b.dec[0][ar.blocks], ar.ch[0]);
-        Act A = gn_silu("dec.out_gn", X0, b.R1);
+        Act A = lev(0, b.gn_out.at("dec.out_gn"), ar.ch[0]);
         wgrad("dec.out", dY, co.cpad, A, 1, 1);
         Act dA = dgrad("dec.out", dY, b.G3);
         gn_bwd("dec.out_gn", X0, dA.p, nullptr, gcur);
@@ -513,7 +554,7 @@ struct TrainExec : Exec {
                   (double)ntok * 64);
         Act dz{b.dz, N, Tq, Hq, Wq, eo.cpad};
         Act XL = lev(L - 1, b.enc[L - 1][ar.blocks], ar.ch[L - 1]);
-        A = gn_silu("enc.out_gn", XL, b.R1);
+        A = lev(L - 1, b.gn_out.at("enc.out_gn"), ar.ch[L - 1]);
         wgrad("enc.out", dz, eo.cpad, A, 1, 1);
         dA = dgrad("enc.out", dz, b.G3);
         gn_bwd("enc.out_gn", XL, dA.p, nullptr, gcur);
