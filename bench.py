@@ -305,7 +305,8 @@ def training(args, params, N=2, T=17, H=256, W=256, steps=5, warmup=2):
     upd = sum(e[2].elapsed_time(e[3]) for e in ev) / steps
     loss = float(tr.loss.item())
     tk.close()
-    return {"workload": f"fwd+bwd step, batch {N}x3x{T}x{H}x{W}, BF16, MSE, STE, drop 10%, per-block recompute",
+    return {"workload": f"fwd+bwd step, batch {N}x3x{T}x{H}x{W}, BF16, MSE, STE, drop 10%, block intermediates "
+                        "kept from the forward, SGD with the weight re-pack",
             "step_ms": fwd + bwd + upd, "fwd_ms": fwd, "bwd_ms": bwd, "sgd_ms": upd, "loss": loss,
             "steps": steps, "warmup": warmup}
 

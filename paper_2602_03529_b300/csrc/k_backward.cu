@@ -683,6 +683,49 @@ __global__ void __launch_bounds__(256) pack_adjoint_kernel(const float* __restri
     }
 }
 
+// All three BF16 layouts of a 3x3x3 conv from one read of its master weights
+// W[co][dt][dh][dw][ci]: the forward rows fwd[co][tap * Cin + ci], the adjoint
+// taps wt[ci][tap'][co] (tap' = the flipped tap) and the frame-0 adjoint taps
+// wf0[ci][tap'][co] (sum of W over dt <= 2 - dt'). A block takes 32 output x
+// 32 input channels of one spatial tap (dh, dw) for all three dt; the two
+// adjoint layouts go through a shared-memory transpose.
+__global__ void __launch_bounds__(256) pack3_kernel(const float* __restrict__ w, int Cout, int Cin, int Cout_pad,
+                                                    int Kpad, int rows_pad, int cpad, __nv_bfloat16* __restrict__ fwd,
+                                                    __nv_bfloat16* __restrict__ wt, __nv_bfloat16* __restrict__ wf0) {
+    __shared__ float tile[3][32][33];
+    const int hw = blockIdx.z, dh = hw / 3, dw = hw % 3;
+    const int co0 = blockIdx.x * 32, ci0 = blockIdx.y * 32;
+    const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
+#pragma unroll
+    for (int dt = 0; dt < 3; ++dt)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int co = co0 + ty + 8 * i, ci = ci0 + tx;
+            const float v = (co < Cout && ci < Cin) ? w[(((long long)co * 3 + dt) * 9 + dh * 3 + dw) * Cin + ci] : 0.f;
+            tile[dt][ty + 8 * i][tx] = v;
+            const int tap = (dt * 3 + dh) * 3 + dw;
+            if (co < Cout_pad && ci < Cin) fwd[(long long)co * Kpad + (long long)tap * Cin + ci] = __float2bfloat16_rn(v);
+        }
+    __syncthreads();
+    // adjoint taps: tap' = (dt', dh', dw') with W(2 - dt', 2 - dh', 2 - dw')
+    const int tp_hw = (2 - dh) * 3 + (2 - dw);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int ci = ci0 + ty + 8 * i, co = co0 + tx;
+        if (ci >= rows_pad || co >= cpad) continue;
+        const float w0 = tile[0][tx][ty + 8 * i], w1 = tile[1][tx][ty + 8 * i], w2 = tile[2][tx][ty + 8 * i];
+        const long long base = (long long)ci * 27;
+#pragma unroll
+        for (int dtp = 0; dtp < 3; ++dtp) {
+            const int tp = dtp * 9 + tp_hw;
+            const float vt = dtp == 0 ? w2 : (dtp == 1 ? w1 : w0);
+            const float vf = dtp == 0 ? w0 + w1 + w2 : (dtp == 1 ? w0 + w1 : w0);
+            wt[(base + tp) * cpad + co] = __float2bfloat16_rn(vt);
+            wf0[(base + tp) * cpad + co] = __float2bfloat16_rn(vf);
+        }
+    }
+}
+
 __global__ void sgd_kernel(float* __restrict__ p, const float* __restrict__ g, long long n, float lr) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < n) p[t] -= lr * g[t];
@@ -845,6 +888,14 @@ int launch_pack_adjoint(const float* w, int Cout, int Cin, int k, int rows_pad, 
 template int launch_pack_adjoint<float>(const float*, int, int, int, int, int, int, float*, cudaStream_t);
 template int launch_pack_adjoint<__nv_bfloat16>(const float*, int, int, int, int, int, int, __nv_bfloat16*,
                                                 cudaStream_t);
+
+int launch_pack3(const float* w, int Cout, int Cin, int Cout_pad, int Kpad, int rows_pad, int cpad,
+                 __nv_bfloat16* fwd, __nv_bfloat16* wt, __nv_bfloat16* wf0, cudaStream_t s) {
+    const int cmax = std::max(Cout_pad, cpad), rmax = std::max(Cin, rows_pad);
+    dim3 grid((cmax + 31) / 32, (rmax + 31) / 32, 9);
+    pack3_kernel<<<grid, 256, 0, s>>>(w, Cout, Cin, Cout_pad, Kpad, rows_pad, cpad, fwd, wt, wf0);
+    return (int)cudaGetLastError();
+}
 
 int launch_sgd(float* p, const float* g, long long n, float lr, cudaStream_t s) {
     if (n <= 0) return 0;

@@ -130,6 +130,9 @@ int launch_zero_insert(const T* dy, int N, int To, int Ho, int Wo, int C, int Ti
                        int sw, T* out, cudaStream_t s);
 template <typename T>
 int launch_mse(const float* xh, const T* x, long long n, float* dxh, float* loss, float* scratch, cudaStream_t s);
+// forward rows, adjoint taps and frame-0 adjoint taps of a BF16 3x3x3 conv in one pass (k_backward.cu)
+int launch_pack3(const float* w, int Cout, int Cin, int Cout_pad, int Kpad, int rows_pad, int cpad,
+                 __nv_bfloat16* fwd, __nv_bfloat16* wt, __nv_bfloat16* wf0, cudaStream_t s);
 template <typename T>
 int launch_pack_adjoint(const float* w, int Cout, int Cin, int k, int rows_pad, int cpad, int corr, T* out,
                         cudaStream_t s);

@@ -663,9 +663,32 @@ int tok_set_params_device(tok_ctx* c, const float* d_flat, void* stream) {
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (cudaMemcpyAsync(c->d_master, d_flat, (size_t)c->param_total * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
         return TOK_ECUDA;
-    for (auto& cw : c->convs)
+    // in a training loop (adjoint layouts already allocated, BF16): the forward rows and
+    // both adjoint layouts of every 3x3x3 conv from one read of its new weights
+    bool adj = c->bf16();
+    for (const auto& cw : c->convs)
+        if (cw.name != "enc.stem" && cw.name != "stage.c0" && !cw.wt) adj = false;
+    for (auto& cw : c->convs) {
+        const bool fused = adj && cw.k == 3 && !cw.im2col && cw.wt && cw.wf0;
+        if (fused) {
+            cw.b = c->d_master + cw.ob;
+            if (launch_pack3(c->d_master + cw.ow, cw.Cout, cw.Cin, cw.Cout_pad, cw.Kpad, cw.rows_pad, cw.cpad,
+                             static_cast<__nv_bfloat16*>(cw.w), static_cast<__nv_bfloat16*>(cw.wt),
+                             static_cast<__nv_bfloat16*>(cw.wf0), s))
+                return TOK_ECUDA;
+            continue;
+        }
         if (upload_conv(c, cw, s) != TOK_OK) return TOK_ECUDA;
-    c->adjoint_dirty = true;
+        if (adj && cw.wt &&
+            launch_pack_adjoint<__nv_bfloat16>(c->d_master + cw.ow, cw.Cout, cw.Cin, cw.k, cw.rows_pad, cw.cpad, 0,
+                                               static_cast<__nv_bfloat16*>(cw.wt), s))
+            return TOK_ECUDA;
+        if (adj && cw.wf0 &&
+            launch_pack_adjoint<__nv_bfloat16>(c->d_master + cw.ow, cw.Cout, cw.Cin, cw.k, cw.rows_pad, cw.cpad, 2,
+                                               static_cast<__nv_bfloat16*>(cw.wf0), s))
+            return TOK_ECUDA;
+    }
+    c->adjoint_dirty = !adj;
     return TOK_OK;
 }
 

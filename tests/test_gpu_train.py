@@ -152,3 +152,30 @@ def test_sgd_reduces_loss_and_autograd_node(P):
     assert torch.equal(params.grad, g2)
     assert tk.status() == 0
     tk.close()
+
+
+def test_repacked_weights_equal_fresh_context(P):
+    """After an SGD step the context re-packs the forward rows and both adjoint layouts of
+    every 3x3x3 conv in one pass; the next gradient must equal, bit for bit, the one of a
+    fresh context given the same parameters (which packs each layout separately)."""
+    from paper_2602_03529_b300.train import Trainer
+    N, T, H, W = 1, 5, 32, 32
+    kw = dict(ch=(64, 128, 256), blocks=1)
+    tk = P.Tokenizer("bf16", **kw)
+    tk.set_params(S.weights_for(tk.param_spec(), seed=4))
+    tr = Trainer(tk, N, T, H, W)
+    x = torch.from_numpy(S.blurred_noise_clip(3, N, T, H, W)).to("cuda", torch.bfloat16)
+    tr.step(x, 0.1, 1, 0, lr=0.05)
+    l1 = tr.forward(x, 0.1, 1, 1).clone()
+    g1 = tr.backward().clone()
+    tk2 = P.Tokenizer("bf16", **kw)
+    tr2 = Trainer(tk2, N, T, H, W)
+    tr2.load(tr.params.clone())
+    l2 = tr2.forward(x, 0.1, 1, 1).clone()
+    g2 = tr2.backward().clone()
+    torch.cuda.synchronize()
+    assert tk.status() == 0 and tk2.status() == 0
+    assert torch.equal(l1, l2)
+    assert torch.equal(g1, g2)
+    tk.close()
+    tk2.close()
