@@ -226,7 +226,20 @@ __global__ void __launch_bounds__(128) im2col_stem_kernel(const __nv_bfloat16* _
             for (int e = tid; e < STEM_PX * 3; e += blockDim.x) dst[e] = 0;
             continue;
         }
-        for (int e = 3 * p_lo + tid; e < 3 * p_hi; e += blockDim.x) dst[e] = __ldg(rs + (long long)w_first * 3 + e);
+        // all of a thread's loads of the row in flight at once (a row is 3 * STEM_PX elements)
+        const uint16_t* src = rs + (long long)w_first * 3;
+        constexpr int RB = (3 * STEM_PX + 127) / 128;
+        uint16_t v[RB];
+#pragma unroll
+        for (int u = 0; u < RB; ++u) {
+            const int e = 3 * p_lo + u * 128 + tid;
+            v[u] = e < 3 * p_hi ? __ldg(src + e) : (uint16_t)0;
+        }
+#pragma unroll
+        for (int u = 0; u < RB; ++u) {
+            const int e = 3 * p_lo + u * 128 + tid;
+            if (e < 3 * p_hi) dst[e] = v[u];
+        }
         for (int e = tid; e < 3 * p_lo; e += blockDim.x) dst[e] = 0;
         for (int e = 3 * p_hi + tid; e < 3 * STEM_PX; e += blockDim.x) {
             const int px = e / 3, c = e - px * 3;
