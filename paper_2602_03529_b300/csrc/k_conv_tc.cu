@@ -1,24 +1,27 @@
 // BF16 causal 3D convolution on the 5th-generation tensor cores (sm_103a).
 //
 // Implicit GEMM: M = output voxels, N = output channels, K = taps x Cin.
-// One CTA per SM (persistent) walks output tiles of 128 voxels x BN channels.
-// A tile of 128 voxels is a BH x BW block of one output frame; each K block
+// Persistent CTAs (one per SM, or CTAs of a bounded number of tiles) walk
+// output tiles; a voxel tile is a BH x BW block of one output frame. A K block
 // is one tap (dt,dh,dw) x 64 input channels, fetched by one TMA box load of
 // the input frame at the tap's offset (boundary padding = TMA out-of-bounds
 // zero fill; stride-2 convs read a parity view of the input, see the host
-// side). The time-causal left padding is folded into the loader: a tap that
-// falls before frame 0 reads the stream's history tensor (streaming), frame 0
+// side) -- or, for stride-1 3x3x3 layers (the halo form), one (dt, dw, 64
+// channels) group: a single box of BH + 2 rows serves the three dh taps. The
+// time-causal left padding is folded into the loader: a tap that falls
+// before frame 0 reads the stream's history tensor (streaming), frame 0
 // (replicate) or nothing (zero fill via an out-of-range coordinate).
 //
 // Warp roles (192 threads):
-//   warp 0      TMA producer (one lane): A (activations) and B (weights) boxes
-//               into a STAGES-deep ring of 128B-swizzled shared-memory tiles.
-//   warp 1      TMEM allocation and MMA issue (one lane): 4 x
-//               tcgen05.mma.kind::f16 (M=128, N=BN, K=16) per stage into one of
-//               two FP32 accumulators in TMEM; tcgen05.commit frees the stage.
+//   warp 0      TMA producer (one lane): activation and weight boxes into a
+//               STAGES-deep ring of 128B-swizzled shared-memory tiles.
+//   warp 1      TMEM allocation and MMA issue (one lane): tcgen05.mma.kind::f16
+//               (K = 16 each) per stage into one of two FP32 accumulators in
+//               TMEM; tcgen05.commit frees the stage.
 //   warps 2..5  epilogue: tcgen05.ld the accumulator (each warp its 32 TMEM
-//               lanes = 32 voxels), add bias and residual, round to BF16 and
-//               store; or scatter through depth-to-space; or FSQ-quantise.
+//               lanes), add bias and residual, round to BF16 and store; or
+//               scatter through depth-to-space; or FSQ-quantise; and reduce
+//               the GroupNorm statistics of the stored values.
 // The epilogue of tile i overlaps the MMAs of tile i+1 (double-buffered TMEM).
 #include <cudaTypedefs.h>
 
@@ -891,7 +894,7 @@ int launch_bn(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int c
 
 // CTA pairs for layers with at least one wave of tiles (weight halves of 64+
 // rows), single CTAs otherwise and whenever CTA lifetimes are bounded.
-template <int BN, bool SWAP, int NCB>
+template <int BN, bool SWAP, int NCB>  // NCB: 64-channel blocks per halo stage
 int launch_bn_halo(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int cta_tiles, cudaStream_t stream) {
     return count == 1 ? launch_bn<BN, SWAP, 1, 1, NCB>(as, gs, 1, num_sms, cta_tiles, stream)
                       : launch_bn<BN, SWAP, kMaxConvGroup, 1, NCB>(as, gs, count, num_sms, cta_tiles, stream);
