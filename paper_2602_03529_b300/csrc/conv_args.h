@@ -53,6 +53,9 @@ struct ConvArgs {
     // weights for the tiles of output frame 0 (same layout), or null: the adjoint of
     // a replicate-padded conv, where input frame 0 also stood in for the padded frames
     const void* w0;
+    // nonzero: w holds a narrow 3x3x3 stride-1 head (Cout <= 16) as rows dw * 16 + co
+    // of K = (dt, dh, ci), 9 * Cin long (the dw-rows form of the tensor-core conv)
+    int w_dwm;
     const float* bias;    // (Cout) fp32
     int Cout, Cout_pad, Kpad;
     int kt, kh, kw, st, sh, sw;

@@ -47,6 +47,7 @@ struct TcGeo {
     int strided;             // parity view (sh = sw = 2)
     long long m_tiles;       // voxel tiles
     int halo;                // K blocks are (dt, dw, channel block) groups of three dh taps
+    int bwo;                 // output columns per tile: BW, or BW - 2 in the dw-rows form (DWM)
 };
 
 // A grouped launch: up to MAXP inputs of one layer (clips or stream chunks of
@@ -93,15 +94,18 @@ namespace {
 //                most 32 channels) loads only its 16 or 32 weight rows per tap
 //                into weight slots whose other rows stay zero.
 constexpr int HALO_BW_MAX = 64;
+constexpr int DWM_BH = 8, DWM_BW = 32;  // dw-rows form: output rows per tile, input box columns
 
 //                HALO = number of 64-channel blocks per stage (0: no halo).
-template <int BN, bool SWAP, int HALO = 0>
+//                DWM: the dw-rows form (a 10 x 32 box, weight slots of 64 rows).
+template <int BN, bool SWAP, int HALO = 0, bool DWM = false>
 struct Cfg {
     static constexpr int ROWS = SWAP ? 256 : 128;  // voxels per tile
     static constexpr int HALO_BW = HALO_BW_MAX;
-    static constexpr int SUB_ACT = (ROWS + (HALO ? 2 * HALO_BW : 0)) * 128;  // one channel block's box
+    // one channel block's input box
+    static constexpr int SUB_ACT = DWM ? (DWM_BH + 2) * DWM_BW * 128 : (ROWS + (HALO ? 2 * HALO_BW : 0)) * 128;
     static constexpr int ACT_BYTES = (HALO ? HALO : 1) * SUB_ACT;  // 64 bf16 channels per row
-    static constexpr int W_TAP_BYTES = BN * 128;
+    static constexpr int W_TAP_BYTES = (DWM ? 64 : BN) * 128;
     static constexpr int W_BYTES = (HALO ? 3 * HALO : 1) * W_TAP_BYTES;
     static constexpr int STAGE = ACT_BYTES + W_BYTES;
     static constexpr int STAGES = (200 * 1024 / STAGE) > 8 ? 8 : (200 * 1024 / STAGE);
@@ -216,9 +220,15 @@ __device__ __forceinline__ long long unit_tile(const TcGeo& g, long long lu, uin
 // the same weight tile; each CTA loads half of every weight box and multicasts
 // it to both, and each stage is released only when both CTAs' MMAs have read
 // it (the empty barrier counts one commit from each CTA).
-template <int BN, bool SWAP, int MAXP, int CL, int HALO>
+// DWM (narrow heads of at most 16 channels, swapped halo form): the three dw
+// taps are MMA rows (row dw * 16 + co, 48 of 64), so a K block is (dt, 64
+// channels) with the three dh taps inside and an input box 32 columns wide
+// serves 30 output columns; the epilogue adds the dw rows with their column
+// shift: out[co][x] = D[co][x] + D[16 + co][x + 1] + D[32 + co][x + 2].
+template <int BN, bool SWAP, int MAXP, int CL, int HALO, bool DWM = false>
 __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__ TcBatch<MAXP> B) {
-    using C = Cfg<BN, SWAP, HALO>;
+    using C = Cfg<BN, SWAP, HALO, DWM>;
+    static_assert(!DWM || (SWAP && HALO == 1), "dw rows: swapped halo form");
     static_assert(CL == 1 || CL == 2, "CTA pairs at most");
     static_assert(!HALO || CL == 1, "halo boxes with single CTAs");
     constexpr uint32_t HALF_W = C::W_BYTES / 2;  // one CTA's share of a weight box
@@ -320,9 +330,9 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                     // and HALO channel blocks inside
                     const int cpg = HALO ? g.cpt / HALO : g.cpt;
                     const int tap = kb / cpg, cb = kb - tap * cpg;
-                    const int dw = HALO ? tap % 3 : tap % a.kw;
+                    const int dw = DWM ? 0 : (HALO ? tap % 3 : tap % a.kw);
                     const int dh = HALO ? 0 : (tap / a.kw) % a.kh;
-                    const int dt = HALO ? tap / 3 : tap / (a.kw * a.kh);
+                    const int dt = DWM ? tap : (HALO ? tap / 3 : tap / (a.kw * a.kh));
                     const int ti = tc.to * a.st + dt + a.t_off;
                     const CUtensorMap* src = &B.tm_x[p];
                     int tcoord;
@@ -348,12 +358,14 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
 #pragma unroll
                         for (int c = 0; c < HALO; ++c) {
                             const int ci = (cb * HALO + c) * 64;
-                            tma_load_4d(sa + c * C::SUB_ACT, src, &full[s], ci, tc.tw * g.BW + dw - 1,
-                                        tc.th * g.BH - 1, tcoord);
+                            // DWM: columns tw*bwo - 1 .. tw*bwo + bwo of the input (all three dw)
+                            tma_load_4d(sa + c * C::SUB_ACT, src, &full[s], ci,
+                                        DWM ? tc.tw * g.bwo - 1 : tc.tw * g.BW + dw - 1, tc.th * g.BH - 1, tcoord);
 #pragma unroll
                             for (int d = 0; d < 3; ++d)
                                 tma_load_2d(sb + (c * 3 + d) * C::W_TAP_BYTES, wmap, &full[s],
-                                            ((dt * 3 + d) * 3 + dw) * a.Cin + ci, tc.nt * BN);
+                                            DWM ? (dt * 3 + d) * a.Cin + ci : ((dt * 3 + d) * 3 + dw) * a.Cin + ci,
+                                            tc.nt * BN);
                         }
                         last_ph[s] = (int)ph;
                         if (++s == C::STAGES) {
@@ -426,7 +438,7 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                     const uint32_t s_act = smem_u32(smem + s * C::STAGE);
                     const uint32_t s_w = s_act + C::ACT_BYTES;
                     if constexpr (HALO > 0) {
-                        const uint32_t idesc = (SWAP && B.w_rows <= 16) ? C::IDESC_M64 : C::IDESC;
+                        const uint32_t idesc = (DWM || (SWAP && B.w_rows <= 16)) ? C::IDESC_M64 : C::IDESC;
 #pragma unroll
                         for (int c = 0; c < HALO; ++c)
 #pragma unroll
@@ -495,6 +507,94 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                 float* stg = epi + q * 16 * C::EPI_STRIDE;
                 const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * C::ACC_COLS);
                 const int j = lane >> 1, half = lane & 1;  // read-back role: voxel j, 16 channels
+                if constexpr (DWM) {
+                    // An M = 64 accumulator keeps rows 16q .. 16q + 15 in lanes 0 .. 15 of
+                    // TMEM quarter q, so quarter dw (< 3) holds the rows of tap dw. One output
+                    // row (32 box columns) at a time is staged in shared memory; then each of
+                    // the 128 epilogue threads adds the dw rows for one channel co = t & 15 at
+                    // columns x = t / 16 + 8 i (FSQ: one voxel per four threads).
+                    float* buf = epi;  // [48 rows][33]
+                    const int t = q * 32 + lane;
+                    const int co = t & 15, xg = t >> 4;
+                    const int Hout = a.Hout, Wout = a.Wout, oT = a.oT, oH = a.oH, oW = a.oW, oC = a.oC;
+                    const int bwo = g.bwo, wo0 = tc.tw * bwo;
+                    const bool fsq = a.mode == OUT_FSQ, f32 = a.out_fp32 != 0;
+                    // this thread's channel: depth-to-space sub-position and stored channel
+                    int ch = co, cc = 0, bb = 0, rw = 1, rh = 1, ot = tc.to;
+                    if (a.mode == OUT_D2S) {
+                        const int sub = co / oC;
+                        ch = co - sub * oC;
+                        rw = a.rw;
+                        rh = a.rh;
+                        cc = sub % rw;
+                        bb = (sub / rw) % rh;
+                        ot = tc.to * a.rt + sub / (rw * rh) - a.drop_t;
+                    }
+                    const bool c_ok = co < a.Cout && ot >= 0 && ot < oT;
+                    const float bias_c = (a.bias && co < a.Cout) ? a.bias[co] : 0.f;
+                    const __nv_bfloat16* const resid = static_cast<const __nv_bfloat16*>(a.residual);
+                    void* const out = a.out;
+                    for (int y = 0; y < g.BH; ++y) {
+                        if (q < 3) {
+                            float v[16];
+#pragma unroll
+                            for (int h2 = 0; h2 < 2; ++h2) {
+                                tmem_ld16(tbase + (uint32_t)(y * 32 + h2 * 16), v);
+                                if (lane < 16) {
+#pragma unroll
+                                    for (int i2 = 0; i2 < 16; ++i2) buf[(q * 16 + lane) * 33 + h2 * 16 + i2] = v[i2];
+                                }
+                            }
+                        }
+                        asm volatile("bar.sync 1, 128;" ::: "memory");
+                        const int ho = tc.th * g.BH + y;
+                        if (ho < Hout) {
+                            if (fsq) {
+                                const int x = t >> 2;
+                                if ((t & 3) == 0 && x < bwo && wo0 + x < Wout) {
+                                    const long long vox =
+                                        (((long long)tc.n * a.Tout + tc.to) * Hout + ho) * Wout + wo0 + x;
+                                    float* z = static_cast<float*>(out) + vox * a.fsq.nlev;
+                                    int idx = 0;
+#pragma unroll
+                                    for (int c = 0; c < 8; ++c) {
+                                        if (c < a.fsq.nlev) {
+                                            const float zz = buf[c * 33 + x] + buf[(16 + c) * 33 + x + 1] +
+                                                             buf[(32 + c) * 33 + x + 2] + (a.bias ? a.bias[c] : 0.f);
+                                            z[c] = zz;
+                                            const float bq =
+                                                tanhf(zz + a.fsq.shift[c]) * a.fsq.half_l[c] - a.fsq.offset[c];
+                                            idx += ((int)rintf(bq) + a.fsq.half_w[c]) * a.fsq.basis[c];
+                                        }
+                                    }
+                                    if (a.idx) a.idx[vox] = idx;
+                                }
+                            } else if (c_ok) {
+                                const int oh = ho * rh + bb;
+                                if (oh < oH) {
+                                    const long long rowoff = (((long long)tc.n * oT + ot) * oH + oh) * oW;
+                                    for (int x = xg; x < bwo; x += 8) {
+                                        const int wo = wo0 + x, ow = wo * rw + cc;
+                                        if (wo >= Wout || ow >= oW) break;
+                                        float o = buf[co * 33 + x] + buf[(16 + co) * 33 + x + 1] +
+                                                  buf[(32 + co) * 33 + x + 2] + bias_c;
+                                        const long long off = (rowoff + ow) * oC + ch;
+                                        if (resid) o += __bfloat162float(resid[off]);
+                                        if (f32)
+                                            static_cast<float*>(out)[off] = o;
+                                        else
+                                            static_cast<__nv_bfloat16*>(out)[off] = __float2bfloat16_rn(o);
+                                    }
+                                }
+                            }
+                        }
+                        asm volatile("bar.sync 1, 128;" ::: "memory");
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&tempty[acc]);
+                    continue;
+                }
                 if (a.Cout <= 32) {
                     // narrow layer (pixel head, latent head): only TMEM lanes 0..Cout-1 hold
                     // channels, all in the warp of quarter 0; the others have nothing to store
@@ -806,18 +906,20 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
     if constexpr (CL > 1) cluster_sync();  // neither CTA leaves while its peer may still address it
 }
 
-template <int BN, bool SWAP, int MAXP, int CL, int HALO = 0>
+template <int BN, bool SWAP, int MAXP, int CL, int HALO = 0, bool DWM = false>
 int launch_bn(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int cta_tiles, cudaStream_t stream) {
-    using C = Cfg<BN, SWAP, HALO>;
-    auto kern = conv_tc_kernel<BN, SWAP, MAXP, CL, HALO>;
+    using C = Cfg<BN, SWAP, HALO, DWM>;
+    auto kern = conv_tc_kernel<BN, SWAP, MAXP, CL, HALO, DWM>;
     TcBatch<MAXP> B;
     memset(&B, 0, sizeof(B));
     // with CTA pairs each CTA loads half of the weight box (BN / 2 rows); a narrow halo
     // layer loads its real rows only
-    B.w_rows = (HALO > 0 && SWAP && as[0].Cout <= 32) ? (as[0].Cout + 15) / 16 * 16 : BN / CL;
-    if (!encode_w_map(&B.tm_w, as[0].w, as[0].Cout_pad, as[0].Kpad, B.w_rows)) return -1;
+    // (DWM: 48 weight rows dw * 16 + co, K = (dt, dh, ci))
+    B.w_rows = DWM ? 48 : (HALO > 0 && SWAP && as[0].Cout <= 32) ? (as[0].Cout + 15) / 16 * 16 : BN / CL;
+    const int wk = DWM ? 9 * as[0].Cin : as[0].Kpad;
+    if (!encode_w_map(&B.tm_w, as[0].w, as[0].Cout_pad, wk, B.w_rows)) return -1;
     if (as[0].w0) {
-        if (!encode_w_map(&B.tm_w0, as[0].w0, as[0].Cout_pad, as[0].Kpad, B.w_rows)) return -1;
+        if (!encode_w_map(&B.tm_w0, as[0].w0, as[0].Cout_pad, wk, B.w_rows)) return -1;
     } else {
         B.tm_w0 = B.tm_w;
     }
@@ -894,10 +996,10 @@ int launch_bn(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int c
 
 // CTA pairs for layers with at least one wave of tiles (weight halves of 64+
 // rows), single CTAs otherwise and whenever CTA lifetimes are bounded.
-template <int BN, bool SWAP, int NCB>  // NCB: 64-channel blocks per halo stage
+template <int BN, bool SWAP, int NCB, bool DWM = false>  // NCB: 64-channel blocks per halo stage
 int launch_bn_halo(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int cta_tiles, cudaStream_t stream) {
-    return count == 1 ? launch_bn<BN, SWAP, 1, 1, NCB>(as, gs, 1, num_sms, cta_tiles, stream)
-                      : launch_bn<BN, SWAP, kMaxConvGroup, 1, NCB>(as, gs, count, num_sms, cta_tiles, stream);
+    return count == 1 ? launch_bn<BN, SWAP, 1, 1, NCB, DWM>(as, gs, 1, num_sms, cta_tiles, stream)
+                      : launch_bn<BN, SWAP, kMaxConvGroup, 1, NCB, DWM>(as, gs, count, num_sms, cta_tiles, stream);
 }
 
 template <int BN, bool SWAP>
@@ -1041,6 +1143,8 @@ ConvRoute conv_route(const ConvArgs& a0) {
     return r;
 }
 
+bool conv_tc_dwm(int Cout, int k, int sh, int sw) { return Cout <= 16 && k == 3 && sh == 1 && sw == 1; }
+
 // GroupNorm statistics come from the swapped wide epilogue (plain or
 // depth-to-space, bf16), for groups of 4, 8 or 16 channels, of 3x3x3 layers:
 // a layer with a short K loop (1x1x1, the stem over its im2col matrix) is
@@ -1087,25 +1191,35 @@ int launch_conv_tc_group(const ConvArgs* as, int count, int num_sms, cudaStream_
     // or a narrow layer (at most 32 channels, weights padded to 128 rows)
     const ConvRoute rt = conv_route(a0);
     const bool swap = rt.swap, halo = rt.halo;
+    const bool dwm = a0.w_dwm != 0;
+    // weights packed in the dw-rows layout only run in that form
+    if (dwm && !(halo && a0.kt == 3 && conv_tc_dwm(a0.Cout, a0.kh, a0.sh, a0.sw) && !a0.w0 && a0.Cin % 64 == 0))
+        return -1;
     for (int p = 0; p < count; ++p)
         if (as[p].gn_part && (!conv_tc_gn_fusable(as[p]) || as[p].gn_cg != a0.gn_cg)) return -1;
     TcGeo gs[kMaxConvGroup];
     for (int p = 0; p < count; ++p) {
         TcGeo& g = gs[p];
         const ConvArgs& a = as[p];
-        if (halo)
+        if (dwm) {
+            g.BH = DWM_BH;
+            g.BW = DWM_BW;  // box columns; DWM_BW - 2 output columns per tile
+        } else if (halo) {
             choose_tile_halo(a.Hout, a.Wout, swap ? 256 : 128, &g.BH, &g.BW);
-        else
+        } else {
             choose_tile(a.Hout, a.Wout, swap ? 256 : 128, &g.BH, &g.BW);
-        g.tiles_w = (a.Wout + g.BW - 1) / g.BW;
+        }
+        g.bwo = dwm ? g.BW - 2 : g.BW;
+        g.tiles_w = (a.Wout + g.bwo - 1) / g.bwo;
         g.tiles_h = (a.Hout + g.BH - 1) / g.BH;
         g.cpt = a.Cin / 64;
-        g.nkb = halo ? a.kt * a.kw * g.cpt : a.kt * a.kh * a.kw * g.cpt;
+        g.nkb = dwm ? a.kt * g.cpt : halo ? a.kt * a.kw * g.cpt : a.kt * a.kh * a.kw * g.cpt;
         g.strided = (a.sh == 2) ? 1 : 0;
         g.halo = halo ? 1 : 0;
         g.n_tiles = 0;
         g.num_tiles = 0;
     }
+    if (dwm) return launch_bn_halo<128, true, 1, true>(as, gs, count, num_sms, cta_tiles, stream);
     if (halo) return launch_bn_halo<128, true, 1>(as, gs, count, num_sms, cta_tiles, stream);
     if (swap) return launch_bn_any<128, true>(as, gs, count, num_sms, cta_tiles, pairs, stream);
     switch (conv_tc_bn(a0.Cout_pad)) {

@@ -669,7 +669,7 @@ int tok_set_params_device(tok_ctx* c, const float* d_flat, void* stream) {
     for (const auto& cw : c->convs)
         if (cw.name != "enc.stem" && cw.name != "stage.c0" && !cw.wt) adj = false;
     for (auto& cw : c->convs) {
-        const bool fused = adj && cw.k == 3 && !cw.im2col && cw.wt && cw.wf0;
+        const bool fused = adj && cw.k == 3 && !cw.im2col && cw.wt && cw.wf0 && !cw.dwm;
         if (fused) {
             cw.b = c->d_master + cw.ob;
             if (launch_pack3(c->d_master + cw.ow, cw.Cout, cw.Cin, cw.Cout_pad, cw.Kpad, cw.rows_pad, cw.cpad,

@@ -2,8 +2,9 @@
 
 Tolerances (stated here, derived in the design doc):
   * conv, FP32 path: the oracle gets the same fp32 inputs; FP32 accumulation
-    of K terms plus one fp32 rounding: |gpu - ref| <= 1e-5 |ref| + 2e-6 * s,
-    s = max |ref|.
+    of K terms plus one fp32 rounding: |gpu - ref| <= 1e-5 |ref| + 2e-6 * s * r,
+    s = max |ref|, r = max(1, sqrt(K / 3456)) (rounding errors of a long sum
+    grow as sqrt(K); the constant was set for K = 27 * 128).
   * conv, BF16 path: the oracle gets the bf16-rounded inputs and weights, so
     products are exact; FP32 accumulation plus one bf16 output rounding:
     |gpu - ref| <= 2^-8 |ref| + 2e-4 * s.
@@ -53,6 +54,12 @@ CONV_CASES = [
     (1, 3, 9, 40, 128, 12, 3, (1, 1, 1), 0),            # narrow head, 16 weight rows
     (1, 3, 11, 37, 64, 24, 3, (1, 1, 1), 1),            # narrow head, 32 weight rows
     (1, 3, 7, 9, 128, 6, 1, (1, 1, 1), 0),              # narrow 1x1x1 (swapped form)
+    # 3x3x3 heads of at most 16 channels: the three dw taps as MMA rows, 30 output
+    # columns per 32-column input box (ragged last tile, frames narrower than a box)
+    (1, 3, 9, 61, 64, 3, 3, (1, 1, 1), 1),              # tiles of 30 + 30 + 1 columns
+    (2, 4, 17, 30, 192, 1, 3, (1, 1, 1), 0),            # one output channel, W = 30
+    (1, 2, 8, 31, 512, 6, 3, (1, 1, 1), 0),             # latent-head width, W = 31
+    (1, 3, 3, 5, 64, 16, 3, (1, 1, 1), 1),              # frame smaller than one box
 ]
 
 
@@ -80,7 +87,7 @@ def test_conv3d_parity(P, prec, case):
         g = got.float().cpu().numpy().astype(np.float64)
         s = np.abs(want).max()
         if prec == "fp32":
-            tol = 1e-5 * np.abs(want) + 2e-6 * s
+            tol = 1e-5 * np.abs(want) + 2e-6 * s * max(1.0, np.sqrt(k ** 3 * Cin / 3456))
         else:
             tol = 2.0 ** -8 * np.abs(want) + 2e-4 * s
         err = np.abs(g - want)
