@@ -207,7 +207,7 @@ __device__ __forceinline__ void unpack(const typename Raw<T>::type& q, float (&v
         v[3] = q.w;
     }
 }
-constexpr int GN_PREFETCH = 4;  // vectors of x and dy in flight per thread
+constexpr int GN_BWD_PF = 2, GN_BWD_MINB = 3;  // GN backward: loads ahead per thread, blocks per SM
 
 template <typename T>
 __device__ __forceinline__ void stv(T* p, const float (&v)[V8<T>::N]) {
@@ -229,70 +229,92 @@ __device__ __forceinline__ void stv(T* p, const float (&v)[V8<T>::N]) {
 //   dx   = rstd * (g - mean_group(g) - xhat * mean_group(g * xhat))
 //   dgamma = sum dh * xhat,  dbeta = sum dh   (over frames and voxels)
 //
-// Pass 1 (per frame and chunk): per group (sum g, sum g*xhat) and per channel
-// (sum dh*xhat, sum dh), combined over the block in a fixed tree order.
+// The group means need a whole frame, so dx takes two sweeps of x and dy: a
+// reduction per (frame, chunk), the group means per frame, then dx per
+// (frame, chunk). (One cooperative launch over L2-sized batches of frames, which
+// reads x and dy from HBM once, measured slower: with one chunk per block and
+// phase, each sweep is a chain of dependent loads.)
+//
+// sigmoid: BF16 path 1/2 + tanh(h/2)/2 (one tanh.approx; its error is below
+// the bf16 rounding of dx), FP32 path 1 / (1 + exp(-h)).
 template <typename T>
-__global__ void __launch_bounds__(NT) gn_bwd_reduce_kernel(const T* __restrict__ x, const T* __restrict__ dy,
-                                                           const float2* __restrict__ stats,
-                                                           const float* __restrict__ gamma,
-                                                           const float* __restrict__ beta, long long vpf, int C,
-                                                           int G, int S, int vpt, float2* __restrict__ pg,
-                                                           float2* __restrict__ pc) {
+__device__ __forceinline__ float gn_bwd_sigmoid(float h) {
+    if constexpr (sizeof(T) == 2)
+        return fmaf(0.5f, tanh_approx(0.5f * h), 0.5f);
+    else
+        return 1.f / (1.f + expf(-h));
+}
+
+template <typename T>
+struct GnBwdArgs {
+    const T* x;
+    const T* dy;
+    const float2* stats;  // (mean, rstd) per (frame, group), from the forward
+    const float* gamma;   // null: 1
+    const float* beta;    // null: 0
+    const T* add;         // null, or a gradient added to dx
+    T* dx;
+    long long frames, vpf;  // vectors of V channels per frame
+    int C, G, S, vpt;       // S chunks of NT * vpt vectors per frame
+    float2* pg;             // [frames][S][G]: (sum g, sum g * xhat) per chunk
+    float2* pc;             // [frames][S][C]: (sum dh * xhat, sum dh) per chunk
+    float2* gstat;          // [frames][G]: (mean g, mean g * xhat)
+};
+
+// Reduction of one (frame, chunk): per channel (sum dh*xhat, sum dh) combined
+// over the block in a fixed tree order; the group sums follow as gamma-weighted
+// channel sums (sum g = sum_c gamma_c sum dh, sum g*xhat = sum_c gamma_c sum dh*xhat).
+template <typename T, int PF>
+__device__ __forceinline__ void gn_bwd_reduce_unit(const GnBwdArgs<T>& a, long long frame, int chunk,
+                                                   float2 (&redc)[V8<T>::N][NT]) {
     constexpr int V = V8<T>::N;
-    // [channel slot][thread]: consecutive threads hit consecutive banks
-    __shared__ float2 redc[V][NT];
-    __shared__ float2 redg[V][NT];
-    const int frame = blockIdx.y, chunk = blockIdx.x, tid = threadIdx.x;
-    const int vpv = C / V, cg = C / G;
+    const int tid = threadIdx.x;
+    const int vpv = a.C / V, cg = a.C / a.G;
     const int c0 = (tid % vpv) * V;
-    float mu[V], rs[V], ga[V], be[V];
+    // xhat = x * rs + xb, h = x * hs + hb (per channel)
+    float rs[V], xb[V], hs[V], hb[V];
 #pragma unroll
     for (int j = 0; j < V; ++j) {
-        const float2 st = stats[(long long)frame * G + (c0 + j) / cg];
-        mu[j] = st.x;
+        const float2 st = a.stats[frame * a.G + (c0 + j) / cg];
+        const float ga = a.gamma ? a.gamma[c0 + j] : 1.f, be = a.beta ? a.beta[c0 + j] : 0.f;
         rs[j] = st.y;
-        ga[j] = gamma ? gamma[c0 + j] : 1.f;
-        be[j] = beta ? beta[c0 + j] : 0.f;
+        xb[j] = -st.x * st.y;
+        hs[j] = st.y * ga;
+        hb[j] = fmaf(xb[j], ga, be);
     }
-    float sdx[V] = {}, sd[V] = {}, sg[V] = {}, sgx[V] = {};
-    const long long base = (long long)frame * vpf * V;
-    const long long v0 = (long long)chunk * NT * vpt;
-    for (int i0 = 0; i0 < vpt; i0 += GN_PREFETCH) {
-        typename Raw<T>::type rx[GN_PREFETCH], rg[GN_PREFETCH];
+    float sdx[V] = {}, sd[V] = {};
+    const long long base = frame * a.vpf * V;
+    const long long v0 = (long long)chunk * NT * a.vpt;
+    for (int i0 = 0; i0 < a.vpt; i0 += PF) {
+        typename Raw<T>::type rx[PF], rg[PF];
 #pragma unroll
-        for (int u = 0; u < GN_PREFETCH; ++u) {
+        for (int u = 0; u < PF; ++u) {
             const long long vi = v0 + (long long)(i0 + u) * NT + tid;
-            if (i0 + u < vpt && vi < vpf) {
-                rx[u] = ldraw(x + base + vi * V);
-                rg[u] = ldraw(dy + base + vi * V);
+            if (i0 + u < a.vpt && vi < a.vpf) {
+                rx[u] = ldraw(a.x + base + vi * V);
+                rg[u] = ldraw(a.dy + base + vi * V);
             }
         }
 #pragma unroll
-        for (int u = 0; u < GN_PREFETCH; ++u) {
-        const long long vi = v0 + (long long)(i0 + u) * NT + tid;
-        if (i0 + u >= vpt || vi >= vpf) break;
-        float xv[V], gv[V];
-        unpack<T>(rx[u], xv);
-        unpack<T>(rg[u], gv);
+        for (int u = 0; u < PF; ++u) {
+            const long long vi = v0 + (long long)(i0 + u) * NT + tid;
+            if (i0 + u >= a.vpt || vi >= a.vpf) break;
+            float xv[V], gv[V];
+            unpack<T>(rx[u], xv);
+            unpack<T>(rg[u], gv);
 #pragma unroll
-        for (int j = 0; j < V; ++j) {
-            const float xh = (xv[j] - mu[j]) * rs[j];
-            const float h = xh * ga[j] + be[j];
-            const float sg1 = sizeof(T) == 2 ? __fdividef(1.f, 1.f + __expf(-h)) : 1.f / (1.f + expf(-h));
-            const float dh = gv[j] * sg1 * (1.f + h * (1.f - sg1));
-            sdx[j] += dh * xh;
-            sd[j] += dh;
-            const float g = dh * ga[j];
-            sg[j] += g;
-            sgx[j] += g * xh;
-        }
+            for (int j = 0; j < V; ++j) {
+                const float xh = fmaf(xv[j], rs[j], xb[j]);
+                const float h = fmaf(xv[j], hs[j], hb[j]);
+                const float sg1 = gn_bwd_sigmoid<T>(h);
+                const float dh = gv[j] * sg1 * fmaf(h, 1.f - sg1, 1.f);
+                sdx[j] = fmaf(dh, xh, sdx[j]);
+                sd[j] += dh;
+            }
         }
     }
 #pragma unroll
-    for (int j = 0; j < V; ++j) {
-        redc[j][tid] = make_float2(sdx[j], sd[j]);
-        redg[j][tid] = make_float2(sg[j], sgx[j]);
-    }
+    for (int j = 0; j < V; ++j) redc[j][tid] = make_float2(sdx[j], sd[j]);
     __syncthreads();
     for (int stride = NT / 2; stride >= vpv; stride >>= 1) {
         if (tid < stride) {
@@ -300,25 +322,91 @@ __global__ void __launch_bounds__(NT) gn_bwd_reduce_kernel(const T* __restrict__
             for (int j = 0; j < V; ++j) {
                 redc[j][tid].x += redc[j][tid + stride].x;
                 redc[j][tid].y += redc[j][tid + stride].y;
-                redg[j][tid].x += redg[j][tid + stride].x;
-                redg[j][tid].y += redg[j][tid + stride].y;
             }
         }
         __syncthreads();
     }
-    for (int c = tid; c < C; c += NT) pc[((long long)frame * S + chunk) * C + c] = redc[c % V][c / V];
-    for (int g = tid; g < G; g += NT) {
+    const long long row = frame * a.S + chunk;
+    for (int c = tid; c < a.C; c += NT) a.pc[row * a.C + c] = redc[c % V][c / V];
+    for (int g = tid; g < a.G; g += NT) {
         float2 acc = make_float2(0.f, 0.f);
         for (int c = g * cg; c < (g + 1) * cg; ++c) {
-            acc.x += redg[c % V][c / V].x;
-            acc.y += redg[c % V][c / V].y;
+            const float2 r = redc[c % V][c / V];
+            const float gc = a.gamma ? a.gamma[c] : 1.f;
+            acc.x = fmaf(gc, r.y, acc.x);
+            acc.y = fmaf(gc, r.x, acc.y);
         }
-        pg[((long long)frame * S + chunk) * G + g] = acc;
+        a.pg[row * a.G + g] = acc;
     }
 }
 
-// Pass 2a: per (frame, group) the chunk sums, one warp each (lanes take
-// chunks lane, lane + 32, ...; a fixed shuffle tree combines them).
+// dx (+ add) of one (frame, chunk), given the frame's group means gst[g] =
+// (mean g, mean g * xhat); 16-byte vectors.
+template <typename T, int PF>
+__device__ __forceinline__ void gn_bwd_apply_unit(const GnBwdArgs<T>& a, long long frame, int chunk,
+                                                  const float2* gst) {
+    constexpr int V = V8<T>::N;
+    const int tid = threadIdx.x;
+    const int vpv = a.C / V, cg = a.C / a.G;
+    const int c0 = (tid % vpv) * V;
+    // h = x * hs + hb; dx = rstd * (dh * gamma - m1 - xhat * m2) = ka * dh + (k0 + k1 * x)
+    // with xhat = (x - mean) * rstd
+    float hs[V], hb[V], ka[V], k0[V], k1[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+        const int g = (c0 + j) / cg;
+        const float2 st = a.stats[frame * a.G + g];
+        const float2 gs = gst[g];
+        const float ga = a.gamma ? a.gamma[c0 + j] : 1.f, be = a.beta ? a.beta[c0 + j] : 0.f;
+        const float mu = st.x, rs = st.y;
+        hs[j] = rs * ga;
+        hb[j] = fmaf(-mu * rs, ga, be);
+        ka[j] = rs * ga;
+        k1[j] = -rs * rs * gs.y;
+        k0[j] = fmaf(rs * rs * gs.y, mu, -rs * gs.x);
+    }
+    const long long base = frame * a.vpf * V;
+    const long long v0 = (long long)chunk * NT * a.vpt;
+    for (int i0 = 0; i0 < a.vpt; i0 += PF) {
+        typename Raw<T>::type rx[PF], rg[PF];
+#pragma unroll
+        for (int u = 0; u < PF; ++u) {
+            const long long vi = v0 + (long long)(i0 + u) * NT + tid;
+            if (i0 + u < a.vpt && vi < a.vpf) {
+                rx[u] = ldraw(a.x + base + vi * V);
+                rg[u] = ldraw(a.dy + base + vi * V);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < PF; ++u) {
+            const long long vi = v0 + (long long)(i0 + u) * NT + tid;
+            if (i0 + u >= a.vpt || vi >= a.vpf) break;
+            const long long o = base + vi * V;
+            float xv[V], gv[V], av[V], r[V];
+            unpack<T>(rx[u], xv);
+            unpack<T>(rg[u], gv);
+            if (a.add) ldv(a.add + o, av);
+#pragma unroll
+            for (int j = 0; j < V; ++j) {
+                const float h = fmaf(xv[j], hs[j], hb[j]);
+                const float sg1 = gn_bwd_sigmoid<T>(h);
+                const float dh = gv[j] * sg1 * fmaf(h, 1.f - sg1, 1.f);
+                r[j] = fmaf(ka[j], dh, fmaf(k1[j], xv[j], k0[j]));
+                if (a.add) r[j] += av[j];
+            }
+            stv(a.dx + o, r);
+        }
+    }
+}
+
+template <typename T, int PF, int MINB>
+__global__ void __launch_bounds__(NT, MINB) gn_bwd_reduce_kernel(const __grid_constant__ GnBwdArgs<T> a) {
+    __shared__ float2 redc[V8<T>::N][NT];  // [channel slot][thread]: consecutive threads, consecutive banks
+    gn_bwd_reduce_unit<T, PF>(a, blockIdx.y, blockIdx.x, redc);
+}
+
+// Per (frame, group) the chunk sums, one warp each (lanes take chunks lane,
+// lane + 32, ...; a fixed shuffle tree combines them).
 __global__ void gn_bwd_finalize_kernel(const float2* __restrict__ pg, long long frames, int S, int G, float inv_n,
                                        float2* __restrict__ gstat) {
     const long long wid = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
@@ -326,23 +414,28 @@ __global__ void gn_bwd_finalize_kernel(const float2* __restrict__ pg, long long 
     if (wid >= frames * G) return;
     const long long frame = wid / G;
     const int g = (int)(wid % G);
-    float a = 0.f, b = 0.f;
+    float s0 = 0.f, s1 = 0.f;
     for (int c = lane; c < S; c += 32) {
         const float2 v = pg[(frame * S + c) * G + g];
-        a += v.x;
-        b += v.y;
+        s0 += v.x;
+        s1 += v.y;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_down_sync(0xffffffffu, a, o);
-        b += __shfl_down_sync(0xffffffffu, b, o);
+        s0 += __shfl_down_sync(0xffffffffu, s0, o);
+        s1 += __shfl_down_sync(0xffffffffu, s1, o);
     }
-    if (lane == 0) gstat[wid] = make_float2(a * inv_n, b * inv_n);
+    if (lane == 0) gstat[wid] = make_float2(s0 * inv_n, s1 * inv_n);
 }
 
-// Pass 2b: per channel over all (frame, chunk) rows, in two steps: blocks of
-// 32 channels x 8 row lanes sum a band of rows into q[band][C], then one warp
-// per channel sums the bands.
+template <typename T, int PF, int MINB>
+__global__ void __launch_bounds__(NT, MINB) gn_bwd_apply_kernel(const __grid_constant__ GnBwdArgs<T> a) {
+    gn_bwd_apply_unit<T, PF>(a, blockIdx.y, blockIdx.x, a.gstat + (long long)blockIdx.y * a.G);
+}
+
+// Per channel over all (frame, chunk) rows, in two steps: blocks of 32 channels
+// x 8 row lanes sum a band of rows into q[band][C], then one warp per channel
+// sums the bands.
 constexpr int GN_BANDS = 128;
 
 __global__ void __launch_bounds__(256) gn_bwd_channel_kernel(const float2* __restrict__ pc, long long rows, int C,
@@ -387,66 +480,6 @@ __global__ void gn_bwd_channel_final_kernel(const float2* __restrict__ q, int C,
     if (lane == 0) {
         if (dgamma) dgamma[c] = a;
         if (dbeta) dbeta[c] = b;
-    }
-}
-
-// Pass 3: dx (+ add), 16-byte vectors.
-template <typename T>
-__global__ void __launch_bounds__(NT) gn_bwd_apply_kernel(const T* __restrict__ x, const T* __restrict__ dy,
-                                                          const float2* __restrict__ stats,
-                                                          const float2* __restrict__ gstat,
-                                                          const float* __restrict__ gamma,
-                                                          const float* __restrict__ beta, const T* __restrict__ add,
-                                                          long long vpf, int C, int G, int vpt, T* __restrict__ dx) {
-    constexpr int V = V8<T>::N;
-    const int frame = blockIdx.y, chunk = blockIdx.x, tid = threadIdx.x;
-    const int vpv = C / V, cg = C / G;
-    const int c0 = (tid % vpv) * V;
-    float mu[V], rs[V], ga[V], be[V], m1[V], m2[V];
-#pragma unroll
-    for (int j = 0; j < V; ++j) {
-        const int g = (c0 + j) / cg;
-        const float2 st = stats[(long long)frame * G + g];
-        const float2 gs = gstat[(long long)frame * G + g];
-        mu[j] = st.x;
-        rs[j] = st.y;
-        m1[j] = gs.x;
-        m2[j] = gs.y;
-        ga[j] = gamma ? gamma[c0 + j] : 1.f;
-        be[j] = beta ? beta[c0 + j] : 0.f;
-    }
-    const long long base = (long long)frame * vpf * V;
-    const long long v0 = (long long)chunk * NT * vpt;
-    for (int i0 = 0; i0 < vpt; i0 += GN_PREFETCH) {
-        typename Raw<T>::type rx[GN_PREFETCH], rg[GN_PREFETCH];
-#pragma unroll
-        for (int u = 0; u < GN_PREFETCH; ++u) {
-            const long long vi = v0 + (long long)(i0 + u) * NT + tid;
-            if (i0 + u < vpt && vi < vpf) {
-                rx[u] = ldraw(x + base + vi * V);
-                rg[u] = ldraw(dy + base + vi * V);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < GN_PREFETCH; ++u) {
-        const long long vi = v0 + (long long)(i0 + u) * NT + tid;
-        if (i0 + u >= vpt || vi >= vpf) break;
-        const long long o = base + vi * V;
-        float xv[V], gv[V], av[V], r[V];
-        unpack<T>(rx[u], xv);
-        unpack<T>(rg[u], gv);
-        if (add) ldv(add + o, av);
-#pragma unroll
-        for (int j = 0; j < V; ++j) {
-            const float xh = (xv[j] - mu[j]) * rs[j];
-            const float h = xh * ga[j] + be[j];
-            const float sg1 = sizeof(T) == 2 ? __fdividef(1.f, 1.f + __expf(-h)) : 1.f / (1.f + expf(-h));
-            const float g = gv[j] * sg1 * (1.f + h * (1.f - sg1)) * ga[j];
-            r[j] = rs[j] * (g - m1[j] - xh * m2[j]);
-            if (add) r[j] += av[j];
-        }
-        stv(dx + o, r);
-        }
     }
 }
 
@@ -774,18 +807,33 @@ int launch_gn_silu_bwd(const T* x, const T* dy, const float2* stats, const float
                        const T* add, long long frames, long long HW, int C, int G, int vpt, int S, void* scratch,
                        float* dgamma, float* dbeta, T* dx, cudaStream_t s) {
     constexpr int V = V8<T>::N;
-    const long long vpf = HW * C / V;
-    float2* pg = static_cast<float2*>(scratch);
-    float2* pc = pg + frames * S * G;
-    float2* gstat = pc + frames * S * C;
-    float2* q = gstat + frames * G;
-    dim3 grid(S, (unsigned)frames);
-    gn_bwd_reduce_kernel<T><<<grid, NT, 0, s>>>(x, dy, stats, gamma, beta, vpf, C, G, S, vpt, pg, pc);
-    gn_bwd_finalize_kernel<<<blocks_for(frames * G * 32, 256), 256, 0, s>>>(pg, frames, S, G,
-                                                                           1.f / (float)(HW * (C / G)), gstat);
-    gn_bwd_channel_kernel<<<dim3((C + 31) / 32, GN_BANDS), 256, 0, s>>>(pc, frames * S, C, q);
+    const int vpv = C / V;
+    if (C % V || C % G || vpv > NT || (vpv & (vpv - 1))) return (int)cudaErrorInvalidValue;
+    GnBwdArgs<T> a;
+    a.x = x;
+    a.dy = dy;
+    a.stats = stats;
+    a.gamma = gamma;
+    a.beta = beta;
+    a.add = add;
+    a.dx = dx;
+    a.frames = frames;
+    a.vpf = HW * C / V;
+    a.C = C;
+    a.G = G;
+    a.S = S;
+    a.vpt = vpt;
+    a.pg = static_cast<float2*>(scratch);
+    a.pc = a.pg + frames * S * G;
+    a.gstat = a.pc + frames * S * C;
+    float2* q = a.gstat + frames * G;
+    const dim3 grid(S, (unsigned)frames);
+    gn_bwd_reduce_kernel<T, GN_BWD_PF, GN_BWD_MINB><<<grid, NT, 0, s>>>(a);
+    gn_bwd_finalize_kernel<<<blocks_for(frames * G * 32, 256), 256, 0, s>>>(a.pg, frames, S, G,
+                                                                           1.f / (float)(HW * (C / G)), a.gstat);
+    gn_bwd_channel_kernel<<<dim3((C + 31) / 32, GN_BANDS), 256, 0, s>>>(a.pc, frames * S, C, q);
     gn_bwd_channel_final_kernel<<<blocks_for((long long)C * 32, 256), 256, 0, s>>>(q, C, dgamma, dbeta);
-    gn_bwd_apply_kernel<T><<<grid, NT, 0, s>>>(x, dy, stats, gstat, gamma, beta, add, vpf, C, G, vpt, dx);
+    gn_bwd_apply_kernel<T, GN_BWD_PF, GN_BWD_MINB><<<grid, NT, 0, s>>>(a);
     return (int)cudaGetLastError();
 }
 template int launch_gn_silu_bwd<float>(const float*, const float*, const float2*, const float*, const float*,
