@@ -48,6 +48,7 @@ struct TcGeo {
     long long m_tiles;       // voxel tiles
     int halo;                // K blocks are (dt, dw, channel block) groups of three dh taps
     int bwo;                 // output columns per tile: BW, or BW - 2 in the dw-rows form (DWM)
+    int nvox;                // swapped forms: voxels per tile = BH * BW = the MMA's N (16 | nvox, <= 256)
 };
 
 // A grouped launch: up to MAXP inputs of one layer (clips or stream chunks of
@@ -438,7 +439,8 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                     const uint32_t s_act = smem_u32(smem + s * C::STAGE);
                     const uint32_t s_w = s_act + C::ACT_BYTES;
                     if constexpr (HALO > 0) {
-                        const uint32_t idesc = (DWM || (SWAP && B.w_rows <= 16)) ? C::IDESC_M64 : C::IDESC;
+                        const uint32_t idesc =
+                            SWAP ? idesc_bf16_f32((DWM || B.w_rows <= 16) ? 64 : BN, gu.nvox) : C::IDESC;
 #pragma unroll
                         for (int c = 0; c < HALO; ++c)
 #pragma unroll
@@ -618,7 +620,7 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                         const bool t_ok = ot >= 0 && ot < oT;
                         const long long fbase = ((long long)tc.n * oT + ot) * oH;
 #pragma unroll 1
-                        for (int c16 = 0; c16 < C::ROWS / 16; ++c16) {
+                        for (int c16 = 0; c16 < g.nvox / 16; ++c16) {
                             float v[16];
                             tmem_ld16(tbase + (uint32_t)(c16 * 16), v);
                             const int vv0 = c16 * 16;
@@ -700,7 +702,7 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                 float gK[4] = {0.f, 0.f, 0.f, 0.f}, gs[4] = {0.f, 0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};
                 float gcnt = 0.f;
 #pragma unroll 1
-                for (int c16 = 0; c16 < C::ROWS / 16; ++c16) {
+                for (int c16 = 0; c16 < g.nvox / 16; ++c16) {
                     float v[16];
                     tmem_ld16(tbase + (uint32_t)(c16 * 16), v);
 #pragma unroll
@@ -1158,13 +1160,50 @@ bool conv_tc_gn_fusable(const ConvArgs& a) {
 
 // Statistics slots per output frame: the spatial tiles of the launch (times
 // the rh x rw sub-positions of a depth-to-space output).
+// Wide swapped halo layers may also take a tile of 192..240 voxels that fits
+// the frame better (e.g. 15 x 16 for a 90 x 160 frame, where 8 x 32 computes
+// 96 rows): per frame, tiles x (N + 48) (the 48 stands for a tile's fixed cost)
+// must drop by 3% or more against the best 256-voxel tile. The choice depends
+// on the frame size only, so a stream chunk and a whole clip tile alike.
+void choose_tile_halo_fit(int Hout, int Wout, int* BH, int* BW) {
+    choose_tile_halo(Hout, Wout, 256, BH, BW);
+    const auto cost = [&](int bh, int bw) {
+        return (long long)((Hout + bh - 1) / bh) * ((Wout + bw - 1) / bw) * (bh * bw + 48);
+    };
+    const long long base = cost(*BH, *BW);
+    long long best = base;
+    int bbh = *BH, bbw = *BW;
+    for (int bw : {16, 32, 64})
+        for (int bh = (192 + bw - 1) / bw; bh * bw < 256; ++bh) {
+            if ((bh * bw) % 16) continue;
+            const long long c = cost(bh, bw);
+            if (c < best) {
+                best = c;
+                bbh = bh;
+                bbw = bw;
+            }
+        }
+    if (best * 100 <= base * 97) {
+        *BH = bbh;
+        *BW = bbw;
+    }
+}
+
+// The output tile of a layer in its route (shared by the launch and the
+// GroupNorm statistics slot count).
+void conv_tc_tile(const ConvArgs& a, const ConvRoute& r, int* BH, int* BW) {
+    if (r.halo && !r.narrow)
+        choose_tile_halo_fit(a.Hout, a.Wout, BH, BW);
+    else if (r.halo)
+        choose_tile_halo(a.Hout, a.Wout, 256, BH, BW);
+    else
+        choose_tile(a.Hout, a.Wout, r.swap ? 256 : 128, BH, BW);
+}
+
 int conv_tc_gn_slots(const ConvArgs& a) {
     const ConvRoute r = conv_route(a);
     int BH = 1, BW = 1;
-    if (r.halo)
-        choose_tile_halo(a.Hout, a.Wout, r.swap ? 256 : 128, &BH, &BW);
-    else
-        choose_tile(a.Hout, a.Wout, r.swap ? 256 : 128, &BH, &BW);
+    conv_tc_tile(a, r, &BH, &BW);
     const int tiles = ((a.Hout + BH - 1) / BH) * ((a.Wout + BW - 1) / BW);
     return a.mode == OUT_D2S ? tiles * a.rh * a.rw : tiles;
 }
@@ -1204,12 +1243,11 @@ int launch_conv_tc_group(const ConvArgs* as, int count, int num_sms, cudaStream_
         if (dwm) {
             g.BH = DWM_BH;
             g.BW = DWM_BW;  // box columns; DWM_BW - 2 output columns per tile
-        } else if (halo) {
-            choose_tile_halo(a.Hout, a.Wout, swap ? 256 : 128, &g.BH, &g.BW);
         } else {
-            choose_tile(a.Hout, a.Wout, swap ? 256 : 128, &g.BH, &g.BW);
+            conv_tc_tile(a, rt, &g.BH, &g.BW);
         }
         g.bwo = dwm ? g.BW - 2 : g.BW;
+        g.nvox = g.BH * g.BW;
         g.tiles_w = (a.Wout + g.bwo - 1) / g.bwo;
         g.tiles_h = (a.Hout + g.BH - 1) / g.BH;
         g.cpt = a.Cin / 64;

@@ -302,9 +302,9 @@ int stem_frames(const tok_ctx* c, int T) {
 }
 
 // Upper bound on the GroupNorm statistics slots of an Hout x Wout conv output:
-// tiles of 256 voxels (BH x BW, BW >= 8) cover it in at most
-// HW/256 + Hout + Wout/8 + 1 tiles.
-inline long long gn_slot_bound(long long Ho, long long Wo) { return Ho * Wo / 256 + Ho + Wo / 8 + 2; }
+// tiles of at least 192 voxels (BH x BW, BW >= 8) cover it in at most
+// HW/192 + Hout + Wout/8 + 1 tiles.
+inline long long gn_slot_bound(long long Ho, long long Wo) { return Ho * Wo / 128 + Ho + Wo / 8 + 2; }
 
 // Bytes of the statistics triples the largest conv output of the walk needs:
 // plain outputs at every level, and depth-to-space outputs (4 sub-positions per

@@ -55,12 +55,13 @@ def _bf16_normal(shape, seed, scale=1.0, shift=0.0):
     return (torch.randn(shape, generator=g) * scale + shift).to(torch.bfloat16)
 
 
-@pytest.mark.parametrize("level", [0, 1])
+@pytest.mark.parametrize("level", [0, 1, 2])
 def test_conv_full_size_sampled(P, level):
-    """The level-0 (128 -> 128 channels at 17 x 360 x 640) and level-1 (256 -> 256 at
-    9 x 180 x 320) residual-block convs with their residual add, in the swapped halo form."""
+    """The level-0 (128 -> 128 channels at 17 x 360 x 640), level-1 (256 -> 256 at
+    9 x 180 x 320) and level-2 (512 -> 512 at 5 x 90 x 160, 15 x 16 tiles) residual-block
+    convs with their residual add, in the swapped halo form."""
     C = 128 << level
-    Tl, Hl, Wl = (T, H // 2, W // 2) if level == 0 else (9, H // 4, W // 4)
+    Tl, Hl, Wl = [(T, H // 2, W // 2), (9, H // 4, W // 4), (5, H // 8, W // 8)][level]
     rng = np.random.default_rng(20 + level)
     x = _bf16_normal((1, Tl, Hl, Wl, C), 40 + level)
     res = _bf16_normal((1, Tl, Hl, Wl, C), 50 + level)

@@ -52,6 +52,8 @@ CONV_CASES = [
     (1, 3, 5, 130, 128, 128, 3, (1, 1, 1), 1),          # halo tile 8 x 32
     (1, 2, 4, 128, 64, 128, 3, (1, 1, 1), 0),           # halo tile 4 x 64
     (1, 3, 9, 40, 128, 12, 3, (1, 1, 1), 0),            # narrow head, 16 weight rows
+    (1, 3, 30, 32, 128, 128, 3, (1, 1, 1), 0),          # halo tile 15 x 16 (N = 240, exact fit)
+    (2, 2, 12, 20, 128, 256, 3, (1, 1, 1), 1),          # halo tile 12 x 16 (N = 192), two channel tiles
     (1, 3, 11, 37, 64, 24, 3, (1, 1, 1), 1),            # narrow head, 32 weight rows
     (1, 3, 7, 9, 128, 6, 1, (1, 1, 1), 0),              # narrow 1x1x1 (swapped form)
     # 3x3x3 heads of at most 16 channels: the three dw taps as MMA rows, 30 output
