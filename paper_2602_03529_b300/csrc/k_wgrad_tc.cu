@@ -421,18 +421,20 @@ int launch_wgrad_tc(const __nv_bfloat16* dy, const __nv_bfloat16* x, const Wgrad
     g.n_tiles = (a.Cin + BN - 1) / BN;
     g.taps = ht ? a.kt * a.kw : a.kt * a.kh * a.kw;
     const long long out_tiles = (long long)g.m_tiles * g.n_tiles * g.taps;
-    // split count: at least 4 voxel tiles per split, partials within max_floats,
-    // and the grid (one CTA per SM) filling its last wave as fully as possible
+    // split count: at least 4 voxel tiles per split, partials within max_floats;
+    // time ~ waves x (voxel tiles per split + a CTA's fixed cost), the fixed cost
+    // (TMEM allocation, pipeline fill, draining three accumulators to the FP32
+    // partials) measured at about 30 voxel tiles' worth of MMAs on B300
+    constexpr double kCtaFixed = 30.0;
     const long long s_max = std::max(1LL, std::min(g.vtiles / 4, (long long)(max_floats / ((size_t)a.Cout * a.K))));
     const long long s_cap = std::min(s_max, std::max(1LL, (4LL * num_sms + out_tiles - 1) / out_tiles));
     long long S = 1;
     double best = -1.0;
     for (long long sc = 1; sc <= s_cap; ++sc) {
         const long long ctas = out_tiles * sc, waves = (ctas + num_sms - 1) / num_sms;
-        // time ~ waves / sc (work per CTA shrinks with sc); small bonus for fewer partials
-        const double score = (double)sc / (double)waves - 1e-3 * (double)sc;
-        if (score > best) {
-            best = score;
+        const double t = (double)waves * ((double)g.vtiles / (double)sc + kCtaFixed);
+        if (best < 0.0 || t < best) {
+            best = t;
             S = sc;
         }
     }
