@@ -240,24 +240,46 @@ __global__ void __launch_bounds__(192, 1)
         okw = __shfl_sync(0xffffffffu, okw, 0);
         if (okw) {
             tc_fence_after();
-            const int co = mt * 128 + q * 32 + lane;
+            // The MMAs are done, so the stage ring is free: each warp stages its 32
+            // output-channel rows there (row stride BN + 4 floats: the 16-byte writes
+            // of 8 consecutive lanes fall in distinct banks), then writes every row as
+            // one coalesced run of BN floats.
+            constexpr int RS = BN + 4;
+            float* buf = reinterpret_cast<float*>(smem) + q * 32 * RS;
             const bool empty_range = v_end <= v_begin;
+            const int n_valid = min(BN, a.Cin - nt * BN);  // input channels of this tile (a multiple of 16)
 #pragma unroll 1
             for (int d = 0; d < (HT ? 3 : 1); ++d) {
                 const int tp = HT ? (dt * 3 + d) * 3 + dw : tap;  // the conv tap of accumulator d
-                float* P = part + ((long long)split * a.Cout + co) * a.K + (long long)tp * a.Cin + nt * BN;
 #pragma unroll 1
-                for (int c16 = 0; c16 < BN / 16; ++c16) {
-                    float v[16];
-                    tmem_ld16(tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * BN + c16 * 16), v);
-                    if (co < a.Cout && nt * BN + c16 * 16 < a.Cin) {
-                        float4* dst = reinterpret_cast<float4*>(P + c16 * 16);
+                for (int c64 = 0; c64 < BN / 64; ++c64) {
+                    uint32_t r[4][16];
+                    const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(d * BN + c64 * 64);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) tmem_ld16_issue(ta + (uint32_t)(k * 16), r[k]);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int k = 0; k < 4; ++k)
 #pragma unroll
                         for (int i = 0; i < 4; ++i)
-                            dst[i] = empty_range ? make_float4(0.f, 0.f, 0.f, 0.f)
-                                                 : make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-                    }
+                            *reinterpret_cast<float4*>(buf + lane * RS + c64 * 64 + k * 16 + 4 * i) =
+                                empty_range ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                            : make_float4(__uint_as_float(r[k][4 * i]), __uint_as_float(r[k][4 * i + 1]),
+                                                          __uint_as_float(r[k][4 * i + 2]),
+                                                          __uint_as_float(r[k][4 * i + 3]));
                 }
+                __syncwarp();
+                const long long row0 = (long long)split * a.Cout + mt * 128 + q * 32;
+                float* P = part + row0 * a.K + (long long)tp * a.Cin + nt * BN;
+                for (int rr = 0; rr < 32; ++rr) {
+                    if (mt * 128 + q * 32 + rr >= a.Cout) break;
+#pragma unroll
+                    for (int c = 4 * lane; c < BN; c += 128)
+                        if (c < n_valid)
+                            *reinterpret_cast<float4*>(P + (long long)rr * a.K + c) =
+                                *reinterpret_cast<const float4*>(buf + rr * RS + c);
+                }
+                __syncwarp();
             }
             tc_fence_before();
         }
