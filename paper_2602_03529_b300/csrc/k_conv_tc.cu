@@ -231,7 +231,8 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
     using C = Cfg<BN, SWAP, HALO, DWM>;
     static_assert(!DWM || (SWAP && HALO == 1), "dw rows: swapped halo form");
     static_assert(CL == 1 || CL == 2, "CTA pairs at most");
-    static_assert(!HALO || CL == 1, "halo boxes with single CTAs");
+    static_assert(!HALO || CL == 1 || (!DWM && (C::W_TAP_BYTES / 2) % 1024 == 0),
+                  "halo pairs: each weight box splits on a swizzle atom");
     constexpr uint32_t HALF_W = C::W_BYTES / 2;  // one CTA's share of a weight box
     static_assert(CL == 1 || HALF_W % 1024 == 0, "weight halves must start on a swizzle atom");
     int* const status = B.a[0].status;
@@ -282,8 +283,9 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
     }
     if constexpr (HALO > 0) {
         // narrow layer: the weight boxes fill only the first w_rows rows of each
-        // 128-row weight slot; the others are zero for the whole launch
-        if (B.w_rows < BN) {
+        // 128-row weight slot; the others are zero for the whole launch (CTA pairs
+        // fill the whole slot, half from each CTA)
+        if (B.w_rows * CL < BN) {
             for (int st = 0; st < C::STAGES; ++st) {
                 uint4* wz = reinterpret_cast<uint4*>(smem + st * C::STAGE + C::ACT_BYTES);
                 for (int i = threadIdx.x; i < C::W_BYTES / 16; i += blockDim.x) wz[i] = make_uint4(0u, 0u, 0u, 0u);
@@ -354,8 +356,9 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                     const CUtensorMap* wmap = (tc.to == 0) ? &B.tm_w0 : &B.tm_w;
                     if constexpr (HALO > 0) {
                         // rows th*BH - 1 .. th*BH + BH of the input frame (zeros outside), per block
+                        // (CTA pairs: both halves of every weight box land here)
                         mbar_arrive_expect_tx(&full[s],
-                                              (uint32_t)(HALO * ((g.BH + 2) * g.BW * 128 + 3 * B.w_rows * 128)));
+                                              (uint32_t)(HALO * ((g.BH + 2) * g.BW * 128 + 3 * B.w_rows * CL * 128)));
 #pragma unroll
                         for (int c = 0; c < HALO; ++c) {
                             const int ci = (cb * HALO + c) * 64;
@@ -363,10 +366,14 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                             tma_load_4d(sa + c * C::SUB_ACT, src, &full[s], ci,
                                         DWM ? tc.tw * g.bwo - 1 : tc.tw * g.BW + dw - 1, tc.th * g.BH - 1, tcoord);
 #pragma unroll
-                            for (int d = 0; d < 3; ++d)
-                                tma_load_2d(sb + (c * 3 + d) * C::W_TAP_BYTES, wmap, &full[s],
-                                            DWM ? (dt * 3 + d) * a.Cin + ci : ((dt * 3 + d) * 3 + dw) * a.Cin + ci,
-                                            tc.nt * BN);
+                            for (int d = 0; d < 3; ++d) {
+                                const int kw0 = DWM ? (dt * 3 + d) * a.Cin + ci : ((dt * 3 + d) * 3 + dw) * a.Cin + ci;
+                                if constexpr (CL == 1)
+                                    tma_load_2d(sb + (c * 3 + d) * C::W_TAP_BYTES, wmap, &full[s], kw0, tc.nt * BN);
+                                else
+                                    tma_load_2d_mc(sb + (c * 3 + d) * C::W_TAP_BYTES + rank * (C::W_TAP_BYTES / 2), wmap,
+                                                   &full[s], kw0, tc.nt * BN + (int)rank * (BN / 2), (uint16_t)0x3);
+                            }
                         }
                         last_ph[s] = (int)ph;
                         if (++s == C::STAGES) {
@@ -999,7 +1006,13 @@ int launch_bn(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int c
 // CTA pairs for layers with at least one wave of tiles (weight halves of 64+
 // rows), single CTAs otherwise and whenever CTA lifetimes are bounded.
 template <int BN, bool SWAP, int NCB, bool DWM = false>  // NCB: 64-channel blocks per halo stage
-int launch_bn_halo(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int cta_tiles, cudaStream_t stream) {
+int launch_bn_halo(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int cta_tiles, cudaStream_t stream,
+                   bool pair = false) {
+    if constexpr (!DWM) {
+        if (pair)
+            return count == 1 ? launch_bn<BN, SWAP, 1, 2, NCB>(as, gs, 1, num_sms, 0, stream)
+                              : launch_bn<BN, SWAP, kMaxConvGroup, 2, NCB>(as, gs, count, num_sms, 0, stream);
+    }
     return count == 1 ? launch_bn<BN, SWAP, 1, 1, NCB, DWM>(as, gs, 1, num_sms, cta_tiles, stream)
                       : launch_bn<BN, SWAP, kMaxConvGroup, 1, NCB, DWM>(as, gs, count, num_sms, cta_tiles, stream);
 }
@@ -1258,7 +1271,16 @@ int launch_conv_tc_group(const ConvArgs* as, int count, int num_sms, cudaStream_
         g.num_tiles = 0;
     }
     if (dwm) return launch_bn_halo<128, true, 1, true>(as, gs, count, num_sms, cta_tiles, stream);
-    if (halo) return launch_bn_halo<128, true, 1>(as, gs, count, num_sms, cta_tiles, stream);
+    if (halo) {
+        // wide layers: clusters of two CTAs share every weight box (each loads half and
+        // multicasts it), when the layer has at least a tile per SM
+        long long tiles = 0;
+        for (int p = 0; p < count; ++p)
+            tiles += (long long)as[p].N * as[p].Tout * gs[p].tiles_h * gs[p].tiles_w *
+                     (std::min(as[p].Cout_pad, (as[p].Cout + 127) / 128 * 128) / 128);
+        const bool pair = pairs && cta_tiles == 0 && !rt.narrow && tiles >= num_sms;
+        return launch_bn_halo<128, true, 1>(as, gs, count, num_sms, cta_tiles, stream, pair);
+    }
     if (swap) return launch_bn_any<128, true>(as, gs, count, num_sms, cta_tiles, pairs, stream);
     switch (conv_tc_bn(a0.Cout_pad)) {
         case 256: return launch_bn_any<256, false>(as, gs, count, num_sms, cta_tiles, pairs, stream);
