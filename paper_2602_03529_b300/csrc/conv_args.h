@@ -53,8 +53,9 @@ struct ConvArgs {
     // weights for the tiles of output frame 0 (same layout), or null: the adjoint of
     // a replicate-padded conv, where input frame 0 also stood in for the padded frames
     const void* w0;
-    // nonzero: w holds a narrow 3x3x3 stride-1 head (Cout <= 16) as rows dw * 16 + co
-    // of K = (dt, dh, ci), 9 * Cin long (the dw-rows form of the tensor-core conv)
+    // spatial taps in the weight rows of a narrow 3x3x3 stride-1 head: 0 (no), 3 (rows
+    // dw * 16 + co over K = (dt, dh, ci), Cout <= 16) or 9 (rows (dh * 3 + dw) * Cout + co
+    // over K = (dt, ci), 9 * Cout <= 128)
     int w_dwm;
     const float* bias;    // (Cout) fp32
     int Cout, Cout_pad, Kpad;

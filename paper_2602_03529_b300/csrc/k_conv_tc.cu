@@ -49,6 +49,7 @@ struct TcGeo {
     int halo;                // K blocks are (dt, dw, channel block) groups of three dh taps
     int bwo;                 // output columns per tile: BW, or BW - 2 in the dw-rows form (DWM)
     int nvox;                // swapped forms: voxels per tile = BH * BW = the MMA's N (16 | nvox, <= 256)
+    int bho;                 // output rows per tile: BH, or BH - 2 when all nine taps are MMA rows
 };
 
 // A grouped launch: up to MAXP inputs of one layer (clips or stream chunks of
@@ -95,31 +96,34 @@ namespace {
 //                most 32 channels) loads only its 16 or 32 weight rows per tap
 //                into weight slots whose other rows stay zero.
 constexpr int HALO_BW_MAX = 64;
-constexpr int DWM_BH = 8, DWM_BW = 32;  // dw-rows form: output rows per tile, input box columns
+constexpr int DWM_BH = 8, DWM_BW = 32;  // taps-in-rows forms: rows (dw rows: output rows) x columns of a tile's box
 
 //                HALO = number of 64-channel blocks per stage (0: no halo).
-//                DWM: the dw-rows form (a 10 x 32 box, weight slots of 64 rows).
-template <int BN, bool SWAP, int HALO = 0, bool DWM = false>
+//                TR: taps in the MMA rows. 3: the dw rows (a 10 x 32 box, weight slots of
+//                64 rows); 9: the (dh, dw) rows (an 8 x 32 box, one 128-row weight slot).
+template <int BN, bool SWAP, int HALO = 0, int TR = 0>
 struct Cfg {
     static constexpr int ROWS = SWAP ? 256 : 128;  // voxels per tile
     static constexpr int HALO_BW = HALO_BW_MAX;
     // one channel block's input box
-    static constexpr int SUB_ACT = DWM ? (DWM_BH + 2) * DWM_BW * 128 : (ROWS + (HALO ? 2 * HALO_BW : 0)) * 128;
+    static constexpr int SUB_ACT = TR == 3   ? (DWM_BH + 2) * DWM_BW * 128
+                                   : TR == 9 ? DWM_BH * DWM_BW * 128
+                                             : (ROWS + (HALO ? 2 * HALO_BW : 0)) * 128;
     static constexpr int ACT_BYTES = (HALO ? HALO : 1) * SUB_ACT;  // 64 bf16 channels per row
-    static constexpr int W_TAP_BYTES = (DWM ? 64 : BN) * 128;
-    static constexpr int W_BYTES = (HALO ? 3 * HALO : 1) * W_TAP_BYTES;
+    static constexpr int W_TAP_BYTES = (TR == 3 ? 64 : BN) * 128;
+    static constexpr int W_BYTES = (TR == 9 ? HALO : HALO ? 3 * HALO : 1) * W_TAP_BYTES;
     static constexpr int STAGE = ACT_BYTES + W_BYTES;
     static constexpr int STAGES = (200 * 1024 / STAGE) > 8 ? 8 : (200 * 1024 / STAGE);
     static constexpr int ACC_COLS = SWAP ? ROWS : BN;  // TMEM columns per accumulator
     static constexpr int TMEM_COLS = (2 * ACC_COLS <= 32) ? 32 : (2 * ACC_COLS <= 64) ? 64 : (2 * ACC_COLS <= 128) ? 128 : (2 * ACC_COLS <= 256) ? 256 : 512;
     static constexpr int BAR_BYTES = 256;
     static constexpr int EPI_STRIDE = 36;  // floats per staged voxel row (16B-aligned, bank-spread)
-    static constexpr int EPI_BYTES = SWAP ? 4 * 16 * EPI_STRIDE * 4 : 0;
+    // (nine taps in rows: a staged box row of 128 accumulator rows and one output row of 16 channels)
+    static constexpr int EPI_BYTES = TR == 9 ? (128 + 16) * 33 * 4 : SWAP ? 4 * 16 * EPI_STRIDE * 4 : 0;
     static constexpr int SMEM = STAGES * STAGE + 1024 + BAR_BYTES + EPI_BYTES;
+    // (the swapped halo forms build theirs per tile: N = the tile's voxels, and M = 64
+    // for heads of at most 16 rows, whose output channel r stays in TMEM lane r)
     static constexpr uint32_t IDESC = SWAP ? idesc_bf16_f32(BN, ROWS) : idesc_bf16_f32(128, BN);
-    // narrow swapped layers of at most 16 channels: an M = 64 MMA (half the padded
-    // rows); output channel r < 16 stays in TMEM lane r
-    static constexpr uint32_t IDESC_M64 = idesc_bf16_f32(64, ROWS);
 };
 
 struct TileCoord {
@@ -226,12 +230,20 @@ __device__ __forceinline__ long long unit_tile(const TcGeo& g, long long lu, uin
 // channels) with the three dh taps inside and an input box 32 columns wide
 // serves 30 output columns; the epilogue adds the dw rows with their column
 // shift: out[co][x] = D[co][x] + D[16 + co][x + 1] + D[32 + co][x + 2].
-template <int BN, bool SWAP, int MAXP, int CL, int HALO, bool DWM = false>
+//
+// Nine taps in rows (narrow heads with 9 * Cout <= 128): the weights are rows
+// (dh * 3 + dw) * Cout + co over K = (dt, ci), so one M = 128 MMA computes all
+// nine spatial taps and a K block is (dt, 64 channels) with one 8 x 32 input
+// box (6 x 30 outputs); the epilogue adds the tap rows with their row and
+// column shifts, out[co][y][x] = sum over dh, dw of D[(dh, dw, co)][y + dh][x + dw].
+template <int BN, bool SWAP, int MAXP, int CL, int HALO, int TR = 0>
 __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__ TcBatch<MAXP> B) {
-    using C = Cfg<BN, SWAP, HALO, DWM>;
-    static_assert(!DWM || (SWAP && HALO == 1), "dw rows: swapped halo form");
+    using C = Cfg<BN, SWAP, HALO, TR>;
+    constexpr bool DWM = TR == 3, T9 = TR == 9;
+    constexpr int NDH = T9 ? 1 : 3;  // weight boxes (dh taps) per channel block of a K block
+    static_assert(TR == 0 || ((TR == 3 || TR == 9) && SWAP && HALO == 1), "taps in rows: swapped halo form");
     static_assert(CL == 1 || CL == 2, "CTA pairs at most");
-    static_assert(!HALO || CL == 1 || (!DWM && (C::W_TAP_BYTES / 2) % 1024 == 0),
+    static_assert(!HALO || CL == 1 || (TR == 0 && (C::W_TAP_BYTES / 2) % 1024 == 0),
                   "halo pairs: each weight box splits on a swizzle atom");
     constexpr uint32_t HALF_W = C::W_BYTES / 2;  // one CTA's share of a weight box
     static_assert(CL == 1 || HALF_W % 1024 == 0, "weight halves must start on a swizzle atom");
@@ -333,9 +345,9 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                     // and HALO channel blocks inside
                     const int cpg = HALO ? g.cpt / HALO : g.cpt;
                     const int tap = kb / cpg, cb = kb - tap * cpg;
-                    const int dw = DWM ? 0 : (HALO ? tap % 3 : tap % a.kw);
+                    const int dw = TR ? 0 : (HALO ? tap % 3 : tap % a.kw);
                     const int dh = HALO ? 0 : (tap / a.kw) % a.kh;
-                    const int dt = DWM ? tap : (HALO ? tap / 3 : tap / (a.kw * a.kh));
+                    const int dt = TR ? tap : (HALO ? tap / 3 : tap / (a.kw * a.kh));
                     const int ti = tc.to * a.st + dt + a.t_off;
                     const CUtensorMap* src = &B.tm_x[p];
                     int tcoord;
@@ -357,22 +369,25 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                     if constexpr (HALO > 0) {
                         // rows th*BH - 1 .. th*BH + BH of the input frame (zeros outside), per block
                         // (CTA pairs: both halves of every weight box land here)
-                        mbar_arrive_expect_tx(&full[s],
-                                              (uint32_t)(HALO * ((g.BH + 2) * g.BW * 128 + 3 * B.w_rows * CL * 128)));
+                        // (nine taps in rows: a box of BH rows, th*bho - 1 .. th*bho + bho)
+                        mbar_arrive_expect_tx(&full[s], (uint32_t)(HALO * ((T9 ? g.BH : g.BH + 2) * g.BW * 128 +
+                                                                           NDH * B.w_rows * CL * 128)));
 #pragma unroll
                         for (int c = 0; c < HALO; ++c) {
                             const int ci = (cb * HALO + c) * 64;
-                            // DWM: columns tw*bwo - 1 .. tw*bwo + bwo of the input (all three dw)
+                            // taps in rows: columns tw*bwo - 1 .. tw*bwo + bwo of the input (all three dw)
                             tma_load_4d(sa + c * C::SUB_ACT, src, &full[s], ci,
-                                        DWM ? tc.tw * g.bwo - 1 : tc.tw * g.BW + dw - 1, tc.th * g.BH - 1, tcoord);
+                                        TR ? tc.tw * g.bwo - 1 : tc.tw * g.BW + dw - 1, tc.th * g.bho - 1, tcoord);
 #pragma unroll
-                            for (int d = 0; d < 3; ++d) {
-                                const int kw0 = DWM ? (dt * 3 + d) * a.Cin + ci : ((dt * 3 + d) * 3 + dw) * a.Cin + ci;
+                            for (int d = 0; d < NDH; ++d) {
+                                const int kw0 = T9    ? dt * a.Cin + ci
+                                                : DWM ? (dt * 3 + d) * a.Cin + ci
+                                                      : ((dt * 3 + d) * 3 + dw) * a.Cin + ci;
                                 if constexpr (CL == 1)
-                                    tma_load_2d(sb + (c * 3 + d) * C::W_TAP_BYTES, wmap, &full[s], kw0, tc.nt * BN);
+                                    tma_load_2d(sb + (c * NDH + d) * C::W_TAP_BYTES, wmap, &full[s], kw0, tc.nt * BN);
                                 else
-                                    tma_load_2d_mc(sb + (c * 3 + d) * C::W_TAP_BYTES + rank * (C::W_TAP_BYTES / 2), wmap,
-                                                   &full[s], kw0, tc.nt * BN + (int)rank * (BN / 2), (uint16_t)0x3);
+                                    tma_load_2d_mc(sb + (c * NDH + d) * C::W_TAP_BYTES + rank * (C::W_TAP_BYTES / 2),
+                                                   wmap, &full[s], kw0, tc.nt * BN + (int)rank * (BN / 2), (uint16_t)0x3);
                             }
                         }
                         last_ph[s] = (int)ph;
@@ -451,9 +466,9 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
 #pragma unroll
                         for (int c = 0; c < HALO; ++c)
 #pragma unroll
-                            for (int dh = 0; dh < 3; ++dh) {
+                            for (int dh = 0; dh < NDH; ++dh) {
                                 const uint32_t xa = s_act + (uint32_t)(c * C::SUB_ACT) + (uint32_t)dh * row_step;
-                                const uint32_t wa = s_w + (uint32_t)((c * 3 + dh) * C::W_TAP_BYTES);
+                                const uint32_t wa = s_w + (uint32_t)((c * NDH + dh) * C::W_TAP_BYTES);
                                 const uint32_t op_a = SWAP ? wa : xa, op_b = SWAP ? xa : wa;
 #pragma unroll
                                 for (int k = 0; k < 4; ++k)
@@ -516,6 +531,126 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                 float* stg = epi + q * 16 * C::EPI_STRIDE;
                 const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * C::ACC_COLS);
                 const int j = lane >> 1, half = lane & 1;  // read-back role: voxel j, 16 channels
+                if constexpr (T9) {
+                    // Row r = (dh * 3 + dw) * Cout + co of the M = 128 accumulator is TMEM lane
+                    // r. Box row b (32 columns) at a time is staged in shared memory; thread t
+                    // keeps channel co = t & 15 at columns x = t / 16 + 8 i and three running
+                    // sums, for output rows b, b - 1 and b - 2, which take tap row dh of box
+                    // row b into output row b - dh; output row b - 2 is complete after box row b.
+                    float* buf = epi;              // [128 rows][33]
+                    float* orow = epi + 128 * 33;  // [16 channels][33]: a finished output row (FSQ)
+                    const int t = q * 32 + lane;
+                    const int co = t & 15, xg = t >> 4;
+                    const int Co = a.Cout, rows_used = 9 * Co;
+                    const int Hout = a.Hout, Wout = a.Wout, oT = a.oT, oH = a.oH, oW = a.oW, oC = a.oC;
+                    const int bwo = g.bwo, wo0 = tc.tw * bwo;
+                    const bool fsq = a.mode == OUT_FSQ, f32 = a.out_fp32 != 0;
+                    int ch = co, cc = 0, bb = 0, rw = 1, rh = 1, ot = tc.to;
+                    if (a.mode == OUT_D2S) {
+                        const int sub = co / oC;
+                        ch = co - sub * oC;
+                        rw = a.rw;
+                        rh = a.rh;
+                        cc = sub % rw;
+                        bb = (sub / rw) % rh;
+                        ot = tc.to * a.rt + sub / (rw * rh) - a.drop_t;
+                    }
+                    const bool c_ok = co < Co && ot >= 0 && ot < oT;
+                    const float bias_c = (a.bias && co < Co) ? a.bias[co] : 0.f;
+                    const __nv_bfloat16* const resid = static_cast<const __nv_bfloat16*>(a.residual);
+                    void* const out = a.out;
+                    float s0[4], s1[4], s2[4];
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) s0[i] = s1[i] = s2[i] = 0.f;
+                    for (int b = 0; b < g.BH; ++b) {
+                        {
+                            float v[16];
+#pragma unroll
+                            for (int h2 = 0; h2 < 2; ++h2) {
+                                tmem_ld16(tbase + (uint32_t)(b * 32 + h2 * 16), v);
+                                if (t < rows_used) {
+#pragma unroll
+                                    for (int i2 = 0; i2 < 16; ++i2) buf[t * 33 + h2 * 16 + i2] = v[i2];
+                                }
+                            }
+                        }
+                        asm volatile("bar.sync 1, 128;" ::: "memory");
+                        if (co < Co) {
+#pragma unroll
+                            for (int i = 0; i < 4; ++i) {
+                                const int x = xg + 8 * i;
+                                if (x < bwo) {
+                                    float p[3];
+#pragma unroll
+                                    for (int dh = 0; dh < 3; ++dh) {
+                                        const float* r0 = buf + ((dh * 3) * Co + co) * 33 + x;
+                                        p[dh] = r0[0] + r0[Co * 33 + 1] + r0[2 * Co * 33 + 2];
+                                    }
+                                    s0[i] += p[0];
+                                    s1[i] += p[1];
+                                    s2[i] += p[2];
+                                }
+                            }
+                        }
+                        const int yo = b - 2, ho = tc.th * g.bho + yo;
+                        if (yo >= 0 && yo < g.bho && ho < Hout) {
+                            if (fsq) {
+                                if (co < Co) {
+#pragma unroll
+                                    for (int i = 0; i < 4; ++i)
+                                        if (xg + 8 * i < bwo) orow[co * 33 + xg + 8 * i] = s2[i] + bias_c;
+                                }
+                                asm volatile("bar.sync 1, 128;" ::: "memory");
+                                const int x = t >> 2;
+                                if ((t & 3) == 0 && x < bwo && wo0 + x < Wout) {
+                                    const long long vox =
+                                        (((long long)tc.n * a.Tout + tc.to) * Hout + ho) * Wout + wo0 + x;
+                                    float* z = static_cast<float*>(out) + vox * a.fsq.nlev;
+                                    int idx = 0;
+#pragma unroll
+                                    for (int c = 0; c < 8; ++c) {
+                                        if (c < a.fsq.nlev) {
+                                            const float zz = orow[c * 33 + x];
+                                            z[c] = zz;
+                                            const float bq =
+                                                tanhf(zz + a.fsq.shift[c]) * a.fsq.half_l[c] - a.fsq.offset[c];
+                                            idx += ((int)rintf(bq) + a.fsq.half_w[c]) * a.fsq.basis[c];
+                                        }
+                                    }
+                                    if (a.idx) a.idx[vox] = idx;
+                                }
+                            } else if (c_ok) {
+                                const int oh = ho * rh + bb;
+                                if (oh < oH) {
+                                    const long long rowoff = (((long long)tc.n * oT + ot) * oH + oh) * oW;
+#pragma unroll
+                                    for (int i = 0; i < 4; ++i) {
+                                        const int x = xg + 8 * i, wo = wo0 + x, ow = wo * rw + cc;
+                                        if (x >= bwo || wo >= Wout || ow >= oW) continue;
+                                        float o = s2[i] + bias_c;
+                                        const long long off = (rowoff + ow) * oC + ch;
+                                        if (resid) o += __bfloat162float(resid[off]);
+                                        if (f32)
+                                            static_cast<float*>(out)[off] = o;
+                                        else
+                                            static_cast<__nv_bfloat16*>(out)[off] = __float2bfloat16_rn(o);
+                                    }
+                                }
+                            }
+                        }
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            s2[i] = s1[i];
+                            s1[i] = s0[i];
+                            s0[i] = 0.f;
+                        }
+                        asm volatile("bar.sync 1, 128;" ::: "memory");
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&tempty[acc]);
+                    continue;
+                }
                 if constexpr (DWM) {
                     // An M = 64 accumulator keeps rows 16q .. 16q + 15 in lanes 0 .. 15 of
                     // TMEM quarter q, so quarter dw (< 3) holds the rows of tap dw. One output
@@ -915,17 +1050,21 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
     if constexpr (CL > 1) cluster_sync();  // neither CTA leaves while its peer may still address it
 }
 
-template <int BN, bool SWAP, int MAXP, int CL, int HALO = 0, bool DWM = false>
+template <int BN, bool SWAP, int MAXP, int CL, int HALO = 0, int TR = 0>
 int launch_bn(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int cta_tiles, cudaStream_t stream) {
-    using C = Cfg<BN, SWAP, HALO, DWM>;
-    auto kern = conv_tc_kernel<BN, SWAP, MAXP, CL, HALO, DWM>;
+    using C = Cfg<BN, SWAP, HALO, TR>;
+    auto kern = conv_tc_kernel<BN, SWAP, MAXP, CL, HALO, TR>;
     TcBatch<MAXP> B;
     memset(&B, 0, sizeof(B));
     // with CTA pairs each CTA loads half of the weight box (BN / 2 rows); a narrow halo
     // layer loads its real rows only
-    // (DWM: 48 weight rows dw * 16 + co, K = (dt, dh, ci))
-    B.w_rows = DWM ? 48 : (HALO > 0 && SWAP && as[0].Cout <= 32) ? (as[0].Cout + 15) / 16 * 16 : BN / CL;
-    const int wk = DWM ? 9 * as[0].Cin : as[0].Kpad;
+    // (taps in rows: 48 weight rows dw * 16 + co over K = (dt, dh, ci), or 128 rows
+    // (dh * 3 + dw) * Cout + co over K = (dt, ci))
+    B.w_rows = TR == 3   ? 48
+               : TR == 9 ? 128
+               : (HALO > 0 && SWAP && as[0].Cout <= 32) ? (as[0].Cout + 15) / 16 * 16
+                                                        : BN / CL;
+    const int wk = TR == 3 ? 9 * as[0].Cin : TR == 9 ? 3 * as[0].Cin : as[0].Kpad;
     if (!encode_w_map(&B.tm_w, as[0].w, as[0].Cout_pad, wk, B.w_rows)) return -1;
     if (as[0].w0) {
         if (!encode_w_map(&B.tm_w0, as[0].w0, as[0].Cout_pad, wk, B.w_rows)) return -1;
@@ -937,7 +1076,8 @@ int launch_bn(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int c
         const ConvArgs& a = as[p];
         TcGeo g = gs[p];
         const bool strided = g.strided != 0;
-        const int box_h = HALO ? g.BH + 2 : g.BH;  // the halo box: one input row above and below
+        // the halo box: one input row above and below (nine taps in rows: BH rows in all)
+        const int box_h = HALO ? (TR == 9 ? g.BH : g.BH + 2) : g.BH;
         if (!encode_act_map(&B.tm_x[p], a.x, a.N * a.Tin, a.Hin, a.Win, a.Cin, box_h, g.BW, strided)) return -1;
         if (a.hist) {
             if (!encode_act_map(&B.tm_h[p], a.hist, a.N * a.hist_T, a.Hin, a.Win, a.Cin, box_h, g.BW, strided))
@@ -1005,16 +1145,16 @@ int launch_bn(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int c
 
 // CTA pairs for layers with at least one wave of tiles (weight halves of 64+
 // rows), single CTAs otherwise and whenever CTA lifetimes are bounded.
-template <int BN, bool SWAP, int NCB, bool DWM = false>  // NCB: 64-channel blocks per halo stage
+template <int BN, bool SWAP, int NCB, int TR = 0>  // NCB: 64-channel blocks per halo stage
 int launch_bn_halo(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int cta_tiles, cudaStream_t stream,
                    bool pair = false) {
-    if constexpr (!DWM) {
+    if constexpr (TR == 0) {
         if (pair)
             return count == 1 ? launch_bn<BN, SWAP, 1, 2, NCB>(as, gs, 1, num_sms, 0, stream)
                               : launch_bn<BN, SWAP, kMaxConvGroup, 2, NCB>(as, gs, count, num_sms, 0, stream);
     }
-    return count == 1 ? launch_bn<BN, SWAP, 1, 1, NCB, DWM>(as, gs, 1, num_sms, cta_tiles, stream)
-                      : launch_bn<BN, SWAP, kMaxConvGroup, 1, NCB, DWM>(as, gs, count, num_sms, cta_tiles, stream);
+    return count == 1 ? launch_bn<BN, SWAP, 1, 1, NCB, TR>(as, gs, 1, num_sms, cta_tiles, stream)
+                      : launch_bn<BN, SWAP, kMaxConvGroup, 1, NCB, TR>(as, gs, count, num_sms, cta_tiles, stream);
 }
 
 template <int BN, bool SWAP>
@@ -1158,7 +1298,16 @@ ConvRoute conv_route(const ConvArgs& a0) {
     return r;
 }
 
-bool conv_tc_dwm(int Cout, int k, int sh, int sw) { return Cout <= 16 && k == 3 && sh == 1 && sw == 1; }
+// Nine taps in rows cut the MMAs per output 2.25-fold against three, but its
+// epilogue (nine shifted adds per output through shared memory) costs a fixed
+// ~75 SM cycles per output: it wins when the K loop is long. Measured on the
+// 720p clip: latent head (512 input channels) 0.098 -> 0.069 ms, pixel head
+// (128 input channels) 0.86 -> 1.30 ms; hence 256 input channels or more.
+int conv_tc_taprows(int Cout, int Cin, int k, int sh, int sw) {
+    if (k != 3 || sh != 1 || sw != 1 || Cout < 1) return 0;
+    if (9 * Cout <= 128 && Cin >= 256) return 9;
+    return Cout <= 16 ? 3 : 0;
+}
 
 // GroupNorm statistics come from the swapped wide epilogue (plain or
 // depth-to-space, bf16), for groups of 4, 8 or 16 channels, of 3x3x3 layers:
@@ -1243,9 +1392,11 @@ int launch_conv_tc_group(const ConvArgs* as, int count, int num_sms, cudaStream_
     // or a narrow layer (at most 32 channels, weights padded to 128 rows)
     const ConvRoute rt = conv_route(a0);
     const bool swap = rt.swap, halo = rt.halo;
-    const bool dwm = a0.w_dwm != 0;
-    // weights packed in the dw-rows layout only run in that form
-    if (dwm && !(halo && a0.kt == 3 && conv_tc_dwm(a0.Cout, a0.kh, a0.sh, a0.sw) && !a0.w0 && a0.Cin % 64 == 0))
+    const int tr = a0.w_dwm;
+    const bool dwm = tr != 0;
+    // weights packed with taps in the rows only run in that form
+    if (dwm && !(halo && a0.kt == 3 && conv_tc_taprows(a0.Cout, a0.Cin, a0.kh, a0.sh, a0.sw) == tr && !a0.w0 &&
+                 a0.Cin % 64 == 0))
         return -1;
     for (int p = 0; p < count; ++p)
         if (as[p].gn_part && (!conv_tc_gn_fusable(as[p]) || as[p].gn_cg != a0.gn_cg)) return -1;
@@ -1254,15 +1405,16 @@ int launch_conv_tc_group(const ConvArgs* as, int count, int num_sms, cudaStream_
         TcGeo& g = gs[p];
         const ConvArgs& a = as[p];
         if (dwm) {
-            g.BH = DWM_BH;
+            g.BH = DWM_BH;  // dw rows: output rows; nine taps: box rows (BH - 2 output rows)
             g.BW = DWM_BW;  // box columns; DWM_BW - 2 output columns per tile
         } else {
             conv_tc_tile(a, rt, &g.BH, &g.BW);
         }
         g.bwo = dwm ? g.BW - 2 : g.BW;
+        g.bho = tr == 9 ? g.BH - 2 : g.BH;
         g.nvox = g.BH * g.BW;
         g.tiles_w = (a.Wout + g.bwo - 1) / g.bwo;
-        g.tiles_h = (a.Hout + g.BH - 1) / g.BH;
+        g.tiles_h = (a.Hout + g.bho - 1) / g.bho;
         g.cpt = a.Cin / 64;
         g.nkb = dwm ? a.kt * g.cpt : halo ? a.kt * a.kw * g.cpt : a.kt * a.kh * a.kw * g.cpt;
         g.strided = (a.sh == 2) ? 1 : 0;
@@ -1270,7 +1422,8 @@ int launch_conv_tc_group(const ConvArgs* as, int count, int num_sms, cudaStream_
         g.n_tiles = 0;
         g.num_tiles = 0;
     }
-    if (dwm) return launch_bn_halo<128, true, 1, true>(as, gs, count, num_sms, cta_tiles, stream);
+    if (tr == 9) return launch_bn_halo<128, true, 1, 9>(as, gs, count, num_sms, cta_tiles, stream);
+    if (tr == 3) return launch_bn_halo<128, true, 1, 3>(as, gs, count, num_sms, cta_tiles, stream);
     if (halo) {
         // wide layers: clusters of two CTAs share every weight box (each loads half and
         // multicasts it), when the layer has at least a tile per SM

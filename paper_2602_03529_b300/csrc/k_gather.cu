@@ -355,27 +355,35 @@ int launch_fill_i32(int32_t* p, long long n, int32_t v, cudaStream_t s) {
     return (int)cudaGetLastError();
 }
 
-// Weights of a narrow 3x3x3 head (at most 16 output channels) for the form in
-// which the three dw taps are MMA rows: out[dw * 16 + co][(dt * 3 + dh) * Cin + ci]
-// = W[co][dt][dh][dw][ci]; rows_out x 9*Cin, rows past 48 (or co >= Cout) zero.
-__global__ void pack_weights_dwm_kernel(const float* __restrict__ w, int Cout, int Cin, int rows_out,
-                                        __nv_bfloat16* __restrict__ out) {
+// Weights of a narrow 3x3x3 head for the forms in which spatial taps are MMA
+// rows (W[co][dt][dh][dw][ci]; rows_out rows, the unused ones zero):
+//   tr = 3 (at most 16 channels): out[dw * 16 + co][(dt * 3 + dh) * Cin + ci], K = 9 Cin;
+//   tr = 9 (9 * Cout <= 128):     out[(dh * 3 + dw) * Cout + co][dt * Cin + ci], K = 3 Cin.
+__global__ void pack_weights_taprows_kernel(const float* __restrict__ w, int Cout, int Cin, int rows_out, int tr,
+                                            __nv_bfloat16* __restrict__ out) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long K = 9LL * Cin;
+    const long long K = (tr == 9 ? 3LL : 9LL) * Cin;
     if (t >= (long long)rows_out * K) return;
     const int r = (int)(t / K);
     const long long k = t - (long long)r * K;
-    const int dw = r / 16, co = r - dw * 16;
-    const int ci = (int)(k % Cin), dtdh = (int)(k / Cin);
+    const int ci = (int)(k % Cin), kk = (int)(k / Cin);  // kk: dt * 3 + dh (tr = 3) or dt (tr = 9)
     float v = 0.f;
-    if (dw < 3 && co < Cout) v = w[((long long)co * 27 + dtdh * 3 + dw) * Cin + ci];
+    if (tr == 9) {
+        const int tap = r / Cout, co = r - tap * Cout;  // tap = dh * 3 + dw
+        if (tap < 9) v = w[((long long)co * 27 + kk * 9 + tap) * Cin + ci];
+    } else {
+        const int dw = r / 16, co = r - dw * 16;
+        if (dw < 3 && co < Cout) v = w[((long long)co * 27 + kk * 3 + dw) * Cin + ci];
+    }
     out[t] = __float2bfloat16_rn(v);
 }
 
-int launch_pack_weights_dwm(const float* w, int Cout, int Cin, int rows_out, __nv_bfloat16* out, cudaStream_t s) {
-    const long long n = (long long)rows_out * 9 * Cin;
+int launch_pack_weights_taprows(const float* w, int Cout, int Cin, int rows_out, int tr, __nv_bfloat16* out,
+                                cudaStream_t s) {
+    if (tr != 3 && tr != 9) return (int)cudaErrorInvalidValue;
+    const long long n = (long long)rows_out * (tr == 9 ? 3 : 9) * Cin;
     if (n <= 0) return 0;
-    pack_weights_dwm_kernel<<<blocks_for(n, 256), 256, 0, s>>>(w, Cout, Cin, rows_out, out);
+    pack_weights_taprows_kernel<<<blocks_for(n, 256), 256, 0, s>>>(w, Cout, Cin, rows_out, tr, out);
     return (int)cudaGetLastError();
 }
 

@@ -12,11 +12,14 @@ namespace tok {
 int launch_conv_tc(const ConvArgs& a, int num_sms, cudaStream_t stream);
 // one launch over up to kMaxConvGroup inputs of the same layer (k_conv_tc.cu)
 ConvRoute conv_route(const ConvArgs& a);
-// A stride-1 3x3x3 BF16 layer of at most 16 output channels runs in the form in
-// which its three dw taps are MMA rows; its weights are packed for that form
-// (launch_pack_weights_dwm) wherever they are packed.
-bool conv_tc_dwm(int Cout, int k, int sh, int sw);
-int launch_pack_weights_dwm(const float* w, int Cout, int Cin, int rows_out, __nv_bfloat16* out, cudaStream_t s);
+// A stride-1 3x3x3 BF16 head runs in a form in which spatial taps are MMA rows:
+// all nine (dh, dw) taps when 9 * Cout <= 128 and Cin >= 256, else the three dw
+// taps when Cout <= 16 (conv_tc_taprows gives 9, 3 or 0); its weights are packed for that
+// form (launch_pack_weights_taprows) wherever they are packed, and ConvArgs.w_dwm
+// carries the form.
+int conv_tc_taprows(int Cout, int Cin, int k, int sh, int sw);
+int launch_pack_weights_taprows(const float* w, int Cout, int Cin, int rows_out, int tr, __nv_bfloat16* out,
+                                cudaStream_t s);
 // The launch writes GroupNorm statistics into a.gn_part (a.gn_cg channels per
 // group) only where this holds; conv_tc_gn_slots gives the slots per frame.
 bool conv_tc_gn_fusable(const ConvArgs& a);

@@ -565,8 +565,9 @@ int tok_conv3d(int precision, const void* x, int N, int T, int H, int W, int Cin
         a.Cout_pad = conv_tc_cout_pad(c16);
         a.Kpad = taps * Cin;
         // narrow 3x3x3 stride-1 heads: the dw taps as MMA rows (same workspace bound)
-        a.w_dwm = k == 3 && conv_tc_dwm(Cout, k, sh, sw);
-        const int e = a.w_dwm ? launch_pack_weights_dwm(w, Cout, Cin, a.Cout_pad, static_cast<__nv_bfloat16*>(ws), s)
+        a.w_dwm = conv_tc_taprows(Cout, Cin, k, sh, sw);
+        const int e = a.w_dwm ? launch_pack_weights_taprows(w, Cout, Cin, a.Cout_pad, a.w_dwm,
+                                                            static_cast<__nv_bfloat16*>(ws), s)
                               : launch_pack_weights<__nv_bfloat16>(w, Cout, taps * Cin, a.Cout_pad, a.Kpad,
                                                                    static_cast<__nv_bfloat16*>(ws), s);
         if (e) return TOK_ECUDA;

@@ -46,7 +46,7 @@ struct ConvW {
     void* wt = nullptr;
     void* wc = nullptr;
     void* wf0 = nullptr;  // BF16: adjoint taps of output frame 0 with the correction folded in
-    int dwm = 0;          // BF16 narrow 3x3x3 head: w in the dw-rows layout (rows dw * 16 + co)
+    int dwm = 0;          // BF16 narrow 3x3x3 head: spatial taps in w's rows (3: dw rows, 9: (dh, dw) rows)
     int rows_pad = 0, cpad = 0;
 };
 
@@ -252,9 +252,10 @@ int upload_conv(tok_ctx* c, ConvW& cw, cudaStream_t st = 0) {
     const float* w = c->d_master + cw.ow;
     cw.b = c->d_master + cw.ob;
     int e;
-    cw.dwm = c->bf16() && cw.k == 3 && !cw.im2col && cw.Cin % 64 == 0 && conv_tc_dwm(cw.Cout, 3, 1, 1);
+    cw.dwm = (c->bf16() && cw.k == 3 && !cw.im2col && cw.Cin % 64 == 0) ? conv_tc_taprows(cw.Cout, cw.Cin, 3, 1, 1) : 0;
     if (cw.dwm)
-        e = launch_pack_weights_dwm(w, cw.Cout, cw.Cin, cw.Cout_pad, static_cast<__nv_bfloat16*>(cw.w), st);
+        e = launch_pack_weights_taprows(w, cw.Cout, cw.Cin, cw.Cout_pad, cw.dwm, static_cast<__nv_bfloat16*>(cw.w),
+                                        st);
     else if (c->bf16())
         e = launch_pack_weights<__nv_bfloat16>(w, cw.Cout, K, cw.Cout_pad, cw.Kpad, static_cast<__nv_bfloat16*>(cw.w),
                                                st);

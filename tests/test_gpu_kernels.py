@@ -44,24 +44,31 @@ CONV_CASES = [
     (1, 9, 16, 24, 64, 64, 3, (2, 2, 2), 1),
     (1, 4, 10, 12, 64, 128, 3, (1, 2, 2), 0),           # stride (1,2,2)
     (1, 3, 7, 9, 128, 64, 1, (1, 1, 1), 0),             # 1x1x1 shortcut
-    (1, 3, 9, 40, 64, 16, 3, (1, 1, 1), 0),             # narrow N (output conv)
+    (1, 3, 9, 40, 64, 16, 3, (1, 1, 1), 0),             # 16-channel head (dw rows)
     (1, 2, 6, 130, 64, 512, 3, (1, 1, 1), 0),           # W > 128, two N tiles of 256
     # stride-1 3x3x3 layers of 128 channels and narrow heads share one input box among
     # the three dh taps (halo tiles of width 16, 32 and 64, ragged edges)
     (1, 3, 10, 70, 128, 128, 3, (1, 1, 1), 0),          # halo tile 16 x 16
     (1, 3, 5, 130, 128, 128, 3, (1, 1, 1), 1),          # halo tile 8 x 32
     (1, 2, 4, 128, 64, 128, 3, (1, 1, 1), 0),           # halo tile 4 x 64
-    (1, 3, 9, 40, 128, 12, 3, (1, 1, 1), 0),            # narrow head, 16 weight rows
+    (1, 3, 9, 40, 128, 12, 3, (1, 1, 1), 0),            # pixel head (dw rows)
     (1, 3, 30, 32, 128, 128, 3, (1, 1, 1), 0),          # halo tile 15 x 16 (N = 240, exact fit)
     (2, 2, 12, 20, 128, 256, 3, (1, 1, 1), 1),          # halo tile 12 x 16 (N = 192), two channel tiles
     (1, 3, 11, 37, 64, 24, 3, (1, 1, 1), 1),            # narrow head, 32 weight rows
     (1, 3, 7, 9, 128, 6, 1, (1, 1, 1), 0),              # narrow 1x1x1 (swapped form)
-    # 3x3x3 heads of at most 16 channels: the three dw taps as MMA rows, 30 output
-    # columns per 32-column input box (ragged last tile, frames narrower than a box)
-    (1, 3, 9, 61, 64, 3, 3, (1, 1, 1), 1),              # tiles of 30 + 30 + 1 columns
-    (2, 4, 17, 30, 192, 1, 3, (1, 1, 1), 0),            # one output channel, W = 30
-    (1, 2, 8, 31, 512, 6, 3, (1, 1, 1), 0),             # latent-head width, W = 31
-    (1, 3, 3, 5, 64, 16, 3, (1, 1, 1), 1),              # frame smaller than one box
+    # 3x3x3 heads with spatial taps as MMA rows, 30 output columns per 32-column input
+    # box (ragged last tile, frames narrower than a box): all nine taps when
+    # 9 * Cout <= 128 and Cin >= 256 (6 output rows per 8-row box), else the three dw
+    # taps up to 16 channels
+    (1, 3, 9, 61, 64, 3, 3, (1, 1, 1), 1),              # dw rows; tiles of 30 + 30 + 1 columns
+    (1, 3, 9, 61, 256, 3, 3, (1, 1, 1), 1),             # nine taps; tiles of 30 + 30 + 1 columns
+    (2, 4, 17, 30, 192, 1, 3, (1, 1, 1), 0),            # dw rows, one output channel, W = 30
+    (2, 4, 17, 30, 256, 1, 3, (1, 1, 1), 0),            # nine taps, one output channel, W = 30
+    (1, 2, 8, 31, 512, 6, 3, (1, 1, 1), 0),             # nine taps, latent-head width, W = 31
+    (1, 3, 13, 45, 256, 12, 3, (1, 1, 1), 0),           # nine taps, pixel-head width (108 rows), 13 rows
+    (1, 2, 7, 33, 256, 14, 3, (1, 1, 1), 1),            # nine taps, 126 rows
+    (1, 3, 3, 5, 64, 16, 3, (1, 1, 1), 1),              # dw rows; frame smaller than one box
+    (1, 3, 10, 62, 128, 15, 3, (1, 1, 1), 0),           # dw rows, 15 channels
 ]
 
 
