@@ -38,7 +38,7 @@ FALLBACK_PEAKS = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustain
 
 # ncu dram__bytes_read.sum + dram__bytes_write.sum over the conv launches of one
 # 1x3x17x720x1280 encode + decode (21.19 GB + 12.68 GB); re-measure when the conv kernel changes
-CONV_DRAM_BYTES_PER_STEP = 33.87e9
+CONV_DRAM_BYTES_PER_STEP = 33.72e9
 
 
 def load_peaks():
