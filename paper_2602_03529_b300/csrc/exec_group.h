@@ -199,13 +199,14 @@ struct GroupExec : Exec {
                 it[p] = {static_cast<const __nv_bfloat16*>(in[p].p), static_cast<__nv_bfloat16*>(out[p].p),
                          (long long)in[p].N * in[p].T, (long long)in[p].H * in[p].W, pr[p].w.gn, in[p].part,
                          in[p].part_S};
-            ck(launch_gn_silu_group<__nv_bfloat16>(it, P, in[0].C, g.G, g.g, g.b, c->arch.gn_eps, true, s));
+            ck(launch_gn_silu_group<__nv_bfloat16>(it, P, in[0].C, g.G, g.g, g.b, c->arch.gn_eps, true, s,
+                                                   c->d_status));
         } else {
             GnItem<float> it[kMaxConvGroup];
             for (int p = 0; p < P; ++p)
                 it[p] = {static_cast<const float*>(in[p].p), static_cast<float*>(out[p].p),
                          (long long)in[p].N * in[p].T, (long long)in[p].H * in[p].W, pr[p].w.gn};
-            ck(launch_gn_silu_group<float>(it, P, in[0].C, g.G, g.g, g.b, c->arch.gn_eps, false, s));
+            ck(launch_gn_silu_group<float>(it, P, in[0].C, g.G, g.g, g.b, c->arch.gn_eps, false, s, c->d_status));
         }
         pend(e, 1, bytes, name);
         c->launches += 3;

@@ -8,7 +8,10 @@
 //                 a fixed tree order (deterministic, no atomics).
 //   gn_finalize : one warp per (frame, group) merges the chunk triples in a
 //                 fixed order into mean and 1/sqrt(var + eps).
-//   gn_apply    : SiLU((x - mean) * rstd * gamma + beta), 16-byte vectors.
+//   gn_apply    : SiLU((x - mean) * rstd * gamma + beta), 16-byte vectors; a
+//                 block pulls its chunk into shared memory with four bulk
+//                 copies (64 KB in flight per block, as many as 3 blocks per
+//                 SM), then normalises from there.
 // The causal tokenizer may not mix frames, hence statistics per frame.
 #include <algorithm>
 #include <cstring>
@@ -214,18 +217,54 @@ __global__ void gn_finalize_kernel(const __grid_constant__ GnBatch<T, MAXP> B, i
     if (lane == 0) P.stats[row] = make_float2(acc.mean, rsqrtf(acc.m2 / fmaxf(acc.n, 1.f) + eps));
 }
 
+// The chunk of a block (NT * GN_VPT_MAX 16-byte vectors at most) arrives in
+// GN_SEGS bulk copies of at most GN_SEG_BYTES, each on its own mbarrier, so that
+// normalising the first segment overlaps the arrival of the others.
+constexpr int GN_VPT_MAX = 16, GN_SEGS = 4;
+constexpr int GN_SEG_BYTES = NT * GN_VPT_MAX * 16 / GN_SEGS;
+constexpr int GN_APPLY_SMEM = GN_SEGS * GN_SEG_BYTES;
+
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
 template <typename T, bool FAST, int MAXP>
 __global__ void __launch_bounds__(NT) gn_apply_kernel(const __grid_constant__ GnBatch<T, MAXP> B, int C, int G,
                                                       const float* __restrict__ gamma,
-                                                      const float* __restrict__ beta) {
+                                                      const float* __restrict__ beta, int* status,
+                                                      unsigned long long wait_ns) {
     constexpr int V = Vec<T>::N;
+    extern __shared__ __align__(128) uint8_t seg[];  // GN_SEGS x GN_SEG_BYTES
+    __shared__ uint64_t bar[GN_SEGS];
     long long lb;
     const GnProb<T>& P = B.p[gn_block_problem(B, blockIdx.x, &lb)];
     const long long vec_per_frame = P.vpf;
     const int vpt = P.vpt;
     const int frame = (int)(lb / P.S), chunk = (int)(lb % P.S), tid = threadIdx.x;
-    const T* __restrict__ x = P.x;
-    T* __restrict__ y = P.y;
+    const long long v0 = (long long)chunk * NT * vpt;
+    const long long bytes = min((long long)NT * vpt, vec_per_frame - v0) * 16;
+    const long long fo = ((long long)frame * vec_per_frame + v0) * V;  // first element of the chunk
+    const T* __restrict__ x = P.x + fo;
+    T* __restrict__ y = P.y + fo;
+    if (tid == 0) {
+        for (int sg = 0; sg < GN_SEGS; ++sg) mbar_init(&bar[sg], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int sg = 0; sg < GN_SEGS; ++sg) {
+            const long long b = min((long long)GN_SEG_BYTES, bytes - (long long)sg * GN_SEG_BYTES);
+            if (b <= 0) break;
+            mbar_arrive_expect_tx(&bar[sg], (uint32_t)b);
+            bulk_copy_g2s(seg + sg * GN_SEG_BYTES, x + (long long)sg * (GN_SEG_BYTES / 16) * V, (uint32_t)b,
+                          &bar[sg]);
+        }
+    }
+    // the thread's channels: vector i of the chunk holds channels (i % vpv) * V ..,
+    // and every vector this thread touches has i = tid (mod NT), NT a multiple of vpv
     const int cg = C / G;
     const int vpv = C / V;
     const int c0 = (tid % vpv) * V;
@@ -238,19 +277,22 @@ __global__ void __launch_bounds__(NT) gn_apply_kernel(const __grid_constant__ Gn
         sc[j] = st.y * ga;
         sh[j] = (beta ? beta[c] : 0.f) - st.x * st.y * ga;
     }
-    const long long fo = (long long)frame * vec_per_frame * V;
-    const long long v0 = (long long)chunk * NT * vpt;
-    for (int i = 0; i < vpt; ++i) {
-        const long long vi = v0 + (long long)i * NT + tid;
-        if (vi >= vec_per_frame) break;
-        float v[V];
-        Vec<T>::load(x + fo + vi * V, v);
+    for (int sg = 0; sg < GN_SEGS; ++sg) {
+        const long long b = min((long long)GN_SEG_BYTES, bytes - (long long)sg * GN_SEG_BYTES);
+        if (b <= 0) break;
+        if (!mbar_wait(&bar[sg], 0, status, wait_ns)) return;
+        const uint4* q = reinterpret_cast<const uint4*>(seg + sg * GN_SEG_BYTES);
+        const int n = (int)(b / 16), i0 = sg * (GN_SEG_BYTES / 16);
+        for (int i = tid; i < n; i += NT) {
+            float v[V];
+            Vec<T>::cvt(q[i], v);
 #pragma unroll
-        for (int j = 0; j < V; ++j) {
-            const float h = fmaf(v[j], sc[j], sh[j]);
-            v[j] = FAST ? silu_fast(h) : silu_exact(h);
+            for (int j = 0; j < V; ++j) {
+                const float h = fmaf(v[j], sc[j], sh[j]);
+                v[j] = FAST ? silu_fast(h) : silu_exact(h);
+            }
+            Vec<T>::store(y + (long long)(i0 + i) * V, v);
         }
-        Vec<T>::store(y + fo + vi * V, v);
     }
 }
 
@@ -260,6 +302,7 @@ __global__ void __launch_bounds__(NT) gn_apply_kernel(const __grid_constant__ Gn
 // order whether it is normalised as part of a whole clip or of a streaming
 // chunk, and a 4-frame chunk still fills the GPU with blocks.
 constexpr int GN_VPT = 16;
+static_assert(GN_VPT <= GN_VPT_MAX, "the apply pass stages a whole chunk in shared memory");
 void gn_plan(long long frames, long long vec_per_frame, int num_sms, int* vpt, int* S) {
     (void)frames;
     (void)num_sms;
@@ -340,20 +383,32 @@ int gn_stats_batch(const GnBatch<T, MAXP>& B, long long blocks, long long rows, 
     return 0;
 }
 
+template <typename T, bool FAST, int MAXP>
+int gn_apply_launch(const GnBatch<T, MAXP>& B, long long blocks, int C, int G, const float* gamma, const float* beta,
+                    int* status, cudaStream_t stream) {
+    static bool ready = false;
+    if (!ready) {
+        if (cudaFuncSetAttribute(gn_apply_kernel<T, FAST, MAXP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 GN_APPLY_SMEM) != cudaSuccess)
+            return (int)cudaGetLastError();
+        ready = true;
+    }
+    gn_apply_kernel<T, FAST, MAXP><<<(unsigned)blocks, NT, GN_APPLY_SMEM, stream>>>(B, C, G, gamma, beta, status,
+                                                                                   2000000000ull);
+    return (int)cudaGetLastError();
+}
+
 template <typename T, int MAXP>
 int gn_silu_batch(const GnItem<T>* items, int count, int C, int G, const float* gamma, const float* beta, float eps,
-                  bool fast, cudaStream_t stream) {
+                  bool fast, cudaStream_t stream, int* status) {
     GnBatch<T, MAXP> B;
     long long blocks, rows;
     bool pre = true;
     for (int p = 0; p < count; ++p) pre = pre && items[p].part != nullptr && items[p].part_S > 0;
     if (!gn_batch(items, count, C, G, &B, &blocks, &rows, pre)) return 0;
     if (const int e = gn_stats_batch(B, blocks, rows, C, G, eps, stream, pre)) return e;
-    if (fast)
-        gn_apply_kernel<T, true, MAXP><<<(unsigned)blocks, NT, 0, stream>>>(B, C, G, gamma, beta);
-    else
-        gn_apply_kernel<T, false, MAXP><<<(unsigned)blocks, NT, 0, stream>>>(B, C, G, gamma, beta);
-    return (int)cudaGetLastError();
+    return fast ? gn_apply_launch<T, true, MAXP>(B, blocks, C, G, gamma, beta, status, stream)
+                : gn_apply_launch<T, false, MAXP>(B, blocks, C, G, gamma, beta, status, stream);
 }
 
 }  // namespace
@@ -364,18 +419,19 @@ int gn_silu_batch(const GnItem<T>* items, int count, int C, int G, const float* 
 // per pass over all items (at most kMaxConvGroup).
 template <typename T>
 int launch_gn_silu_group(const GnItem<T>* items, int count, int C, int G, const float* gamma, const float* beta,
-                         float eps, bool fast, cudaStream_t stream) {
+                         float eps, bool fast, cudaStream_t stream, int* status) {
     if (count < 1 || count > kMaxConvGroup) return (int)cudaErrorInvalidValue;
-    return count == 1 ? gn_silu_batch<T, 1>(items, 1, C, G, gamma, beta, eps, fast, stream)
-                      : gn_silu_batch<T, kMaxConvGroup>(items, count, C, G, gamma, beta, eps, fast, stream);
+    return count == 1 ? gn_silu_batch<T, 1>(items, 1, C, G, gamma, beta, eps, fast, stream, status)
+                      : gn_silu_batch<T, kMaxConvGroup>(items, count, C, G, gamma, beta, eps, fast, stream, status);
 }
 
 template <typename T>
 int launch_gn_silu(const T* x, T* y, long long frames, long long HW, int C, int G, const float* gamma,
-                   const float* beta, float eps, void* scratch, int num_sms, bool fast, cudaStream_t stream) {
+                   const float* beta, float eps, void* scratch, int num_sms, bool fast, cudaStream_t stream,
+                   int* status) {
     (void)num_sms;
     GnItem<T> it{x, y, frames, HW, scratch};
-    return launch_gn_silu_group<T>(&it, 1, C, G, gamma, beta, eps, fast, stream);
+    return launch_gn_silu_group<T>(&it, 1, C, G, gamma, beta, eps, fast, stream, status);
 }
 
 template <typename T>
@@ -398,12 +454,12 @@ template int launch_gn_stats<__nv_bfloat16>(const __nv_bfloat16*, long long, lon
                                             cudaStream_t, float2**, int*, int*);
 
 template int launch_gn_silu<float>(const float*, float*, long long, long long, int, int, const float*, const float*,
-                                   float, void*, int, bool, cudaStream_t);
+                                   float, void*, int, bool, cudaStream_t, int*);
 template int launch_gn_silu<__nv_bfloat16>(const __nv_bfloat16*, __nv_bfloat16*, long long, long long, int, int,
-                                           const float*, const float*, float, void*, int, bool, cudaStream_t);
+                                           const float*, const float*, float, void*, int, bool, cudaStream_t, int*);
 template int launch_gn_silu_group<float>(const GnItem<float>*, int, int, int, const float*, const float*, float, bool,
-                                         cudaStream_t);
+                                         cudaStream_t, int*);
 template int launch_gn_silu_group<__nv_bfloat16>(const GnItem<__nv_bfloat16>*, int, int, int, const float*,
-                                                 const float*, float, bool, cudaStream_t);
+                                                 const float*, float, bool, cudaStream_t, int*);
 
 }  // namespace tok

@@ -43,12 +43,14 @@ struct GnItem {
     const GnTriple* part = nullptr;
     int part_S = 0;
 };
+// status: a context's device status word (bounded waits record a timeout there), or null
 template <typename T>
 int launch_gn_silu_group(const GnItem<T>* items, int count, int C, int G, const float* gamma, const float* beta,
-                         float eps, bool fast, cudaStream_t stream);
+                         float eps, bool fast, cudaStream_t stream, int* status = nullptr);
 template <typename T>
 int launch_gn_silu(const T* x, T* y, long long frames, long long HW, int C, int G, const float* gamma,
-                   const float* beta, float eps, void* scratch, int num_sms, bool fast, cudaStream_t stream);
+                   const float* beta, float eps, void* scratch, int num_sms, bool fast, cudaStream_t stream,
+                   int* status = nullptr);
 
 int launch_fsq(const float* z, long long ntok, const FsqConsts& f, int32_t* idx, float* codes, cudaStream_t s);
 int launch_dequant(const int32_t* idx, long long ntok, const FsqConsts& f, float* codes, cudaStream_t s);

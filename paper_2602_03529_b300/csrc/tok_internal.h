@@ -638,10 +638,10 @@ struct Exec {
         if (c->bf16()) {
             GnItem<__nv_bfloat16> it{static_cast<const __nv_bfloat16*>(in.p), static_cast<__nv_bfloat16*>(out), frames,
                                      HW, w.gn, in.part, in.part_S};
-            ck(launch_gn_silu_group<__nv_bfloat16>(&it, 1, in.C, g.G, g.g, g.b, c->arch.gn_eps, true, s));
+            ck(launch_gn_silu_group<__nv_bfloat16>(&it, 1, in.C, g.G, g.g, g.b, c->arch.gn_eps, true, s, c->d_status));
         } else
             ck(launch_gn_silu<float>(static_cast<const float*>(in.p), static_cast<float*>(out), frames, HW, in.C, g.G,
-                                     g.g, g.b, c->arch.gn_eps, w.gn, c->num_sms, false, s));
+                                     g.g, g.b, c->arch.gn_eps, w.gn, c->num_sms, false, s, c->d_status));
         pend(e, 1, 2.0 * (double)frames * HW * in.C * c->esize(), name);
         c->launches += 3;
         return Act{out, in.N, in.T, in.H, in.W, in.C};
