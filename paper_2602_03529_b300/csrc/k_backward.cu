@@ -207,7 +207,7 @@ __device__ __forceinline__ void unpack(const typename Raw<T>::type& q, float (&v
         v[3] = q.w;
     }
 }
-constexpr int GN_BWD_PF = 2, GN_BWD_MINB = 3;  // GN backward: loads ahead per thread, blocks per SM
+constexpr int GN_BWD_VPT = 8;  // GN backward: 16-byte vectors per thread of a chunk
 
 template <typename T>
 __device__ __forceinline__ void stv(T* p, const float (&v)[V8<T>::N]) {
@@ -259,18 +259,62 @@ struct GnBwdArgs {
     float2* pg;             // [frames][S][G]: (sum g, sum g * xhat) per chunk
     float2* pc;             // [frames][S][C]: (sum dh * xhat, sum dh) per chunk
     float2* gstat;          // [frames][G]: (mean g, mean g * xhat)
+    int* status;
+    unsigned long long wait_ns;
 };
+
+// A chunk's vectors of x, dy (and add) arrive in GN_BWD_SEGS bulk copies per
+// tensor into shared memory (one mbarrier per segment for all tensors), so that
+// each thread works from shared memory while later segments land; 32 KB of
+// every tensor per chunk keeps three blocks per SM.
+constexpr int GN_BWD_SEGS = 4;
+constexpr int GN_BWD_SEG = NT * GN_BWD_VPT * 16 / GN_BWD_SEGS;  // bytes per segment and tensor
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Issue the copies of one chunk (thread 0); returns the chunk's bytes per tensor.
+template <typename T>
+__device__ __forceinline__ long long gn_bwd_stage(const GnBwdArgs<T>& a, long long frame, int chunk, uint8_t* sm,
+                                                  uint64_t* bar, int ntensors) {
+    constexpr int V = V8<T>::N;
+    const long long v0 = (long long)chunk * NT * a.vpt;
+    const long long bytes = min((long long)NT * a.vpt, a.vpf - v0) * 16;
+    const long long e0 = (frame * a.vpf + v0) * V;  // first element of the chunk
+    if (threadIdx.x == 0) {
+        for (int sg = 0; sg < GN_BWD_SEGS; ++sg) mbar_init(&bar[sg], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const T* src[3] = {a.x + e0, a.dy + e0, a.add ? a.add + e0 : nullptr};
+        for (int sg = 0; sg < GN_BWD_SEGS; ++sg) {
+            const long long b = min((long long)GN_BWD_SEG, bytes - (long long)sg * GN_BWD_SEG);
+            if (b <= 0) break;
+            mbar_arrive_expect_tx(&bar[sg], (uint32_t)(b * ntensors));
+            for (int t = 0; t < ntensors; ++t)
+                bulk_g2s(sm + (t * GN_BWD_SEGS + sg) * GN_BWD_SEG, src[t] + (long long)sg * (GN_BWD_SEG / 16) * V,
+                         (uint32_t)b, &bar[sg]);
+        }
+    }
+    return bytes;
+}
 
 // Reduction of one (frame, chunk): per channel (sum dh*xhat, sum dh) combined
 // over the block in a fixed tree order; the group sums follow as gamma-weighted
 // channel sums (sum g = sum_c gamma_c sum dh, sum g*xhat = sum_c gamma_c sum dh*xhat).
-template <typename T, int PF>
-__device__ __forceinline__ void gn_bwd_reduce_unit(const GnBwdArgs<T>& a, long long frame, int chunk,
-                                                   float2 (&redc)[V8<T>::N][NT]) {
+template <typename T>
+__device__ __forceinline__ void gn_bwd_reduce_unit(const GnBwdArgs<T>& a, long long frame, int chunk, uint8_t* sm,
+                                                   uint64_t* bar, float2 (&redc)[V8<T>::N][NT]) {
     constexpr int V = V8<T>::N;
     const int tid = threadIdx.x;
     const int vpv = a.C / V, cg = a.C / a.G;
-    const int c0 = (tid % vpv) * V;
+    const int c0 = (tid % vpv) * V;  // vector i of the chunk holds channels (i % vpv) * V .., i = tid (mod NT)
+    const long long bytes = gn_bwd_stage(a, frame, chunk, sm, bar, 2);
     // xhat = x * rs + xb, h = x * hs + hb (per channel)
     float rs[V], xb[V], hs[V], hb[V];
 #pragma unroll
@@ -283,25 +327,21 @@ __device__ __forceinline__ void gn_bwd_reduce_unit(const GnBwdArgs<T>& a, long l
         hb[j] = fmaf(xb[j], ga, be);
     }
     float sdx[V] = {}, sd[V] = {};
-    const long long base = frame * a.vpf * V;
-    const long long v0 = (long long)chunk * NT * a.vpt;
-    for (int i0 = 0; i0 < a.vpt; i0 += PF) {
-        typename Raw<T>::type rx[PF], rg[PF];
-#pragma unroll
-        for (int u = 0; u < PF; ++u) {
-            const long long vi = v0 + (long long)(i0 + u) * NT + tid;
-            if (i0 + u < a.vpt && vi < a.vpf) {
-                rx[u] = ldraw(a.x + base + vi * V);
-                rg[u] = ldraw(a.dy + base + vi * V);
-            }
+    bool ok = true;
+    for (int sg = 0; sg < GN_BWD_SEGS && ok; ++sg) {
+        const long long b = min((long long)GN_BWD_SEG, bytes - (long long)sg * GN_BWD_SEG);
+        if (b <= 0) break;
+        if (!mbar_wait(&bar[sg], 0, a.status, a.wait_ns)) {
+            ok = false;
+            break;
         }
-#pragma unroll
-        for (int u = 0; u < PF; ++u) {
-            const long long vi = v0 + (long long)(i0 + u) * NT + tid;
-            if (i0 + u >= a.vpt || vi >= a.vpf) break;
+        const uint4* qx = reinterpret_cast<const uint4*>(sm + sg * GN_BWD_SEG);
+        const uint4* qg = reinterpret_cast<const uint4*>(sm + (GN_BWD_SEGS + sg) * GN_BWD_SEG);
+        const int n = (int)(b / 16);
+        for (int i = tid; i < n; i += NT) {
             float xv[V], gv[V];
-            unpack<T>(rx[u], xv);
-            unpack<T>(rg[u], gv);
+            unpack<T>(*reinterpret_cast<const typename Raw<T>::type*>(qx + i), xv);
+            unpack<T>(*reinterpret_cast<const typename Raw<T>::type*>(qg + i), gv);
 #pragma unroll
             for (int j = 0; j < V; ++j) {
                 const float xh = fmaf(xv[j], rs[j], xb[j]);
@@ -341,14 +381,16 @@ __device__ __forceinline__ void gn_bwd_reduce_unit(const GnBwdArgs<T>& a, long l
 }
 
 // dx (+ add) of one (frame, chunk), given the frame's group means gst[g] =
-// (mean g, mean g * xhat); 16-byte vectors.
-template <typename T, int PF>
-__device__ __forceinline__ void gn_bwd_apply_unit(const GnBwdArgs<T>& a, long long frame, int chunk,
-                                                  const float2* gst) {
+// (mean g, mean g * xhat).
+template <typename T>
+__device__ __forceinline__ void gn_bwd_apply_unit(const GnBwdArgs<T>& a, long long frame, int chunk, uint8_t* sm,
+                                                  uint64_t* bar, const float2* gst) {
     constexpr int V = V8<T>::N;
     const int tid = threadIdx.x;
     const int vpv = a.C / V, cg = a.C / a.G;
     const int c0 = (tid % vpv) * V;
+    const int nt = a.add ? 3 : 2;
+    const long long bytes = gn_bwd_stage(a, frame, chunk, sm, bar, nt);
     // h = x * hs + hb; dx = rstd * (dh * gamma - m1 - xhat * m2) = ka * dh + (k0 + k1 * x)
     // with xhat = (x - mean) * rstd
     float hs[V], hb[V], ka[V], k0[V], k1[V];
@@ -365,27 +407,20 @@ __device__ __forceinline__ void gn_bwd_apply_unit(const GnBwdArgs<T>& a, long lo
         k1[j] = -rs * rs * gs.y;
         k0[j] = fmaf(rs * rs * gs.y, mu, -rs * gs.x);
     }
-    const long long base = frame * a.vpf * V;
-    const long long v0 = (long long)chunk * NT * a.vpt;
-    for (int i0 = 0; i0 < a.vpt; i0 += PF) {
-        typename Raw<T>::type rx[PF], rg[PF];
-#pragma unroll
-        for (int u = 0; u < PF; ++u) {
-            const long long vi = v0 + (long long)(i0 + u) * NT + tid;
-            if (i0 + u < a.vpt && vi < a.vpf) {
-                rx[u] = ldraw(a.x + base + vi * V);
-                rg[u] = ldraw(a.dy + base + vi * V);
-            }
-        }
-#pragma unroll
-        for (int u = 0; u < PF; ++u) {
-            const long long vi = v0 + (long long)(i0 + u) * NT + tid;
-            if (i0 + u >= a.vpt || vi >= a.vpf) break;
-            const long long o = base + vi * V;
+    const long long e0 = (frame * a.vpf + (long long)chunk * NT * a.vpt) * V;
+    for (int sg = 0; sg < GN_BWD_SEGS; ++sg) {
+        const long long b = min((long long)GN_BWD_SEG, bytes - (long long)sg * GN_BWD_SEG);
+        if (b <= 0) break;
+        if (!mbar_wait(&bar[sg], 0, a.status, a.wait_ns)) return;
+        const uint4* qx = reinterpret_cast<const uint4*>(sm + sg * GN_BWD_SEG);
+        const uint4* qg = reinterpret_cast<const uint4*>(sm + (GN_BWD_SEGS + sg) * GN_BWD_SEG);
+        const uint4* qa = reinterpret_cast<const uint4*>(sm + (2 * GN_BWD_SEGS + sg) * GN_BWD_SEG);
+        const int n = (int)(b / 16), i0 = sg * (GN_BWD_SEG / 16);
+        for (int i = tid; i < n; i += NT) {
             float xv[V], gv[V], av[V], r[V];
-            unpack<T>(rx[u], xv);
-            unpack<T>(rg[u], gv);
-            if (a.add) ldv(a.add + o, av);
+            unpack<T>(*reinterpret_cast<const typename Raw<T>::type*>(qx + i), xv);
+            unpack<T>(*reinterpret_cast<const typename Raw<T>::type*>(qg + i), gv);
+            if (a.add) unpack<T>(*reinterpret_cast<const typename Raw<T>::type*>(qa + i), av);
 #pragma unroll
             for (int j = 0; j < V; ++j) {
                 const float h = fmaf(xv[j], hs[j], hb[j]);
@@ -394,15 +429,17 @@ __device__ __forceinline__ void gn_bwd_apply_unit(const GnBwdArgs<T>& a, long lo
                 r[j] = fmaf(ka[j], dh, fmaf(k1[j], xv[j], k0[j]));
                 if (a.add) r[j] += av[j];
             }
-            stv(a.dx + o, r);
+            stv(a.dx + e0 + (long long)(i0 + i) * V, r);
         }
     }
 }
 
-template <typename T, int PF, int MINB>
-__global__ void __launch_bounds__(NT, MINB) gn_bwd_reduce_kernel(const __grid_constant__ GnBwdArgs<T> a) {
+template <typename T>
+__global__ void __launch_bounds__(NT, 3) gn_bwd_reduce_kernel(const __grid_constant__ GnBwdArgs<T> a) {
+    extern __shared__ __align__(128) uint8_t sm[];
     __shared__ float2 redc[V8<T>::N][NT];  // [channel slot][thread]: consecutive threads, consecutive banks
-    gn_bwd_reduce_unit<T, PF>(a, blockIdx.y, blockIdx.x, redc);
+    __shared__ uint64_t bar[GN_BWD_SEGS];
+    gn_bwd_reduce_unit<T>(a, blockIdx.y, blockIdx.x, sm, bar, redc);
 }
 
 // Per (frame, group) the chunk sums, one warp each (lanes take chunks lane,
@@ -428,9 +465,11 @@ __global__ void gn_bwd_finalize_kernel(const float2* __restrict__ pg, long long 
     if (lane == 0) gstat[wid] = make_float2(s0 * inv_n, s1 * inv_n);
 }
 
-template <typename T, int PF, int MINB>
-__global__ void __launch_bounds__(NT, MINB) gn_bwd_apply_kernel(const __grid_constant__ GnBwdArgs<T> a) {
-    gn_bwd_apply_unit<T, PF>(a, blockIdx.y, blockIdx.x, a.gstat + (long long)blockIdx.y * a.G);
+template <typename T>
+__global__ void __launch_bounds__(NT, 2) gn_bwd_apply_kernel(const __grid_constant__ GnBwdArgs<T> a) {
+    extern __shared__ __align__(128) uint8_t sm[];
+    __shared__ uint64_t bar[GN_BWD_SEGS];
+    gn_bwd_apply_unit<T>(a, blockIdx.y, blockIdx.x, sm, bar, a.gstat + (long long)blockIdx.y * a.G);
 }
 
 // Per channel over all (frame, chunk) rows, in two steps: blocks of 32 channels
@@ -801,14 +840,32 @@ size_t gn_bwd_scratch_bytes(long long frames, int S, int C, int G) {
            256;
 }
 
-// stats: (mean, rstd) per (frame, group) from the forward statistics pass.
+int gn_bwd_vectors_per_thread() { return GN_BWD_VPT; }
+int gn_bwd_chunks_per_frame(long long HW, int C, int vec) {
+    const long long vpf = HW * C / vec;
+    return (int)std::max<long long>(1, (vpf + (long long)NT * GN_BWD_VPT - 1) / ((long long)NT * GN_BWD_VPT));
+}
+
+// stats: (mean, rstd) per (frame, group) from the forward statistics pass;
+// S chunks of NT * vpt vectors per frame (vpt <= GN_BWD_VPT).
 template <typename T>
 int launch_gn_silu_bwd(const T* x, const T* dy, const float2* stats, const float* gamma, const float* beta,
                        const T* add, long long frames, long long HW, int C, int G, int vpt, int S, void* scratch,
-                       float* dgamma, float* dbeta, T* dx, cudaStream_t s) {
+                       float* dgamma, float* dbeta, T* dx, int* status, unsigned long long wait_ns, cudaStream_t s) {
     constexpr int V = V8<T>::N;
     const int vpv = C / V;
-    if (C % V || C % G || vpv > NT || (vpv & (vpv - 1))) return (int)cudaErrorInvalidValue;
+    if (C % V || C % G || vpv > NT || (vpv & (vpv - 1)) || vpt < 1 || vpt > GN_BWD_VPT ||
+        (long long)S * NT * vpt < HW * C / V)
+        return (int)cudaErrorInvalidValue;
+    static bool ready = false;
+    if (!ready) {
+        if (cudaFuncSetAttribute(gn_bwd_reduce_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 2 * GN_BWD_SEGS * GN_BWD_SEG) != cudaSuccess ||
+            cudaFuncSetAttribute(gn_bwd_apply_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 3 * GN_BWD_SEGS * GN_BWD_SEG) != cudaSuccess)
+            return (int)cudaGetLastError();
+        ready = true;
+    }
     GnBwdArgs<T> a;
     a.x = x;
     a.dy = dy;
@@ -826,23 +883,25 @@ int launch_gn_silu_bwd(const T* x, const T* dy, const float2* stats, const float
     a.pg = static_cast<float2*>(scratch);
     a.pc = a.pg + frames * S * G;
     a.gstat = a.pc + frames * S * C;
+    a.status = status;
+    a.wait_ns = wait_ns;
     float2* q = a.gstat + frames * G;
     const dim3 grid(S, (unsigned)frames);
-    gn_bwd_reduce_kernel<T, GN_BWD_PF, GN_BWD_MINB><<<grid, NT, 0, s>>>(a);
+    gn_bwd_reduce_kernel<T><<<grid, NT, 2 * GN_BWD_SEGS * GN_BWD_SEG, s>>>(a);
     gn_bwd_finalize_kernel<<<blocks_for(frames * G * 32, 256), 256, 0, s>>>(a.pg, frames, S, G,
                                                                            1.f / (float)(HW * (C / G)), a.gstat);
     gn_bwd_channel_kernel<<<dim3((C + 31) / 32, GN_BANDS), 256, 0, s>>>(a.pc, frames * S, C, q);
     gn_bwd_channel_final_kernel<<<blocks_for((long long)C * 32, 256), 256, 0, s>>>(q, C, dgamma, dbeta);
-    gn_bwd_apply_kernel<T, GN_BWD_PF, GN_BWD_MINB><<<grid, NT, 0, s>>>(a);
+    gn_bwd_apply_kernel<T><<<grid, NT, (add ? 3 : 2) * GN_BWD_SEGS * GN_BWD_SEG, s>>>(a);
     return (int)cudaGetLastError();
 }
 template int launch_gn_silu_bwd<float>(const float*, const float*, const float2*, const float*, const float*,
                                        const float*, long long, long long, int, int, int, int, void*, float*, float*,
-                                       float*, cudaStream_t);
+                                       float*, int*, unsigned long long, cudaStream_t);
 template int launch_gn_silu_bwd<__nv_bfloat16>(const __nv_bfloat16*, const __nv_bfloat16*, const float2*,
                                                const float*, const float*, const __nv_bfloat16*, long long, long long,
                                                int, int, int, int, void*, float*, float*, __nv_bfloat16*,
-                                               cudaStream_t);
+                                               int*, unsigned long long, cudaStream_t);
 
 template <typename T>
 int launch_ste_bwd(const T* dcodes, int Cd, const float* z, const uint32_t* keep_bits, long long ntok, int Wq,

@@ -126,7 +126,11 @@ int gn_vectors_per_thread();  // k_norm.cu
 template <typename T>
 int launch_gn_silu_bwd(const T* x, const T* dy, const float2* stats, const float* gamma, const float* beta,
                        const T* add, long long frames, long long HW, int C, int G, int vpt, int S, void* scratch,
-                       float* dgamma, float* dbeta, T* dx, cudaStream_t s);
+                       float* dgamma, float* dbeta, T* dx, int* status, unsigned long long wait_ns,
+                       cudaStream_t s);
+// chunking of the GroupNorm backward (k_backward.cu)
+int gn_bwd_vectors_per_thread();
+int gn_bwd_chunks_per_frame(long long HW, int C, int vec);
 template <typename T>
 int launch_ste_bwd(const T* dcodes, int Cd, const float* z, const uint32_t* keep_bits, long long ntok, int Wq,
                    const FsqConsts& f, T* dz, int Co, cudaStream_t s);

@@ -91,7 +91,8 @@ TrainBufs train_layout(const tok_ctx* c, int N, int T, int H, int W, char* base)
         {
             const long long hw = (long long)(H >> (l + 1)) * (W >> (l + 1));
             const int cmax = std::max(a.ch[l], cin0), vec = c->bf16() ? 8 : 4;
-            const int smax = std::max(gn_chunks_per_frame(hw, a.ch[l], vec), gn_chunks_per_frame(hw, cin0, vec));
+            const int smax =
+                std::max(gn_bwd_chunks_per_frame(hw, a.ch[l], vec), gn_bwd_chunks_per_frame(hw, cin0, vec));
             gn = std::max(gn, gn_bwd_scratch_bytes((long long)N * Tl[l], smax, cmax, std::max(a.gn_groups, 1)));
         }
         if (l > 0) {
@@ -430,17 +431,18 @@ struct TrainExec : Exec {
         // the forward's statistics, kept in this GroupNorm's scratch
         const int vec = c->bf16() ? 8 : 4;
         const float2* stats = gn_stats_of_scratch(b.gn_sc.at(name), frames, HW, x.C, g.G, vec);
-        const int vpt = gn_vectors_per_thread(), S = gn_chunks_per_frame(HW, x.C, vec);
+        const int vpt = gn_bwd_vectors_per_thread(), S = gn_bwd_chunks_per_frame(HW, x.C, vec);
         const int e = pbegin();
         if (c->bf16()) {
             ck(launch_gn_silu_bwd<__nv_bfloat16>(
                 static_cast<const __nv_bfloat16*>(x.p), static_cast<const __nv_bfloat16*>(dy), stats, g.g, g.b,
                 static_cast<const __nv_bfloat16*>(add), frames, HW, x.C, g.G, vpt, S, b.gnb, grads + g.og,
-                grads + g.ob, static_cast<__nv_bfloat16*>(dx), s));
+                grads + g.ob, static_cast<__nv_bfloat16*>(dx), c->d_status, kWaitNs, s));
         } else {
             ck(launch_gn_silu_bwd<float>(static_cast<const float*>(x.p), static_cast<const float*>(dy), stats, g.g,
                                          g.b, static_cast<const float*>(add), frames, HW, x.C, g.G, vpt, S, b.gnb,
-                                         grads + g.og, grads + g.ob, static_cast<float*>(dx), s));
+                                         grads + g.og, grads + g.ob, static_cast<float*>(dx), c->d_status, kWaitNs,
+                                         s));
         }
         pend(e, 1, 4.0 * (double)frames * HW * x.C * c->esize(), name + ".bwd");
         c->launches += 5;
