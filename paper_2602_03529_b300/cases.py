@@ -71,19 +71,41 @@ def downsample(N: int, T: int, H: int, W: int, s: int) -> None:
     print("downsample ok", tuple(y.shape))
 
 
+def select(N: int, T: int, H: int, W: int) -> None:
+    """Token selection over N streams x T P latent frames of H x W tokens (half of the P
+    tokens equal to the I token at their position), drop rate 0.25."""
+    import numpy as np
+    import torch
+
+    from . import similarity_mask
+
+    rng = np.random.default_rng(5)
+    ii = rng.integers(0, 64000, (N, 1, H, W))
+    ip = np.where(rng.random((N, T, H, W)) < 0.5, np.repeat(ii, T, axis=1), rng.integers(0, 64000, (N, T, H, W)))
+    dp = torch.from_numpy(ip.astype(np.int32)).cuda()
+    di = torch.from_numpy(ii.astype(np.int32)).cuda()
+    for _ in range(3):
+        out, kb, _ = similarity_mask(dp, di, 0.25)
+    torch.cuda.synchronize()
+    print("select ok", tuple(out.shape), int((out == 32036).sum()))
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["clip", "train", "downsample"])
+    ap.add_argument("case", choices=["clip", "train", "downsample", "select"])
     ap.add_argument("--N", type=int)
     ap.add_argument("--T", type=int)
     ap.add_argument("--H", type=int)
     ap.add_argument("--W", type=int)
     ap.add_argument("--s", type=int, default=3)
     a = ap.parse_args()
-    dflt = {"clip": (1, 5, 720, 1280), "train": (2, 17, 256, 256), "downsample": (4, 17, 1080, 1920)}[a.case]
+    dflt = {"clip": (1, 5, 720, 1280), "train": (2, 17, 256, 256), "downsample": (4, 17, 1080, 1920),
+            "select": (256, 4, 90, 160)}[a.case]
     shape = [v if v is not None else d for v, d in zip((a.N, a.T, a.H, a.W), dflt)]
     if a.case == "downsample":
         downsample(*shape, a.s)
+    elif a.case == "select":
+        select(*shape)
     else:
         (clip if a.case == "clip" else train)(*shape)
 
