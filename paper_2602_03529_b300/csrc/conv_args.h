@@ -106,6 +106,10 @@ struct WgradArgs {
     int K;                            // taps * Cin
     long long V;                      // N * Tout * Hout * Wout
     long long vchunk;                 // voxels per split
+    // dw rows (narrow 3x3x3 stride-1 layers): dY holds the three w-shifted copies of
+    // the gradient as rows dw * 16 + co (Cout = 48 rows, cout_real real channels), and a
+    // CTA slot is dt alone
+    int dwrows, cout_real;
 };
 
 }  // namespace tok

@@ -107,9 +107,10 @@ __global__ void __launch_bounds__(192, 1)
     const int split = (int)(t / g.taps);
     const long long v_begin = (long long)split * g.vtiles / g.S, v_end = (long long)(split + 1) * g.vtiles / g.S;
     // halo form: `tap` is the (dt, dw) slot; dh = 0, 1, 2 are the three accumulators
-    const int dw = HT ? tap % 3 : tap % a.kw;
+    // (dw rows: `tap` is dt, the X box unshifted, the dw taps in the rows of dY)
+    const int dw = a.dwrows ? 1 : HT ? tap % 3 : tap % a.kw;
     const int dh = HT ? 0 : (tap / a.kw) % a.kh;
-    const int dt = HT ? tap / 3 : tap / (a.kw * a.kh);
+    const int dt = a.dwrows ? tap : HT ? tap / 3 : tap / (a.kw * a.kh);
     const int a_boxes = (mt * 128 + 64 < a.Cout) ? 2 : 1;
     const int b_boxes = min(BN / 64, (a.Cin - nt * BN) / 64);
     const int xrows = HT ? (g.BH + 2) * g.BW : KV;  // rows of one X box
@@ -269,15 +270,22 @@ __global__ void __launch_bounds__(192, 1)
                                                           __uint_as_float(r[k][4 * i + 3]));
                 }
                 __syncwarp();
-                const long long row0 = (long long)split * a.Cout + mt * 128 + q * 32;
-                float* P = part + row0 * a.K + (long long)tp * a.Cin + nt * BN;
                 for (int rr = 0; rr < 32; ++rr) {
-                    if (mt * 128 + q * 32 + rr >= a.Cout) break;
+                    const int r = mt * 128 + q * 32 + rr;  // accumulator row
+                    if (r >= a.Cout) break;
+                    // output channel and tap of the row (dw rows: r = dw * 16 + co)
+                    int co = r, tpr = tp;
+                    if (a.dwrows) {
+                        co = r % 16;
+                        tpr = (dt * 3 + d) * 3 + r / 16;
+                        if (co >= a.cout_real) continue;
+                    }
+                    float* P = part + ((long long)split * (a.dwrows ? a.cout_real : a.Cout) + co) * a.K +
+                               (long long)tpr * a.Cin + nt * BN;
 #pragma unroll
                     for (int c = 4 * lane; c < BN; c += 128)
                         if (c < n_valid)
-                            *reinterpret_cast<float4*>(P + (long long)rr * a.K + c) =
-                                *reinterpret_cast<const float4*>(buf + rr * RS + c);
+                            *reinterpret_cast<float4*>(P + c) = *reinterpret_cast<const float4*>(buf + rr * RS + c);
                 }
                 __syncwarp();
             }
@@ -339,6 +347,21 @@ __global__ void colsum_reduce_kernel(const float* __restrict__ part, int chunks,
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if (lane == 0) db[co] = s;
+}
+
+// dY of a narrow layer as three w-shifted copies: out[v][dw * 16 + co] = dY at
+// (v with w - (dw - 1)) channel co, zero outside the frame, past Cout and in
+// channels 48..63 (out row pitch 64).
+__global__ void dy_dwrows_kernel(const __nv_bfloat16* __restrict__ dy, long long V, int W, int Cdy, int Cout,
+                                 __nv_bfloat16* __restrict__ out) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= V * 64) return;
+    const long long v = t / 64;
+    const int j = (int)(t % 64), dwv = j / 16, co = j % 16;
+    const int w = (int)(v % W), ws = w - (dwv - 1);
+    __nv_bfloat16 val = __float2bfloat16_rn(0.f);
+    if (dwv < 3 && co < Cout && ws >= 0 && ws < W) val = dy[(v - (dwv - 1)) * Cdy + co];
+    out[t] = val;
 }
 
 __global__ void partial_reduce_kernel(const float* __restrict__ part, int S, long long n, float* __restrict__ out) {
@@ -439,9 +462,26 @@ int launch_wgrad_tc(const __nv_bfloat16* dy, const __nv_bfloat16* x, const Wgrad
     g.tiles_h = (a.Hout + g.BH - 1) / g.BH;
     g.vtiles = (long long)a.N * a.Tout * g.tiles_h * g.tiles_w;
     const int BN = (!ht && a.Cin % 256 == 0) ? 256 : 128;
-    g.m_tiles = (a.Cout + 127) / 128;
+    // a narrow stride-1 3x3x3 layer runs with its dw taps as rows of a shifted copy of
+    // dY (one CTA slot per dt instead of per (dt, dw)); the copy sits at the end of the
+    // partials buffer
+    WgradArgs ar = a;
+    ar.dwrows = 0;
+    ar.cout_real = a.Cout;
+    const __nv_bfloat16* dyk = dy;
+    const size_t dy3_floats = ((size_t)a.V * 64 * 2 + 255) / 256 * 64;  // bf16 copy, in floats, 256-byte granules
+    if (ht && a.kt == 3 && a.st == 1 && a.Cout <= 16 && k_valid <= 0 && dy3_floats < max_floats / 2) {
+        __nv_bfloat16* dy3 = reinterpret_cast<__nv_bfloat16*>(part + (max_floats - dy3_floats) / 64 * 64);
+        dy_dwrows_kernel<<<blocks_for(a.V * 64, 256), 256, 0, s>>>(dy, a.V, a.Wout, a.Cdy, a.Cout, dy3);
+        max_floats = (max_floats - dy3_floats) / 64 * 64;
+        ar.dwrows = 1;
+        ar.Cout = 48;
+        ar.Cdy = 64;
+        dyk = dy3;
+    }
+    g.m_tiles = (ar.Cout + 127) / 128;
     g.n_tiles = (a.Cin + BN - 1) / BN;
-    g.taps = ht ? a.kt * a.kw : a.kt * a.kh * a.kw;
+    g.taps = ar.dwrows ? a.kt : ht ? a.kt * a.kw : a.kt * a.kh * a.kw;
     const long long out_tiles = (long long)g.m_tiles * g.n_tiles * g.taps;
     // split count: at least 4 voxel tiles per split, partials within max_floats;
     // time ~ waves x (voxel tiles per split + a CTA's fixed cost), the fixed cost
@@ -462,9 +502,9 @@ int launch_wgrad_tc(const __nv_bfloat16* dy, const __nv_bfloat16* x, const Wgrad
     }
     if ((size_t)S * a.Cout * a.K > max_floats) return -1;
     g.S = (int)S;
-    int e = ht ? launch_bn<128, true>(dy, x, a, g, part, status, wait_ns, s)
-               : (BN == 256) ? launch_bn<256, false>(dy, x, a, g, part, status, wait_ns, s)
-                             : launch_bn<128, false>(dy, x, a, g, part, status, wait_ns, s);
+    int e = ht ? launch_bn<128, true>(dyk, x, ar, g, part, status, wait_ns, s)
+               : (BN == 256) ? launch_bn<256, false>(dyk, x, ar, g, part, status, wait_ns, s)
+                             : launch_bn<128, false>(dyk, x, ar, g, part, status, wait_ns, s);
     if (e) return e;
     const long long n = (long long)a.Cout * a.K;
     if (k_valid > 0 && k_valid < a.K)

@@ -106,7 +106,10 @@ def test_conv3d_parity(P, prec, case):
 
 @pytest.mark.parametrize("prec", ["fp32", "bf16"])
 @pytest.mark.parametrize("shape,G", [((1, 3, 16, 16, 128), 32), ((2, 2, 8, 12, 256), 32),
-                                     ((1, 2, 4, 4, 512), 32), ((1, 3, 5, 7, 16), 8), ((1, 2, 9, 9, 64), 32)])
+                                     ((1, 2, 4, 4, 512), 32), ((1, 3, 5, 7, 16), 8), ((1, 2, 9, 9, 64), 32),
+                                     # a chunk's last bulk-copy segment partly filled; frames of
+                                     # several chunks with a ragged last one
+                                     ((1, 2, 10, 13, 128), 32), ((2, 3, 40, 60, 128), 32)])
 def test_groupnorm_silu_parity(P, prec, shape, G):
     rng = np.random.default_rng(7)
     x = (rng.standard_normal(shape) * 2 + 0.5).astype(np.float32)
