@@ -1313,7 +1313,7 @@ int conv_tc_taprows(int Cout, int Cin, int k, int sh, int sw) {
 // depth-to-space, bf16), for groups of 4, 8 or 16 channels, of 3x3x3 layers:
 // a layer with a short K loop (1x1x1, the stem over its im2col matrix) is
 // bound by its epilogue, where the extra work costs more than the statistics
-// pass it would save.
+// pass it would save (720p stem: conv 0.63 -> 0.98 ms against 0.23 ms saved).
 bool conv_tc_gn_fusable(const ConvArgs& a) {
     const ConvRoute r = conv_route(a);
     return r.swap && !r.narrow && a.kh == 3 && (a.mode == OUT_PLAIN || a.mode == OUT_D2S) && !a.out_fp32 &&
