@@ -30,6 +30,12 @@
 // voxel row dh * BW on, a whole number of 8-row (1 KB) groups, so its operand
 // descriptor starts there and the two 64-channel halves of X lie one halo box
 // apart (the leading byte offset). X bytes per MMA drop about 2.4-fold.
+//
+// The bias gradient stays a separate column-sum pass over dY (~5 TB/s): taking
+// it inside this kernel, in the CTAs of one tap slot, lengthened the launch's
+// single wave more than the pass costs (extra M = 128, N = 16 MMAs against a
+// tile of ones: +15-23%; the epilogue warps summing each dY stage before its
+// release: +18-25%).
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -351,17 +357,28 @@ __global__ void colsum_reduce_kernel(const float* __restrict__ part, int chunks,
 
 // dY of a narrow layer as three w-shifted copies: out[v][dw * 16 + co] = dY at
 // (v with w - (dw - 1)) channel co, zero outside the frame, past Cout and in
-// channels 48..63 (out row pitch 64).
+// channels 48..63 (out row pitch 64). A thread writes one 16-byte group of 8
+// channels (Cdy a multiple of 8, dY rows 16-byte aligned).
 __global__ void dy_dwrows_kernel(const __nv_bfloat16* __restrict__ dy, long long V, int W, int Cdy, int Cout,
                                  __nv_bfloat16* __restrict__ out) {
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= V * 64) return;
-    const long long v = t / 64;
-    const int j = (int)(t % 64), dwv = j / 16, co = j % 16;
+    if (t >= V * 8) return;
+    const long long v = t >> 3;
+    const int grp = (int)(t & 7), dwv = grp >> 1, co0 = (grp & 1) * 8;
     const int w = (int)(v % W), ws = w - (dwv - 1);
-    __nv_bfloat16 val = __float2bfloat16_rn(0.f);
-    if (dwv < 3 && co < Cout && ws >= 0 && ws < W) val = dy[(v - (dwv - 1)) * Cdy + co];
-    out[t] = val;
+    uint4 q = make_uint4(0u, 0u, 0u, 0u);
+    if (dwv < 3 && co0 < Cout && ws >= 0 && ws < W) {
+        q = *reinterpret_cast<const uint4*>(dy + (v - (dwv - 1)) * Cdy + co0);
+        // channels past Cout read as zero
+        uint32_t u[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (co0 + 2 * i >= Cout) u[i] = 0u;
+            else if (co0 + 2 * i + 1 >= Cout) u[i] &= 0xFFFFu;
+        }
+        q = make_uint4(u[0], u[1], u[2], u[3]);
+    }
+    reinterpret_cast<uint4*>(out)[t] = q;
 }
 
 __global__ void partial_reduce_kernel(const float* __restrict__ part, int S, long long n, float* __restrict__ out) {
@@ -472,7 +489,7 @@ int launch_wgrad_tc(const __nv_bfloat16* dy, const __nv_bfloat16* x, const Wgrad
     const size_t dy3_floats = ((size_t)a.V * 64 * 2 + 255) / 256 * 64;  // bf16 copy, in floats, 256-byte granules
     if (ht && a.kt == 3 && a.st == 1 && a.Cout <= 16 && k_valid <= 0 && dy3_floats < max_floats / 2) {
         __nv_bfloat16* dy3 = reinterpret_cast<__nv_bfloat16*>(part + (max_floats - dy3_floats) / 64 * 64);
-        dy_dwrows_kernel<<<blocks_for(a.V * 64, 256), 256, 0, s>>>(dy, a.V, a.Wout, a.Cdy, a.Cout, dy3);
+        dy_dwrows_kernel<<<blocks_for(a.V * 8, 256), 256, 0, s>>>(dy, a.V, a.Wout, a.Cdy, a.Cout, dy3);
         max_floats = (max_floats - dy3_floats) / 64 * 64;
         ar.dwrows = 1;
         ar.Cout = 48;
