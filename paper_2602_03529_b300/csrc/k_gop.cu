@@ -56,11 +56,31 @@ __global__ void tloss_partial_kernel(const float* __restrict__ xc, const float* 
     const float* a = xc + (s * Tc + i) * E;
     const float* b = xp + (s * Tp + (Tp - n + i)) * E;
     float acc = 0.f;  // 16 squares in float32, then FP64 across the block
-    for (int j = 0; j < LPER; ++j) {
-        const long long e = ch * LCHUNK + (long long)j * LT + threadIdx.x;
-        if (e < E) {
-            const float d = a[e] - b[e];
-            acc = fmaf(d, d, acc);
+    if ((E & 3) == 0 && ((reinterpret_cast<uintptr_t>(xc) | reinterpret_cast<uintptr_t>(xp)) & 15u) == 0) {
+        // four float4 per thread, all requested before use (thread covers 4 runs of 4)
+        float4 va[LPER / 4], vb[LPER / 4];
+#pragma unroll
+        for (int j = 0; j < LPER / 4; ++j) {
+            const long long e = ch * LCHUNK + ((long long)j * LT + threadIdx.x) * 4;
+            va[j] = e < E ? *reinterpret_cast<const float4*>(a + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+            vb[j] = e < E ? *reinterpret_cast<const float4*>(b + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int j = 0; j < LPER / 4; ++j) {
+            const float d0 = va[j].x - vb[j].x, d1 = va[j].y - vb[j].y, d2 = va[j].z - vb[j].z,
+                        d3 = va[j].w - vb[j].w;
+            acc = fmaf(d0, d0, acc);
+            acc = fmaf(d1, d1, acc);
+            acc = fmaf(d2, d2, acc);
+            acc = fmaf(d3, d3, acc);
+        }
+    } else {
+        for (int j = 0; j < LPER; ++j) {
+            const long long e = ch * LCHUNK + (long long)j * LT + threadIdx.x;
+            if (e < E) {
+                const float d = a[e] - b[e];
+                acc = fmaf(d, d, acc);
+            }
         }
     }
     red[threadIdx.x] = (double)acc;
@@ -98,6 +118,24 @@ __global__ void tloss_sum_kernel(const double* __restrict__ norms, long long pai
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if (lane == 0) *loss = (float)(acc / (double)Nn);
+}
+
+// the same, four elements per thread (E % 4 == 0, 16-byte aligned frames)
+__global__ void tloss_grad4_kernel(const float4* __restrict__ xc, const float4* __restrict__ xp, int Tc, int Tp,
+                                   long long E4, int n, long long N, const float* __restrict__ scale,
+                                   float4* __restrict__ g) {
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N * Tc * E4) return;
+    const long long e = k % E4;
+    const int t = (int)((k / E4) % Tc);
+    const long long s = k / (E4 * Tc);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (t < n) {
+        const float4 c = xc[k], p = xp[(s * Tp + (Tp - n + t)) * E4 + e];
+        const float sc = scale[s * n + t];
+        v = make_float4((c.x - p.x) * sc, (c.y - p.y) * sc, (c.z - p.z) * sc, (c.w - p.w) * sc);
+    }
+    g[k] = v;
 }
 
 __global__ void tloss_grad_kernel(const float* __restrict__ xc, const float* __restrict__ xp, int Tc, int Tp,
@@ -146,7 +184,14 @@ int launch_temporal_loss(const float* xc, const float* xp, long long N, int Tc, 
     tloss_partial_kernel<<<(unsigned)(N * n * chunks), LT, 0, s>>>(xc, xp, Tc, Tp, E, n, chunks, part);
     tloss_norm_kernel<<<blocks_for(N * n * 32, 256), 256, 0, s>>>(part, N * n, chunks, N * n, scale, norms);
     tloss_sum_kernel<<<1, 32, 0, s>>>(norms, N * n, N * n, loss);
-    if (grad) tloss_grad_kernel<<<blocks_for(N * Tc * E, 256), 256, 0, s>>>(xc, xp, Tc, Tp, E, n, N, scale, grad);
+    const bool vec4 = E % 4 == 0 && ((reinterpret_cast<uintptr_t>(xc) | reinterpret_cast<uintptr_t>(xp) |
+                                      reinterpret_cast<uintptr_t>(grad)) & 15u) == 0;
+    if (grad && vec4)
+        tloss_grad4_kernel<<<blocks_for(N * Tc * E / 4, 256), 256, 0, s>>>(
+            reinterpret_cast<const float4*>(xc), reinterpret_cast<const float4*>(xp), Tc, Tp, E / 4, n, N, scale,
+            reinterpret_cast<float4*>(grad));
+    else if (grad)
+        tloss_grad_kernel<<<blocks_for(N * Tc * E, 256), 256, 0, s>>>(xc, xp, Tc, Tp, E, n, N, scale, grad);
     return (int)cudaGetLastError();
 }
 

@@ -91,16 +91,29 @@ __global__ void residual_mean4_kernel(const T* __restrict__ x, const float* __re
 
 constexpr int CH_THREADS = 256, CH_PER = 16, CHUNK = CH_THREADS * CH_PER;
 
-// nonzero count of every CHUNK-element chunk of every segment
+// nonzero count of every CHUNK-element chunk of every segment (16-byte loads when
+// the segment is 16-byte aligned: E % 4 == 0)
 __global__ void count_kernel(const float* __restrict__ r, long long E, long long chunks, long long* __restrict__ cnt) {
     __shared__ int red[CH_THREADS];
     const long long seg = blockIdx.x / chunks, ch = blockIdx.x % chunks;
     const long long base = seg * E + ch * CHUNK;
     const long long lim = min((long long)CHUNK, E - ch * CHUNK);
     int c = 0;
-    for (int j = 0; j < CH_PER; ++j) {
-        const long long l = (long long)j * CH_THREADS + threadIdx.x;
-        if (l < lim && r[base + l] != 0.f) ++c;
+    if ((E & 3) == 0 && (reinterpret_cast<uintptr_t>(r) & 15u) == 0) {
+        float4 v[CH_PER / 4];
+#pragma unroll
+        for (int j = 0; j < CH_PER / 4; ++j) {
+            const long long l = ((long long)j * CH_THREADS + threadIdx.x) * 4;
+            v[j] = l < lim ? *reinterpret_cast<const float4*>(r + base + l) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int j = 0; j < CH_PER / 4; ++j)
+            c += (v[j].x != 0.f) + (v[j].y != 0.f) + (v[j].z != 0.f) + (v[j].w != 0.f);
+    } else {
+        for (int j = 0; j < CH_PER; ++j) {
+            const long long l = (long long)j * CH_THREADS + threadIdx.x;
+            if (l < lim && r[base + l] != 0.f) ++c;
+        }
     }
     red[threadIdx.x] = c;
     __syncthreads();
@@ -136,38 +149,48 @@ __global__ void scan_kernel(long long* __restrict__ cnt, long long n) {
     if (threadIdx.x == 0) cnt[n] = carry;
 }
 
-// position-ordered scatter of the nonzeros of every chunk
+// position-ordered scatter of the nonzeros of every chunk: CH_PER steps of
+// CH_THREADS consecutive elements (coalesced), a warp ballot for the order within
+// a warp and a scan of the warps' counts for the order across the block
 __global__ void scatter_kernel(const float* __restrict__ r, long long E, long long chunks,
                                const long long* __restrict__ off, int32_t* __restrict__ pos,
                                float* __restrict__ val) {
-    __shared__ int scan[CH_THREADS];
+    constexpr int NW = CH_THREADS / 32;
+    __shared__ int wcnt[CH_PER][NW];
     const long long seg = blockIdx.x / chunks, ch = blockIdx.x % chunks;
     const long long base = seg * E + ch * CHUNK;
     const long long lim = min((long long)CHUNK, E - ch * CHUNK);
-    // each thread owns CH_PER consecutive elements of the chunk
-    const long long l0 = (long long)threadIdx.x * CH_PER;
-    int c = 0;
-    for (int j = 0; j < CH_PER; ++j)
-        if (l0 + j < lim && r[base + l0 + j] != 0.f) ++c;
-    scan[threadIdx.x] = c;
-    __syncthreads();
-    for (int o = 1; o < CH_THREADS; o <<= 1) {
-        const int add = threadIdx.x >= o ? scan[threadIdx.x - o] : 0;
-        __syncthreads();
-        scan[threadIdx.x] += add;
-        __syncthreads();
-    }
-    long long w = off[blockIdx.x] + scan[threadIdx.x] - c;
+    const int lane = threadIdx.x % 32, warp = threadIdx.x / 32;
+    float v[CH_PER];
+    uint32_t bal[CH_PER];
+#pragma unroll
     for (int j = 0; j < CH_PER; ++j) {
-        const long long l = l0 + j;
-        if (l < lim) {
-            const float v = r[base + l];
-            if (v != 0.f) {
-                pos[w] = (int32_t)(ch * CHUNK + l);
-                val[w] = v;
-                ++w;
-            }
+        const long long l = (long long)j * CH_THREADS + threadIdx.x;
+        v[j] = l < lim ? r[base + l] : 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < CH_PER; ++j) {
+        bal[j] = __ballot_sync(0xffffffffu, v[j] != 0.f);
+        if (lane == 0) wcnt[j][warp] = __popc(bal[j]);
+    }
+    __syncthreads();
+    // nonzeros before (step j, warp): all of steps < j, then warps < warp of step j
+    long long w = off[blockIdx.x];
+#pragma unroll
+    for (int j = 0; j < CH_PER; ++j) {
+        int before = 0, step = 0;
+#pragma unroll
+        for (int k = 0; k < NW; ++k) {
+            const int cnt = wcnt[j][k];
+            before += k < warp ? cnt : 0;
+            step += cnt;
         }
+        if (v[j] != 0.f) {
+            const long long d = w + before + __popc(bal[j] & ((1u << lane) - 1u));
+            pos[d] = (int32_t)(ch * CHUNK + (long long)j * CH_THREADS + threadIdx.x);
+            val[d] = v[j];
+        }
+        w += step;
     }
 }
 
@@ -195,9 +218,19 @@ __global__ void apply_kernel(float* __restrict__ xh, long long N, int Tf, long l
     const int k = (int)(lo % nwin);
     const int t0 = k * window, t1 = min(t0 + window, Tf);
     const float v = val[i];
-    for (int t = t0; t < t1; ++t) {
-        float* p = xh + (n * Tf + t) * E + pos[i];
-        *p = __fadd_rn(*p, v);
+    float* const p0 = xh + (n * Tf + t0) * E + pos[i];
+    // the window's frames are E apart (distinct elements): read them all, then write
+    constexpr int MAXW = 8;
+    if (t1 - t0 <= MAXW) {
+        float a[MAXW];
+#pragma unroll
+        for (int t = 0; t < MAXW; ++t)
+            if (t < t1 - t0) a[t] = p0[(long long)t * E];
+#pragma unroll
+        for (int t = 0; t < MAXW; ++t)
+            if (t < t1 - t0) p0[(long long)t * E] = __fadd_rn(a[t], v);
+    } else {
+        for (int t = 0; t < t1 - t0; ++t) p0[(long long)t * E] = __fadd_rn(p0[(long long)t * E], v);
     }
 }
 
