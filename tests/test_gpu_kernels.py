@@ -128,6 +128,26 @@ def test_groupnorm_silu_parity(P, prec, shape, G):
     assert np.all(err <= tol), float(err.max())
 
 
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_groupnorm_silu_in_place(P, prec):
+    """y may alias x: every chunk is in shared memory before any of its outputs is
+    written (frames of several chunks, a ragged last one)."""
+    rng = np.random.default_rng(11)
+    shape, G = (2, 2, 40, 60, 128), 32
+    x = (rng.standard_normal(shape) * 2 + 0.5).astype(np.float32)
+    if prec == "bf16":
+        x = S.to_bf16_f32(x)
+    ref = ops.silu(ops.group_norm_frames(x, G, 1e-6, None, None))
+    dt = torch.bfloat16 if prec == "bf16" else torch.float32
+    xd = _dev(x, dt)
+    y = P.groupnorm_silu(xd, G, None, None, 1e-6, out=xd)
+    torch.cuda.synchronize()
+    assert y.data_ptr() == xd.data_ptr()
+    g = xd.float().cpu().numpy()
+    tol = (1e-5 * (np.abs(ref) + 1.0)) if prec == "fp32" else (2.0 ** -8 * np.abs(ref) + 4e-3)
+    assert np.all(np.abs(g - ref) <= tol), float(np.abs(g - ref).max())
+
+
 def test_fsq_parity_with_tie_band(P):
     rng = np.random.default_rng(11)
     z = (rng.standard_normal((1 << 20, 6)) * 1.5).astype(np.float32)
