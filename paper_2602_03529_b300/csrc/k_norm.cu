@@ -312,12 +312,6 @@ void gn_plan(long long frames, long long vec_per_frame, int num_sms, int* vpt, i
 
 }  // namespace
 
-int gn_chunks_per_frame(long long HW, int C, int vec) {
-    int vpt, S;
-    gn_plan(1, HW * C / vec, 0, &vpt, &S);
-    return S;
-}
-
 // Where a forward launch left the (mean, rstd) of every (frame, group) in its scratch.
 float2* gn_stats_of_scratch(void* scratch, long long frames, long long HW, int C, int G, int vec) {
     int vpt, S;
@@ -325,8 +319,6 @@ float2* gn_stats_of_scratch(void* scratch, long long frames, long long HW, int C
     Triple* own = static_cast<Triple*>(scratch);
     return reinterpret_cast<float2*>((reinterpret_cast<uintptr_t>(own + frames * S * G) + 15) & ~uintptr_t(15));
 }
-
-int gn_vectors_per_thread() { return GN_VPT; }
 
 size_t gn_scratch_bytes(long long frames, long long HW, int C, int G, int num_sms, int vec) {
     int vpt, S;

@@ -120,9 +120,7 @@ int wgrad_splits(const WgradArgs& a, int num_sms, size_t max_partial_floats);
 template <typename T>
 int launch_wgrad(const T* dy, const T* x, WgradArgs a, int S, float* part, float* dw, float* db, cudaStream_t s);
 size_t gn_bwd_scratch_bytes(long long frames, int S, int C, int G);
-int gn_chunks_per_frame(long long HW, int C, int vec);  // k_norm.cu
 float2* gn_stats_of_scratch(void* scratch, long long frames, long long HW, int C, int G, int vec);  // k_norm.cu
-int gn_vectors_per_thread();  // k_norm.cu
 template <typename T>
 int launch_gn_silu_bwd(const T* x, const T* dy, const float2* stats, const float* gamma, const float* beta,
                        const T* add, long long frames, long long HW, int C, int G, int vpt, int S, void* scratch,
