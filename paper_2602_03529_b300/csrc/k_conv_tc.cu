@@ -843,6 +843,25 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                 const bool gstat = a.gn_part != nullptr;
                 float gK[4] = {0.f, 0.f, 0.f, 0.f}, gs[4] = {0.f, 0.f, 0.f, 0.f}, gq[4] = {0.f, 0.f, 0.f, 0.f};
                 float gcnt = 0.f;
+                // per tile: this lane's 16 channels (c0 ..) and, for a depth-to-space output,
+                // their sub-position (t, b, c) of the output block (oC % 16 == 0); BW is a
+                // power of two, so voxel vv of the tile is (vv >> bwl, vv & (BW - 1))
+                const int c0 = tc.nt * BN + q * 32 + half * 16;
+                const int bwl = __ffs(g.BW) - 1;
+                const int Hout = a.Hout, Wout = a.Wout, oT = a.oT, oH = a.oH, oW = a.oW, oC = a.oC;
+                int ot = tc.to, ch0 = c0, rh = 1, rw = 1, bb = 0, cc = 0;
+                if (a.mode == OUT_D2S) {
+                    const int sub = c0 / oC;
+                    ch0 = c0 - sub * oC;
+                    rw = a.rw;
+                    rh = a.rh;
+                    cc = sub % rw;
+                    bb = (sub / rw) % rh;
+                    ot = tc.to * a.rt + sub / (rw * rh) - a.drop_t;
+                }
+                const bool lane_ok = c0 < a.Cout && ot >= 0 && ot < oT;
+                const long long fbase = ((long long)tc.n * oT + ot) * oH;  // first output row of the frame
+                const int ho0 = tc.th * g.BH, wo0 = tc.tw * g.BW;
 #pragma unroll 1
                 for (int c16 = 0; c16 < g.nvox / 16; ++c16) {
                     float v[16];
@@ -851,9 +870,8 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                     for (int i = 0; i < 16; ++i) stg[i * C::EPI_STRIDE + lane] = v[i] + bias;
                     __syncwarp();
                     const int vv = c16 * 16 + j;
-                    const int ho = tc.th * g.BH + vv / g.BW, wo = tc.tw * g.BW + vv % g.BW;
-                    const int c0 = tc.nt * BN + q * 32 + half * 16;
-                    if (ho < a.Hout && wo < a.Wout && c0 < a.Cout) {
+                    const int ho = ho0 + (vv >> bwl), wo = wo0 + (vv & (g.BW - 1));
+                    if (ho < Hout && wo < Wout && c0 < a.Cout) {
                         float o[16];
                         const float4* src = reinterpret_cast<const float4*>(stg + j * C::EPI_STRIDE + half * 16);
 #pragma unroll
@@ -864,19 +882,10 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                             o[4 * i + 2] = f.z;
                             o[4 * i + 3] = f.w;
                         }
-                        // plain: voxel (to, ho, wo); depth-to-space (oC % 16 == 0): the 16 channels
-                        // lie in one sub-position (t, b, c) of the output block
-                        int ot = tc.to, oh = ho, ow = wo, ch0 = c0;
-                        if (a.mode == OUT_D2S) {
-                            const int sub = c0 / a.oC;
-                            ch0 = c0 - sub * a.oC;
-                            ow = wo * a.rw + sub % a.rw;
-                            oh = ho * a.rh + (sub / a.rw) % a.rh;
-                            ot = tc.to * a.rt + sub / (a.rw * a.rh) - a.drop_t;
-                        }
-                        if (ot >= 0 && ot < a.oT && oh < a.oH && ow < a.oW) {
-                            const long long off =
-                                ((((long long)tc.n * a.oT + ot) * a.oH + oh) * a.oW + ow) * a.oC + ch0;
+                        // plain: voxel (to, ho, wo); depth-to-space: sub-position (ot, bb, cc)
+                        const int oh = ho * rh + bb, ow = wo * rw + cc;
+                        if (lane_ok && oh < oH && ow < oW) {
+                            const long long off = ((fbase + oh) * oW + ow) * oC + ch0;
                             if (a.residual) add_bf16x16(static_cast<const __nv_bfloat16*>(a.residual) + off, o);
                             uint32_t w8[8];
 #pragma unroll
@@ -1412,6 +1421,7 @@ int launch_conv_tc_group(const ConvArgs* as, int count, int num_sms, cudaStream_
         }
         g.bwo = dwm ? g.BW - 2 : g.BW;
         g.bho = tr == 9 ? g.BH - 2 : g.BH;
+        if (swap && (g.BW & (g.BW - 1))) return -1;  // the swapped epilogue splits voxels by shifts
         g.nvox = g.BH * g.BW;
         g.tiles_w = (a.Wout + g.bwo - 1) / g.bwo;
         g.tiles_h = (a.Hout + g.bho - 1) / g.bho;
