@@ -940,19 +940,19 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                         t[1] = gn_merge(t[2], t[3]);
                     }
                     if (cg == 16) t[0] = gn_merge(t[0], t[1]);
-                    const int c0 = tc.nt * BN + q * 32 + lane * 16;  // lanes 0, 1: the two halves
-                    if (lane < 2 && c0 < a.Cout) {
-                        int ch0 = c0, fr = tc.to, slot = tc.th * g.tiles_w + tc.tw, S = g.tiles_h * g.tiles_w;
+                    const int gc0 = tc.nt * BN + q * 32 + lane * 16;  // lanes 0, 1: the two halves
+                    if (lane < 2 && gc0 < a.Cout) {
+                        int gch = gc0, fr = tc.to, slot = tc.th * g.tiles_w + tc.tw, S = g.tiles_h * g.tiles_w;
                         if (a.mode == OUT_D2S) {
-                            const int sub = c0 / a.oC;
-                            ch0 = c0 - sub * a.oC;
+                            const int sub = gc0 / a.oC;
+                            gch = gc0 - sub * a.oC;
                             fr = tc.to * a.rt + sub / (a.rw * a.rh) - a.drop_t;
                             slot = (slot * a.rh + (sub / a.rw) % a.rh) * a.rw + sub % a.rw;
                             S *= a.rh * a.rw;
                         }
                         if (fr >= 0 && fr < a.oT) {
                             const int G = a.oC / cg;
-                            GnTriple* dst = a.gn_part + (((long long)tc.n * a.oT + fr) * S + slot) * G + ch0 / cg;
+                            GnTriple* dst = a.gn_part + (((long long)tc.n * a.oT + fr) * S + slot) * G + gch / cg;
                             const int ng = 16 / cg;
 #pragma unroll
                             for (int k = 0; k < 4; ++k)
