@@ -1360,11 +1360,62 @@ void choose_tile_halo_fit(int Hout, int Wout, int* BH, int* BW) {
     }
 }
 
+static int device_sms() {
+    static const int n = [] {
+        int dev = 0, v = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) !=
+                                                         cudaSuccess || v < 1)
+            v = 148;
+        return v;
+    }();
+    return n;
+}
+
+// Wave-aware refinement of the wide halo tile. The persistent grid deals the
+// units (tile, 128-channel block) to one CTA per SM in turn, so the busiest
+// CTA runs ceil(units / SMs) of them, each costing about (voxels + 48). A
+// layer with few units (the 512-channel level of a 720p clip: 1200 units of
+// 15 x 16 is 8.1 waves, paid as 9) can gain by another tile size: 7 x 32 gives
+// 1300 units, still 9 waves, of 224 instead of 240 voxels. Tiles of 128 to
+// 256 voxels, width 16, 32 or 64; taken only when at least 3% cheaper. Only
+// for layers that do not reduce GroupNorm statistics: those are summed per
+// tile, and a tile that depends on the frame count would make a stream of
+// chunks round them differently from the whole clip (the conv outputs
+// themselves do not depend on the tile).
+static void choose_tile_halo_waves(const ConvArgs& a, int* BH, int* BW) {
+    choose_tile_halo_fit(a.Hout, a.Wout, BH, BW);
+    const long long blocks = (long long)a.N * a.Tout * (a.Cout_pad / 128);
+    const long long sms = device_sms();
+    const auto cost = [&](int bh, int bw) {
+        const long long units = (long long)((a.Hout + bh - 1) / bh) * ((a.Wout + bw - 1) / bw) * blocks;
+        return (units + sms - 1) / sms * (bh * bw + 48);
+    };
+    const long long base = cost(*BH, *BW);
+    long long best = base;
+    int bbh = *BH, bbw = *BW;
+    for (int bw : {16, 32, 64})
+        for (int bh = 128 / bw; bh * bw <= 256; ++bh) {
+            if ((bh * bw) % 16) continue;
+            const long long c = cost(bh, bw);
+            if (c < best || (c == best && bh * bw > bbh * bbw)) {
+                best = c;
+                bbh = bh;
+                bbw = bw;
+            }
+        }
+    if (best * 100 <= base * 97) {
+        *BH = bbh;
+        *BW = bbw;
+    }
+}
+
 // The output tile of a layer in its route (shared by the launch and the
 // GroupNorm statistics slot count).
 void conv_tc_tile(const ConvArgs& a, const ConvRoute& r, int* BH, int* BW) {
-    if (r.halo && !r.narrow)
+    if (r.halo && !r.narrow && a.gn_cg)
         choose_tile_halo_fit(a.Hout, a.Wout, BH, BW);
+    else if (r.halo && !r.narrow)
+        choose_tile_halo_waves(a, BH, BW);
     else if (r.halo)
         choose_tile_halo(a.Hout, a.Wout, 256, BH, BW);
     else

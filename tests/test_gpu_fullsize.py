@@ -58,7 +58,7 @@ def _bf16_normal(shape, seed, scale=1.0, shift=0.0):
 @pytest.mark.parametrize("level", [0, 1, 2, "2@1080p"])
 def test_conv_full_size_sampled(P, level):
     """The level-0 (128 -> 128 channels at 17 x 360 x 640), level-1 (256 -> 256 at
-    9 x 180 x 320) and level-2 (512 -> 512 at 5 x 90 x 160, 15 x 16 tiles; and at 1080p,
+    9 x 180 x 320) and level-2 (512 -> 512 at 5 x 90 x 160, 7 x 32 tiles; and at 1080p,
     5 x 135 x 240, 15 x 16 tiles) residual-block convs with their residual add, in the
     swapped halo form."""
     shapes = {0: (T, H // 2, W // 2, 128), 1: (9, H // 4, W // 4, 256), 2: (5, H // 8, W // 8, 512),

@@ -46,14 +46,25 @@ CONV_CASES = [
     (1, 3, 7, 9, 128, 64, 1, (1, 1, 1), 0),             # 1x1x1 shortcut
     (1, 3, 9, 40, 64, 16, 3, (1, 1, 1), 0),             # 16-channel head (dw rows)
     (1, 2, 6, 130, 64, 512, 3, (1, 1, 1), 0),           # W > 128, two N tiles of 256
-    # stride-1 3x3x3 layers of 128 channels and narrow heads share one input box among
-    # the three dh taps (halo tiles of width 16, 32 and 64, ragged edges)
-    (1, 3, 10, 70, 128, 128, 3, (1, 1, 1), 0),          # halo tile 16 x 16
-    (1, 3, 5, 130, 128, 128, 3, (1, 1, 1), 1),          # halo tile 8 x 32
-    (1, 2, 4, 128, 64, 128, 3, (1, 1, 1), 0),           # halo tile 4 x 64
+    # stride-1 3x3x3 layers of 128k channels and narrow heads share one input box among
+    # the three dh taps; a layer of less than one wave of (tile, 128-channel) units on
+    # 148 SMs takes 8 x 16 tiles (ragged edges)
+    (1, 3, 10, 70, 128, 128, 3, (1, 1, 1), 0),
+    (1, 3, 5, 130, 128, 128, 3, (1, 1, 1), 1),
+    (1, 2, 4, 128, 64, 128, 3, (1, 1, 1), 0),
     (1, 3, 9, 40, 128, 12, 3, (1, 1, 1), 0),            # pixel head (dw rows)
-    (1, 3, 30, 32, 128, 128, 3, (1, 1, 1), 0),          # halo tile 15 x 16 (N = 240, exact fit)
-    (2, 2, 12, 20, 128, 256, 3, (1, 1, 1), 1),          # halo tile 12 x 16 (N = 192), two channel tiles
+    (1, 3, 30, 32, 128, 128, 3, (1, 1, 1), 0),
+    (2, 2, 12, 20, 128, 256, 3, (1, 1, 1), 1),          # two channel tiles
+    # larger layers take the tile that minimises waves x (voxels + 48); one column
+    # past a whole number of tiles
+    (1, 38, 4, 33, 64, 256, 3, (1, 1, 1), 0),           # 4 x 64
+    (1, 38, 8, 17, 64, 256, 3, (1, 1, 1), 1),           # 8 x 32
+    (1, 38, 5, 17, 64, 256, 3, (1, 1, 1), 0),           # 5 x 32 (N = 160)
+    (1, 38, 7, 17, 64, 256, 3, (1, 1, 1), 1),           # 7 x 32 (N = 224)
+    (1, 25, 13, 17, 64, 256, 3, (1, 1, 1), 0),          # 13 x 16 (N = 208)
+    (1, 25, 15, 17, 64, 256, 3, (1, 1, 1), 1),          # 15 x 16 (N = 240)
+    (1, 25, 12, 33, 64, 128, 3, (1, 1, 1), 0),          # 12 x 16 (N = 192)
+    (1, 25, 9, 33, 64, 128, 3, (1, 1, 1), 1),           # 2 x 64 (N = 128)
     (1, 3, 11, 37, 64, 24, 3, (1, 1, 1), 1),            # narrow head, 32 weight rows
     (1, 3, 7, 9, 128, 6, 1, (1, 1, 1), 0),              # narrow 1x1x1 (swapped form)
     # 3x3x3 heads with spatial taps as MMA rows, 30 output columns per 32-column input
