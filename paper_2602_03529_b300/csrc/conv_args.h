@@ -78,6 +78,9 @@ struct ConvArgs {
     // gn_cg consecutive channels. Null: none. Only the swapped wide form writes them.
     GnTriple* gn_part;
     int gn_cg;
+    // 1: the tile of a layer with statistics may depend on the frame count (a
+    // training forward, which no stream of chunks has to reproduce bit for bit)
+    int gn_any_tile;
     // device status / bounded waits
     int* status;
     unsigned long long wait_ns;

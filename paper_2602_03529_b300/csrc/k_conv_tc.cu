@@ -1381,7 +1381,7 @@ static int device_sms() {
 // for layers that do not reduce GroupNorm statistics: those are summed per
 // tile, and a tile that depends on the frame count would make a stream of
 // chunks round them differently from the whole clip (the conv outputs
-// themselves do not depend on the tile).
+// themselves do not depend on the tile), unless the caller allows it.
 static void choose_tile_halo_waves(const ConvArgs& a, int* BH, int* BW) {
     choose_tile_halo_fit(a.Hout, a.Wout, BH, BW);
     const long long blocks = (long long)a.N * a.Tout * (a.Cout_pad / 128);
@@ -1412,7 +1412,7 @@ static void choose_tile_halo_waves(const ConvArgs& a, int* BH, int* BW) {
 // The output tile of a layer in its route (shared by the launch and the
 // GroupNorm statistics slot count).
 void conv_tc_tile(const ConvArgs& a, const ConvRoute& r, int* BH, int* BW) {
-    if (r.halo && !r.narrow && a.gn_cg)
+    if (r.halo && !r.narrow && a.gn_cg && !a.gn_any_tile)
         choose_tile_halo_fit(a.Hout, a.Wout, BH, BW);
     else if (r.halo && !r.narrow)
         choose_tile_halo_waves(a, BH, BW);

@@ -462,6 +462,9 @@ struct Exec {
     cudaStream_t s;
     Work w;
     int err = 0;
+    // conv tiles may depend on the frame count also where GroupNorm statistics
+    // are reduced (no stream of chunks has to match this pass bit for bit)
+    bool any_tile = false;
     void ck(int e) {
         if (e && !err) err = TOK_ECUDA;
     }
@@ -496,6 +499,7 @@ struct Exec {
         a.Cin = in.C;
         a.w = cw.w;
         a.w_dwm = cw.dwm;
+        a.gn_any_tile = any_tile ? 1 : 0;
         a.bias = cw.b;
         a.Cout = cw.Cout;
         a.Cout_pad = cw.Cout_pad;

@@ -159,6 +159,8 @@ struct TrainExec : Exec {
     TrainBufs b;
     float* grads = nullptr;  // flat dL/dparams
 
+    TrainExec() { any_tile = true; }
+
     void set_work() {
         w.gather = b.gather;
         w.gn = b.gn;
