@@ -119,7 +119,8 @@ struct Cfg {
     static constexpr int BAR_BYTES = 256;
     static constexpr int EPI_STRIDE = 36;  // floats per staged voxel row (16B-aligned, bank-spread)
     // (nine taps in rows: a staged box row of 128 accumulator rows and one output row of 16 channels)
-    static constexpr int EPI_BYTES = TR == 9 ? (128 + 16) * 33 * 4 : SWAP ? 4 * 16 * EPI_STRIDE * 4 : 0;
+    // (unswapped: per epilogue warp 32 voxel rows of 64 bf16 channels)
+    static constexpr int EPI_BYTES = TR == 9 ? (128 + 16) * 33 * 4 : SWAP ? 4 * 16 * EPI_STRIDE * 4 : 4 * 32 * 128;
     static constexpr int SMEM = STAGES * STAGE + 1024 + BAR_BYTES + EPI_BYTES;
     // (the swapped halo forms build theirs per tile: N = the tile's voxels, and M = 64
     // for heads of at most 16 rows, whose output channel r stays in TMEM lane r)
@@ -970,13 +971,95 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
             const bool valid = ho < a.Hout && wo < a.Wout;
             const uint32_t tbase = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(acc * C::ACC_COLS);
             const long long vox = (((long long)tc.n * a.Tout + tc.to) * a.Hout + ho) * a.Wout + wo;
+            // one voxel per thread. Plain bf16 output of whole 64-channel groups: four TMEM
+            // loads and the group's bias in flight at once, then the warp's staging rows
+            // (64 channels = 128 B of each of its 32 voxels) written as whole 128-byte
+            // lines (a direct store would touch 32 lines per instruction, one per voxel).
+            // The other channels (a ragged last group, fp32 or depth-to-space or FSQ
+            // output) 16 per step, the TMEM load of the next step in flight.
+            const bool bias4 = a.bias && (reinterpret_cast<uintptr_t>(a.bias) & 15) == 0;
+            const int ngrp = (BN >= 64 && a.mode == OUT_PLAIN && !a.out_fp32 && (a.oC & 7) == 0)
+                                 ? max(0, min(BN, a.Cout - tc.nt * BN)) / 64
+                                 : 0;  // whole 64-channel groups taken staged
+            const long long fbase = ((long long)tc.n * a.oT + tc.to) * a.oH;
+            {
+                uint8_t* const srow = reinterpret_cast<uint8_t*>(epi) + q * 4096;  // 16-byte slots XOR row & 7
+                const int bwl = __ffs(g.BW) - 1, sw = lane & 7;
+                const __nv_bfloat16* const resid = static_cast<const __nv_bfloat16*>(a.residual);
+                __nv_bfloat16* const outp = static_cast<__nv_bfloat16*>(a.out);
 #pragma unroll 1
-            for (int c16 = 0; c16 < BN / 16; ++c16) {
+                for (int g4 = 0; g4 < ngrp; ++g4) {
+                    const int g0 = tc.nt * BN + g4 * 64;
+                    uint32_t rr[4][16];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) tmem_ld16_issue(tbase + (uint32_t)(g4 * 64 + k * 16), rr[k]);
+                    float bv[64];
+                    if (bias4) {
+                        const float4* b4 = reinterpret_cast<const float4*>(a.bias + g0);
+#pragma unroll
+                        for (int m = 0; m < 16; ++m) {
+                            const float4 b = __ldg(b4 + m);
+                            bv[4 * m] = b.x;
+                            bv[4 * m + 1] = b.y;
+                            bv[4 * m + 2] = b.z;
+                            bv[4 * m + 3] = b.w;
+                        }
+                    } else {
+#pragma unroll
+                        for (int m = 0; m < 64; ++m) bv[m] = a.bias ? a.bias[g0 + m] : 0.f;
+                    }
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) tmem_regs_fence(rr[k]);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        float v[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(rr[k][j]) + bv[16 * k + j];
+                        if (resid && valid) add_bf16x16(resid + ((fbase + ho) * a.oW + wo) * a.oC + g0 + 16 * k, v);
+                        uint4 o0, o1;
+                        o0.x = pack_bf16x2(v[0], v[1]);
+                        o0.y = pack_bf16x2(v[2], v[3]);
+                        o0.z = pack_bf16x2(v[4], v[5]);
+                        o0.w = pack_bf16x2(v[6], v[7]);
+                        o1.x = pack_bf16x2(v[8], v[9]);
+                        o1.y = pack_bf16x2(v[10], v[11]);
+                        o1.z = pack_bf16x2(v[12], v[13]);
+                        o1.w = pack_bf16x2(v[14], v[15]);
+                        *reinterpret_cast<uint4*>(srow + lane * 128 + (((2 * k) ^ sw) << 4)) = o0;
+                        *reinterpret_cast<uint4*>(srow + lane * 128 + (((2 * k + 1) ^ sw) << 4)) = o1;
+                    }
+                    __syncwarp();
+                    // 8 lanes per voxel row, 4 rows per store
+#pragma unroll
+                    for (int i = 0; i < 8; ++i) {
+                        const int vl = i * 4 + (lane >> 3);
+                        const uint4 d = *reinterpret_cast<const uint4*>(srow + vl * 128 + ((sw ^ (vl & 7)) << 4));
+                        const int r2 = q * 32 + vl;
+                        const int ho2 = tc.th * g.BH + (r2 >> bwl), wo2 = tc.tw * g.BW + (r2 & (g.BW - 1));
+                        if (ho2 < a.Hout && wo2 < a.Wout)
+                            *reinterpret_cast<uint4*>(outp + ((fbase + ho2) * a.oW + wo2) * a.oC + g0 + sw * 8) = d;
+                    }
+                    __syncwarp();
+                }
+            }
+            const auto emit = [&](const uint32_t(&r)[16], int c16) {
                 float v[16];
-                tmem_ld16(tbase + (uint32_t)(c16 * 16), v);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
                 const int co0 = tc.nt * BN + c16 * 16;
-                if (!valid || co0 >= a.Cout) continue;
-                if (a.bias) {
+                if (!valid || co0 >= a.Cout) return;
+                if (bias4 && co0 + 16 <= a.Cout) {
+                    const float4* b4 = reinterpret_cast<const float4*>(a.bias + co0);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const float4 b = __ldg(b4 + k);
+                        v[4 * k] += b.x;
+                        v[4 * k + 1] += b.y;
+                        v[4 * k + 2] += b.z;
+                        v[4 * k + 3] += b.w;
+                    }
+                } else if (a.bias) {
 #pragma unroll
                     for (int j = 0; j < 16; ++j) v[j] += (co0 + j < a.Cout) ? a.bias[co0 + j] : 0.f;
                 }
@@ -1044,6 +1127,21 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                         }
                     }
                     if (a.idx) a.idx[vox] = idx;
+                }
+            };
+            uint32_t r0[16], r1[16];
+            if (ngrp * 4 < BN / 16) tmem_ld16_issue(tbase + (uint32_t)(ngrp * 64), r0);
+#pragma unroll 1
+            for (int c16 = ngrp * 4; c16 < BN / 16; c16 += 2) {
+                tmem_ld_wait();
+                tmem_regs_fence(r0);
+                if (c16 + 1 < BN / 16) tmem_ld16_issue(tbase + (uint32_t)((c16 + 1) * 16), r1);
+                emit(r0, c16);
+                if (c16 + 1 < BN / 16) {
+                    tmem_ld_wait();
+                    tmem_regs_fence(r1);
+                    if (c16 + 2 < BN / 16) tmem_ld16_issue(tbase + (uint32_t)((c16 + 2) * 16), r0);
+                    emit(r1, c16 + 1);
                 }
             }
             tc_fence_before();

@@ -266,6 +266,8 @@ __global__ void __launch_bounds__(192, 1)
                     for (int k = 0; k < 4; ++k) tmem_ld16_issue(ta + (uint32_t)(k * 16), r[k]);
                     tmem_ld_wait();
 #pragma unroll
+                    for (int k = 0; k < 4; ++k) tmem_regs_fence(r[k]);
+#pragma unroll
                     for (int k = 0; k < 4; ++k)
 #pragma unroll
                         for (int i = 0; i < 4; ++i)

@@ -44,6 +44,11 @@ CONV_CASES = [
     (1, 9, 16, 24, 64, 64, 3, (2, 2, 2), 1),
     (1, 4, 10, 12, 64, 128, 3, (1, 2, 2), 0),           # stride (1,2,2)
     (1, 3, 7, 9, 128, 64, 1, (1, 1, 1), 0),             # 1x1x1 shortcut
+    # one voxel per thread: whole 64-channel groups staged in shared memory and
+    # stored as whole lines, the rest 16 channels at a time
+    (1, 3, 9, 24, 128, 256, 1, (1, 1, 1), 1),           # four staged groups, ragged tiles
+    (1, 3, 7, 9, 128, 200, 1, (1, 1, 1), 0),            # second channel tile: one group + 8 channels
+    (1, 5, 16, 24, 64, 256, 3, (2, 2, 2), 0),           # strided, 256 channels
     (1, 3, 9, 40, 64, 16, 3, (1, 1, 1), 0),             # 16-channel head (dw rows)
     (1, 2, 6, 130, 64, 512, 3, (1, 1, 1), 0),           # W > 128, two N tiles of 256
     # stride-1 3x3x3 layers of 128k channels and narrow heads share one input box among
