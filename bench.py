@@ -705,6 +705,105 @@ def reference_arm(args):
                              "sample": sample},
             "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
+# ------------------------------------------------------------- profiling workloads
+# `python bench.py --case NAME [--N --T --H --W --s]` runs one fixed workload once
+# and exits (no JSON line); the ncu captures kept with the measurements name these
+# commands. Inputs come from the seeded generators; weights are He-normal from seed 0.
+
+def case_clip(N, T, H, W):
+    """One encode + decode of a seeded blurred-noise clip, BF16."""
+    import torch
+
+    import paper_2602_03529_b300 as P
+    import synthetic as S
+
+    tk = P.Tokenizer("bf16")
+    tk.set_params(S.weights_for(tk.param_spec(), seed=0))
+    tk.reserve(N, T, H, W)
+    x = torch.from_numpy(S.to_bf16_f32(S.blurred_noise_clip(1, N, T, H, W))).to("cuda", torch.bfloat16)
+    _, idx = tk.encode(x, want_z=False)
+    tk.decode(idx, H, W)
+    torch.cuda.synchronize()
+    if tk.status() != 0:
+        sys.exit(f"device status {tk.status()}")
+    print("clip ok", N, T, H, W, f"{tk.workspace_bytes(N, T, H, W) / 1e9:.2f} GB workspace")
+
+
+def case_train(N, T, H, W, recompute=False):
+    """One training step (forward with 10% drop, MSE, backward, SGD), then one more
+    forward + backward."""
+    import torch
+
+    import paper_2602_03529_b300 as P
+    from paper_2602_03529_b300.train import Trainer
+    import synthetic as S
+
+    tk = P.Tokenizer("bf16")
+    tk.set_params(S.weights_for(tk.param_spec(), seed=0))
+    tr = Trainer(tk, N, T, H, W, **({"recompute": True} if recompute else {}))
+    x = torch.from_numpy(S.blurred_noise_clip(7, N, T, H, W)).to("cuda", torch.bfloat16)
+    tr.step(x, 0.1, 1, 0, 1e-5)
+    tr.forward(x, 0.1, 1, 1)
+    tr.backward()
+    torch.cuda.synchronize()
+    if tk.status() != 0:
+        sys.exit(f"device status {tk.status()}")
+    print("train ok", N, T, H, W)
+
+
+def case_downsample(N, T, H, W, s):
+    """Three s x s area downsamples of seeded uint8 frames to bf16 (the resolution
+    control of the 1080p encoder input)."""
+    import numpy as np
+    import torch
+
+    import paper_2602_03529_b300 as P
+
+    x = torch.from_numpy(np.random.default_rng(8).integers(0, 256, (N, T, H, W, 3), dtype=np.uint8)).cuda()
+    y = P.downsample(x, s, torch.bfloat16)
+    for _ in range(2):
+        P.downsample(x, s, torch.bfloat16, out=y)
+    torch.cuda.synchronize()
+    print("downsample ok", tuple(y.shape))
+
+
+def case_select(N, T, H, W):
+    """Token selection over N streams x T P latent frames of H x W tokens (half of the P
+    tokens equal to the I token at their position), drop rate 0.25, three times."""
+    import numpy as np
+    import torch
+
+    import paper_2602_03529_b300 as P
+
+    rng = np.random.default_rng(5)
+    ii = rng.integers(0, 64000, (N, 1, H, W))
+    ip = np.where(rng.random((N, T, H, W)) < 0.5, np.repeat(ii, T, axis=1), rng.integers(0, 64000, (N, T, H, W)))
+    dp = torch.from_numpy(ip.astype(np.int32)).cuda()
+    di = torch.from_numpy(ii.astype(np.int32)).cuda()
+    for _ in range(3):
+        out, kb, _ = P.similarity_mask(dp, di, 0.25)
+    torch.cuda.synchronize()
+    print("select ok", tuple(out.shape), int((out == 32036).sum()))
+
+
+CASE_SHAPES = {"clip": (1, 5, 720, 1280), "train": (2, 17, 256, 256), "train-recompute": (2, 17, 256, 256),
+               "downsample": (4, 17, 1080, 1920), "select": (256, 4, 90, 160)}
+
+
+def run_case(args):
+    shape = [v if v is not None else d for v, d in zip((args.N, args.T_case, args.H_case, args.W_case),
+                                                       CASE_SHAPES[args.case])]
+    if args.case == "clip":
+        case_clip(*shape)
+    elif args.case == "train":
+        case_train(*shape)
+    elif args.case == "train-recompute":
+        case_train(*shape, recompute=True)
+    elif args.case == "downsample":
+        case_downsample(*shape, args.s)
+    else:
+        case_select(*shape)
+
 
 def main():
     ap = argparse.ArgumentParser()
@@ -728,7 +827,16 @@ def main():
     ap.add_argument("--serve-load", type=float, default=0.6)
     ap.add_argument("--serve-batch", type=int, default=4)
     ap.add_argument("--serve-no-align", action="store_true")
+    ap.add_argument("--case", choices=sorted(CASE_SHAPES), help="run one fixed profiling workload and exit")
+    ap.add_argument("--N", type=int, help="--case: batch")
+    ap.add_argument("--case-T", dest="T_case", type=int, help="--case: frames")
+    ap.add_argument("--case-H", dest="H_case", type=int, help="--case: height")
+    ap.add_argument("--case-W", dest="W_case", type=int, help="--case: width")
+    ap.add_argument("--s", type=int, default=3, help="--case downsample: factor")
     args = ap.parse_args()
+    if args.case:
+        run_case(args)
+        return
     out = reference_arm(args) if args.impl == "reference" else gpu_arm(args)
     if out is not None:
         print(json.dumps(out), flush=True)

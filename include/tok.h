@@ -147,13 +147,6 @@ int tok_decode(tok_ctx* ctx, const int32_t* d_idx, int N, int Tq, int Hq, int Wq
  * not depend on n. Not in the paper: a serving control. */
 int tok_set_cta_tiles(tok_ctx* ctx, int tiles);
 
-/* Whether this context's conv launches may run as clusters of two CTAs that
- * share every weight box by TMA multicast (off by default: measured 3-4%
- * slower, the conv mainloop is not held by L2 bandwidth for weights; used
- * for layers with at least one wave of tiles and persistent CTAs). Results
- * do not depend on it. Not in the paper: a performance control. */
-int tok_set_conv_pairs(tok_ctx* ctx, int on);
-
 /* Grouped encode / decode (one launch per layer over several inputs).
  * A batch holds 1 .. TOK_MAX_BATCH items of any sizes: whole clips, chunks of
  * streams (each stream at most once per batch), or both. Every convolution
@@ -405,9 +398,11 @@ int tok_sgd(float* d_params, const float* d_grads, int64_t n, float lr, void* st
  * that loads the library until the process exits. Returns TOK_ENOMEM when
  * the problem needs more scratch than that (tok_groupnorm_workspace_bytes
  * tells how much it needs). Allocates nothing. The first call on a device
- * looks up the array's device address, so make that first call before any
- * stream capture. All calls share the array: calls whose kernels overlap on
- * the GPU (other streams, other threads) race on it; serialise them. */
+ * (and the first after cudaDeviceReset, or in another context) looks up the
+ * array's device address, so make that first call before any stream
+ * capture. TOK_EDEVICE when the current device cannot be queried. All calls
+ * share the array: calls whose kernels overlap on the GPU (other streams,
+ * other threads) race on it; serialise them. */
 #define TOK_GN_NOALLOC_MAX_SCRATCH_BYTES (4u << 20)
 int tok_groupnorm_silu_noalloc(int precision, const void* d_x, int64_t frames, int64_t HW, int C, int G,
                                const float* d_gamma, const float* d_beta, float eps, void* d_y,
@@ -422,6 +417,28 @@ const char* tok_strerror(int code);
  * ever signals, with a bounded wait of `limit_ns`; the kernel gives up,
  * records TOK_ETIMEOUT in the context's status word and returns. */
 int tok_selftest_timeout(tok_ctx* ctx, int64_t limit_ns, void* stream);
+
+/* Test hook: layer traces. While armed, every tok_encode / tok_decode (and
+ * their batch forms, item 0) of this context copies, after the launch of the
+ * named layer, that layer's tensors into the caller's device buffers with
+ * device-to-device copies on the call's stream:
+ *   conv layers ("enc.stem", "enc.l0.b0.c1", "enc.down0", "dec.up1", ...):
+ *     d_in  <- its input activation (N,T,H,W,Cin) (the im2col matrix for the
+ *              stem and the decoder input of the BF16 path),
+ *     d_res <- the residual it adds (same shape as the output), when it adds one,
+ *     d_out <- its output: (N,T,H,W,Cout) bf16/fp32, after depth-to-space for
+ *              the up convs and the pixel head, the latent z (fp32) for
+ *              the last encoder conv;
+ *   GroupNorm+SiLU layers ("enc.l0.b0.gn1", "dec.out_gn", ...):
+ *     d_in <- its input, d_out <- its output.
+ * A NULL buffer (or 0 bytes) skips that tensor. A buffer smaller than its
+ * tensor makes the encode / decode return TOK_EINVAL. Several traces may be
+ * armed at once; name == NULL disarms all. Returns TOK_EINVAL for an unknown
+ * layer name. The buffers are the caller's and must stay valid while armed.
+ * Not in the paper: it lets tests compare each layer of the full-size
+ * network with the oracle on that layer's own input. */
+int tok_trace_layer(tok_ctx* ctx, const char* name, void* d_in, size_t in_bytes, void* d_res, size_t res_bytes,
+                    void* d_out, size_t out_bytes);
 
 /* Number of kernels the library has launched since the context was created
  * (for launch accounting in benchmarks). */

@@ -87,6 +87,7 @@ _SIGS = {
     "tok_encode": (i32, [vp, vp, i32, i32, i32, i32, vp, vp, vp, vp]),
     "tok_decode": (i32, [vp, vp, i32, i32, i32, i32, i32, i32, vp, vp, vp]),
     "tok_set_cta_tiles": (i32, [vp, i32]),
+    "tok_trace_layer": (i32, [vp, C.c_char_p, vp, sz, vp, sz, vp, sz]),
     "tok_downsample": (i32, [i32, vp, i32, i32, i32, i32, i32, i32, vp, vp]),
     "tok_gop_blend": (i32, [vp, i32, vp, vp, i32, i32, i32, i32, i32, i32, vp]),
     "tok_temporal_loss_workspace_bytes": (sz, [i32, i32, i32, i32, i32]),
@@ -97,7 +98,6 @@ _SIGS = {
     "tok_residual_apply": (i32, [vp, i32, i32, i32, i32, i32, i32, vp, vp, vp, i64, vp]),
     "tok_similarity_workspace_bytes": (sz, [i32, i32, i32, i32]),
     "tok_similarity_mask": (i32, [vp, vp, i32, i32, i32, i32, C.POINTER(i32), i32, f32, vp, vp, vp, vp, sz, vp]),
-    "tok_set_conv_pairs": (i32, [vp, i32]),
     "tok_batch_workspace_bytes": (sz, [vp, C.POINTER(tok_shape), i32]),
     "tok_reserve_batch": (i32, [vp, C.POINTER(tok_shape), i32]),
     "tok_encode_batch": (i32, [vp, C.POINTER(tok_enc_item), i32, vp]),
@@ -278,8 +278,9 @@ def tok_set_cta_tiles(ctx, tiles: int) -> None:
     _ck(_call("tok_set_cta_tiles", ctx, tiles), "tok_set_cta_tiles")
 
 
-def tok_set_conv_pairs(ctx, on: bool) -> None:
-    _ck(_call("tok_set_conv_pairs", ctx, 1 if on else 0), "tok_set_conv_pairs")
+def tok_trace_layer(ctx, name, d_in, in_bytes, d_res, res_bytes, d_out, out_bytes) -> None:
+    _ck(_call("tok_trace_layer", ctx, None if name is None else name.encode(), d_in, in_bytes, d_res, res_bytes,
+              d_out, out_bytes), "tok_trace_layer")
 
 
 def _shapes(shapes):

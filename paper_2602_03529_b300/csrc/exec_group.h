@@ -75,13 +75,14 @@ struct GroupExec : Exec {
                     (double)(cw.k * cw.k * cw.k) * cw.Cin;
         const int e = pbegin();
         if (c->bf16()) {
-            ck(launch_conv_tc_group(as, P, c->num_sms, s, c->cta_tiles, c->conv_pairs != 0));
+            ck(launch_conv_tc_group(as, P, c->num_sms, s, c->cta_tiles));
             c->launches += 1;
         } else {
             for (int p = 0; p < P; ++p) ck(launch_conv_simt(as[p], s));
             c->launches += P;
         }
         pend(e, 0, flop, cw.name);
+        trace_conv(cw.name, as[0]);
     }
 
     void slot(int i, void** out) const {
@@ -210,6 +211,8 @@ struct GroupExec : Exec {
         }
         pend(e, 1, bytes, name);
         c->launches += 3;
+        const size_t nb = (size_t)in[0].N * in[0].T * in[0].H * in[0].W * in[0].C * c->esize();
+        trace(name, in[0].p, nb, nullptr, 0, out[0].p, nb);
         return out;
     }
 

@@ -55,16 +55,13 @@ struct TcGeo {
 // A grouped launch: up to MAXP inputs of one layer (clips or stream chunks of
 // different sizes), one weight tensor. Tiles are numbered problem after
 // problem (tile_end holds the running totals) and a tile never spans two
-// problems; the persistent CTAs stride over all of them.
-//
-// Work is handed out in units: a unit is one tile, or (CTA pairs) two voxel
-// tiles of the same weight tile, one per CTA of the cluster; unit_end holds
-// the running totals of units per problem.
+// problems; the persistent CTAs stride over all of them. unit_end holds the
+// running totals of tiles per problem.
 template <int MAXP>
 struct TcBatch {
     CUtensorMap tm_w;
     CUtensorMap tm_w0;  // weights of the output-frame-0 tiles (a.w0), else a copy of tm_w
-    int w_rows;  // rows of each weight box: BN (/ CL), or the 16/32 real rows of a narrow halo layer
+    int w_rows;  // rows of each weight box: BN, or the 16/32 real rows of a narrow halo layer
     CUtensorMap tm_x[MAXP];
     CUtensorMap tm_h[MAXP];
     ConvArgs a[MAXP];
@@ -204,28 +201,7 @@ __device__ __forceinline__ int problem_of(const TcBatch<MAXP>& B, long long unit
     return p;
 }
 
-// Tile of CTA `rank` in a unit. With CTA pairs a unit is (pair of voxel tiles,
-// weight tile); the second CTA of a pair whose second voxel tile does not
-// exist recomputes the first one and stores nothing (phantom), so that both
-// CTAs always run the same K loop.
-template <int CL>
-__device__ __forceinline__ long long unit_tile(const TcGeo& g, long long lu, uint32_t rank, bool* phantom) {
-    if constexpr (CL == 1) {
-        *phantom = false;
-        return lu;
-    } else {
-        const long long nt = lu % g.n_tiles, mp = lu / g.n_tiles;
-        long long m = 2 * mp + rank;
-        *phantom = m >= g.m_tiles;
-        if (*phantom) m = 2 * mp;
-        return m * g.n_tiles + nt;
-    }
-}
-
-// CL = 1: one CTA per unit. CL = 2: clusters of two CTAs on two voxel tiles of
-// the same weight tile; each CTA loads half of every weight box and multicasts
-// it to both, and each stage is released only when both CTAs' MMAs have read
-// it (the empty barrier counts one commit from each CTA).
+// One CTA per tile; persistent CTAs stride over the tiles of all problems.
 // DWM (narrow heads of at most 16 channels, swapped halo form): the three dw
 // taps are MMA rows (row dw * 16 + co, 48 of 64), so a K block is (dt, 64
 // channels) with the three dh taps inside and an input box 32 columns wide
@@ -237,17 +213,12 @@ __device__ __forceinline__ long long unit_tile(const TcGeo& g, long long lu, uin
 // nine spatial taps and a K block is (dt, 64 channels) with one 8 x 32 input
 // box (6 x 30 outputs); the epilogue adds the tap rows with their row and
 // column shifts, out[co][y][x] = sum over dh, dw of D[(dh, dw, co)][y + dh][x + dw].
-template <int BN, bool SWAP, int MAXP, int CL, int HALO, int TR = 0>
+template <int BN, bool SWAP, int MAXP, int HALO, int TR = 0>
 __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__ TcBatch<MAXP> B) {
     using C = Cfg<BN, SWAP, HALO, TR>;
     constexpr bool DWM = TR == 3, T9 = TR == 9;
     constexpr int NDH = T9 ? 1 : 3;  // weight boxes (dh taps) per channel block of a K block
     static_assert(TR == 0 || ((TR == 3 || TR == 9) && SWAP && HALO == 1), "taps in rows: swapped halo form");
-    static_assert(CL == 1 || CL == 2, "CTA pairs at most");
-    static_assert(!HALO || CL == 1 || (TR == 0 && (C::W_TAP_BYTES / 2) % 1024 == 0),
-                  "halo pairs: each weight box splits on a swizzle atom");
-    constexpr uint32_t HALF_W = C::W_BYTES / 2;  // one CTA's share of a weight box
-    static_assert(CL == 1 || HALF_W % 1024 == 0, "weight halves must start on a swizzle atom");
     int* const status = B.a[0].status;
     const unsigned long long wait_ns = B.a[0].wait_ns;
     extern __shared__ uint8_t smem_raw[];
@@ -261,21 +232,17 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
     float* epi = reinterpret_cast<float*>(smem + C::STAGES * C::STAGE + C::BAR_BYTES);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-    const uint32_t rank = CL > 1 ? cluster_ctarank() : 0;
-    const long long cid = blockIdx.x / CL, ncl = gridDim.x / CL;
-    // A context already in error skips the launch (decided once per CTA, or
-    // once per cluster: both CTAs of a pair take the same path).
+    const long long cid = blockIdx.x, ncl = gridDim.x;
+    // A context already in error skips the launch (decided once per CTA).
     __shared__ int s_skip;
     if (threadIdx.x == 0) s_skip = (status && *(volatile int*)status != 0) ? 1 : 0;
-    if constexpr (CL == 1) {
-        __syncthreads();
-        if (s_skip) return;
-    }
+    __syncthreads();
+    if (s_skip) return;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::STAGES; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], CL);
+            mbar_init(&empty[s], 1);
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(&tfull[i], 1);
@@ -283,22 +250,10 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
         }
         fence_mbar_init();
     }
-    if constexpr (CL > 1) {
-        // the peer's barriers exist before any multicast reaches them
-        cluster_sync();
-        __shared__ int s_skip_pair;
-        if (threadIdx.x == 0) s_skip_pair = s_skip | (int)ld_peer_u32(&s_skip, rank ^ 1u);
-        __syncthreads();
-        if (s_skip_pair) {
-            cluster_sync();
-            return;
-        }
-    }
     if constexpr (HALO > 0) {
         // narrow layer: the weight boxes fill only the first w_rows rows of each
-        // 128-row weight slot; the others are zero for the whole launch (CTA pairs
-        // fill the whole slot, half from each CTA)
-        if (B.w_rows * CL < BN) {
+        // 128-row weight slot; the others are zero for the whole launch
+        if (B.w_rows < BN) {
             for (int st = 0; st < C::STAGES; ++st) {
                 uint4* wz = reinterpret_cast<uint4*>(smem + st * C::STAGE + C::ACT_BYTES);
                 for (int i = threadIdx.x; i < C::W_BYTES / 16; i += blockDim.x) wz[i] = make_uint4(0u, 0u, 0u, 0u);
@@ -335,8 +290,7 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                 const ConvArgs& a = B.a[p];
                 const TcGeo& g = B.g[p];
                 const int ph_ = (a.kh - 1) / 2, pw_ = (a.kw - 1) / 2;
-                bool phantom;
-                const TileCoord tc = decode_tile(a, g, unit_tile<CL>(g, lu, rank, &phantom));
+                const TileCoord tc = decode_tile(a, g, lu);
                 for (int kb = 0; kb < g.nkb; ++kb) {
                     if (!mbar_wait(&empty[s], ph ^ 1, status, wait_ns)) {
                         ok = false;
@@ -369,10 +323,9 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                     const CUtensorMap* wmap = (tc.to == 0) ? &B.tm_w0 : &B.tm_w;
                     if constexpr (HALO > 0) {
                         // rows th*BH - 1 .. th*BH + BH of the input frame (zeros outside), per block
-                        // (CTA pairs: both halves of every weight box land here)
                         // (nine taps in rows: a box of BH rows, th*bho - 1 .. th*bho + bho)
                         mbar_arrive_expect_tx(&full[s], (uint32_t)(HALO * ((T9 ? g.BH : g.BH + 2) * g.BW * 128 +
-                                                                           NDH * B.w_rows * CL * 128)));
+                                                                           NDH * B.w_rows * 128)));
 #pragma unroll
                         for (int c = 0; c < HALO; ++c) {
                             const int ci = (cb * HALO + c) * 64;
@@ -384,11 +337,7 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                                 const int kw0 = T9    ? dt * a.Cin + ci
                                                 : DWM ? (dt * 3 + d) * a.Cin + ci
                                                       : ((dt * 3 + d) * 3 + dw) * a.Cin + ci;
-                                if constexpr (CL == 1)
-                                    tma_load_2d(sb + (c * NDH + d) * C::W_TAP_BYTES, wmap, &full[s], kw0, tc.nt * BN);
-                                else
-                                    tma_load_2d_mc(sb + (c * NDH + d) * C::W_TAP_BYTES + rank * (C::W_TAP_BYTES / 2),
-                                                   wmap, &full[s], kw0, tc.nt * BN + (int)rank * (BN / 2), (uint16_t)0x3);
+                                tma_load_2d(sb + (c * NDH + d) * C::W_TAP_BYTES, wmap, &full[s], kw0, tc.nt * BN);
                             }
                         }
                         last_ph[s] = (int)ph;
@@ -407,11 +356,7 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                         tma_load_5d(sa, src, &full[s], pwp * a.Cin + cb * 64, tc.tw * g.BW + (dw == 0 ? -1 : 0), php,
                                     tc.th * g.BH + (dh == 0 ? -1 : 0), tcoord);
                     }
-                    if constexpr (CL == 1)
-                        tma_load_2d(sb, wmap, &full[s], tap * a.Cin + cb * 64, tc.nt * BN);
-                    else
-                        tma_load_2d_mc(sb + rank * HALF_W, wmap, &full[s], tap * a.Cin + cb * 64,
-                                       tc.nt * BN + (int)rank * (BN / 2), (uint16_t)0x3);
+                    tma_load_2d(sb, wmap, &full[s], tap * a.Cin + cb * 64, tc.nt * BN);
                     last_ph[s] = (int)ph;
                     if (++s == C::STAGES) {
                         s = 0;
@@ -419,21 +364,9 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                     }
                 }
             }
-            if constexpr (CL == 1) {
-                // make sure no copy is still in flight before the CTA may exit
-                for (int i = 0; i < C::STAGES; ++i)
-                    if (last_ph[i] >= 0) mbar_wait(&full[i], (uint32_t)last_ph[i], status, wait_ns);
-            } else {
-                // producer tail: wait until both CTAs' MMAs have released every stage, so
-                // that no copy into this CTA and no arrival on its barriers is in flight
-                for (int i = 0; i < C::STAGES; ++i) {
-                    if (!mbar_wait(&empty[s], ph ^ 1, status, wait_ns)) break;
-                    if (++s == C::STAGES) {
-                        s = 0;
-                        ph ^= 1;
-                    }
-                }
-            }
+            // make sure no copy is still in flight before the CTA may exit
+            for (int i = 0; i < C::STAGES; ++i)
+                if (last_ph[i] >= 0) mbar_wait(&full[i], (uint32_t)last_ph[i], status, wait_ns);
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -483,10 +416,7 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                             tc_mma_bf16(d, sw128_desc(op_a + k * 32), sw128_desc(op_b + k * 32), C::IDESC,
                                         (kb | k) != 0 ? 1u : 0u);
                     }
-                    if constexpr (CL == 1)
-                        tc_commit(&empty[s]);
-                    else
-                        tc_commit_mc(&empty[s], (uint16_t)0x3);
+                    tc_commit(&empty[s]);
                     if (++s == C::STAGES) {
                         s = 0;
                         ph ^= 1;
@@ -516,15 +446,7 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
             const int p = problem_of(B, u, &lu);
             const ConvArgs& a = B.a[p];
             const TcGeo& g = B.g[p];
-            bool phantom;
-            const TileCoord tc = decode_tile(a, g, unit_tile<CL>(g, lu, rank, &phantom));
-            if (phantom) {
-                // the pair's missing tile: computed for the K loop's sake, not stored
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&tempty[acc]);
-                continue;
-            }
+            const TileCoord tc = decode_tile(a, g, lu);
             if constexpr (SWAP) {
                 // lane = output channel co, TMEM column = voxel of the 256-voxel tile
                 const int co = tc.nt * BN + r;
@@ -1154,23 +1076,21 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
     __syncthreads();
     tc_fence_after();
     if (warp == 1) tmem_dealloc(tmem_base, C::TMEM_COLS);
-    if constexpr (CL > 1) cluster_sync();  // neither CTA leaves while its peer may still address it
 }
 
-template <int BN, bool SWAP, int MAXP, int CL, int HALO = 0, int TR = 0>
+template <int BN, bool SWAP, int MAXP, int HALO = 0, int TR = 0>
 int launch_bn(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int cta_tiles, cudaStream_t stream) {
     using C = Cfg<BN, SWAP, HALO, TR>;
-    auto kern = conv_tc_kernel<BN, SWAP, MAXP, CL, HALO, TR>;
+    auto kern = conv_tc_kernel<BN, SWAP, MAXP, HALO, TR>;
     TcBatch<MAXP> B;
     memset(&B, 0, sizeof(B));
-    // with CTA pairs each CTA loads half of the weight box (BN / 2 rows); a narrow halo
-    // layer loads its real rows only
+    // a narrow halo layer loads its real weight rows only
     // (taps in rows: 48 weight rows dw * 16 + co over K = (dt, dh, ci), or 128 rows
     // (dh * 3 + dw) * Cout + co over K = (dt, ci))
     B.w_rows = TR == 3   ? 48
                : TR == 9 ? 128
                : (HALO > 0 && SWAP && as[0].Cout <= 32) ? (as[0].Cout + 15) / 16 * 16
-                                                        : BN / CL;
+                                                        : BN;
     const int wk = TR == 3 ? 9 * as[0].Cin : TR == 9 ? 3 * as[0].Cin : as[0].Kpad;
     if (!encode_w_map(&B.tm_w, as[0].w, as[0].Cout_pad, wk, B.w_rows)) return -1;
     if (as[0].w0) {
@@ -1196,7 +1116,7 @@ int launch_bn(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int c
         g.n_tiles = std::min(a.Cout_pad, (a.Cout + BN - 1) / BN * BN) / BN;
         g.m_tiles = (long long)a.N * a.Tout * g.tiles_h * g.tiles_w;
         g.num_tiles = g.m_tiles * g.n_tiles;
-        total += CL == 1 ? g.num_tiles : (g.m_tiles + 1) / 2 * g.n_tiles;
+        total += g.num_tiles;
         B.a[p] = a;
         B.g[p] = g;
         B.unit_end[p] = total;
@@ -1204,80 +1124,29 @@ int launch_bn(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int c
     B.count = count;
     B.num_units = total;
     if (total == 0) return 0;
-    static int max_clusters = -1;
-    if (max_clusters < 0) {
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
-        max_clusters = num_sms / CL;
-        if (CL > 1) {
-            cudaLaunchConfig_t q = {};
-            q.gridDim = dim3((unsigned)(CL * max_clusters));
-            q.blockDim = dim3(192);
-            q.dynamicSmemBytes = C::SMEM;
-            cudaLaunchAttribute at;
-            at.id = cudaLaunchAttributeClusterDimension;
-            at.val.clusterDim.x = CL;
-            at.val.clusterDim.y = 1;
-            at.val.clusterDim.z = 1;
-            q.attrs = &at;
-            q.numAttrs = 1;
-            int n = 0;
-            if (cudaOccupancyMaxActiveClusters(&n, kern, &q) == cudaSuccess && n > 0) max_clusters = n;
-            cudaGetLastError();
-        }
+    static bool attr_set = false;
+    if (!attr_set) {
+        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) != cudaSuccess)
+            return -1;
+        attr_set = true;
     }
-    if constexpr (CL == 1) {
-        // persistent (one CTA per SM), or CTAs of at most cta_tiles tiles each
-        long long grid = std::min<long long>(total, num_sms);
-        if (cta_tiles > 0)
-            grid = std::max(grid, std::min<long long>((total + cta_tiles - 1) / cta_tiles, 1LL << 30));
-        kern<<<(unsigned)grid, 192, C::SMEM, stream>>>(B);
-    } else {
-        const long long clusters = std::min<long long>(total, max_clusters);
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)(CL * clusters));
-        cfg.blockDim = dim3(192);
-        cfg.dynamicSmemBytes = C::SMEM;
-        cfg.stream = stream;
-        cudaLaunchAttribute at;
-        at.id = cudaLaunchAttributeClusterDimension;
-        at.val.clusterDim.x = CL;
-        at.val.clusterDim.y = 1;
-        at.val.clusterDim.z = 1;
-        cfg.attrs = &at;
-        cfg.numAttrs = 1;
-        if (cudaLaunchKernelEx(&cfg, kern, B) != cudaSuccess) return -1;
-    }
+    // persistent (one CTA per SM), or CTAs of at most cta_tiles tiles each
+    long long grid = std::min<long long>(total, num_sms);
+    if (cta_tiles > 0) grid = std::max(grid, std::min<long long>((total + cta_tiles - 1) / cta_tiles, 1LL << 30));
+    kern<<<(unsigned)grid, 192, C::SMEM, stream>>>(B);
     return (int)cudaGetLastError();
 }
 
-// CTA pairs for layers with at least one wave of tiles (weight halves of 64+
-// rows), single CTAs otherwise and whenever CTA lifetimes are bounded.
 template <int BN, bool SWAP, int NCB, int TR = 0>  // NCB: 64-channel blocks per halo stage
-int launch_bn_halo(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int cta_tiles, cudaStream_t stream,
-                   bool pair = false) {
-    if constexpr (TR == 0) {
-        if (pair)
-            return count == 1 ? launch_bn<BN, SWAP, 1, 2, NCB>(as, gs, 1, num_sms, 0, stream)
-                              : launch_bn<BN, SWAP, kMaxConvGroup, 2, NCB>(as, gs, count, num_sms, 0, stream);
-    }
-    return count == 1 ? launch_bn<BN, SWAP, 1, 1, NCB, TR>(as, gs, 1, num_sms, cta_tiles, stream)
-                      : launch_bn<BN, SWAP, kMaxConvGroup, 1, NCB, TR>(as, gs, count, num_sms, cta_tiles, stream);
+int launch_bn_halo(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int cta_tiles, cudaStream_t stream) {
+    return count == 1 ? launch_bn<BN, SWAP, 1, NCB, TR>(as, gs, 1, num_sms, cta_tiles, stream)
+                      : launch_bn<BN, SWAP, kMaxConvGroup, NCB, TR>(as, gs, count, num_sms, cta_tiles, stream);
 }
 
 template <int BN, bool SWAP>
-int launch_bn_any(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int cta_tiles, bool pairs,
-                  cudaStream_t stream) {
-    long long tiles = 0;
-    for (int p = 0; p < count; ++p) {
-        const TcGeo& g = gs[p];
-        tiles += (long long)as[p].N * as[p].Tout * g.tiles_h * g.tiles_w * (as[p].Cout_pad / BN);
-    }
-    const bool pair = pairs && cta_tiles == 0 && (SWAP || BN >= 128) && tiles >= num_sms;
-    if (pair)
-        return count == 1 ? launch_bn<BN, SWAP, 1, 2>(as, gs, 1, num_sms, 0, stream)
-                          : launch_bn<BN, SWAP, kMaxConvGroup, 2>(as, gs, count, num_sms, 0, stream);
-    return count == 1 ? launch_bn<BN, SWAP, 1, 1>(as, gs, 1, num_sms, cta_tiles, stream)
-                      : launch_bn<BN, SWAP, kMaxConvGroup, 1>(as, gs, count, num_sms, cta_tiles, stream);
+int launch_bn_any(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int cta_tiles, cudaStream_t stream) {
+    return count == 1 ? launch_bn<BN, SWAP, 1>(as, gs, 1, num_sms, cta_tiles, stream)
+                      : launch_bn<BN, SWAP, kMaxConvGroup>(as, gs, count, num_sms, cta_tiles, stream);
 }
 
 }  // namespace
@@ -1535,10 +1404,8 @@ int conv_tc_gn_slots(const ConvArgs& a) {
 // mode; inputs, outputs, sizes and histories are per problem. cta_tiles = 0
 // launches one persistent CTA per SM; n > 0 gives every CTA at most n tiles,
 // so that a kernel on a higher-priority CUDA stream gets SMs within one short
-// CTA lifetime instead of after the whole layer. pairs allows clusters of two
-// CTAs sharing each weight box by multicast (results are the same either way).
-int launch_conv_tc_group(const ConvArgs* as, int count, int num_sms, cudaStream_t stream, int cta_tiles,
-                         bool pairs) {
+// CTA lifetime instead of after the whole layer.
+int launch_conv_tc_group(const ConvArgs* as, int count, int num_sms, cudaStream_t stream, int cta_tiles) {
     if (count < 1 || count > kMaxConvGroup) return -1;
     const ConvArgs& a0 = as[0];
     for (int p = 1; p < count; ++p)
@@ -1583,28 +1450,19 @@ int launch_conv_tc_group(const ConvArgs* as, int count, int num_sms, cudaStream_
     }
     if (tr == 9) return launch_bn_halo<128, true, 1, 9>(as, gs, count, num_sms, cta_tiles, stream);
     if (tr == 3) return launch_bn_halo<128, true, 1, 3>(as, gs, count, num_sms, cta_tiles, stream);
-    if (halo) {
-        // wide layers: clusters of two CTAs share every weight box (each loads half and
-        // multicasts it), when the layer has at least a tile per SM
-        long long tiles = 0;
-        for (int p = 0; p < count; ++p)
-            tiles += (long long)as[p].N * as[p].Tout * gs[p].tiles_h * gs[p].tiles_w *
-                     (std::min(as[p].Cout_pad, (as[p].Cout + 127) / 128 * 128) / 128);
-        const bool pair = pairs && cta_tiles == 0 && !rt.narrow && tiles >= num_sms;
-        return launch_bn_halo<128, true, 1>(as, gs, count, num_sms, cta_tiles, stream, pair);
-    }
-    if (swap) return launch_bn_any<128, true>(as, gs, count, num_sms, cta_tiles, pairs, stream);
+    if (halo) return launch_bn_halo<128, true, 1>(as, gs, count, num_sms, cta_tiles, stream);
+    if (swap) return launch_bn_any<128, true>(as, gs, count, num_sms, cta_tiles, stream);
     switch (conv_tc_bn(a0.Cout_pad)) {
-        case 256: return launch_bn_any<256, false>(as, gs, count, num_sms, cta_tiles, pairs, stream);
-        case 128: return launch_bn_any<128, false>(as, gs, count, num_sms, cta_tiles, pairs, stream);
-        case 64: return launch_bn_any<64, false>(as, gs, count, num_sms, cta_tiles, pairs, stream);
-        case 32: return launch_bn_any<32, false>(as, gs, count, num_sms, cta_tiles, pairs, stream);
-        default: return launch_bn_any<16, false>(as, gs, count, num_sms, cta_tiles, pairs, stream);
+        case 256: return launch_bn_any<256, false>(as, gs, count, num_sms, cta_tiles, stream);
+        case 128: return launch_bn_any<128, false>(as, gs, count, num_sms, cta_tiles, stream);
+        case 64: return launch_bn_any<64, false>(as, gs, count, num_sms, cta_tiles, stream);
+        case 32: return launch_bn_any<32, false>(as, gs, count, num_sms, cta_tiles, stream);
+        default: return launch_bn_any<16, false>(as, gs, count, num_sms, cta_tiles, stream);
     }
 }
 
 int launch_conv_tc(const ConvArgs& a, int num_sms, cudaStream_t stream) {
-    return launch_conv_tc_group(&a, 1, num_sms, stream, 0, true);
+    return launch_conv_tc_group(&a, 1, num_sms, stream, 0);
 }
 
 }  // namespace tok

@@ -13,7 +13,10 @@
 // symbol, not a device address: passing it to a kernel would fault or, where
 // the GPU can reach host memory, silently use the wrong memory. So the first
 // call on each device looks up the real device address with
-// cudaGetSymbolAddress (with that device current) and caches it.
+// cudaGetSymbolAddress (with that device current) and caches it; make that
+// first call before any stream capture. The cache remembers the CUDA context
+// it was taken in (its process-unique id), so a call after cudaDeviceReset,
+// or in another context of the same device, looks the address up again.
 //
 // The kernels fully overwrite the part of the scratch they read in the same
 // call (every partial triple and every group's statistics are written before
@@ -21,6 +24,7 @@
 // the one array: two calls whose kernels overlap on the GPU (different
 // streams, or different host threads) race on it and may return wrong
 // results; serialise them on one stream.
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -36,20 +40,49 @@ static __device__ __align__(256) unsigned char g_gn_scratch[TOK_GN_NOALLOC_MAX_S
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_addr[kMaxDevices] = {};
+unsigned long long g_ctx_id[kMaxDevices] = {};  // context the address was looked up in
 
-// Device address of g_gn_scratch on the current device (looked up once per device).
+// Process-unique id of the current CUDA context, or 0 when there is none yet
+// (the driver calls are reached through the runtime's entry-point query, as
+// the tensor-map encoder is).
+unsigned long long current_context_id() {
+    static PFN_cuCtxGetCurrent_v4000 get_cur = nullptr;
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        if (cudaGetDriverEntryPoint("cuCtxGetCurrent", &p, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_cur = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(p);
+        p = nullptr;
+        if (cudaGetDriverEntryPoint("cuCtxGetId", &p, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(p);
+    });
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_cur || !get_id || get_cur(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
+
+// Device address of g_gn_scratch on the current device: looked up once per
+// device and context (the set-up of the first call there).
 int scratch_address(void** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return TOK_EDEVICE;
     if (dev < 0 || dev >= kMaxDevices) return TOK_EDEVICE;
     std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
+    const unsigned long long id = current_context_id();
+    if (!g_addr[dev] || id == 0 || id != g_ctx_id[dev]) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_gn_scratch) != cudaSuccess || p == nullptr) {
             cudaGetLastError();
+            g_addr[dev] = nullptr;
             return TOK_ECUDA;
         }
         g_addr[dev] = p;
+        g_ctx_id[dev] = current_context_id();  // the lookup has made the context current
     }
     *out = g_addr[dev];
     return TOK_OK;
@@ -67,9 +100,12 @@ extern "C" int tok_groupnorm_silu_noalloc(int precision, const void* x, int64_t 
     if (C % V || C % G || C / G < 2 || G > 64 || vpv > 256 || (vpv & (vpv - 1))) return TOK_ESHAPE;
     const int cg = C / G;
     if (!(cg % V == 0 || V % cg == 0)) return TOK_ESHAPE;
-    int dev = 0, nsm = 148;
+    int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return TOK_EDEVICE;
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) {
+        cudaGetLastError();
+        return TOK_EDEVICE;
+    }
     // Problems whose scratch exceeds the fixed array are refused.
     if (tok::gn_scratch_bytes(frames, HW, C, G, nsm, V) > (size_t)TOK_GN_NOALLOC_MAX_SCRATCH_BYTES)
         return TOK_ENOMEM;

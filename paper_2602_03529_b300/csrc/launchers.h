@@ -24,8 +24,7 @@ int launch_pack_weights_taprows(const float* w, int Cout, int Cin, int rows_out,
 // group) only where this holds; conv_tc_gn_slots gives the slots per frame.
 bool conv_tc_gn_fusable(const ConvArgs& a);
 int conv_tc_gn_slots(const ConvArgs& a);
-int launch_conv_tc_group(const ConvArgs* as, int count, int num_sms, cudaStream_t stream, int cta_tiles = 0,
-                         bool pairs = true);
+int launch_conv_tc_group(const ConvArgs* as, int count, int num_sms, cudaStream_t stream, int cta_tiles = 0);
 int conv_tc_bn(int cout_pad16);
 int conv_tc_cout_pad(int Cout);  // packed weight rows of a BF16 conv
 int launch_conv_simt(const ConvArgs& a, cudaStream_t stream);

@@ -306,15 +306,23 @@ int tok_decode_batch(tok_ctx* c, const tok_dec_item* items, int count, void* str
     return ex.err;
 }
 
-int tok_set_cta_tiles(tok_ctx* c, int tiles) {
-    if (!c || tiles < 0) return TOK_EINVAL;
-    c->cta_tiles = tiles;
+int tok_trace_layer(tok_ctx* c, const char* name, void* in, size_t in_bytes, void* res, size_t res_bytes, void* out,
+                    size_t out_bytes) {
+    if (!c) return TOK_EINVAL;
+    if (!name) {
+        c->traces.clear();
+        return TOK_OK;
+    }
+    if (!c->cindex.count(name) && !c->gindex.count(name)) return TOK_EINVAL;
+    if ((!in || !in_bytes) && (!res || !res_bytes) && (!out || !out_bytes)) return TOK_EINVAL;
+    c->traces.push_back(tok_ctx::Trace{name, in_bytes ? in : nullptr, in_bytes, res_bytes ? res : nullptr, res_bytes,
+                                       out_bytes ? out : nullptr, out_bytes});
     return TOK_OK;
 }
 
-int tok_set_conv_pairs(tok_ctx* c, int on) {
-    if (!c) return TOK_EINVAL;
-    c->conv_pairs = on ? 1 : 0;
+int tok_set_cta_tiles(tok_ctx* c, int tiles) {
+    if (!c || tiles < 0) return TOK_EINVAL;
+    c->cta_tiles = tiles;
     return TOK_OK;
 }
 

@@ -68,7 +68,6 @@ struct tok_ctx {
     int precision;
     int device = 0, num_sms = 148;
     int cta_tiles = 0;  // conv launches: 0 persistent, n > 0 at most n tiles per CTA
-    int conv_pairs = 0;  // conv launches may use CTA pairs with weight multicast (measured slower)
     std::vector<ParamInfo> params;
     std::map<std::string, int> pindex;
     std::vector<std::vector<float>> host;
@@ -102,6 +101,17 @@ struct tok_ctx {
     std::vector<cudaEvent_t> events;
     std::vector<ProfRec> recs;
     int ev_used = 0;
+    // layer traces (tok_trace_layer): copies of a named layer's tensors
+    struct Trace {
+        std::string name;
+        void* in;
+        size_t in_cap;
+        void* res;
+        size_t res_cap;
+        void* out;
+        size_t out_cap;
+    };
+    std::vector<Trace> traces;
     bool bf16() const { return precision == TOK_BF16; }
     size_t esize() const { return bf16() ? 2 : 4; }
 };
@@ -551,11 +561,44 @@ struct Exec {
                             cw.Cin;
         const int e = pbegin();
         if (c->bf16())
-            ck(launch_conv_tc_group(&a, 1, c->num_sms, s, 0, c->conv_pairs != 0));
+            ck(launch_conv_tc_group(&a, 1, c->num_sms, s, 0));
         else
             ck(launch_conv_simt(a, s));
         pend(e, 0, flop, cw.name);
         c->launches += 1;
+    }
+
+    // Layer trace (a test hook): device-to-device copies, on the executor's
+    // stream, of the tensors of a traced layer; a buffer too small for its
+    // tensor makes the call fail with TOK_EINVAL.
+    void trace(const std::string& name, const void* in, size_t in_b, const void* res, size_t res_b, const void* out,
+               size_t out_b) {
+        if (err || c->traces.empty()) return;
+        for (const auto& t : c->traces) {
+            if (t.name != name) continue;
+            const std::pair<const void*, size_t> src[3] = {{in, in_b}, {res, res_b}, {out, out_b}};
+            void* const dst[3] = {t.in, t.res, t.out};
+            const size_t cap[3] = {t.in_cap, t.res_cap, t.out_cap};
+            for (int i = 0; i < 3; ++i) {
+                if (!dst[i] || !src[i].first) continue;
+                if (src[i].second > cap[i]) {
+                    err = TOK_EINVAL;
+                    return;
+                }
+                if (cudaMemcpyAsync(dst[i], src[i].first, src[i].second, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+                    ck(1);
+            }
+        }
+    }
+    void trace_conv(const std::string& name, const ConvArgs& a) {
+        if (c->traces.empty()) return;
+        const size_t es = c->esize();
+        const size_t in_b = (size_t)a.N * a.Tin * a.Hin * a.Win * a.Cin * es;
+        const size_t o_vox = (size_t)a.N * a.oT * a.oH * a.oW;
+        const size_t res_b = o_vox * a.oC * es;
+        const size_t out_b = a.mode == OUT_FSQ ? (size_t)a.N * a.Tout * a.Hout * a.Wout * c->arch.nlev * 4
+                                               : o_vox * a.oC * (a.out_fp32 ? 4 : es);
+        trace(name, a.x, in_b, a.residual, res_b, a.out, out_b);
     }
 
     // Other (bandwidth-bound) kernels: bytes of algorithmic traffic.

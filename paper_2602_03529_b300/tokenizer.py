@@ -139,10 +139,16 @@ class Tokenizer:
         work on higher-priority CUDA streams; results are unchanged)."""
         L.tok_set_cta_tiles(self.ctx, tiles)
 
-    def set_conv_pairs(self, on: bool):
-        """Allow (default) or forbid conv launches as CTA pairs sharing weight boxes by
-        TMA multicast; results are unchanged."""
-        L.tok_set_conv_pairs(self.ctx, on)
+    def trace_layer(self, name, inp=None, res=None, out=None):
+        """Arm a layer trace (a test hook): the next encodes / decodes copy the named
+        layer's input, residual and output into the given device tensors (None skips
+        one). trace_layer(None) disarms all traces."""
+        def pb(t):
+            return (None, 0) if t is None else (t.data_ptr(), t.numel() * t.element_size())
+        if name is None:
+            L.tok_trace_layer(self.ctx, None, None, 0, None, 0, None, 0)
+            return
+        L.tok_trace_layer(self.ctx, name, *pb(inp), *pb(res), *pb(out))
 
     # -- grouped (one launch per layer over several inputs) --------------------
     def reserve_batch(self, shapes):

@@ -169,25 +169,3 @@ def test_short_lived_ctas_give_the_same_result(P, tiles):
     for a, b in zip(zr + ir + xr, zt + it + xt):
         assert torch.equal(a, b)
     tk.close()
-
-
-def test_cta_pairs_give_the_same_result(P):
-    """Conv launches as clusters of two CTAs sharing every weight box by TMA multicast
-    (including a pair whose second voxel tile does not exist) compute every tile
-    exactly as single CTAs do: encode and decode of a default-width tokenizer."""
-    tk = P.Tokenizer("bf16", ch=(128, 256, 512), blocks=1)
-    tk.set_params(S.weights_for(tk.param_spec(), seed=4))
-    shapes = [(1, 9, 144, 200), (1, 5, 72, 96)]
-    xs = _clips("bf16", shapes)
-    tk.reserve_batch(shapes)
-    outs = {}
-    for pairs in (False, True):
-        tk.set_conv_pairs(pairs)
-        z, i = tk.encode_batch(xs)
-        x = tk.decode_batch(i, [(H, W) for (_, _, H, W) in shapes])
-        torch.cuda.synchronize()
-        assert tk.status() == 0
-        outs[pairs] = z + i + x
-    for a, b in zip(outs[False], outs[True]):
-        assert torch.equal(a, b)
-    tk.close()

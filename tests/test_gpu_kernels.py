@@ -1,6 +1,6 @@
 """Parity of the individual CUDA kernels against the FP64 oracle, through the C-ABI.
 
-Tolerances (stated here, derived in the design doc):
+Tolerances (each with the arithmetic it follows from):
   * conv, FP32 path: the oracle gets the same fp32 inputs; FP32 accumulation
     of K terms plus one fp32 rounding: |gpu - ref| <= 1e-5 |ref| + 2e-6 * s * r,
     s = max |ref|, r = max(1, sqrt(K / 3456)) (rounding errors of a long sum
