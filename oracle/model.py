@@ -110,10 +110,20 @@ def param_spec(arch: Arch):
 
 
 class Oracle:
-    """The reference tokenizer over a dict of named float parameters."""
+    """The reference tokenizer over a dict of named float parameters.
 
-    def __init__(self, arch: Arch, params: dict):
+    act_bf16: model BF16 activations ("BF16 weights/activations with FP32
+    accumulation" of the workload description): every tensor a layer stores
+    between layers -- the stem, residual-block and down-conv outputs, every
+    GroupNorm+SiLU output, the up-conv outputs and the decoder input conv's
+    output -- is the exact value rounded to float32 and then to the nearest
+    bfloat16 (ties to even), as an FP32 accumulator is stored in bf16. A
+    residual block's output is rounded once, after its skip is added. The
+    latent z and the decoded pixels stay unrounded. Default: exact FP64."""
+
+    def __init__(self, arch: Arch, params: dict, act_bf16: bool = False):
         self.arch = arch
+        self.act_bf16 = act_bf16
         self.p = {k: np.asarray(v, dtype=np.float64) for k, v in params.items()}
         names = [n for n, _, _ in param_spec(arch)]
         missing = [n for n in names if n not in self.p]
@@ -121,21 +131,27 @@ class Oracle:
             raise KeyError(f"missing parameters: {missing[:5]}")
 
     # -- building blocks -------------------------------------------------
+    def store(self, x):
+        """The value of a stored activation (see act_bf16)."""
+        if not self.act_bf16:
+            return x
+        return ops.round_to_bf16(np.asarray(x, dtype=np.float32)).astype(np.float64)
+
     def conv(self, name, x, stride=(1, 1, 1)):
         return ops.conv3d(x, self.p[name + ".w"], self.p[name + ".b"], stride, self.arch.time_pad)
 
     def gn_silu(self, name, x):
         C = x.shape[-1]
         g = ops.gn_groups(C, self.arch.gn_groups)
-        return ops.silu(ops.group_norm_frames(x, g, self.arch.gn_eps,
-                                              self.p[name + ".g"], self.p[name + ".b"]))
+        return self.store(ops.silu(ops.group_norm_frames(x, g, self.arch.gn_eps,
+                                                         self.p[name + ".g"], self.p[name + ".b"])))
 
     def block(self, name, x):
         """Causal residual block: skip(x) + conv2(SiLU(GN2(conv1(SiLU(GN1(x))))))."""
-        h = self.conv(name + ".c1", self.gn_silu(name + ".gn1", x))
+        h = self.store(self.conv(name + ".c1", self.gn_silu(name + ".gn1", x)))
         h = self.conv(name + ".c2", self.gn_silu(name + ".gn2", h))
-        skip = self.conv(name + ".sc", x) if (name + ".sc.w") in self.p else x
-        return skip + h
+        skip = self.store(self.conv(name + ".sc", x)) if (name + ".sc.w") in self.p else x
+        return self.store(skip + h)
 
     # -- encoder ---------------------------------------------------------
     def encode_latent(self, x):
@@ -143,15 +159,15 @@ class Oracle:
         a = self.arch
         x = ops.edge_pad_to_multiple(np.asarray(x, dtype=np.float64), a.s_hw)
         if a.kind == "stage":
-            h = self.conv("stage.c0", x)
-            h = self.conv("stage.c1", h, (1, 2, 2))
+            h = self.store(self.conv("stage.c0", x))
+            h = self.store(self.conv("stage.c1", h, (1, 2, 2)))
             return self.conv("stage.out", self.gn_silu("stage.gn", h))
-        h = self.conv("enc.stem", x, (a.t_stem, 2, 2))
+        h = self.store(self.conv("enc.stem", x, (a.t_stem, 2, 2)))
         for l in range(a.nlevels):
             for b in range(a.blocks):
                 h = self.block(f"enc.l{l}.b{b}", h)
             if l < a.nlevels - 1:
-                h = self.conv(f"enc.down{l}", h, (2, 2, 2))
+                h = self.store(self.conv(f"enc.down{l}", h, (2, 2, 2)))
         return self.conv("enc.out", self.gn_silu("enc.out_gn", h))
 
     def encode(self, x):
@@ -164,12 +180,12 @@ class Oracle:
     def decode_codes(self, codes, H, W):
         """Code vectors (N,T',H',W',zdim) -> pixels (N,T,H,W,3), cropped to H x W."""
         a = self.arch
-        h = self.conv("dec.in", codes)
+        h = self.store(self.conv("dec.in", codes))
         for l in reversed(range(a.nlevels)):
             for b in range(a.blocks):
                 h = self.block(f"dec.l{l}.b{b}", h)
             if l > 0:
-                h = ops.depth_to_space(self.conv(f"dec.up{l - 1}", h), (2, 2, 2))
+                h = self.store(ops.depth_to_space(self.conv(f"dec.up{l - 1}", h), (2, 2, 2)))
         y = self.conv("dec.out", self.gn_silu("dec.out_gn", h))
         y = ops.depth_to_space(y, (a.t_stem, 2, 2))
         return y[:, :, :H, :W, :]

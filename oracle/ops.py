@@ -111,6 +111,77 @@ def conv3d_wgrad(dy, x, k, stride=(1, 1, 1), pad_mode=PAD_REPLICATE):
     return dw, db
 
 
+def _tap_frames(To, dt, st, kt, T, pad_mode):
+    """Input frame read by every output frame at temporal tap dt (the causal rule of
+    :func:`conv3d`): -1 where the tap reads zero padding."""
+    ti = np.arange(To) * st + dt - (kt - 1)
+    if pad_mode == PAD_REPLICATE:
+        return np.where(ti < 0, 0, ti)
+    return np.where(ti < 0, -1, ti)
+
+
+def _tap_pos(O, d, s, k, extent):
+    """Input row (column) read by every output row (column) at spatial tap d; -1 outside."""
+    i = np.arange(O) * s + d - (k - 1) // 2
+    return np.where((i < 0) | (i >= extent), -1, i)
+
+
+def conv3d_wgrad_entries(dy, x, k, entries, stride=(1, 1, 1), pad_mode=PAD_REPLICATE):
+    """Selected entries dW[co, dt, dh, dw, ci] of the weight gradient of :func:`conv3d`.
+
+    Each entry is the sum over output voxels v of dy[v, co] * x[src(v, tap), ci],
+    src being the forward's tap rule (causal frames, zero spatial padding); it
+    lets a test check single entries of a gradient whose full computation would
+    take too long (large clips). ``entries`` is a list of (co, dt, dh, dw, ci).
+    Returns (values, magnitudes): the sums and the sums of |terms|."""
+    kt, kh, kw = k
+    st, sh, sw = stride
+    N, To, Ho, Wo, _ = dy.shape
+    _, T, H, W, _ = x.shape
+    vals, mags = [], []
+    for co, dt, dh, dw, ci in entries:
+        ti = _tap_frames(To, dt, st, kt, T, pad_mode)
+        hi = _tap_pos(Ho, dh, sh, kh, H)
+        wi = _tap_pos(Wo, dw, sw, kw, W)
+        xc = np.asarray(x[..., ci], dtype=np.float64)
+        g = xc[:, np.maximum(ti, 0)][:, :, np.maximum(hi, 0)][:, :, :, np.maximum(wi, 0)]
+        valid = (ti >= 0)[:, None, None] & (hi >= 0)[None, :, None] & (wi >= 0)[None, None, :]
+        terms = np.asarray(dy[..., co], dtype=np.float64) * np.where(valid[None], g, 0.0)
+        vals.append(terms.sum())
+        mags.append(np.abs(terms).sum())
+    return np.array(vals), np.array(mags)
+
+
+def conv3d_dgrad_entries(dy, w, x_shape, points, stride=(1, 1, 1), pad_mode=PAD_REPLICATE):
+    """dX[n, t, h, w, :] of :func:`conv3d` at the given points (n, t, h, w): the sum, over
+    taps and the output voxels whose tap reads (t, h, w) under the forward's rule
+    (with replicate padding, frame 0 is read by every tap that falls before it),
+    of w[:, tap, :]^T dy[output voxel, :]. Returns (values (P, Cin), magnitudes
+    (P, Cin): the sums of |terms|)."""
+    Cout, kt, kh, kw, Cin = w.shape
+    st, sh, sw = stride
+    N, To, Ho, Wo, _ = dy.shape
+    _, T, H, W, _ = x_shape
+    w = np.asarray(w, dtype=np.float64)
+    vals = np.zeros((len(points), Cin))
+    mags = np.zeros((len(points), Cin))
+    for p, (n, t, h, wv) in enumerate(points):
+        for dt in range(kt):
+            ots = np.nonzero(_tap_frames(To, dt, st, kt, T, pad_mode) == t)[0]
+            for dh in range(kh):
+                ohs = np.nonzero(_tap_pos(Ho, dh, sh, kh, H) == h)[0]
+                for dw in range(kw):
+                    ows = np.nonzero(_tap_pos(Wo, dw, sw, kw, W) == wv)[0]
+                    for ot in ots:
+                        for oh in ohs:
+                            for ow in ows:
+                                g = np.asarray(dy[n, ot, oh, ow], dtype=np.float64)
+                                term = g[:, None] * w[:, dt, dh, dw, :]
+                                vals[p] += term.sum(axis=0)
+                                mags[p] += np.abs(term).sum(axis=0)
+    return vals, mags
+
+
 # --------------------------------------------------------------------------
 # GroupNorm + SiLU
 # --------------------------------------------------------------------------

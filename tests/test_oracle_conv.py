@@ -147,3 +147,31 @@ def test_conv_adjoint_identities():
         lhs = float((y * dy).sum())
         assert abs(lhs - float((x * dx).sum())) < 1e-9 * max(1.0, abs(lhs))
         assert abs(lhs - float((w * dw).sum())) < 1e-9 * max(1.0, abs(lhs))
+
+
+@pytest.mark.parametrize("shape,k,stride,pad", [
+    ((1, 5, 6, 7, 3), (3, 3, 3), (1, 1, 1), ops.PAD_REPLICATE),
+    ((2, 9, 8, 6, 4), (3, 3, 3), (2, 2, 2), ops.PAD_REPLICATE),
+    ((1, 5, 6, 6, 3), (3, 3, 3), (1, 2, 2), ops.PAD_ZERO),
+    ((1, 3, 4, 4, 5), (1, 1, 1), (1, 1, 1), ops.PAD_REPLICATE),
+])
+def test_gradient_entries_match_full_gradients(shape, k, stride, pad):
+    """The single-entry weight and input gradients (used to check large clips on
+    samples) equal the full dgrad / wgrad at every entry and every point; the
+    magnitudes bound the values and are positive where a term exists."""
+    rng = np.random.default_rng(9)
+    x = rng.standard_normal(shape)
+    w = rng.standard_normal((5, *k, shape[-1]))
+    y = ops.conv3d(x, w, None, stride, pad)
+    dy = rng.standard_normal(y.shape)
+    dx = ops.conv3d_dgrad(dy, w, x.shape, stride, pad)
+    dw, _ = ops.conv3d_wgrad(dy, x, k, stride, pad)
+    entries = [tuple(int(v) for v in e) for e in np.ndindex(dw.shape)]
+    vals, mags = ops.conv3d_wgrad_entries(dy, x, k, entries, stride, pad)
+    np.testing.assert_allclose(vals, dw.reshape(-1), rtol=1e-12, atol=1e-12)
+    assert np.all(mags >= np.abs(vals) - 1e-12)
+    N, T, H, W, _ = shape
+    points = [(n, t, h, wv) for n in range(N) for t in range(T) for h in range(H) for wv in range(W)]
+    vals, mags = ops.conv3d_dgrad_entries(dy, w, x.shape, points, stride, pad)
+    np.testing.assert_allclose(vals, dx.reshape(len(points), -1), rtol=1e-12, atol=1e-12)
+    assert np.all(mags >= np.abs(vals) - 1e-12)

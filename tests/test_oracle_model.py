@@ -265,3 +265,47 @@ def test_888_model_matches_torch_fp64():
             h = _td2s(_tconv(h, p, f"dec.up{l - 1}"), (2, 2, 2))
     yt = _td2s(_tconv(_tgn(h, p, "dec.out_gn"), p, "dec.out"), (2, 2, 2))
     np.testing.assert_allclose(y, yt.permute(0, 2, 3, 4, 1).numpy(), rtol=1e-9, atol=1e-9)
+
+
+# --- BF16 activations: the oracle's rounding points against torch's bf16 casts ---
+
+def _r16(t):
+    """torch's own float32 and bfloat16 casts (round to nearest, ties to even)."""
+    return t.to(torch.float32).to(torch.bfloat16).to(torch.float64)
+
+
+def _tblock16(x, p, name):
+    h = _r16(_tconv(_r16(_tgn(x, p, name + ".gn1")), p, name + ".c1"))
+    h = _tconv(_r16(_tgn(h, p, name + ".gn2")), p, name + ".c2")
+    s = _r16(_tconv(x, p, name + ".sc")) if name + ".sc.w" in p else x
+    return _r16(s + h)
+
+
+def test_bf16_activation_model_matches_torch_bf16_casts():
+    """Oracle(act_bf16=True) rounds every stored activation as an FP32 accumulator is
+    stored in bf16; an independent torch FP64 build that applies torch's float32 and
+    bfloat16 casts at the same points gives the same latent and frames, and both
+    differ from the exact FP64 network by bf16-sized amounts."""
+    a = SMALL
+    p = {k: S.to_bf16_f32(v) for k, v in _small_params(a, seed=12).items()}
+    x = S.to_bf16_f32(S.blurred_noise_clip(4, 1, 5, 16, 24))
+    o16, o64 = Oracle(a, p, act_bf16=True), Oracle(a, p)
+    z16, z64 = o16.encode_latent(x), o64.encode_latent(x)
+    h = _r16(_tconv(_t(x).permute(0, 4, 1, 2, 3), p, "enc.stem", (1, 2, 2)))
+    for l in range(3):
+        h = _tblock16(h, p, f"enc.l{l}.b0")
+        if l < 2:
+            h = _r16(_tconv(h, p, f"enc.down{l}", (2, 2, 2)))
+    zt = _tconv(_r16(_tgn(h, p, "enc.out_gn")), p, "enc.out").permute(0, 2, 3, 4, 1).numpy()
+    np.testing.assert_allclose(z16, zt, rtol=1e-9, atol=1e-9)
+    d = np.abs(z16 - z64).max() / np.abs(z64).max()
+    assert 1e-5 < d < 0.05, d
+    codes = np.random.default_rng(3).uniform(-1, 1, z16.shape)
+    y16 = o16.decode_codes(codes, 16, 24)
+    h = _r16(_tconv(_t(codes).permute(0, 4, 1, 2, 3), p, "dec.in"))
+    for l in (2, 1, 0):
+        h = _tblock16(h, p, f"dec.l{l}.b0")
+        if l > 0:
+            h = _r16(_td2s(_tconv(h, p, f"dec.up{l - 1}"), (2, 2, 2)))
+    yt = _td2s(_tconv(_r16(_tgn(h, p, "dec.out_gn")), p, "dec.out"), (1, 2, 2))
+    np.testing.assert_allclose(y16, yt.permute(0, 2, 3, 4, 1).numpy(), rtol=1e-9, atol=1e-9)
