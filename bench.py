@@ -36,9 +36,15 @@ LEVELS = (8, 8, 8, 5, 5, 5)
 FALLBACK_PEAKS = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0}
 
 
-# ncu dram__bytes_read.sum + dram__bytes_write.sum over the conv launches of one
-# 1x3x17x720x1280 encode + decode (21.19 GB + 12.68 GB); re-measure when the conv kernel changes
-CONV_DRAM_BYTES_PER_STEP = 33.72e9
+# DRAM bytes (read + write) of the 34 conv launches of one 1x3x17x720x1280 encode + decode:
+# the ncu dram__bytes_read.sum + dram__bytes_write.sum of the same launches on a 5-frame
+# 720p clip, each launch scaled by its tensors' sizes at 17 and at 5 frames. Algorithmic:
+# every layer's input read once, its residual read once, its output written once.
+# Re-measure when the conv kernel changes.
+CONV_DRAM_BYTES_PER_STEP = 31.45e9
+CONV_ALGORITHMIC_BYTES_PER_STEP = 33.57e9
+CONV_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the 34 conv launches of a "
+                       "1x3x5x720x1280 encode + decode, each scaled to the 17-frame launch by its tensor sizes")
 
 
 def load_peaks():
@@ -245,10 +251,8 @@ def gpu_arm(args):
         "frac": conv_tflops / peak,
         "peak_source": f"{peak_src} bf16_tflops_sustained (kernel inside a long step)",
         "frac_of_burst_peak": conv_tflops / float(peaks["bf16_tflops"]),
-        # DRAM bytes (read + write) of the 34 conv launches of one step, from the ncu
-        # capture summarised in profiles/conv_dram_tokenizer_720p_bf16.md (same kernels)
         "traffic": CONV_DRAM_BYTES_PER_STEP, "traffic_unit": "bytes per step (34 launches)",
-        "traffic_algorithmic": 28.40e9,
+        "traffic_algorithmic": CONV_ALGORITHMIC_BYTES_PER_STEP, "traffic_source": CONV_TRAFFIC_SOURCE,
         "flop_per_step": prof["conv_flop"] / args.steps, "launches_per_step": prof["conv_launches"] / args.steps,
         "conv_ms_per_step": prof["conv_ms"] / args.steps,
         "conv_share_of_step": prof["conv_ms"] / max(total_ms, 1e-9),

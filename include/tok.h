@@ -361,9 +361,21 @@ int tok_groupnorm_silu(int precision, const void* d_x, int64_t frames, int64_t H
  * data that are not available here; the objective is
  * L = mean((x_hat - x)^2). FSQ rounding is passed straight through:
  * d code_i / d z_i = h_i (1 - tanh^2(z_i + s_i)) / floor(L_i/2), and 0 at
- * dropped tokens. Only residual-block inputs are kept; the activations inside
- * a block are recomputed in the backward. FULL architecture, H and W
- * multiples of s_HW, T = 1 mod s_T.
+ * dropped tokens. FULL architecture, H and W multiples of s_HW,
+ * T = 1 mod s_T.
+ *
+ * Memory mode (tok_set_train_mode, before tok_reserve_train):
+ *   TOK_TRAIN_RECOMPUTE (default): per residual block the forward keeps only
+ *     the block's input (and the GroupNorm statistics, a few KB per norm);
+ *     the backward rebuilds the block's interior, SiLU(GN1(x)), c1 of it
+ *     and SiLU(GN2(.)), from them before it runs the block's backward.
+ *   TOK_TRAIN_KEEP: the forward also keeps those three interior tensors and
+ *     the backward recomputes nothing (more memory, e.g. about 2.3 GB more at
+ *     2 x 3 x 17 x 256 x 256, and no recomputed convs).
+ * Both modes give bitwise-equal gradients. tok_backward returns TOK_ESTATE
+ * when the mode was changed after the forward it belongs to, and
+ * tok_train_forward TOK_ENOMEM when the reserved workspace was sized for the
+ * smaller mode.
  *
  * Parameters as one flat FP32 vector in the order of tok_param_info
  * (tok_param_total floats). tok_get_params copies the context's parameters
@@ -377,6 +389,9 @@ int tok_groupnorm_silu(int precision, const void* d_x, int64_t frames, int64_t H
  * token selection, Sec. 4.3 Eq. 3, or lost packets). tok_backward
  * writes dL/dparams (flat FP32, every entry written) for the most recent
  * tok_train_forward, given dL/dx_hat. tok_sgd: params -= lr * grads. */
+#define TOK_TRAIN_RECOMPUTE 0
+#define TOK_TRAIN_KEEP 1
+int tok_set_train_mode(tok_ctx* ctx, int mode);
 int64_t tok_param_total(const tok_ctx* ctx);
 int tok_get_params(tok_ctx* ctx, float* d_flat, void* stream);
 int tok_set_params_device(tok_ctx* ctx, const float* d_flat, void* stream);

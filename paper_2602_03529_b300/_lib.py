@@ -117,6 +117,7 @@ _SIGS = {
                          vp]),
     "tok_groupnorm_workspace_bytes": (sz, [i32, i64, i64, i32, i32]),
     "tok_groupnorm_silu": (i32, [i32, vp, i64, i64, i32, i32, vp, vp, f32, vp, vp, sz, vp]),
+    "tok_set_train_mode": (i32, [vp, i32]),
     "tok_param_total": (i64, [vp]),
     "tok_get_params": (i32, [vp, vp, vp]),
     "tok_set_params_device": (i32, [vp, vp, vp]),
@@ -440,6 +441,13 @@ def tok_set_params_device(ctx, d_flat, cuda_stream) -> None:
 
 def tok_train_workspace_bytes(ctx, N, T, H, W) -> int:
     return _call("tok_train_workspace_bytes", ctx, N, T, H, W)
+
+
+TOK_TRAIN_RECOMPUTE, TOK_TRAIN_KEEP = 0, 1
+
+
+def tok_set_train_mode(ctx, mode: int) -> None:
+    _ck(_call("tok_set_train_mode", ctx, mode), "tok_set_train_mode")
 
 
 def tok_reserve_train(ctx, N, T, H, W) -> None:

@@ -426,6 +426,26 @@ int launch_gn_silu(const T* x, T* y, long long frames, long long HW, int C, int 
     return launch_gn_silu_group<T>(&it, 1, C, G, gamma, beta, eps, fast, stream, status);
 }
 
+// The apply pass alone, with the (mean, rstd) an earlier launch over the same
+// tensor shape left in `scratch` (the training backward rebuilds a block's
+// normalised activations from its kept input and statistics): the same
+// chunking and arithmetic as that launch's apply pass, so the result is
+// bitwise the same.
+template <typename T>
+int launch_gn_apply_kept(const T* x, T* y, long long frames, long long HW, int C, int G, const float* gamma,
+                         const float* beta, void* scratch, bool fast, cudaStream_t stream, int* status) {
+    GnItem<T> it{x, y, frames, HW, scratch};
+    GnBatch<T, 1> B;
+    long long blocks, rows;
+    if (!gn_batch(&it, 1, C, G, &B, &blocks, &rows)) return 0;
+    return fast ? gn_apply_launch<T, true, 1>(B, blocks, C, G, gamma, beta, status, stream)
+                : gn_apply_launch<T, false, 1>(B, blocks, C, G, gamma, beta, status, stream);
+}
+template int launch_gn_apply_kept<float>(const float*, float*, long long, long long, int, int, const float*,
+                                         const float*, void*, bool, cudaStream_t, int*);
+template int launch_gn_apply_kept<__nv_bfloat16>(const __nv_bfloat16*, __nv_bfloat16*, long long, long long, int,
+                                                 int, const float*, const float*, void*, bool, cudaStream_t, int*);
+
 template <typename T>
 int launch_gn_stats(const T* x, long long frames, long long HW, int C, int G, float eps, void* scratch, int num_sms,
                     cudaStream_t stream, float2** stats_out, int* vpt_out, int* S_out) {

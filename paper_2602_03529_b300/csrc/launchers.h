@@ -50,6 +50,10 @@ template <typename T>
 int launch_gn_silu(const T* x, T* y, long long frames, long long HW, int C, int G, const float* gamma,
                    const float* beta, float eps, void* scratch, int num_sms, bool fast, cudaStream_t stream,
                    int* status = nullptr);
+// The apply pass alone, with statistics an earlier launch left in `scratch`.
+template <typename T>
+int launch_gn_apply_kept(const T* x, T* y, long long frames, long long HW, int C, int G, const float* gamma,
+                         const float* beta, void* scratch, bool fast, cudaStream_t stream, int* status);
 
 int launch_fsq(const float* z, long long ntok, const FsqConsts& f, int32_t* idx, float* codes, cudaStream_t s);
 int launch_dequant(const int32_t* idx, long long ntok, const FsqConsts& f, float* codes, cudaStream_t s);

@@ -80,6 +80,8 @@ struct tok_ctx {
     int train_N = 0, train_T = 0, train_H = 0, train_W = 0;
     bool train_ready = false;
     const void* train_x = nullptr;
+    int train_mode = TOK_TRAIN_RECOMPUTE;  // memory mode of the next reserve / forward
+    int train_mode_fwd = -1;               // mode the last training forward ran in
     std::vector<ConvW> convs;
     std::map<std::string, int> cindex;
     std::vector<GnW> gns;
@@ -625,6 +627,7 @@ struct Exec {
         a.oC = cw.Cout;
         want_gn_stats(a, w, cw.Cout);
         launch(a, cw);
+        trace_conv(cw.name, a);
         Act o{out, in.N, a.Tout, a.Hout, a.Wout, cw.Cout};
         tag_gn_stats(o, a);
         return o;
@@ -648,6 +651,7 @@ struct Exec {
         a.oC = cw.Cout / (rt * rh * rw);
         if (!out_fp32) want_gn_stats(a, w, a.oC);
         launch(a, cw);
+        trace_conv(cw.name, a);
         Act o{out, in.N, a.oT, oH, oW, a.oC};
         tag_gn_stats(o, a);
         return o;
@@ -672,6 +676,7 @@ struct Exec {
         a.oC = cw.Cout;
         if (mode == OUT_PLAIN) want_gn_stats(a, w, cw.Cout);
         launch(a, cw);
+        trace_conv(cw.name, a);
         Act o{out, N, Tout, Hout, Wout, cw.Cout};
         tag_gn_stats(o, a);
         return o;
@@ -691,6 +696,8 @@ struct Exec {
                                      g.g, g.b, c->arch.gn_eps, w.gn, c->num_sms, false, s, c->d_status));
         pend(e, 1, 2.0 * (double)frames * HW * in.C * c->esize(), name);
         c->launches += 3;
+        const size_t nb = (size_t)frames * HW * in.C * c->esize();
+        trace(name, in.p, nb, nullptr, 0, out, nb);
         return Act{out, in.N, in.T, in.H, in.W, in.C};
     }
 
@@ -708,10 +715,12 @@ struct Exec {
             a.mode = OUT_FSQ;
             a.idx = idx;
             launch(a, cw);
+            trace_conv(cw.name, a);
         } else {
             a.mode = OUT_PLAIN;
             a.out_fp32 = 1;
             launch(a, cw);
+            trace_conv(cw.name, a);
             if (idx) other([&] { return launch_fsq(z, ntok, c->fsq, idx, nullptr, s); }, (double)ntok * (4 * cw.Cout + 4));
         }
     }

@@ -2,9 +2,12 @@
 // and the hand-written backward (see include/tok.h, "Training").
 //
 // Backward per residual block y = skip(x) + c2(SiLU(GN2(c1(SiLU(GN1(x)))))):
-// recompute A1 = SiLU(GN1(x)), H = c1(A1), A2 = SiLU(GN2(H)) from the kept x,
-// then dW(c2), dA2 = c2^T(dy); dH = GN2^T(dA2); dW(c1), dA1 = c1^T(dH);
-// dx = GN1^T(dA1) + skip^T(dy). Input gradients of convs (c^T) run on the
+// A1 = SiLU(GN1(x)), H = c1(A1), A2 = SiLU(GN2(H)) are either kept from the
+// forward (TOK_TRAIN_KEEP) or rebuilt from the kept x and the kept GroupNorm
+// statistics (TOK_TRAIN_RECOMPUTE: the apply pass with the forward's mean and
+// rstd, then c1 on the same kernel and tile as the forward, so the rebuilt
+// tensors are bitwise the forward's); then dW(c2), dA2 = c2^T(dy);
+// dH = GN2^T(dA2); dW(c1), dA1 = c1^T(dH); dx = GN1^T(dA1) + skip^T(dy). Input gradients of convs (c^T) run on the
 // same conv kernels as the forward with flipped/transposed weights reading
 // ahead in time; stride-2 convs see dY spread onto their input grid; under
 // replicate padding a two-tap correction adds the clamped taps into frame 0.
@@ -39,8 +42,10 @@ struct TrainBufs {
     char* gnpart = nullptr;  // GroupNorm statistics reduced by the forward convs
     size_t gnpart_bytes = 0;
     // kept from the forward for the backward: per residual block its GN1 output,
-    // first conv output and GN2 output; the output GroupNorms' outputs; and every
-    // GroupNorm's scratch, which holds the (mean, rstd) its backward reuses
+    // first conv output and GN2 output (TOK_TRAIN_KEEP only); the output
+    // GroupNorms' outputs; and every GroupNorm's scratch, which holds the
+    // (mean, rstd) its backward (and a recomputation) reuses
+    bool keep_blocks = false;
     std::map<std::string, std::array<char*, 3>> blk;
     std::map<std::string, char*> gn_out;
     std::map<std::string, char*> gn_sc;
@@ -60,8 +65,9 @@ int adj_rows(const tok_ctx* c, int Cin) {
 }
 
 // Bump layout of the training workspace; base == nullptr only sizes it.
-TrainBufs train_layout(const tok_ctx* c, int N, int T, int H, int W, char* base) {
+TrainBufs train_layout(const tok_ctx* c, int N, int T, int H, int W, char* base, int mode) {
     TrainBufs b;
+    b.keep_blocks = mode == TOK_TRAIN_KEEP;
     size_t off = 0;
     auto take = [&](size_t bytes) -> char* {
         char* p = base ? base + off : nullptr;
@@ -116,7 +122,9 @@ TrainBufs train_layout(const tok_ctx* c, int N, int T, int H, int W, char* base)
                     const std::string nm = std::string(side ? "dec.l" : "enc.l") + std::to_string(l) + ".b" +
                                            std::to_string(k);
                     const int cin = (!side && k == 0) ? (l > 0 ? a.ch[l - 1] : a.ch[0]) : a.ch[l];
-                    b.blk[nm] = {take(vox(l) * cin * es), take(vox(l) * a.ch[l] * es), take(vox(l) * a.ch[l] * es)};
+                    if (b.keep_blocks)
+                        b.blk[nm] = {take(vox(l) * cin * es), take(vox(l) * a.ch[l] * es),
+                                     take(vox(l) * a.ch[l] * es)};
                     gn_keep(nm + ".gn1", l, cin);
                     gn_keep(nm + ".gn2", l, a.ch[l]);
                 }
@@ -179,9 +187,11 @@ struct TrainExec : Exec {
         return A;
     }
 
-    // Residual block forward into `out`; GN1 output, first conv output and GN2 output kept.
+    // Residual block forward into `out`; the GN1 output, first conv output and GN2
+    // output go to kept buffers (TOK_TRAIN_KEEP) or to work buffers.
     Act block_fwd(const std::string& name, const Act& X, void* out) {
-        const auto& kb = b.blk.at(name);
+        std::array<char*, 3> kb = {b.R1, b.R2, b.R1};
+        if (b.keep_blocks) kb = b.blk.at(name);
         Act A1 = gn_kept(name + ".gn1", X, kb[0]);
         Act H = conv(name + ".c1", A1, kb[1]);
         Act A2 = gn_kept(name + ".gn2", H, kb[2]);
@@ -366,6 +376,9 @@ struct TrainExec : Exec {
                                    grads + cw.ow, grads + cw.ob, s));
         pend(e, 0, flop, name + ".wgrad");
         c->launches += tc ? 4 : 2;
+        const size_t es = c->esize();
+        trace(name + ".wgrad", xin.p, (size_t)xin.N * xin.T * xin.H * xin.W * cw.Cin * es, dy.p,
+              (size_t)a.V * Cdy * es, nullptr, 0);
     }
 
     // Input gradient of a stride-1 conv: the adjoint conv over dY (cpad
@@ -422,6 +435,8 @@ struct TrainExec : Exec {
             sh2.name = name + ".dgrad0";
             launch(b2, sh2);
         }
+        const size_t nb = (size_t)dy.N * dy.T * dy.H * dy.W * c->esize();
+        trace(name + ".dgrad", dy.p, nb * cw.cpad, nullptr, 0, out, nb * cw.rows_pad);
         return Act{out, dy.N, dy.T, dy.H, dy.W, cw.rows_pad};
     }
 
@@ -450,10 +465,39 @@ struct TrainExec : Exec {
         c->launches += 5;
     }
 
+    // GroupNorm+SiLU of X with the statistics its forward launch kept (apply pass only).
+    void gn_apply_kept(const std::string& name, const Act& X, void* out) {
+        if (err) return;
+        const GnW& g = c->gns[c->gindex[name]];
+        const long long frames = (long long)X.N * X.T, HW = (long long)X.H * X.W;
+        const int e = pbegin();
+        if (c->bf16())
+            ck(launch_gn_apply_kept<__nv_bfloat16>(static_cast<const __nv_bfloat16*>(X.p),
+                                                   static_cast<__nv_bfloat16*>(out), frames, HW, X.C, g.G, g.g, g.b,
+                                                   b.gn_sc.at(name), true, s, c->d_status));
+        else
+            ck(launch_gn_apply_kept<float>(static_cast<const float*>(X.p), static_cast<float*>(out), frames, HW, X.C,
+                                           g.G, g.g, g.b, b.gn_sc.at(name), false, s, c->d_status));
+        pend(e, 1, 2.0 * (double)frames * HW * X.C * c->esize(), name + ".recompute");
+        c->launches += 1;
+    }
+
     // Block backward; the block-output gradient G is replaced by the block-input gradient.
     void block_bwd(const std::string& name, const Act& X, Act& G) {
-        const auto& kb = b.blk.at(name);
         const int Ch = c->convs[c->cindex[name + ".c1"]].Cout;
+        std::array<char*, 3> kb = {b.R1, b.R2, b.Z};
+        if (b.keep_blocks) {
+            kb = b.blk.at(name);
+        } else {
+            // rebuild the block's interior from its input and the kept statistics; c1
+            // runs without the statistics epilogue (its GN2 statistics are kept)
+            gn_apply_kept(name + ".gn1", X, kb[0]);
+            char* gp = w.gnpart;
+            w.gnpart = nullptr;
+            conv(name + ".c1", Act{kb[0], X.N, X.T, X.H, X.W, X.C}, kb[1]);
+            w.gnpart = gp;
+            gn_apply_kept(name + ".gn2", Act{kb[1], X.N, X.T, X.H, X.W, Ch}, kb[2]);
+        }
         Act A1{kb[0], X.N, X.T, X.H, X.W, X.C};
         Act H{kb[1], X.N, X.T, X.H, X.W, Ch};
         Act A2{kb[2], X.N, X.T, X.H, X.W, Ch};
@@ -652,6 +696,12 @@ bool train_shape_ok(const tok_ctx* c, int N, int T, int H, int W) {
 
 extern "C" {
 
+int tok_set_train_mode(tok_ctx* c, int mode) {
+    if (!c || (mode != TOK_TRAIN_RECOMPUTE && mode != TOK_TRAIN_KEEP)) return TOK_EINVAL;
+    c->train_mode = mode;
+    return TOK_OK;
+}
+
 int64_t tok_param_total(const tok_ctx* c) { return c ? c->param_total : 0; }
 
 int tok_get_params(tok_ctx* c, float* d_flat, void* stream) {
@@ -698,13 +748,13 @@ int tok_set_params_device(tok_ctx* c, const float* d_flat, void* stream) {
 
 size_t tok_train_workspace_bytes(const tok_ctx* c, int N, int T, int H, int W) {
     if (!c || !train_shape_ok(c, N, T, H, W)) return 0;
-    return train_layout(c, N, T, H, W, nullptr).total;
+    return train_layout(c, N, T, H, W, nullptr, c->train_mode).total;
 }
 
 int tok_reserve_train(tok_ctx* c, int N, int T, int H, int W) {
     if (!c) return TOK_EINVAL;
     if (!train_shape_ok(c, N, T, H, W)) return TOK_ESHAPE;
-    const size_t need = train_layout(c, N, T, H, W, nullptr).total;
+    const size_t need = train_layout(c, N, T, H, W, nullptr, c->train_mode).total;
     if (need > c->tbytes) {
         if (c->tarena) {
             cudaDeviceSynchronize();
@@ -725,12 +775,12 @@ int tok_train_forward(tok_ctx* c, const void* x, int N, int T, int H, int W, flo
                       const uint32_t* keep_bits, float* xhat, float* loss, float* dxhat, void* stream) {
     if (!c || !x || !xhat || !loss || !dxhat || !(rate == rate)) return TOK_EINVAL;
     if (!train_shape_ok(c, N, T, H, W)) return TOK_ESHAPE;
-    const size_t need = train_layout(c, N, T, H, W, nullptr).total;
+    const size_t need = train_layout(c, N, T, H, W, nullptr, c->train_mode).total;
     if (need > c->tbytes) return TOK_ENOMEM;
     TrainExec ex;
     ex.c = c;
     ex.s = static_cast<cudaStream_t>(stream);
-    ex.b = train_layout(c, N, T, H, W, c->tarena);
+    ex.b = train_layout(c, N, T, H, W, c->tarena, c->train_mode);
     ex.set_work();
     ex.forward(x, N, T, H, W, rate, seed, step, keep_bits, xhat, loss, dxhat);
     if (ex.err) return ex.err;
@@ -740,12 +790,13 @@ int tok_train_forward(tok_ctx* c, const void* x, int N, int T, int H, int W, flo
     c->train_W = W;
     c->train_x = x;
     c->train_ready = true;
+    c->train_mode_fwd = c->train_mode;
     return TOK_OK;
 }
 
 int tok_backward(tok_ctx* c, const float* dxhat, float* dparams, void* stream) {
     if (!c || !dxhat || !dparams) return TOK_EINVAL;
-    if (!c->train_ready) return TOK_ESTATE;
+    if (!c->train_ready || c->train_mode_fwd != c->train_mode) return TOK_ESTATE;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (c->adjoint_dirty) {
         const int e = pack_adjoints(c, s);
@@ -754,7 +805,7 @@ int tok_backward(tok_ctx* c, const float* dxhat, float* dparams, void* stream) {
     TrainExec ex;
     ex.c = c;
     ex.s = s;
-    ex.b = train_layout(c, c->train_N, c->train_T, c->train_H, c->train_W, c->tarena);
+    ex.b = train_layout(c, c->train_N, c->train_T, c->train_H, c->train_W, c->tarena, c->train_mode_fwd);
     ex.set_work();
     ex.grads = dparams;
     ex.backward(dxhat);

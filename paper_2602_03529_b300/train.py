@@ -2,8 +2,11 @@
 
 The step runs entirely in the CUDA library: tok_train_forward (encode ->
 Bernoulli token drop with zero fill -> decode -> MSE loss and its gradient)
-and tok_backward (hand-written backward with straight-through FSQ and
-per-residual-block recomputation). This module only marshals tensors:
+and tok_backward (hand-written backward with straight-through FSQ). By
+default the forward keeps only each residual block's input and the backward
+rebuilds the block's interior from it (per-residual-block recomputation);
+recompute=False keeps the interiors instead (more memory, no recomputed
+convs, bitwise the same gradients). This module only marshals tensors:
 `TokenizerLoss.apply(params, x, ...)` returns the loss as a torch scalar whose
 .backward() fills params.grad through tok_backward.
 """
@@ -18,10 +21,12 @@ from .tokenizer import Tokenizer, _ptr, _stream_ptr
 class Trainer:
     """Owns the flat FP32 parameter vector of a Tokenizer and the training workspace."""
 
-    def __init__(self, tk: Tokenizer, N: int, T: int, H: int, W: int):
+    def __init__(self, tk: Tokenizer, N: int, T: int, H: int, W: int, recompute: bool = True):
         self.tk = tk
         self.shape = (N, T, H, W)
+        L.tok_set_train_mode(tk.ctx, L.TOK_TRAIN_RECOMPUTE if recompute else L.TOK_TRAIN_KEEP)
         L.tok_reserve_train(tk.ctx, N, T, H, W)
+        self.workspace_bytes = L.tok_train_workspace_bytes(tk.ctx, N, T, H, W)
         n = L.tok_param_total(tk.ctx)
         self.params = torch.empty(n, device="cuda", dtype=torch.float32)
         L.tok_get_params(tk.ctx, _ptr(self.params), _stream_ptr(None))
