@@ -279,6 +279,7 @@ def gpu_arm(args):
         out["grouped"] = grouped(args, params, roofline["peak"])
     out["selection"] = selection(args, roofline["groupnorm"]["peak_gbs"])
     out["gop_smoothing"] = gop_smoothing(roofline["groupnorm"]["peak_gbs"])
+    out["token_kernels"] = token_kernels(roofline["groupnorm"]["peak_gbs"])
     if not args.no_rsa:
         tk8 = P.Tokenizer("bf16", t_stem=2)
         p8 = S.weights_for(tk8.param_spec(), seed=0)
@@ -298,41 +299,45 @@ def gpu_arm(args):
 
 def training(args, params, N=2, T=17, H=256, W=256, steps=5, warmup=2):
     """Joint training step (forward with drop + MSE + hand-written backward + SGD) of the
-    default tokenizer on a 2x3x17x256x256 BF16 batch."""
+    default tokenizer on a 2x3x17x256x256 BF16 batch, in both memory modes: per-residual-
+    block recomputation (the default; block interiors rebuilt in the backward) and keeping
+    the interiors from the forward."""
     import torch
 
     import paper_2602_03529_b300 as P
     from paper_2602_03529_b300.train import Trainer
     import synthetic as S
 
-    tk = P.Tokenizer("bf16")
-    tk.set_params(params)
-    tr = Trainer(tk, N, T, H, W)
     x = torch.from_numpy(S.blurred_noise_clip(7, N, T, H, W)).to("cuda", torch.bfloat16)
-    for i in range(warmup):
-        tr.step(x, 0.1, 1, i, lr=1e-5)
-    torch.cuda.synchronize()
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
-    for i in range(steps):
-        e = ev[i]
-        e[0].record()
-        tr.forward(x, 0.1, 1, 100 + i)
-        e[1].record()
-        tr.backward()
-        e[2].record()
-        tr.sgd(1e-5)
-        e[3].record()
-    torch.cuda.synchronize()
-    assert tk.status() == 0, "device-side error in the training step"
-    fwd = sum(e[0].elapsed_time(e[1]) for e in ev) / steps
-    bwd = sum(e[1].elapsed_time(e[2]) for e in ev) / steps
-    upd = sum(e[2].elapsed_time(e[3]) for e in ev) / steps
-    loss = float(tr.loss.item())
-    tk.close()
-    return {"workload": f"fwd+bwd step, batch {N}x3x{T}x{H}x{W}, BF16, MSE, STE, drop 10%, block intermediates "
-                        "kept from the forward, SGD with the weight re-pack",
-            "step_ms": fwd + bwd + upd, "fwd_ms": fwd, "bwd_ms": bwd, "sgd_ms": upd, "loss": loss,
-            "steps": steps, "warmup": warmup}
+    out = {"workload": f"fwd+bwd step, batch {N}x3x{T}x{H}x{W}, BF16, MSE, STE, drop 10%, SGD with the weight "
+                       "re-pack", "steps": steps, "warmup": warmup}
+    for mode, rc in (("recompute", True), ("keep", False)):
+        tk = P.Tokenizer("bf16")
+        tk.set_params(params)
+        tr = Trainer(tk, N, T, H, W, recompute=rc)
+        for i in range(warmup):
+            tr.step(x, 0.1, 1, i, lr=1e-5)
+        torch.cuda.synchronize()
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+        for i in range(steps):
+            e = ev[i]
+            e[0].record()
+            tr.forward(x, 0.1, 1, 100 + i)
+            e[1].record()
+            tr.backward()
+            e[2].record()
+            tr.sgd(1e-5)
+            e[3].record()
+        torch.cuda.synchronize()
+        assert tk.status() == 0, "device-side error in the training step"
+        fwd = sum(e[0].elapsed_time(e[1]) for e in ev) / steps
+        bwd = sum(e[1].elapsed_time(e[2]) for e in ev) / steps
+        upd = sum(e[2].elapsed_time(e[3]) for e in ev) / steps
+        out[mode] = {"step_ms": fwd + bwd + upd, "fwd_ms": fwd, "bwd_ms": bwd, "sgd_ms": upd,
+                     "loss": float(tr.loss.item()), "workspace_bytes": tr.workspace_bytes}
+        tk.close()
+    out["step_ms"] = out["recompute"]["step_ms"]  # the default mode
+    return out
 
 
 # ------------------------------------------------------------- grouped
@@ -451,6 +456,55 @@ def selection(args, hbm_gbs, streams=256, Tp=4, Hq=90, Wq=160, rate=0.25, steps=
             "note": "2 launches: digit table, then one block per latent frame (similarity, 3-pass radix "
                     "select over shared memory, tie cut by position, drop and keep bits); latency-bound per "
                     "frame (about 77 us for a 90x160 frame), not by HBM"}
+
+
+# ------------------------------------------------------------- FSQ and drop mask alone
+
+def token_kernels(hbm_gbs, steps=10, warmup=3):
+    """The FSQ (K3) and drop-mask (K4) kernels stand-alone at working sets above 1 GB:
+    tok_quantize over 2^26 latent vectors of 6 fp32 channels (24 B in + 4 B out per
+    token: 1.88 GB), tok_drop_mask over 2048 streams x 4 latent frames x 90 x 160 tokens
+    of 720p chunks at rate 0.15 (4 B in + 4 B out per token + 4 B per 32-token row word:
+    0.96 GB). Device-resident inputs; every launch streams more than 8x L2."""
+    import torch
+
+    import paper_2602_03529_b300 as P
+
+    g = torch.Generator(device="cuda").manual_seed(11)
+    ntok = 1 << 26
+    z = torch.randn((ntok, len(LEVELS)), device="cuda", generator=g)
+    idx = torch.empty(ntok, device="cuda", dtype=torch.int32)
+
+    def q():
+        P._lib.tok_quantize(z.data_ptr(), ntok, list(LEVELS), idx.data_ptr(), None, None)
+
+    shape = (2048, 4, 90, 160)
+    tok = torch.randint(0, 64000, shape, device="cuda", dtype=torch.int32, generator=g)
+    out = torch.empty_like(tok)
+    kb = torch.empty(shape[:3] + ((shape[3] + 31) // 32,), device="cuda", dtype=torch.int32)
+
+    def d(i=[0]):
+        i[0] += 1
+        P.drop_mask(tok, 0.15, seed=5, stream_id=0, chunk_id=i[0], levels=LEVELS, out=out, keep_bits=kb)
+
+    res = {"workload": "tok_quantize: 2^26 tokens x 6 fp32 channels; tok_drop_mask: 2048 x 4 x 90 x 160 tokens, "
+                       "rate 0.15", "peak_gbs": hbm_gbs}
+    for name, fn, nbytes, n in (("quantize", q, ntok * (4 * len(LEVELS) + 4), ntok),
+                                ("drop_mask", d, tok.numel() * 8 + kb.numel() * 4, tok.numel())):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        gbs = nbytes / (ms / 1e3) / 1e9
+        res[name] = {"tokens": n, "ms": ms, "algorithmic_bytes": nbytes, "achieved_gbs": gbs, "frac": gbs / hbm_gbs,
+                     "tokens_per_s": n / (ms / 1e3)}
+    return res
 
 
 # ------------------------------------------------------------- pixel residuals
@@ -790,8 +844,46 @@ def case_select(N, T, H, W):
     print("select ok", tuple(out.shape), int((out == 32036).sum()))
 
 
+def case_chunk(N, T, H, W, chunks=6):
+    """One stream of H x W (N and T unused): chunk 0, then `chunks` 4-frame chunks,
+    encode + decode each; prints per chunk the event-timed milliseconds and the
+    library's per-class kernel time (conv, GroupNorm, other), then, for the last
+    chunk, every launch with its time."""
+    import torch
+
+    import paper_2602_03529_b300 as P
+    import synthetic as S
+
+    tk = P.Tokenizer("bf16")
+    tk.set_params(S.weights_for(tk.param_spec(), seed=0))
+    x = torch.from_numpy(S.moving_rects_clip(3, 1 + 4 * chunks, H, W)[None]).to("cuda", torch.bfloat16)
+    vid = tk.stream_open(H, W)
+    tk.profile(True)
+    for k in range(chunks + 1):
+        a, b = (0, 1) if k == 0 else (4 * k - 3, 4 * k + 1)
+        xc = x[:, a:b].contiguous()
+        torch.cuda.synchronize()
+        tk.profile_read()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _, idx = tk.encode(xc, video=vid, want_z=False)
+        tk.decode(idx, H, W, video=vid, first_chunk=(k == 0))
+        e1.record()
+        torch.cuda.synchronize()
+        recs = tk.profile_records()
+        prof = tk.profile_read()
+        print(f"chunk {k}: {e0.elapsed_time(e1):.3f} ms, conv {prof['conv_ms']:.3f} ms "
+              f"({prof['conv_flop'] / 1e12:.2f} TFLOP), gn {prof['gn_ms']:.3f} ms, other {prof['other_ms']:.3f} ms, "
+              f"launches {len(recs)}")
+    for r in recs:
+        print(f"  {r['name']:<24} cls {r['cls']} {r['ms']:.4f} ms")
+    tk.stream_close(vid)
+    if tk.status() != 0:
+        sys.exit(f"device status {tk.status()}")
+
+
 CASE_SHAPES = {"clip": (1, 5, 720, 1280), "train": (2, 17, 256, 256), "train-recompute": (2, 17, 256, 256),
-               "downsample": (4, 17, 1080, 1920), "select": (256, 4, 90, 160)}
+               "downsample": (4, 17, 1080, 1920), "select": (256, 4, 90, 160), "chunk": (1, 5, 1080, 1920)}
 
 
 def run_case(args):
@@ -805,6 +897,8 @@ def run_case(args):
         case_train(*shape, recompute=True)
     elif args.case == "downsample":
         case_downsample(*shape, args.s)
+    elif args.case == "chunk":
+        case_chunk(*shape)
     else:
         case_select(*shape)
 

@@ -445,7 +445,17 @@ int tok_selftest_timeout(tok_ctx* ctx, int64_t limit_ns, void* stream);
  *              the up convs and the pixel head, the latent z (fp32) for
  *              the last encoder conv;
  *   GroupNorm+SiLU layers ("enc.l0.b0.gn1", "dec.out_gn", ...):
- *     d_in <- its input, d_out <- its output.
+ *     d_in <- its input, d_out <- its output;
+ *   in tok_train_forward the same layers as above; in tok_backward
+ *   "<conv>.wgrad" (d_in <- the conv's forward input, NULL for the stem and
+ *     the decoder input, whose weight gradient runs on a rebuilt im2col
+ *     matrix; d_res <- the gradient of its output as the weight gradient reads
+ *     it: Cdy channels, the output channels padded to the adjoint's layout
+ *     for narrow heads; before depth-to-space for the up convs and the pixel
+ *     head) and "<conv>.dgrad" (d_in <- that output gradient as the adjoint
+ *     conv reads it, zero-inserted onto the input grid for stride-2 convs;
+ *     d_out <- the input gradient, its channels padded to the adjoint's
+ *     rows).
  * A NULL buffer (or 0 bytes) skips that tensor. A buffer smaller than its
  * tensor makes the encode / decode return TOK_EINVAL. Several traces may be
  * armed at once; name == NULL disarms all. Returns TOK_EINVAL for an unknown

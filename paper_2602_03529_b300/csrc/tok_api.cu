@@ -313,7 +313,15 @@ int tok_trace_layer(tok_ctx* c, const char* name, void* in, size_t in_bytes, voi
         c->traces.clear();
         return TOK_OK;
     }
-    if (!c->cindex.count(name) && !c->gindex.count(name)) return TOK_EINVAL;
+    std::string base(name);
+    for (const char* suf : {".wgrad", ".dgrad"}) {
+        const size_t n = strlen(suf);
+        if (base.size() > n && base.compare(base.size() - n, n, suf) == 0) {
+            base.resize(base.size() - n);
+            if (!c->cindex.count(base)) return TOK_EINVAL;
+        }
+    }
+    if (!c->cindex.count(base) && !c->gindex.count(base)) return TOK_EINVAL;
     if ((!in || !in_bytes) && (!res || !res_bytes) && (!out || !out_bytes)) return TOK_EINVAL;
     c->traces.push_back(tok_ctx::Trace{name, in_bytes ? in : nullptr, in_bytes, res_bytes ? res : nullptr, res_bytes,
                                        out_bytes ? out : nullptr, out_bytes});

@@ -335,6 +335,7 @@ struct TrainExec : Exec {
                            s, kv));
         pend(e, 0, 2.0 * (double)a.V * a.Cout * kv, name + ".wgrad");
         c->launches += 4;
+        trace(name + ".wgrad", nullptr, 0, dy.p, (size_t)a.V * Cdy * c->esize(), nullptr, 0);
     }
 
     void wgrad(const std::string& name, const Act& dy, int Cdy, const Act& xin, int tst, int ss) {

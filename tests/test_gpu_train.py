@@ -179,3 +179,173 @@ def test_repacked_weights_equal_fresh_context(P):
     assert torch.equal(g1, g2)
     tk.close()
     tk2.close()
+
+
+# ------------------------------------------------------------ memory modes
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_recompute_and_keep_modes_give_equal_gradients(P, prec):
+    """Per-residual-block recomputation (the default: block interiors rebuilt in the
+    backward from the kept block input and GroupNorm statistics) and the keep mode
+    (interiors kept from the forward) give bitwise the same loss and gradient; the
+    recomputing workspace is the smaller one. A backward whose forward ran in the other
+    mode is refused."""
+    from paper_2602_03529_b300 import _lib as L
+    from paper_2602_03529_b300.train import Trainer
+    kw = dict(ch=(64, 128, 256), blocks=2)
+    p = _params(Arch(**kw), 11)
+    if prec == "bf16":
+        p = {k: S.to_bf16_f32(v) for k, v in p.items()}
+    N, T, H, W = 1, 9, 32, 32
+    dt = torch.bfloat16 if prec == "bf16" else torch.float32
+    xd = torch.from_numpy(S.blurred_noise_clip(5, N, T, H, W)).to("cuda", dt)
+    out = {}
+    for rc in (True, False):
+        tk = P.Tokenizer(prec, **kw)
+        tk.set_params(p)
+        tr = Trainer(tk, N, T, H, W, recompute=rc)
+        loss = tr.forward(xd, 0.2, 7, 3).clone()
+        g = tr.backward().clone()
+        torch.cuda.synchronize()
+        assert tk.status() == 0
+        out[rc] = (loss, g, tr.workspace_bytes)
+        if rc:
+            L.tok_set_train_mode(tk.ctx, L.TOK_TRAIN_KEEP)
+            with pytest.raises(L.TokError) as e:
+                tr.backward()
+            assert e.value.code == L.TOK_ESTATE
+        tk.close()
+    assert torch.equal(out[True][0], out[False][0])
+    assert torch.equal(out[True][1], out[False][1])
+    assert out[True][2] < out[False][2], (out[True][2], out[False][2])
+
+
+def test_fp32_gradient_elementwise(P):
+    """FP32 path, every gradient element against the FP64 oracle:
+    |g - g_ref| <= 1e-4 * max|g_ref| (of its tensor) + 1e-3 * |g_ref|."""
+    from paper_2602_03529_b300.train import Trainer
+    arch = Arch(ch=(16, 32, 64), blocks=1)
+    p = _params(arch, 11)
+    N, T, H, W = 1, 5, 32, 32
+    x = S.blurred_noise_clip(5, N, T, H, W)
+    tk = P.Tokenizer("fp32", ch=(16, 32, 64), blocks=1)
+    tk.set_params(p)
+    tr = Trainer(tk, N, T, H, W)
+    Tq, Hq, Wq = tk.latent_shape(T, H, W)
+    dropped = ops.drop_mask(N, Tq, Hq, Wq, 0.2, 7, 0, 3)
+    tr.forward(torch.from_numpy(x).cuda(), 0.2, 7, 3)
+    g = tr.backward().cpu().numpy().astype(np.float64)
+    torch.cuda.synchronize()
+    assert tk.status() == 0
+    o = OracleTrain(arch, p, surrogate=False)
+    _, _, saved = o.forward_train(x, dropped)
+    gref, _ = o.backward(saved)
+    off, worst = 0, (None, 0.0)
+    for name, shp in tk.param_list():
+        n = int(np.prod(shp))
+        gg, ref = g[off:off + n].reshape(shp), gref[name]
+        off += n
+        tol = 1e-4 * np.abs(ref).max() + 1e-3 * np.abs(ref) + 1e-30
+        r = float((np.abs(gg - ref) / tol).max())
+        worst = max(worst, (name, r), key=lambda t: t[1])
+    tk.close()
+    print("fp32 elementwise worst (error / tolerance)", worst)
+    assert worst[1] <= 1.0, worst
+
+
+# --------------------------------------- sampled gradients at the training shape
+
+# conv -> (kernel size, forward stride, shapes at 2 x 3 x 17 x 256 x 256: forward input,
+# output gradient as the weight gradient reads it, input gradient of the adjoint conv)
+_L0, _L1 = (2, 17, 128, 128), (2, 9, 64, 64)
+SAMPLED = {
+    "enc.stem": (3, (1, 2, 2), None, _L0 + (128,), None),
+    "enc.l0.b0.c1": (3, (1, 1, 1), _L0 + (128,), _L0 + (128,), _L0 + (128,)),
+    "enc.down0": (3, (2, 2, 2), _L0 + (128,), _L1 + (128,), _L0 + (128,)),
+    "enc.l1.b0.sc": (1, (1, 1, 1), _L1 + (128,), _L1 + (256,), _L1 + (128,)),
+    "dec.up0": (3, (1, 1, 1), _L1 + (256,), _L1 + (1024,), _L1 + (256,)),
+    "dec.out": (3, (1, 1, 1), _L0 + (128,), _L0 + (64,), _L0 + (128,)),
+}
+
+
+def test_bf16_sampled_gradients_at_training_shape(P):
+    """The weight and input gradients of the BF16 training step at its benchmark shape
+    (2 x 3 x 17 x 256 x 256, default tokenizer, recomputing backward, full split-K),
+    checked on sampled entries against the oracle's single-entry gradients, computed
+    from the traced forward input and output gradient of each layer: the stem (im2col),
+    a level-0 3x3x3 conv, the stride-2 down conv, a 1x1x1 shortcut, the up conv before
+    its depth-to-space, the 12-channel pixel head. Weight gradients (fp32 sums of exact
+    bf16 products over ~560k voxels): |g - ref| <= 2e-5 * sum|terms|; input gradients
+    (bf16): |g - ref| <= 2^-8 |ref| + 2e-5 * sum|terms|, and at input frame 0 of a
+    replicate-padded 3x3x3 conv 2^-8 (|ref| + sum|terms|): there the adjoint reads the
+    summed taps of the padded frames (W0 + W1 + W2, W0 + W1) as one bf16 weight map,
+    each sum rounded to bf16. Also: the keep mode gives bitwise the same gradient at
+    this shape."""
+    from paper_2602_03529_b300.train import Trainer
+    arch = Arch()
+    p = {k: S.to_bf16_f32(v) for k, v in _params(arch, 11).items()}
+    N, T, H, W = 2, 17, 256, 256
+    x = S.to_bf16_f32(S.blurred_noise_clip(5, N, T, H, W))
+    xd = torch.from_numpy(x).to("cuda", torch.bfloat16)
+    tk = P.Tokenizer("bf16")
+    tk.set_params(p)
+    tr = Trainer(tk, N, T, H, W)
+    bufs = {}
+    for name, (k, st, xs, ys, dxs) in SAMPLED.items():
+        b = {"x": None if xs is None else torch.empty(xs, device="cuda", dtype=torch.bfloat16),
+             "dy": torch.empty(ys, device="cuda", dtype=torch.bfloat16),
+             "dx": None if dxs is None else torch.empty(dxs, device="cuda", dtype=torch.bfloat16)}
+        tk.trace_layer(name + ".wgrad", b["x"], b["dy"], None)
+        if b["dx"] is not None:
+            tk.trace_layer(name + ".dgrad", None, None, b["dx"])
+        bufs[name] = b
+    tr.forward(xd, 0.1, 3, 1)
+    g = tr.backward().clone()
+    torch.cuda.synchronize()
+    assert tk.status() == 0
+    tk.trace_layer(None)
+    offs, o = {}, 0
+    for name, shp in tk.param_list():
+        offs[name] = (o, tuple(shp))
+        o += int(np.prod(shp))
+    gh = g.cpu().numpy().astype(np.float64)
+    rng = np.random.default_rng(17)
+    worst = {}
+    for name, (k, st, xs, ys, dxs) in SAMPLED.items():
+        b = bufs[name]
+        w = p[name + ".w"]
+        Cout, Cin = w.shape[0], w.shape[-1]
+        xin = x if name == "enc.stem" else b["x"].float().cpu().numpy()
+        dy = b["dy"][..., :Cout].float().cpu().numpy()
+        ent = [(int(rng.integers(Cout)), int(rng.integers(k)), int(rng.integers(k)), int(rng.integers(k)),
+                int(rng.integers(Cin))) for _ in range(12)]
+        ent += [(0, 0, 0, 0, 0), (Cout - 1, k - 1, k - 1, k - 1, Cin - 1)]
+        ref, mag = ops.conv3d_wgrad_entries(dy, xin, (k, k, k), ent, st)
+        o0, shp = offs[name + ".w"]
+        got = np.array([gh[o0 + np.ravel_multi_index(e, shp)] for e in ent])
+        r = np.abs(got - ref) / (2e-5 * mag + 1e-30)
+        worst[name + " dW"] = float(r.max())
+        if b["dx"] is None:
+            continue
+        Nn, Tn, Hn, Wn = xs[:4]
+        pts = [(0, 0, 0, 0), (Nn - 1, Tn - 1, Hn - 1, Wn - 1), (1, 1, Hn - 1, 0)]
+        pts += [(int(rng.integers(Nn)), int(rng.integers(Tn)), int(rng.integers(Hn)), int(rng.integers(Wn)))
+                for _ in range(9)]
+        ref, mag = ops.conv3d_dgrad_entries(dy, w, xs, pts, st)
+        got = np.stack([b["dx"][n, t, h, wv, :Cin].double().cpu().numpy() for n, t, h, wv in pts])
+        fold = np.array([t == 0 and k == 3 for _, t, _, _ in pts])[:, None]
+        tol = 2.0 ** -8 * np.abs(ref) + np.where(fold, 2.0 ** -8, 2e-5) * mag + 1e-30
+        r = np.abs(got - ref) / tol
+        worst[name + " dX"] = float(r.max())
+    print("sampled gradients, worst error / tolerance:", worst)
+    assert max(worst.values()) <= 1.0, worst
+    tk.close()
+    tk2 = P.Tokenizer("bf16")
+    tk2.set_params(p)
+    tr2 = Trainer(tk2, N, T, H, W, recompute=False)
+    tr2.forward(xd, 0.1, 3, 1)
+    g2 = tr2.backward().clone()
+    torch.cuda.synchronize()
+    assert tk2.status() == 0
+    assert torch.equal(g, g2)
+    tk2.close()
