@@ -286,8 +286,7 @@ def gpu_arm(args):
         tk8.close()
         out["rsa_8x8x8"] = rsa_8x8x8(p8, roofline["groupnorm"]["peak_gbs"])
     if not args.no_serve:
-        cap = value / world * args.H * args.W * 3.94e6  # algorithmic FLOP/s one GPU sustains
-        out["serving"] = serving(args, params, cap, rank, world)
+        out["serving"] = serving(args, params, rank, world)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args)
     R.barrier()
@@ -660,7 +659,7 @@ def rsa_8x8x8(params8, hbm_gbs, N=4, T=17, steps=3, warmup=2):
 SERVE_RES = [(480, 854), (720, 1280), (1080, 1920)]
 
 
-def serving(args, params, capacity_flops, rank, world):
+def serving(args, params, rank, world):
     """Streaming loop: Poisson-arriving streams of mixed 480p/720p/1080p at 30 fps, causal
     4-frame chunks with on-device conv caches, per-chunk token drop U[0, 30%], BF16."""
     import numpy as np
@@ -668,7 +667,7 @@ def serving(args, params, capacity_flops, rank, world):
 
     import synthetic as S
     from paper_2602_03529_b300 import replicas as R
-    from paper_2602_03529_b300.serve import GpuExecutor, Server, StreamSpec
+    from paper_2602_03529_b300.serve import GpuExecutor, MemoryPool, Server, StreamSpec
 
     n = args.serve_streams
     rng = np.random.default_rng(1)
@@ -682,33 +681,41 @@ def serving(args, params, capacity_flops, rank, world):
     def content(spec):
         return torch.roll(clips[((spec.H, spec.W), spec.sid % 2)], shifts=spec.sid % 9, dims=0)
 
-    slots = {SERVE_RES[0]: 8, SERVE_RES[1]: 8, SERVE_RES[2]: 4}
     mb = args.serve_batch
-    ex = GpuExecutor(args.serve_lanes, params, slots, content_fn=content, max_batch=mb, priorities=True)
-    budget = args.serve_load * capacity_flops
+    ex = GpuExecutor(args.serve_lanes, params, None, content_fn=content, max_batch=mb, priorities=True,
+                     resolutions=SERVE_RES)
 
     # chunk time of each resolution alone on the urgent lane, with 25% for sharing the GPU
-    alone = ex.calibrate()
+    alone = ex.calibrate(resolutions=SERVE_RES)
 
     def service_time(spec):
         return 1.25 * alone[(spec.H, spec.W)]
 
+    # admission: memory from the device's free bytes (conv caches + buffers per stream),
+    # compute by the streams' measured chunk time per second against the load bound
+    mem_budget = ex.memory_budget()
+    pool = MemoryPool(ex, mem_budget)
     # warm-up: every lane, every resolution, batches of every size
     warm = [StreamSpec(10_000 + i, *SERVE_RES[i % 3], start=0.0, n_chunks=2) for i in range(12)]
-    Server(ex, args.serve_lanes, slots, 1e30, stall_timeout=5.0, max_batch=mb).run(warm, horizon=1.0)
+    Server(ex, args.serve_lanes, pool, 1e30, stall_timeout=5.0, max_batch=mb).run(warm, horizon=1.0)
     torch.cuda.synchronize()
-    rep = Server(ex, args.serve_lanes, slots, budget, target_latency=0.033, stall_timeout=1.0,
-                 service_time=service_time, max_batch=mb, align_phases=not args.serve_no_align).run(
-        mine, horizon=args.serve_horizon)
+    rep = Server(ex, args.serve_lanes, pool, 0.0, target_latency=0.033, stall_timeout=1.0,
+                 service_time=service_time, max_batch=mb, align_phases=not args.serve_no_align,
+                 load=args.serve_load).run(mine, horizon=args.serve_horizon)
     torch.cuda.synchronize()
     assert all(s == 0 for s in ex.status()), "device-side error while serving"
+    slots_opened = {f"{h}x{w}": sum(1 for x in ex.slots.get((h, w), []) if x is not None) for h, w in SERVE_RES}
+    stream_gb = {f"{h}x{w}": ex.stream_bytes((h, w)) / 1e9 for h, w in SERVE_RES}
     ex.close()
     rep.pop("admission_wait_s", None)  # per-stream detail; the p50 stays
     rep.update({"lanes": args.serve_lanes, "max_batch": mb, "phase_aligned": not args.serve_no_align,
                 "urgent": {f"{h}x{w}": service_time(StreamSpec(0, h, w, 0.0, 1)) <= 0.033 for h, w in SERVE_RES},
                 "service_ms": {f"{h}x{w}": 1e3 * service_time(StreamSpec(0, h, w, 0.0, 1)) for h, w in SERVE_RES},
-                "slots": {f"{h}x{w}": k for (h, w), k in slots.items()},
-                "budget_tflops": budget / 1e12, "load_factor": args.serve_load,
+                "admission": {"memory_budget_gb": mem_budget / 1e9, "stream_gb": stream_gb,
+                              "slots_opened": slots_opened, "memory_allocated_gb": pool.allocated / 1e9,
+                              "compute": "sum over admitted streams of chunk service time x 7.5 chunks/s "
+                                         f"<= {args.serve_load}"},
+                "load_factor": args.serve_load,
                 "stream_chunks": args.serve_chunks, "arrival_horizon_s": args.serve_horizon,
                 "drop_rate": "U[0, 0.30] per chunk", "target_ms": 33.0})
     return rep
@@ -922,7 +929,8 @@ def main():
     ap.add_argument("--serve-horizon", type=float, default=20.0)
     ap.add_argument("--serve-chunks", type=int, default=16)
     ap.add_argument("--serve-lanes", type=int, default=2)
-    ap.add_argument("--serve-load", type=float, default=0.6)
+    ap.add_argument("--serve-load", type=float, default=0.75,
+                    help="admitted streams' GPU time per second (measured chunk times) at most this")
     ap.add_argument("--serve-batch", type=int, default=4)
     ap.add_argument("--serve-no-align", action="store_true")
     ap.add_argument("--case", choices=sorted(CASE_SHAPES), help="run one fixed profiling workload and exit")

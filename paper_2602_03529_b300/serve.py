@@ -31,10 +31,20 @@ Scheduling:
     admission, like one that finds no free slot. The offset is part of the
     reported admission wait; chunk latencies are still counted from each
     chunk's last frame.
-  * admission: a stream is admitted when a cache slot of its resolution is
-    free (memory: tok_stream_bytes per slot, preallocated) and its compute
-    demand (FLOP/s at its frame rate) fits the compute budget; otherwise it
-    waits in arrival order.
+  * admission: a stream is admitted when its conv caches fit in device memory
+    and its compute demand fits the compute budget; otherwise it waits in
+    arrival order. Memory: with a byte budget (from free device memory,
+    cudaMemGetInfo, in GpuExecutor.memory_budget) a stream of H x W takes
+    tok_stream_bytes(H, W); a stream's caches (a slot) are opened when no
+    free slot of its resolution exists and the bytes fit, kept when the
+    stream ends and handed to the next stream of that resolution, and free
+    slots of other resolutions are closed when a new one does not fit
+    otherwise (MemoryPool); a fixed slot table per resolution is the other
+    form. Compute: with per-chunk service times and a load bound, a stream
+    demands service time x chunks per second of the GPU and is admitted
+    while the admitted streams' sum stays within the bound (the service
+    times are measured on chunks, not derived from clip throughput);
+    otherwise FLOP/s at its frame rate against a FLOP/s budget.
   * dispatch: among ready chunks of admitted streams (one in flight per
     stream, in order), earliest deadline first (deadline = ready + target).
   * a stream whose next chunk has not arrived `stall_timeout` after it was
@@ -87,12 +97,65 @@ class StreamState:
     runs: list = dataclasses.field(default_factory=list)    # dispatched -> done
 
 
+class SlotTable:
+    """A fixed number of preallocated cache slots per resolution."""
+
+    def __init__(self, slots_per_res: dict):
+        self.free = {res: list(range(n)) for res, n in slots_per_res.items()}
+
+    def acquire(self, res):
+        return self.free[res].pop() if self.free.get(res) else None
+
+    def release(self, res, slot):
+        self.free[res].append(slot)
+
+
+class MemoryPool:
+    """Cache slots admitted by device memory. A stream of resolution `res` needs
+    `ex.stream_bytes(res)` bytes; the slots ever opened (`ex.open_slot(res)`) may
+    hold at most `budget` bytes together. A released slot stays open for the next
+    stream of its resolution; a new slot that does not fit closes free slots of
+    other resolutions (largest first, `ex.close_slot`) before giving up."""
+
+    def __init__(self, ex, budget_bytes: float):
+        self.ex = ex
+        self.budget = budget_bytes
+        self.allocated = 0.0
+        self.free: dict = {}
+        self.opened: dict = {}
+
+    def acquire(self, res):
+        if self.free.get(res):
+            return self.free[res].pop()
+        need = self.ex.stream_bytes(res)
+        while self.allocated + need > self.budget:
+            others = sorted((r for r, v in self.free.items() if v and r != res),
+                            key=lambda r: -self.ex.stream_bytes(r))
+            if not others:
+                return None
+            r = others[0]
+            self.ex.close_slot(r, self.free[r].pop())
+            self.allocated -= self.ex.stream_bytes(r)
+            self.opened[r] -= 1
+        slot = self.ex.open_slot(res)
+        self.allocated += need
+        self.opened[res] = self.opened.get(res, 0) + 1
+        return slot
+
+    def release(self, res, slot):
+        self.free.setdefault(res, []).append(slot)
+
+
 class Server:
-    def __init__(self, executor, n_lanes: int, slots_per_res: dict, budget_flops: float,
+    def __init__(self, executor, n_lanes: int, slots_per_res, budget_flops: float,
                  target_latency: float = 0.033, stall_timeout: float = 0.5,
                  clock: Callable[[], float] | None = None, sleep: Callable[[float], None] | None = None,
                  service_time: Callable[[StreamSpec], float] | None = None, max_batch: int = 1,
-                 align_phases: bool = False, guard_s: float = 0.002):
+                 align_phases: bool = False, guard_s: float = 0.002, load: float | None = None):
+        """slots_per_res: {(H, W): n} (a fixed slot table) or a MemoryPool.
+        load: with service_time, admit while the admitted streams' GPU time per
+        second (chunk service time x chunks per second) stays within `load`
+        (budget_flops is then unused)."""
         self.ex = executor
         self.n_lanes = n_lanes
         self.service_time = service_time
@@ -100,7 +163,8 @@ class Server:
         self.align = align_phases and service_time is not None
         self.guard = guard_s
         self.windows: dict[int, tuple[float, float, float]] = {}  # sid -> (start, length, period)
-        self.free_slots = {res: list(range(n)) for res, n in slots_per_res.items()}
+        self.slots = slots_per_res if hasattr(slots_per_res, "acquire") else SlotTable(slots_per_res)
+        self.load = load if service_time is not None else None
         self.budget = budget_flops
         self.target = target_latency
         self.stall_timeout = stall_timeout
@@ -147,9 +211,9 @@ class Server:
                     st.done = True
                     active.remove(st)
                     self.windows.pop(st.spec.sid, None)
-                    used -= st.spec.demand_flops()
-                    self.free_slots[(st.spec.H, st.spec.W)].append(st.slot)
+                    used -= self._demand(st.spec)
                     self.ex.release(st.spec, st.slot)
+                    self.slots.release((st.spec.H, st.spec.W), st.slot)
             # 3. arrivals and admission (arrival order)
             while ai < len(arrivals) and arrivals[ai].start <= t and arrivals[ai].start <= horizon:
                 waiting.append(states[arrivals[ai].sid])
@@ -157,16 +221,21 @@ class Server:
             while waiting:
                 st = waiting[0]
                 res = (st.spec.H, st.spec.W)
-                if not self.free_slots.get(res) or used + st.spec.demand_flops() > self.budget:
+                cap = self.load if self.load is not None else self.budget
+                if used + self._demand(st.spec) > cap:
                     break
-                off = self._offset(st.spec, t)
+                off = self._offset(st.spec, t, commit=False)
                 if off is None:
                     break
+                slot = self.slots.acquire(res)
+                if slot is None:
+                    break
+                self._offset(st.spec, t)
                 waiting.pop(0)
-                st.slot = self.free_slots[res].pop()
+                st.slot = slot
                 self.ex.attach(st.spec, st.slot)
                 st.admitted_at = t + off
-                used += st.spec.demand_flops()
+                used += self._demand(st.spec)
                 active.append(st)
                 admitted_total += 1
             max_admitted = max(max_admitted, len(active))
@@ -205,10 +274,18 @@ class Server:
             self.sleep(poll_s)
         return self._report(states, max_admitted, admitted_total, now())
 
-    def _offset(self, spec, t) -> float | None:
+    def _demand(self, spec) -> float:
+        """A stream's share of the compute budget: GPU seconds per second (with a load
+        bound and service times) or FLOP/s."""
+        if self.load is not None:
+            return self.service_time(spec) * spec.fps / 4.0
+        return spec.demand_flops()
+
+    def _offset(self, spec, t, commit: bool = True) -> float | None:
         """Start offset (s) of a newly admitted stream: 0 unless phases are aligned; then
         the earliest offset in [0, period) whose window avoids every admitted urgent
-        stream's window, or None when there is none (the stream waits)."""
+        stream's window, or None when there is none (the stream waits). commit=False
+        only looks."""
         if not self.align or not self.urgent(spec):
             return 0.0
         period = 4.0 / spec.fps
@@ -224,7 +301,7 @@ class Server:
 
         cands = sorted({0.0} | {(b0 + db - t) % period for b0, db, _ in self.windows.values()})
         off = next((c for c in cands if clear(t + c)), None)
-        if off is not None:
+        if off is not None and commit:
             self.windows[spec.sid] = (t + off, d, period)
         return off
 
@@ -294,13 +371,16 @@ class Server:
 
 class GpuExecutor:
     """Runs chunks through the CUDA library: one tokenizer context + CUDA stream per lane
-    (lane 0 on the highest stream priority when `priorities`), preallocated stream-cache
-    slots per resolution, one content loop per stream. A submitted batch is one grouped
-    encode, a drop mask per chunk and one grouped decode."""
+    (lane 0 on the highest stream priority when `priorities`), stream-cache slots per
+    resolution (preallocated from `slots_per_res`, or opened and closed by a MemoryPool
+    on the executor's stream_bytes / open_slot / close_slot), one content loop per
+    stream. A submitted batch is one grouped encode, a drop mask per chunk and one
+    grouped decode."""
 
-    def __init__(self, n_lanes: int, params: dict, slots_per_res: dict, drop_seed: int = 1000,
+    def __init__(self, n_lanes: int, params: dict, slots_per_res: dict | None = None, drop_seed: int = 1000,
                  drop_range=(0.0, 0.30), content_frames: int = 9, keep_outputs: bool = False,
-                 arch: dict | None = None, content_fn=None, max_batch: int = 1, priorities: bool = False):
+                 arch: dict | None = None, content_fn=None, max_batch: int = 1, priorities: bool = False,
+                 resolutions=None):
         import numpy as np
         import torch
 
@@ -324,10 +404,12 @@ class GpuExecutor:
         self.s_t = tk0.s_t
         self.slots = {}
         self.max_batch = max(1, max_batch)
-        big = max(slots_per_res, key=lambda r: r[0] * r[1])
+        res = list(slots_per_res) if slots_per_res else list(resolutions)
+        big = max(res, key=lambda r: r[0] * r[1])
+        nb = min(self.max_batch, sum(slots_per_res.values())) if slots_per_res else self.max_batch
         for lane in self.lanes:
-            lane["tk"].reserve_batch([(1, self.s_t, *big)] * min(self.max_batch, sum(slots_per_res.values())))
-        for (H, W), n in slots_per_res.items():
+            lane["tk"].reserve_batch([(1, self.s_t, *big)] * nb)
+        for (H, W), n in (slots_per_res or {}).items():
             self.slots[(H, W)] = [tk0.stream_open(H, W) for _ in range(n)]
         self.bufs = {}
         self.drop_seed = drop_seed
@@ -341,6 +423,39 @@ class GpuExecutor:
         self.outputs = {}
         self.tokens = {}
         self._np = np
+
+    # -- memory admission (MemoryPool) ------------------------------------------
+    def stream_bytes(self, res) -> int:
+        """Device bytes one stream of resolution res holds: its conv caches
+        (tok_stream_bytes) plus its source frames and its chunk's token and output
+        buffers."""
+        H, W = res
+        caches = self.lanes[0]["tk"].stream_bytes(H, W)
+        Tq, Hq, Wq = self.lanes[0]["tk"].latent_shape(1, H, W)
+        bufs = 3 * Hq * Wq * 4 + (self.s_t + 1) * H * W * 3 * 4
+        return caches + bufs + self.content_frames * H * W * 3 * 2
+
+    def open_slot(self, res) -> int:
+        hs = self.slots.setdefault(res, [])
+        for i, h in enumerate(hs):
+            if h is None:
+                hs[i] = self.lanes[0]["tk"].stream_open(*res)
+                return i
+        hs.append(self.lanes[0]["tk"].stream_open(*res))
+        return len(hs) - 1
+
+    def close_slot(self, res, slot) -> None:
+        self.torch.cuda.synchronize()  # no lane may still run a chunk on these caches
+        self.lanes[0]["tk"].stream_close(self.slots[res][slot])
+        self.slots[res][slot] = None
+        self.bufs.pop((res[0], res[1], slot), None)
+
+    def memory_budget(self, reserve_bytes: float = 4e9, fraction: float = 0.9) -> float:
+        """Bytes of stream state the device can still hold: the free device memory
+        (cudaMemGetInfo) after the lanes' workspaces, less a reserve, times `fraction`."""
+        self.torch.cuda.synchronize()
+        free, _ = self.torch.cuda.mem_get_info()
+        return max(0.0, (free - reserve_bytes) * fraction)
 
     def _content(self, spec):
         """The stream's source frames on the device, made on a side stream (an event marks
@@ -387,25 +502,26 @@ class GpuExecutor:
             }
         return self.bufs[key]
 
-    def calibrate(self, reps: int = 5) -> dict:
-        """Seconds one chunk of each slot resolution takes alone on lane 0 (median of
-        `reps` steady-state chunks through a stream slot, which is reset afterwards)."""
+    def calibrate(self, reps: int = 5, resolutions=None) -> dict:
+        """Seconds one chunk of each resolution takes alone on lane 0 (median of `reps`
+        steady-state chunks through a stream slot opened for it and closed after)."""
         torch = self.torch
         out = {}
-        for (H, W) in self.slots:
+        for (H, W) in (resolutions or list(self.slots)):
             spec = StreamSpec(-1 - len(out), H, W, 0.0, reps + 1)
-            self.attach(spec, 0)
+            slot = self.open_slot((H, W))
+            self.attach(spec, slot)
             times = []
             for k in range(reps + 1):
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(self.lanes[0]["stream"])
-                self.submit(0, [(spec, 0, k)])
+                self.submit(0, [(spec, slot, k)])
                 e1.record(self.lanes[0]["stream"])
                 e1.synchronize()
                 if k > 0:
                     times.append(e0.elapsed_time(e1) / 1e3)
-            self.release(spec, 0)
-            self.lanes[0]["tk"].stream_reset(self.slots[(H, W)][0])
+            self.release(spec, slot)
+            self.close_slot((H, W), slot)
             out[(H, W)] = sorted(times)[len(times) // 2]
         return out
 
@@ -465,6 +581,7 @@ class GpuExecutor:
     def close(self):
         for (H, W), hs in self.slots.items():
             for h in hs:
-                self.lanes[0]["tk"].stream_close(h)
+                if h is not None:
+                    self.lanes[0]["tk"].stream_close(h)
         for lane in self.lanes:
             lane["tk"].close()

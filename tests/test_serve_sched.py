@@ -181,3 +181,59 @@ def test_urgent_stream_without_a_free_window_waits_for_admission():
     assert rep["chunks"] == 21 and rep["p99_ms"] <= 22.0
     waits = sorted(rep["admission_wait_s"].values())
     assert waits[5] < 4 / 30.0 and waits[6] > 0.2   # the 7th waited for a retirement
+
+
+class FakeMemExec(FakeExec):
+    """FakeExec with device memory: a stream of (H, W) holds H * W bytes; slots are
+    opened and closed on demand."""
+
+    def __init__(self, clock, dur):
+        super().__init__(clock, dur)
+        self.opened, self.closed = [], []
+        self.n = {}
+
+    def stream_bytes(self, res):
+        return res[0] * res[1]
+
+    def open_slot(self, res):
+        self.n[res] = self.n.get(res, 0) + 1
+        self.opened.append(res)
+        return self.n[res] - 1
+
+    def close_slot(self, res, slot):
+        self.closed.append((res, slot))
+
+
+def test_admission_by_memory_reuses_and_reclaims_slots():
+    """Memory budget 200 bytes; 8x8 streams take 64, 12x12 streams 144. Three 8x8
+    streams fit together (192), the fourth waits for one to end and takes its slot
+    (no new allocation); a 12x12 stream that arrives when only free 8x8 slots remain
+    closes all three of them to fit (144 + 64 > 200)."""
+    from paper_2602_03529_b300.serve import MemoryPool
+    c = Clock()
+    ex = FakeMemExec(c, {(8, 8): 0.005, (12, 12): 0.005})
+    pool = MemoryPool(ex, 200)
+    specs = [StreamSpec(i, 8, 8, start=0.001 * i, n_chunks=3) for i in range(4)]
+    specs.append(StreamSpec(9, 12, 12, start=1.0, n_chunks=2))
+    rep = Server(ex, 2, pool, 1e30, stall_timeout=0.2, clock=c, sleep=c.sleep).run(specs, horizon=2.0,
+                                                                                    poll_s=1e-3)
+    assert rep["admitted_total"] == 5 and rep["never_admitted"] == 0
+    assert rep["max_concurrent"] == 3
+    waits = rep["admission_wait_s"]
+    assert max(waits[i] for i in range(3)) < 0.01 and waits[3] > 0.1   # the 4th waited for memory
+    assert ex.opened == [(8, 8)] * 3 + [(12, 12)]                      # its slot was reused
+    assert len(ex.closed) == 3 and all(r == (8, 8) for r, _ in ex.closed)
+    assert pool.allocated <= 200
+
+
+def test_compute_admission_by_measured_chunk_time():
+    """With service times and a load bound, a stream demands service x chunks per second
+    of the GPU: 30 ms chunks at 7.5 chunks/s are 0.225 each, so a 0.5 bound admits two."""
+    c = Clock()
+    dur = {(8, 8): 0.030}
+    ex = FakeExec(c, dur)
+    svc = lambda spec: dur[(spec.H, spec.W)]  # noqa: E731
+    specs = [StreamSpec(i, 8, 8, start=0.0, n_chunks=3) for i in range(4)]
+    rep = Server(ex, 2, {(8, 8): 4}, 0.0, stall_timeout=0.2, clock=c, sleep=c.sleep, service_time=svc,
+                 load=0.5).run(specs, horizon=2.0, poll_s=1e-3)
+    assert rep["max_concurrent"] == 2 and rep["admitted_total"] == 4
