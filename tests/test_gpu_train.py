@@ -275,7 +275,11 @@ def test_bf16_sampled_gradients_at_training_shape(P):
     from the traced forward input and output gradient of each layer: the stem (im2col),
     a level-0 3x3x3 conv, the stride-2 down conv, a 1x1x1 shortcut, the up conv before
     its depth-to-space, the 12-channel pixel head. Weight gradients (fp32 sums of exact
-    bf16 products over ~560k voxels): |g - ref| <= 2e-5 * sum|terms|; input gradients
+    bf16 products over up to ~560k voxels): |g - ref| <= 2e-5 * sum|terms| + 5e-4 |ref|,
+    the second term for the tensor cores' FP32 accumulation, which truncates toward zero
+    over a long split (measured on the 1024-channel up conv: every entry 0.3 - 2.3e-4
+    closer to zero than the exact sum; a wrong tap, channel or padding rule is off by
+    the order of |ref| itself); input gradients
     (bf16): |g - ref| <= 2^-8 |ref| + 2e-5 * sum|terms|, and at input frame 0 of a
     replicate-padded 3x3x3 conv 2^-8 (|ref| + sum|terms|): there the adjoint reads the
     summed taps of the padded frames (W0 + W1 + W2, W0 + W1) as one bf16 weight map,
@@ -323,8 +327,12 @@ def test_bf16_sampled_gradients_at_training_shape(P):
         ref, mag = ops.conv3d_wgrad_entries(dy, xin, (k, k, k), ent, st)
         o0, shp = offs[name + ".w"]
         got = np.array([gh[o0 + np.ravel_multi_index(e, shp)] for e in ent])
-        r = np.abs(got - ref) / (2e-5 * mag + 1e-30)
+        r = np.abs(got - ref) / (2e-5 * mag + 5e-4 * np.abs(ref) + 1e-30)
         worst[name + " dW"] = float(r.max())
+        if r.max() > 0.5:
+            for e, gv, rv, mv in zip(ent, got, ref, mag):
+                print(f"  {name} dW{e}: got {gv:.6e} ref {rv:.6e} sum|terms| {mv:.6e} "
+                      f"err/|ref| {abs(gv - rv) / max(abs(rv), 1e-30):.2e} err/sum {abs(gv - rv) / mv:.2e}")
         if b["dx"] is None:
             continue
         Nn, Tn, Hn, Wn = xs[:4]
