@@ -191,8 +191,11 @@ def test_fsq_closed_forms_on_gpu(P):
 
 
 @pytest.mark.parametrize("rate", [0.0, 0.13, 0.3, 1.0])
-@pytest.mark.parametrize("shape", [(1, 5, 45, 80), (2, 1, 7, 37), (1, 3, 135, 240)])
+@pytest.mark.parametrize("shape", [(1, 5, 45, 80), (2, 1, 7, 37), (1, 3, 135, 240), (3, 2, 9, 131),
+                                   (1, 1, 3, 301)])
 def test_drop_mask_bit_exact(P, rate, shape):
+    """Rows whose first token is or is not on a multiple of 4 (one or two Philox blocks
+    per lane), one to three 128-token segments per row, ragged last mask word."""
     N, Tq, Hq, Wq = shape
     rng = np.random.default_rng(3)
     idx = rng.integers(0, 64000, size=shape).astype(np.int32)
