@@ -685,11 +685,12 @@ def serving(args, params, rank, world):
     ex = GpuExecutor(args.serve_lanes, params, None, content_fn=content, max_batch=mb, priorities=True,
                      resolutions=SERVE_RES)
 
-    # chunk time of each resolution alone on the urgent lane, with 25% for sharing the GPU
-    alone = ex.calibrate(resolutions=SERVE_RES)
+    # chunk time of each resolution alone on the urgent lane (steady state: the median of
+    # 8 chunks after a first one), with a margin for sharing the GPU with background lanes
+    alone = ex.calibrate(reps=8, resolutions=SERVE_RES)
 
     def service_time(spec):
-        return 1.25 * alone[(spec.H, spec.W)]
+        return args.serve_margin * alone[(spec.H, spec.W)]
 
     # admission: memory from the device's free bytes (conv caches + buffers per stream),
     # compute by the streams' measured chunk time per second against the load bound
@@ -711,6 +712,8 @@ def serving(args, params, rank, world):
     rep.update({"lanes": args.serve_lanes, "max_batch": mb, "phase_aligned": not args.serve_no_align,
                 "urgent": {f"{h}x{w}": service_time(StreamSpec(0, h, w, 0.0, 1)) <= 0.033 for h, w in SERVE_RES},
                 "service_ms": {f"{h}x{w}": 1e3 * service_time(StreamSpec(0, h, w, 0.0, 1)) for h, w in SERVE_RES},
+                "chunk_alone_ms": {f"{h}x{w}": 1e3 * alone[(h, w)] for h, w in SERVE_RES},
+                "service_margin": args.serve_margin,
                 "admission": {"memory_budget_gb": mem_budget / 1e9, "stream_gb": stream_gb,
                               "slots_opened": slots_opened, "memory_allocated_gb": pool.allocated / 1e9,
                               "compute": "sum over admitted streams of chunk service time x 7.5 chunks/s "
@@ -932,6 +935,8 @@ def main():
     ap.add_argument("--serve-load", type=float, default=0.75,
                     help="admitted streams' GPU time per second (measured chunk times) at most this")
     ap.add_argument("--serve-batch", type=int, default=4)
+    ap.add_argument("--serve-margin", type=float, default=1.10,
+                    help="service estimate = margin x measured chunk time alone (urgent iff <= 33 ms)")
     ap.add_argument("--serve-no-align", action="store_true")
     ap.add_argument("--case", choices=sorted(CASE_SHAPES), help="run one fixed profiling workload and exit")
     ap.add_argument("--N", type=int, help="--case: batch")

@@ -286,6 +286,16 @@ int tok_gop_blend(const float* d_prev, int T_prev, const float* d_curr, float* d
  * (zero outside the first n frames; add it to the reconstruction gradient
  * given to tok_backward). Deterministic (fixed-order FP64 sums). d_ws:
  * tok_temporal_loss_workspace_bytes. */
+/* A GoP's decode with the boundary blend (Sec. 6.1, Eq. 2) fused into the
+ * pixel head's epilogue: tok_decode of a whole clip (N, Tq, Hq, Wq tokens ->
+ * d_xhat (N,T,H,W,3) fp32, T = 1 + s_T (Tq - 1)) whose first n frames are
+ * blended as tok_gop_blend blends them, with the last n frames of the
+ * previous GoP's reconstruction d_prev (N,T_prev,H,W,3) fp32; the result is
+ * bitwise that of tok_decode followed by tok_gop_blend, without the extra
+ * pass over the frames. n = 0: plain tok_decode. Errors: TOK_EINVAL
+ * (pointers, n > min(T_prev, T), d_prev == d_xhat), as tok_decode otherwise. */
+int tok_decode_gop(tok_ctx* ctx, const int32_t* d_idx, int N, int Tq, int Hq, int Wq, int H, int W,
+                   const float* d_prev, int T_prev, int n, float* d_xhat, void* stream);
 size_t tok_temporal_loss_workspace_bytes(int N, int n, int H, int W, int C);
 int tok_temporal_loss(const float* d_xhat_curr, const float* d_x_prev, int N, int T_curr, int T_prev, int H, int W,
                       int C, int n, float* d_loss, float* d_grad, void* d_ws, size_t ws_bytes, void* stream);

@@ -90,6 +90,7 @@ _SIGS = {
     "tok_trace_layer": (i32, [vp, C.c_char_p, vp, sz, vp, sz, vp, sz]),
     "tok_downsample": (i32, [i32, vp, i32, i32, i32, i32, i32, i32, vp, vp]),
     "tok_gop_blend": (i32, [vp, i32, vp, vp, i32, i32, i32, i32, i32, i32, vp]),
+    "tok_decode_gop": (i32, [vp, vp, i32, i32, i32, i32, i32, i32, vp, i32, i32, vp, vp]),
     "tok_temporal_loss_workspace_bytes": (sz, [i32, i32, i32, i32, i32]),
     "tok_temporal_loss": (i32, [vp, vp, i32, i32, i32, i32, i32, i32, i32, vp, vp, vp, sz, vp]),
     "tok_residual": (i32, [i32, vp, vp, i32, i32, i32, i32, i32, i32, f32, vp, vp]),
@@ -264,6 +265,10 @@ def tok_downsample(in_type, x, F, H, W, C, s, out_precision, y, cuda_stream) -> 
 
 def tok_gop_blend(prev, Tp, curr, out, N, T, H, W, C, n, cuda_stream) -> None:
     _ck(_call("tok_gop_blend", prev, Tp, curr, out, N, T, H, W, C, n, cuda_stream), "tok_gop_blend")
+
+
+def tok_decode_gop(ctx, idx, N, Tq, Hq, Wq, H, W, prev, Tp, n, xhat, cuda_stream) -> None:
+    _ck(_call("tok_decode_gop", ctx, idx, N, Tq, Hq, Wq, H, W, prev, Tp, n, xhat, cuda_stream), "tok_decode_gop")
 
 
 def tok_temporal_loss_workspace_bytes(N, n, H, W, C) -> int:

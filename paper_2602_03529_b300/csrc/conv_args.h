@@ -16,6 +16,8 @@
 //               (to,ho,wo) goes to out[n, to*rt + a - drop_t, ho*rh+b, wo*rw+c, ch];
 //               frames < 0 are dropped, rows/cols >= oH/oW are cropped.
 //   OUT_FSQ   : out is the fp32 latent z; idx gets the FSQ token index.
+// An fp32 output may be blended with the previous GoP's reconstruction at the
+// GoP boundary (Sec. 6.1, Eq. 2): see blend_prev below.
 #pragma once
 #include <stdint.h>
 
@@ -81,10 +83,33 @@ struct ConvArgs {
     // 1: the tile of a layer with statistics may depend on the frame count (a
     // training forward, which no stream of chunks has to reproduce bit for bit)
     int gn_any_tile;
+    // GoP boundary blend of an fp32 output (Eq. 2): output frame ot < blend_n of
+    // sample n becomes a * prev[n, blend_Tp - blend_n + ot] + (1 - a) * out with
+    // a = (blend_n - 1 - ot) / blend_n; prev is (N, blend_Tp, oH, oW, oC) fp32.
+    // blend_n = 0: none.
+    const float* blend_prev;
+    int blend_n, blend_Tp;
     // device status / bounded waits
     int* status;
     unsigned long long wait_ns;
 };
+
+#ifdef __CUDACC__
+// The value an fp32 output element at flat offset `off` is stored as: itself, or
+// its Eq. 2 blend with the previous GoP (the same float operations as the
+// stand-alone blend kernel, so the two agree bit for bit).
+__device__ __forceinline__ float gop_blend_out(const ConvArgs& a, long long off, float o) {
+    if (a.blend_n <= 0) return o;
+    const long long fe = (long long)a.oH * a.oW * a.oC;
+    const long long f = off / fe;
+    const int ot = (int)(f % a.oT);
+    if (ot >= a.blend_n) return o;
+    const long long n = f / a.oT;
+    const float al = __fdiv_rn((float)(a.blend_n - 1 - ot), (float)a.blend_n);
+    const float p = a.blend_prev[(n * a.blend_Tp + (a.blend_Tp - a.blend_n + ot)) * fe + (off - f * fe)];
+    return __fmaf_rn(al, p, __fmul_rn(__fsub_rn(1.f, al), o));
+}
+#endif
 
 // The tensor-core kernel form of a BF16 conv (see conv_route).
 struct ConvRoute {

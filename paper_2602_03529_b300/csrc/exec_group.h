@@ -17,6 +17,9 @@ struct GroupExec : Exec {
         Work w;
         tok_stream* st = nullptr;  // chunked streaming (null: whole clip)
         bool chunk0 = true;        // first chunk of a stream: clip-mode causal padding
+        // GoP boundary blend of the decoded frames with the previous GoP (Eq. 2)
+        const float* blend_prev = nullptr;
+        int blend_n = 0, blend_Tp = 0;
     };
     using MAct = std::array<Act, kMaxConvGroup>;
     int P = 0;
@@ -123,7 +126,7 @@ struct GroupExec : Exec {
 
     // Conv followed by depth-to-space (rt, rh, rw), cropped to oH[p] x oW[p].
     MAct conv_d2s(const std::string& name, const MAct& in, void* const* outs, int rt, int rh, int rw, const int* oH,
-                  const int* oW, bool out_fp32) {
+                  const int* oW, bool out_fp32, bool pixels = false) {
         const ConvW& cw = c->convs[c->cindex[name]];
         ConvArgs as[kMaxConvGroup];
         MAct out;
@@ -144,6 +147,11 @@ struct GroupExec : Exec {
             a.oW = oW[p];
             a.oC = cw.Cout / (rt * rh * rw);
             if (!out_fp32) want_gn_stats(a, pr[p].w, a.oC);
+            if (pixels && pr[p].blend_n > 0) {
+                a.blend_prev = pr[p].blend_prev;
+                a.blend_n = pr[p].blend_n;
+                a.blend_Tp = pr[p].blend_Tp;
+            }
             out[p] = Act{outs[p], in[p].N, a.oT, oH[p], oW[p], a.oC};
             tag_gn_stats(out[p], a);
         }
@@ -412,7 +420,7 @@ struct GroupExec : Exec {
         MAct A = gn_silu("dec.out_gn", X, other_slot(ix));
         void* o[kMaxConvGroup];
         for (int p = 0; p < P; ++p) o[p] = xhat[p];
-        conv_d2s("dec.out", A, o, ar.t_stem, 2, 2, H, W, true);
+        conv_d2s("dec.out", A, o, ar.t_stem, 2, 2, H, W, true, true);
     }
 };
 

@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(NT) conv_simt_kernel(ConvArgs a) {
             if (off < 0) continue;
             float v = acc[i][j] + (a.bias ? a.bias[co] : 0.f);
             if (res) v += res[off];
-            out[off] = v;
+            out[off] = gop_blend_out(a, off, v);
         }
     }
 }

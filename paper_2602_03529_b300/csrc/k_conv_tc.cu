@@ -554,7 +554,7 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                                         const long long off = (rowoff + ow) * oC + ch;
                                         if (resid) o += __bfloat162float(resid[off]);
                                         if (f32)
-                                            static_cast<float*>(out)[off] = o;
+                                            static_cast<float*>(out)[off] = gop_blend_out(a, off, o);
                                         else
                                             static_cast<__nv_bfloat16*>(out)[off] = __float2bfloat16_rn(o);
                                     }
@@ -648,7 +648,7 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                                         const long long off = (rowoff + ow) * oC + ch;
                                         if (resid) o += __bfloat162float(resid[off]);
                                         if (f32)
-                                            static_cast<float*>(out)[off] = o;
+                                            static_cast<float*>(out)[off] = gop_blend_out(a, off, o);
                                         else
                                             static_cast<__nv_bfloat16*>(out)[off] = __float2bfloat16_rn(o);
                                     }
@@ -734,7 +734,7 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                                     float x = v[i2] + bias;
                                     if (resid) x += __bfloat162float(resid[off]);
                                     if (f32)
-                                        static_cast<float*>(out)[off] = x;
+                                        static_cast<float*>(out)[off] = gop_blend_out(a, off, x);
                                     else
                                         static_cast<__nv_bfloat16*>(out)[off] = __float2bfloat16_rn(x);
                                 }
@@ -750,7 +750,7 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                                 float x = v[i2] + bias;
                                 if (resid) x += __bfloat162float(resid[off]);
                                 if (f32)
-                                    static_cast<float*>(out)[off] = x;
+                                    static_cast<float*>(out)[off] = gop_blend_out(a, off, x);
                                 else
                                     static_cast<__nv_bfloat16*>(out)[off] = __float2bfloat16_rn(x);
                             }
@@ -1014,7 +1014,7 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                             if (a.out_fp32) {
                                 float* o = static_cast<float*>(a.out) + off;
 #pragma unroll
-                                for (int j = 0; j < 16; ++j) o[j] = v[j];
+                                for (int j = 0; j < 16; ++j) o[j] = gop_blend_out(a, off + j, v[j]);
                             } else {
                                 store_bf16x16(static_cast<__nv_bfloat16*>(a.out) + off, v);
                             }
@@ -1031,7 +1031,7 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                             const long long off =
                                 ((((long long)tc.n * a.oT + ot) * a.oH + oh) * a.oW + ow) * a.oC + ch;
                             if (a.out_fp32)
-                                static_cast<float*>(a.out)[off] = v[j];
+                                static_cast<float*>(a.out)[off] = gop_blend_out(a, off, v[j]);
                             else
                                 static_cast<__nv_bfloat16*>(a.out)[off] = __float2bfloat16_rn(v[j]);
                         }

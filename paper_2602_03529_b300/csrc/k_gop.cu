@@ -21,9 +21,11 @@ __global__ void gop_blend_kernel(const float4* __restrict__ prev, const float4* 
     const long long s = i / (E4 * T);
     float4 c = curr[i];
     if (t < n) {
-        const float a = (float)(n - 1 - t) / (float)n, b = 1.f - a;
+        // explicitly rounded, as the blend fused into the pixel head's epilogue
+        const float a = __fdiv_rn((float)(n - 1 - t), (float)n), b = __fsub_rn(1.f, a);
         const float4 p = prev[(s * Tp + (Tp - n + t)) * E4 + e];
-        c = make_float4(a * p.x + b * c.x, a * p.y + b * c.y, a * p.z + b * c.z, a * p.w + b * c.w);
+        c = make_float4(__fmaf_rn(a, p.x, __fmul_rn(b, c.x)), __fmaf_rn(a, p.y, __fmul_rn(b, c.y)),
+                        __fmaf_rn(a, p.z, __fmul_rn(b, c.z)), __fmaf_rn(a, p.w, __fmul_rn(b, c.w)));
     }
     out[i] = c;
 }
@@ -37,8 +39,8 @@ __global__ void gop_blend1_kernel(const float* __restrict__ prev, const float* _
     const long long s = i / (E * T);
     float c = curr[i];
     if (t < n) {
-        const float a = (float)(n - 1 - t) / (float)n;
-        c = a * prev[(s * Tp + (Tp - n + t)) * E + e] + (1.f - a) * c;
+        const float a = __fdiv_rn((float)(n - 1 - t), (float)n);
+        c = __fmaf_rn(a, prev[(s * Tp + (Tp - n + t)) * E + e], __fmul_rn(__fsub_rn(1.f, a), c));
     }
     out[i] = c;
 }

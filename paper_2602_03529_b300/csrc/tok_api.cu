@@ -256,7 +256,9 @@ int tok_encode_batch(tok_ctx* c, const tok_enc_item* items, int count, void* str
     return ex.err;
 }
 
-int tok_decode_batch(tok_ctx* c, const tok_dec_item* items, int count, void* stream) {
+// The grouped decode; item 0 may take the GoP boundary blend (blend_n > 0).
+static int decode_items(tok_ctx* c, const tok_dec_item* items, int count, void* stream, const float* blend_prev,
+                        int blend_Tp, int blend_n) {
     if (!c || !items || count < 1 || count > TOK_MAX_BATCH) return TOK_EINVAL;
     if (c->arch.kind != TOK_ARCH_FULL) return TOK_ESTATE;
     GroupExec ex;
@@ -299,11 +301,31 @@ int tok_decode_batch(tok_ctx* c, const tok_dec_item* items, int count, void* str
         xhat[p] = it.d_xhat;
     }
     if (off > c->arena_bytes) return TOK_ENOMEM;
+    if (blend_n > 0) {
+        ex.pr[0].blend_prev = blend_prev;
+        ex.pr[0].blend_Tp = blend_Tp;
+        ex.pr[0].blend_n = blend_n;
+    }
     ex.decode(idx, N, Tq, Hq, Wq, H, W, xhat);
     if (!ex.err)
         for (int p = 0; p < count; ++p)
             if (items[p].s) items[p].s->dec_chunk++;
     return ex.err;
+}
+
+int tok_decode_batch(tok_ctx* c, const tok_dec_item* items, int count, void* stream) {
+    return decode_items(c, items, count, stream, nullptr, 0, 0);
+}
+
+int tok_decode_gop(tok_ctx* c, const int32_t* idx, int N, int Tq, int Hq, int Wq, int H, int W, const float* prev,
+                   int T_prev, int n, float* xhat, void* stream) {
+    if (!c || !idx || !xhat || N < 1 || Tq < 1 || Hq < 1 || Wq < 1 || H < 1 || W < 1 || n < 0) return TOK_EINVAL;
+    if (c->arch.kind != TOK_ARCH_FULL) return TOK_ESTATE;
+    const int T = 1 + c->s_t * (Tq - 1);
+    if (n > 0 && (!prev || T_prev < n || T < n)) return TOK_EINVAL;
+    if (n > 0 && prev == xhat) return TOK_EINVAL;
+    const tok_dec_item it{idx, N, Tq, Hq, Wq, H, W, xhat, nullptr};
+    return decode_items(c, &it, 1, stream, prev, T_prev, n);
 }
 
 int tok_trace_layer(tok_ctx* c, const char* name, void* in, size_t in_bytes, void* res, size_t res_bytes, void* out,

@@ -134,6 +134,19 @@ class Tokenizer:
         L.tok_decode(self.ctx, _ptr(idx), N, Tq, Hq, Wq, H, W, _ptr(out), video, _stream_ptr(stream))
         return out
 
+    def decode_gop(self, idx: torch.Tensor, H: int, W: int, prev: torch.Tensor, n: int,
+                   out: torch.Tensor | None = None, stream=None):
+        """Decode a GoP's tokens (a whole clip) with its first n frames blended with the
+        last n frames of the previous GoP's reconstruction `prev` (N, T_prev, H, W, 3)
+        fp32 (Eq. 2, fused into the pixel head)."""
+        N, Tq, Hq, Wq = idx.shape
+        T = 1 + (Tq - 1) * self.s_t
+        if out is None:
+            out = torch.empty((N, T, H, W, 3), device=idx.device, dtype=torch.float32)
+        L.tok_decode_gop(self.ctx, _ptr(idx), N, Tq, Hq, Wq, H, W, _ptr(prev), prev.shape[1], n, _ptr(out),
+                         _stream_ptr(stream))
+        return out
+
     def set_cta_tiles(self, tiles: int):
         """0: persistent conv CTAs; n > 0: at most n tiles per CTA (yields SMs quickly to
         work on higher-priority CUDA streams; results are unchanged)."""
