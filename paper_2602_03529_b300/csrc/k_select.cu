@@ -303,10 +303,363 @@ __global__ void __launch_bounds__(FS_THREADS) select_fused_kernel(
     }
 }
 
+// ---------------------------------------------------------------- integer form
+//
+// When every channel's half-width floor(L/2) is a power of two (FSQ [8,8,8,5,5,5]:
+// 4, 4, 4, 2, 2, 2), every code value q/hw is a dyadic rational and the float32
+// sums of the definition are exact: with Q = max hw^2 and w = Q / hw^2 per
+// channel, dot = D / Q, |p|^2 = A / Q, |q|^2 = B / Q for the integers
+// D = sum w qp qi, A = sum w qp^2, B = sum w qi^2, and the product of the squared
+// norms A B / Q^2 is exact too. So S = D/Q divided (rounded) by the rounded
+// square root of A B / Q^2, which a table indexed by P = A B holds: the same
+// float32 value, bit for bit, as the three sums, one square root and one
+// division. A token index is split as lo + 2^shift hi; small tables give the
+// centered digits q (one signed byte per channel) and w q of each part, and two
+// dp4a per dot product sum them.
+//
+// The k-th largest similarity of a frame is then found from a 2048-bucket
+// histogram of S (bucket = floor((S + 1) * 1023.5): monotone in S), built in the
+// same pass as the similarities: the bucket holding the k-th largest is either
+// one value (often: P tokens equal to their I token all have S = 1), resolved at
+// once, or a short list of candidates, radix-selected in shared memory; only a
+// bucket of more than SB_CAND tokens with distinct values falls back to the
+// radix select over the whole frame.
+constexpr int SB_THREADS = 1024, SB_BINS = 2048, SB_CAND = 1024;
+constexpr long long SB_MAX_TOKENS = 16384;
+constexpr int SB_TAB_MAX = 512;     // entries of each index-part table
+constexpr int SB_PMAX = 16383;      // largest A B the square-root table holds
+
+struct SelTables {
+    const uint4* lo;   // [2^shift]: bytes of x, y = q of channels 0..7 (lo part), bytes of z, w = w q
+    const uint4* hi;   // [nhi]: the same for the hi part (disjoint channels, OR-able)
+    const float* rsq;  // [pmax + 1]: fsqrt_rn(P / Q^2)
+    float invQ, invQ2;
+    int shift, nhi, prod, pmax;
+};
+
+__global__ void sel_tables_kernel(FsqConsts f, int split_c, int shift, int nhi, int Q, int pmax, uint4* lo, uint4* hi,
+                                  float* rsq) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nlo = 1 << shift;
+    auto pack = [&](int part, int v) {
+        uint32_t q[2] = {0u, 0u}, wq[2] = {0u, 0u};
+        for (int c = 0; c < f.nlev; ++c) {
+            if ((c < split_c) != (part == 0)) continue;
+            const int base = part == 0 ? f.basis[c] : f.basis[c] / nlo;
+            const int d = (v / base) % f.levels[c];
+            const int qc = d - f.half_w[c], w = Q / (f.half_w[c] * f.half_w[c]);
+            q[c / 4] |= (uint32_t)(qc & 0xFF) << (8 * (c % 4));
+            wq[c / 4] |= (uint32_t)((w * qc) & 0xFF) << (8 * (c % 4));
+        }
+        return make_uint4(q[0], q[1], wq[0], wq[1]);
+    };
+    if (i < nlo) lo[i] = pack(0, i);
+    if (i < nhi) hi[i] = pack(1, i);
+    if (i <= pmax) rsq[i] = __fsqrt_rn(__fmul_rn((float)i, 1.0f / (float)(Q * Q)));
+}
+
+// Code vector (q and w q) of a token index; an index outside [0, prod) is decoded
+// as the other forms decode it.
+__device__ __forceinline__ uint4 sel_code(int idx, const SelTables& t, const FsqConsts& f) {
+    if ((unsigned)idx < (unsigned)t.prod) {
+        const uint4 a = t.lo[idx & ((1 << t.shift) - 1)], b = t.hi[idx >> t.shift];
+        return make_uint4(a.x | b.x, a.y | b.y, a.z | b.z, a.w | b.w);
+    }
+    const int Q = (int)(1.0f / t.invQ);
+    uint32_t q[2] = {0u, 0u}, wq[2] = {0u, 0u};
+    for (int c = 0; c < f.nlev; ++c) {
+        const int d = (idx / f.basis[c]) % f.levels[c];
+        const int qc = d - f.half_w[c], w = Q / (f.half_w[c] * f.half_w[c]);
+        q[c / 4] |= (uint32_t)(qc & 0xFF) << (8 * (c % 4));
+        wq[c / 4] |= (uint32_t)((w * qc) & 0xFF) << (8 * (c % 4));
+    }
+    return make_uint4(q[0], q[1], wq[0], wq[1]);
+}
+
+__device__ __forceinline__ uint32_t sim_order(float S) {
+    const uint32_t u = __float_as_uint(S);
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__device__ __forceinline__ int sim_bucket(float S) {
+    const int b = (int)__fmul_rn(__fadd_rn(S, 1.0f), 1023.5f);
+    return min(max(b, 0), SB_BINS - 1);
+}
+
+__device__ __forceinline__ float sim_of_order(uint32_t o) {
+    return __uint_as_float((o & 0x80000000u) ? (o & 0x7FFFFFFFu) : ~o);
+}
+
+// Digit d (from the top) holding the rem-th largest of a histogram of nb bins,
+// counted from bin nb - 1 down; warp 0 calls it. Returns (digit, rem within it).
+__device__ __forceinline__ void top_digit(const uint32_t* hist, int nb, long long rem, int lane, int* d_out,
+                                          long long* rem_out) {
+    const int per = nb / 32, hi = nb - per * lane;
+    long long own = 0;
+    for (int b = hi - 1; b >= hi - per; --b) own += hist[b];
+    long long incl = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const uint32_t hit = __ballot_sync(0xffffffffu, incl >= rem);
+    if (hit && lane == __ffs(hit) - 1) {
+        long long cum = incl - own;
+        int d = hi - 1;
+        for (; d > hi - per; --d) {
+            if (cum + (long long)hist[d] >= rem) break;
+            cum += hist[d];
+        }
+        *d_out = d;
+        *rem_out = rem - cum;
+    }
+}
+
+// Block-wide: the rem-th largest of keys key(0 .. n-1) (MSB-first radix over 11, 11
+// and 10 bits). Every thread calls it; the result (value, rem among the keys equal
+// to it) is in *star / *rem_out after the closing barrier.
+template <typename F>
+__device__ void radix_kth(F key, int n, long long rem, uint32_t* hist, uint32_t* s_prefix, uint32_t* s_mask,
+                          long long* s_rem) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        *s_prefix = 0u;
+        *s_mask = 0u;
+        *s_rem = rem;
+    }
+    const int shifts[3] = {21, 10, 0};
+    const uint32_t dmasks[3] = {0x7FFu, 0x7FFu, 0x3FFu};
+    for (int pass = 0; pass < 3; ++pass) {
+        for (int i = tid; i < SB_BINS; i += SB_THREADS) hist[i] = 0u;
+        __syncthreads();
+        const uint32_t prefix = *s_prefix, mask = *s_mask;
+        const int shift = shifts[pass];
+        const uint32_t dm = dmasks[pass];
+        for (int it = 0; it < (n + SB_THREADS - 1) / SB_THREADS; ++it) {
+            const int j = it * SB_THREADS + tid;
+            const uint32_t o = j < n ? key(j) : 0u;
+            const bool act = j < n && (o & mask) == prefix;
+            const uint32_t dig = (o >> shift) & dm;
+            const uint32_t am = __ballot_sync(0xffffffffu, act);
+            if (act) {
+                const uint32_t same = __match_any_sync(am, dig);
+                if (lane == __ffs(same) - 1) atomicAdd(&hist[dig], (uint32_t)__popc(same));
+            }
+        }
+        __syncthreads();
+        if (warp == 0) {
+            int d = -1;
+            long long r = 0;
+            top_digit(hist, pass < 2 ? 2048 : 1024, *s_rem, lane, &d, &r);
+            if (d >= 0) {  // the lane that found the digit publishes it
+                *s_rem = r;
+                *s_prefix = prefix | ((uint32_t)d << shift);
+                *s_mask = mask | (dm << shift);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(SB_THREADS, 2) select_bucket_kernel(
+    const int32_t* __restrict__ idx_p, const int32_t* __restrict__ idx_i, const SelTables tb, FsqConsts f, int Tp,
+    int Hq, int Wq, long long k, int32_t zero_index, int32_t* __restrict__ out, uint32_t* __restrict__ keep_bits,
+    float* __restrict__ sim) {
+    extern __shared__ uint32_t ords[];  // HW order-preserving similarity images
+    __shared__ uint32_t hist[SB_BINS];
+    __shared__ uint32_t cand[SB_CAND];  // order images of the threshold bucket's tokens
+    __shared__ uint32_t wsum[SB_THREADS / 32];
+    __shared__ uint32_t s_prefix, s_mask, s_pos, s_min, s_max, s_n;
+    __shared__ int s_bin;
+    __shared__ long long s_rem;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long frame = blockIdx.x, n = frame / Tp;
+    const int HW = Hq * Wq;
+    const int32_t* fp = idx_p + frame * HW;
+    const int32_t* fi = idx_i + n * HW;
+    for (int i = tid; i < SB_BINS; i += SB_THREADS) hist[i] = 0u;
+    if (tid == 0) {
+        s_min = 0xFFFFFFFFu;
+        s_max = 0u;
+        s_n = 0u;
+        s_pos = 0u;
+        s_bin = 0;
+        s_rem = 0;
+    }
+    __syncthreads();
+    // phase 1: similarities, their order images and the bucket histogram
+    const int iters = (HW + SB_THREADS - 1) / SB_THREADS;
+    for (int it = 0; it < iters; ++it) {
+        const int j = it * SB_THREADS + tid;
+        const bool act = j < HW;
+        int bkt = 0;
+        if (act) {
+            const uint4 a = sel_code(fp[j], tb, f), b = sel_code(fi[j], tb, f);
+            const int D = __dp4a((int)a.z, (int)b.x, __dp4a((int)a.w, (int)b.y, 0));
+            const int A = __dp4a((int)a.z, (int)a.x, __dp4a((int)a.w, (int)a.y, 0));
+            const int B = __dp4a((int)b.z, (int)b.x, __dp4a((int)b.w, (int)b.y, 0));
+            const int Pq = A * B;
+            float S = 0.f;
+            if (Pq > 0) {
+                const float den = Pq <= tb.pmax ? tb.rsq[Pq] : __fsqrt_rn(__fmul_rn((float)Pq, tb.invQ2));
+                S = __fdiv_rn(__fmul_rn((float)D, tb.invQ), den);
+            }
+            S = __fadd_rn(S, 0.f);  // -0 -> +0: equal similarities have equal images
+            ords[j] = sim_order(S);
+            bkt = sim_bucket(S);
+            if (sim) sim[frame * HW + j] = S;
+        }
+        const uint32_t am = __ballot_sync(0xffffffffu, act);
+        if (act) {
+            const uint32_t same = __match_any_sync(am, bkt);
+            if (lane == __ffs(same) - 1) atomicAdd(&hist[bkt], (uint32_t)__popc(same));
+        }
+    }
+    __syncthreads();
+    const bool all_drop = k >= HW, none = k <= 0;
+    uint32_t star = 0u;
+    if (!all_drop && !none) {
+        // phase 2: the bucket holding the k-th largest similarity
+        if (warp == 0) {
+            int d = -1;
+            long long r = 0;
+            top_digit(hist, SB_BINS, k, lane, &d, &r);
+            if (d >= 0) {
+                s_bin = d;
+                s_rem = r;
+            }
+        }
+        __syncthreads();
+        const int bin = s_bin;
+        const long long rem_b = s_rem;
+        const uint32_t m = hist[bin];
+        // phase 3: that bucket's tokens: extent of their images, and the images themselves
+        for (int it = 0; it < iters; ++it) {
+            const int j = it * SB_THREADS + tid;
+            const bool in = j < HW && sim_bucket(sim_of_order(ords[j])) == bin;
+            const uint32_t o = in ? ords[j] : 0u;
+            const uint32_t bm = __ballot_sync(0xffffffffu, in);
+            if (bm) {
+                const uint32_t mn = __reduce_min_sync(0xffffffffu, in ? o : 0xFFFFFFFFu);
+                const uint32_t mx = __reduce_max_sync(0xffffffffu, o);
+                uint32_t base = 0u;
+                if (lane == 0) {
+                    atomicMin(&s_min, mn);
+                    atomicMax(&s_max, mx);
+                    if (m <= SB_CAND) base = atomicAdd(&s_n, (uint32_t)__popc(bm));
+                }
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (in && m <= SB_CAND) cand[base + __popc(bm & ((1u << lane) - 1u))] = o;
+            }
+        }
+        __syncthreads();
+        if (s_min == s_max) {
+            star = s_min;  // one value: the rem_b lowest positions among its tokens drop
+            if (tid == 0) s_rem = rem_b;
+            __syncthreads();
+        } else if (m <= SB_CAND) {
+            radix_kth([&](int i) { return cand[i]; }, (int)m, rem_b, hist, &s_prefix, &s_mask, &s_rem);
+            star = s_prefix;
+        } else {
+            radix_kth([&](int i) { return ords[i]; }, HW, k, hist, &s_prefix, &s_mask, &s_rem);
+            star = s_prefix;
+        }
+        // phase 4: among the tokens equal to the k-th largest, the s_rem lowest positions drop
+        const int per = (HW + SB_THREADS - 1) / SB_THREADS;
+        const int j0 = tid * per, j1 = min(j0 + per, HW);
+        uint32_t cnt = 0;
+        for (int j = j0; j < j1; ++j) cnt += ords[j] == star ? 1u : 0u;
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t w = wsum[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t v = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += v;
+            }
+            wsum[lane] = w;
+        }
+        __syncthreads();
+        const uint32_t before = incl - cnt + (warp > 0 ? wsum[warp - 1] : 0u);
+        const long long rem = s_rem;
+        if ((long long)before < rem && rem <= (long long)(before + cnt)) {
+            long long need = rem - before;
+            for (int j = j0; j < j1; ++j)
+                if (ords[j] == star && --need == 0) {
+                    s_pos = (uint32_t)j;
+                    break;
+                }
+        }
+        __syncthreads();
+    }
+    // phase 5: drop, indices and keep bits (a warp per 32 tokens of a row)
+    const uint32_t pos = s_pos;
+    const int nwords = (Wq + 31) / 32;
+    for (int rw = warp; rw < Hq * nwords; rw += SB_THREADS / 32) {
+        const int h = rw / nwords, word = rw - h * nwords, w = word * 32 + lane;
+        bool keep = false;
+        if (w < Wq) {
+            const int j = h * Wq + w;
+            const uint32_t o = ords[j];
+            const bool drop = all_drop || (!none && (o > star || (o == star && (uint32_t)j <= pos)));
+            keep = !drop;
+            out[frame * HW + j] = keep ? fp[j] : zero_index;
+        }
+        const uint32_t msk = __ballot_sync(0xffffffffu, keep);
+        if (keep_bits && lane == 0) keep_bits[(frame * Hq + h) * nwords + word] = msk;
+    }
+}
+
+// Whether the integer form applies (see above), and its table geometry.
+struct SelPlan {
+    bool ok = false;
+    int split_c = 0, shift = 0, nhi = 0, Q = 0, pmax = 0, prod = 0;
+};
+
+SelPlan sel_plan(const FsqConsts& f, long long HW) {
+    SelPlan p;
+    if (HW > SB_MAX_TOKENS || HW < 1) return p;
+    int Q = 1;
+    for (int c = 0; c < f.nlev; ++c) {
+        const int h = f.half_w[c];
+        if (h < 1 || (h & (h - 1)) || h > 8) return p;
+        Q = std::max(Q, h * h);
+    }
+    const long long prod = (long long)f.basis[f.nlev - 1] * f.levels[f.nlev - 1];
+    const int dmax = f.nlev * Q;
+    if ((long long)dmax * dmax > SB_PMAX) return p;
+    for (int c = 1; c < f.nlev; ++c) {
+        const int b = f.basis[c];
+        if (b & (b - 1)) continue;
+        if (b <= SB_TAB_MAX && prod / b <= SB_TAB_MAX && prod % b == 0) {
+            p.ok = true;
+            p.split_c = c;
+            p.shift = __builtin_ctz((unsigned)b);
+            p.nhi = (int)(prod / b);
+            p.Q = Q;
+            p.pmax = dmax * dmax;
+            p.prod = (int)prod;
+            return p;
+        }
+    }
+    return p;
+}
+
 }  // namespace
 
 size_t similarity_workspace_bytes(long long N, int Tp, long long HW) {
-    return (size_t)(N * Tp * HW) * 8 + (size_t)(N * Tp) * 8 + (size_t)DIGIT_TAB * 4 + 512;
+    // per-token keys and per-frame thresholds (the three-kernel form), the digit
+    // table, and the integer form's tables
+    return (size_t)(N * Tp * HW) * 8 + (size_t)(N * Tp) * 8 + (size_t)DIGIT_TAB * 4 + 512 +
+           (size_t)2 * SB_TAB_MAX * 16 + (size_t)(SB_PMAX + 1) * 4 + 512;
 }
 
 int launch_similarity_mask(const int32_t* idx_p, const int32_t* idx_i, long long N, int Tp, int Hq, int Wq,
@@ -316,6 +669,38 @@ int launch_similarity_mask(const int32_t* idx_p, const int32_t* idx_i, long long
     if (ntok <= 0) return 0;
     unsigned long long* keys = static_cast<unsigned long long*>(ws);
     unsigned long long* thr = keys + ntok;
+    const SelPlan pl = sel_plan(f, HW);
+    if (pl.ok) {
+        // the integer form: its tables after the digit table (see the workspace size)
+        char* tb = reinterpret_cast<char*>(thr + frames) + (size_t)DIGIT_TAB * 4;
+        tb = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(tb) + 255) & ~uintptr_t(255));
+        uint4* lo = reinterpret_cast<uint4*>(tb);
+        uint4* hi = lo + SB_TAB_MAX;
+        float* rsq = reinterpret_cast<float*>(hi + SB_TAB_MAX);
+        const int nt = std::max(std::max(1 << pl.shift, pl.nhi), pl.pmax + 1);
+        sel_tables_kernel<<<blocks_for(nt, 256), 256, 0, s>>>(f, pl.split_c, pl.shift, pl.nhi, pl.Q, pl.pmax, lo, hi,
+                                                              rsq);
+        SelTables t;
+        t.lo = lo;
+        t.hi = hi;
+        t.rsq = rsq;
+        t.invQ = 1.0f / (float)pl.Q;
+        t.invQ2 = 1.0f / (float)(pl.Q * pl.Q);
+        t.shift = pl.shift;
+        t.nhi = pl.nhi;
+        t.prod = pl.prod;
+        t.pmax = pl.pmax;
+        static bool attr_b = false;
+        if (!attr_b) {
+            if (cudaFuncSetAttribute(select_bucket_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(SB_MAX_TOKENS * 4)) != cudaSuccess)
+                return (int)cudaGetLastError();
+            attr_b = true;
+        }
+        select_bucket_kernel<<<(unsigned)frames, SB_THREADS, (size_t)HW * 4, s>>>(idx_p, idx_i, t, f, Tp, Hq, Wq, k,
+                                                                                  zero_index, out, keep_bits, sim);
+        return (int)cudaGetLastError();
+    }
     bool small_levels = true;
     for (int c = 0; c < f.nlev; ++c) small_levels = small_levels && f.levels[c] <= 16;
     if (HW <= FUSED_MAX_TOKENS && small_levels) {

@@ -111,3 +111,38 @@ def test_large_frames_take_the_three_kernel_form(P):
     ip = np.where(rng.random((N, Tp, H, W)) < 0.3, np.repeat(ii, Tp, axis=1), rng.integers(0, 64000, (N, Tp, H, W)))
     for rate in (0.0, 0.2, 1.0):
         _check(P, ip, ii, rate)
+
+
+def _bucket_codes():
+    """Against the I token 12345: P codes of two distinct similarities that share one of
+    the 2048 similarity buckets (width ~1e-3) the selection's first pass uses, and codes
+    of clearly lower similarity."""
+    ip = np.arange(64000).reshape(1, 1, 1, -1)
+    S = ops.token_similarity(ip, np.full((1, 1, 1, 64000), 12345), LV)[0, 0, 0]
+    b = np.floor((S.astype(np.float32) + np.float32(1)) * np.float32(1023.5)).astype(int)
+    for bb in range(2047, 0, -1):
+        vals = np.unique(S[b == bb])
+        if len(vals) >= 2:
+            c1 = int(np.nonzero(S == vals[0])[0][0])
+            c2 = int(np.nonzero(S == vals[-1])[0][0])
+            low = np.nonzero(S < vals[0] - 0.05)[0]
+            return c1, c2, low
+    raise AssertionError("no bucket with two similarities")
+
+
+@pytest.mark.parametrize("per_value,rate", [(1500, 0.3), (300, 0.05), (300, 0.13)])
+def test_bucket_with_distinct_similarities(P, per_value, rate):
+    """The k-th largest similarity falls in a bucket holding two different values: more
+    tokens there than the candidate list takes (whole-frame radix select) or fewer
+    (radix select over the bucket's candidates)."""
+    c1, c2, low = _bucket_codes()
+    rng = np.random.default_rng(per_value)
+    N, Tp, H, W = 1, 2, 60, 80
+    ip = rng.choice(low, size=(N, Tp, H, W))
+    for t in range(Tp):
+        pos = rng.permutation(H * W)[:2 * per_value]
+        flat = ip[0, t].reshape(-1)
+        flat[pos[:per_value]] = c1
+        flat[pos[per_value:]] = c2
+    ii = np.full((N, 1, H, W), 12345)
+    _check(P, ip, ii, rate)
