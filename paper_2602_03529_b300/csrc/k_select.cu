@@ -462,16 +462,11 @@ __device__ void radix_kth(F key, int n, long long rem, uint32_t* hist, uint32_t*
     }
 }
 
-// The frame's P indices and its I indices are first copied into shared memory
-// (independent loads, many in flight per thread), so that the similarity pass
-// runs from there; the I buffer then becomes the order images in place.
-__global__ void __launch_bounds__(SB_THREADS, 1) select_bucket_kernel(
+__global__ void __launch_bounds__(SB_THREADS, 2) select_bucket_kernel(
     const int32_t* __restrict__ idx_p, const int32_t* __restrict__ idx_i, const SelTables tb, FsqConsts f, int Tp,
     int Hq, int Wq, long long k, int32_t zero_index, int32_t* __restrict__ out, uint32_t* __restrict__ keep_bits,
     float* __restrict__ sim) {
-    extern __shared__ uint32_t smem_sel[];
-    uint32_t* ords = smem_sel;                                          // HW: I indices, then order images
-    int32_t* pidx = reinterpret_cast<int32_t*>(smem_sel + Hq * Wq);  // HW: P indices
+    extern __shared__ uint32_t ords[];  // HW order-preserving similarity images
     __shared__ uint32_t hist[SB_BINS];
     __shared__ uint32_t cand[SB_CAND];  // order images of the threshold bucket's tokens
     __shared__ uint32_t wsum[SB_THREADS / 32];
@@ -492,23 +487,15 @@ __global__ void __launch_bounds__(SB_THREADS, 1) select_bucket_kernel(
         s_bin = 0;
         s_rem = 0;
     }
-    const int iters = (HW + SB_THREADS - 1) / SB_THREADS;
-#pragma unroll 4
-    for (int it = 0; it < iters; ++it) {
-        const int j = it * SB_THREADS + tid;
-        if (j < HW) {
-            pidx[j] = fp[j];
-            ords[j] = (uint32_t)fi[j];
-        }
-    }
     __syncthreads();
     // phase 1: similarities, their order images and the bucket histogram
+    const int iters = (HW + SB_THREADS - 1) / SB_THREADS;
     for (int it = 0; it < iters; ++it) {
         const int j = it * SB_THREADS + tid;
         const bool act = j < HW;
         int bkt = 0;
         if (act) {
-            const uint4 a = sel_code(pidx[j], tb, f), b = sel_code((int)ords[j], tb, f);
+            const uint4 a = sel_code(fp[j], tb, f), b = sel_code(fi[j], tb, f);
             const int D = __dp4a((int)a.z, (int)b.x, __dp4a((int)a.w, (int)b.y, 0));
             const int A = __dp4a((int)a.z, (int)a.x, __dp4a((int)a.w, (int)a.y, 0));
             const int B = __dp4a((int)b.z, (int)b.x, __dp4a((int)b.w, (int)b.y, 0));
@@ -547,24 +534,32 @@ __global__ void __launch_bounds__(SB_THREADS, 1) select_bucket_kernel(
         const int bin = s_bin;
         const long long rem_b = s_rem;
         const uint32_t m = hist[bin];
-        // phase 3: that bucket's tokens: extent of their images, and the images themselves
+        // phase 3: that bucket's tokens: extent of their images (per thread, then one
+        // warp reduction and one shared atomic per warp), and the images themselves
+        uint32_t tmin = 0xFFFFFFFFu, tmax = 0u;
         for (int it = 0; it < iters; ++it) {
             const int j = it * SB_THREADS + tid;
-            const bool in = j < HW && sim_bucket(sim_of_order(ords[j])) == bin;
-            const uint32_t o = in ? ords[j] : 0u;
-            const uint32_t bm = __ballot_sync(0xffffffffu, in);
-            if (bm) {
-                const uint32_t mn = __reduce_min_sync(0xffffffffu, in ? o : 0xFFFFFFFFu);
-                const uint32_t mx = __reduce_max_sync(0xffffffffu, o);
-                uint32_t base = 0u;
-                if (lane == 0) {
-                    atomicMin(&s_min, mn);
-                    atomicMax(&s_max, mx);
-                    if (m <= SB_CAND) base = atomicAdd(&s_n, (uint32_t)__popc(bm));
-                }
-                base = __shfl_sync(0xffffffffu, base, 0);
-                if (in && m <= SB_CAND) cand[base + __popc(bm & ((1u << lane) - 1u))] = o;
+            const uint32_t o = j < HW ? ords[j] : 0u;
+            const bool in = j < HW && sim_bucket(sim_of_order(o)) == bin;
+            if (in) {
+                tmin = min(tmin, o);
+                tmax = max(tmax, o);
             }
+            if (m <= SB_CAND) {
+                const uint32_t bm = __ballot_sync(0xffffffffu, in);
+                if (bm) {
+                    uint32_t base = 0u;
+                    if (lane == 0) base = atomicAdd(&s_n, (uint32_t)__popc(bm));
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    if (in) cand[base + __popc(bm & ((1u << lane) - 1u))] = o;
+                }
+            }
+        }
+        tmin = __reduce_min_sync(0xffffffffu, tmin);
+        tmax = __reduce_max_sync(0xffffffffu, tmax);
+        if (lane == 0) {
+            atomicMin(&s_min, tmin);
+            atomicMax(&s_max, tmax);
         }
         __syncthreads();
         if (s_min == s_max) {
@@ -624,7 +619,7 @@ __global__ void __launch_bounds__(SB_THREADS, 1) select_bucket_kernel(
             const uint32_t o = ords[j];
             const bool drop = all_drop || (!none && (o > star || (o == star && (uint32_t)j <= pos)));
             keep = !drop;
-            out[frame * HW + j] = keep ? pidx[j] : zero_index;
+            out[frame * HW + j] = keep ? fp[j] : zero_index;
         }
         const uint32_t msk = __ballot_sync(0xffffffffu, keep);
         if (keep_bits && lane == 0) keep_bits[(frame * Hq + h) * nwords + word] = msk;
@@ -706,11 +701,11 @@ int launch_similarity_mask(const int32_t* idx_p, const int32_t* idx_i, long long
         static bool attr_b = false;
         if (!attr_b) {
             if (cudaFuncSetAttribute(select_bucket_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(SB_MAX_TOKENS * 8)) != cudaSuccess)
+                                     (int)(SB_MAX_TOKENS * 4)) != cudaSuccess)
                 return (int)cudaGetLastError();
             attr_b = true;
         }
-        select_bucket_kernel<<<(unsigned)frames, SB_THREADS, (size_t)HW * 8, s>>>(idx_p, idx_i, t, f, Tp, Hq, Wq, k,
+        select_bucket_kernel<<<(unsigned)frames, SB_THREADS, (size_t)HW * 4, s>>>(idx_p, idx_i, t, f, Tp, Hq, Wq, k,
                                                                                   zero_index, out, keep_bits, sim);
         return (int)cudaGetLastError();
     }
