@@ -327,18 +327,19 @@ __global__ void __launch_bounds__(FS_THREADS) select_fused_kernel(
 constexpr int SB_THREADS = 1024, SB_BINS = 2048, SB_CAND = 1024;
 constexpr long long SB_MAX_TOKENS = 16384;
 constexpr int SB_TAB_MAX = 512;     // entries of each index-part table
-constexpr int SB_PMAX = 16383;      // largest A B the square-root table holds
+constexpr int SB_PMAX = 16383;      // largest A B the similarity table holds
+constexpr long long SB_STAB_MAX = 1 << 21;  // entries of the similarity table ((dmax + 1) (pmax + 1))
 
 struct SelTables {
     const uint4* lo;   // [2^shift]: bytes of x, y = q of channels 0..7 (lo part), bytes of z, w = w q
     const uint4* hi;   // [nhi]: the same for the hi part (disjoint channels, OR-able)
-    const float* rsq;  // [pmax + 1]: fsqrt_rn(P / Q^2)
+    const float* stab; // [(dmax + 1) (pmax + 1)]: S for |D| and P = A B (0 for P = 0)
     float invQ, invQ2;
-    int shift, nhi, prod, pmax;
+    int shift, nhi, prod, pmax, dmax;
 };
 
-__global__ void sel_tables_kernel(FsqConsts f, int split_c, int shift, int nhi, int Q, int pmax, uint4* lo, uint4* hi,
-                                  float* rsq) {
+__global__ void sel_tables_kernel(FsqConsts f, int split_c, int shift, int nhi, int Q, int pmax, int dmax, uint4* lo,
+                                  uint4* hi, float* stab) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int nlo = 1 << shift;
     auto pack = [&](int part, int v) {
@@ -355,7 +356,14 @@ __global__ void sel_tables_kernel(FsqConsts f, int split_c, int shift, int nhi, 
     };
     if (i < nlo) lo[i] = pack(0, i);
     if (i < nhi) hi[i] = pack(1, i);
-    if (i <= pmax) rsq[i] = __fsqrt_rn(__fmul_rn((float)i, 1.0f / (float)(Q * Q)));
+    // S of |D| and P = A B: the definition's one rounded square root of the exact
+    // norm product and one rounded division of the exact dot product
+    if (i < (dmax + 1) * (pmax + 1)) {
+        const int d = i / (pmax + 1), P = i - d * (pmax + 1);
+        stab[i] = P > 0 ? __fdiv_rn(__fmul_rn((float)d, 1.0f / (float)Q),
+                                    __fsqrt_rn(__fmul_rn((float)P, 1.0f / (float)(Q * Q))))
+                        : 0.f;
+    }
 }
 
 // Code vector (q and w q) of a token index; an index outside [0, prod) is decoded
@@ -489,26 +497,42 @@ __global__ void __launch_bounds__(SB_THREADS, 2) select_bucket_kernel(
     }
     __syncthreads();
     // phase 1: similarities, their order images and the bucket histogram
-    const int iters = (HW + SB_THREADS - 1) / SB_THREADS;
+    const int iters = (HW + SB_THREADS - 1) / SB_THREADS, full = HW / SB_THREADS;
+    float* const simf = sim ? sim + frame * HW : nullptr;
+    const uint32_t lomask = (1u << tb.shift) - 1u;
+    const int prow = tb.pmax + 1;
+    const auto similarity = [&](int ip, int ii) {
+        uint4 a, b;
+        if ((unsigned)ip < (unsigned)tb.prod && (unsigned)ii < (unsigned)tb.prod) {
+            const uint4 a0 = tb.lo[ip & lomask], a1 = tb.hi[ip >> tb.shift];
+            const uint4 b0 = tb.lo[ii & lomask], b1 = tb.hi[ii >> tb.shift];
+            a = make_uint4(a0.x | a1.x, a0.y | a1.y, a0.z | a1.z, a0.w | a1.w);
+            b = make_uint4(b0.x | b1.x, b0.y | b1.y, b0.z | b1.z, b0.w | b1.w);
+        } else {
+            a = sel_code(ip, tb, f);
+            b = sel_code(ii, tb, f);
+        }
+        const int D = __dp4a((int)a.z, (int)b.x, __dp4a((int)a.w, (int)b.y, 0));
+        const int A = __dp4a((int)a.z, (int)a.x, __dp4a((int)a.w, (int)a.y, 0));
+        const int B = __dp4a((int)b.z, (int)b.x, __dp4a((int)b.w, (int)b.y, 0));
+        const int Pq = A * B, aD = abs(D);
+        float S;
+        if (Pq <= tb.pmax && aD <= tb.dmax) {
+            S = tb.stab[aD * prow + Pq];
+        } else {
+            S = Pq > 0 ? __fdiv_rn(__fmul_rn((float)aD, tb.invQ), __fsqrt_rn(__fmul_rn((float)Pq, tb.invQ2))) : 0.f;
+        }
+        return D < 0 ? -S : S;  // rounding is symmetric; D = 0 gives +0
+    };
     for (int it = 0; it < iters; ++it) {
         const int j = it * SB_THREADS + tid;
-        const bool act = j < HW;
+        const bool act = it < full || j < HW;
         int bkt = 0;
         if (act) {
-            const uint4 a = sel_code(fp[j], tb, f), b = sel_code(fi[j], tb, f);
-            const int D = __dp4a((int)a.z, (int)b.x, __dp4a((int)a.w, (int)b.y, 0));
-            const int A = __dp4a((int)a.z, (int)a.x, __dp4a((int)a.w, (int)a.y, 0));
-            const int B = __dp4a((int)b.z, (int)b.x, __dp4a((int)b.w, (int)b.y, 0));
-            const int Pq = A * B;
-            float S = 0.f;
-            if (Pq > 0) {
-                const float den = Pq <= tb.pmax ? tb.rsq[Pq] : __fsqrt_rn(__fmul_rn((float)Pq, tb.invQ2));
-                S = __fdiv_rn(__fmul_rn((float)D, tb.invQ), den);
-            }
-            S = __fadd_rn(S, 0.f);  // -0 -> +0: equal similarities have equal images
+            const float S = similarity(fp[j], fi[j]);
             ords[j] = sim_order(S);
             bkt = sim_bucket(S);
-            if (sim) sim[frame * HW + j] = S;
+            if (simf) simf[j] = S;
         }
         const uint32_t am = __ballot_sync(0xffffffffu, act);
         if (act) {
@@ -629,7 +653,7 @@ __global__ void __launch_bounds__(SB_THREADS, 2) select_bucket_kernel(
 // Whether the integer form applies (see above), and its table geometry.
 struct SelPlan {
     bool ok = false;
-    int split_c = 0, shift = 0, nhi = 0, Q = 0, pmax = 0, prod = 0;
+    int split_c = 0, shift = 0, nhi = 0, Q = 0, pmax = 0, prod = 0, dmax = 0;
 };
 
 SelPlan sel_plan(const FsqConsts& f, long long HW) {
@@ -643,7 +667,7 @@ SelPlan sel_plan(const FsqConsts& f, long long HW) {
     }
     const long long prod = (long long)f.basis[f.nlev - 1] * f.levels[f.nlev - 1];
     const int dmax = f.nlev * Q;
-    if ((long long)dmax * dmax > SB_PMAX) return p;
+    if ((long long)dmax * dmax > SB_PMAX || (long long)(dmax + 1) * (dmax * dmax + 1) > SB_STAB_MAX) return p;
     for (int c = 1; c < f.nlev; ++c) {
         const int b = f.basis[c];
         if (b & (b - 1)) continue;
@@ -654,6 +678,7 @@ SelPlan sel_plan(const FsqConsts& f, long long HW) {
             p.nhi = (int)(prod / b);
             p.Q = Q;
             p.pmax = dmax * dmax;
+            p.dmax = dmax;
             p.prod = (int)prod;
             return p;
         }
@@ -667,7 +692,7 @@ size_t similarity_workspace_bytes(long long N, int Tp, long long HW) {
     // per-token keys and per-frame thresholds (the three-kernel form), the digit
     // table, and the integer form's tables
     return (size_t)(N * Tp * HW) * 8 + (size_t)(N * Tp) * 8 + (size_t)DIGIT_TAB * 4 + 512 +
-           (size_t)2 * SB_TAB_MAX * 16 + (size_t)(SB_PMAX + 1) * 4 + 512;
+           (size_t)2 * SB_TAB_MAX * 16 + (size_t)SB_STAB_MAX * 4 + 512;
 }
 
 int launch_similarity_mask(const int32_t* idx_p, const int32_t* idx_i, long long N, int Tp, int Hq, int Wq,
@@ -684,14 +709,16 @@ int launch_similarity_mask(const int32_t* idx_p, const int32_t* idx_i, long long
         tb = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(tb) + 255) & ~uintptr_t(255));
         uint4* lo = reinterpret_cast<uint4*>(tb);
         uint4* hi = lo + SB_TAB_MAX;
-        float* rsq = reinterpret_cast<float*>(hi + SB_TAB_MAX);
-        const int nt = std::max(std::max(1 << pl.shift, pl.nhi), pl.pmax + 1);
-        sel_tables_kernel<<<blocks_for(nt, 256), 256, 0, s>>>(f, pl.split_c, pl.shift, pl.nhi, pl.Q, pl.pmax, lo, hi,
-                                                              rsq);
+        float* stab = reinterpret_cast<float*>(hi + SB_TAB_MAX);
+        const int dmax = pl.dmax;
+        const int nt = std::max(std::max(1 << pl.shift, pl.nhi), (dmax + 1) * (pl.pmax + 1));
+        sel_tables_kernel<<<blocks_for(nt, 256), 256, 0, s>>>(f, pl.split_c, pl.shift, pl.nhi, pl.Q, pl.pmax, dmax, lo,
+                                                              hi, stab);
         SelTables t;
         t.lo = lo;
         t.hi = hi;
-        t.rsq = rsq;
+        t.stab = stab;
+        t.dmax = dmax;
         t.invQ = 1.0f / (float)pl.Q;
         t.invQ2 = 1.0f / (float)(pl.Q * pl.Q);
         t.shift = pl.shift;

@@ -64,66 +64,69 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
     return c;
 }
 
-// One warp per (row, 128-token segment): lane l takes tokens w = 128 s + 4 l .. + 3
-// of the row, whose decisions come from one Philox block (counter j >> 2, j the
-// token's index in its sample) when the row starts on a multiple of 4 tokens, or
-// from two when it does not; the lane's four keep bits are ORed into the row's
-// mask words over the 8 lanes that share a word. IDX is int (rows * segments
-// below 2^31) or long long.
+// Rows are cut into 32-token segments (one keep-mask word each) and a warp takes
+// four consecutive segments, 8 lanes each: lane l of a segment decides tokens
+// w = 32 s + 4 l .. + 3 of its row from one Philox block (counter j >> 2, j the
+// token's index in its sample) when the row starts on a multiple of 4 tokens,
+// or from two when it does not; the 8 lanes OR their nibbles into the word.
+// Only the last segment of a row can be partial, so a row of a multiple of 32
+// tokens keeps every lane busy. IDX is int (segments below 2^31) or long long.
 template <typename IDX>
-__global__ void drop4_kernel(const int32_t* __restrict__ idx, int TH, int Wq, int nseg, IDX warps,
+__global__ void drop4_kernel(const int32_t* __restrict__ idx, int TH, int Wq, int nseg, IDX segs,
                              unsigned long long thr, uint2 key, uint32_t chunk_lo, uint32_t stream_lo,
                              int32_t zero_index, int32_t* __restrict__ out, uint32_t* __restrict__ keep_bits) {
-    const IDX gw = ((IDX)blockIdx.x * blockDim.x + threadIdx.x) / 32;
-    const int lane = threadIdx.x % 32;
-    if (gw >= warps) return;
-    const IDX row = gw / nseg;
-    const int seg = (int)(gw - row * nseg);
-    const int n = (int)(row / TH);
-    const uint32_t rin = (uint32_t)(row - (IDX)n * TH);  // t*Hq + h within sample n
-    const int w0 = seg * 128 + 4 * lane;
-    const int nw = min(4, Wq - w0);  // tokens of this lane (<= 0: none)
+    const IDX gs = ((IDX)blockIdx.x * blockDim.x + threadIdx.x) / 8;  // global segment of this lane
+    const int lane = threadIdx.x % 32, sl = lane & 7;
     uint32_t nib = 0;
-    if (nw > 0) {
-        const uint32_t j0 = rin * (uint32_t)Wq + (uint32_t)w0;  // sample-local index of the first token
-        const uint4 r0 = philox4x32_10(make_uint4(j0 >> 2, (uint32_t)n, chunk_lo, stream_lo), key);
-        uint4 r1 = r0;
-        if ((j0 & 3u) != 0u && nw > 4 - (int)(j0 & 3u))
-            r1 = philox4x32_10(make_uint4((j0 >> 2) + 1u, (uint32_t)n, chunk_lo, stream_lo), key);
-        const long long o = (long long)row * Wq + w0;
-        int32_t v[4];
-        const bool vec = nw == 4 && (o & 3) == 0;
-        if (vec) {
-            const int4 q = *reinterpret_cast<const int4*>(idx + o);
-            v[0] = q.x;
-            v[1] = q.y;
-            v[2] = q.z;
-            v[3] = q.w;
-        } else {
-            for (int i = 0; i < 4; ++i) v[i] = i < nw ? idx[o + i] : 0;
-        }
+    IDX row = 0;
+    int sr = 0;
+    if (gs < segs) {
+        row = gs / nseg;
+        sr = (int)(gs - row * nseg);
+        const int n = (int)(row / TH);
+        const uint32_t rin = (uint32_t)(row - (IDX)n * TH);  // t*Hq + h within sample n
+        const int w0 = sr * 32 + 4 * sl;
+        const int nw = min(4, Wq - w0);  // tokens of this lane (<= 0: none)
+        if (nw > 0) {
+            const uint32_t j0 = rin * (uint32_t)Wq + (uint32_t)w0;  // sample-local index of the first token
+            const uint4 r0 = philox4x32_10(make_uint4(j0 >> 2, (uint32_t)n, chunk_lo, stream_lo), key);
+            uint4 r1 = r0;
+            if ((j0 & 3u) != 0u && nw > 4 - (int)(j0 & 3u))
+                r1 = philox4x32_10(make_uint4((j0 >> 2) + 1u, (uint32_t)n, chunk_lo, stream_lo), key);
+            const long long o = (long long)row * Wq + w0;
+            int32_t v[4];
+            const bool vec = nw == 4 && (o & 3) == 0;
+            if (vec) {
+                const int4 q = *reinterpret_cast<const int4*>(idx + o);
+                v[0] = q.x;
+                v[1] = q.y;
+                v[2] = q.z;
+                v[3] = q.w;
+            } else {
+                for (int i = 0; i < 4; ++i) v[i] = i < nw ? idx[o + i] : 0;
+            }
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const uint32_t j = j0 + (uint32_t)i;
-            const uint4& r = ((j >> 2) == (j0 >> 2)) ? r0 : r1;
-            const uint32_t word32 = (j & 3u) == 0 ? r.x : (j & 3u) == 1 ? r.y : (j & 3u) == 2 ? r.z : r.w;
-            const bool keep = i < nw && !((unsigned long long)word32 < thr);
-            if (keep) nib |= 1u << i;
-            if (!keep) v[i] = zero_index;
-        }
-        if (vec) {
-            *reinterpret_cast<int4*>(out + o) = make_int4(v[0], v[1], v[2], v[3]);
-        } else {
-            for (int i = 0; i < nw; ++i) out[o + i] = v[i];
+            for (int i = 0; i < 4; ++i) {
+                const uint32_t j = j0 + (uint32_t)i;
+                const uint4& r = ((j >> 2) == (j0 >> 2)) ? r0 : r1;
+                const uint32_t word32 = (j & 3u) == 0 ? r.x : (j & 3u) == 1 ? r.y : (j & 3u) == 2 ? r.z : r.w;
+                const bool keep = i < nw && !((unsigned long long)word32 < thr);
+                if (keep) nib |= 1u << i;
+                if (!keep) v[i] = zero_index;
+            }
+            if (vec) {
+                *reinterpret_cast<int4*>(out + o) = make_int4(v[0], v[1], v[2], v[3]);
+            } else {
+                for (int i = 0; i < nw; ++i) out[o + i] = v[i];
+            }
         }
     }
-    // lanes 8q .. 8q + 7 hold word 4 s + q of the row (bits 4 (lane % 8) ..)
-    uint32_t m = nib << (4 * (lane & 7));
+    // the 8 lanes of a segment hold its word: bits 4 (lane % 8) ..
+    uint32_t m = nib << (4 * sl);
     m |= __shfl_xor_sync(0xffffffffu, m, 1);
     m |= __shfl_xor_sync(0xffffffffu, m, 2);
     m |= __shfl_xor_sync(0xffffffffu, m, 4);
-    const int nwords = (Wq + 31) / 32, word = seg * 4 + lane / 8;
-    if (keep_bits && (lane & 7) == 0 && word < nwords) keep_bits[(long long)row * nwords + word] = m;
+    if (keep_bits && sl == 0 && gs < segs) keep_bits[(long long)row * nseg + sr] = m;
 }
 
 // --------------------------------------------------------- row packets
@@ -239,18 +242,19 @@ int launch_drop(const int32_t* idx, int N, int Tq, int Hq, int Wq, unsigned long
                 uint64_t stream_id, uint64_t chunk_id, int32_t zero_index, int32_t* out, uint32_t* keep_bits,
                 cudaStream_t s) {
     const long long rows = (long long)N * Tq * Hq;
-    const int nseg = (Wq + 127) / 128;
-    const long long warps = rows * nseg;
-    if (warps <= 0) return 0;
+    const int nseg = (Wq + 31) / 32;  // 32-token segments (keep-mask words) per row
+    const long long segs = rows * nseg;
+    if (segs <= 0) return 0;
     const uint2 key = make_uint2((uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32));
     const uint32_t clo = (uint32_t)(chunk_id & 0xffffffffu), slo = (uint32_t)(stream_id & 0xffffffffu);
     const int TH = Tq * Hq;
-    if (warps * 32 < (1LL << 31))
-        drop4_kernel<int><<<blocks_for(warps * 32, 256), 256, 0, s>>>(idx, TH, Wq, nseg, (int)warps, thr, key, clo,
-                                                                      slo, zero_index, out, keep_bits);
+    const long long threads = (segs + 3) / 4 * 32;  // four segments per warp
+    if (threads < (1LL << 31))
+        drop4_kernel<int><<<blocks_for(threads, 256), 256, 0, s>>>(idx, TH, Wq, nseg, (int)segs, thr, key, clo,
+                                                                   slo, zero_index, out, keep_bits);
     else
-        drop4_kernel<long long><<<blocks_for(warps * 32, 256), 256, 0, s>>>(idx, TH, Wq, nseg, warps, thr, key,
-                                                                            clo, slo, zero_index, out, keep_bits);
+        drop4_kernel<long long><<<blocks_for(threads, 256), 256, 0, s>>>(idx, TH, Wq, nseg, segs, thr, key, clo,
+                                                                         slo, zero_index, out, keep_bits);
     return (int)cudaGetLastError();
 }
 
