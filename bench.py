@@ -280,6 +280,7 @@ def gpu_arm(args):
     out["selection"] = selection(args, roofline["groupnorm"]["peak_gbs"])
     out["gop_smoothing"] = gop_smoothing(roofline["groupnorm"]["peak_gbs"])
     out["token_kernels"] = token_kernels(roofline["groupnorm"]["peak_gbs"])
+    out["cudnn_reference"] = cudnn_reference(roofline["peak"])
     if not args.no_rsa:
         tk8 = P.Tokenizer("bf16", t_stem=2)
         p8 = S.weights_for(tk8.param_spec(), seed=0)
@@ -455,6 +456,48 @@ def selection(args, hbm_gbs, streams=256, Tp=4, Hq=90, Wq=160, rate=0.25, steps=
             "note": "2 launches: digit table, then one block per latent frame (similarity, 3-pass radix "
                     "select over shared memory, tie cut by position, drop and keep bits); latency-bound per "
                     "frame (about 77 us for a 90x160 frame), not by HBM"}
+
+
+# ------------------------------------------------------------- a library reference point
+
+def cudnn_reference(peak_tflops, steps=10, warmup=3):
+    """A labelled reference point, not part of the timed step: torch's conv3d (cuDNN)
+    in BF16 on the level-0 layer of the 720p step (17 x 360 x 640, 128 -> 128 channels,
+    3x3x3; zero-padded in time instead of causal, the same FLOPs), channels-last, beside
+    this library's tok_conv3d on the same layer (replicate-causal)."""
+    import torch
+    import torch.nn.functional as F
+
+    import paper_2602_03529_b300 as P
+
+    T, H, W, C = 17, 360, 640, 128
+    g = torch.Generator(device="cuda").manual_seed(4)
+    x = torch.randn((1, T, H, W, C), device="cuda", generator=g).to(torch.bfloat16)
+    w = torch.randn((C, 3, 3, 3, C), device="cuda", generator=g) * 0.02
+    b = torch.zeros(C, device="cuda")
+    flop = 2.0 * T * H * W * C * 27 * C
+    xt = x.permute(0, 4, 1, 2, 3).contiguous(memory_format=torch.channels_last_3d)
+    wt = w.permute(0, 4, 1, 2, 3).to(torch.bfloat16).contiguous(memory_format=torch.channels_last_3d)
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / steps
+
+    ms_cudnn = timed(lambda: F.conv3d(xt, wt, padding=1))
+    ms_ours = timed(lambda: P.conv3d(x, w, b, (1, 1, 1), "replicate"))
+    return {"workload": "level-0 conv of the 720p step: 1x17x360x640, 128 -> 128 channels, 3x3x3, BF16",
+            "tflop": flop / 1e12, "cudnn_ms": ms_cudnn, "cudnn_tflops": flop / (ms_cudnn / 1e3) / 1e12,
+            "ours_ms": ms_ours, "ours_tflops": flop / (ms_ours / 1e3) / 1e12, "peak_tflops": peak_tflops,
+            "note": "torch.nn.functional.conv3d (cuDNN), channels_last_3d, symmetric zero padding; ours: tok_conv3d "
+                    "(weight packing included in every call)"}
 
 
 # ------------------------------------------------------------- FSQ and drop mask alone
