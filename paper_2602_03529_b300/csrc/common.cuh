@@ -212,6 +212,18 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t smem_addr) {
     return d;
 }
 
+// The same for 64-byte swizzle: rows of 64 B (32 bf16 of K), 8-row atoms of
+// 512 B stacked along M/N.
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t smem_addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((smem_addr >> 4) & 0x3FFFu);       // start address
+    d |= (uint64_t)1u << 16;                             // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(512u >> 4) << 32;                    // stride byte offset
+    d |= (uint64_t)1u << 46;                             // descriptor version (sm_100 family)
+    d |= (uint64_t)4u << 61;                             // swizzle: 64B
+    return d;
+}
+
 // Instruction descriptor for kind::f16: BF16 x BF16 -> FP32, both K-major.
 __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
     return (1u << 4)                     // D format: F32

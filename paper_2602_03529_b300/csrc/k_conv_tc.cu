@@ -34,15 +34,16 @@
 
 namespace tok {
 
-bool encode_act_map(CUtensorMap* m, const void* base, int frames, int H, int W, int C, int BH, int BW, bool strided);
-bool encode_w_map(CUtensorMap* m, const void* base, int rows, int Kpad, int BN);
+bool encode_act_map(CUtensorMap* m, const void* base, int frames, int H, int W, int C, int BH, int BW, bool strided,
+                    int kc = 64);
+bool encode_w_map(CUtensorMap* m, const void* base, int rows, int Kpad, int BN, int kc = 64);
 
 struct TcGeo {
     int BH, BW;              // output tile = BH rows x BW cols of one frame
     int tiles_w, tiles_h;
     int n_tiles;             // Cout_pad / BN
     long long num_tiles;     // m tiles x n tiles
-    int cpt;                 // 64-channel blocks per tap
+    int cpt;                 // KC-channel blocks per tap
     int nkb;                 // K blocks per tile = taps * cpt
     int strided;             // parity view (sh = sw = 2)
     long long m_tiles;       // voxel tiles
@@ -93,21 +94,32 @@ namespace {
 //                most 32 channels) loads only its 16 or 32 weight rows per tap
 //                into weight slots whose other rows stay zero.
 constexpr int HALO_BW_MAX = 64;
+// Input channels per K block of the wide halo form: 64 (128-byte rows, two 96 KB
+// stages in flight) or 32 (64-byte rows, four 48 KB stages). Measured on the
+// level-0 layer of the 720p step: 32 gives no gain (1383 against 1415 TFLOP/s);
+// the operand bytes per FLOP it pulls from L2 are the same, and the deeper
+// pipeline does not raise the tensor pipe's share, so that stays 64.
+constexpr int kHaloKC = 64;
 constexpr int DWM_BH = 8, DWM_BW = 32;  // taps-in-rows forms: rows (dw rows: output rows) x columns of a tile's box
 
 //                HALO = number of 64-channel blocks per stage (0: no halo).
 //                TR: taps in the MMA rows. 3: the dw rows (a 10 x 32 box, weight slots of
 //                64 rows); 9: the (dh, dw) rows (an 8 x 32 box, one 128-row weight slot).
-template <int BN, bool SWAP, int HALO = 0, int TR = 0>
+//                KC: input channels per K block (64: rows of 128 B, 128-byte swizzle;
+//                32: rows of 64 B, 64-byte swizzle, stages half as large and twice
+//                as many in flight).
+template <int BN, bool SWAP, int HALO = 0, int TR = 0, int KC = 64>
 struct Cfg {
+    static_assert(KC == 64 || (KC == 32 && TR == 0), "32-channel K blocks: plain and halo forms");
+    static constexpr int ROWB = KC * 2;            // bytes of one voxel's (or weight row's) K block
     static constexpr int ROWS = SWAP ? 256 : 128;  // voxels per tile
     static constexpr int HALO_BW = HALO_BW_MAX;
     // one channel block's input box
-    static constexpr int SUB_ACT = TR == 3   ? (DWM_BH + 2) * DWM_BW * 128
-                                   : TR == 9 ? DWM_BH * DWM_BW * 128
-                                             : (ROWS + (HALO ? 2 * HALO_BW : 0)) * 128;
-    static constexpr int ACT_BYTES = (HALO ? HALO : 1) * SUB_ACT;  // 64 bf16 channels per row
-    static constexpr int W_TAP_BYTES = (TR == 3 ? 64 : BN) * 128;
+    static constexpr int SUB_ACT = TR == 3   ? (DWM_BH + 2) * DWM_BW * ROWB
+                                   : TR == 9 ? DWM_BH * DWM_BW * ROWB
+                                             : (ROWS + (HALO ? 2 * HALO_BW : 0)) * ROWB;
+    static constexpr int ACT_BYTES = (HALO ? HALO : 1) * SUB_ACT;  // KC bf16 channels per row
+    static constexpr int W_TAP_BYTES = (TR == 3 ? 64 : BN) * ROWB;
     static constexpr int W_BYTES = (TR == 9 ? HALO : HALO ? 3 * HALO : 1) * W_TAP_BYTES;
     static constexpr int STAGE = ACT_BYTES + W_BYTES;
     static constexpr int STAGES = (200 * 1024 / STAGE) > 8 ? 8 : (200 * 1024 / STAGE);
@@ -127,6 +139,15 @@ struct Cfg {
 struct TileCoord {
     int n, to, th, tw, nt;
 };
+
+// Operand descriptor of a K block of KC channels (128- or 64-byte swizzle).
+template <int KC>
+__device__ __forceinline__ uint64_t kdesc(uint32_t addr) {
+    if constexpr (KC == 64)
+        return sw128_desc(addr);
+    else
+        return sw64_desc(addr);
+}
 
 // Voxel tiles are numbered with the output frame fastest: the CTAs working at
 // the same time cover a few spatial blocks across all frames, so an input
@@ -213,9 +234,9 @@ __device__ __forceinline__ int problem_of(const TcBatch<MAXP>& B, long long unit
 // nine spatial taps and a K block is (dt, 64 channels) with one 8 x 32 input
 // box (6 x 30 outputs); the epilogue adds the tap rows with their row and
 // column shifts, out[co][y][x] = sum over dh, dw of D[(dh, dw, co)][y + dh][x + dw].
-template <int BN, bool SWAP, int MAXP, int HALO, int TR = 0>
+template <int BN, bool SWAP, int MAXP, int HALO, int TR = 0, int KC = 64>
 __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__ TcBatch<MAXP> B) {
-    using C = Cfg<BN, SWAP, HALO, TR>;
+    using C = Cfg<BN, SWAP, HALO, TR, KC>;
     constexpr bool DWM = TR == 3, T9 = TR == 9;
     constexpr int NDH = T9 ? 1 : 3;  // weight boxes (dh taps) per channel block of a K block
     static_assert(TR == 0 || ((TR == 3 || TR == 9) && SWAP && HALO == 1), "taps in rows: swapped halo form");
@@ -324,11 +345,11 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                     if constexpr (HALO > 0) {
                         // rows th*BH - 1 .. th*BH + BH of the input frame (zeros outside), per block
                         // (nine taps in rows: a box of BH rows, th*bho - 1 .. th*bho + bho)
-                        mbar_arrive_expect_tx(&full[s], (uint32_t)(HALO * ((T9 ? g.BH : g.BH + 2) * g.BW * 128 +
-                                                                           NDH * B.w_rows * 128)));
+                        mbar_arrive_expect_tx(&full[s], (uint32_t)(HALO * ((T9 ? g.BH : g.BH + 2) * g.BW * C::ROWB +
+                                                                           NDH * B.w_rows * C::ROWB)));
 #pragma unroll
                         for (int c = 0; c < HALO; ++c) {
-                            const int ci = (cb * HALO + c) * 64;
+                            const int ci = (cb * HALO + c) * KC;
                             // taps in rows: columns tw*bwo - 1 .. tw*bwo + bwo of the input (all three dw)
                             tma_load_4d(sa + c * C::SUB_ACT, src, &full[s], ci,
                                         TR ? tc.tw * g.bwo - 1 : tc.tw * g.BW + dw - 1, tc.th * g.bho - 1, tcoord);
@@ -349,14 +370,14 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                     }
                     mbar_arrive_expect_tx(&full[s], C::STAGE);
                     if (!g.strided) {
-                        tma_load_4d(sa, src, &full[s], cb * 64, tc.tw * g.BW + dw - pw_, tc.th * g.BH + dh - ph_,
+                        tma_load_4d(sa, src, &full[s], cb * KC, tc.tw * g.BW + dw - pw_, tc.th * g.BH + dh - ph_,
                                     tcoord);
                     } else {
                         const int pwp = (dw == 1) ? 0 : 1, php = (dh == 1) ? 0 : 1;
-                        tma_load_5d(sa, src, &full[s], pwp * a.Cin + cb * 64, tc.tw * g.BW + (dw == 0 ? -1 : 0), php,
+                        tma_load_5d(sa, src, &full[s], pwp * a.Cin + cb * KC, tc.tw * g.BW + (dw == 0 ? -1 : 0), php,
                                     tc.th * g.BH + (dh == 0 ? -1 : 0), tcoord);
                     }
-                    tma_load_2d(sb, wmap, &full[s], tap * a.Cin + cb * 64, tc.nt * BN);
+                    tma_load_2d(sb, wmap, &full[s], tap * a.Cin + cb * KC, tc.nt * BN);
                     last_ph[s] = (int)ph;
                     if (++s == C::STAGES) {
                         s = 0;
@@ -380,7 +401,7 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                 long long lu;
                 const TcGeo& gu = B.g[problem_of(B, u, &lu)];
                 const int nkb = gu.nkb;
-                const uint32_t row_step = (uint32_t)gu.BW * 128u;  // one input row of the halo box
+                const uint32_t row_step = (uint32_t)gu.BW * C::ROWB;  // one input row of the halo box
                 const int acc = it & 1;
                 const uint32_t aph = (uint32_t)((it >> 1) & 1);
                 if (!mbar_wait(&tempty[acc], aph ^ 1, status, wait_ns)) break;
@@ -405,15 +426,15 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                                 const uint32_t wa = s_w + (uint32_t)((c * NDH + dh) * C::W_TAP_BYTES);
                                 const uint32_t op_a = SWAP ? wa : xa, op_b = SWAP ? xa : wa;
 #pragma unroll
-                                for (int k = 0; k < 4; ++k)
-                                    tc_mma_bf16(d, sw128_desc(op_a + k * 32), sw128_desc(op_b + k * 32), idesc,
+                                for (int k = 0; k < KC / 16; ++k)
+                                    tc_mma_bf16(d, kdesc<KC>(op_a + k * 32), kdesc<KC>(op_b + k * 32), idesc,
                                                 (kb | c | dh | k) != 0 ? 1u : 0u);
                             }
                     } else {
                         const uint32_t op_a = SWAP ? s_w : s_act, op_b = SWAP ? s_act : s_w;
 #pragma unroll
-                        for (int k = 0; k < 4; ++k)
-                            tc_mma_bf16(d, sw128_desc(op_a + k * 32), sw128_desc(op_b + k * 32), C::IDESC,
+                        for (int k = 0; k < KC / 16; ++k)
+                            tc_mma_bf16(d, kdesc<KC>(op_a + k * 32), kdesc<KC>(op_b + k * 32), C::IDESC,
                                         (kb | k) != 0 ? 1u : 0u);
                     }
                     tc_commit(&empty[s]);
@@ -1078,10 +1099,10 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
     if (warp == 1) tmem_dealloc(tmem_base, C::TMEM_COLS);
 }
 
-template <int BN, bool SWAP, int MAXP, int HALO = 0, int TR = 0>
+template <int BN, bool SWAP, int MAXP, int HALO = 0, int TR = 0, int KC = 64>
 int launch_bn(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int cta_tiles, cudaStream_t stream) {
-    using C = Cfg<BN, SWAP, HALO, TR>;
-    auto kern = conv_tc_kernel<BN, SWAP, MAXP, HALO, TR>;
+    using C = Cfg<BN, SWAP, HALO, TR, KC>;
+    auto kern = conv_tc_kernel<BN, SWAP, MAXP, HALO, TR, KC>;
     TcBatch<MAXP> B;
     memset(&B, 0, sizeof(B));
     // a narrow halo layer loads its real weight rows only
@@ -1092,9 +1113,9 @@ int launch_bn(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int c
                : (HALO > 0 && SWAP && as[0].Cout <= 32) ? (as[0].Cout + 15) / 16 * 16
                                                         : BN;
     const int wk = TR == 3 ? 9 * as[0].Cin : TR == 9 ? 3 * as[0].Cin : as[0].Kpad;
-    if (!encode_w_map(&B.tm_w, as[0].w, as[0].Cout_pad, wk, B.w_rows)) return -1;
+    if (!encode_w_map(&B.tm_w, as[0].w, as[0].Cout_pad, wk, B.w_rows, KC)) return -1;
     if (as[0].w0) {
-        if (!encode_w_map(&B.tm_w0, as[0].w0, as[0].Cout_pad, wk, B.w_rows)) return -1;
+        if (!encode_w_map(&B.tm_w0, as[0].w0, as[0].Cout_pad, wk, B.w_rows, KC)) return -1;
     } else {
         B.tm_w0 = B.tm_w;
     }
@@ -1105,9 +1126,9 @@ int launch_bn(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int c
         const bool strided = g.strided != 0;
         // the halo box: one input row above and below (nine taps in rows: BH rows in all)
         const int box_h = HALO ? (TR == 9 ? g.BH : g.BH + 2) : g.BH;
-        if (!encode_act_map(&B.tm_x[p], a.x, a.N * a.Tin, a.Hin, a.Win, a.Cin, box_h, g.BW, strided)) return -1;
+        if (!encode_act_map(&B.tm_x[p], a.x, a.N * a.Tin, a.Hin, a.Win, a.Cin, box_h, g.BW, strided, KC)) return -1;
         if (a.hist) {
-            if (!encode_act_map(&B.tm_h[p], a.hist, a.N * a.hist_T, a.Hin, a.Win, a.Cin, box_h, g.BW, strided))
+            if (!encode_act_map(&B.tm_h[p], a.hist, a.N * a.hist_T, a.Hin, a.Win, a.Cin, box_h, g.BW, strided, KC))
                 return -1;
         } else {
             B.tm_h[p] = B.tm_x[p];
@@ -1137,10 +1158,10 @@ int launch_bn(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int c
     return (int)cudaGetLastError();
 }
 
-template <int BN, bool SWAP, int NCB, int TR = 0>  // NCB: 64-channel blocks per halo stage
+template <int BN, bool SWAP, int NCB, int TR = 0, int KC = 64>  // NCB: KC-channel blocks per halo stage
 int launch_bn_halo(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int cta_tiles, cudaStream_t stream) {
-    return count == 1 ? launch_bn<BN, SWAP, 1, NCB, TR>(as, gs, 1, num_sms, cta_tiles, stream)
-                      : launch_bn<BN, SWAP, kMaxConvGroup, NCB, TR>(as, gs, count, num_sms, cta_tiles, stream);
+    return count == 1 ? launch_bn<BN, SWAP, 1, NCB, TR, KC>(as, gs, 1, num_sms, cta_tiles, stream)
+                      : launch_bn<BN, SWAP, kMaxConvGroup, NCB, TR, KC>(as, gs, count, num_sms, cta_tiles, stream);
 }
 
 template <int BN, bool SWAP>
@@ -1166,44 +1187,46 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
     return fn;
 }
 
-// Activation map: plain (C, W, H, N*T) or parity view (2C, W/2, 2, H/2, N*T).
+// Activation map: plain (C, W, H, N*T) or parity view (2C, W/2, 2, H/2, N*T); boxes of
+// kc channels (64: 128-byte swizzle, 32: 64-byte swizzle).
 bool encode_act_map(CUtensorMap* m, const void* base, int frames, int H, int W, int C, int BH, int BW,
-                    bool strided) {
+                    bool strided, int kc) {
     auto enc = get_encode_fn();
     if (!enc) return false;
     const uint64_t es = 2;
+    const CUtensorMapSwizzle sw = kc == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B;
     CUresult r;
     if (!strided) {
         cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)frames};
         cuuint64_t strides[3] = {C * es, (uint64_t)W * C * es, (uint64_t)H * W * C * es};
-        cuuint32_t box[4] = {64, (cuuint32_t)BW, (cuuint32_t)BH, 1};
+        cuuint32_t box[4] = {(cuuint32_t)kc, (cuuint32_t)BW, (cuuint32_t)BH, 1};
         cuuint32_t estr[4] = {1, 1, 1, 1};
         r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, strides, box, estr,
-                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     } else {
         cuuint64_t dims[5] = {(cuuint64_t)(2 * C), (cuuint64_t)(W / 2), 2, (cuuint64_t)(H / 2),
                               (cuuint64_t)frames};
         cuuint64_t strides[4] = {2 * C * es, (uint64_t)W * C * es, 2ull * W * C * es, (uint64_t)H * W * C * es};
-        cuuint32_t box[5] = {64, (cuuint32_t)BW, 1, (cuuint32_t)BH, 1};
+        cuuint32_t box[5] = {(cuuint32_t)kc, (cuuint32_t)BW, 1, (cuuint32_t)BH, 1};
         cuuint32_t estr[5] = {1, 1, 1, 1, 1};
         r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<void*>(base), dims, strides, box, estr,
-                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     }
     return r == CUDA_SUCCESS;
 }
 
-bool encode_w_map(CUtensorMap* m, const void* base, int rows, int Kpad, int BN) {
+bool encode_w_map(CUtensorMap* m, const void* base, int rows, int Kpad, int BN, int kc) {
     auto enc = get_encode_fn();
     if (!enc) return false;
     cuuint64_t dims[2] = {(cuuint64_t)Kpad, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)Kpad * 2};
-    cuuint32_t box[2] = {64, (cuuint32_t)BN};
+    cuuint32_t box[2] = {(cuuint32_t)kc, (cuuint32_t)BN};
     cuuint32_t estr[2] = {1, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+               CU_TENSOR_MAP_INTERLEAVE_NONE, kc == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // Choose the output tile shape (BH x BW = 128) that covers Hout x Wout with
@@ -1425,6 +1448,8 @@ int launch_conv_tc_group(const ConvArgs* as, int count, int num_sms, cudaStream_
         return -1;
     for (int p = 0; p < count; ++p)
         if (as[p].gn_part && (!conv_tc_gn_fusable(as[p]) || as[p].gn_cg != a0.gn_cg)) return -1;
+    // wide stride-1 3x3x3 layers: K blocks of kHaloKC channels
+    const bool wide_halo = halo && !rt.narrow && tr == 0 && a0.Cin % kHaloKC == 0;
     TcGeo gs[kMaxConvGroup];
     for (int p = 0; p < count; ++p) {
         TcGeo& g = gs[p];
@@ -1441,7 +1466,7 @@ int launch_conv_tc_group(const ConvArgs* as, int count, int num_sms, cudaStream_
         g.nvox = g.BH * g.BW;
         g.tiles_w = (a.Wout + g.bwo - 1) / g.bwo;
         g.tiles_h = (a.Hout + g.bho - 1) / g.bho;
-        g.cpt = a.Cin / 64;
+        g.cpt = a.Cin / (wide_halo ? kHaloKC : 64);
         g.nkb = dwm ? a.kt * g.cpt : halo ? a.kt * a.kw * g.cpt : a.kt * a.kh * a.kw * g.cpt;
         g.strided = (a.sh == 2) ? 1 : 0;
         g.halo = halo ? 1 : 0;
@@ -1450,6 +1475,8 @@ int launch_conv_tc_group(const ConvArgs* as, int count, int num_sms, cudaStream_
     }
     if (tr == 9) return launch_bn_halo<128, true, 1, 9>(as, gs, count, num_sms, cta_tiles, stream);
     if (tr == 3) return launch_bn_halo<128, true, 1, 3>(as, gs, count, num_sms, cta_tiles, stream);
+    if constexpr (kHaloKC != 64)
+        if (halo && wide_halo) return launch_bn_halo<128, true, 1, 0, kHaloKC>(as, gs, count, num_sms, cta_tiles, stream);
     if (halo) return launch_bn_halo<128, true, 1>(as, gs, count, num_sms, cta_tiles, stream);
     if (swap) return launch_bn_any<128, true>(as, gs, count, num_sms, cta_tiles, stream);
     switch (conv_tc_bn(a0.Cout_pad)) {

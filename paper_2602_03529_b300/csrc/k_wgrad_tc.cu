@@ -45,7 +45,8 @@
 
 namespace tok {
 
-bool encode_act_map(CUtensorMap* m, const void* base, int frames, int H, int W, int C, int BH, int BW, bool strided);
+bool encode_act_map(CUtensorMap* m, const void* base, int frames, int H, int W, int C, int BH, int BW, bool strided,
+                    int kc);
 
 namespace {
 
@@ -436,8 +437,8 @@ int launch_bn(const __nv_bfloat16* dy, const __nv_bfloat16* x, const WgradArgs& 
               int* status, unsigned long long wait_ns, cudaStream_t s) {
     using C = WCfg<BN, HT>;
     CUtensorMap mdy, mx;
-    if (!encode_act_map(&mdy, dy, a.N * a.Tout, a.Hout, a.Wout, a.Cdy, g.BH, g.BW, false)) return -1;
-    if (!encode_act_map(&mx, x, a.N * a.Tin, a.Hin, a.Win, a.Cin, HT ? g.BH + 2 : g.BH, g.BW, g.strided != 0))
+    if (!encode_act_map(&mdy, dy, a.N * a.Tout, a.Hout, a.Wout, a.Cdy, g.BH, g.BW, false, 64)) return -1;
+    if (!encode_act_map(&mx, x, a.N * a.Tin, a.Hin, a.Win, a.Cin, HT ? g.BH + 2 : g.BH, g.BW, g.strided != 0, 64))
         return -1;
     static bool attr = false;
     if (!attr) {
