@@ -70,6 +70,8 @@ struct TcBatch {
     long long unit_end[MAXP];
     long long num_units;
     int count;
+    int na;        // split rings: activation slots in flight (2..4)
+    int act_slot;  // split rings: bytes per activation slot (a multiple of 1 KB)
 };
 
 namespace {
@@ -100,6 +102,7 @@ constexpr int HALO_BW_MAX = 64;
 // the operand bytes per FLOP it pulls from L2 are the same, and the deeper
 // pipeline does not raise the tensor pipe's share, so that stays 64.
 constexpr int kHaloKC = 64;
+constexpr bool kHaloSplit = true;  // 64-channel K blocks in the split rings (see Cfg)
 constexpr int DWM_BH = 8, DWM_BW = 32;  // taps-in-rows forms: rows (dw rows: output rows) x columns of a tile's box
 
 //                HALO = number of 64-channel blocks per stage (0: no halo).
@@ -108,8 +111,18 @@ constexpr int DWM_BH = 8, DWM_BW = 32;  // taps-in-rows forms: rows (dw rows: ou
 //                KC: input channels per K block (64: rows of 128 B, 128-byte swizzle;
 //                32: rows of 64 B, 64-byte swizzle, stages half as large and twice
 //                as many in flight).
-template <int BN, bool SWAP, int HALO = 0, int TR = 0, int KC = 64>
+//                SPLIT: separate rings for the wide halo form (KC = 64): NW weight
+//                slots of one dh tap each (16 KB), and activation slots sized at
+//                launch for the largest box of the launch (2..4 of them in the
+//                rest of the 227 KB). One stage of the unified ring (box + three
+//                weight boxes, up to 96 KB) allows two stages in flight, and a
+//                stage's refill (issued when its MMAs retire) takes longer to land
+//                than the next stage's MMAs run, so the tensor pipe waited on TMA
+//                about a fifth of the time; the split rings keep two K blocks of
+//                weights and three boxes in flight.
+template <int BN, bool SWAP, int HALO = 0, int TR = 0, int KC = 64, bool SPLIT = false>
 struct Cfg {
+    static_assert(!SPLIT || (HALO == 1 && TR == 0 && KC == 64 && SWAP), "split rings: the wide halo form");
     static_assert(KC == 64 || (KC == 32 && TR == 0), "32-channel K blocks: plain and halo forms");
     static constexpr int ROWB = KC * 2;            // bytes of one voxel's (or weight row's) K block
     static constexpr int ROWS = SWAP ? 256 : 128;  // voxels per tile
@@ -130,7 +143,17 @@ struct Cfg {
     // (nine taps in rows: a staged box row of 128 accumulator rows and one output row of 16 channels)
     // (unswapped: per epilogue warp 32 voxel rows of 64 bf16 channels)
     static constexpr int EPI_BYTES = TR == 9 ? (128 + 16) * 33 * 4 : SWAP ? 4 * 16 * EPI_STRIDE * 4 : 4 * 32 * 128;
-    static constexpr int SMEM = STAGES * STAGE + 1024 + BAR_BYTES + EPI_BYTES;
+    static constexpr int NW = 6;                  // split rings: weight slots
+    static constexpr int W_SLOT = BN * ROWB;      // split rings: one dh tap's weight box
+    // a CTA's shared memory (227 KB) holds the kernel's static variables too: 64 bytes
+    // are left for them; aligning the (16-byte aligned) dynamic base to 1 KB costs at
+    // most 1008 bytes
+    static constexpr int SMEM_LIMIT = 232448 - 64;
+    static constexpr int SLACK = SPLIT ? 1008 : 1024;
+    static constexpr int SPLIT_ACT_BYTES = SMEM_LIMIT - NW * W_SLOT - SLACK - BAR_BYTES - EPI_BYTES;
+    static constexpr int BAR_OFF = SPLIT ? NW * W_SLOT + SPLIT_ACT_BYTES : STAGES * STAGE;
+    static constexpr int SMEM = BAR_OFF + SLACK + BAR_BYTES + EPI_BYTES;
+    static_assert(SMEM <= SMEM_LIMIT, "shared memory");
     // (the swapped halo forms build theirs per tile: N = the tile's voxels, and M = 64
     // for heads of at most 16 rows, whose output channel r stays in TMEM lane r)
     static constexpr uint32_t IDESC = SWAP ? idesc_bf16_f32(BN, ROWS) : idesc_bf16_f32(128, BN);
@@ -212,6 +235,22 @@ __device__ __forceinline__ GnTriple gn_shfl_down(GnTriple t, int o) {
     return b;
 }
 
+// Frame coordinate of input frame ti of sample n in the map *src it is read from:
+// frames past the last read zeros (adjoint convs read ahead), frames before the
+// first read the stream's history, frame 0 (replicate padding) or zeros.
+template <int MAXP>
+__device__ __forceinline__ int tap_frame(const TcBatch<MAXP>& B, int p, int n, int ti, const CUtensorMap** src) {
+    const ConvArgs& a = B.a[p];
+    *src = &B.tm_x[p];
+    if (ti >= a.Tin) return -1;  // whole box out of range -> zeros
+    if (ti >= 0) return n * a.Tin + ti;
+    if (a.hist) {
+        *src = &B.tm_h[p];
+        return n * a.hist_T + a.hist_T + ti;
+    }
+    return a.pad_mode == 0 ? n * a.Tin : -1;
+}
+
 // Problem of a global unit index and the unit's index within that problem.
 template <int MAXP>
 __device__ __forceinline__ int problem_of(const TcBatch<MAXP>& B, long long unit, long long* local) {
@@ -234,9 +273,9 @@ __device__ __forceinline__ int problem_of(const TcBatch<MAXP>& B, long long unit
 // nine spatial taps and a K block is (dt, 64 channels) with one 8 x 32 input
 // box (6 x 30 outputs); the epilogue adds the tap rows with their row and
 // column shifts, out[co][y][x] = sum over dh, dw of D[(dh, dw, co)][y + dh][x + dw].
-template <int BN, bool SWAP, int MAXP, int HALO, int TR = 0, int KC = 64>
+template <int BN, bool SWAP, int MAXP, int HALO, int TR = 0, int KC = 64, bool SPLIT = false>
 __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__ TcBatch<MAXP> B) {
-    using C = Cfg<BN, SWAP, HALO, TR, KC>;
+    using C = Cfg<BN, SWAP, HALO, TR, KC, SPLIT>;
     constexpr bool DWM = TR == 3, T9 = TR == 9;
     constexpr int NDH = T9 ? 1 : 3;  // weight boxes (dh taps) per channel block of a K block
     static_assert(TR == 0 || ((TR == 3 || TR == 9) && SWAP && HALO == 1), "taps in rows: swapped halo form");
@@ -245,12 +284,17 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw_addr = smem_u32(smem_raw);
     uint8_t* smem = smem_raw + (((raw_addr + 1023u) & ~1023u) - raw_addr);
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::STAGES * C::STAGE);
-    uint64_t* empty = full + C::STAGES;
-    uint64_t* tfull = empty + C::STAGES;
+    // full/empty: the stages of the unified ring, or the activation slots of the split
+    // rings (wfull/wempty: their weight slots)
+    constexpr int NFE = SPLIT ? 4 : C::STAGES, NWB = SPLIT ? C::NW : 0;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + C::BAR_OFF);
+    uint64_t* empty = full + NFE;
+    uint64_t* wfull = empty + NFE;
+    uint64_t* wempty = wfull + NWB;
+    uint64_t* tfull = wempty + NWB;
     uint64_t* tempty = tfull + 2;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
-    float* epi = reinterpret_cast<float*>(smem + C::STAGES * C::STAGE + C::BAR_BYTES);
+    float* epi = reinterpret_cast<float*>(smem + C::BAR_OFF + C::BAR_BYTES);
 
     const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
     const long long cid = blockIdx.x, ncl = gridDim.x;
@@ -261,9 +305,13 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
     if (s_skip) return;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < C::STAGES; ++s) {
+        for (int s = 0; s < NFE; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
+        }
+        for (int s = 0; s < NWB; ++s) {
+            mbar_init(&wfull[s], 1);
+            mbar_init(&wempty[s], 1);
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(&tfull[i], 1);
@@ -271,7 +319,7 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
         }
         fence_mbar_init();
     }
-    if constexpr (HALO > 0) {
+    if constexpr (HALO > 0 && !SPLIT) {
         // narrow layer: the weight boxes fill only the first w_rows rows of each
         // 128-row weight slot; the others are zero for the whole launch
         if (B.w_rows < BN) {
@@ -297,7 +345,65 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
     const uint32_t tmem_base = *tmem_slot;
 
     if (warp == 0) {
-        if (lane == 0) {
+        if (SPLIT && lane == 0) {
+            // ------------------------------------------------ TMA producer, split rings
+            // per K block (dt, dw, 64 channels): the box into the next activation slot,
+            // then the three dh taps' weight boxes into the next three weight slots
+            int sa = 0, sw = 0;
+            uint32_t pa = 0, pw = 0;
+            int last_a[4] = {-1, -1, -1, -1}, last_w[C::NW];
+#pragma unroll
+            for (int i = 0; i < C::NW; ++i) last_w[i] = -1;
+            const int na = B.na;
+            const uint32_t w_bytes = (uint32_t)(B.w_rows * C::ROWB);
+            bool ok = true;
+            for (long long u = cid; u < B.num_units && ok; u += ncl) {
+                long long lu;
+                const int p = problem_of(B, u, &lu);
+                const ConvArgs& a = B.a[p];
+                const TcGeo& g = B.g[p];
+                const TileCoord tc = decode_tile(a, g, lu);
+                const uint32_t act_bytes = (uint32_t)((g.BH + 2) * g.BW * C::ROWB);
+                const CUtensorMap* wmap = (tc.to == 0) ? &B.tm_w0 : &B.tm_w;
+                for (int kb = 0; kb < g.nkb && ok; ++kb) {
+                    const int tap = kb / g.cpt, cb = kb - tap * g.cpt;
+                    const int dw = tap % 3, dt = tap / 3;
+                    const CUtensorMap* src;
+                    const int tcoord = tap_frame(B, p, tc.n, tc.to * a.st + dt + a.t_off, &src);
+                    if (!mbar_wait(&empty[sa], pa ^ 1, status, wait_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&full[sa], act_bytes);
+                    tma_load_4d(smem + C::NW * C::W_SLOT + sa * B.act_slot, src, &full[sa], cb * KC,
+                                tc.tw * g.BW + dw - 1, tc.th * g.BH - 1, tcoord);
+                    last_a[sa] = (int)pa;
+                    if (++sa == na) {
+                        sa = 0;
+                        pa ^= 1;
+                    }
+                    for (int d = 0; d < 3; ++d) {
+                        if (!mbar_wait(&wempty[sw], pw ^ 1, status, wait_ns)) {
+                            ok = false;
+                            break;
+                        }
+                        mbar_arrive_expect_tx(&wfull[sw], w_bytes);
+                        tma_load_2d(smem + sw * C::W_SLOT, wmap, &wfull[sw], ((dt * 3 + d) * 3 + dw) * a.Cin + cb * KC,
+                                    tc.nt * BN);
+                        last_w[sw] = (int)pw;
+                        if (++sw == C::NW) {
+                            sw = 0;
+                            pw ^= 1;
+                        }
+                    }
+                }
+            }
+            // no copy may still be in flight when the CTA exits
+            for (int i = 0; i < na; ++i)
+                if (last_a[i] >= 0) mbar_wait(&full[i], (uint32_t)last_a[i], status, wait_ns);
+            for (int i = 0; i < C::NW; ++i)
+                if (last_w[i] >= 0) mbar_wait(&wfull[i], (uint32_t)last_w[i], status, wait_ns);
+        } else if (lane == 0) {
             // ------------------------------------------------ TMA producer
             int s = 0;
             uint32_t ph = 0;
@@ -324,21 +430,8 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                     const int dw = TR ? 0 : (HALO ? tap % 3 : tap % a.kw);
                     const int dh = HALO ? 0 : (tap / a.kw) % a.kh;
                     const int dt = TR ? tap : (HALO ? tap / 3 : tap / (a.kw * a.kh));
-                    const int ti = tc.to * a.st + dt + a.t_off;
-                    const CUtensorMap* src = &B.tm_x[p];
-                    int tcoord;
-                    if (ti >= a.Tin) {
-                        tcoord = -1;  // past the last frame (adjoint convs read ahead): zeros
-                    } else if (ti >= 0) {
-                        tcoord = tc.n * a.Tin + ti;
-                    } else if (a.hist) {
-                        src = &B.tm_h[p];
-                        tcoord = tc.n * a.hist_T + a.hist_T + ti;
-                    } else if (a.pad_mode == 0) {
-                        tcoord = tc.n * a.Tin;
-                    } else {
-                        tcoord = -1;  // whole box out of range -> zeros
-                    }
+                    const CUtensorMap* src;
+                    const int tcoord = tap_frame(B, p, tc.n, tc.to * a.st + dt + a.t_off, &src);
                     uint8_t* sa = smem + s * C::STAGE;
                     uint8_t* sb = sa + C::ACT_BYTES;
                     const CUtensorMap* wmap = (tc.to == 0) ? &B.tm_w0 : &B.tm_w;
@@ -390,7 +483,65 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                 if (last_ph[i] >= 0) mbar_wait(&full[i], (uint32_t)last_ph[i], status, wait_ns);
         }
     } else if (warp == 1) {
-        if (lane == 0) {
+        if (SPLIT && lane == 0) {
+            // ------------------------------------------------ MMA issuer, split rings
+            // per K block: wait for the box, then per dh tap for its weight slot, four
+            // MMAs (K = 16 each) reading the box from row dh * BW on, and release that
+            // weight slot; the box is released after the third tap
+            int sa = 0, sw = 0;
+            uint32_t pa = 0, pw = 0;
+            const int na = B.na;
+            int last_acc_ph[2] = {-1, -1};
+            bool ok = true;
+            int it = 0;
+            for (long long u = cid; u < B.num_units && ok; u += ncl, ++it) {
+                long long lu;
+                const TcGeo& gu = B.g[problem_of(B, u, &lu)];
+                const uint32_t row_step = (uint32_t)gu.BW * C::ROWB;
+                const uint32_t idesc = idesc_bf16_f32(BN, gu.nvox);
+                const int acc = it & 1;
+                const uint32_t aph = (uint32_t)((it >> 1) & 1);
+                if (!mbar_wait(&tempty[acc], aph ^ 1, status, wait_ns)) break;
+                tc_fence_after();
+                const uint32_t d = tmem_base + (uint32_t)(acc * C::ACC_COLS);
+                for (int kb = 0; kb < gu.nkb && ok; ++kb) {
+                    if (!mbar_wait(&full[sa], pa, status, wait_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t xa = smem_u32(smem + C::NW * C::W_SLOT + sa * B.act_slot);
+                    for (int dh = 0; dh < 3; ++dh) {
+                        if (!mbar_wait(&wfull[sw], pw, status, wait_ns)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t wa = smem_u32(smem + sw * C::W_SLOT);
+#pragma unroll
+                        for (int k = 0; k < KC / 16; ++k)
+                            tc_mma_bf16(d, kdesc<KC>(wa + k * 32), kdesc<KC>(xa + (uint32_t)dh * row_step + k * 32), idesc,
+                                        (kb | dh | k) != 0 ? 1u : 0u);
+                        tc_commit(&wempty[sw]);
+                        if (++sw == C::NW) {
+                            sw = 0;
+                            pw ^= 1;
+                        }
+                    }
+                    if (!ok) break;
+                    tc_commit(&empty[sa]);
+                    if (++sa == na) {
+                        sa = 0;
+                        pa ^= 1;
+                    }
+                }
+                tc_commit(&tfull[acc]);
+                last_acc_ph[acc] = (int)aph;
+            }
+            // wait for our own MMAs before TMEM can be released
+            for (int i = 0; i < 2; ++i)
+                if (last_acc_ph[i] >= 0) mbar_wait(&tfull[i], (uint32_t)last_acc_ph[i], status, wait_ns);
+        } else if (lane == 0) {
             // ------------------------------------------------ MMA issuer
             int s = 0;
             uint32_t ph = 0;
@@ -1099,10 +1250,10 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
     if (warp == 1) tmem_dealloc(tmem_base, C::TMEM_COLS);
 }
 
-template <int BN, bool SWAP, int MAXP, int HALO = 0, int TR = 0, int KC = 64>
+template <int BN, bool SWAP, int MAXP, int HALO = 0, int TR = 0, int KC = 64, bool SPLIT = false>
 int launch_bn(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int cta_tiles, cudaStream_t stream) {
-    using C = Cfg<BN, SWAP, HALO, TR, KC>;
-    auto kern = conv_tc_kernel<BN, SWAP, MAXP, HALO, TR, KC>;
+    using C = Cfg<BN, SWAP, HALO, TR, KC, SPLIT>;
+    auto kern = conv_tc_kernel<BN, SWAP, MAXP, HALO, TR, KC, SPLIT>;
     TcBatch<MAXP> B;
     memset(&B, 0, sizeof(B));
     // a narrow halo layer loads its real weight rows only
@@ -1145,6 +1296,14 @@ int launch_bn(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int c
     B.count = count;
     B.num_units = total;
     if (total == 0) return 0;
+    if constexpr (SPLIT) {
+        // activation slots: the launch's largest box, 1 KB aligned (swizzle atoms)
+        int box = 0;
+        for (int p = 0; p < count; ++p) box = std::max(box, (B.g[p].BH + 2) * B.g[p].BW * C::ROWB);
+        B.act_slot = (box + 1023) / 1024 * 1024;
+        B.na = std::min(4, C::SPLIT_ACT_BYTES / B.act_slot);
+        if (B.na < 2 || B.w_rows != BN) return -1;
+    }
     static bool attr_set = false;
     if (!attr_set) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) != cudaSuccess)
@@ -1158,10 +1317,10 @@ int launch_bn(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int c
     return (int)cudaGetLastError();
 }
 
-template <int BN, bool SWAP, int NCB, int TR = 0, int KC = 64>  // NCB: KC-channel blocks per halo stage
+template <int BN, bool SWAP, int NCB, int TR = 0, int KC = 64, bool SPLIT = false>  // NCB: KC-channel blocks per halo stage
 int launch_bn_halo(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int cta_tiles, cudaStream_t stream) {
-    return count == 1 ? launch_bn<BN, SWAP, 1, NCB, TR, KC>(as, gs, 1, num_sms, cta_tiles, stream)
-                      : launch_bn<BN, SWAP, kMaxConvGroup, NCB, TR, KC>(as, gs, count, num_sms, cta_tiles, stream);
+    return count == 1 ? launch_bn<BN, SWAP, 1, NCB, TR, KC, SPLIT>(as, gs, 1, num_sms, cta_tiles, stream)
+                      : launch_bn<BN, SWAP, kMaxConvGroup, NCB, TR, KC, SPLIT>(as, gs, count, num_sms, cta_tiles, stream);
 }
 
 template <int BN, bool SWAP>
@@ -1475,8 +1634,12 @@ int launch_conv_tc_group(const ConvArgs* as, int count, int num_sms, cudaStream_
     }
     if (tr == 9) return launch_bn_halo<128, true, 1, 9>(as, gs, count, num_sms, cta_tiles, stream);
     if (tr == 3) return launch_bn_halo<128, true, 1, 3>(as, gs, count, num_sms, cta_tiles, stream);
-    if constexpr (kHaloKC != 64)
-        if (halo && wide_halo) return launch_bn_halo<128, true, 1, 0, kHaloKC>(as, gs, count, num_sms, cta_tiles, stream);
+    if (halo && wide_halo) {
+        if constexpr (kHaloKC != 64)
+            return launch_bn_halo<128, true, 1, 0, kHaloKC>(as, gs, count, num_sms, cta_tiles, stream);
+        else
+            return launch_bn_halo<128, true, 1, 0, 64, kHaloSplit>(as, gs, count, num_sms, cta_tiles, stream);
+    }
     if (halo) return launch_bn_halo<128, true, 1>(as, gs, count, num_sms, cta_tiles, stream);
     if (swap) return launch_bn_any<128, true>(as, gs, count, num_sms, cta_tiles, stream);
     switch (conv_tc_bn(a0.Cout_pad)) {
