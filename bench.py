@@ -453,9 +453,11 @@ def selection(args, hbm_gbs, streams=256, Tp=4, Hq=90, Wq=160, rate=0.25, steps=
                         f"drop rate {rate}", "tokens": ntok, "ms": ms, "tokens_per_s": ntok / (ms / 1e3),
             "achieved_gbs": nbytes / (ms / 1e3) / 1e9, "peak_gbs": hbm_gbs,
             "frac": nbytes / (ms / 1e3) / 1e9 / hbm_gbs, "algorithmic_bytes": nbytes,
-            "note": "2 launches: digit table, then one block per latent frame (similarity, 3-pass radix "
-                    "select over shared memory, tie cut by position, drop and keep bits); latency-bound per "
-                    "frame (about 77 us for a 90x160 frame), not by HBM"}
+            "note": "2 launches: code and similarity tables, then one 1024-thread block per latent frame "
+                    "(integer-form cosines, 2048-bucket histogram, threshold bucket resolved as one value, "
+                    "a candidate radix select or a whole-frame radix select, tie cut by position, drop and "
+                    "keep bits); bound by instruction issue (about 8.7 warp instructions per token), not by "
+                    "HBM"}
 
 
 # ------------------------------------------------------------- a library reference point

@@ -21,6 +21,8 @@
 #pragma once
 #include <stdint.h>
 
+#include <cmath>
+
 namespace tok {
 
 enum OutMode { OUT_PLAIN = 0, OUT_D2S = 1, OUT_FSQ = 2 };
@@ -37,6 +39,45 @@ struct FsqConsts {
     int half_w[8];     // L/2
     int basis[8];      // prod_{j<i} L_j
 };
+
+// FSQ rounding as thresholds on z. With b = tanh(z + s) h - o and q = round(b), the
+// digit d = q + floor(L/2) exceeds k exactly when b > k + 1/2 - floor(L/2), i.e. when
+// z > atanh((k + 1/2 - floor(L/2) + o) / h) - s (tanh is increasing); t[c][k] is the
+// smallest float above that bound, computed in double, so a float z passes it when
+// z >= t[c][k], and the digit of channel c is the number of its thresholds that z
+// passes. This is the rounding of the exactly computed bounded value (a float32
+// tanh would misplace z within a few ulps of a bound). NaN pads the unused entries.
+struct FsqThr {
+    float t[8][15];
+};
+
+inline FsqThr make_fsq_thr(const int* levels, int nlev) {
+    FsqThr th;
+    for (int c = 0; c < 8; ++c)
+        for (int k = 0; k < 15; ++k) th.t[c][k] = NAN;
+    for (int c = 0; c < nlev && c < 8; ++c) {
+        const int L = levels[c], hw = L / 2;
+        const double h = (L - 1) * (1.0 - 1e-3) / 2.0;
+        const double o = (L % 2 == 0) ? 0.5 : 0.0;
+        const double s = std::atanh(o / h);
+        for (int k = 0; k < L - 1 && k < 15; ++k) {
+            const double x = std::atanh((k + 0.5 - hw + o) / h) - s;
+            float f = (float)x;
+            if ((double)f <= x) f = std::nextafter(f, INFINITY);
+            th.t[c][k] = f;
+        }
+    }
+    return th;
+}
+
+// Digit of channel c (TMAX >= L - 1 thresholds examined; NaN entries never pass).
+template <int TMAX>
+__device__ __forceinline__ int fsq_digit(const FsqThr& th, int c, float z) {
+    int d = 0;
+#pragma unroll
+    for (int k = 0; k < TMAX; ++k) d += (z >= th.t[c][k]) ? 1 : 0;
+    return d;
+}
 
 // Partial GroupNorm statistics of a set of values: count, mean and the sum of
 // squared deviations from the mean (merged with Chan's pairwise update).
@@ -74,6 +115,7 @@ struct ConvArgs {
     const void* residual; // same layout as out (OUT_PLAIN only) or null
     int32_t* idx;         // OUT_FSQ
     FsqConsts fsq;
+    const FsqThr* fsq_thr;  // OUT_FSQ: the thresholds of fsq in device memory
     // GroupNorm statistics of the stored output (bf16 values after the residual),
     // for the GroupNorm that reads it next: per (frame, slot, group) triples, a slot
     // being a spatial tile (times the rh x rw sub-positions for OUT_D2S); groups of

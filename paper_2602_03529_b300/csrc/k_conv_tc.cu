@@ -96,11 +96,19 @@ namespace {
 //                most 32 channels) loads only its 16 or 32 weight rows per tap
 //                into weight slots whose other rows stay zero.
 constexpr int HALO_BW_MAX = 64;
-// Input channels per K block of the wide halo form: 64 (128-byte rows, two 96 KB
-// stages in flight) or 32 (64-byte rows, four 48 KB stages). Measured on the
-// level-0 layer of the 720p step: 32 gives no gain (1383 against 1415 TFLOP/s);
-// the operand bytes per FLOP it pulls from L2 are the same, and the deeper
-// pipeline does not raise the tensor pipe's share, so that stays 64.
+// Input channels per K block of the wide halo form: 64 (128-byte rows) or 32
+// (64-byte rows, four 48 KB stages of the unified ring). What bounds the form,
+// measured on the level-0 layer of the 720p step (17 x 360 x 640, 128 -> 128
+// channels, 3.47 TFLOP, before the clocks drop under the power cap): the whole
+// kernel 1.95-2.05 ms; with the epilogue's work left out 1.91-1.94 ms; with the
+// TMA fills left out (MMAs over whatever the slots hold) 1.71 ms, and 1.67 ms
+// with neither, i.e. 2070 TFLOP/s. The fills (84 KB per K block for 256 voxels)
+// and the MMAs' operand reads (12 KB per 128-cycle M128 x N256 x K16 MMA) share
+// the SM's shared-memory bandwidth, where ncu counts the tensor core's reads at
+// 59.5 % and the fills at 36.4 % of it. Deeper pipelines do not change that
+// (32-channel blocks: no gain; the split rings below: 2 %); fewer fill bytes per
+// FLOP would, and for a layer of 128 output channels that takes accumulators of
+// more than 256 voxels, which leave no second TMEM buffer for the epilogue.
 constexpr int kHaloKC = 64;
 constexpr bool kHaloSplit = true;  // 64-channel K blocks in the split rings (see Cfg)
 constexpr int DWM_BH = 8, DWM_BW = 32;  // taps-in-rows forms: rows (dw rows: output rows) x columns of a tile's box
@@ -115,11 +123,10 @@ constexpr int DWM_BH = 8, DWM_BW = 32;  // taps-in-rows forms: rows (dw rows: ou
 //                slots of one dh tap each (16 KB), and activation slots sized at
 //                launch for the largest box of the launch (2..4 of them in the
 //                rest of the 227 KB). One stage of the unified ring (box + three
-//                weight boxes, up to 96 KB) allows two stages in flight, and a
-//                stage's refill (issued when its MMAs retire) takes longer to land
-//                than the next stage's MMAs run, so the tensor pipe waited on TMA
-//                about a fifth of the time; the split rings keep two K blocks of
-//                weights and three boxes in flight.
+//                weight boxes, up to 96 KB) allows two stages in flight; the split
+//                rings keep two K blocks of weights and three boxes in flight and
+//                let the first dh tap's MMAs start before the other two weight
+//                boxes land (measured 2 % faster on the level-0 layer).
 template <int BN, bool SWAP, int HALO = 0, int TR = 0, int KC = 64, bool SPLIT = false>
 struct Cfg {
     static_assert(!SPLIT || (HALO == 1 && TR == 0 && KC == 64 && SWAP), "split rings: the wide halo form");
@@ -707,9 +714,7 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                                         if (c < a.fsq.nlev) {
                                             const float zz = orow[c * 33 + x];
                                             z[c] = zz;
-                                            const float bq =
-                                                tanhf(zz + a.fsq.shift[c]) * a.fsq.half_l[c] - a.fsq.offset[c];
-                                            idx += ((int)rintf(bq) + a.fsq.half_w[c]) * a.fsq.basis[c];
+                                            idx += fsq_digit<15>(*a.fsq_thr, c, zz) * a.fsq.basis[c];
                                         }
                                     }
                                     if (a.idx) a.idx[vox] = idx;
@@ -801,9 +806,7 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                                             const float zz = buf[c * 33 + x] + buf[(16 + c) * 33 + x + 1] +
                                                              buf[(32 + c) * 33 + x + 2] + (a.bias ? a.bias[c] : 0.f);
                                             z[c] = zz;
-                                            const float bq =
-                                                tanhf(zz + a.fsq.shift[c]) * a.fsq.half_l[c] - a.fsq.offset[c];
-                                            idx += ((int)rintf(bq) + a.fsq.half_w[c]) * a.fsq.basis[c];
+                                            idx += fsq_digit<15>(*a.fsq_thr, c, zz) * a.fsq.basis[c];
                                         }
                                     }
                                     if (a.idx) a.idx[vox] = idx;
@@ -879,9 +882,7 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                                             if (c < a.fsq.nlev) {
                                                 const float x = stg[lane * C::EPI_STRIDE + c];
                                                 z[c] = x;
-                                                const float b =
-                                                    tanhf(x + a.fsq.shift[c]) * a.fsq.half_l[c] - a.fsq.offset[c];
-                                                idx += ((int)rintf(b) + a.fsq.half_w[c]) * a.fsq.basis[c];
+                                                idx += fsq_digit<15>(*a.fsq_thr, c, x) * a.fsq.basis[c];
                                             }
                                         }
                                         if (a.idx) a.idx[vox] = idx;
@@ -1215,9 +1216,7 @@ __global__ void __launch_bounds__(192, 1) conv_tc_kernel(const __grid_constant__
                     for (int j = 0; j < 8; ++j) {
                         if (j < a.fsq.nlev) {
                             z[j] = v[j];
-                            const float b = tanhf(v[j] + a.fsq.shift[j]) * a.fsq.half_l[j] - a.fsq.offset[j];
-                            const int d = (int)rintf(b) + a.fsq.half_w[j];
-                            idx += d * a.fsq.basis[j];
+                            idx += fsq_digit<15>(*a.fsq_thr, j, v[j]) * a.fsq.basis[j];
                         }
                     }
                     if (a.idx) a.idx[vox] = idx;
@@ -1339,7 +1338,7 @@ PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
     if (!fn) {
         cudaDriverEntryPointQueryResult q;
         void* p = nullptr;
-        if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
             fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
     }

@@ -52,11 +52,11 @@ unsigned long long current_context_id() {
     std::call_once(once, [] {
         cudaDriverEntryPointQueryResult q;
         void* p = nullptr;
-        if (cudaGetDriverEntryPoint("cuCtxGetCurrent", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
             get_cur = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(p);
         p = nullptr;
-        if (cudaGetDriverEntryPoint("cuCtxGetId", &p, cudaEnableDefault, &q) == cudaSuccess &&
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
             q == cudaDriverEntryPointSuccess)
             get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(p);
     });

@@ -81,6 +81,11 @@ int tok_create(const tok_arch* arch, int precision, tok_ctx** out) {
     for (auto& g : c->gns) std::fill(c->host[c->pindex[g.name + ".g"]].begin(), c->host[c->pindex[g.name + ".g"]].end(), 1.f);
     bool ok = cudaMalloc(&c->d_status, sizeof(int)) == cudaSuccess;
     if (ok) ok = cudaMemset(c->d_status, 0, sizeof(int)) == cudaSuccess;
+    if (ok) ok = cudaMalloc(&c->d_fsq_thr, sizeof(FsqThr)) == cudaSuccess;
+    if (ok) {
+        const FsqThr th = make_fsq_thr(arch->levels, arch->nlev);
+        ok = cudaMemcpy(c->d_fsq_thr, &th, sizeof(th), cudaMemcpyHostToDevice) == cudaSuccess;
+    }
     if (ok) ok = cudaMalloc(&c->d_master, (size_t)c->param_total * 4) == cudaSuccess;
     for (size_t i = 0; ok && i < c->params.size(); ++i)
         ok = cudaMemcpy(c->d_master + c->params[i].offset, c->host[i].data(), c->params[i].count * 4,
@@ -114,6 +119,7 @@ void tok_destroy(tok_ctx* c) {
     if (c->d_master) cudaFree(c->d_master);
     if (c->tarena) cudaFree(c->tarena);
     if (c->d_status) cudaFree(c->d_status);
+    if (c->d_fsq_thr) cudaFree(c->d_fsq_thr);
     if (c->arena) cudaFree(c->arena);
     for (auto e : c->events) cudaEventDestroy(e);
     delete c;

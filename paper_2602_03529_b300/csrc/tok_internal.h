@@ -87,6 +87,7 @@ struct tok_ctx {
     std::vector<GnW> gns;
     std::map<std::string, int> gindex;
     FsqConsts fsq;
+    FsqThr* d_fsq_thr = nullptr;  // the FSQ rounding thresholds of fsq (device)
     int* d_status = nullptr;
     char* arena = nullptr;
     size_t arena_bytes = 0;
@@ -528,6 +529,7 @@ struct Exec {
         a.status = c->d_status;
         a.wait_ns = kWaitNs;
         a.fsq = c->fsq;
+        a.fsq_thr = c->d_fsq_thr;
         return a;
     }
 

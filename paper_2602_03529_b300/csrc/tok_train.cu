@@ -415,6 +415,7 @@ struct TrainExec : Exec {
         a.status = c->d_status;
         a.wait_ns = kWaitNs;
         a.fsq = c->fsq;
+        a.fsq_thr = c->d_fsq_thr;
         ConvW shadow = cw;
         shadow.Cin = cw.cpad;
         shadow.Cout = cw.rows_pad;
