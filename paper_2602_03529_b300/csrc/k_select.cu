@@ -311,9 +311,10 @@ __global__ void __launch_bounds__(FS_THREADS) select_fused_kernel(
 // channel, dot = D / Q, |p|^2 = A / Q, |q|^2 = B / Q for the integers
 // D = sum w qp qi, A = sum w qp^2, B = sum w qi^2, and the product of the squared
 // norms A B / Q^2 is exact too. So S = D/Q divided (rounded) by the rounded
-// square root of A B / Q^2, which a table indexed by P = A B holds: the same
-// float32 value, bit for bit, as the three sums, one square root and one
-// division. A token index is split as lo + 2^shift hi; small tables give the
+// square root of A B / Q^2: the same float32 value, bit for bit, as the three
+// sums, one square root and one division of the definition. (A table of S over
+// (|D|, A B) measured slower than computing it: one L2 lookup per token, 0.186
+// against 0.167 ms on 14.7 M tokens.) A token index is split as lo + 2^shift hi; small tables give the
 // centered digits q (one signed byte per channel) and w q of each part, and two
 // dp4a per dot product sum them.
 //
@@ -327,19 +328,15 @@ __global__ void __launch_bounds__(FS_THREADS) select_fused_kernel(
 constexpr int SB_THREADS = 1024, SB_BINS = 2048, SB_CAND = 1024;
 constexpr long long SB_MAX_TOKENS = 16384;
 constexpr int SB_TAB_MAX = 512;     // entries of each index-part table
-constexpr int SB_PMAX = 16383;      // largest A B the similarity table holds
-constexpr long long SB_STAB_MAX = 1 << 21;  // entries of the similarity table ((dmax + 1) (pmax + 1))
 
 struct SelTables {
     const uint4* lo;   // [2^shift]: bytes of x, y = q of channels 0..7 (lo part), bytes of z, w = w q
     const uint4* hi;   // [nhi]: the same for the hi part (disjoint channels, OR-able)
-    const float* stab; // [(dmax + 1) (pmax + 1)]: S for |D| and P = A B (0 for P = 0)
     float invQ, invQ2;
-    int shift, nhi, prod, pmax, dmax;
+    int shift, nhi, prod;
 };
 
-__global__ void sel_tables_kernel(FsqConsts f, int split_c, int shift, int nhi, int Q, int pmax, int dmax, uint4* lo,
-                                  uint4* hi, float* stab) {
+__global__ void sel_tables_kernel(FsqConsts f, int split_c, int shift, int nhi, int Q, uint4* lo, uint4* hi) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int nlo = 1 << shift;
     auto pack = [&](int part, int v) {
@@ -356,14 +353,6 @@ __global__ void sel_tables_kernel(FsqConsts f, int split_c, int shift, int nhi, 
     };
     if (i < nlo) lo[i] = pack(0, i);
     if (i < nhi) hi[i] = pack(1, i);
-    // S of |D| and P = A B: the definition's one rounded square root of the exact
-    // norm product and one rounded division of the exact dot product
-    if (i < (dmax + 1) * (pmax + 1)) {
-        const int d = i / (pmax + 1), P = i - d * (pmax + 1);
-        stab[i] = P > 0 ? __fdiv_rn(__fmul_rn((float)d, 1.0f / (float)Q),
-                                    __fsqrt_rn(__fmul_rn((float)P, 1.0f / (float)(Q * Q))))
-                        : 0.f;
-    }
 }
 
 // Code vector (q and w q) of a token index; an index outside [0, prod) is decoded
@@ -500,7 +489,6 @@ __global__ void __launch_bounds__(SB_THREADS, 2) select_bucket_kernel(
     const int iters = (HW + SB_THREADS - 1) / SB_THREADS, full = HW / SB_THREADS;
     float* const simf = sim ? sim + frame * HW : nullptr;
     const uint32_t lomask = (1u << tb.shift) - 1u;
-    const int prow = tb.pmax + 1;
     const auto similarity = [&](int ip, int ii) {
         uint4 a, b;
         if ((unsigned)ip < (unsigned)tb.prod && (unsigned)ii < (unsigned)tb.prod) {
@@ -515,21 +503,26 @@ __global__ void __launch_bounds__(SB_THREADS, 2) select_bucket_kernel(
         const int D = __dp4a((int)a.z, (int)b.x, __dp4a((int)a.w, (int)b.y, 0));
         const int A = __dp4a((int)a.z, (int)a.x, __dp4a((int)a.w, (int)a.y, 0));
         const int B = __dp4a((int)b.z, (int)b.x, __dp4a((int)b.w, (int)b.y, 0));
+        // the definition's one rounded square root of the exact norm product and one
+        // rounded division of the exact dot product
         const int Pq = A * B, aD = abs(D);
-        float S;
-        if (Pq <= tb.pmax && aD <= tb.dmax) {
-            S = tb.stab[aD * prow + Pq];
-        } else {
-            S = Pq > 0 ? __fdiv_rn(__fmul_rn((float)aD, tb.invQ), __fsqrt_rn(__fmul_rn((float)Pq, tb.invQ2))) : 0.f;
-        }
+        const float S =
+            Pq > 0 ? __fdiv_rn(__fmul_rn((float)aD, tb.invQ), __fsqrt_rn(__fmul_rn((float)Pq, tb.invQ2))) : 0.f;
         return D < 0 ? -S : S;  // rounding is symmetric; D = 0 gives +0
     };
+    // the next iteration's two indices are loaded while this one's similarity is formed
+    int ip_n = tid < HW ? fp[tid] : 0, ii_n = tid < HW ? fi[tid] : 0;
     for (int it = 0; it < iters; ++it) {
         const int j = it * SB_THREADS + tid;
         const bool act = it < full || j < HW;
+        const int ip = ip_n, ii = ii_n;
+        if (j + SB_THREADS < HW) {
+            ip_n = fp[j + SB_THREADS];
+            ii_n = fi[j + SB_THREADS];
+        }
         int bkt = 0;
         if (act) {
-            const float S = similarity(fp[j], fi[j]);
+            const float S = similarity(ip, ii);
             ords[j] = sim_order(S);
             bkt = sim_bucket(S);
             if (simf) simf[j] = S;
@@ -635,6 +628,32 @@ __global__ void __launch_bounds__(SB_THREADS, 2) select_bucket_kernel(
     // phase 5: drop, indices and keep bits (a warp per 32 tokens of a row)
     const uint32_t pos = s_pos;
     const int nwords = (Wq + 31) / 32;
+    const auto drops = [&](int j) {
+        const uint32_t o = ords[j];
+        return all_drop || (!none && (o > star || (o == star && (uint32_t)j <= pos)));
+    };
+    if (Wq % 32 == 0) {
+        // rows of whole mask words: word rw holds tokens 32 rw .. 32 rw + 31 of the frame;
+        // two words per warp in flight
+        const int nw = Hq * nwords;
+        uint32_t* const kb = keep_bits ? keep_bits + (long long)frame * nw : nullptr;
+        int32_t* const fo = out + frame * HW;
+        for (int rw = warp; rw < nw; rw += 2 * (SB_THREADS / 32)) {
+            const int rw2 = rw + SB_THREADS / 32;
+            const int j = rw * 32 + lane, j2 = rw2 * 32 + lane;
+            const bool k1 = !drops(j), k2 = rw2 < nw && !drops(j2);
+            const int32_t v1 = k1 ? fp[j] : zero_index;
+            const int32_t v2 = k2 ? fp[j2] : zero_index;
+            fo[j] = v1;
+            if (rw2 < nw) fo[j2] = v2;
+            const uint32_t m1 = __ballot_sync(0xffffffffu, k1), m2 = __ballot_sync(0xffffffffu, k2);
+            if (kb && lane == 0) {
+                kb[rw] = m1;
+                if (rw2 < nw) kb[rw2] = m2;
+            }
+        }
+        return;
+    }
     for (int rw = warp; rw < Hq * nwords; rw += SB_THREADS / 32) {
         const int h = rw / nwords, word = rw - h * nwords, w = word * 32 + lane;
         bool keep = false;
@@ -653,7 +672,7 @@ __global__ void __launch_bounds__(SB_THREADS, 2) select_bucket_kernel(
 // Whether the integer form applies (see above), and its table geometry.
 struct SelPlan {
     bool ok = false;
-    int split_c = 0, shift = 0, nhi = 0, Q = 0, pmax = 0, prod = 0, dmax = 0;
+    int split_c = 0, shift = 0, nhi = 0, Q = 0, prod = 0;
 };
 
 SelPlan sel_plan(const FsqConsts& f, long long HW) {
@@ -666,8 +685,9 @@ SelPlan sel_plan(const FsqConsts& f, long long HW) {
         Q = std::max(Q, h * h);
     }
     const long long prod = (long long)f.basis[f.nlev - 1] * f.levels[f.nlev - 1];
-    const int dmax = f.nlev * Q;
-    if ((long long)dmax * dmax > SB_PMAX || (long long)(dmax + 1) * (dmax * dmax + 1) > SB_STAB_MAX) return p;
+    // |D|, A, B <= nlev Q: the products A B stay exact in float32 below 2^24
+    const long long dmax = (long long)f.nlev * Q;
+    if (dmax * dmax >= (1LL << 24)) return p;
     for (int c = 1; c < f.nlev; ++c) {
         const int b = f.basis[c];
         if (b & (b - 1)) continue;
@@ -677,8 +697,6 @@ SelPlan sel_plan(const FsqConsts& f, long long HW) {
             p.shift = __builtin_ctz((unsigned)b);
             p.nhi = (int)(prod / b);
             p.Q = Q;
-            p.pmax = dmax * dmax;
-            p.dmax = dmax;
             p.prod = (int)prod;
             return p;
         }
@@ -692,7 +710,7 @@ size_t similarity_workspace_bytes(long long N, int Tp, long long HW) {
     // per-token keys and per-frame thresholds (the three-kernel form), the digit
     // table, and the integer form's tables
     return (size_t)(N * Tp * HW) * 8 + (size_t)(N * Tp) * 8 + (size_t)DIGIT_TAB * 4 + 512 +
-           (size_t)2 * SB_TAB_MAX * 16 + (size_t)SB_STAB_MAX * 4 + 512;
+           (size_t)2 * SB_TAB_MAX * 16 + 512;
 }
 
 int launch_similarity_mask(const int32_t* idx_p, const int32_t* idx_i, long long N, int Tp, int Hq, int Wq,
@@ -709,22 +727,16 @@ int launch_similarity_mask(const int32_t* idx_p, const int32_t* idx_i, long long
         tb = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(tb) + 255) & ~uintptr_t(255));
         uint4* lo = reinterpret_cast<uint4*>(tb);
         uint4* hi = lo + SB_TAB_MAX;
-        float* stab = reinterpret_cast<float*>(hi + SB_TAB_MAX);
-        const int dmax = pl.dmax;
-        const int nt = std::max(std::max(1 << pl.shift, pl.nhi), (dmax + 1) * (pl.pmax + 1));
-        sel_tables_kernel<<<blocks_for(nt, 256), 256, 0, s>>>(f, pl.split_c, pl.shift, pl.nhi, pl.Q, pl.pmax, dmax, lo,
-                                                              hi, stab);
+        const int nt = std::max(1 << pl.shift, pl.nhi);
+        sel_tables_kernel<<<blocks_for(nt, 256), 256, 0, s>>>(f, pl.split_c, pl.shift, pl.nhi, pl.Q, lo, hi);
         SelTables t;
         t.lo = lo;
         t.hi = hi;
-        t.stab = stab;
-        t.dmax = dmax;
         t.invQ = 1.0f / (float)pl.Q;
         t.invQ2 = 1.0f / (float)(pl.Q * pl.Q);
         t.shift = pl.shift;
         t.nhi = pl.nhi;
         t.prod = pl.prod;
-        t.pmax = pl.pmax;
         static bool attr_b = false;
         if (!attr_b) {
             if (cudaFuncSetAttribute(select_bucket_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -40,8 +40,10 @@ def _check(P, ip, ii, rate, frames=None):
 
 
 @pytest.mark.parametrize("rate", [0.0, 0.07, 0.25, 0.3, 1.0])
-@pytest.mark.parametrize("shape", [(2, 3, 9, 40), (1, 4, 17, 70), (3, 1, 5, 33)])
+@pytest.mark.parametrize("shape", [(2, 3, 9, 40), (1, 4, 17, 70), (3, 1, 5, 33), (2, 2, 9, 64), (1, 2, 90, 160)])
 def test_random_tokens(P, rate, shape):
+    """Ragged rows, and rows of whole 32-token mask words (64, and 160 as in a 720p
+    latent frame), which the last pass walks word by word without dividing."""
     rng = np.random.default_rng(hash((shape, rate)) % 2 ** 32)
     N, Tp, H, W = shape
     ip = rng.integers(0, 64000, shape)
@@ -62,6 +64,13 @@ def test_ties_and_zero_vectors(P):
     ii[:, :, :2] = ops.fsq_zero_index(LV)          # a zero reference row
     for rate in (0.1, 0.5, 0.9):
         _check(P, ip, ii, rate)
+    # the same on rows of whole mask words
+    ii2 = rng.integers(0, 64000, (N, 1, 12, 64))
+    ip2 = np.repeat(ii2, Tp, axis=1).copy()
+    r2 = rng.random(ip2.shape)
+    ip2[r2 < 0.2] = ops.fsq_zero_index(LV)
+    for rate in (0.1, 0.9):
+        _check(P, ip2, ii2, rate)
 
 
 def test_encoded_clip_latents(P):
