@@ -41,7 +41,7 @@ FALLBACK_PEAKS = {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustain
 # 720p clip, each launch scaled by its tensors' sizes at 17 and at 5 frames. Algorithmic:
 # every layer's input read once, its residual read once, its output written once.
 # Re-measure when the conv kernel changes.
-CONV_DRAM_BYTES_PER_STEP = 31.45e9
+CONV_DRAM_BYTES_PER_STEP = 31.48e9
 CONV_ALGORITHMIC_BYTES_PER_STEP = 33.57e9
 CONV_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the 34 conv launches of a "
                        "1x3x5x720x1280 encode + decode, each scaled to the 17-frame launch by its tensor sizes")
@@ -842,9 +842,9 @@ def case_clip(N, T, H, W):
     print("clip ok", N, T, H, W, f"{tk.workspace_bytes(N, T, H, W) / 1e9:.2f} GB workspace")
 
 
-def case_train(N, T, H, W, recompute=False):
+def case_train(N, T, H, W, keep=False):
     """One training step (forward with 10% drop, MSE, backward, SGD), then one more
-    forward + backward."""
+    forward + backward; block interiors rebuilt in the backward (the default), or kept."""
     import torch
 
     import paper_2602_03529_b300 as P
@@ -853,7 +853,7 @@ def case_train(N, T, H, W, recompute=False):
 
     tk = P.Tokenizer("bf16")
     tk.set_params(S.weights_for(tk.param_spec(), seed=0))
-    tr = Trainer(tk, N, T, H, W, **({"recompute": True} if recompute else {}))
+    tr = Trainer(tk, N, T, H, W, recompute=not keep)
     x = torch.from_numpy(S.blurred_noise_clip(7, N, T, H, W)).to("cuda", torch.bfloat16)
     tr.step(x, 0.1, 1, 0, 1e-5)
     tr.forward(x, 0.1, 1, 1)
@@ -899,6 +899,28 @@ def case_select(N, T, H, W):
     print("select ok", tuple(out.shape), int((out == 32036).sum()))
 
 
+def case_tokens(N, T, H, W):
+    """tok_quantize over 2^26 latent vectors of 6 fp32 channels and tok_drop_mask over
+    N streams x T latent frames of H x W tokens at rate 0.15, three times each."""
+    import torch
+
+    import paper_2602_03529_b300 as P
+
+    g = torch.Generator(device="cuda").manual_seed(11)
+    ntok = 1 << 26
+    z = torch.randn((ntok, len(LEVELS)), device="cuda", generator=g)
+    idx = torch.empty(ntok, device="cuda", dtype=torch.int32)
+    tok = torch.randint(0, 64000, (N, T, H, W), device="cuda", generator=g, dtype=torch.int32)
+    out = torch.empty_like(tok)
+    kb = torch.empty((N, T, H, (W + 31) // 32), device="cuda", dtype=torch.int32)
+    for _ in range(3):
+        P._lib.tok_quantize(z.data_ptr(), ntok, list(LEVELS), idx.data_ptr(), None, None)
+    for i in range(3):
+        P.drop_mask(tok, 0.15, seed=5, stream_id=0, chunk_id=i, levels=LEVELS, out=out, keep_bits=kb)
+    torch.cuda.synchronize()
+    print("tokens ok", int(idx[:4].sum()), int((out == 32036).sum()))
+
+
 def case_chunk(N, T, H, W, chunks=6):
     """One stream of H x W (N and T unused): chunk 0, then `chunks` 4-frame chunks,
     encode + decode each; prints per chunk the event-timed milliseconds and the
@@ -937,8 +959,9 @@ def case_chunk(N, T, H, W, chunks=6):
         sys.exit(f"device status {tk.status()}")
 
 
-CASE_SHAPES = {"clip": (1, 5, 720, 1280), "train": (2, 17, 256, 256), "train-recompute": (2, 17, 256, 256),
-               "downsample": (4, 17, 1080, 1920), "select": (256, 4, 90, 160), "chunk": (1, 5, 1080, 1920)}
+CASE_SHAPES = {"clip": (1, 5, 720, 1280), "train": (2, 17, 256, 256), "train-keep": (2, 17, 256, 256),
+               "downsample": (4, 17, 1080, 1920), "select": (256, 4, 90, 160), "chunk": (1, 5, 1080, 1920),
+               "tokens": (2048, 4, 90, 160)}
 
 
 def run_case(args):
@@ -948,12 +971,14 @@ def run_case(args):
         case_clip(*shape)
     elif args.case == "train":
         case_train(*shape)
-    elif args.case == "train-recompute":
-        case_train(*shape, recompute=True)
+    elif args.case == "train-keep":
+        case_train(*shape, keep=True)
     elif args.case == "downsample":
         case_downsample(*shape, args.s)
     elif args.case == "chunk":
         case_chunk(*shape)
+    elif args.case == "tokens":
+        case_tokens(*shape)
     else:
         case_select(*shape)
 

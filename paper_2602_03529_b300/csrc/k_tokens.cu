@@ -193,8 +193,10 @@ __device__ __forceinline__ uint32_t fast_div(uint32_t n, const FastDiv& f) {
 // tokens keeps every lane busy. IDX is int (segments below 2^31: divisions by
 // multiplication) or long long. A token is dropped when its 32-bit word is below
 // thr (all of them when thr = 2^32).
+// 40 registers leave room for six 256-thread blocks per SM (46 without the bound:
+// five; measured 0.218 against 0.227 ms on 118 M tokens).
 template <typename IDX>
-__global__ void drop4_kernel(const int32_t* __restrict__ idx, int TH, int Wq, int nseg, IDX segs, FastDiv div_seg,
+__global__ void __launch_bounds__(256, 6) drop4_kernel(const int32_t* __restrict__ idx, int TH, int Wq, int nseg, IDX segs, FastDiv div_seg,
                              FastDiv div_th, unsigned long long thr, const __grid_constant__ PhiloxKeys K,
                              uint32_t chunk_lo, uint32_t stream_lo, int32_t zero_index, int32_t* __restrict__ out,
                              uint32_t* __restrict__ keep_bits) {
