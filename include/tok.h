@@ -184,7 +184,11 @@ int tok_decode_batch(tok_ctx* ctx, const tok_dec_item* h_items, int count, void*
 /* Stand-alone FSQ (Mentzer et al. 2023): per token of nlev channels,
  * b = tanh(z + atanh(o/h))*h - o with h = (L-1)(1-1e-3)/2, o = 0.5 for even
  * L else 0; q = round-half-even(b); idx = sum (q + L/2) * prod_{j<i} L_j;
- * codes = q / floor(L/2). FP32 arithmetic.
+ * codes = q / floor(L/2) (FP32). The rounding of b is taken exactly for the
+ * float32 z: per channel the L-1 bounds in z where q steps (tanh is
+ * increasing) are precomputed in double, and q + L/2 is the number of them z
+ * passes; no tanh is evaluated. 16-byte aligned d_z and d_idx (and d_codes)
+ * take a vectorised form; any alignment is accepted.
  * d_z (ntok, nlev) fp32; h_levels host array of nlev levels (<= 8);
  * d_idx (ntok) int32; d_codes (ntok, nlev) fp32 or NULL. */
 int tok_quantize(const float* d_z, int64_t ntok, const int* h_levels, int nlev,

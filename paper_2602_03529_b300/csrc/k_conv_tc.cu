@@ -14,13 +14,15 @@
 //
 // Warp roles (192 threads):
 //   warp 0      TMA producer (one lane): activation and weight boxes into a
-//               STAGES-deep ring of 128B-swizzled shared-memory tiles.
+//               ring of 128B-swizzled shared-memory stages, or (the wide halo
+//               form) into separate rings of activation and weight slots.
 //   warp 1      TMEM allocation and MMA issue (one lane): tcgen05.mma.kind::f16
 //               (K = 16 each) per stage into one of two FP32 accumulators in
-//               TMEM; tcgen05.commit frees the stage.
+//               TMEM; tcgen05.commit frees the stage (or slot).
 //   warps 2..5  epilogue: tcgen05.ld the accumulator (each warp its 32 TMEM
 //               lanes), add bias and residual, round to BF16 and store; or
-//               scatter through depth-to-space; or FSQ-quantise; and reduce
+//               scatter through depth-to-space; or FSQ-quantise (rounding
+//               thresholds on z); and reduce
 //               the GroupNorm statistics of the stored values.
 // The epilogue of tile i overlaps the MMAs of tile i+1 (double-buffered TMEM).
 #include <cudaTypedefs.h>

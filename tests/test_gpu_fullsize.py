@@ -323,8 +323,8 @@ LEVELS = (8, 8, 8, 5, 5, 5)
 def test_network_latent_head_fsq_indices(traced):
     """The FSQ epilogue of the latent head at 720p (5 x 90 x 160 tokens): the oracle's FSQ
     of the GPU's own z gives the GPU's index at every token outside 2^-16 of a rounding
-    tie (the epilogue rounds float32 bounded values), and the mismatches inside that
-    band stay under 1e-4 of the tokens."""
+    tie (the epilogue takes the rounding of the exact bounded value, by thresholds on
+    z), and the mismatches inside that band stay under 1e-4 of the tokens."""
     z = traced["z"].double().cpu().numpy()
     idx = traced["idx"].cpu().numpy()
     ref, _, bnd = ops.fsq_quantize(z, LEVELS)
