@@ -481,23 +481,35 @@ def cudnn_reference(peak_tflops, steps=10, warmup=3):
     xt = x.permute(0, 4, 1, 2, 3).contiguous(memory_format=torch.channels_last_3d)
     wt = w.permute(0, 4, 1, 2, 3).to(torch.bfloat16).contiguous(memory_format=torch.channels_last_3d)
 
-    def timed(fn):
-        for _ in range(warmup):
+    def timed(fn, reps=steps):
+        for _ in range(min(warmup, reps)):
             fn()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
-        for _ in range(steps):
+        for _ in range(reps):
             fn()
         e1.record()
         torch.cuda.synchronize()
-        return e0.elapsed_time(e1) / steps
+        return e0.elapsed_time(e1) / reps
 
     ms_cudnn = timed(lambda: F.conv3d(xt, wt, padding=1))
     ms_ours = timed(lambda: P.conv3d(x, w, b, (1, 1, 1), "replicate"))
+    # plain FP32 on the CUDA cores on both sides (no TF32): cuDNN against this library's FP32 path
+    x32, xt32, wt32 = x.float(), xt.float(), wt.float()
+    tf32 = torch.backends.cudnn.allow_tf32
+    torch.backends.cudnn.allow_tf32 = False
+    try:
+        ms_cudnn32 = timed(lambda: F.conv3d(xt32, wt32, padding=1), reps=3)
+    finally:
+        torch.backends.cudnn.allow_tf32 = tf32
+    ms_ours32 = timed(lambda: P.conv3d(x32, w, b, (1, 1, 1), "replicate"), reps=3)
     return {"workload": "level-0 conv of the 720p step: 1x17x360x640, 128 -> 128 channels, 3x3x3, BF16",
             "tflop": flop / 1e12, "cudnn_ms": ms_cudnn, "cudnn_tflops": flop / (ms_cudnn / 1e3) / 1e12,
             "ours_ms": ms_ours, "ours_tflops": flop / (ms_ours / 1e3) / 1e12, "peak_tflops": peak_tflops,
+            "fp32": {"cudnn_ms": ms_cudnn32, "cudnn_tflops": flop / (ms_cudnn32 / 1e3) / 1e12, "ours_ms": ms_ours32,
+                     "ours_tflops": flop / (ms_ours32 / 1e3) / 1e12,
+                     "note": "plain FP32 (cuDNN with TF32 off; ours: the CUDA-core FP32 path)"},
             "note": "torch.nn.functional.conv3d (cuDNN), channels_last_3d, symmetric zero padding; ours: tok_conv3d "
                     "(weight packing included in every call)"}
 
