@@ -394,7 +394,12 @@ int tok_groupnorm_silu(int precision, const void* d_x, int64_t frames, int64_t H
  * Parameters as one flat FP32 vector in the order of tok_param_info
  * (tok_param_total floats). tok_get_params copies the context's parameters
  * out, tok_set_params_device loads them from device memory (both enqueued on
- * `stream`). tok_train_forward runs encode -> drop (Bernoulli(drop_rate),
+ * `stream`). tok_params returns the device address of the context's own flat
+ * vector (owned by the context, valid until tok_destroy): a caller may update
+ * it in place (e.g. tok_sgd on it) and then call tok_repack, which rebuilds the
+ * layouts the kernels read from it (the BF16 forward rows and, once a backward
+ * has run, both adjoint layouts; every 3x3x3 conv's three layouts in one
+ * launch); tok_set_params_device given that address skips the copy. tok_train_forward runs encode -> drop (Bernoulli(drop_rate),
  * Philox key seed, counter step) -> decode, writes x_hat (N,T,H,W,3) fp32, the
  * loss (one fp32 on the device) and dL/dx_hat (N,T,H,W,3) fp32, and keeps what
  * the backward needs; d_x must stay valid until tok_backward. A non-NULL
@@ -409,6 +414,8 @@ int tok_set_train_mode(tok_ctx* ctx, int mode);
 int64_t tok_param_total(const tok_ctx* ctx);
 int tok_get_params(tok_ctx* ctx, float* d_flat, void* stream);
 int tok_set_params_device(tok_ctx* ctx, const float* d_flat, void* stream);
+float* tok_params(tok_ctx* ctx);
+int tok_repack(tok_ctx* ctx, void* stream);
 size_t tok_train_workspace_bytes(const tok_ctx* ctx, int N, int T, int H, int W);
 int tok_reserve_train(tok_ctx* ctx, int N, int T, int H, int W);
 int tok_train_forward(tok_ctx* ctx, const void* d_x, int N, int T, int H, int W, float drop_rate,

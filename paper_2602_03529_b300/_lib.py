@@ -122,6 +122,8 @@ _SIGS = {
     "tok_param_total": (i64, [vp]),
     "tok_get_params": (i32, [vp, vp, vp]),
     "tok_set_params_device": (i32, [vp, vp, vp]),
+    "tok_params": (vp, [vp]),
+    "tok_repack": (i32, [vp, vp]),
     "tok_train_workspace_bytes": (sz, [vp, i32, i32, i32, i32]),
     "tok_reserve_train": (i32, [vp, i32, i32, i32, i32]),
     "tok_train_forward": (i32, [vp, vp, i32, i32, i32, i32, f32, u64, u64, vp, vp, vp, vp, vp]),
@@ -442,6 +444,15 @@ def tok_get_params(ctx, d_flat, cuda_stream) -> None:
 
 def tok_set_params_device(ctx, d_flat, cuda_stream) -> None:
     _ck(_call("tok_set_params_device", ctx, d_flat, cuda_stream), "tok_set_params_device")
+
+
+def tok_params(ctx) -> int:
+    """Device address of the context's flat FP32 parameters (owned by the context)."""
+    return _call("tok_params", ctx)
+
+
+def tok_repack(ctx, cuda_stream) -> None:
+    _ck(_call("tok_repack", ctx, cuda_stream), "tok_repack")
 
 
 def tok_train_workspace_bytes(ctx, N, T, H, W) -> int:

@@ -19,6 +19,7 @@
 // All are bandwidth-bound except wgrad (CUDA-core FP32 FMA).
 #include "common.cuh"
 #include "conv_args.h"
+#include "launchers.h"
 
 #include <algorithm>
 #include <type_traits>
@@ -761,12 +762,12 @@ __global__ void __launch_bounds__(256) pack_adjoint_kernel(const float* __restri
 // wf0[ci][tap'][co] (sum of W over dt <= 2 - dt'). A block takes 32 output x
 // 32 input channels of one spatial tap (dh, dw) for all three dt; the two
 // adjoint layouts go through a shared-memory transpose.
-__global__ void __launch_bounds__(256) pack3_kernel(const float* __restrict__ w, int Cout, int Cin, int Cout_pad,
-                                                    int Kpad, int rows_pad, int cpad, __nv_bfloat16* __restrict__ fwd,
-                                                    __nv_bfloat16* __restrict__ wt, __nv_bfloat16* __restrict__ wf0) {
-    __shared__ float tile[3][32][33];
-    const int hw = blockIdx.z, dh = hw / 3, dw = hw % 3;
-    const int co0 = blockIdx.x * 32, ci0 = blockIdx.y * 32;
+__device__ __forceinline__ void pack3_tile(const float* __restrict__ w, int Cout, int Cin, int Cout_pad, int Kpad,
+                                           int rows_pad, int cpad, __nv_bfloat16* __restrict__ fwd,
+                                           __nv_bfloat16* __restrict__ wt, __nv_bfloat16* __restrict__ wf0, int bx,
+                                           int by, int hw, float (&tile)[3][32][33]) {
+    const int dh = hw / 3, dw = hw % 3;
+    const int co0 = bx * 32, ci0 = by * 32;
     const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;
 #pragma unroll
     for (int dt = 0; dt < 3; ++dt)
@@ -796,6 +797,36 @@ __global__ void __launch_bounds__(256) pack3_kernel(const float* __restrict__ w,
             wf0[(base + tp) * cpad + co] = __float2bfloat16_rn(vf);
         }
     }
+}
+
+__global__ void __launch_bounds__(256) pack3_kernel(const float* __restrict__ w, int Cout, int Cin, int Cout_pad,
+                                                    int Kpad, int rows_pad, int cpad, __nv_bfloat16* __restrict__ fwd,
+                                                    __nv_bfloat16* __restrict__ wt, __nv_bfloat16* __restrict__ wf0) {
+    __shared__ float tile[3][32][33];
+    pack3_tile(w, Cout, Cin, Cout_pad, Kpad, rows_pad, cpad, fwd, wt, wf0, blockIdx.x, blockIdx.y, blockIdx.z, tile);
+}
+
+// All the 3x3x3 convs of a network in one launch: block b belongs to the job whose
+// first block is the largest block0 <= b (jobs in order of block0).
+__global__ void __launch_bounds__(256) pack3_batch_kernel(const Pack3Job* __restrict__ jobs, int njobs) {
+    __shared__ float tile[3][32][33];
+    __shared__ int s_job;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = njobs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) / 2;
+            if (jobs[mid].block0 <= (long long)blockIdx.x)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        s_job = lo;
+    }
+    __syncthreads();
+    const Pack3Job& J = jobs[s_job];
+    const long long lb = (long long)blockIdx.x - J.block0;
+    const int bx = (int)(lb % J.gx), by = (int)((lb / J.gx) % J.gy), hw = (int)(lb / ((long long)J.gx * J.gy));
+    pack3_tile(J.w, J.Cout, J.Cin, J.Cout_pad, J.Kpad, J.rows_pad, J.cpad, J.fwd, J.wt, J.wf0, bx, by, hw, tile);
 }
 
 // p -= lr * g, four floats per thread when both are 16-byte aligned (the tail and
@@ -1019,6 +1050,31 @@ int launch_pack3(const float* w, int Cout, int Cin, int Cout_pad, int Kpad, int 
     const int cmax = std::max(Cout_pad, cpad), rmax = std::max(Cin, rows_pad);
     dim3 grid((cmax + 31) / 32, (rmax + 31) / 32, 9);
     pack3_kernel<<<grid, 256, 0, s>>>(w, Cout, Cin, Cout_pad, Kpad, rows_pad, cpad, fwd, wt, wf0);
+    return (int)cudaGetLastError();
+}
+
+Pack3Job pack3_job(const float* w, int Cout, int Cin, int Cout_pad, int Kpad, int rows_pad, int cpad,
+                   __nv_bfloat16* fwd, __nv_bfloat16* wt, __nv_bfloat16* wf0, long long block0) {
+    Pack3Job j;
+    j.w = w;
+    j.fwd = fwd;
+    j.wt = wt;
+    j.wf0 = wf0;
+    j.Cout = Cout;
+    j.Cin = Cin;
+    j.Cout_pad = Cout_pad;
+    j.Kpad = Kpad;
+    j.rows_pad = rows_pad;
+    j.cpad = cpad;
+    j.gx = (std::max(Cout_pad, cpad) + 31) / 32;
+    j.gy = (std::max(Cin, rows_pad) + 31) / 32;
+    j.block0 = block0;
+    return j;
+}
+
+int launch_pack3_batch(const Pack3Job* d_jobs, int njobs, long long blocks, cudaStream_t s) {
+    if (njobs <= 0 || blocks <= 0) return 0;
+    pack3_batch_kernel<<<(unsigned)blocks, 256, 0, s>>>(d_jobs, njobs);
     return (int)cudaGetLastError();
 }
 

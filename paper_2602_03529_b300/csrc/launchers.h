@@ -148,6 +148,17 @@ int launch_mse(const float* xh, const T* x, long long n, float* dxh, float* loss
 // forward rows, adjoint taps and frame-0 adjoint taps of a BF16 3x3x3 conv in one pass (k_backward.cu)
 int launch_pack3(const float* w, int Cout, int Cin, int Cout_pad, int Kpad, int rows_pad, int cpad,
                  __nv_bfloat16* fwd, __nv_bfloat16* wt, __nv_bfloat16* wf0, cudaStream_t s);
+// One conv's three BF16 layouts (forward rows, adjoint taps, frame-0 adjoint taps)
+// as a job of the batched pack: gx x gy x 9 blocks from block0 on.
+struct Pack3Job {
+    const float* w;
+    __nv_bfloat16 *fwd, *wt, *wf0;
+    int Cout, Cin, Cout_pad, Kpad, rows_pad, cpad, gx, gy;
+    long long block0;
+};
+Pack3Job pack3_job(const float* w, int Cout, int Cin, int Cout_pad, int Kpad, int rows_pad, int cpad,
+                   __nv_bfloat16* fwd, __nv_bfloat16* wt, __nv_bfloat16* wf0, long long block0);
+int launch_pack3_batch(const Pack3Job* d_jobs, int njobs, long long blocks, cudaStream_t s);
 template <typename T>
 int launch_pack_adjoint(const float* w, int Cout, int Cin, int k, int rows_pad, int cpad, int corr, T* out,
                         cudaStream_t s);

@@ -120,6 +120,7 @@ void tok_destroy(tok_ctx* c) {
     if (c->tarena) cudaFree(c->tarena);
     if (c->d_status) cudaFree(c->d_status);
     if (c->d_fsq_thr) cudaFree(c->d_fsq_thr);
+    if (c->d_pack3_jobs) cudaFree(c->d_pack3_jobs);
     if (c->arena) cudaFree(c->arena);
     for (auto e : c->events) cudaEventDestroy(e);
     delete c;

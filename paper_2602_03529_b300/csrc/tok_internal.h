@@ -88,6 +88,11 @@ struct tok_ctx {
     std::map<std::string, int> gindex;
     FsqConsts fsq;
     FsqThr* d_fsq_thr = nullptr;  // the FSQ rounding thresholds of fsq (device)
+    // the batched re-pack of the 3x3x3 convs' BF16 layouts (built once the adjoint
+    // layouts exist; their addresses never change afterwards)
+    void* d_pack3_jobs = nullptr;
+    int n_pack3_jobs = 0;
+    long long pack3_blocks = 0;
     int* d_status = nullptr;
     char* arena = nullptr;
     size_t arena_bytes = 0;

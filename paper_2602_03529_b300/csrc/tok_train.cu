@@ -714,24 +714,43 @@ int tok_get_params(tok_ctx* c, float* d_flat, void* stream) {
                : TOK_ECUDA;
 }
 
-int tok_set_params_device(tok_ctx* c, const float* d_flat, void* stream) {
-    if (!c || !d_flat) return TOK_EINVAL;
+float* tok_params(tok_ctx* c) { return c ? c->d_master : nullptr; }
+
+int tok_repack(tok_ctx* c, void* stream) {
+    if (!c) return TOK_EINVAL;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (cudaMemcpyAsync(c->d_master, d_flat, (size_t)c->param_total * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
-        return TOK_ECUDA;
     // in a training loop (adjoint layouts already allocated, BF16): the forward rows and
-    // both adjoint layouts of every 3x3x3 conv from one read of its new weights
+    // both adjoint layouts of every 3x3x3 conv from one read of its new weights, all
+    // such convs in one launch
     bool adj = c->bf16();
     for (const auto& cw : c->convs)
         if (cw.name != "enc.stem" && cw.name != "stage.c0" && !cw.wt) adj = false;
-    for (auto& cw : c->convs) {
-        const bool fused = adj && cw.k == 3 && !cw.im2col && cw.wt && cw.wf0 && !cw.dwm;
-        if (fused) {
-            cw.b = c->d_master + cw.ob;
-            if (launch_pack3(c->d_master + cw.ow, cw.Cout, cw.Cin, cw.Cout_pad, cw.Kpad, cw.rows_pad, cw.cpad,
-                             static_cast<__nv_bfloat16*>(cw.w), static_cast<__nv_bfloat16*>(cw.wt),
-                             static_cast<__nv_bfloat16*>(cw.wf0), s))
+    const auto fused = [&](const ConvW& cw) { return adj && cw.k == 3 && !cw.im2col && cw.wt && cw.wf0 && !cw.dwm; };
+    if (adj && !c->d_pack3_jobs) {
+        std::vector<Pack3Job> jobs;
+        long long blocks = 0;
+        for (const auto& cw : c->convs) {
+            if (!fused(cw)) continue;
+            jobs.push_back(pack3_job(c->d_master + cw.ow, cw.Cout, cw.Cin, cw.Cout_pad, cw.Kpad, cw.rows_pad, cw.cpad,
+                                     static_cast<__nv_bfloat16*>(cw.w), static_cast<__nv_bfloat16*>(cw.wt),
+                                     static_cast<__nv_bfloat16*>(cw.wf0), blocks));
+            blocks += (long long)jobs.back().gx * jobs.back().gy * 9;
+        }
+        if (!jobs.empty()) {
+            if (cudaMalloc(&c->d_pack3_jobs, jobs.size() * sizeof(Pack3Job)) != cudaSuccess) return TOK_ENOMEM;
+            if (cudaMemcpy(c->d_pack3_jobs, jobs.data(), jobs.size() * sizeof(Pack3Job), cudaMemcpyHostToDevice) !=
+                cudaSuccess)
                 return TOK_ECUDA;
+        }
+        c->n_pack3_jobs = (int)jobs.size();
+        c->pack3_blocks = blocks;
+    }
+    if (adj && c->n_pack3_jobs > 0 &&
+        launch_pack3_batch(static_cast<const Pack3Job*>(c->d_pack3_jobs), c->n_pack3_jobs, c->pack3_blocks, s))
+        return TOK_ECUDA;
+    for (auto& cw : c->convs) {
+        if (fused(cw)) {
+            cw.b = c->d_master + cw.ob;
             continue;
         }
         if (upload_conv(c, cw, s) != TOK_OK) return TOK_ECUDA;
@@ -746,6 +765,15 @@ int tok_set_params_device(tok_ctx* c, const float* d_flat, void* stream) {
     }
     c->adjoint_dirty = !adj;
     return TOK_OK;
+}
+
+int tok_set_params_device(tok_ctx* c, const float* d_flat, void* stream) {
+    if (!c || !d_flat) return TOK_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (d_flat != c->d_master &&
+        cudaMemcpyAsync(c->d_master, d_flat, (size_t)c->param_total * 4, cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+        return TOK_ECUDA;
+    return tok_repack(c, stream);
 }
 
 size_t tok_train_workspace_bytes(const tok_ctx* c, int N, int T, int H, int W) {

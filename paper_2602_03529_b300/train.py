@@ -18,8 +18,17 @@ from . import _lib as L
 from .tokenizer import Tokenizer, _ptr, _stream_ptr
 
 
+class _DeviceFloats:
+    """n float32 values at a device address, as a CUDA array interface (for a zero-copy
+    torch view; the memory stays owned by its context)."""
+
+    def __init__(self, ptr: int, n: int):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<f4", "data": (ptr, False), "version": 3}
+
+
 class Trainer:
-    """Owns the flat FP32 parameter vector of a Tokenizer and the training workspace."""
+    """Holds a view of a Tokenizer's flat FP32 parameters (the context's own memory: valid
+    while the Tokenizer is open) and reserves its training workspace."""
 
     def __init__(self, tk: Tokenizer, N: int, T: int, H: int, W: int, recompute: bool = True):
         self.tk = tk
@@ -28,17 +37,22 @@ class Trainer:
         L.tok_reserve_train(tk.ctx, N, T, H, W)
         self.workspace_bytes = L.tok_train_workspace_bytes(tk.ctx, N, T, H, W)
         n = L.tok_param_total(tk.ctx)
-        self.params = torch.empty(n, device="cuda", dtype=torch.float32)
-        L.tok_get_params(tk.ctx, _ptr(self.params), _stream_ptr(None))
+        # a view of the context's own flat parameters (no copy): SGD updates them in
+        # place and only the packed layouts are rebuilt
+        self.params = torch.as_tensor(_DeviceFloats(L.tok_params(tk.ctx), n), device="cuda")
         self.grads = torch.zeros_like(self.params)
         self.xhat = torch.empty((N, T, H, W, 3), device="cuda", dtype=torch.float32)
         self.dxhat = torch.empty_like(self.xhat)
         self.loss = torch.zeros(1, device="cuda", dtype=torch.float32)
 
     def load(self, params: torch.Tensor | None = None):
-        """Push the flat parameters (default: self.params) into the context's device layouts."""
+        """Push the flat parameters (default: self.params, the context's own) into the
+        context's device layouts."""
         p = self.params if params is None else params
-        L.tok_set_params_device(self.tk.ctx, _ptr(p), _stream_ptr(None))
+        if p.data_ptr() == self.params.data_ptr():
+            L.tok_repack(self.tk.ctx, _stream_ptr(None))
+        else:
+            L.tok_set_params_device(self.tk.ctx, _ptr(p), _stream_ptr(None))
 
     def forward(self, x: torch.Tensor, drop_rate: float, seed: int, step: int, keep_bits: torch.Tensor | None = None):
         """keep_bits (optional): row masks (N, T', H', ceil(W'/32)) int32 replacing the random drop."""
