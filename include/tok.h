@@ -49,7 +49,8 @@ enum tok_err {
     TOK_ECUDA = 4,     /* a CUDA runtime/driver call failed */
     TOK_ETIMEOUT = 5,  /* a device-side bounded wait ran out (kernel returned early) */
     TOK_EDEVICE = 6,   /* no usable sm_100-family device */
-    TOK_ESTATE = 7     /* call out of order (e.g. weights not set, stream misuse) */
+    TOK_ESTATE = 7,    /* call out of order (e.g. weights not set, stream misuse) */
+    TOK_EFILE = 8      /* weights file missing, unreadable, malformed or corrupt */
 };
 
 enum tok_precision { TOK_BF16 = 1, TOK_FP32 = 2 };
@@ -98,6 +99,23 @@ void tok_arch_default(tok_arch* a);
  * set). Returns TOK_EDEVICE if the device is not sm_100-family. */
 int tok_create(const tok_arch* arch, int precision, tok_ctx** out);
 void tok_destroy(tok_ctx* ctx);
+
+/* Weights files: the flat FP32 parameters (tok_param_info order) with the
+ * descriptor they belong to. Layout (little-endian): a 104-byte header
+ *   0 "TOKW"  4 version 1  8 kind  12 in_ch  16 nlevels  20 ch[4]  36 blocks
+ *   40 nlev  44 levels[8]  76 gn_groups  80 gn_eps (float32)  84 time_pad
+ *   88 t_stem  92 zero  96 n = parameter count (int64)
+ * then n float32 values, then the 64-bit FNV-1a hash of those 4n bytes.
+ * tok_save_params writes the context's parameters (synchronous; through a
+ * temporary file renamed into place). tok_create_from_file creates a context
+ * on the current device from such a file (as tok_create, then the weights).
+ * tok_read_weights_header reads and checks a file's header on the host (no
+ * device): the descriptor must be one tok_create builds, n its parameter
+ * count, the file size 104 + 4n + 8. Errors: TOK_EFILE (missing, short,
+ * malformed, wrong count, hash mismatch), and tok_create's. */
+int tok_save_params(tok_ctx* ctx, const char* path);
+int tok_create_from_file(const char* path, int precision, tok_ctx** out);
+int tok_read_weights_header(const char* path, tok_arch* arch, int64_t* param_total);
 
 /* Parameter list in the architecture's order: name (owned by the context,
  * valid until tok_destroy), rank and dims. Conv weights are

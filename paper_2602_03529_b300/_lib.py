@@ -13,7 +13,7 @@ import os
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmorphe_tok.so")
 
-TOK_OK, TOK_EINVAL, TOK_ESHAPE, TOK_ENOMEM, TOK_ECUDA, TOK_ETIMEOUT, TOK_EDEVICE, TOK_ESTATE = range(8)
+TOK_OK, TOK_EINVAL, TOK_ESHAPE, TOK_ENOMEM, TOK_ECUDA, TOK_ETIMEOUT, TOK_EDEVICE, TOK_ESTATE, TOK_EFILE = range(9)
 TOK_BF16, TOK_FP32 = 1, 2
 TOK_PAD_REPLICATE, TOK_PAD_ZERO = 0, 1
 TOK_ARCH_FULL, TOK_ARCH_STAGE = 0, 1
@@ -77,6 +77,9 @@ vp, i32, i64, u64, f32, sz = C.c_void_p, C.c_int, C.c_int64, C.c_uint64, C.c_flo
 _SIGS = {
     "tok_arch_default": (None, [C.POINTER(tok_arch)]),
     "tok_create": (i32, [C.POINTER(tok_arch), i32, C.POINTER(vp)]),
+    "tok_save_params": (i32, [vp, C.c_char_p]),
+    "tok_create_from_file": (i32, [C.c_char_p, i32, C.POINTER(vp)]),
+    "tok_read_weights_header": (i32, [C.c_char_p, C.POINTER(tok_arch), C.POINTER(i64)]),
     "tok_destroy": (None, [vp]),
     "tok_param_count": (i32, [vp]),
     "tok_param_info": (i32, [vp, i32, C.POINTER(C.c_char_p), C.POINTER(i32), C.POINTER(i64)]),
@@ -186,6 +189,24 @@ def tok_create(arch: tok_arch, precision: int) -> int:
     h = vp()
     _ck(_call("tok_create", C.byref(arch), precision, C.byref(h)), "tok_create")
     return h.value
+
+
+def tok_save_params(ctx: int, path: str) -> None:
+    _ck(_call("tok_save_params", ctx, os.fsencode(path)), "tok_save_params")
+
+
+def tok_create_from_file(path: str, precision: int) -> int:
+    h = vp()
+    _ck(_call("tok_create_from_file", os.fsencode(path), precision, C.byref(h)), "tok_create_from_file")
+    return h.value
+
+
+def tok_read_weights_header(path: str):
+    """(tok_arch, parameter count) of a weights file; host only."""
+    a = tok_arch()
+    n = i64()
+    _ck(_call("tok_read_weights_header", os.fsencode(path), C.byref(a), C.byref(n)), "tok_read_weights_header")
+    return a, n.value
 
 
 def tok_destroy(ctx: int) -> None:

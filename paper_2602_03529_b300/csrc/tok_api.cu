@@ -36,6 +36,211 @@ void tok_arch_default(tok_arch* a) {
     a->t_stem = 1;
 }
 
+}  // extern "C"
+
+namespace {
+
+// Whether an architecture descriptor is one the library builds (TOK_OK) on the
+// given path (TOK_BF16 needs channel counts that are multiples of 64).
+int arch_error(const tok_arch& a, int precision) {
+    if (a.in_ch != 3 || !valid_levels(a.levels, a.nlev)) return TOK_EINVAL;
+    if (a.kind == TOK_ARCH_FULL) {
+        if (a.nlevels < 1 || a.nlevels > 4 || a.blocks < 0) return TOK_EINVAL;
+        if (a.t_stem != 1 && a.t_stem != 2) return TOK_EINVAL;
+    } else if (a.kind != TOK_ARCH_STAGE) {
+        return TOK_EINVAL;
+    }
+    const int nch = a.kind == TOK_ARCH_STAGE ? 2 : a.nlevels;
+    for (int i = 0; i < nch; ++i) {
+        const int C = a.ch[i];
+        if (C < 16 || C % 16 != 0) return TOK_EINVAL;
+        if (precision == TOK_BF16 && C % 64 != 0) return TOK_EINVAL;
+    }
+    return TOK_OK;
+}
+
+// ---- weights file: the flat FP32 parameters with the descriptor they belong to.
+// Little-endian, 104-byte header:
+//   0 "TOKW"   4 version (1)   8 kind   12 in_ch   16 nlevels   20 ch[4]   36 blocks
+//   40 nlev   44 levels[8]   76 gn_groups   80 gn_eps (float32 bits)   84 time_pad
+//   88 t_stem   92 0   96 parameter count n (int64)
+// then n float32 values in the order of tok_param_info, then the 64-bit FNV-1a hash
+// of those 4 n bytes.
+constexpr uint32_t kWeightsMagic = 0x574B4F54u;  // "TOKW" read as a little-endian word
+constexpr uint32_t kWeightsVersion = 1;
+constexpr size_t kWeightsHeader = 104;
+
+void put_u32(uint8_t* p, uint32_t v) {
+    for (int i = 0; i < 4; ++i) p[i] = (uint8_t)(v >> (8 * i));
+}
+uint32_t get_u32(const uint8_t* p) {
+    uint32_t v = 0;
+    for (int i = 0; i < 4; ++i) v |= (uint32_t)p[i] << (8 * i);
+    return v;
+}
+void put_u64(uint8_t* p, uint64_t v) {
+    for (int i = 0; i < 8; ++i) p[i] = (uint8_t)(v >> (8 * i));
+}
+uint64_t get_u64(const uint8_t* p) {
+    uint64_t v = 0;
+    for (int i = 0; i < 8; ++i) v |= (uint64_t)p[i] << (8 * i);
+    return v;
+}
+
+uint64_t fnv1a64(const uint8_t* p, size_t n) {
+    uint64_t h = 0xcbf29ce484222325ull;
+    for (size_t i = 0; i < n; ++i) {
+        h ^= p[i];
+        h *= 0x100000001b3ull;
+    }
+    return h;
+}
+
+bool host_little_endian() {
+    const uint32_t one = 1;
+    uint8_t b;
+    memcpy(&b, &one, 1);
+    return b == 1;
+}
+
+void encode_weights_header(const tok_arch& a, int64_t n, uint8_t* h) {
+    memset(h, 0, kWeightsHeader);
+    put_u32(h + 0, kWeightsMagic);
+    put_u32(h + 4, kWeightsVersion);
+    put_u32(h + 8, (uint32_t)a.kind);
+    put_u32(h + 12, (uint32_t)a.in_ch);
+    put_u32(h + 16, (uint32_t)a.nlevels);
+    for (int i = 0; i < 4; ++i) put_u32(h + 20 + 4 * i, (uint32_t)a.ch[i]);
+    put_u32(h + 36, (uint32_t)a.blocks);
+    put_u32(h + 40, (uint32_t)a.nlev);
+    for (int i = 0; i < 8; ++i) put_u32(h + 44 + 4 * i, (uint32_t)a.levels[i]);
+    put_u32(h + 76, (uint32_t)a.gn_groups);
+    uint32_t eps;
+    memcpy(&eps, &a.gn_eps, 4);
+    put_u32(h + 80, eps);
+    put_u32(h + 84, (uint32_t)a.time_pad);
+    put_u32(h + 88, (uint32_t)a.t_stem);
+    put_u64(h + 96, (uint64_t)n);
+}
+
+bool decode_weights_header(const uint8_t* h, tok_arch* a, int64_t* n) {
+    if (get_u32(h) != kWeightsMagic || get_u32(h + 4) != kWeightsVersion) return false;
+    memset(a, 0, sizeof(*a));
+    a->kind = (int)get_u32(h + 8);
+    a->in_ch = (int)get_u32(h + 12);
+    a->nlevels = (int)get_u32(h + 16);
+    for (int i = 0; i < 4; ++i) a->ch[i] = (int)get_u32(h + 20 + 4 * i);
+    a->blocks = (int)get_u32(h + 36);
+    a->nlev = (int)get_u32(h + 40);
+    for (int i = 0; i < 8; ++i) a->levels[i] = (int)get_u32(h + 44 + 4 * i);
+    a->gn_groups = (int)get_u32(h + 76);
+    const uint32_t eps = get_u32(h + 80);
+    memcpy(&a->gn_eps, &eps, 4);
+    a->time_pad = (int)get_u32(h + 84);
+    a->t_stem = (int)get_u32(h + 88);
+    *n = (int64_t)get_u64(h + 96);
+    return true;
+}
+
+// Parameter count of an architecture (the host-side layer list only).
+int64_t arch_param_total(const tok_arch& a) {
+    tok_ctx tmp;
+    tmp.arch = a;
+    tmp.precision = TOK_BF16;
+    tmp.fsq = make_fsq(a.levels, a.nlev);
+    build_layers(&tmp);
+    return tmp.param_total;
+}
+
+// Reads and checks a weights file's header (descriptor buildable, parameter count
+// that of the descriptor, file size header + 4 n + 8).
+int read_weights_header(FILE* f, tok_arch* a, int64_t* n) {
+    uint8_t h[kWeightsHeader];
+    if (fread(h, 1, kWeightsHeader, f) != kWeightsHeader) return TOK_EFILE;
+    if (!decode_weights_header(h, a, n)) return TOK_EFILE;
+    if (arch_error(*a, TOK_FP32) != TOK_OK || a->time_pad < 0 || a->time_pad > 1 || !(a->gn_eps > 0.f)) return TOK_EFILE;
+    if (*n <= 0 || *n != arch_param_total(*a)) return TOK_EFILE;
+    if (fseek(f, 0, SEEK_END) != 0) return TOK_EFILE;
+    const long size = ftell(f);
+    if (size < 0 || (uint64_t)size != kWeightsHeader + 4ull * (uint64_t)*n + 8ull) return TOK_EFILE;
+    if (fseek(f, (long)kWeightsHeader, SEEK_SET) != 0) return TOK_EFILE;
+    return TOK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tok_read_weights_header(const char* path, tok_arch* arch, int64_t* param_total) {
+    if (!path || !arch || !param_total) return TOK_EINVAL;
+    if (!host_little_endian()) return TOK_EFILE;
+    FILE* f = fopen(path, "rb");
+    if (!f) return TOK_EFILE;
+    const int e = read_weights_header(f, arch, param_total);
+    fclose(f);
+    return e;
+}
+
+int tok_save_params(tok_ctx* c, const char* path) {
+    if (!c || !path) return TOK_EINVAL;
+    if (!host_little_endian()) return TOK_EFILE;
+    std::vector<float> p((size_t)c->param_total);
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(p.data(), c->d_master, p.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return TOK_ECUDA;
+    uint8_t h[kWeightsHeader], tail[8];
+    encode_weights_header(c->arch, c->param_total, h);
+    put_u64(tail, fnv1a64(reinterpret_cast<const uint8_t*>(p.data()), p.size() * 4));
+    // written next to the target and renamed into place, so a reader never sees half a file
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE* f = fopen(tmp.c_str(), "wb");
+    if (!f) return TOK_EFILE;
+    bool ok = fwrite(h, 1, kWeightsHeader, f) == kWeightsHeader && fwrite(p.data(), 4, p.size(), f) == p.size() &&
+              fwrite(tail, 1, 8, f) == 8;
+    ok = (fclose(f) == 0) && ok;
+    if (!ok || rename(tmp.c_str(), path) != 0) {
+        remove(tmp.c_str());
+        return TOK_EFILE;
+    }
+    return TOK_OK;
+}
+
+int tok_create_from_file(const char* path, int precision, tok_ctx** out) {
+    if (!path || !out) return TOK_EINVAL;
+    *out = nullptr;
+    if (!host_little_endian()) return TOK_EFILE;
+    FILE* f = fopen(path, "rb");
+    if (!f) return TOK_EFILE;
+    tok_arch a;
+    int64_t n = 0;
+    int e = read_weights_header(f, &a, &n);
+    std::vector<float> p;
+    if (!e) {
+        p.resize((size_t)n);
+        uint8_t tail[8];
+        if (fread(p.data(), 4, p.size(), f) != p.size() || fread(tail, 1, 8, f) != 8 ||
+            get_u64(tail) != fnv1a64(reinterpret_cast<const uint8_t*>(p.data()), p.size() * 4))
+            e = TOK_EFILE;
+    }
+    fclose(f);
+    if (e) return e;
+    tok_ctx* c = nullptr;
+    e = tok_create(&a, precision, &c);
+    if (e) return e;
+    for (size_t i = 0; i < c->params.size(); ++i)
+        std::copy(p.begin() + c->params[i].offset, p.begin() + c->params[i].offset + c->params[i].count,
+                  c->host[i].begin());
+    if (cudaMemcpy(c->d_master, p.data(), p.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) e = TOK_ECUDA;
+    if (!e) e = tok_repack(c, nullptr);
+    if (!e && cudaDeviceSynchronize() != cudaSuccess) e = TOK_ECUDA;
+    if (e) {
+        tok_destroy(c);
+        return e;
+    }
+    *out = c;
+    return TOK_OK;
+}
+
 const char* tok_strerror(int code) {
     switch (code) {
         case TOK_OK: return "ok";
@@ -46,6 +251,7 @@ const char* tok_strerror(int code) {
         case TOK_ETIMEOUT: return "device-side bounded wait timed out";
         case TOK_EDEVICE: return "no usable sm_100-family device";
         case TOK_ESTATE: return "call out of order";
+        case TOK_EFILE: return "weights file unreadable or malformed";
         default: return "unknown error";
     }
 }
@@ -54,19 +260,7 @@ int tok_create(const tok_arch* arch, int precision, tok_ctx** out) {
     if (!arch || !out) return TOK_EINVAL;
     *out = nullptr;
     if (precision != TOK_BF16 && precision != TOK_FP32) return TOK_EINVAL;
-    if (arch->in_ch != 3 || !valid_levels(arch->levels, arch->nlev)) return TOK_EINVAL;
-    if (arch->kind == TOK_ARCH_FULL) {
-        if (arch->nlevels < 1 || arch->nlevels > 4 || arch->blocks < 0) return TOK_EINVAL;
-        if (arch->t_stem != 1 && arch->t_stem != 2) return TOK_EINVAL;
-    } else if (arch->kind != TOK_ARCH_STAGE) {
-        return TOK_EINVAL;
-    }
-    const int nch = arch->kind == TOK_ARCH_STAGE ? 2 : arch->nlevels;
-    for (int i = 0; i < nch; ++i) {
-        const int C = arch->ch[i];
-        if (C < 16 || C % 16 != 0) return TOK_EINVAL;
-        if (precision == TOK_BF16 && C % 64 != 0) return TOK_EINVAL;
-    }
+    if (const int ea = arch_error(*arch, precision)) return ea;
     int nsm = 0;
     int e = check_cuda_device(&nsm);
     if (e) return e;

@@ -37,6 +37,14 @@ def make_arch(kind="full", ch=(128, 256, 512), blocks=2, levels=(8, 8, 8, 5, 5, 
     return a
 
 
+def arch_kwargs(a: L.tok_arch) -> dict:
+    """The make_arch keywords of a descriptor."""
+    n = 2 if a.kind == L.TOK_ARCH_STAGE else a.nlevels
+    return dict(kind="stage" if a.kind == L.TOK_ARCH_STAGE else "full", ch=tuple(a.ch[:n]), blocks=a.blocks,
+                levels=tuple(a.levels[:a.nlev]), gn_groups=a.gn_groups, gn_eps=a.gn_eps,
+                time_pad="replicate" if a.time_pad == L.TOK_PAD_REPLICATE else "zero", t_stem=a.t_stem)
+
+
 def _stream_ptr(stream):
     if stream is None:
         stream = torch.cuda.current_stream()
@@ -63,6 +71,23 @@ class Tokenizer:
         self.levels = tuple(arch.get("levels", (8, 8, 8, 5, 5, 5)))
         self.ctx = L.tok_create(self.arch, PRECISIONS[precision])
         self.dtype = torch.bfloat16 if precision == "bf16" else torch.float32
+
+    @classmethod
+    def from_file(cls, path: str, precision: str = "bf16"):
+        """A context whose descriptor and weights come from a file written by save()."""
+        arch, _ = L.tok_read_weights_header(path)
+        self = cls.__new__(cls)
+        self.precision = precision
+        self.arch = arch
+        self.arch_kw = arch_kwargs(arch)
+        self.levels = tuple(arch.levels[:arch.nlev])
+        self.ctx = L.tok_create_from_file(path, PRECISIONS[precision])
+        self.dtype = torch.bfloat16 if precision == "bf16" else torch.float32
+        return self
+
+    def save(self, path: str):
+        """Write the descriptor and the flat FP32 parameters (synchronous)."""
+        L.tok_save_params(self.ctx, path)
 
     # -- parameters -------------------------------------------------------
     def param_list(self):
