@@ -50,7 +50,8 @@ enum tok_err {
     TOK_ETIMEOUT = 5,  /* a device-side bounded wait ran out (kernel returned early) */
     TOK_EDEVICE = 6,   /* no usable sm_100-family device */
     TOK_ESTATE = 7,    /* call out of order (e.g. weights not set, stream misuse) */
-    TOK_EFILE = 8      /* weights file missing, unreadable, malformed or corrupt */
+    TOK_EFILE = 8,     /* weights file missing, unreadable, malformed or corrupt */
+    TOK_EGUARD = 9     /* a workspace guard band was overwritten (tok_check_guards) */
 };
 
 enum tok_precision { TOK_BF16 = 1, TOK_FP32 = 2 };
@@ -467,10 +468,27 @@ int tok_groupnorm_silu_noalloc(int precision, const void* d_x, int64_t frames, i
 int tok_status(tok_ctx* ctx);
 const char* tok_strerror(int code);
 
+/* Guard bands (a check in place of a memory sanitizer): the context's
+ * workspaces (inference arena, training workspace) and every stream's caches
+ * are allocated with 4 KB of a fixed byte pattern before and after the bytes
+ * the kernels use. tok_check_guards (the context's) and
+ * tok_stream_check_guards (one stream's) synchronise the device and compare
+ * the bands with the pattern: TOK_OK, or TOK_EGUARD if a kernel wrote outside
+ * its workspace. tok_stream_bytes includes a stream's two bands. */
+int tok_check_guards(tok_ctx* ctx);
+int tok_stream_check_guards(tok_stream* s);
+
 /* Debug/self-test: launch one kernel that waits on a device barrier nothing
  * ever signals, with a bounded wait of `limit_ns`; the kernel gives up,
  * records TOK_ETIMEOUT in the context's status word and returns. */
 int tok_selftest_timeout(tok_ctx* ctx, int64_t limit_ns, void* stream);
+
+/* Self-test of the guard bands: writes one byte of the reserved arena's
+ * trailing band with cudaMemset (inside the allocation), checks that
+ * tok_check_guards reports TOK_EGUARD, restores the band and checks that it
+ * reports TOK_OK again. Returns TOK_OK when both checks behaved, TOK_ESTATE
+ * when no arena is reserved, TOK_EGUARD otherwise. */
+int tok_selftest_guards(tok_ctx* ctx);
 
 /* Test hook: layer traces. While armed, every tok_encode / tok_decode (and
  * their batch forms, item 0) of this context copies, after the launch of the

@@ -13,7 +13,8 @@ import os
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libmorphe_tok.so")
 
-TOK_OK, TOK_EINVAL, TOK_ESHAPE, TOK_ENOMEM, TOK_ECUDA, TOK_ETIMEOUT, TOK_EDEVICE, TOK_ESTATE, TOK_EFILE = range(9)
+(TOK_OK, TOK_EINVAL, TOK_ESHAPE, TOK_ENOMEM, TOK_ECUDA, TOK_ETIMEOUT, TOK_EDEVICE, TOK_ESTATE, TOK_EFILE,
+ TOK_EGUARD) = range(10)
 TOK_BF16, TOK_FP32 = 1, 2
 TOK_PAD_REPLICATE, TOK_PAD_ZERO = 0, 1
 TOK_ARCH_FULL, TOK_ARCH_STAGE = 0, 1
@@ -135,6 +136,9 @@ _SIGS = {
     "tok_groupnorm_silu_noalloc": (i32, [i32, vp, i64, i64, i32, i32, vp, vp, f32, vp, vp]),
     "tok_status": (i32, [vp]),
     "tok_strerror": (C.c_char_p, [i32]),
+    "tok_check_guards": (i32, [vp]),
+    "tok_stream_check_guards": (i32, [vp]),
+    "tok_selftest_guards": (i32, [vp]),
     "tok_selftest_timeout": (i32, [vp, i64, vp]),
     "tok_launch_count": (i64, [vp]),
     "tok_profile_enable": (i32, [vp, i32]),
@@ -207,6 +211,19 @@ def tok_read_weights_header(path: str):
     n = i64()
     _ck(_call("tok_read_weights_header", os.fsencode(path), C.byref(a), C.byref(n)), "tok_read_weights_header")
     return a, n.value
+
+
+def tok_check_guards(ctx: int) -> int:
+    """TOK_OK or TOK_EGUARD (a kernel wrote outside the context's workspaces)."""
+    return _call("tok_check_guards", ctx)
+
+
+def tok_stream_check_guards(st: int) -> int:
+    return _call("tok_stream_check_guards", st)
+
+
+def tok_selftest_guards(ctx: int) -> int:
+    return _call("tok_selftest_guards", ctx)
 
 
 def tok_destroy(ctx: int) -> None:

@@ -252,6 +252,7 @@ const char* tok_strerror(int code) {
         case TOK_EDEVICE: return "no usable sm_100-family device";
         case TOK_ESTATE: return "call out of order";
         case TOK_EFILE: return "weights file unreadable or malformed";
+        case TOK_EGUARD: return "a workspace guard band was overwritten";
         default: return "unknown error";
     }
 }
@@ -311,11 +312,11 @@ void tok_destroy(tok_ctx* c) {
         if (cw.wf0) cudaFree(cw.wf0);
     }
     if (c->d_master) cudaFree(c->d_master);
-    if (c->tarena) cudaFree(c->tarena);
+    guarded_free(c->tarena);
     if (c->d_status) cudaFree(c->d_status);
     if (c->d_fsq_thr) cudaFree(c->d_fsq_thr);
     if (c->d_pack3_jobs) cudaFree(c->d_pack3_jobs);
-    if (c->arena) cudaFree(c->arena);
+    guarded_free(c->arena);
     for (auto e : c->events) cudaEventDestroy(e);
     delete c;
 }
@@ -393,14 +394,12 @@ static int reserve_bytes(tok_ctx* c, size_t need) {
     if (need <= c->arena_bytes) return TOK_OK;
     if (c->arena) {
         cudaDeviceSynchronize();
-        cudaFree(c->arena);
+        guarded_free(c->arena);
         c->arena = nullptr;
         c->arena_bytes = 0;
     }
-    if (cudaMalloc(&c->arena, need) != cudaSuccess) {
-        cudaGetLastError();
-        return TOK_ENOMEM;
-    }
+    c->arena = guarded_alloc(need);
+    if (!c->arena) return TOK_ENOMEM;
     c->arena_bytes = need;
     return TOK_OK;
 }
@@ -727,7 +726,7 @@ int tok_unpack_rows(const int32_t* payload, const int64_t* row_offsets, const ui
 
 size_t tok_stream_bytes(const tok_ctx* c, int H, int W) {
     if (!c || H < 1 || W < 1) return 0;
-    size_t total = 0;
+    size_t total = 2 * kGuardBytes;  // the guard bands of its allocation
     for (const auto& kv : stream_frames(c, H, W)) total += align256(2 * kv.second);
     return total;
 }
@@ -735,13 +734,13 @@ size_t tok_stream_bytes(const tok_ctx* c, int H, int W) {
 int tok_stream_open(tok_ctx* c, int H, int W, tok_stream** out) {
     if (!c || !out || H < 1 || W < 1) return TOK_EINVAL;
     *out = nullptr;
-    const size_t bytes = tok_stream_bytes(c, H, W);
+    const size_t bytes = tok_stream_bytes(c, H, W) - 2 * kGuardBytes;
     tok_stream* st = new tok_stream();
     st->ctx = c;
     st->H = H;
     st->W = W;
-    if (cudaMalloc(&st->mem, bytes) != cudaSuccess) {
-        cudaGetLastError();
+    st->mem = guarded_alloc(bytes);
+    if (!st->mem) {
         delete st;
         return TOK_ENOMEM;
     }
@@ -758,8 +757,31 @@ int tok_stream_open(tok_ctx* c, int H, int W, tok_stream** out) {
 
 void tok_stream_close(tok_stream* s) {
     if (!s) return;
-    if (s->mem) cudaFree(s->mem);
+    guarded_free(s->mem);
     delete s;
+}
+
+int tok_check_guards(tok_ctx* c) {
+    if (!c) return TOK_EINVAL;
+    const int e = guards_check(c->arena, c->arena_bytes);
+    return e ? e : guards_check(c->tarena, c->tbytes);
+}
+
+int tok_selftest_guards(tok_ctx* c) {
+    if (!c) return TOK_EINVAL;
+    if (!c->arena) return TOK_ESTATE;
+    if (tok_check_guards(c) != TOK_OK) return TOK_EGUARD;
+    char* band = c->arena + c->arena_bytes;  // the trailing band
+    if (cudaMemset(band + 17, kGuardByte ^ 0xFF, 1) != cudaSuccess) return TOK_ECUDA;
+    const bool caught = tok_check_guards(c) == TOK_EGUARD;
+    if (cudaMemset(band + 17, kGuardByte, 1) != cudaSuccess) return TOK_ECUDA;
+    const bool clean = tok_check_guards(c) == TOK_OK;
+    return caught && clean ? TOK_OK : TOK_EGUARD;
+}
+
+int tok_stream_check_guards(tok_stream* s) {
+    if (!s) return TOK_EINVAL;
+    return guards_check(s->mem, s->bytes);
 }
 
 int tok_stream_reset(tok_stream* s) {

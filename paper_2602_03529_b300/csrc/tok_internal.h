@@ -127,6 +127,44 @@ struct tok_ctx {
 // One video stream's causal state: for every conv with temporal taps, the
 // last two frames of its input (the left context of the next chunk), plus
 // chunk counters for the encoder and the decoder side.
+// Guard bands: every workspace allocation (the inference arena, the training
+// workspace, a stream's caches) has kGuardBytes of the byte kGuardByte before and
+// after the bytes it hands out; tok_check_guards / tok_stream_check_guards read
+// them back, so a kernel that wrote outside its workspace is caught by the tests.
+constexpr size_t kGuardBytes = 4096;
+constexpr unsigned char kGuardByte = 0xA5;
+
+inline char* guarded_alloc(size_t bytes) {
+    char* base = nullptr;
+    if (cudaMalloc(&base, bytes + 2 * kGuardBytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (cudaMemset(base, kGuardByte, kGuardBytes) != cudaSuccess ||
+        cudaMemset(base + kGuardBytes + bytes, kGuardByte, kGuardBytes) != cudaSuccess) {
+        cudaFree(base);
+        return nullptr;
+    }
+    return base + kGuardBytes;
+}
+
+inline void guarded_free(char* p) {
+    if (p) cudaFree(p - kGuardBytes);
+}
+
+// TOK_OK, TOK_EGUARD (a band changed) or TOK_ECUDA; synchronous.
+inline int guards_check(const char* p, size_t bytes) {
+    if (!p) return TOK_OK;
+    std::vector<unsigned char> h(2 * kGuardBytes);
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(h.data(), p - kGuardBytes, kGuardBytes, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(h.data() + kGuardBytes, p + bytes, kGuardBytes, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return TOK_ECUDA;
+    for (unsigned char b : h)
+        if (b != kGuardByte) return TOK_EGUARD;
+    return TOK_OK;
+}
+
 struct tok_stream {
     tok_ctx* ctx = nullptr;
     int H = 0, W = 0;

@@ -788,14 +788,12 @@ int tok_reserve_train(tok_ctx* c, int N, int T, int H, int W) {
     if (need > c->tbytes) {
         if (c->tarena) {
             cudaDeviceSynchronize();
-            cudaFree(c->tarena);
+            guarded_free(c->tarena);
             c->tarena = nullptr;
             c->tbytes = 0;
         }
-        if (cudaMalloc(&c->tarena, need) != cudaSuccess) {
-            cudaGetLastError();
-            return TOK_ENOMEM;
-        }
+        c->tarena = guarded_alloc(need);
+        if (!c->tarena) return TOK_ENOMEM;
         c->tbytes = need;
     }
     return TOK_OK;

@@ -251,6 +251,10 @@ class Tokenizer:
     def status(self) -> int:
         return L.tok_status(self.ctx)
 
+    def check_guards(self) -> int:
+        """TOK_OK, or TOK_EGUARD if a kernel wrote outside the context's workspaces."""
+        return L.tok_check_guards(self.ctx)
+
     def launch_count(self) -> int:
         return L.tok_launch_count(self.ctx)
 

@@ -20,6 +20,8 @@ import numpy as np
 import pytest
 import torch
 
+from paper_2602_03529_b300 import _lib as _L
+
 import synthetic as S
 from oracle import ops
 
@@ -104,6 +106,7 @@ def coder(P):
     tk.reserve(1, T, H, W)
     x = torch.from_numpy(S.to_bf16_f32(S.blurred_noise_clip(1000, 1, T, H, W))).to("cuda", torch.bfloat16)
     yield tk, x
+    assert tk.check_guards() == 0
     tk.close()
 
 
@@ -149,6 +152,7 @@ def test_full_size_stream_equals_clip(P, coder):
         ids.append(i)
         xs.append(tk.decode(i, H, W, video=vid, first_chunk=(k == 0)))
     torch.cuda.synchronize()
+    assert _L.tok_stream_check_guards(vid) == 0
     tk.stream_close(vid)
     assert torch.equal(torch.cat(zs, 1), z_c)
     assert torch.equal(torch.cat(ids, 1), i_c)
@@ -228,6 +232,7 @@ def traced(P):
     tk.trace_layer(None)
     oracle_p = {k: (S.to_bf16_f32(v) if k.endswith(".w") else v).astype(np.float64) for k, v in params.items()}
     yield {"x": x, "z": z, "idx": idx, "xh": xh, "bufs": bufs, "p": oracle_p}
+    assert tk.check_guards() == 0
     tk.close()
 
 

@@ -11,6 +11,8 @@ import numpy as np
 import pytest
 import torch
 
+from paper_2602_03529_b300 import _lib as _L
+
 import synthetic as S
 
 pytestmark = pytest.mark.gpu
@@ -57,6 +59,7 @@ def test_batch_equals_single_calls(P, prec):
         assert torch.equal(ib[i], i1), i
         assert torch.equal(xb[i], x1), i
     assert tk.status() == 0
+    assert tk.check_guards() == 0
     tk.close()
 
 
@@ -69,6 +72,7 @@ def test_batch_of_one_equals_single_call(P):
     (zb,), (ib,) = tk.encode_batch([x])
     torch.cuda.synchronize()
     assert torch.equal(z1, zb) and torch.equal(i1, ib)
+    assert tk.check_guards() == 0
     tk.close()
 
 
@@ -93,6 +97,7 @@ def test_streams_in_mixed_batches_equal_streams_alone(P):
             _, idx = tk.encode(x[:, a:b].contiguous(), video=v)
             ids.append(idx)
             xs.append(tk.decode(idx, H, W, video=v, first_chunk=(k == 0)))
+        assert _L.tok_stream_check_guards(v) == 0
         tk.stream_close(v)
         alone.append((torch.cat(ids, 1), torch.cat(xs, 1)))
     # batched: stream 2 starts one step late, and a clip rides along in step 1
@@ -123,7 +128,9 @@ def test_streams_in_mixed_batches_equal_streams_alone(P):
         assert torch.equal(torch.cat(got[i][0], 1), alone[i][0]), i
         assert torch.equal(torch.cat(got[i][1], 1), alone[i][1]), i
     for v in vids:
+        assert _L.tok_stream_check_guards(v) == 0
         tk.stream_close(v)
+    assert tk.check_guards() == 0
     tk.close()
 
 
@@ -148,7 +155,9 @@ def test_batch_argument_errors(P):
     assert e.value.code == L.TOK_ENOMEM
     torch.cuda.synchronize()
     assert tk.status() == 0
+    assert _L.tok_stream_check_guards(v) == 0
     tk.stream_close(v)
+    assert tk.check_guards() == 0
     tk.close()
 
 
@@ -168,4 +177,5 @@ def test_short_lived_ctas_give_the_same_result(P, tiles):
     assert tk.status() == 0
     for a, b in zip(zr + ir + xr, zt + it + xt):
         assert torch.equal(a, b)
+    assert tk.check_guards() == 0
     tk.close()

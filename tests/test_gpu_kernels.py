@@ -267,6 +267,18 @@ def test_packets_bit_exact(P):
     np.testing.assert_array_equal(got.cpu().numpy(), ref)
 
 
+def test_guard_bands_catch_a_write_outside_the_workspace(P):
+    """The check behind every test's closing guard assertion: a byte written into the
+    arena's trailing band is reported, and the restored band passes again."""
+    from paper_2602_03529_b300 import _lib as L
+    tk = P.Tokenizer("bf16", kind="stage", ch=(64, 128))
+    assert L.tok_selftest_guards(tk.ctx) == L.TOK_ESTATE   # nothing reserved yet
+    tk.reserve(1, 5, 32, 32)
+    assert L.tok_selftest_guards(tk.ctx) == L.TOK_OK
+    assert tk.check_guards() == L.TOK_OK
+    tk.close()
+
+
 def test_bounded_wait_times_out_and_context_survives(P):
     from paper_2602_03529_b300 import _lib as L
     tk = P.Tokenizer("bf16", kind="stage", ch=(64, 128))

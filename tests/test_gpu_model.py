@@ -102,6 +102,7 @@ def run_case(P, prec, arch_kw, oarch, N, T, H, W, seed=0, decode=True):
         torch.cuda.synchronize()
         rep["x_err"] = float(np.abs(xh.cpu().numpy() - xh_ref).max())
         rep["x_shape_ok"] = xh.shape == xh_ref.shape
+    assert tk.check_guards() == 0
     tk.close()
     return rep
 
@@ -167,4 +168,5 @@ def test_t_stem_validation(P):
     with pytest.raises(L.TokError) as e:
         tk.latent_shape(13, 64, 64)        # a clip's T - 1 must be a multiple of 8
     assert e.value.code == L.TOK_ESHAPE
+    assert tk.check_guards() == 0
     tk.close()

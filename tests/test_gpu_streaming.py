@@ -13,6 +13,8 @@ import numpy as np
 import pytest
 import torch
 
+from paper_2602_03529_b300 import _lib as _L
+
 import synthetic as S
 
 pytestmark = pytest.mark.gpu
@@ -45,8 +47,10 @@ def _run(P, prec, kw, T, H, W, seed=0):
     xs = [tk.decode(idx, H, W, video=vid, first_chunk=(k == 0)) for k, idx in enumerate(ids)]
     torch.cuda.synchronize()
     assert tk.status() == 0
+    assert _L.tok_stream_check_guards(vid) == 0
     tk.stream_close(vid)
     out = dict(z=(torch.cat(zs, 1), z_c), idx=(torch.cat(ids, 1), idx_c), x=(torch.cat(xs, 1), xh_c))
+    assert tk.check_guards() == 0
     tk.close()
     return out
 
@@ -90,5 +94,7 @@ def test_stream_rejects_wrong_chunk_sizes(P):
     tk.stream_reset(vid)
     tk.encode(x4[:, :1].contiguous(), video=vid)      # after a reset: a new first chunk
     torch.cuda.synchronize()
+    assert _L.tok_stream_check_guards(vid) == 0
     tk.stream_close(vid)
+    assert tk.check_guards() == 0
     tk.close()

@@ -76,6 +76,7 @@ def _run(P, prec, ch, shape, rate=0.2, seed=7, step=3, margin_keep=None, blocks=
         off += n
         ref = gref[name]
         rel[name] = float(np.linalg.norm(gg - ref) / max(np.linalg.norm(ref), 1e-30))
+    assert tk.check_guards() == 0
     tk.close()
     return loss, loss_ref, rel
 
@@ -151,6 +152,7 @@ def test_sgd_reduces_loss_and_autograd_node(P):
     torch.cuda.synchronize()
     assert torch.equal(params.grad, g2)
     assert tk.status() == 0
+    assert tk.check_guards() == 0
     tk.close()
 
 
@@ -177,7 +179,9 @@ def test_repacked_weights_equal_fresh_context(P):
     assert tk.status() == 0 and tk2.status() == 0
     assert torch.equal(l1, l2)
     assert torch.equal(g1, g2)
+    assert tk.check_guards() == 0
     tk.close()
+    assert tk2.check_guards() == 0
     tk2.close()
 
 
@@ -214,6 +218,7 @@ def test_recompute_and_keep_modes_give_equal_gradients(P, prec):
             with pytest.raises(L.TokError) as e:
                 tr.backward()
             assert e.value.code == L.TOK_ESTATE
+        assert tk.check_guards() == 0
         tk.close()
     assert torch.equal(out[True][0], out[False][0])
     assert torch.equal(out[True][1], out[False][1])
@@ -248,6 +253,7 @@ def test_fp32_gradient_elementwise(P):
         tol = 1e-4 * np.abs(ref).max() + 1e-3 * np.abs(ref) + 1e-30
         r = float((np.abs(gg - ref) / tol).max())
         worst = max(worst, (name, r), key=lambda t: t[1])
+    assert tk.check_guards() == 0
     tk.close()
     print("fp32 elementwise worst (error / tolerance)", worst)
     assert worst[1] <= 1.0, worst
@@ -347,6 +353,7 @@ def test_bf16_sampled_gradients_at_training_shape(P):
         worst[name + " dX"] = float(r.max())
     print("sampled gradients, worst error / tolerance:", worst)
     assert max(worst.values()) <= 1.0, worst
+    assert tk.check_guards() == 0
     tk.close()
     tk2 = P.Tokenizer("bf16")
     tk2.set_params(p)
@@ -356,4 +363,5 @@ def test_bf16_sampled_gradients_at_training_shape(P):
     torch.cuda.synchronize()
     assert tk2.status() == 0
     assert torch.equal(g, g2)
+    assert tk2.check_guards() == 0
     tk2.close()
