@@ -6,6 +6,7 @@
 // context's device status word and reports failure, so that a kernel can
 // release its resources and return instead of hanging.
 #pragma once
+#include <atomic>
 
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -254,6 +255,23 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
 __device__ __forceinline__ float2 unpack_bf16x2(uint32_t u) {
     __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&u);
     return __bfloat1622float2(h);
+}
+
+
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) for a kernel once per device: the
+// attribute belongs to the device current at the call, so a process that drives two
+// devices sets it on each. done: the caller's static bit set of devices done (a race
+// only repeats the call, which is idempotent).
+template <typename Kernel>
+inline cudaError_t smem_attr_once(Kernel kernel, int bytes, std::atomic<unsigned long long>& done) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
+    if (bit && (done.load(std::memory_order_relaxed) & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_relaxed);
+    return e;
 }
 
 }  // namespace tok

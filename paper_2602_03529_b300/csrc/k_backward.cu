@@ -906,15 +906,10 @@ int launch_gn_silu_bwd(const T* x, const T* dy, const float2* stats, const float
     if (C % V || C % G || vpv > NT || (vpv & (vpv - 1)) || vpt < 1 || vpt > GN_BWD_VPT ||
         (long long)S * NT * vpt < HW * C / V)
         return (int)cudaErrorInvalidValue;
-    static bool ready = false;
-    if (!ready) {
-        if (cudaFuncSetAttribute(gn_bwd_reduce_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 2 * GN_BWD_SEGS * GN_BWD_SEG) != cudaSuccess ||
-            cudaFuncSetAttribute(gn_bwd_apply_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 3 * GN_BWD_SEGS * GN_BWD_SEG) != cudaSuccess)
-            return (int)cudaGetLastError();
-        ready = true;
-    }
+    static std::atomic<unsigned long long> done_r{0}, done_a{0};
+    if (smem_attr_once(gn_bwd_reduce_kernel<T>, 2 * GN_BWD_SEGS * GN_BWD_SEG, done_r) != cudaSuccess ||
+        smem_attr_once(gn_bwd_apply_kernel<T>, 3 * GN_BWD_SEGS * GN_BWD_SEG, done_a) != cudaSuccess)
+        return (int)cudaGetLastError();
     GnBwdArgs<T> a;
     a.x = x;
     a.dy = dy;

@@ -1305,12 +1305,8 @@ int launch_bn(const ConvArgs* as, const TcGeo* gs, int count, int num_sms, int c
         B.na = std::min(4, C::SPLIT_ACT_BYTES / B.act_slot);
         if (B.na < 2 || B.w_rows != BN) return -1;
     }
-    static bool attr_set = false;
-    if (!attr_set) {
-        if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) != cudaSuccess)
-            return -1;
-        attr_set = true;
-    }
+    static std::atomic<unsigned long long> attr_done{0};
+    if (smem_attr_once(kern, C::SMEM, attr_done) != cudaSuccess) return -1;
     // persistent (one CTA per SM), or CTAs of at most cta_tiles tiles each
     long long grid = std::min<long long>(total, num_sms);
     if (cta_tiles > 0) grid = std::max(grid, std::min<long long>((total + cta_tiles - 1) / cta_tiles, 1LL << 30));

@@ -378,13 +378,9 @@ int gn_stats_batch(const GnBatch<T, MAXP>& B, long long blocks, long long rows, 
 template <typename T, bool FAST, int MAXP>
 int gn_apply_launch(const GnBatch<T, MAXP>& B, long long blocks, int C, int G, const float* gamma, const float* beta,
                     int* status, cudaStream_t stream) {
-    static bool ready = false;
-    if (!ready) {
-        if (cudaFuncSetAttribute(gn_apply_kernel<T, FAST, MAXP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 GN_APPLY_SMEM) != cudaSuccess)
-            return (int)cudaGetLastError();
-        ready = true;
-    }
+    static std::atomic<unsigned long long> done{0};
+    if (smem_attr_once(gn_apply_kernel<T, FAST, MAXP>, GN_APPLY_SMEM, done) != cudaSuccess)
+        return (int)cudaGetLastError();
     gn_apply_kernel<T, FAST, MAXP><<<(unsigned)blocks, NT, GN_APPLY_SMEM, stream>>>(B, C, G, gamma, beta, status,
                                                                                    2000000000ull);
     return (int)cudaGetLastError();

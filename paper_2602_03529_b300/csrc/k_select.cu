@@ -738,13 +738,9 @@ int launch_similarity_mask(const int32_t* idx_p, const int32_t* idx_i, long long
         t.shift = pl.shift;
         t.nhi = pl.nhi;
         t.prod = pl.prod;
-        static bool attr_b = false;
-        if (!attr_b) {
-            if (cudaFuncSetAttribute(select_bucket_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)(SB_MAX_TOKENS * 4)) != cudaSuccess)
-                return (int)cudaGetLastError();
-            attr_b = true;
-        }
+        static std::atomic<unsigned long long> attr_b{0};
+        if (smem_attr_once(select_bucket_kernel, (int)(SB_MAX_TOKENS * 4), attr_b) != cudaSuccess)
+            return (int)cudaGetLastError();
         select_bucket_kernel<<<(unsigned)frames, SB_THREADS, (size_t)HW * 4, s>>>(idx_p, idx_i, t, f, Tp, Hq, Wq, k,
                                                                                   zero_index, out, keep_bits, sim);
         return (int)cudaGetLastError();
@@ -758,12 +754,9 @@ int launch_similarity_mask(const int32_t* idx_p, const int32_t* idx_i, long long
         const int ntab = prod < DIGIT_TAB ? prod : DIGIT_TAB;
         digit_table_kernel<<<blocks_for(ntab, 256), 256, 0, s>>>(f, ntab, tab);
         const size_t smem = (size_t)HW * 4;
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(select_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(FUSED_MAX_TOKENS * 4));
-            attr = true;
-        }
+        static std::atomic<unsigned long long> attr{0};
+        if (smem_attr_once(select_fused_kernel, (int)(FUSED_MAX_TOKENS * 4), attr) != cudaSuccess)
+            return (int)cudaGetLastError();
         select_fused_kernel<<<(unsigned)frames, FS_THREADS, smem, s>>>(idx_p, idx_i, tab, ntab, f, Tp, Hq, Wq, k,
                                                                        zero_index, out, keep_bits, sim);
         return (int)cudaGetLastError();

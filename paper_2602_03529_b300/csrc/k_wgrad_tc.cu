@@ -440,11 +440,8 @@ int launch_bn(const __nv_bfloat16* dy, const __nv_bfloat16* x, const WgradArgs& 
     if (!encode_act_map(&mdy, dy, a.N * a.Tout, a.Hout, a.Wout, a.Cdy, g.BH, g.BW, false, 64)) return -1;
     if (!encode_act_map(&mx, x, a.N * a.Tin, a.Hin, a.Win, a.Cin, HT ? g.BH + 2 : g.BH, g.BW, g.strided != 0, 64))
         return -1;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(wgrad_tc_kernel<BN, HT>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
-        attr = true;
-    }
+    static std::atomic<unsigned long long> attr{0};
+    if (smem_attr_once(wgrad_tc_kernel<BN, HT>, C::SMEM, attr) != cudaSuccess) return (int)cudaGetLastError();
     const long long grid = (long long)g.m_tiles * g.n_tiles * g.taps * g.S;
     wgrad_tc_kernel<BN, HT><<<(unsigned)grid, 192, C::SMEM, s>>>(mdy, mx, a, g, part, status, wait_ns);
     return (int)cudaGetLastError();
