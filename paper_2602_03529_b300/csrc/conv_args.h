@@ -167,6 +167,25 @@ struct GatherGeo {
     int Kpad;
 };
 
+// One problem of the fused BF16 stem (k_stem_tc.cu): the causal 3x3x3 conv with
+// stride (st, 2, 2) from the pixels x (N, Tin, H, W, 3) to out (N, Tout, H/2,
+// W/2, Cout), frames before the clip taken from hist (N, hist_T, H, W, 3) when
+// it is given, else frame 0 (pad_mode 0) or zeros; zeros outside the frame.
+struct StemArgs {
+    const void* x;
+    const void* hist;  // or null
+    int hist_T;
+    int N, Tin, H, W;
+    int Tout, st, t_off, pad_mode;
+    const void* w;       // packed (Cout_pad, Kpad) bf16, K = (dt, dh, dw, ci), zeros from 81 on
+    const float* bias;   // (Cout) or null
+    int Cout, Cout_pad, Kpad;
+    void* out;           // bf16
+    GnTriple* gn_part;   // GroupNorm statistics (N * Tout, stem_tc_gn_slots, 32) triples, or null
+    int* status;
+    unsigned long long wait_ns;
+};
+
 // One weight-gradient problem: dY of a conv (N,Tout,Hout,Wout,Cdy) against its input
 // (N,Tin,Hin,Win,Cin); same tap rule as the forward conv.
 struct WgradArgs {

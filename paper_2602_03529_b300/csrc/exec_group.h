@@ -70,8 +70,9 @@ struct GroupExec : Exec {
 
     // ------------------------------------------------------------ launches
 
-    void launch_group(ConvArgs* as, const ConvW& cw) {
+    void launch_group(ConvArgs* as, const ConvW& cw, int n = -1) {
         if (err) return;
+        const int P = n < 0 ? this->P : n;
         double flop = 0;
         for (int p = 0; p < P; ++p)
             flop += 2.0 * (double)as[p].N * as[p].Tout * as[p].Hout * as[p].Wout * cw.Cout *
@@ -162,14 +163,18 @@ struct GroupExec : Exec {
 
     // Conv over each problem's im2col matrix (BF16 path), a 1x1x1 conv over
     // (N, Tout, Hout, Wout, Kpad).
-    MAct conv_gathered(const std::string& name, const MAct& dims, void* const* outs, int mode, int32_t* const* idx) {
+    // Problems with skip[p] set are left out (their outputs are not touched).
+    MAct conv_gathered(const std::string& name, const MAct& dims, void* const* outs, int mode, int32_t* const* idx,
+                       const bool* skip = nullptr) {
         const ConvW& cw = c->convs[c->cindex[name]];
         ConvArgs as[kMaxConvGroup];
         MAct out;
+        int n = 0;
         for (int p = 0; p < P; ++p) {
+            if (skip && skip[p]) continue;
             const Act& d = dims[p];
             Act in{pr[p].w.gather, d.N, d.T, d.H, d.W, cw.Kpad};
-            ConvArgs& a = as[p];
+            ConvArgs& a = as[n++];
             a = base_args(cw, in, 1, 1, 1);
             a.Cin = cw.Kpad;
             a.kt = a.kh = a.kw = 1;
@@ -185,7 +190,7 @@ struct GroupExec : Exec {
             out[p] = Act{outs[p], d.N, d.T, d.H, d.W, cw.Cout};
             tag_gn_stats(out[p], a);
         }
-        launch_group(as, cw);
+        if (n) launch_group(as, cw, n);
         return out;
     }
 
@@ -252,9 +257,10 @@ struct GroupExec : Exec {
     // path edge-pads. A stem with temporal stride 2 sees a stream's later
     // chunks start one frame after an output frame, as the stride-2 convs do.
     MAct first_input(const char* name, const void* const* x, const int* N, const int* T, const int* H, const int* W,
-                     int stride_hw, int stride_t) {
+                     int stride_hw, int stride_t, const bool* skip = nullptr) {
         MAct dims;
         for (int p = 0; p < P; ++p) {
+            if (skip && skip[p]) continue;
             const Dims d = clip_dims(c, T[p], H[p], W[p]);
             if (c->bf16()) {
                 GatherGeo g = gather_pixels(N[p], T[p], H[p], W[p], d.Hp, d.Wp, stride_hw);
@@ -281,6 +287,38 @@ struct GroupExec : Exec {
             }
         }
         return dims;
+    }
+
+    // BF16 stem with its im2col rows formed on chip (one launch, no gather pass)
+    // for the problems whose frame needs no edge extension: done[p] marks them
+    // (the others take the im2col gather and the 1x1x1 conv), so that a problem
+    // takes the same path in a group as alone. A stream's later chunks read the
+    // two frames before them from its history, as the gather does.
+    void stem_fused(const char* name, const void* const* x, const int* N, const int* T, const int* H, const int* W,
+                    int stride_t, void* const* outs, MAct* X, bool* done) {
+        for (int p = 0; p < P; ++p) done[p] = false;
+        if (!c->bf16()) return;
+        const ConvW& cw = c->convs[c->cindex[name]];
+        StemArgs as[kMaxConvGroup];
+        int at[kMaxConvGroup];
+        int n = 0;
+        for (int p = 0; p < P; ++p) {
+            const Dims d = clip_dims(c, T[p], H[p], W[p]);
+            if (d.Hp != H[p] || d.Wp != W[p]) continue;
+            GatherGeo g = gather_pixels(N[p], T[p], H[p], W[p], d.Hp, d.Wp, 2);
+            const __nv_bfloat16* ph = stream_hist_pixels(p, g, name);
+            as[n] = stem_args(cw, x[p], ph, N[p], T[p], H[p], W[p], stride_t, ph && stride_t == 2 ? -1 : -2, outs[p],
+                              pr[p].w);
+            if (!stem_tc_accepts(&as[n], 1)) continue;
+            at[n++] = p;
+        }
+        if (!n || !stem_launch(as, n, cw)) return;
+        for (int i = 0; i < n; ++i) {
+            const int p = at[i];
+            stream_update(p, name, x[p], T[p]);
+            (*X)[p] = stem_out(as[i]);
+            done[p] = true;
+        }
     }
 
     // Last encoder conv: latent z (fp32) and FSQ token indices.
@@ -336,11 +374,20 @@ struct GroupExec : Exec {
             out_conv("stage.out", A, z, idx);
             return;
         }
-        MAct in = first_input("enc.stem", x, N, T, H, W, 2, ar.t_stem);
-        if (c->bf16())
-            X = conv_gathered("enc.stem", in, s0, OUT_PLAIN, nullptr);
-        else
-            X = conv("enc.stem", in, s0, nullptr, ar.t_stem, 2, 2);
+        bool fused[kMaxConvGroup];
+        stem_fused("enc.stem", x, N, T, H, W, ar.t_stem, s0, &X, fused);
+        int nf = 0;
+        for (int p = 0; p < P; ++p) nf += fused[p] ? 1 : 0;
+        if (nf < P) {
+            MAct in = first_input("enc.stem", x, N, T, H, W, 2, ar.t_stem, fused);
+            if (c->bf16()) {
+                const MAct G = conv_gathered("enc.stem", in, s0, OUT_PLAIN, nullptr, fused);
+                for (int p = 0; p < P; ++p)
+                    if (!fused[p]) X[p] = G[p];
+            } else {
+                X = conv("enc.stem", in, s0, nullptr, ar.t_stem, 2, 2);
+            }
+        }
         for (int l = 0; l < ar.nlevels; ++l) {
             for (int b = 0; b < ar.blocks; ++b) ix = block("enc.l" + std::to_string(l) + ".b" + std::to_string(b), ix, X);
             if (l < ar.nlevels - 1) {

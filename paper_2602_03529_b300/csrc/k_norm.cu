@@ -101,6 +101,7 @@ struct GnProb {
     int vpt, S;             // vectors per thread, chunks per frame (apply and statistics passes)
     Triple* part;           // (frames, Sp, G) statistics slots
     int Sp;                 // slots per frame: S, or those of the producing conv
+    int pre;                // the producing conv reduced the slots (no statistics pass)
     float2* stats;          // (frames, G): mean, rstd
     long long blk_end, row_end;
 };
@@ -129,6 +130,7 @@ __global__ void __launch_bounds__(NT) gn_partial_kernel(const __grid_constant__ 
     __shared__ Triple red[NT][NGV];
     long long lb;
     const GnProb<T>& P = B.p[gn_block_problem(B, blockIdx.x, &lb)];
+    if (P.pre) return;  // statistics from the producing conv
     const long long vec_per_frame = P.vpf;
     const int S = P.S, vpt = P.vpt;
     const int frame = (int)(lb / S), chunk = (int)(lb % S), tid = threadIdx.x;
@@ -329,7 +331,8 @@ size_t gn_scratch_bytes(long long frames, long long HW, int C, int G, int num_sm
 namespace {
 
 // Plan a batch: per-problem chunking, scratch carving, block numbering.
-// pre: every item has precomputed statistics (used instead of the statistics pass)
+// pre: an item's precomputed statistics (GnItem::part), where it has them, are used
+// instead of the statistics pass, item by item
 template <typename T, int MAXP>
 bool gn_batch(const GnItem<T>* items, int count, int C, int G, GnBatch<T, MAXP>* B, long long* blocks,
               long long* rows, bool pre = false) {
@@ -345,8 +348,9 @@ bool gn_batch(const GnItem<T>* items, int count, int C, int G, GnBatch<T, MAXP>*
         P.vpf = items[p].HW * C / V;
         gn_plan(P.frames, P.vpf, 0, &P.vpt, &P.S);
         Triple* own = static_cast<Triple*>(items[p].scratch);
-        P.part = pre ? const_cast<Triple*>(items[p].part) : own;
-        P.Sp = pre ? items[p].part_S : P.S;
+        P.pre = pre && items[p].part != nullptr && items[p].part_S > 0 ? 1 : 0;
+        P.part = P.pre ? const_cast<Triple*>(items[p].part) : own;
+        P.Sp = P.pre ? items[p].part_S : P.S;
         P.stats = reinterpret_cast<float2*>(
             (reinterpret_cast<uintptr_t>(own + P.frames * P.S * G) + 15) & ~uintptr_t(15));
         nb += P.frames * P.S;
@@ -365,7 +369,11 @@ int gn_stats_batch(const GnBatch<T, MAXP>& B, long long blocks, long long rows, 
     constexpr int V = Vec<T>::N;
     const int cg = C / G;
     const int ngv = cg >= V ? 1 : V / cg;
-    if (!pre) switch (ngv) {
+    // the statistics pass, unless every item has its statistics (its blocks of such
+    // items return at once)
+    bool all_pre = pre;
+    for (int p = 0; p < B.count; ++p) all_pre = all_pre && B.p[p].pre;
+    if (!all_pre) switch (ngv) {
         case 1: gn_partial_kernel<T, 1, MAXP><<<(unsigned)blocks, NT, 0, stream>>>(B, C, G); break;
         case 2: gn_partial_kernel<T, 2, MAXP><<<(unsigned)blocks, NT, 0, stream>>>(B, C, G); break;
         case 4: gn_partial_kernel<T, 4, MAXP><<<(unsigned)blocks, NT, 0, stream>>>(B, C, G); break;
@@ -391,10 +399,8 @@ int gn_silu_batch(const GnItem<T>* items, int count, int C, int G, const float* 
                   bool fast, cudaStream_t stream, int* status) {
     GnBatch<T, MAXP> B;
     long long blocks, rows;
-    bool pre = true;
-    for (int p = 0; p < count; ++p) pre = pre && items[p].part != nullptr && items[p].part_S > 0;
-    if (!gn_batch(items, count, C, G, &B, &blocks, &rows, pre)) return 0;
-    if (const int e = gn_stats_batch(B, blocks, rows, C, G, eps, stream, pre)) return e;
+    if (!gn_batch(items, count, C, G, &B, &blocks, &rows, true)) return 0;
+    if (const int e = gn_stats_batch(B, blocks, rows, C, G, eps, stream, true)) return e;
     return fast ? gn_apply_launch<T, true, MAXP>(B, blocks, C, G, gamma, beta, status, stream)
                 : gn_apply_launch<T, false, MAXP>(B, blocks, C, G, gamma, beta, status, stream);
 }

@@ -1,0 +1,599 @@
+// The encoder's stem on the tensor cores with its im2col rows formed on chip:
+// the causal 3x3x3 conv from the 3 pixel channels to the first level's Cout
+// channels (64 or 128), stride (st, 2, 2) (Sec. 2.4's encoder input; the 8x8x8
+// setting of Sec. 4.1 uses st = 2), plus its bias, the BF16 output and the
+// GroupNorm statistics of that output, in one persistent kernel.
+//
+// Tile: 128 consecutive output voxels of one output row, (n, to, ho, wo0 ..
+// wo0 + 127): the MMA's M = 128 (TMEM lane = voxel), N = Cout channels, K =
+// (dt, dh, dw, ci) = 81 taps x channels, zero-padded to 96 (six K = 16 steps).
+// The input a tile reads -- 3 frames x 3 rows x the 257 pixels (771 BF16
+// values, x = 3 w + ci) of its window -- arrives by TMA as 12 boxes of 3 rows
+// x 200 values; the TMA's zero fill gives the spatial zero padding (the frame
+// needs no edge extension: H and W are the padded extent), frames before the
+// clip come from the stream history, frame 0 or a zero box.
+//
+// Warp roles (512 threads, one CTA per SM):
+//   warp 0      TMA producer (weights once, then the input boxes per tile)
+//   warp 1      MMA issuer: six tcgen05.mma into one of two TMEM accumulators
+//   warp 2      TMEM allocation
+//   warp 3      output: TMA store of the staged tile; merges the statistics
+//   warps 4-7   im2col: thread v writes row v of the A tile (128B-swizzled,
+//               K-major) from the input boxes
+//   warps 8-15  epilogue: TMEM -> + bias -> BF16 -> staging tile, and the
+//               statistics of its 32 voxels x Cout/2 channels
+// Every wait is bounded; a wait that gives up records TOK_ETIMEOUT and every
+// role leaves its loop, drains its own copies and MMAs, and the CTA frees TMEM.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstring>
+
+#include "common.cuh"
+#include "conv_args.h"
+#include "launchers.h"
+
+namespace tok {
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn();
+bool encode_w_map(CUtensorMap* m, const void* base, int rows, int Kpad, int BN, int kc);
+
+namespace {
+
+constexpr int SV = 128;                    // output voxels per tile
+constexpr int XB = 200;                    // BF16 values per input box row
+constexpr int NXB = 4;                     // boxes along x: 800 >= 6 * 127 + 14
+constexpr int BOXB = 1280;                 // 3 rows x 200 values (1200 B), 128-byte aligned
+constexpr int RAWB = 3 * NXB * BOXB;       // one tile's input boxes
+constexpr uint32_t RAW_TX = 3 * NXB * 3 * XB * 2;
+constexpr int KSTEPS = 6;                  // K = 96
+constexpr int NTHREADS = 512;
+
+template <int CO>
+struct StemCfg {
+    static constexpr int W_ATOM = CO * 128;       // 64 K values of every weight row, SW128
+    static constexpr int A_ATOM = SV * 128;       // 64 K values of every voxel row, SW128
+    static constexpr int A_STAGE = 2 * A_ATOM;
+    static constexpr int NOB = CO / 64;           // 64-channel boxes of an output tile
+    static constexpr int O_BOX = SV * 128;
+    static constexpr int O_BUF = NOB * O_BOX;
+    static constexpr int OFF_W = 0;
+    static constexpr int OFF_A = 2 * W_ATOM;
+    static constexpr int OFF_O = OFF_A + 2 * A_STAGE;
+    static constexpr int OFF_RAW = OFF_O + 2 * O_BUF;
+    static constexpr int OFF_BIAS = OFF_RAW + 2 * RAWB;
+    // statistics of a tile per buffer: shifts K[4][32], sums (s, q)[4][32], counts n[4]
+    static constexpr int OFF_STK = OFF_BIAS + CO * 4;
+    static constexpr int OFF_STSQ = OFF_STK + 2 * 4 * 32 * 4;
+    static constexpr int OFF_STN = OFF_STSQ + 2 * 4 * 32 * 8;
+    static constexpr int OFF_BAR = OFF_STN + 2 * 4 * 4;
+    static constexpr int NBAR = 17;
+    static constexpr int SMEM = OFF_BAR + NBAR * 8 + 8 + 1024;  // + TMEM address, + alignment slack
+    static constexpr int TMEM_COLS = 2 * CO;
+    static constexpr uint32_t IDESC = idesc_bf16_f32(128, CO);
+    static_assert(OFF_A % 1024 == 0 && OFF_O % 1024 == 0 && OFF_RAW % 1024 == 0, "swizzle atoms");
+    static_assert(SMEM <= 232448 - 64, "shared memory");
+};
+
+struct StemProb {
+    CUtensorMap tm_x, tm_h, tm_o;
+    long long tile_end;  // tiles of the problems up to this one
+    GnTriple* gn_part;
+    int N, Tin, hist_T, Tout, Hout, Wout, st, t_off, pad_mode, tiles_w, has_hist;
+};
+
+template <int MAXP>
+struct StemBatch {
+    CUtensorMap tm_w;
+    StemProb q[MAXP];
+    const float* bias;
+    int* status;
+    unsigned long long wait_ns;
+    long long num_tiles;
+    int count;
+};
+
+struct StemTile {
+    int p, n, to, ho, tw;
+};
+
+template <int MAXP>
+__device__ __forceinline__ StemTile stem_tile(const StemBatch<MAXP>& B, long long u) {
+    StemTile t;
+    int p = 0;
+    if constexpr (MAXP > 1)
+        while (p + 1 < B.count && u >= B.q[p].tile_end) ++p;
+    long long lu = p ? u - B.q[p - 1].tile_end : u;
+    const StemProb& q = B.q[p];
+    t.p = p;
+    t.tw = (int)(lu % q.tiles_w);
+    lu /= q.tiles_w;
+    t.ho = (int)(lu % q.Hout);
+    lu /= q.Hout;
+    t.to = (int)(lu % q.Tout);
+    t.n = (int)(lu / q.Tout);
+    return t;
+}
+
+// Frame coordinate of input frame ti of sample n and the map it is read from:
+// the clip, the history before it, frame 0 (replicate padding) or -1 (a box
+// wholly outside the tensor: zeros).
+__device__ __forceinline__ int stem_frame(const StemProb& q, int n, int ti, const CUtensorMap** m) {
+    *m = &q.tm_x;
+    if (ti >= q.Tin) return -1;
+    if (ti >= 0) return n * q.Tin + ti;
+    if (q.has_hist) {
+        *m = &q.tm_h;
+        return n * q.hist_T + q.hist_T + ti;
+    }
+    return q.pad_mode == 0 ? n * q.Tin : -1;
+}
+
+// Every lane waits; the warp goes on only if all of them saw the phase.
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, int* status, unsigned long long ns) {
+    const bool ok = mbar_wait(bar, parity, status, ns);
+    return __all_sync(0xffffffffu, ok);
+}
+
+// 16 bits (half ha of a, half hb of b) -> one word, a's half in the low bits.
+__device__ __forceinline__ uint32_t pick2(uint32_t a, int ha, uint32_t b, int hb) {
+    return __byte_perm(a, b, (unsigned)((ha ? 0x32 : 0x10) | ((hb ? 0x76 : 0x54) << 8)));
+}
+
+__device__ __forceinline__ GnTriple stem_merge(GnTriple a, GnTriple b) {
+    if (b.n == 0.f) return a;
+    if (a.n == 0.f) return b;
+    GnTriple r;
+    r.n = a.n + b.n;
+    const float d = b.mean - a.mean;
+    const float fb = b.n / r.n;
+    r.mean = a.mean + d * fb;
+    r.m2 = a.m2 + b.m2 + d * d * a.n * fb;
+    return r;
+}
+
+__device__ __forceinline__ uint32_t ld_shared_u32(const uint8_t* p) {
+    return *reinterpret_cast<const uint32_t*>(p);
+}
+
+template <int CO, int MAXP>
+__global__ void __launch_bounds__(NTHREADS, 1) stem_tc_kernel(const __grid_constant__ StemBatch<MAXP> B) {
+    using C = StemCfg<CO>;
+    extern __shared__ uint8_t smem_dyn[];
+    uint8_t* smem = smem_dyn + ((1024u - (smem_u32(smem_dyn) & 1023u)) & 1023u);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::OFF_BAR);
+    uint64_t* raw_full = bars;        // [2] TMA bytes of a tile's input boxes
+    uint64_t* raw_empty = bars + 2;   // [2] 4 im2col warps
+    uint64_t* a_full = bars + 4;      // [2] 4 im2col warps
+    uint64_t* a_empty = bars + 6;     // [2] MMA commit
+    uint64_t* t_full = bars + 8;      // [2] MMA commit
+    uint64_t* t_empty = bars + 10;    // [2] 8 epilogue warps
+    uint64_t* o_ready = bars + 12;    // [2] 8 epilogue warps
+    uint64_t* o_free = bars + 14;     // [2] output warp
+    uint64_t* w_full = bars + 16;     // weights
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + C::NBAR);
+    float* sbias = reinterpret_cast<float*>(smem + C::OFF_BIAS);
+
+    int* status = B.status;
+    const unsigned long long wait_ns = B.wait_ns;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const long long cid = blockIdx.x, ncl = gridDim.x;
+    // a context already in error skips the launch (decided once per CTA)
+    __shared__ int s_skip;
+    if (threadIdx.x == 0) s_skip = (status && *(volatile int*)status != 0) ? 1 : 0;
+    __syncthreads();
+    if (s_skip) return;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&raw_full[i], 1);
+            mbar_init(&raw_empty[i], 4);
+            mbar_init(&a_full[i], 4);
+            mbar_init(&a_empty[i], 1);
+            mbar_init(&t_full[i], 1);
+            mbar_init(&t_empty[i], 8);
+            mbar_init(&o_ready[i], 8);
+            mbar_init(&o_free[i], 1);
+        }
+        mbar_init(w_full, 1);
+        fence_mbar_init();
+    }
+    for (int i = threadIdx.x; i < CO; i += NTHREADS) sbias[i] = B.bias ? B.bias[i] : 0.f;
+    if (warp == 0 && lane < B.count) {
+        tma_prefetch_desc(&B.q[lane].tm_x);
+        if (B.q[lane].has_hist) tma_prefetch_desc(&B.q[lane].tm_h);
+        tma_prefetch_desc(&B.q[lane].tm_o);
+    }
+    if (warp == 2) {
+        tmem_alloc(tmem_slot, C::TMEM_COLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------------------------------------------- TMA producer
+            mbar_arrive_expect_tx(w_full, 2 * C::W_ATOM);
+            tma_load_2d(smem + C::OFF_W, &B.tm_w, w_full, 0, 0);
+            tma_load_2d(smem + C::OFF_W + C::W_ATOM, &B.tm_w, w_full, 64, 0);
+            int last[2] = {-1, -1};
+            int it = 0;
+            for (long long u = cid; u < B.num_tiles; u += ncl, ++it) {
+                const int s = it & 1;
+                const uint32_t ph = (uint32_t)((it >> 1) & 1);
+                if (!mbar_wait(&raw_empty[s], ph ^ 1, status, wait_ns)) break;
+                const StemTile t = stem_tile(B, u);
+                const StemProb& q = B.q[t.p];
+                uint8_t* dst = smem + C::OFF_RAW + s * RAWB;
+                mbar_arrive_expect_tx(&raw_full[s], RAW_TX);
+                // x = 3 w + ci from the window's first pixel 2 wo0 - 1, rounded down to a
+                // 16-byte boundary (8 values): x0 = 6 wo0 - 8
+                const int x0 = t.tw * (6 * SV) - 8, h0 = 2 * t.ho - 1;
+#pragma unroll
+                for (int dt = 0; dt < 3; ++dt) {
+                    const CUtensorMap* m;
+                    const int f = stem_frame(q, t.n, t.to * q.st + dt + q.t_off, &m);
+#pragma unroll
+                    for (int b = 0; b < NXB; ++b)
+                        tma_load_3d(dst + (dt * NXB + b) * BOXB, m, &raw_full[s], x0 + b * XB, h0, f);
+                }
+                last[s] = (int)ph;
+            }
+            // no copy may still be in flight when the CTA exits
+            for (int i = 0; i < 2; ++i)
+                if (last[i] >= 0) mbar_wait(&raw_full[i], (uint32_t)last[i], status, wait_ns);
+            mbar_wait(w_full, 0, status, wait_ns);
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------------------------------------------- MMA issuer
+            int last[2] = {-1, -1};
+            if (mbar_wait(w_full, 0, status, wait_ns)) {
+                tc_fence_after();
+                const uint32_t wa = smem_u32(smem + C::OFF_W);
+                int it = 0;
+                for (long long u = cid; u < B.num_tiles; u += ncl, ++it) {
+                    const int s = it & 1;
+                    const uint32_t ph = (uint32_t)((it >> 1) & 1);
+                    if (!mbar_wait(&t_empty[s], ph ^ 1, status, wait_ns)) break;
+                    if (!mbar_wait(&a_full[s], ph, status, wait_ns)) break;
+                    tc_fence_after();
+                    const uint32_t aa = smem_u32(smem + C::OFF_A + s * C::A_STAGE);
+                    const uint32_t d = tmem_base + (uint32_t)(s * CO);
+#pragma unroll
+                    for (int k = 0; k < KSTEPS; ++k)
+                        tc_mma_bf16(d, sw128_desc(aa + (uint32_t)((k >> 2) * C::A_ATOM + (k & 3) * 32)),
+                                    sw128_desc(wa + (uint32_t)((k >> 2) * C::W_ATOM + (k & 3) * 32)), C::IDESC,
+                                    k ? 1u : 0u);
+                    tc_commit(&a_empty[s]);
+                    tc_commit(&t_full[s]);
+                    last[s] = (int)ph;
+                }
+            }
+            // our own MMAs complete before TMEM can be released
+            for (int i = 0; i < 2; ++i)
+                if (last[i] >= 0) mbar_wait(&t_full[i], (uint32_t)last[i], status, wait_ns);
+        }
+    } else if (warp == 3) {
+        // -------------------------------------------------------- output
+        // the staged tile goes out as Cout / 64 boxes of 64 channels x 128 voxels
+        // (voxels past the row's end are not written); lane g merges group g's
+        // statistics over the four TMEM lane quarters in a fixed order
+        int it = 0;
+        for (long long u = cid; u < B.num_tiles; u += ncl, ++it) {
+            const int s = it & 1;
+            const uint32_t ph = (uint32_t)((it >> 1) & 1);
+            if (!warp_wait(&o_ready[s], ph, status, wait_ns)) break;
+            const StemTile t = stem_tile(B, u);
+            const StemProb& pq = B.q[t.p];
+            if (lane == 0) {
+                const uint8_t* ob = smem + C::OFF_O + s * C::O_BUF;
+                const int row = (t.n * pq.Tout + t.to) * pq.Hout + t.ho;
+#pragma unroll
+                for (int b = 0; b < C::NOB; ++b) tma_store_3d(&pq.tm_o, ob + b * C::O_BOX, b * 64, t.tw * SV, row);
+                bulk_commit();
+            }
+            if (pq.gn_part) {
+                const float* stk = reinterpret_cast<const float*>(smem + C::OFF_STK) + s * 4 * 32;
+                const float2* stsq = reinterpret_cast<const float2*>(smem + C::OFF_STSQ) + s * 4 * 32;
+                const float* stn = reinterpret_cast<const float*>(smem + C::OFF_STN) + s * 4;
+                GnTriple tr[4];
+#pragma unroll
+                for (int qq = 0; qq < 4; ++qq) {
+                    const float n = stn[qq], K = stk[qq * 32 + lane];
+                    const float2 sq = stsq[qq * 32 + lane];
+                    tr[qq].n = n;
+                    tr[qq].mean = n > 0.f ? K + sq.x / n : 0.f;
+                    tr[qq].m2 = n > 0.f ? fmaxf(sq.y - sq.x * sq.x / n, 0.f) : 0.f;
+                }
+                const long long S = (long long)pq.Hout * pq.tiles_w;
+                pq.gn_part[(((long long)t.n * pq.Tout + t.to) * S + (long long)t.ho * pq.tiles_w + t.tw) * 32 + lane] =
+                    stem_merge(stem_merge(tr[0], tr[1]), stem_merge(tr[2], tr[3]));
+            }
+            if (lane == 0) bulk_wait_read_all();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&o_free[s]);
+        }
+        if (lane == 0) bulk_wait_all();
+    } else if (warp >= 4 && warp < 8) {
+        // -------------------------------------------------------- im2col
+        // Row v of the A tile is voxel v: K = 9 r + k with r = dt * 3 + dh and k = 3 dw +
+        // ci is value x = 6 v + 5 + k of input row r (x from x0). Its ten values x = 6 v +
+        // 4 .. 6 v + 13 are five aligned words (no word straddles two boxes: a box row
+        // holds an even number of values), read once per row.
+        const int v = threadIdx.x - 128;
+        uint32_t woff[5];
+#pragma unroll
+        for (int j = 0; j < 5; ++j) {
+            const int e = 6 * v + 4 + 2 * j, b = e / XB;
+            woff[j] = (uint32_t)(b * BOXB + (e - b * XB) * 2);
+        }
+        const uint32_t arow = (uint32_t)v * 128u, sw = (uint32_t)(v & 7);
+        int it = 0;
+        for (long long u = cid; u < B.num_tiles; u += ncl, ++it) {
+            const int s = it & 1;
+            const uint32_t ph = (uint32_t)((it >> 1) & 1);
+            if (!warp_wait(&raw_full[s], ph, status, wait_ns)) break;
+            if (!warp_wait(&a_empty[s], ph ^ 1, status, wait_ns)) break;
+            const uint8_t* rb = smem + C::OFF_RAW + s * RAWB;
+            uint32_t w[9][5];
+#pragma unroll
+            for (int r = 0; r < 9; ++r)
+#pragma unroll
+                for (int j = 0; j < 5; ++j)
+                    w[r][j] = ld_shared_u32(rb + ((r / 3) * NXB * BOXB + (r % 3) * XB * 2) + woff[j]);
+            // value k of row r is half k + 1 of the row's ten (word (k + 1) / 2); K >= 81 is zero
+            uint32_t o[48];
+#pragma unroll
+            for (int m = 0; m < 48; ++m) {
+                const int k0 = 2 * m, k1 = 2 * m + 1;
+                const uint32_t a = k0 < 81 ? w[k0 / 9][(k0 % 9 + 1) >> 1] : 0u;
+                const uint32_t b = k1 < 81 ? w[k1 / 9][(k1 % 9 + 1) >> 1] : 0u;
+                o[m] = pick2(a, k0 < 81 ? (k0 % 9 + 1) & 1 : 0, b, k1 < 81 ? (k1 % 9 + 1) & 1 : 0);
+            }
+            uint8_t* ab = smem + C::OFF_A + s * C::A_STAGE;
+#pragma unroll
+            for (int c = 0; c < 12; ++c) {
+                uint8_t* dst = ab + (c >> 3) * C::A_ATOM + arow + ((((uint32_t)c & 7u) ^ sw) << 4);
+                *reinterpret_cast<uint4*>(dst) = make_uint4(o[4 * c], o[4 * c + 1], o[4 * c + 2], o[4 * c + 3]);
+            }
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&a_full[s]);
+                mbar_arrive(&raw_empty[s]);
+            }
+        }
+    } else if (warp >= 8) {
+        // -------------------------------------------------------- epilogue
+        // warp (q, h): TMEM lanes 32 q .. 32 q + 31 (voxels), channels h * Cout/2 ..;
+        // GroupNorm of 32 groups: CG channels each, NG = 16 groups per warp. The
+        // statistics are those of the stored BF16 values, as shifted sums per group
+        // (the shift: lane 0's first value of the group), reduced over the warp's
+        // voxels by a butterfly that leaves group (lane >> 1) on each lane pair.
+        constexpr int HC = CO / 2;
+        constexpr int CG = CO / 32;
+        constexpr int NG = HC / CG;
+        static_assert(NG == 16, "16 groups per epilogue warp");
+        const int e = warp - 8, q = warp & 3, h = e >> 2;
+        const int v = q * 32 + lane;
+        const float* bias = sbias + h * HC;
+        int it = 0;
+        for (long long u = cid; u < B.num_tiles; u += ncl, ++it) {
+            const int s = it & 1;
+            const uint32_t ph = (uint32_t)((it >> 1) & 1);
+            if (!warp_wait(&t_full[s], ph, status, wait_ns)) break;
+            tc_fence_after();
+            const StemTile t = stem_tile(B, u);
+            const StemProb& pq = B.q[t.p];
+            const bool valid = t.tw * SV + v < pq.Wout;
+            const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(s * CO + h * HC);
+            uint32_t pk[HC / 2];
+#pragma unroll
+            for (int c32 = 0; c32 < HC / 32; ++c32) {
+                uint32_t r0[16], r1[16];
+                tmem_ld16_issue(ta + (uint32_t)(c32 * 32), r0);
+                tmem_ld16_issue(ta + (uint32_t)(c32 * 32 + 16), r1);
+                tmem_ld_wait();
+                tmem_regs_fence(r0);
+                tmem_regs_fence(r1);
+                // columns c32 * 32 + 4 i .. (r0) and c32 * 32 + 16 + 4 i .. (r1)
+                const float4* b4 = reinterpret_cast<const float4*>(bias + c32 * 32);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float4 ba = b4[i], bb = b4[4 + i];
+                    pk[c32 * 16 + 2 * i] =
+                        pack_bf16x2(__uint_as_float(r0[4 * i]) + ba.x, __uint_as_float(r0[4 * i + 1]) + ba.y);
+                    pk[c32 * 16 + 2 * i + 1] =
+                        pack_bf16x2(__uint_as_float(r0[4 * i + 2]) + ba.z, __uint_as_float(r0[4 * i + 3]) + ba.w);
+                    pk[c32 * 16 + 8 + 2 * i] =
+                        pack_bf16x2(__uint_as_float(r1[4 * i]) + bb.x, __uint_as_float(r1[4 * i + 1]) + bb.y);
+                    pk[c32 * 16 + 8 + 2 * i + 1] =
+                        pack_bf16x2(__uint_as_float(r1[4 * i + 2]) + bb.z, __uint_as_float(r1[4 * i + 3]) + bb.w);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&t_empty[s]);
+            float gs[NG], gq[NG], gk[NG];
+            const bool gstat = pq.gn_part != nullptr;
+            if (gstat) {
+#pragma unroll
+                for (int g = 0; g < NG; ++g) {
+                    float x[CG];
+#pragma unroll
+                    for (int j = 0; j < CG / 2; ++j) {
+                        const float2 f = unpack_bf16x2(pk[g * (CG / 2) + j]);
+                        x[2 * j] = f.x;
+                        x[2 * j + 1] = f.y;
+                    }
+                    gk[g] = __shfl_sync(0xffffffffu, x[0], 0);
+                    float a = 0.f, b = 0.f;
+#pragma unroll
+                    for (int j = 0; j < CG; ++j) {
+                        const float d = valid ? x[j] - gk[g] : 0.f;
+                        a += d;
+                        b = fmaf(d, d, b);
+                    }
+                    gs[g] = a;
+                    gq[g] = b;
+                }
+                // step o: a lane keeps the lower (upper if lane & o) half of its groups and
+                // adds its partner's sums of them
+#pragma unroll
+                for (int o = 16; o >= 2; o >>= 1) {
+                    const int half = o / 2;
+                    const bool up = (lane & o) != 0;
+#pragma unroll
+                    for (int i = 0; i < half; ++i) {
+                        const float rs = __shfl_xor_sync(0xffffffffu, up ? gs[i] : gs[i + half], o);
+                        const float rq = __shfl_xor_sync(0xffffffffu, up ? gq[i] : gq[i + half], o);
+                        gs[i] = (up ? gs[i + half] : gs[i]) + rs;
+                        gq[i] = (up ? gq[i + half] : gq[i]) + rq;
+                    }
+                }
+                gs[0] += __shfl_xor_sync(0xffffffffu, gs[0], 1);
+                gq[0] += __shfl_xor_sync(0xffffffffu, gq[0], 1);
+            }
+            const float nq = (float)(CG * __popc(__ballot_sync(0xffffffffu, valid)));
+            if (!warp_wait(&o_free[s], ph ^ 1, status, wait_ns)) break;
+            uint8_t* ob = smem + C::OFF_O + s * C::O_BUF;
+#pragma unroll
+            for (int j = 0; j < HC / 8; ++j) {
+                const int c0 = h * HC + 8 * j;
+                uint8_t* dst = ob + (c0 >> 6) * C::O_BOX + v * 128 + ((((c0 & 63) >> 3) ^ (v & 7)) << 4);
+                *reinterpret_cast<uint4*>(dst) = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+            }
+            if (gstat) {
+                float* stk = reinterpret_cast<float*>(smem + C::OFF_STK) + (s * 4 + q) * 32 + h * NG;
+                float2* stsq = reinterpret_cast<float2*>(smem + C::OFF_STSQ) + (s * 4 + q) * 32 + h * NG;
+                if (lane == 0) {
+#pragma unroll
+                    for (int g = 0; g < NG; ++g) stk[g] = gk[g];
+                }
+                if ((lane & 1) == 0) stsq[lane >> 1] = make_float2(gs[0], gq[0]);
+                if (lane == 0 && h == 0) reinterpret_cast<float*>(smem + C::OFF_STN)[s * 4 + q] = nq;
+            }
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&o_ready[s]);
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 2) tmem_dealloc(tmem_base, C::TMEM_COLS);
+}
+
+// Pixels as (x = 3 w + ci, h, frame), boxes of 200 values x 3 rows x 1 frame,
+// no swizzle; reads outside the tensor are zeros.
+bool encode_pixels_map(CUtensorMap* m, const void* base, long long frames, int H, int W) {
+    auto enc = get_encode_fn();
+    if (!enc) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)3 * W, (cuuint64_t)H, (cuuint64_t)frames};
+    cuuint64_t strides[2] = {(cuuint64_t)6 * W, (cuuint64_t)6 * W * H};
+    cuuint32_t box[3] = {(cuuint32_t)XB, 3, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Output as (channel, w, row = (n * Tout + t) * Hout + h), boxes of 64 channels x
+// 128 voxels, 128-byte swizzle.
+bool encode_stem_out_map(CUtensorMap* m, void* base, long long rows, int Wout, int C) {
+    auto enc = get_encode_fn();
+    if (!enc) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)C, (cuuint64_t)Wout, (cuuint64_t)rows};
+    cuuint64_t strides[2] = {(cuuint64_t)C * 2, (cuuint64_t)Wout * C * 2};
+    cuuint32_t box[3] = {64, (cuuint32_t)SV, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+bool stem_form_ok(const StemArgs& a) {
+    return (a.Cout == 64 || a.Cout == 128) && a.Cout_pad == a.Cout && a.Kpad == 128 && a.N > 0 && a.Tin > 0 &&
+           a.Tout > 0 && a.H >= 2 && a.H % 2 == 0 && a.W >= 8 && a.W % 8 == 0 && (a.st == 1 || a.st == 2) &&
+           aligned16(a.x) && aligned16(a.out) && aligned16(a.w) && (!a.hist || (aligned16(a.hist) && a.hist_T > 0));
+}
+
+template <int CO, int MAXP>
+int launch_co(const StemArgs* as, int count, int num_sms, cudaStream_t stream, int cta_tiles) {
+    using C = StemCfg<CO>;
+    auto kern = stem_tc_kernel<CO, MAXP>;
+    StemBatch<MAXP> B;
+    memset(&B, 0, sizeof(B));
+    if (!encode_w_map(&B.tm_w, as[0].w, as[0].Cout_pad, as[0].Kpad, CO, 64)) return kStemDeclined;
+    long long total = 0;
+    for (int p = 0; p < count; ++p) {
+        const StemArgs& a = as[p];
+        StemProb& q = B.q[p];
+        q.N = a.N;
+        q.Tin = a.Tin;
+        q.Tout = a.Tout;
+        q.Hout = a.H / 2;
+        q.Wout = a.W / 2;
+        q.st = a.st;
+        q.t_off = a.t_off;
+        q.pad_mode = a.pad_mode;
+        q.tiles_w = (q.Wout + SV - 1) / SV;
+        q.gn_part = a.gn_part;
+        if (!encode_pixels_map(&q.tm_x, a.x, (long long)a.N * a.Tin, a.H, a.W)) return kStemDeclined;
+        if (a.hist) {
+            if (!encode_pixels_map(&q.tm_h, a.hist, (long long)a.N * a.hist_T, a.H, a.W)) return kStemDeclined;
+            q.has_hist = 1;
+            q.hist_T = a.hist_T;
+        } else {
+            q.tm_h = q.tm_x;
+        }
+        if (!encode_stem_out_map(&q.tm_o, a.out, (long long)a.N * a.Tout * q.Hout, q.Wout, CO)) return kStemDeclined;
+        total += (long long)a.N * a.Tout * q.Hout * q.tiles_w;
+        q.tile_end = total;
+    }
+    B.bias = as[0].bias;
+    B.status = as[0].status;
+    B.wait_ns = as[0].wait_ns;
+    B.num_tiles = total;
+    B.count = count;
+    if (total == 0) return 0;
+    static std::atomic<unsigned long long> attr_done{0};
+    if (smem_attr_once(kern, C::SMEM, attr_done) != cudaSuccess) return (int)cudaGetLastError();
+    // persistent (one CTA per SM), or CTAs of at most cta_tiles tiles each
+    long long grid = std::min<long long>(total, num_sms);
+    if (cta_tiles > 0) grid = std::max(grid, std::min<long long>((total + cta_tiles - 1) / cta_tiles, 1LL << 30));
+    kern<<<(unsigned)grid, NTHREADS, C::SMEM, stream>>>(B);
+    return (int)cudaGetLastError();
+}
+
+template <int CO>
+int launch_cog(const StemArgs* as, int count, int num_sms, cudaStream_t stream, int cta_tiles) {
+    return count == 1 ? launch_co<CO, 1>(as, 1, num_sms, stream, cta_tiles)
+                      : launch_co<CO, kMaxConvGroup>(as, count, num_sms, stream, cta_tiles);
+}
+
+}  // namespace
+
+int stem_tc_gn_slots(int H, int W) { return (H / 2) * ((W / 2 + SV - 1) / SV); }
+
+bool stem_tc_accepts(const StemArgs* as, int count) {
+    if (count < 1 || count > kMaxConvGroup) return false;
+    for (int p = 0; p < count; ++p)
+        if (!stem_form_ok(as[p]) || as[p].Cout != as[0].Cout || as[p].w != as[0].w) return false;
+    return true;
+}
+
+int launch_stem_tc(const StemArgs* as, int count, int num_sms, cudaStream_t stream, int cta_tiles) {
+    if (!stem_tc_accepts(as, count)) return kStemDeclined;
+    return as[0].Cout == 64 ? launch_cog<64>(as, count, num_sms, stream, cta_tiles)
+                            : launch_cog<128>(as, count, num_sms, stream, cta_tiles);
+}
+
+}  // namespace tok

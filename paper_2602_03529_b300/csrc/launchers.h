@@ -25,6 +25,16 @@ int launch_pack_weights_taprows(const float* w, int Cout, int Cin, int rows_out,
 bool conv_tc_gn_fusable(const ConvArgs& a);
 int conv_tc_gn_slots(const ConvArgs& a);
 int launch_conv_tc_group(const ConvArgs* as, int count, int num_sms, cudaStream_t stream, int cta_tiles = 0);
+// Fused BF16 stem (k_stem_tc.cu) over up to kMaxConvGroup problems of one layer.
+// Returns kStemDeclined, having enqueued nothing, where a problem is outside its
+// form (Cout 64 or 128, Kpad 128, H even, W % 8 == 0, 16-byte aligned tensors);
+// the caller then runs the im2col gather and the 1x1x1 conv instead. With
+// gn_part set, the launch writes the GroupNorm statistics of 32 groups of its
+// output: stem_tc_gn_slots per frame.
+constexpr int kStemDeclined = -2;
+bool stem_tc_accepts(const StemArgs* as, int count);
+int launch_stem_tc(const StemArgs* as, int count, int num_sms, cudaStream_t stream, int cta_tiles = 0);
+int stem_tc_gn_slots(int H, int W);
 int conv_tc_bn(int cout_pad16);
 int conv_tc_cout_pad(int Cout);  // packed weight rows of a BF16 conv
 int launch_conv_simt(const ConvArgs& a, cudaStream_t stream);

@@ -727,6 +727,67 @@ struct Exec {
         return o;
     }
 
+    // One problem of the fused BF16 stem: pixels x (N, T, H, W, 3) (H, W the padded
+    // extent) with the stream history hist or null, into out; the GroupNorm
+    // statistics of the output go to wk.gnpart when its 32 groups fit there.
+    StemArgs stem_args(const ConvW& cw, const void* x, const void* hist, int N, int T, int H, int W, int st, int t_off,
+                       void* out, const Work& wk) const {
+        StemArgs a;
+        memset(&a, 0, sizeof(a));
+        a.x = x;
+        a.hist = hist;
+        a.hist_T = hist ? 2 : 0;
+        a.N = N;
+        a.Tin = T;
+        a.H = H;
+        a.W = W;
+        a.Tout = (T - 1) / st + 1;
+        a.st = st;
+        a.t_off = t_off;
+        a.pad_mode = c->arch.time_pad;
+        a.w = cw.w;
+        a.bias = cw.b;
+        a.Cout = cw.Cout;
+        a.Cout_pad = cw.Cout_pad;
+        a.Kpad = cw.Kpad;
+        a.out = out;
+        a.status = c->d_status;
+        a.wait_ns = kWaitNs;
+        const int G = std::max(1, std::min(c->arch.gn_groups, cw.Cout / 2));
+        if (wk.gnpart && G == 32 && cw.Cout % 32 == 0) {
+            const size_t need = (size_t)N * a.Tout * stem_tc_gn_slots(H, W) * 32 * sizeof(GnTriple);
+            if (need <= wk.gnpart_bytes) a.gn_part = reinterpret_cast<GnTriple*>(wk.gnpart);
+        }
+        return a;
+    }
+
+    // The fused stem over as[0 .. count): false, with nothing enqueued, where a
+    // problem is outside its form (the caller then gathers the im2col matrix).
+    bool stem_launch(const StemArgs* as, int count, const ConvW& cw) {
+        if (!c->bf16() || !stem_tc_accepts(as, count)) return false;
+        if (err) return true;
+        double flop = 0;
+        for (int p = 0; p < count; ++p)
+            flop += 2.0 * (double)as[p].N * as[p].Tout * (as[p].H / 2) * (as[p].W / 2) * cw.Cout *
+                    (double)(cw.k * cw.k * cw.k) * cw.Cin;
+        const int e = pbegin();
+        ck(launch_stem_tc(as, count, c->num_sms, s, c->cta_tiles));
+        pend(e, 0, flop, cw.name);
+        c->launches += 1;
+        const StemArgs& a = as[0];
+        trace(cw.name, a.x, (size_t)a.N * a.Tin * a.H * a.W * 3 * 2, nullptr, 0, a.out,
+              (size_t)a.N * a.Tout * (a.H / 2) * (a.W / 2) * cw.Cout * 2);
+        return true;
+    }
+    static Act stem_out(const StemArgs& a) {
+        Act o{a.out, a.N, a.Tout, a.H / 2, a.W / 2, a.Cout};
+        if (a.gn_part) {
+            o.part = a.gn_part;
+            o.part_S = stem_tc_gn_slots(a.H, a.W);
+        }
+        return o;
+    }
+
     Act gn_silu(const std::string& name, const Act& in, void* out) {
         const GnW& g = c->gns[c->gindex[name]];
         if (err) return Act{out, in.N, in.T, in.H, in.W, in.C};

@@ -205,7 +205,11 @@ struct TrainExec : Exec {
         const tok_arch& ar = c->arch;
         const int L = ar.nlevels;
         Act X;
-        if (c->bf16()) {
+        const StemArgs sa = stem_args(c->convs[c->cindex["enc.stem"]], x, nullptr, N, T, H, W, ar.t_stem, -2,
+                                      b.enc[0][0], w);
+        if (stem_launch(&sa, 1, c->convs[c->cindex["enc.stem"]])) {
+            X = stem_out(sa);
+        } else if (c->bf16()) {
             const GatherGeo g = stem_geo(N, T, H, W);
             other([&] { return launch_im2col_pixels(static_cast<const __nv_bfloat16*>(x), nullptr, g,
                                                     reinterpret_cast<__nv_bfloat16*>(w.gather), s); },
