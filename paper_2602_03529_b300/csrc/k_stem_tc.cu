@@ -13,15 +13,19 @@
 // needs no edge extension: H and W are the padded extent), frames before the
 // clip come from the stream history, frame 0 or a zero box.
 //
-// Warp roles (512 threads, one CTA per SM):
-//   warp 0      TMA producer (weights once, then the input boxes per tile)
+// Warp roles (768 threads, one CTA per SM):
+//   warp 0      TMA producer (weights once, then the input boxes per tile,
+//               up to four tiles ahead)
 //   warp 1      MMA issuer: six tcgen05.mma into one of two TMEM accumulators
 //   warp 2      TMEM allocation
-//   warp 3      output: TMA store of the staged tile; merges the statistics
+//   warp 3      statistics: merges the epilogue warps' sums per tile
 //   warps 4-7   im2col: thread v writes row v of the A tile (128B-swizzled,
 //               K-major) from the input boxes
-//   warps 8-15  epilogue: TMEM -> + bias -> BF16 -> staging tile, and the
-//               statistics of its 32 voxels x Cout/2 channels
+//   warps 8-23  epilogue: TMEM -> + bias -> BF16, written out through a
+//               per-warp staging area with 16-byte stores (the TMA unit is
+//               left to the input boxes), and the statistics of its 32
+//               voxels x Cout/4 channels (four epilogue warps per SM
+//               sub-partition hide each other's latencies)
 // Every wait is bounded; a wait that gives up records TOK_ETIMEOUT and every
 // role leaves its loop, drains its own copies and MMAs, and the CTA frees TMEM.
 #include <cudaTypedefs.h>
@@ -45,40 +49,41 @@ constexpr int XB = 200;                    // BF16 values per input box row
 constexpr int NXB = 4;                     // boxes along x: 800 >= 6 * 127 + 14
 constexpr int BOXB = 1280;                 // 3 rows x 200 values (1200 B), 128-byte aligned
 constexpr int RAWB = 3 * NXB * BOXB;       // one tile's input boxes
+constexpr int NRAW = 4;                    // input stages (tiles of input in flight)
+constexpr int NSB = 4;                     // statistics buffers (tiles the merge may lag behind)
 constexpr uint32_t RAW_TX = 3 * NXB * 3 * XB * 2;
 constexpr int KSTEPS = 6;                  // K = 96
-constexpr int NTHREADS = 512;
+constexpr int NTHREADS = 768;
 
 template <int CO>
 struct StemCfg {
     static constexpr int W_ATOM = CO * 128;       // 64 K values of every weight row, SW128
     static constexpr int A_ATOM = SV * 128;       // 64 K values of every voxel row, SW128
     static constexpr int A_STAGE = 2 * A_ATOM;
-    static constexpr int NOB = CO / 64;           // 64-channel boxes of an output tile
-    static constexpr int O_BOX = SV * 128;
-    static constexpr int O_BUF = NOB * O_BOX;
+    static constexpr int RB = CO / 2;             // bytes of an epilogue warp's staged row (Cout/4 bf16)
     static constexpr int OFF_W = 0;
     static constexpr int OFF_A = 2 * W_ATOM;
-    static constexpr int OFF_O = OFF_A + 2 * A_STAGE;
-    static constexpr int OFF_RAW = OFF_O + 2 * O_BUF;
-    static constexpr int OFF_BIAS = OFF_RAW + 2 * RAWB;
+    static constexpr int OFF_RAW = OFF_A + 2 * A_STAGE;
+    static constexpr int OFF_STG = OFF_RAW + NRAW * RAWB;  // 16 warps x 32 rows x RB
+    static constexpr int OFF_BIAS = OFF_STG + 16 * 32 * RB;
     // statistics of a tile per buffer: shifts K[4][32], sums (s, q)[4][32], counts n[4]
     static constexpr int OFF_STK = OFF_BIAS + CO * 4;
-    static constexpr int OFF_STSQ = OFF_STK + 2 * 4 * 32 * 4;
-    static constexpr int OFF_STN = OFF_STSQ + 2 * 4 * 32 * 8;
-    static constexpr int OFF_BAR = OFF_STN + 2 * 4 * 4;
-    static constexpr int NBAR = 17;
+    static constexpr int OFF_STSQ = OFF_STK + NSB * 4 * 32 * 4;
+    static constexpr int OFF_STN = OFF_STSQ + NSB * 4 * 32 * 8;
+    static constexpr int OFF_BAR = OFF_STN + NSB * 4 * 4;
+    static constexpr int NBAR = 2 * NRAW + 9 + 2 * NSB;
     static constexpr int SMEM = OFF_BAR + NBAR * 8 + 8 + 1024;  // + TMEM address, + alignment slack
     static constexpr int TMEM_COLS = 2 * CO;
     static constexpr uint32_t IDESC = idesc_bf16_f32(128, CO);
-    static_assert(OFF_A % 1024 == 0 && OFF_O % 1024 == 0 && OFF_RAW % 1024 == 0, "swizzle atoms");
+    static_assert(OFF_A % 1024 == 0 && OFF_RAW % 1024 == 0, "swizzle atoms");
     static_assert(SMEM <= 232448 - 64, "shared memory");
 };
 
 struct StemProb {
-    CUtensorMap tm_x, tm_h, tm_o;
+    CUtensorMap tm_x, tm_h;
     long long tile_end;  // tiles of the problems up to this one
     GnTriple* gn_part;
+    __nv_bfloat16* out;
     int N, Tin, hist_T, Tout, Hout, Wout, st, t_off, pad_mode, tiles_w, has_hist;
 };
 
@@ -103,15 +108,19 @@ __device__ __forceinline__ StemTile stem_tile(const StemBatch<MAXP>& B, long lon
     int p = 0;
     if constexpr (MAXP > 1)
         while (p + 1 < B.count && u >= B.q[p].tile_end) ++p;
-    long long lu = p ? u - B.q[p - 1].tile_end : u;
+    // 32-bit arithmetic (a launch holds fewer than 2^31 tiles)
+    int lu = (int)(p ? u - B.q[p - 1].tile_end : u);
     const StemProb& q = B.q[p];
     t.p = p;
-    t.tw = (int)(lu % q.tiles_w);
-    lu /= q.tiles_w;
-    t.ho = (int)(lu % q.Hout);
-    lu /= q.Hout;
-    t.to = (int)(lu % q.Tout);
-    t.n = (int)(lu / q.Tout);
+    int r = lu / q.tiles_w;
+    t.tw = lu - r * q.tiles_w;
+    lu = r;
+    r = lu / q.Hout;
+    t.ho = lu - r * q.Hout;
+    lu = r;
+    r = lu / q.Tout;
+    t.to = lu - r * q.Tout;
+    t.n = r;
     return t;
 }
 
@@ -146,7 +155,7 @@ __device__ __forceinline__ GnTriple stem_merge(GnTriple a, GnTriple b) {
     GnTriple r;
     r.n = a.n + b.n;
     const float d = b.mean - a.mean;
-    const float fb = b.n / r.n;
+    const float fb = b.n * __frcp_rn(r.n);  // counts: small integers
     r.mean = a.mean + d * fb;
     r.m2 = a.m2 + b.m2 + d * d * a.n * fb;
     return r;
@@ -156,21 +165,58 @@ __device__ __forceinline__ uint32_t ld_shared_u32(const uint8_t* p) {
     return *reinterpret_cast<const uint32_t*>(p);
 }
 
+// Two FP32 values in one 64-bit register (low: first) and the paired FP32
+// arithmetic of sm_100-family SMs (each lane rounded as the scalar operation).
+__device__ __forceinline__ uint64_t f2(float lo, float hi) {
+    return (uint64_t)__float_as_uint(lo) | ((uint64_t)__float_as_uint(hi) << 32);
+}
+__device__ __forceinline__ float f2_lo(uint64_t v) { return __uint_as_float((uint32_t)v); }
+__device__ __forceinline__ float f2_hi(uint64_t v) { return __uint_as_float((uint32_t)(v >> 32)); }
+__device__ __forceinline__ uint64_t add2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t sub2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t mul2(uint64_t a, uint64_t b) {
+    uint64_t d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ uint64_t fma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ uint64_t shfl_xor2(uint64_t v, int o) {
+    const uint32_t lo = __shfl_xor_sync(0xffffffffu, (uint32_t)v, o);
+    const uint32_t hi = __shfl_xor_sync(0xffffffffu, (uint32_t)(v >> 32), o);
+    return (uint64_t)lo | ((uint64_t)hi << 32);
+}
+// bf16 pair (low: first) -> the two values as FP32
+__device__ __forceinline__ uint64_t bf2_to_f2(uint32_t w) {
+    return f2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+}
+
 template <int CO, int MAXP>
 __global__ void __launch_bounds__(NTHREADS, 1) stem_tc_kernel(const __grid_constant__ StemBatch<MAXP> B) {
     using C = StemCfg<CO>;
     extern __shared__ uint8_t smem_dyn[];
     uint8_t* smem = smem_dyn + ((1024u - (smem_u32(smem_dyn) & 1023u)) & 1023u);
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::OFF_BAR);
-    uint64_t* raw_full = bars;        // [2] TMA bytes of a tile's input boxes
-    uint64_t* raw_empty = bars + 2;   // [2] 4 im2col warps
-    uint64_t* a_full = bars + 4;      // [2] 4 im2col warps
-    uint64_t* a_empty = bars + 6;     // [2] MMA commit
-    uint64_t* t_full = bars + 8;      // [2] MMA commit
-    uint64_t* t_empty = bars + 10;    // [2] 8 epilogue warps
-    uint64_t* o_ready = bars + 12;    // [2] 8 epilogue warps
-    uint64_t* o_free = bars + 14;     // [2] output warp
-    uint64_t* w_full = bars + 16;     // weights
+    uint64_t* raw_full = bars;                // [NRAW] TMA bytes of a tile's input boxes
+    uint64_t* raw_empty = bars + NRAW;        // [NRAW] 4 im2col warps
+    uint64_t* a_full = bars + 2 * NRAW;       // [2] 4 im2col warps
+    uint64_t* a_empty = a_full + 2;           // [2] MMA commit
+    uint64_t* t_full = a_full + 4;            // [2] MMA commit
+    uint64_t* t_empty = a_full + 6;           // [2] 16 epilogue warps
+    uint64_t* o_ready = a_full + 8;           // [NSB] 16 epilogue warps: a tile's statistics staged
+    uint64_t* o_free = o_ready + NSB;         // [NSB] statistics warp
+    uint64_t* w_full = o_free + NSB;          // weights
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + C::NBAR);
     float* sbias = reinterpret_cast<float*>(smem + C::OFF_BIAS);
 
@@ -185,14 +231,18 @@ __global__ void __launch_bounds__(NTHREADS, 1) stem_tc_kernel(const __grid_const
     if (s_skip) return;
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < NRAW; ++i) {
             mbar_init(&raw_full[i], 1);
             mbar_init(&raw_empty[i], 4);
+        }
+        for (int i = 0; i < 2; ++i) {
             mbar_init(&a_full[i], 4);
             mbar_init(&a_empty[i], 1);
             mbar_init(&t_full[i], 1);
-            mbar_init(&t_empty[i], 8);
-            mbar_init(&o_ready[i], 8);
+            mbar_init(&t_empty[i], 16);
+        }
+        for (int i = 0; i < NSB; ++i) {
+            mbar_init(&o_ready[i], 16);
             mbar_init(&o_free[i], 1);
         }
         mbar_init(w_full, 1);
@@ -202,7 +252,6 @@ __global__ void __launch_bounds__(NTHREADS, 1) stem_tc_kernel(const __grid_const
     if (warp == 0 && lane < B.count) {
         tma_prefetch_desc(&B.q[lane].tm_x);
         if (B.q[lane].has_hist) tma_prefetch_desc(&B.q[lane].tm_h);
-        tma_prefetch_desc(&B.q[lane].tm_o);
     }
     if (warp == 2) {
         tmem_alloc(tmem_slot, C::TMEM_COLS);
@@ -219,13 +268,15 @@ __global__ void __launch_bounds__(NTHREADS, 1) stem_tc_kernel(const __grid_const
             mbar_arrive_expect_tx(w_full, 2 * C::W_ATOM);
             tma_load_2d(smem + C::OFF_W, &B.tm_w, w_full, 0, 0);
             tma_load_2d(smem + C::OFF_W + C::W_ATOM, &B.tm_w, w_full, 64, 0);
-            int last[2] = {-1, -1};
+            int last[NRAW];
+#pragma unroll
+            for (int i = 0; i < NRAW; ++i) last[i] = -1;
             int it = 0;
             for (long long u = cid; u < B.num_tiles; u += ncl, ++it) {
-                const int s = it & 1;
-                const uint32_t ph = (uint32_t)((it >> 1) & 1);
-                if (!mbar_wait(&raw_empty[s], ph ^ 1, status, wait_ns)) break;
+                const int s = it % NRAW;
+                const uint32_t ph = (uint32_t)((it / NRAW) & 1);
                 const StemTile t = stem_tile(B, u);
+                if (!mbar_wait(&raw_empty[s], ph ^ 1, status, wait_ns)) break;
                 const StemProb& q = B.q[t.p];
                 uint8_t* dst = smem + C::OFF_RAW + s * RAWB;
                 mbar_arrive_expect_tx(&raw_full[s], RAW_TX);
@@ -240,17 +291,20 @@ __global__ void __launch_bounds__(NTHREADS, 1) stem_tc_kernel(const __grid_const
                     for (int b = 0; b < NXB; ++b)
                         tma_load_3d(dst + (dt * NXB + b) * BOXB, m, &raw_full[s], x0 + b * XB, h0, f);
                 }
-                last[s] = (int)ph;
+#pragma unroll
+                for (int i = 0; i < NRAW; ++i)
+                    if (i == s) last[i] = (int)ph;
             }
             // no copy may still be in flight when the CTA exits
-            for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int i = 0; i < NRAW; ++i)
                 if (last[i] >= 0) mbar_wait(&raw_full[i], (uint32_t)last[i], status, wait_ns);
             mbar_wait(w_full, 0, status, wait_ns);
         }
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------------------------------------------- MMA issuer
-            int last[2] = {-1, -1};
+            int last0 = -1, last1 = -1;
             if (mbar_wait(w_full, 0, status, wait_ns)) {
                 tc_fence_after();
                 const uint32_t wa = smem_u32(smem + C::OFF_W);
@@ -270,32 +324,25 @@ __global__ void __launch_bounds__(NTHREADS, 1) stem_tc_kernel(const __grid_const
                                     k ? 1u : 0u);
                     tc_commit(&a_empty[s]);
                     tc_commit(&t_full[s]);
-                    last[s] = (int)ph;
+                    if (s) last1 = (int)ph;
+                    else last0 = (int)ph;
                 }
             }
             // our own MMAs complete before TMEM can be released
-            for (int i = 0; i < 2; ++i)
-                if (last[i] >= 0) mbar_wait(&t_full[i], (uint32_t)last[i], status, wait_ns);
+            if (last0 >= 0) mbar_wait(&t_full[0], (uint32_t)last0, status, wait_ns);
+            if (last1 >= 0) mbar_wait(&t_full[1], (uint32_t)last1, status, wait_ns);
         }
     } else if (warp == 3) {
-        // -------------------------------------------------------- output
-        // the staged tile goes out as Cout / 64 boxes of 64 channels x 128 voxels
-        // (voxels past the row's end are not written); lane g merges group g's
-        // statistics over the four TMEM lane quarters in a fixed order
+        // -------------------------------------------------------- statistics
+        // lane g merges group g's shifted sums over the four TMEM lane quarters in a
+        // fixed order into the tile's statistics slot
         int it = 0;
         for (long long u = cid; u < B.num_tiles; u += ncl, ++it) {
-            const int s = it & 1;
-            const uint32_t ph = (uint32_t)((it >> 1) & 1);
-            if (!warp_wait(&o_ready[s], ph, status, wait_ns)) break;
+            const int s = it % NSB;
+            const uint32_t ph = (uint32_t)((it / NSB) & 1);
             const StemTile t = stem_tile(B, u);
+            if (!warp_wait(&o_ready[s], ph, status, wait_ns)) break;
             const StemProb& pq = B.q[t.p];
-            if (lane == 0) {
-                const uint8_t* ob = smem + C::OFF_O + s * C::O_BUF;
-                const int row = (t.n * pq.Tout + t.to) * pq.Hout + t.ho;
-#pragma unroll
-                for (int b = 0; b < C::NOB; ++b) tma_store_3d(&pq.tm_o, ob + b * C::O_BOX, b * 64, t.tw * SV, row);
-                bulk_commit();
-            }
             if (pq.gn_part) {
                 const float* stk = reinterpret_cast<const float*>(smem + C::OFF_STK) + s * 4 * 32;
                 const float2* stsq = reinterpret_cast<const float2*>(smem + C::OFF_STSQ) + s * 4 * 32;
@@ -305,19 +352,19 @@ __global__ void __launch_bounds__(NTHREADS, 1) stem_tc_kernel(const __grid_const
                 for (int qq = 0; qq < 4; ++qq) {
                     const float n = stn[qq], K = stk[qq * 32 + lane];
                     const float2 sq = stsq[qq * 32 + lane];
+                    const float inv = n > 0.f ? __frcp_rn(n) : 0.f;
+                    const float sm = sq.x * inv;
                     tr[qq].n = n;
-                    tr[qq].mean = n > 0.f ? K + sq.x / n : 0.f;
-                    tr[qq].m2 = n > 0.f ? fmaxf(sq.y - sq.x * sq.x / n, 0.f) : 0.f;
+                    tr[qq].mean = K + sm;
+                    tr[qq].m2 = fmaxf(sq.y - sq.x * sm, 0.f);
                 }
                 const long long S = (long long)pq.Hout * pq.tiles_w;
                 pq.gn_part[(((long long)t.n * pq.Tout + t.to) * S + (long long)t.ho * pq.tiles_w + t.tw) * 32 + lane] =
                     stem_merge(stem_merge(tr[0], tr[1]), stem_merge(tr[2], tr[3]));
             }
-            if (lane == 0) bulk_wait_read_all();
             __syncwarp();
             if (lane == 0) mbar_arrive(&o_free[s]);
         }
-        if (lane == 0) bulk_wait_all();
     } else if (warp >= 4 && warp < 8) {
         // -------------------------------------------------------- im2col
         // Row v of the A tile is voxel v: K = 9 r + k with r = dt * 3 + dh and k = 3 dw +
@@ -334,152 +381,183 @@ __global__ void __launch_bounds__(NTHREADS, 1) stem_tc_kernel(const __grid_const
         const uint32_t arow = (uint32_t)v * 128u, sw = (uint32_t)(v & 7);
         int it = 0;
         for (long long u = cid; u < B.num_tiles; u += ncl, ++it) {
-            const int s = it & 1;
-            const uint32_t ph = (uint32_t)((it >> 1) & 1);
-            if (!warp_wait(&raw_full[s], ph, status, wait_ns)) break;
-            if (!warp_wait(&a_empty[s], ph ^ 1, status, wait_ns)) break;
-            const uint8_t* rb = smem + C::OFF_RAW + s * RAWB;
-            uint32_t w[9][5];
-#pragma unroll
-            for (int r = 0; r < 9; ++r)
-#pragma unroll
-                for (int j = 0; j < 5; ++j)
-                    w[r][j] = ld_shared_u32(rb + ((r / 3) * NXB * BOXB + (r % 3) * XB * 2) + woff[j]);
-            // value k of row r is half k + 1 of the row's ten (word (k + 1) / 2); K >= 81 is zero
-            uint32_t o[48];
+            const int sr = it % NRAW, s = it & 1;
+            if (!warp_wait(&raw_full[sr], (uint32_t)((it / NRAW) & 1), status, wait_ns)) break;
+            if (!warp_wait(&a_empty[s], (uint32_t)(((it >> 1) & 1) ^ 1), status, wait_ns)) break;
+            const uint8_t* rb = smem + C::OFF_RAW + sr * RAWB;
+            uint8_t* ab = smem + C::OFF_A + s * C::A_STAGE;
+            // output word m = K values (2m, 2m + 1); value k of row r is half k + 1 of the
+            // row's ten (word (k + 1) / 2); K >= 81 is zero. Rows are read in order, two
+            // live at a time (cur: row `rc`, prev: row rc - 1), and every 16-byte chunk is
+            // stored as soon as its four words are formed.
+            uint32_t cur[5], prev[5], o4[4];
+            int rc = -1;
 #pragma unroll
             for (int m = 0; m < 48; ++m) {
                 const int k0 = 2 * m, k1 = 2 * m + 1;
-                const uint32_t a = k0 < 81 ? w[k0 / 9][(k0 % 9 + 1) >> 1] : 0u;
-                const uint32_t b = k1 < 81 ? w[k1 / 9][(k1 % 9 + 1) >> 1] : 0u;
-                o[m] = pick2(a, k0 < 81 ? (k0 % 9 + 1) & 1 : 0, b, k1 < 81 ? (k1 % 9 + 1) & 1 : 0);
-            }
-            uint8_t* ab = smem + C::OFF_A + s * C::A_STAGE;
+                const int rneed = (k1 < 81 ? k1 : 80) / 9;
+                if (rneed > rc) {
 #pragma unroll
-            for (int c = 0; c < 12; ++c) {
-                uint8_t* dst = ab + (c >> 3) * C::A_ATOM + arow + ((((uint32_t)c & 7u) ^ sw) << 4);
-                *reinterpret_cast<uint4*>(dst) = make_uint4(o[4 * c], o[4 * c + 1], o[4 * c + 2], o[4 * c + 3]);
+                    for (int j = 0; j < 5; ++j) prev[j] = cur[j];
+                    rc = rneed;
+#pragma unroll
+                    for (int j = 0; j < 5; ++j)
+                        cur[j] = ld_shared_u32(rb + ((rc / 3) * NXB * BOXB + (rc % 3) * XB * 2) + woff[j]);
+                }
+                auto word = [&](int k) -> uint32_t {
+                    if (k >= 81) return 0u;
+                    const int r = k / 9, wj = (k % 9 + 1) >> 1;
+                    return r == rc ? cur[wj] : prev[wj];
+                };
+                o4[m & 3] = pick2(word(k0), k0 < 81 ? (k0 % 9 + 1) & 1 : 0, word(k1), k1 < 81 ? (k1 % 9 + 1) & 1 : 0);
+                if ((m & 3) == 3) {
+                    const int c = m >> 2;
+                    uint8_t* dst = ab + (c >> 3) * C::A_ATOM + arow + ((((uint32_t)c & 7u) ^ sw) << 4);
+                    *reinterpret_cast<uint4*>(dst) = make_uint4(o4[0], o4[1], o4[2], o4[3]);
+                }
             }
             fence_proxy_async_smem();
             __syncwarp();
             if (lane == 0) {
                 mbar_arrive(&a_full[s]);
-                mbar_arrive(&raw_empty[s]);
+                mbar_arrive(&raw_empty[sr]);
             }
         }
     } else if (warp >= 8) {
         // -------------------------------------------------------- epilogue
-        // warp (q, h): TMEM lanes 32 q .. 32 q + 31 (voxels), channels h * Cout/2 ..;
-        // GroupNorm of 32 groups: CG channels each, NG = 16 groups per warp. The
+        // warp (q, c4): TMEM lanes 32 q .. 32 q + 31 (voxels), channels c4 * Cout/4 ..;
+        // GroupNorm of 32 groups: CG channels each, NG = 8 groups per warp. The
         // statistics are those of the stored BF16 values, as shifted sums per group
-        // (the shift: lane 0's first value of the group), reduced over the warp's
-        // voxels by a butterfly that leaves group (lane >> 1) on each lane pair.
-        constexpr int HC = CO / 2;
+        // (the shift: lane 0's first value of the group; voxels past the row's end
+        // weigh 0), reduced over the warp's voxels by a butterfly that leaves group
+        // (lane >> 2) on lanes 4g .. 4g + 3. The warp stages its 32 rows in its own
+        // region and writes them out with 16-byte stores, each row's bytes contiguous.
+        constexpr int HC = CO / 4;
         constexpr int CG = CO / 32;
         constexpr int NG = HC / CG;
-        static_assert(NG == 16, "16 groups per epilogue warp");
-        const int e = warp - 8, q = warp & 3, h = e >> 2;
+        constexpr int WPG = CG / 2;        // bf16 pairs per group
+        constexpr int RB = C::RB;          // staged bytes per voxel row
+        constexpr int CPR = RB / 16;       // 16-byte chunks per staged row
+        constexpr int RPI = 32 / CPR;      // staged rows per copy-out instruction
+        static_assert(NG == 8 && (CPR == 4 || CPR == 2) && RB == HC * 2, "epilogue shape");
+        const int e = warp - 8, q = warp & 3, c4 = e >> 2;
         const int v = q * 32 + lane;
-        const float* bias = sbias + h * HC;
+        const float* bias = sbias + c4 * HC;
+        uint8_t* stg = smem + C::OFF_STG + e * 32 * RB;
+        // chunk j of staged row r sits at chunk j ^ swz(r): the row-per-lane writes and
+        // the contiguous reads are both free of bank conflicts
+        auto swz = [](int r) { return CPR == 4 ? ((r >> 1) & 3) : ((r >> 2) & 1); };
+        const int crow = lane / CPR, cchk = lane % CPR;
         int it = 0;
+        StemTile tn = stem_tile(B, cid < B.num_tiles ? cid : 0);
         for (long long u = cid; u < B.num_tiles; u += ncl, ++it) {
             const int s = it & 1;
             const uint32_t ph = (uint32_t)((it >> 1) & 1);
+            const int sb = it % NSB;
+            const StemTile t = tn;
             if (!warp_wait(&t_full[s], ph, status, wait_ns)) break;
             tc_fence_after();
-            const StemTile t = stem_tile(B, u);
             const StemProb& pq = B.q[t.p];
-            const bool valid = t.tw * SV + v < pq.Wout;
-            const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(s * CO + h * HC);
-            uint32_t pk[HC / 2];
+            const int wo0 = t.tw * SV;
+            const int nvalid = min(SV, pq.Wout - wo0);  // voxels of the tile inside the row
+            const uint32_t ta = tmem_base + ((uint32_t)(q * 32) << 16) + (uint32_t)(s * CO + c4 * HC);
+            uint32_t r[HC / 16][16];
 #pragma unroll
-            for (int c32 = 0; c32 < HC / 32; ++c32) {
-                uint32_t r0[16], r1[16];
-                tmem_ld16_issue(ta + (uint32_t)(c32 * 32), r0);
-                tmem_ld16_issue(ta + (uint32_t)(c32 * 32 + 16), r1);
-                tmem_ld_wait();
-                tmem_regs_fence(r0);
-                tmem_regs_fence(r1);
-                // columns c32 * 32 + 4 i .. (r0) and c32 * 32 + 16 + 4 i .. (r1)
-                const float4* b4 = reinterpret_cast<const float4*>(bias + c32 * 32);
+            for (int b = 0; b < HC / 16; ++b) tmem_ld16_issue(ta + (uint32_t)(b * 16), r[b]);
+            tmem_ld_wait();
 #pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const float4 ba = b4[i], bb = b4[4 + i];
-                    pk[c32 * 16 + 2 * i] =
-                        pack_bf16x2(__uint_as_float(r0[4 * i]) + ba.x, __uint_as_float(r0[4 * i + 1]) + ba.y);
-                    pk[c32 * 16 + 2 * i + 1] =
-                        pack_bf16x2(__uint_as_float(r0[4 * i + 2]) + ba.z, __uint_as_float(r0[4 * i + 3]) + ba.w);
-                    pk[c32 * 16 + 8 + 2 * i] =
-                        pack_bf16x2(__uint_as_float(r1[4 * i]) + bb.x, __uint_as_float(r1[4 * i + 1]) + bb.y);
-                    pk[c32 * 16 + 8 + 2 * i + 1] =
-                        pack_bf16x2(__uint_as_float(r1[4 * i + 2]) + bb.z, __uint_as_float(r1[4 * i + 3]) + bb.w);
-                }
-            }
+            for (int b = 0; b < HC / 16; ++b) tmem_regs_fence(r[b]);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&t_empty[s]);
-            float gs[NG], gq[NG], gk[NG];
+            // + bias, to BF16 pairs: columns b * 16 + 4 i ..
+            uint32_t pk[HC / 2];
+#pragma unroll
+            for (int b = 0; b < HC / 16; ++b) {
+                const float4* b4 = reinterpret_cast<const float4*>(bias + b * 16);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float4 bb = b4[i];
+                    const uint64_t x0 = add2(f2(__uint_as_float(r[b][4 * i]), __uint_as_float(r[b][4 * i + 1])), f2(bb.x, bb.y));
+                    const uint64_t x1 =
+                        add2(f2(__uint_as_float(r[b][4 * i + 2]), __uint_as_float(r[b][4 * i + 3])), f2(bb.z, bb.w));
+                    pk[b * 8 + 2 * i] = pack_bf16x2(f2_lo(x0), f2_hi(x0));
+                    pk[b * 8 + 2 * i + 1] = pack_bf16x2(f2_lo(x1), f2_hi(x1));
+                }
+            }
+            // statistics: (sum, sum of squares) of the shifted values per group, into the
+            // buffer the statistics warp has released (every tile passes both barriers)
+            if (u + ncl < B.num_tiles) tn = stem_tile(B, u + ncl);  // the next tile's coordinates, early
+            if (!warp_wait(&o_free[sb], (uint32_t)(((it / NSB) & 1) ^ 1), status, wait_ns)) break;
             const bool gstat = pq.gn_part != nullptr;
+            uint64_t sq[NG];
             if (gstat) {
+                // the shifts first, all eight broadcasts in flight together
+                float Kg[NG];
+#pragma unroll
+                for (int g = 0; g < NG; ++g) Kg[g] = __shfl_sync(0xffffffffu, __uint_as_float(pk[g * WPG] << 16), 0);
+                if (lane == 0) {
+                    float4* stk = reinterpret_cast<float4*>(reinterpret_cast<float*>(smem + C::OFF_STK) +
+                                                            (sb * 4 + q) * 32 + c4 * NG);
+                    stk[0] = make_float4(Kg[0], Kg[1], Kg[2], Kg[3]);
+                    stk[1] = make_float4(Kg[4], Kg[5], Kg[6], Kg[7]);
+                }
+                const float m = v < nvalid ? 1.f : 0.f;
+                const uint64_t M = f2(m, m);
 #pragma unroll
                 for (int g = 0; g < NG; ++g) {
-                    float x[CG];
+                    const uint64_t x0 = bf2_to_f2(pk[g * WPG]);
+                    const uint64_t KK = f2(Kg[g], Kg[g]);
+                    uint64_t d = mul2(sub2(x0, KK), M);
+                    uint64_t s2 = d, q2 = mul2(d, d);
 #pragma unroll
-                    for (int j = 0; j < CG / 2; ++j) {
-                        const float2 f = unpack_bf16x2(pk[g * (CG / 2) + j]);
-                        x[2 * j] = f.x;
-                        x[2 * j + 1] = f.y;
+                    for (int j = 1; j < WPG; ++j) {
+                        d = mul2(sub2(bf2_to_f2(pk[g * WPG + j]), KK), M);
+                        s2 = add2(s2, d);
+                        q2 = fma2(d, d, q2);
                     }
-                    gk[g] = __shfl_sync(0xffffffffu, x[0], 0);
-                    float a = 0.f, b = 0.f;
-#pragma unroll
-                    for (int j = 0; j < CG; ++j) {
-                        const float d = valid ? x[j] - gk[g] : 0.f;
-                        a += d;
-                        b = fmaf(d, d, b);
-                    }
-                    gs[g] = a;
-                    gq[g] = b;
+                    sq[g] = f2(f2_lo(s2) + f2_hi(s2), f2_lo(q2) + f2_hi(q2));
                 }
                 // step o: a lane keeps the lower (upper if lane & o) half of its groups and
-                // adds its partner's sums of them
+                // adds its partner's sums of them; then lanes 4g .. 4g + 3 sum group g
 #pragma unroll
-                for (int o = 16; o >= 2; o >>= 1) {
-                    const int half = o / 2;
+                for (int o = 16; o >= 4; o >>= 1) {
+                    const int half = o / 4;
                     const bool up = (lane & o) != 0;
 #pragma unroll
                     for (int i = 0; i < half; ++i) {
-                        const float rs = __shfl_xor_sync(0xffffffffu, up ? gs[i] : gs[i + half], o);
-                        const float rq = __shfl_xor_sync(0xffffffffu, up ? gq[i] : gq[i + half], o);
-                        gs[i] = (up ? gs[i + half] : gs[i]) + rs;
-                        gq[i] = (up ? gq[i + half] : gq[i]) + rq;
+                        const uint64_t rr = shfl_xor2(up ? sq[i] : sq[i + half], o);
+                        sq[i] = add2(up ? sq[i + half] : sq[i], rr);
                     }
                 }
-                gs[0] += __shfl_xor_sync(0xffffffffu, gs[0], 1);
-                gq[0] += __shfl_xor_sync(0xffffffffu, gq[0], 1);
+                sq[0] = add2(sq[0], shfl_xor2(sq[0], 2));
+                sq[0] = add2(sq[0], shfl_xor2(sq[0], 1));
+                uint64_t* stsq = reinterpret_cast<uint64_t*>(smem + C::OFF_STSQ) + (sb * 4 + q) * 32 + c4 * NG;
+                if ((lane & 3) == 0) stsq[lane >> 2] = sq[0];
+                if (lane == 0 && c4 == 0)
+                    reinterpret_cast<float*>(smem + C::OFF_STN)[sb * 4 + q] =
+                        (float)(CG * max(0, min(32, nvalid - q * 32)));
             }
-            const float nq = (float)(CG * __popc(__ballot_sync(0xffffffffu, valid)));
-            if (!warp_wait(&o_free[s], ph ^ 1, status, wait_ns)) break;
-            uint8_t* ob = smem + C::OFF_O + s * C::O_BUF;
-#pragma unroll
-            for (int j = 0; j < HC / 8; ++j) {
-                const int c0 = h * HC + 8 * j;
-                uint8_t* dst = ob + (c0 >> 6) * C::O_BOX + v * 128 + ((((c0 & 63) >> 3) ^ (v & 7)) << 4);
-                *reinterpret_cast<uint4*>(dst) = make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
-            }
-            if (gstat) {
-                float* stk = reinterpret_cast<float*>(smem + C::OFF_STK) + (s * 4 + q) * 32 + h * NG;
-                float2* stsq = reinterpret_cast<float2*>(smem + C::OFF_STSQ) + (s * 4 + q) * 32 + h * NG;
-                if (lane == 0) {
-#pragma unroll
-                    for (int g = 0; g < NG; ++g) stk[g] = gk[g];
-                }
-                if ((lane & 1) == 0) stsq[lane >> 1] = make_float2(gs[0], gq[0]);
-                if (lane == 0 && h == 0) reinterpret_cast<float*>(smem + C::OFF_STN)[s * 4 + q] = nq;
-            }
-            fence_proxy_async_smem();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&o_ready[s]);
+            if (lane == 0) mbar_arrive(&o_ready[sb]);
+            // stage this warp's 32 rows, then write them out: RPI rows per instruction,
+            // CPR lanes on each row's contiguous bytes
+#pragma unroll
+            for (int j = 0; j < CPR; ++j)
+                *reinterpret_cast<uint4*>(stg + lane * RB + ((j ^ swz(lane)) << 4)) =
+                    make_uint4(pk[4 * j], pk[4 * j + 1], pk[4 * j + 2], pk[4 * j + 3]);
+            __syncwarp();
+            {
+                const long long vox0 = (((long long)t.n * pq.Tout + t.to) * pq.Hout + t.ho) * pq.Wout + wo0 + q * 32;
+                __nv_bfloat16* op = pq.out + vox0 * CO + c4 * HC + cchk * 8;
+#pragma unroll
+                for (int i = 0; i < 32 / RPI; ++i) {
+                    const int rr = crow + RPI * i;
+                    const uint4 val = *reinterpret_cast<const uint4*>(stg + rr * RB + ((cchk ^ swz(rr)) << 4));
+                    if (q * 32 + rr < nvalid) *reinterpret_cast<uint4*>(op + (long long)rr * CO) = val;
+                }
+            }
+            __syncwarp();
         }
     }
 
@@ -500,20 +578,6 @@ bool encode_pixels_map(CUtensorMap* m, const void* base, long long frames, int H
     cuuint32_t estr[3] = {1, 1, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box, estr,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
-// Output as (channel, w, row = (n * Tout + t) * Hout + h), boxes of 64 channels x
-// 128 voxels, 128-byte swizzle.
-bool encode_stem_out_map(CUtensorMap* m, void* base, long long rows, int Wout, int C) {
-    auto enc = get_encode_fn();
-    if (!enc) return false;
-    cuuint64_t dims[3] = {(cuuint64_t)C, (cuuint64_t)Wout, (cuuint64_t)rows};
-    cuuint64_t strides[2] = {(cuuint64_t)C * 2, (cuuint64_t)Wout * C * 2};
-    cuuint32_t box[3] = {64, (cuuint32_t)SV, 1};
-    cuuint32_t estr[3] = {1, 1, 1};
-    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -554,7 +618,7 @@ int launch_co(const StemArgs* as, int count, int num_sms, cudaStream_t stream, i
         } else {
             q.tm_h = q.tm_x;
         }
-        if (!encode_stem_out_map(&q.tm_o, a.out, (long long)a.N * a.Tout * q.Hout, q.Wout, CO)) return kStemDeclined;
+        q.out = static_cast<__nv_bfloat16*>(a.out);
         total += (long long)a.N * a.Tout * q.Hout * q.tiles_w;
         q.tile_end = total;
     }
@@ -564,6 +628,7 @@ int launch_co(const StemArgs* as, int count, int num_sms, cudaStream_t stream, i
     B.num_tiles = total;
     B.count = count;
     if (total == 0) return 0;
+    if (total >= (1LL << 31)) return kStemDeclined;
     static std::atomic<unsigned long long> attr_done{0};
     if (smem_attr_once(kern, C::SMEM, attr_done) != cudaSuccess) return (int)cudaGetLastError();
     // persistent (one CTA per SM), or CTAs of at most cta_tiles tiles each
