@@ -124,6 +124,52 @@ __device__ __forceinline__ StemTile stem_tile(const StemBatch<MAXP>& B, long lon
     return t;
 }
 
+// The tiles one CTA visits (u = blockIdx.x, + gridDim.x, ...), decoded once and
+// then advanced by the stride in mixed radix (tw, ho, to, n) with carries; a
+// step into the next problem decodes again.
+template <int MAXP>
+struct StemCursor {
+    long long u;
+    StemTile t;
+    int s0, s1, s2, s3;  // the stride in the current problem's radices
+    __device__ __forceinline__ void stride_digits(const StemBatch<MAXP>& B, int ncl) {
+        const StemProb& q = B.q[t.p];
+        int r = ncl / q.tiles_w;
+        s0 = ncl - r * q.tiles_w;
+        int r2 = r / q.Hout;
+        s1 = r - r2 * q.Hout;
+        s3 = r2 / q.Tout;
+        s2 = r2 - s3 * q.Tout;
+    }
+    __device__ __forceinline__ void start(const StemBatch<MAXP>& B, long long u0, int ncl) {
+        u = u0;
+        t = stem_tile(B, u0 < B.num_tiles ? u0 : 0);
+        stride_digits(B, ncl);
+    }
+    __device__ __forceinline__ void next(const StemBatch<MAXP>& B, int ncl) {
+        u += ncl;
+        if (u >= B.num_tiles) return;
+        if (MAXP > 1 && u >= B.q[t.p].tile_end) {
+            const int p0 = t.p;
+            t = stem_tile(B, u);
+            if (t.p != p0) stride_digits(B, ncl);
+            return;
+        }
+        const StemProb& q = B.q[t.p];
+        int c;
+        t.tw += s0;
+        c = t.tw >= q.tiles_w;
+        t.tw -= c ? q.tiles_w : 0;
+        t.ho += s1 + c;
+        c = t.ho >= q.Hout;
+        t.ho -= c ? q.Hout : 0;
+        t.to += s2 + c;
+        c = t.to >= q.Tout;
+        t.to -= c ? q.Tout : 0;
+        t.n += s3 + c;
+    }
+};
+
 // Frame coordinate of input frame ti of sample n and the map it is read from:
 // the clip, the history before it, frame 0 (replicate padding) or -1 (a box
 // wholly outside the tensor: zeros).
@@ -202,6 +248,28 @@ __device__ __forceinline__ uint64_t bf2_to_f2(uint32_t w) {
     return f2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
 }
 
+// Per group g of WPG bf16 pairs: (sum, sum of squares) of the values minus the
+// group's shift Kg[g], each weighted by M (0 or 1 per lane) when MASK.
+template <int NG, int WPG, bool MASK>
+__device__ __forceinline__ void group_sums(const uint32_t (&pk)[NG * WPG], const float (&Kg)[NG], uint64_t M,
+                                           uint64_t (&sq)[NG]) {
+#pragma unroll
+    for (int g = 0; g < NG; ++g) {
+        const uint64_t KK = f2(Kg[g], Kg[g]);
+        uint64_t d = sub2(bf2_to_f2(pk[g * WPG]), KK);
+        if (MASK) d = mul2(d, M);
+        uint64_t s2 = d, q2 = mul2(d, d);
+#pragma unroll
+        for (int j = 1; j < WPG; ++j) {
+            d = sub2(bf2_to_f2(pk[g * WPG + j]), KK);
+            if (MASK) d = mul2(d, M);
+            s2 = add2(s2, d);
+            q2 = fma2(d, d, q2);
+        }
+        sq[g] = f2(f2_lo(s2) + f2_hi(s2), f2_lo(q2) + f2_hi(q2));
+    }
+}
+
 template <int CO, int MAXP>
 __global__ void __launch_bounds__(NTHREADS, 1) stem_tc_kernel(const __grid_constant__ StemBatch<MAXP> B) {
     using C = StemCfg<CO>;
@@ -272,10 +340,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) stem_tc_kernel(const __grid_const
 #pragma unroll
             for (int i = 0; i < NRAW; ++i) last[i] = -1;
             int it = 0;
-            for (long long u = cid; u < B.num_tiles; u += ncl, ++it) {
+            StemCursor<MAXP> cur;
+            cur.start(B, cid, (int)ncl);
+            for (; cur.u < B.num_tiles; cur.next(B, (int)ncl), ++it) {
                 const int s = it % NRAW;
                 const uint32_t ph = (uint32_t)((it / NRAW) & 1);
-                const StemTile t = stem_tile(B, u);
+                const StemTile t = cur.t;
                 if (!mbar_wait(&raw_empty[s], ph ^ 1, status, wait_ns)) break;
                 const StemProb& q = B.q[t.p];
                 uint8_t* dst = smem + C::OFF_RAW + s * RAWB;
@@ -337,10 +407,12 @@ __global__ void __launch_bounds__(NTHREADS, 1) stem_tc_kernel(const __grid_const
         // lane g merges group g's shifted sums over the four TMEM lane quarters in a
         // fixed order into the tile's statistics slot
         int it = 0;
-        for (long long u = cid; u < B.num_tiles; u += ncl, ++it) {
+        StemCursor<MAXP> cur;
+        cur.start(B, cid, (int)ncl);
+        for (; cur.u < B.num_tiles; cur.next(B, (int)ncl), ++it) {
             const int s = it % NSB;
             const uint32_t ph = (uint32_t)((it / NSB) & 1);
-            const StemTile t = stem_tile(B, u);
+            const StemTile t = cur.t;
             if (!warp_wait(&o_ready[s], ph, status, wait_ns)) break;
             const StemProb& pq = B.q[t.p];
             if (pq.gn_part) {
@@ -449,12 +521,13 @@ __global__ void __launch_bounds__(NTHREADS, 1) stem_tc_kernel(const __grid_const
         auto swz = [](int r) { return CPR == 4 ? ((r >> 1) & 3) : ((r >> 2) & 1); };
         const int crow = lane / CPR, cchk = lane % CPR;
         int it = 0;
-        StemTile tn = stem_tile(B, cid < B.num_tiles ? cid : 0);
-        for (long long u = cid; u < B.num_tiles; u += ncl, ++it) {
+        StemCursor<MAXP> cur;
+        cur.start(B, cid, (int)ncl);
+        while (cur.u < B.num_tiles) {
             const int s = it & 1;
             const uint32_t ph = (uint32_t)((it >> 1) & 1);
             const int sb = it % NSB;
-            const StemTile t = tn;
+            const StemTile t = cur.t;
             if (!warp_wait(&t_full[s], ph, status, wait_ns)) break;
             tc_fence_after();
             const StemProb& pq = B.q[t.p];
@@ -487,7 +560,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) stem_tc_kernel(const __grid_const
             }
             // statistics: (sum, sum of squares) of the shifted values per group, into the
             // buffer the statistics warp has released (every tile passes both barriers)
-            if (u + ncl < B.num_tiles) tn = stem_tile(B, u + ncl);  // the next tile's coordinates, early
+            cur.next(B, (int)ncl);  // the next tile's coordinates, early
             if (!warp_wait(&o_free[sb], (uint32_t)(((it / NSB) & 1) ^ 1), status, wait_ns)) break;
             const bool gstat = pq.gn_part != nullptr;
             uint64_t sq[NG];
@@ -503,21 +576,10 @@ __global__ void __launch_bounds__(NTHREADS, 1) stem_tc_kernel(const __grid_const
                     stk[1] = make_float4(Kg[4], Kg[5], Kg[6], Kg[7]);
                 }
                 const float m = v < nvalid ? 1.f : 0.f;
-                const uint64_t M = f2(m, m);
-#pragma unroll
-                for (int g = 0; g < NG; ++g) {
-                    const uint64_t x0 = bf2_to_f2(pk[g * WPG]);
-                    const uint64_t KK = f2(Kg[g], Kg[g]);
-                    uint64_t d = mul2(sub2(x0, KK), M);
-                    uint64_t s2 = d, q2 = mul2(d, d);
-#pragma unroll
-                    for (int j = 1; j < WPG; ++j) {
-                        d = mul2(sub2(bf2_to_f2(pk[g * WPG + j]), KK), M);
-                        s2 = add2(s2, d);
-                        q2 = fma2(d, d, q2);
-                    }
-                    sq[g] = f2(f2_lo(s2) + f2_hi(s2), f2_lo(q2) + f2_hi(q2));
-                }
+                if (nvalid == SV)  // a whole tile (uniform over the CTA): no weights
+                    group_sums<NG, WPG, false>(pk, Kg, 0ull, sq);
+                else
+                    group_sums<NG, WPG, true>(pk, Kg, f2(m, m), sq);
                 // step o: a lane keeps the lower (upper if lane & o) half of its groups and
                 // adds its partner's sums of them; then lanes 4g .. 4g + 3 sum group g
 #pragma unroll
@@ -558,6 +620,7 @@ __global__ void __launch_bounds__(NTHREADS, 1) stem_tc_kernel(const __grid_const
                 }
             }
             __syncwarp();
+            ++it;
         }
     }
 
