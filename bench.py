@@ -51,7 +51,7 @@ CONV_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the 
 # algorithmic bytes (the BF16 pixels read once, its output written once).
 STEM_DRAM_BYTES_PER_STEP = 0.940e9
 STEM_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the stem launch of a 1x3x5x720x1280 "
-                       "encode (32.2 + 244.1 MB), times 17/5")
+                       "encode (32.3 + 243.3 MB), times 17/5")
 
 
 def load_peaks():
@@ -277,8 +277,8 @@ def gpu_arm(args):
                  "algorithmic_bytes": stem_alg, "achieved_gbs": stem_gbs, "peak_gbs": float(peaks["hbm_gbs"]),
                  "frac": stem_gbs / float(peaks["hbm_gbs"]), "traffic": STEM_DRAM_BYTES_PER_STEP,
                  "traffic_source": STEM_TRAFFIC_SOURCE,
-                 "note": "bound by instruction issue in its epilogue (about 9300 warp instructions per "
-                         "128-voxel tile, 64% issue active under ncu), not by HBM"},
+                 "note": "bound by instruction issue in its epilogue (about 8300 warp instructions per "
+                         "128-voxel tile, 61% issue active under ncu), not by HBM"},
         "groupnorm": {"ms_per_step": prof["gn_ms"] / args.steps,
                       "achieved_gbs": prof["gn_bytes"] / (prof["gn_ms"] / 1e3) / 1e9 if prof["gn_ms"] else 0.0,
                       "peak_gbs": float(peaks["hbm_gbs"])},
