@@ -495,8 +495,10 @@ int tok_selftest_guards(tok_ctx* ctx);
  * named layer, that layer's tensors into the caller's device buffers with
  * device-to-device copies on the call's stream:
  *   conv layers ("enc.stem", "enc.l0.b0.c1", "enc.down0", "dec.up1", ...):
- *     d_in  <- its input activation (N,T,H,W,Cin) (the im2col matrix for the
- *              stem and the decoder input of the BF16 path),
+ *     d_in  <- its input activation (N,T,H,W,Cin) (for the BF16 path: the
+ *              pixels for the stem where it forms its im2col rows on chip,
+ *              the im2col matrix where the stem's frame needs edge extension,
+ *              and the im2col matrix for the decoder input),
  *     d_res <- the residual it adds (same shape as the output), when it adds one,
  *     d_out <- its output: (N,T,H,W,Cout) bf16/fp32, after depth-to-space for
  *              the up convs and the pixel head, the latent z (fp32) for
