@@ -123,3 +123,61 @@ def test_stem_stream_equals_clip(P, ts):
     assert tk.check_guards() == 0
     tk.close()
     assert torch.equal(torch.cat(outs, 1), clip)
+
+
+def _stem_voxel(x, w, b, t, h, wv, ts):
+    """Oracle value (all channels) of stem output voxel (t, h, wv) of the pixels x (a
+    host array): its 3 x 3 x 3 neighbourhood of pixels (frames before 0 replicate frame 0, zeros outside the
+    frame) through the oracle's conv, read at the block's causal centre."""
+    _, Tn, Hn, Wn, C = x.shape
+    blk = np.zeros((1, 3, 3, 3, C))
+    for a in range(3):
+        ti = max(0, t * ts + a - 2)
+        for r in range(3):
+            hh = 2 * h + r - 1
+            for c in range(3):
+                ww = 2 * wv + c - 1
+                if 0 <= hh < Hn and 0 <= ww < Wn:
+                    blk[0, a, r, c] = x[0, ti, hh, ww]
+    return ops.conv3d(blk, w, b, (1, 1, 1), ops.PAD_REPLICATE)[0, 2, 1, 1]
+
+
+def test_stem_1080p_sampled(P):
+    """The default tokenizer's stem on a 1x3x5x1080x1920 clip: output rows of 960
+    voxels (seven whole tiles and a ragged eighth of 64), 40 sampled voxels (frame 0,
+    the corners, the ragged tile, random) against the oracle, and frames 0 and 4 of
+    the GroupNorm+SiLU fed by the stem's statistics against the oracle's."""
+    T, H, W = 5, 1080, 1920
+    tk = P.Tokenizer("bf16")
+    params = _params(tk, 3)
+    tk.set_params(params)
+    tk.reserve(1, T, H, W)
+    x = torch.from_numpy(S.to_bf16_f32(S.blurred_noise_clip(21, 1, T, H, W))).to("cuda", torch.bfloat16)
+    stem = torch.empty((1, T, H // 2, W // 2, 128), device="cuda", dtype=torch.bfloat16)
+    gn_out = torch.empty_like(stem)
+    tk.trace_layer("enc.stem", None, None, stem)
+    tk.trace_layer("enc.l0.b0.gn1", None, None, gn_out)
+    tk.encode(x, want_z=False)
+    torch.cuda.synchronize()
+    assert tk.status() == 0
+    tk.trace_layer(None)
+    assert tk.check_guards() == 0
+    tk.close()
+    w = S.to_bf16_f32(params["enc.stem.w"]).astype(np.float64)
+    b = params["enc.stem.b"].astype(np.float64)
+    Ho, Wo = H // 2, W // 2
+    rng = np.random.default_rng(4)
+    pts = [(0, 0, 0), (0, Ho - 1, Wo - 1), (T - 1, 0, Wo - 1), (T - 1, Ho - 1, 0), (2, 100, 896), (3, 17, 959)]
+    while len(pts) < 40:
+        pts.append((int(rng.integers(0, T)), int(rng.integers(0, Ho)), int(rng.integers(0, Wo))))
+    xc = x.double().cpu().numpy()
+    ref = np.stack([_stem_voxel(xc, w, b, t, h, wv, 1) for t, h, wv in pts])
+    got = np.stack([stem[0, t, h, wv].double().cpu().numpy() for t, h, wv in pts])
+    tol = 2.0 ** -8 * np.abs(ref) + 2e-4 * np.abs(ref).max()
+    assert np.all(np.abs(got - ref) <= tol), float((np.abs(got - ref) / tol).max())
+    G = ops.gn_groups(128, 32)
+    for t in (0, T - 1):
+        xin = stem[:, t:t + 1].double().cpu().numpy()
+        r = ops.silu(ops.group_norm_frames(xin, G, 1e-6, params["enc.l0.b0.gn1.g"], params["enc.l0.b0.gn1.b"]))
+        g = gn_out[:, t:t + 1].double().cpu().numpy()
+        assert np.all(np.abs(g - r) <= 2.0 ** -8 * np.abs(r) + 4e-3), (t, float(np.abs(g - r).max()))
