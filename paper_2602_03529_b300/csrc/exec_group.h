@@ -70,7 +70,8 @@ struct GroupExec : Exec {
 
     // ------------------------------------------------------------ launches
 
-    void launch_group(ConvArgs* as, const ConvW& cw, int n = -1) {
+    // trace_first: as[0] is batch item 0, the problem a layer trace records
+    void launch_group(ConvArgs* as, const ConvW& cw, int n = -1, bool trace_first = true) {
         if (err) return;
         const int P = n < 0 ? this->P : n;
         double flop = 0;
@@ -86,7 +87,7 @@ struct GroupExec : Exec {
             c->launches += P;
         }
         pend(e, 0, flop, cw.name);
-        trace_conv(cw.name, as[0]);
+        if (trace_first) trace_conv(cw.name, as[0]);
     }
 
     void slot(int i, void** out) const {
@@ -190,7 +191,7 @@ struct GroupExec : Exec {
             out[p] = Act{outs[p], d.N, d.T, d.H, d.W, cw.Cout};
             tag_gn_stats(out[p], a);
         }
-        if (n) launch_group(as, cw, n);
+        if (n) launch_group(as, cw, n, !(skip && skip[0]));
         return out;
     }
 
@@ -312,7 +313,7 @@ struct GroupExec : Exec {
             if (!stem_tc_accepts(&as[n], 1)) continue;
             at[n++] = p;
         }
-        if (!n || !stem_launch(as, n, cw)) return;
+        if (!n || !stem_launch(as, n, cw, at[0] == 0)) return;
         for (int i = 0; i < n; ++i) {
             const int p = at[i];
             stream_update(p, name, x[p], T[p]);

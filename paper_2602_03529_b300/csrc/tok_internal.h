@@ -763,7 +763,8 @@ struct Exec {
 
     // The fused stem over as[0 .. count): false, with nothing enqueued, where a
     // problem is outside its form (the caller then gathers the im2col matrix).
-    bool stem_launch(const StemArgs* as, int count, const ConvW& cw) {
+    // trace_first: as[0] is the problem a layer trace records (batch item 0).
+    bool stem_launch(const StemArgs* as, int count, const ConvW& cw, bool trace_first = true) {
         if (!c->bf16() || !stem_tc_accepts(as, count)) return false;
         if (err) return true;
         double flop = 0;
@@ -775,7 +776,7 @@ struct Exec {
         pend(e, 0, flop, cw.name);
         c->launches += 1;
         const StemArgs& a = as[0];
-        trace(cw.name, a.x, (size_t)a.N * a.Tin * a.H * a.W * 3 * 2, nullptr, 0, a.out,
+        if (trace_first) trace(cw.name, a.x, (size_t)a.N * a.Tin * a.H * a.W * 3 * 2, nullptr, 0, a.out,
               (size_t)a.N * a.Tout * (a.H / 2) * (a.W / 2) * cw.Cout * 2);
         return true;
     }
